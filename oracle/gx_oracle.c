@@ -1,0 +1,968 @@
+/*
+ * gx_oracle.c -- plain, slow, FP64 CPU oracle of the GL-ECSIM hot path.
+ *
+ * TEST INFRASTRUCTURE.  Only the test-suite, the smoke check and the
+ * benchmark's CPU-baseline / reference arm load this library.  The product path
+ * (the CUDA library under paper_2506_11320_gb300/) never calls it, and the two
+ * share no code, header, table or constant.
+ *
+ * It follows Chen, Zhou & Toth, "Suppressing spurious oscillations and particle
+ * noise in particle-in-cell simulations" (arXiv 2506.11320), cited below by
+ * section and equation.  Sections are numbered as in the paper's source:
+ * Sec. 1.1 "Discretization of Maxwell's equations", Sec. 1.2 "Suppressing
+ * spurious oscillations", Sec. 1.4 "From smoothing fields to the Lax-Friedrichs
+ * diffusion", Sec. 2.1 "Calculating current in the comoving frame", Sec. 2.2
+ * "Smoothing the current".
+ *
+ * Everything is written at the level of the definitions: direct loops over
+ * particles and grid points, the mass matrix stored in full (every node keeps
+ * all 27 neighbour blocks, no symmetry used), the comoving current done in two
+ * passes (bulk velocity first, then the deposit of deviations from it), textbook
+ * restarted GMRES with modified Gram-Schmidt, and dense Gaussian elimination as
+ * a second solver for tiny grids.
+ *
+ * Mesh (Sec. 1.1): collocated staggered grid, E at nodes, B at cell centres.
+ * Node (i,j,k) sits at (i dx, j dy, k dz); cell (i,j,k) spans
+ * [i,i+1]x[j,j+1]x[k,k+1] cell widths.  All axes are periodic.  An axis with a
+ * single cell is "collapsed": the periodic wrap makes node i+1 the same node as
+ * node i, so derivatives along it vanish and averages along it are the identity,
+ * and the same code covers 1D, 2D and 3D.  Positions along a collapsed axis are
+ * not advanced and carry no weight.
+ *
+ * Units are Gaussian with an explicit speed of light c: Ampere's law
+ * dE/dt = c curl B - 4 pi J (Eq. 1), Faraday's law dB/dt = -c curl E (Eq. 2) and
+ * the Lorentz force q (E + v x B / c).
+ *
+ * Readings taken where the paper is silent or garbled (each is repeated at the
+ * routine that uses it):
+ *   - the shape function W is linear (cloud-in-cell) on the 2^d corner nodes;
+ *   - B is averaged from cell centres to nodes (mean of the 2^d adjacent
+ *     cells) before it is interpolated to particles with the same W as E;
+ *   - the mover is the ECSIM one: positions live at half steps,
+ *     v^{n+1} = 2 vbar - v^n, x^{n+3/2} = x^{n+1/2} + dt v^{n+1};
+ *   - the mass-term prefactor printed as 4 pi/(c dV) in Eq. 35 is read as
+ *     4 pi theta dt / dV (what substituting Jbar into Eq. 7 gives);
+ *   - Eq. 8's "c theta dt" is read as "c dt" (Eq. 5 and Eq. 13 agree);
+ *   - the implicit Lax-Friedrichs term on E (Eq. 19) enters with a minus sign
+ *     (diffusive); with the printed plus sign it would be anti-diffusive;
+ *   - the E limiter and diffusion speed are frozen at E^n, which keeps the
+ *     field equation linear;
+ *   - the 1D diffusion and filter are applied per axis and per component;
+ *   - the diffusion speed a is |u| (the smoothed bulk velocity) averaged over
+ *     the face / edge, or c for vacuum tests;
+ *   - "plasma velocity" is mass weighted over all species, 0 where no mass;
+ *   - a smoothness ratio with a zero denominator is taken as 0.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_PI 3.14159265358979323846
+
+/* Grid and method parameters.  Layout must match oracle/__init__.py. */
+typedef struct {
+    int32_t n[3];          /* cells per axis (1 = collapsed axis) */
+    int32_t comoving;      /* 1: comoving-frame current (Sec. 2.1) */
+    int32_t lf_on;         /* 1: limited Lax-Friedrichs diffusion on E and B (Sec. 1.2) */
+    int32_t lf_speed_c;    /* 1: diffusion speed a = c; 0: a = |u| */
+    int32_t ns_j;          /* passes of the digital filter on the current (Sec. 2.2) */
+    int32_t nsmooth_u;     /* passes of the digital filter on the bulk velocity (Sec. 2.1) */
+    int32_t gmres_restart;
+    int32_t gmres_maxit;
+    int32_t _pad[2];
+    double dx[3];
+    double c;              /* speed of light */
+    double theta;          /* time centring of the theta scheme (Eq. 5-6) */
+    double dt;
+    double lf_beta;        /* MC limiter parameter beta (Eq. 21) */
+    double gmres_tol;      /* relative residual target */
+} or_cfg;
+
+/* ---------------------------------------------------------------- indexing */
+
+static inline int64_t n_nodes(const or_cfg *g) { return (int64_t)g->n[0] * g->n[1] * g->n[2]; }
+
+static inline int wrapi(int i, int n) { i %= n; return i < 0 ? i + n : i; }
+
+/* Linear index of node (or cell) (i,j,k) with periodic wrap. */
+static inline int64_t ix(const or_cfg *g, int i, int j, int k) {
+    return (int64_t)wrapi(i, g->n[0]) +
+           (int64_t)g->n[0] * ((int64_t)wrapi(j, g->n[1]) + (int64_t)g->n[1] * wrapi(k, g->n[2]));
+}
+
+static inline void unix3(const or_cfg *g, int64_t idx, int *i, int *j, int *k) {
+    *i = (int)(idx % g->n[0]);
+    *j = (int)((idx / g->n[0]) % g->n[1]);
+    *k = (int)(idx / ((int64_t)g->n[0] * g->n[1]));
+}
+
+static inline double cell_volume(const or_cfg *g) { return g->dx[0] * g->dx[1] * g->dx[2]; }
+
+/* ----------------------------------------------------------- shape function */
+
+/* Interpolation function W of Eq. 27, read as the linear (cloud-in-cell) shape:
+ * the particle's cell (lowest corner node) and the weight of each of the 8
+ * corners a = ax + 2 ay + 4 az.  Collapsed axes put all weight on corner 0. */
+static void shape(const or_cfg *g, const double pos[3], int cell[3], double w[8]) {
+    double f[3];
+    for (int d = 0; d < 3; ++d) {
+        double s = pos[d] / g->dx[d];
+        double fl = floor(s);
+        cell[d] = (int)fl;
+        f[d] = (g->n[d] == 1) ? 0.0 : s - fl;
+    }
+    for (int a = 0; a < 8; ++a) {
+        int ax = a & 1, ay = (a >> 1) & 1, az = (a >> 2) & 1;
+        w[a] = (ax ? f[0] : 1.0 - f[0]) * (ay ? f[1] : 1.0 - f[1]) * (az ? f[2] : 1.0 - f[2]);
+    }
+}
+
+static inline int64_t corner_node(const or_cfg *g, const int cell[3], int a) {
+    return ix(g, cell[0] + (a & 1), cell[1] + ((a >> 1) & 1), cell[2] + ((a >> 2) & 1));
+}
+
+/* Interpolate a 3-component node field F[3][Nn] to a particle. */
+static void gather3(const or_cfg *g, const double *F, const int cell[3], const double w[8], double out[3]) {
+    int64_t N = n_nodes(g);
+    out[0] = out[1] = out[2] = 0.0;
+    for (int a = 0; a < 8; ++a) {
+        int64_t nd = corner_node(g, cell, a);
+        for (int c = 0; c < 3; ++c) out[c] += w[a] * F[c * N + nd];
+    }
+}
+
+/* ------------------------------------------------------------ alpha tensor */
+
+/* Rotation tensor of Sec. 2.1, Eq. 30, with b = beta_s B / c (Gaussian units put
+ * the 1/c of the Lorentz force here).  Row-major 3x3 acting on a column vector:
+ * alpha a = (a + a x b + (a.b) b) / (1 + b.b).
+ * The dyadic form -beta I x B applied to a gives beta a x B, hence the + a x b. */
+void or_alpha(const double b[3], double al[9]) {
+    double D = 1.0 + b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
+    al[0] = 1.0 + b[0] * b[0]; al[1] = b[2] + b[0] * b[1];  al[2] = -b[1] + b[0] * b[2];
+    al[3] = -b[2] + b[1] * b[0]; al[4] = 1.0 + b[1] * b[1]; al[5] = b[0] + b[1] * b[2];
+    al[6] = b[1] + b[2] * b[0];  al[7] = -b[0] + b[2] * b[1]; al[8] = 1.0 + b[2] * b[2];
+    for (int i = 0; i < 9; ++i) al[i] /= D;
+}
+
+static void matvec3(const double A[9], const double v[3], double out[3]) {
+    for (int i = 0; i < 3; ++i) out[i] = A[3 * i] * v[0] + A[3 * i + 1] * v[1] + A[3 * i + 2] * v[2];
+}
+
+/* ---------------------------------------------------------- grid averaging */
+
+/* B from cell centres to nodes: the mean of the 8 cells around each node
+ * (reading: the paper keeps B at cell centres and does not say how it reaches
+ * the particles; it is averaged to nodes and then interpolated with W). */
+void or_node_avg(const or_cfg *g, const double *Bc, double *Bn) {
+    int64_t N = n_nodes(g);
+    for (int64_t nd = 0; nd < N; ++nd) {
+        int i, j, k;
+        unix3(g, nd, &i, &j, &k);
+        for (int c = 0; c < 3; ++c) {
+            double s = 0.0;
+            for (int a = 0; a < 8; ++a)
+                s += Bc[c * N + ix(g, i - 1 + (a & 1), j - 1 + ((a >> 1) & 1), k - 1 + ((a >> 2) & 1))];
+            Bn[c * N + nd] = s / 8.0;
+        }
+    }
+}
+
+/* ------------------------------------------------------------ digital filter */
+
+/* One pass of the digital filter of Sec. 1.4, Eq. 26,
+ * v*_i = phi v_i + (1-phi)/2 (v_{i-d} + v_{i+d}), on a node field of ncomp
+ * components.  Its multi-dimensional form is not stated; it is applied along
+ * x, then y, then z, each sweep acting on the result of the previous one. */
+void or_filter(const or_cfg *g, double *f, int ncomp, int d, double phi) {
+    int64_t N = n_nodes(g);
+    double *tmp = (double *)malloc(sizeof(double) * N);
+    for (int c = 0; c < ncomp; ++c) {
+        double *v = f + c * N;
+        for (int ax = 0; ax < 3; ++ax) {
+            if (g->n[ax] == 1) continue;
+            for (int64_t nd = 0; nd < N; ++nd) {
+                int i, j, k;
+                unix3(g, nd, &i, &j, &k);
+                int p[3] = {i, j, k}, m[3] = {i, j, k};
+                p[ax] += d;
+                m[ax] -= d;
+                tmp[nd] = phi * v[nd] + 0.5 * (1.0 - phi) * (v[ix(g, m[0], m[1], m[2])] + v[ix(g, p[0], p[1], p[2])]);
+            }
+            memcpy(v, tmp, sizeof(double) * N);
+        }
+    }
+    free(tmp);
+}
+
+/* ------------------------------------------------------- particle moments */
+
+/* Mass density and momentum density at nodes (numerators of the plasma
+ * velocity of Sec. 2.1): rho_m = sum m_p W_pg, P = sum m_p v_p W_pg over all
+ * species.  Reading: the "plasma velocity" is mass weighted. */
+void or_bulk_moments(const or_cfg *g, const double *qs, const double *ms, int64_t np,
+                     const int32_t *sp, const double *x, const double *y, const double *z,
+                     const double *vx, const double *vy, const double *vz, const double *w,
+                     double *rho_m, double *P) {
+    (void)qs;
+    int64_t N = n_nodes(g);
+    memset(rho_m, 0, sizeof(double) * N);
+    memset(P, 0, sizeof(double) * 3 * N);
+    for (int64_t p = 0; p < np; ++p) {
+        double pos[3] = {x[p], y[p], z[p]}, W[8];
+        int cell[3];
+        shape(g, pos, cell, W);
+        double mp = ms[sp[p]] * w[p];
+        for (int a = 0; a < 8; ++a) {
+            int64_t nd = corner_node(g, cell, a);
+            rho_m[nd] += mp * W[a];
+            P[nd] += mp * vx[p] * W[a];
+            P[N + nd] += mp * vy[p] * W[a];
+            P[2 * N + nd] += mp * vz[p] * W[a];
+        }
+    }
+}
+
+/* Comoving-frame velocity u(x) of Sec. 2.1: the plasma velocity P / rho_m
+ * (0 at nodes without mass), smoothed by nsmooth_u passes of Eq. 26 with
+ * phi = 0.5 and the stride alternating d = 1, 2, 1, 2, ... */
+void or_bulk_velocity(const or_cfg *g, const double *rho_m, const double *P, double *u) {
+    int64_t N = n_nodes(g);
+    for (int64_t nd = 0; nd < N; ++nd)
+        for (int c = 0; c < 3; ++c)
+            u[c * N + nd] = rho_m[nd] != 0.0 ? P[c * N + nd] / rho_m[nd] : 0.0;
+    for (int pass = 0; pass < g->nsmooth_u; ++pass) or_filter(g, u, 3, (pass % 2 == 0) ? 1 : 2, 0.5);
+}
+
+/* Moments the implicit field solve needs (Sec. 2.1):
+ *   rho_g = (1/dV) sum_p q_p W_pg                                   (charge density)
+ *   J_g   = (1/dV) sum_p q_p alpha_p (v_p - u(x_p)) W_pg            (Eq. 34, comoving)
+ *         = (1/dV) sum_p q_p alpha_p v_p W_pg                       (u == NULL: standard)
+ *   M_g,g' = sum_s beta_s sum_p q_p alpha_p W_pg W_pg'              (mass matrix, Eq. 33)
+ * with u(x_p) = sum_g W_pg u_g and alpha_p built from B^n at the particle.
+ * M is stored in full: M[((g * 27 + o) * 3 + i) * 3 + j], o = (ox+1) + 3 (oy+1) +
+ * 9 (oz+1) the offset of g' from g in corner steps. */
+void or_deposit(const or_cfg *g, const double *qs, const double *ms, int64_t np, const int32_t *sp,
+                const double *x, const double *y, const double *z,
+                const double *vx, const double *vy, const double *vz, const double *w,
+                const double *Bn, const double *u, double *rho, double *J, double *M) {
+    int64_t N = n_nodes(g);
+    double dV = cell_volume(g);
+    memset(rho, 0, sizeof(double) * N);
+    memset(J, 0, sizeof(double) * 3 * N);
+    memset(M, 0, sizeof(double) * N * 27 * 9);
+    for (int64_t p = 0; p < np; ++p) {
+        int s = sp[p];
+        double beta = qs[s] * g->dt / (2.0 * ms[s]);
+        double qp = qs[s] * w[p];
+        double pos[3] = {x[p], y[p], z[p]}, W[8], Bp[3], b[3], al[9];
+        int cell[3];
+        shape(g, pos, cell, W);
+        gather3(g, Bn, cell, W, Bp);
+        for (int c = 0; c < 3; ++c) b[c] = beta * Bp[c] / g->c;
+        or_alpha(b, al);
+        double dv[3] = {vx[p], vy[p], vz[p]};
+        if (u) {
+            double up[3];
+            gather3(g, u, cell, W, up);
+            for (int c = 0; c < 3; ++c) dv[c] -= up[c];
+        }
+        double adv[3];
+        matvec3(al, dv, adv);
+        for (int a = 0; a < 8; ++a) {
+            if (W[a] == 0.0) continue;
+            int64_t na = corner_node(g, cell, a);
+            rho[na] += qp * W[a] / dV;
+            for (int c = 0; c < 3; ++c) J[c * N + na] += qp * adv[c] * W[a] / dV;
+            for (int bb = 0; bb < 8; ++bb) {
+                if (W[bb] == 0.0) continue;
+                int o = ((bb & 1) - (a & 1) + 1) + 3 * (((bb >> 1) & 1) - ((a >> 1) & 1) + 1) +
+                        9 * (((bb >> 2) & 1) - ((a >> 2) & 1) + 1);
+                double f = beta * qp * W[a] * W[bb];
+                double *blk = M + ((na * 27 + o) * 9);
+                for (int e = 0; e < 9; ++e) blk[e] += f * al[e];
+            }
+        }
+    }
+}
+
+/* ns_j passes of the digital filter (Eq. 26, phi = 0.5, d = 1) on the current,
+ * Sec. 2.2. */
+void or_smooth_current(const or_cfg *g, double *J, int ns_j) {
+    for (int pass = 0; pass < ns_j; ++pass) or_filter(g, J, 3, 1, 0.5);
+}
+
+/* ------------------------------------------------------ discrete operators */
+
+/* Derivative along axis d of a node field, evaluated at cell (i,j,k): the mean
+ * of the 4 nodes on the cell's +d face minus the mean on its -d face, over dx_d.
+ * (Collocated staggered mesh of Sec. 1.1.) */
+static double dC(const or_cfg *g, const double *f, int i, int j, int k, int d) {
+    double s = 0.0;
+    for (int a = 0; a < 8; ++a) {
+        int o[3] = {a & 1, (a >> 1) & 1, (a >> 2) & 1};
+        double sgn = o[d] ? 1.0 : -1.0;
+        s += sgn * f[ix(g, i + o[0], j + o[1], k + o[2])];
+    }
+    return s / (4.0 * g->dx[d]);
+}
+
+/* Derivative along axis d of a cell field, evaluated at node (i,j,k): the mean
+ * of the 4 cells on the node's +d side minus the mean on its -d side, over dx_d. */
+static double dN(const or_cfg *g, const double *f, int i, int j, int k, int d) {
+    double s = 0.0;
+    for (int a = 0; a < 8; ++a) {
+        int o[3] = {a & 1, (a >> 1) & 1, (a >> 2) & 1};
+        double sgn = o[d] ? 1.0 : -1.0;
+        s += sgn * f[ix(g, i - 1 + o[0], j - 1 + o[1], k - 1 + o[2])];
+    }
+    return s / (4.0 * g->dx[d]);
+}
+
+/* curl of a node vector field, at cell centres. */
+void or_curl_C(const or_cfg *g, const double *E, double *out) {
+    int64_t N = n_nodes(g);
+    const double *Ex = E, *Ey = E + N, *Ez = E + 2 * N;
+    for (int64_t c = 0; c < N; ++c) {
+        int i, j, k;
+        unix3(g, c, &i, &j, &k);
+        out[c] = dC(g, Ez, i, j, k, 1) - dC(g, Ey, i, j, k, 2);
+        out[N + c] = dC(g, Ex, i, j, k, 2) - dC(g, Ez, i, j, k, 0);
+        out[2 * N + c] = dC(g, Ey, i, j, k, 0) - dC(g, Ex, i, j, k, 1);
+    }
+}
+
+/* curl of a cell vector field, at nodes. */
+void or_curl_N(const or_cfg *g, const double *B, double *out) {
+    int64_t N = n_nodes(g);
+    const double *Bx = B, *By = B + N, *Bz = B + 2 * N;
+    for (int64_t nd = 0; nd < N; ++nd) {
+        int i, j, k;
+        unix3(g, nd, &i, &j, &k);
+        out[nd] = dN(g, Bz, i, j, k, 1) - dN(g, By, i, j, k, 2);
+        out[N + nd] = dN(g, Bx, i, j, k, 2) - dN(g, Bz, i, j, k, 0);
+        out[2 * N + nd] = dN(g, By, i, j, k, 0) - dN(g, Bx, i, j, k, 1);
+    }
+}
+
+/* divergence of a node vector field, at cells. */
+void or_div_C(const or_cfg *g, const double *E, double *out) {
+    int64_t N = n_nodes(g);
+    for (int64_t c = 0; c < N; ++c) {
+        int i, j, k;
+        unix3(g, c, &i, &j, &k);
+        out[c] = dC(g, E, i, j, k, 0) + dC(g, E + N, i, j, k, 1) + dC(g, E + 2 * N, i, j, k, 2);
+    }
+}
+
+/* divergence of a cell vector field, at nodes. */
+void or_div_N(const or_cfg *g, const double *B, double *out) {
+    int64_t N = n_nodes(g);
+    for (int64_t nd = 0; nd < N; ++nd) {
+        int i, j, k;
+        unix3(g, nd, &i, &j, &k);
+        out[nd] = dN(g, B, i, j, k, 0) + dN(g, B + N, i, j, k, 1) + dN(g, B + 2 * N, i, j, k, 2);
+    }
+}
+
+/* gradient of a cell scalar, at nodes. */
+void or_grad_N(const or_cfg *g, const double *f, double *out) {
+    int64_t N = n_nodes(g);
+    for (int64_t nd = 0; nd < N; ++nd) {
+        int i, j, k;
+        unix3(g, nd, &i, &j, &k);
+        for (int d = 0; d < 3; ++d) out[d * N + nd] = dN(g, f, i, j, k, d);
+    }
+}
+
+/* gradient of a node scalar, at cells. */
+void or_grad_C(const or_cfg *g, const double *f, double *out) {
+    int64_t N = n_nodes(g);
+    for (int64_t c = 0; c < N; ++c) {
+        int i, j, k;
+        unix3(g, c, &i, &j, &k);
+        for (int d = 0; d < 3; ++d) out[d * N + c] = dC(g, f, i, j, k, d);
+    }
+}
+
+/* ------------------------------------------------------------ the limiter */
+
+/* Generalised MC limiter of Sec. 1.2, Eq. 21: phi(r, beta) =
+ * max(0, min(beta r, (1+r)/2, beta)). */
+double or_mc_limiter(double r, double beta) {
+    double v = fmin(fmin(beta * r, 0.5 * (1.0 + r)), beta);
+    return v > 0.0 ? v : 0.0;
+}
+
+/* Smoothness ratio of Eq. 22 / Eq. 23; a zero denominator gives r = 0 (the flux
+ * it scales multiplies that zero difference anyway). */
+static double ratio(double prev, double cur) { return cur == 0.0 ? 0.0 : prev / cur; }
+
+static double umag(const or_cfg *g, const double *u, int64_t nd) {
+    int64_t N = n_nodes(g);
+    return sqrt(u[nd] * u[nd] + u[N + nd] * u[N + nd] + u[2 * N + nd] * u[2 * N + nd]);
+}
+
+/* Diffusion coefficients kappa = (1 - phi_E) a / 2 of the implicit
+ * Lax-Friedrichs term on E (Sec. 1.2, Eq. 19-20), on every edge from node g to
+ * its +d neighbour, for each component: kappa[(d * 3 + comp) * Nn + g].
+ * Readings: phi_E and a are frozen at E^n (keeps the solve linear); the 1D term
+ * is applied per axis and component, with r taken along that axis (Eq. 23 with
+ * the paper's left-biased stencil); a = |u| averaged over the edge's two nodes,
+ * or c. */
+void or_lf_kappa_E(const or_cfg *g, const double *En, const double *u, double *kappa) {
+    int64_t N = n_nodes(g);
+    memset(kappa, 0, sizeof(double) * 9 * N);
+    for (int d = 0; d < 3; ++d) {
+        if (g->n[d] == 1) continue;
+        for (int comp = 0; comp < 3; ++comp) {
+            const double *E = En + comp * N;
+            for (int64_t nd = 0; nd < N; ++nd) {
+                int i, j, k;
+                unix3(g, nd, &i, &j, &k);
+                int p[3] = {i, j, k}, m[3] = {i, j, k};
+                p[d] += 1;
+                m[d] -= 1;
+                int64_t np_ = ix(g, p[0], p[1], p[2]), nm = ix(g, m[0], m[1], m[2]);
+                double r = ratio(E[nd] - E[nm], E[np_] - E[nd]);
+                double phi = or_mc_limiter(r, g->lf_beta);
+                double a = g->lf_speed_c ? g->c : 0.5 * (umag(g, u, nd) + umag(g, u, np_));
+                kappa[(d * 3 + comp) * N + nd] = (1.0 - phi) * a / 2.0;
+            }
+        }
+    }
+}
+
+/* The implicit field operator of Sec. 1.2 and Sec. 2.1 (Eq. 7 with the mass
+ * term of Eq. 35 and the diffusion of Eq. 19):
+ *   A E = E + (c theta dt)^2 curl_N curl_C E + (4 pi theta dt / dV) M E
+ *         - theta dt sum_d (1/dx_d) [kappa_+ (E_+ - E) - kappa_- (E - E_-)]
+ * curl_N curl_C equals grad(div) - lap on this mesh.  kappa == NULL: no
+ * diffusion term.  M == NULL: vacuum. */
+void or_apply_A(const or_cfg *g, const double *M, const double *kappa, const double *E, double *out) {
+    int64_t N = n_nodes(g);
+    double *cC = (double *)malloc(sizeof(double) * 3 * N);
+    double *cc = (double *)malloc(sizeof(double) * 3 * N);
+    or_curl_C(g, E, cC);
+    or_curl_N(g, cC, cc);
+    double ct = g->c * g->theta * g->dt;
+    double mfac = 4.0 * OR_PI * g->theta * g->dt / cell_volume(g);
+    for (int64_t q = 0; q < 3 * N; ++q) out[q] = E[q] + ct * ct * cc[q];
+    if (M) {
+        for (int64_t nd = 0; nd < N; ++nd) {
+            int i, j, k;
+            unix3(g, nd, &i, &j, &k);
+            for (int o = 0; o < 27; ++o) {
+                int64_t nb = ix(g, i + (o % 3) - 1, j + (o / 3) % 3 - 1, k + o / 9 - 1);
+                const double *blk = M + (nd * 27 + o) * 9;
+                for (int r = 0; r < 3; ++r)
+                    for (int c = 0; c < 3; ++c) out[r * N + nd] += mfac * blk[3 * r + c] * E[c * N + nb];
+            }
+        }
+    }
+    if (kappa) {
+        for (int d = 0; d < 3; ++d) {
+            if (g->n[d] == 1) continue;
+            double f = g->theta * g->dt / g->dx[d];
+            for (int comp = 0; comp < 3; ++comp) {
+                const double *Ec = E + comp * N;
+                const double *kp = kappa + (d * 3 + comp) * N;
+                for (int64_t nd = 0; nd < N; ++nd) {
+                    int i, j, k;
+                    unix3(g, nd, &i, &j, &k);
+                    int p[3] = {i, j, k}, m[3] = {i, j, k};
+                    p[d] += 1;
+                    m[d] -= 1;
+                    int64_t np_ = ix(g, p[0], p[1], p[2]), nm = ix(g, m[0], m[1], m[2]);
+                    out[comp * N + nd] -= f * (kp[nd] * (Ec[np_] - Ec[nd]) - kp[nm] * (Ec[nd] - Ec[nm]));
+                }
+            }
+        }
+    }
+    free(cC);
+    free(cc);
+}
+
+/* Right-hand side of the E solve (Eq. 7; comoving form Eq. 35):
+ *   b = E^n + c theta dt [curl_N B^n - (4 pi / c)(J - (1/dV) M E_M)]
+ * with J the comoving current and E_M = -u x B^n / c the motional field at
+ * nodes (B^n node averaged) when comoving != 0, and J the standard predicted-
+ * current part without the E_M term otherwise. */
+void or_rhs(const or_cfg *g, const double *En, const double *Bc, const double *J, const double *M,
+            const double *u, const double *Bn, double *b) {
+    int64_t N = n_nodes(g);
+    double *cn = (double *)malloc(sizeof(double) * 3 * N);
+    or_curl_N(g, Bc, cn);
+    double ct = g->c * g->theta * g->dt;
+    double jf = 4.0 * OR_PI * g->theta * g->dt;
+    for (int64_t q = 0; q < 3 * N; ++q) b[q] = En[q] + ct * cn[q] - jf * J[q];
+    if (g->comoving && M) {
+        double *EM = (double *)malloc(sizeof(double) * 3 * N);
+        for (int64_t nd = 0; nd < N; ++nd) {
+            double ux = u[nd], uy = u[N + nd], uz = u[2 * N + nd];
+            double bx = Bn[nd], by = Bn[N + nd], bz = Bn[2 * N + nd];
+            EM[nd] = -(uy * bz - uz * by) / g->c;
+            EM[N + nd] = -(uz * bx - ux * bz) / g->c;
+            EM[2 * N + nd] = -(ux * by - uy * bx) / g->c;
+        }
+        double mf = jf / cell_volume(g);
+        for (int64_t nd = 0; nd < N; ++nd) {
+            int i, j, k;
+            unix3(g, nd, &i, &j, &k);
+            for (int o = 0; o < 27; ++o) {
+                int64_t nb = ix(g, i + (o % 3) - 1, j + (o / 3) % 3 - 1, k + o / 9 - 1);
+                const double *blk = M + (nd * 27 + o) * 9;
+                for (int r = 0; r < 3; ++r)
+                    for (int c = 0; c < 3; ++c) b[r * N + nd] += mf * blk[3 * r + c] * EM[c * N + nb];
+            }
+        }
+        free(EM);
+    }
+    free(cn);
+}
+
+/* ------------------------------------------------------------------ solvers */
+
+static double dot(int64_t n, const double *a, const double *b) {
+    double s = 0.0;
+    for (int64_t i = 0; i < n; ++i) s += a[i] * b[i];
+    return s;
+}
+
+/* Restarted GMRES(m) with modified Gram-Schmidt and Givens rotations (the
+ * paper names no solver; the field equation is non-symmetric because alpha is).
+ * x holds the initial guess on entry and the solution on exit.  Stops when the
+ * relative residual ||b - A x|| / ||b|| reaches gmres_tol or after gmres_maxit
+ * matrix-vector products.  Returns 0 if converged, 1 otherwise; writes the true
+ * final relative residual and the number of products. */
+int or_gmres(const or_cfg *g, const double *M, const double *kappa, const double *b, double *x,
+             double *relres, int *iters) {
+    int64_t n = 3 * n_nodes(g);
+    int m = g->gmres_restart;
+    double *V = (double *)malloc(sizeof(double) * n * (m + 1));
+    double *H = (double *)calloc((size_t)(m + 1) * m, sizeof(double));
+    double *cs = (double *)malloc(sizeof(double) * m), *sn = (double *)malloc(sizeof(double) * m);
+    double *gg = (double *)malloc(sizeof(double) * (m + 1)), *y = (double *)malloc(sizeof(double) * m);
+    double *r = (double *)malloc(sizeof(double) * n);
+    double bnorm = sqrt(dot(n, b, b));
+    int total = 0, conv = 0;
+    if (bnorm == 0.0) {
+        memset(x, 0, sizeof(double) * n);
+        *relres = 0.0;
+        *iters = 0;
+        free(V); free(H); free(cs); free(sn); free(gg); free(y); free(r);
+        return 0;
+    }
+    for (;;) {
+        or_apply_A(g, M, kappa, x, r);
+        for (int64_t i = 0; i < n; ++i) r[i] = b[i] - r[i];
+        double beta = sqrt(dot(n, r, r));
+        if (beta / bnorm <= g->gmres_tol) { conv = 1; break; }
+        if (total >= g->gmres_maxit) break;
+        for (int64_t i = 0; i < n; ++i) V[i] = r[i] / beta;
+        memset(gg, 0, sizeof(double) * (m + 1));
+        gg[0] = beta;
+        int jend = -1;
+        for (int j = 0; j < m; ++j) {
+            double *w = V + (int64_t)(j + 1) * n;
+            or_apply_A(g, M, kappa, V + (int64_t)j * n, w);
+            ++total;
+            for (int i = 0; i <= j; ++i) {
+                double h = dot(n, w, V + (int64_t)i * n);
+                H[i * m + j] = h;
+                for (int64_t q = 0; q < n; ++q) w[q] -= h * V[(int64_t)i * n + q];
+            }
+            double hn = sqrt(dot(n, w, w));
+            H[(j + 1) * m + j] = hn;
+            if (hn > 0.0)
+                for (int64_t q = 0; q < n; ++q) w[q] /= hn;
+            for (int i = 0; i < j; ++i) {
+                double t = cs[i] * H[i * m + j] + sn[i] * H[(i + 1) * m + j];
+                H[(i + 1) * m + j] = -sn[i] * H[i * m + j] + cs[i] * H[(i + 1) * m + j];
+                H[i * m + j] = t;
+            }
+            double a = H[j * m + j], bb = H[(j + 1) * m + j];
+            double den = sqrt(a * a + bb * bb);
+            cs[j] = den == 0.0 ? 1.0 : a / den;
+            sn[j] = den == 0.0 ? 0.0 : bb / den;
+            H[j * m + j] = cs[j] * a + sn[j] * bb;
+            H[(j + 1) * m + j] = 0.0;
+            gg[j + 1] = -sn[j] * gg[j];
+            gg[j] = cs[j] * gg[j];
+            jend = j;
+            if (fabs(gg[j + 1]) / bnorm <= g->gmres_tol || total >= g->gmres_maxit || hn == 0.0) break;
+        }
+        for (int i = jend; i >= 0; --i) {
+            double s = gg[i];
+            for (int k = i + 1; k <= jend; ++k) s -= H[i * m + k] * y[k];
+            y[i] = s / H[i * m + i];
+        }
+        for (int i = 0; i <= jend; ++i)
+            for (int64_t q = 0; q < n; ++q) x[q] += y[i] * V[(int64_t)i * n + q];
+    }
+    or_apply_A(g, M, kappa, x, r);
+    for (int64_t i = 0; i < n; ++i) r[i] = b[i] - r[i];
+    *relres = sqrt(dot(n, r, r)) / bnorm;
+    *iters = total;
+    free(V); free(H); free(cs); free(sn); free(gg); free(y); free(r);
+    return conv ? 0 : 1;
+}
+
+/* Second solver for tiny grids: assemble A column by column and solve by
+ * Gaussian elimination with partial pivoting.  Returns 1 if singular. */
+int or_dense_solve(const or_cfg *g, const double *M, const double *kappa, const double *b, double *x) {
+    int64_t n = 3 * n_nodes(g);
+    double *A = (double *)malloc(sizeof(double) * n * n);
+    double *e = (double *)calloc((size_t)n, sizeof(double)), *col = (double *)malloc(sizeof(double) * n);
+    for (int64_t j = 0; j < n; ++j) {
+        e[j] = 1.0;
+        or_apply_A(g, M, kappa, e, col);
+        e[j] = 0.0;
+        for (int64_t i = 0; i < n; ++i) A[i * n + j] = col[i];
+    }
+    memcpy(x, b, sizeof(double) * n);
+    int sing = 0;
+    for (int64_t k = 0; k < n; ++k) {
+        int64_t piv = k;
+        for (int64_t i = k + 1; i < n; ++i)
+            if (fabs(A[i * n + k]) > fabs(A[piv * n + k])) piv = i;
+        if (A[piv * n + k] == 0.0) { sing = 1; break; }
+        if (piv != k) {
+            for (int64_t j = 0; j < n; ++j) { double t = A[k * n + j]; A[k * n + j] = A[piv * n + j]; A[piv * n + j] = t; }
+            double t = x[k]; x[k] = x[piv]; x[piv] = t;
+        }
+        for (int64_t i = k + 1; i < n; ++i) {
+            double f = A[i * n + k] / A[k * n + k];
+            if (f == 0.0) continue;
+            for (int64_t j = k; j < n; ++j) A[i * n + j] -= f * A[k * n + j];
+            x[i] -= f * x[k];
+        }
+    }
+    if (!sing)
+        for (int64_t i = n - 1; i >= 0; --i) {
+            double s = x[i];
+            for (int64_t j = i + 1; j < n; ++j) s -= A[i * n + j] * x[j];
+            x[i] = s / A[i * n + i];
+        }
+    free(A); free(e); free(col);
+    return sing;
+}
+
+/* ---------------------------------------------------------- field advance */
+
+/* B^{n+1} = B^n - c dt curl_C E^{n+theta} + (limited LF diffusion), Eq. 5 and
+ * Eq. 17-18 (read with c dt, not c theta dt, see Eq. 8), and
+ * E^{n+1} = (E^{n+theta} - (1-theta) E^n) / theta (Eq. 10).
+ * The LF term adds dt/dx_d (F_{c+1/2} - F_{c-1/2}) to every component along
+ * every axis, F = (1 - phi_B) a / 2 (B_{c+1} - B_c), phi_B = MC(r, beta) with
+ * r = (B_c - B_{c-1}) / (B_{c+1} - B_c) (Eq. 22), a = |u| averaged over the
+ * face's 4 nodes (or c).  u may be NULL when lf_speed_c != 0. */
+void or_advance_fields(const or_cfg *g, const double *En, const double *Bc, const double *Eth,
+                       const double *u, double *Enew, double *Bnew) {
+    int64_t N = n_nodes(g);
+    double *cc = (double *)malloc(sizeof(double) * 3 * N);
+    or_curl_C(g, Eth, cc);
+    for (int64_t q = 0; q < 3 * N; ++q) Bnew[q] = Bc[q] - g->c * g->dt * cc[q];
+    if (g->lf_on) {
+        double *F = (double *)malloc(sizeof(double) * N);
+        for (int d = 0; d < 3; ++d) {
+            if (g->n[d] == 1) continue;
+            double f = g->dt / g->dx[d];
+            for (int comp = 0; comp < 3; ++comp) {
+                const double *B = Bc + comp * N;
+                for (int64_t c = 0; c < N; ++c) {
+                    int i, j, k;
+                    unix3(g, c, &i, &j, &k);
+                    int p[3] = {i, j, k}, m[3] = {i, j, k};
+                    p[d] += 1;
+                    m[d] -= 1;
+                    int64_t cp = ix(g, p[0], p[1], p[2]), cm = ix(g, m[0], m[1], m[2]);
+                    double r = ratio(B[c] - B[cm], B[cp] - B[c]);
+                    double phi = or_mc_limiter(r, g->lf_beta);
+                    double a;
+                    if (g->lf_speed_c) {
+                        a = g->c;
+                    } else {
+                        /* face between cell c and c+e_d: nodes with index_d = c_d + 1 */
+                        double s = 0.0;
+                        for (int t = 0; t < 4; ++t) {
+                            int o[3] = {0, 0, 0};
+                            int e1 = (d + 1) % 3, e2 = (d + 2) % 3;
+                            o[d] = 1;
+                            o[e1] = t & 1;
+                            o[e2] = (t >> 1) & 1;
+                            s += umag(g, u, ix(g, i + o[0], j + o[1], k + o[2]));
+                        }
+                        a = s / 4.0;
+                    }
+                    F[c] = (1.0 - phi) * a / 2.0 * (B[cp] - B[c]);
+                }
+                for (int64_t c = 0; c < N; ++c) {
+                    int i, j, k;
+                    unix3(g, c, &i, &j, &k);
+                    int m[3] = {i, j, k};
+                    m[d] -= 1;
+                    Bnew[comp * N + c] += f * (F[c] - F[ix(g, m[0], m[1], m[2])]);
+                }
+            }
+        }
+        free(F);
+    }
+    for (int64_t q = 0; q < 3 * N; ++q) Enew[q] = (Eth[q] - (1.0 - g->theta) * En[q]) / g->theta;
+    free(cc);
+}
+
+/* ------------------------------------------------------------------- mover */
+
+/* theta-implicit mover (Sec. 2.1, Eq. 29-30 and the ECSIM update they cite):
+ * vbar = alpha (v^n + beta_s E^{n+theta}(x^{n+1/2})), v^{n+1} = 2 vbar - v^n,
+ * x^{n+3/2} = x^{n+1/2} + dt v^{n+1}, periodic wrap.  alpha uses the same
+ * node-averaged B^n as the deposit.  vbar_out (3*np, may be NULL) receives vbar.
+ * Returns the largest displacement in cell widths. */
+double or_mover(const or_cfg *g, const double *qs, const double *ms, int64_t np, const int32_t *sp,
+                double *x, double *y, double *z, double *vx, double *vy, double *vz,
+                const double *Eth, const double *Bn, double *vbar_out) {
+    double maxdisp = 0.0;
+    for (int64_t p = 0; p < np; ++p) {
+        int s = sp[p];
+        double beta = qs[s] * g->dt / (2.0 * ms[s]);
+        double pos[3] = {x[p], y[p], z[p]}, W[8], Ep[3], Bp[3], b[3], al[9];
+        int cell[3];
+        shape(g, pos, cell, W);
+        gather3(g, Eth, cell, W, Ep);
+        gather3(g, Bn, cell, W, Bp);
+        for (int c = 0; c < 3; ++c) b[c] = beta * Bp[c] / g->c;
+        or_alpha(b, al);
+        double a[3] = {vx[p] + beta * Ep[0], vy[p] + beta * Ep[1], vz[p] + beta * Ep[2]}, vb[3];
+        matvec3(al, a, vb);
+        double vn[3] = {2.0 * vb[0] - vx[p], 2.0 * vb[1] - vy[p], 2.0 * vb[2] - vz[p]};
+        if (vbar_out) { vbar_out[3 * p] = vb[0]; vbar_out[3 * p + 1] = vb[1]; vbar_out[3 * p + 2] = vb[2]; }
+        vx[p] = vn[0]; vy[p] = vn[1]; vz[p] = vn[2];
+        double *xs[3] = {x + p, y + p, z + p};
+        for (int d = 0; d < 3; ++d) {
+            if (g->n[d] == 1) continue;
+            double disp = g->dt * vn[d];
+            double L = g->n[d] * g->dx[d];
+            double xn = *xs[d] + disp;
+            xn = fmod(xn, L);
+            if (xn < 0.0) xn += L;
+            if (xn >= L) xn -= L;
+            *xs[d] = xn;
+            double dc = fabs(disp) / g->dx[d];
+            if (dc > maxdisp) maxdisp = dc;
+        }
+    }
+    return maxdisp;
+}
+
+/* -------------------------------------------------------------- diagnostics */
+
+/* out[0] = electric energy dV sum |E|^2 / 8 pi, out[1] = magnetic energy,
+ * out[2] = kinetic energy sum m_p |v|^2 / 2, out[3..5] = particle momentum. */
+void or_energy(const or_cfg *g, const double *ms, int64_t np, const int32_t *sp,
+               const double *vx, const double *vy, const double *vz, const double *w,
+               const double *E, const double *Bc, double *out) {
+    int64_t N = n_nodes(g);
+    double dV = cell_volume(g);
+    double we = 0.0, wb = 0.0, ke = 0.0, px = 0.0, py = 0.0, pz = 0.0;
+    for (int64_t q = 0; q < 3 * N; ++q) { we += E[q] * E[q]; wb += Bc[q] * Bc[q]; }
+    for (int64_t p = 0; p < np; ++p) {
+        double mp = ms[sp[p]] * w[p];
+        ke += 0.5 * mp * (vx[p] * vx[p] + vy[p] * vy[p] + vz[p] * vz[p]);
+        px += mp * vx[p]; py += mp * vy[p]; pz += mp * vz[p];
+    }
+    out[0] = we * dV / (8.0 * OR_PI);
+    out[1] = wb * dV / (8.0 * OR_PI);
+    out[2] = ke;
+    out[3] = px; out[4] = py; out[5] = pz;
+}
+
+/* ------------------------------------------------------------ one time step */
+
+/* One full step (Sec. 1.1, 1.2, 2.1, 2.2) from (x^{n+1/2}, v^n, E^n, B^n):
+ *  1. B^n averaged to nodes;
+ *  2. bulk velocity u (needed for the comoving current and for a = |u|);
+ *  3. deposit rho, J (comoving or standard), M with alpha from B^n;
+ *  4. ns_j filter passes on J;
+ *  5. LF coefficients from E^n;
+ *  6. right-hand side, GMRES from x0 = E^n -> E^{n+theta};
+ *  7. B^{n+1}, E^{n+1};
+ *  8. mover with E^{n+theta} and B^n.
+ * E and B are updated in place; particles too.  Optional outputs (may be NULL):
+ * Eth_out (3 Nn), J_out (3 Nn), M_out (Nn 27 9), u_out (3 Nn), vbar_out (3 np).
+ * stats[0] = GMRES products, stats[1] = final relative residual,
+ * stats[2] = max displacement in cells.  Returns 0 or 1 (GMRES not converged). */
+int or_step(const or_cfg *g, const double *qs, const double *ms, int64_t np, const int32_t *sp,
+            double *x, double *y, double *z, double *vx, double *vy, double *vz, const double *w,
+            double *E, double *Bc, double *Eth_out, double *J_out, double *M_out, double *u_out,
+            double *vbar_out, double *stats) {
+    int64_t N = n_nodes(g);
+    double *Bn = (double *)malloc(sizeof(double) * 3 * N);
+    double *u = (double *)calloc((size_t)(3 * N), sizeof(double));
+    double *rho = (double *)malloc(sizeof(double) * N), *J = (double *)malloc(sizeof(double) * 3 * N);
+    double *M = (double *)malloc(sizeof(double) * N * 27 * 9);
+    double *kappa = (double *)malloc(sizeof(double) * 9 * N);
+    double *b = (double *)malloc(sizeof(double) * 3 * N), *Eth = (double *)malloc(sizeof(double) * 3 * N);
+    double *En1 = (double *)malloc(sizeof(double) * 3 * N), *Bn1 = (double *)malloc(sizeof(double) * 3 * N);
+    or_node_avg(g, Bc, Bn);
+    int need_u = g->comoving || (g->lf_on && !g->lf_speed_c);
+    if (need_u) {
+        double *rm = (double *)malloc(sizeof(double) * N), *P = (double *)malloc(sizeof(double) * 3 * N);
+        or_bulk_moments(g, qs, ms, np, sp, x, y, z, vx, vy, vz, w, rm, P);
+        or_bulk_velocity(g, rm, P, u);
+        free(rm); free(P);
+    }
+    or_deposit(g, qs, ms, np, sp, x, y, z, vx, vy, vz, w, Bn, g->comoving ? u : NULL, rho, J, M);
+    or_smooth_current(g, J, g->ns_j);
+    if (g->lf_on) or_lf_kappa_E(g, E, u, kappa);
+    or_rhs(g, E, Bc, J, M, u, Bn, b);
+    memcpy(Eth, E, sizeof(double) * 3 * N);
+    double relres = 0.0;
+    int iters = 0;
+    int rc = or_gmres(g, M, g->lf_on ? kappa : NULL, b, Eth, &relres, &iters);
+    or_advance_fields(g, E, Bc, Eth, u, En1, Bn1);
+    double md = or_mover(g, qs, ms, np, sp, x, y, z, vx, vy, vz, Eth, Bn, vbar_out);
+    memcpy(E, En1, sizeof(double) * 3 * N);
+    memcpy(Bc, Bn1, sizeof(double) * 3 * N);
+    if (Eth_out) memcpy(Eth_out, Eth, sizeof(double) * 3 * N);
+    if (J_out) memcpy(J_out, J, sizeof(double) * 3 * N);
+    if (M_out) memcpy(M_out, M, sizeof(double) * N * 27 * 9);
+    if (u_out) memcpy(u_out, u, sizeof(double) * 3 * N);
+    if (stats) { stats[0] = iters; stats[1] = relres; stats[2] = md; }
+    free(Bn); free(u); free(rho); free(J); free(M); free(kappa); free(b); free(Eth); free(En1); free(Bn1);
+    return rc;
+}
+
+/* ------------------------------------------------- learned preconditioner net */
+
+/* The convolutional correction network of the learned GMRES preconditioner (an
+ * addition of this project; the paper has no such network).  Four 3x3
+ * convolutions with channel counts 3 -> 32 -> 32 -> 32 -> 3 and ReLU between
+ * them, on a 2D grid of H rows and W columns, channel-major tensors
+ * x[C][H][W].  params: for each layer l, the weights Wl[Cout][Cin][3][3] then
+ * the bias bl[Cout].  Padding is a periodic wrap (periodic != 0) or zeros. */
+static const int NET_C[5] = {3, 32, 32, 32, 3};
+
+int64_t or_net_param_count(void) {
+    int64_t n = 0;
+    for (int l = 0; l < 4; ++l) n += (int64_t)NET_C[l + 1] * NET_C[l] * 9 + NET_C[l + 1];
+    return n;
+}
+
+/* Size of the activation buffer or_net_forward needs: for layers 1-3 the
+ * pre-activation values, 3 * 32 * H * W doubles. */
+int64_t or_net_act_count(int H, int W) { return (int64_t)3 * 32 * H * W; }
+
+static double pad_at(const double *x, int H, int W, int periodic, int i, int j) {
+    if (periodic) return x[wrapi(i, H) * W + wrapi(j, W)];
+    if (i < 0 || i >= H || j < 0 || j >= W) return 0.0;
+    return x[i * W + j];
+}
+
+static void conv3x3(int H, int W, int periodic, int cin, int cout, const double *Wt, const double *bias,
+                    const double *x, double *y) {
+    for (int co = 0; co < cout; ++co)
+        for (int i = 0; i < H; ++i)
+            for (int j = 0; j < W; ++j) {
+                double s = bias[co];
+                for (int ci = 0; ci < cin; ++ci)
+                    for (int ky = 0; ky < 3; ++ky)
+                        for (int kx = 0; kx < 3; ++kx)
+                            s += Wt[((co * cin + ci) * 3 + ky) * 3 + kx] *
+                                 pad_at(x + (int64_t)ci * H * W, H, W, periodic, i + ky - 1, j + kx - 1);
+                y[((int64_t)co * H + i) * W + j] = s;
+            }
+}
+
+/* Forward pass: y = N(x).  acts (or_net_act_count doubles, may be NULL)
+ * receives the pre-activation outputs of layers 1-3. */
+void or_net_forward(int H, int W, int periodic, const double *params, const double *x, double *y, double *acts) {
+    int64_t HW = (int64_t)H * W;
+    double *a = (double *)malloc(sizeof(double) * 32 * HW), *h = (double *)malloc(sizeof(double) * 32 * HW);
+    const double *in = x;
+    const double *p = params;
+    for (int l = 0; l < 4; ++l) {
+        int cin = NET_C[l], cout = NET_C[l + 1];
+        const double *Wt = p, *bias = p + (int64_t)cout * cin * 9;
+        p = bias + cout;
+        if (l < 3) {
+            conv3x3(H, W, periodic, cin, cout, Wt, bias, in, a);   /* reads in (x or h), writes a */
+            if (acts) memcpy(acts + (int64_t)l * 32 * HW, a, sizeof(double) * 32 * HW);
+            for (int64_t q = 0; q < (int64_t)cout * HW; ++q) h[q] = a[q] > 0.0 ? a[q] : 0.0;
+            in = h;
+        } else {
+            conv3x3(H, W, periodic, cin, cout, Wt, bias, in, y);
+        }
+    }
+    free(a); free(h);
+}
+
+/* Loss L = (1/(2 Nout)) sum (N(x) - t)^2 with Nout = 3 H W, and its gradient
+ * with respect to every parameter (grad_params, same layout as params) and to
+ * the input (grad_x, may be NULL).  Returns L. */
+double or_net_loss_backward(int H, int W, int periodic, const double *params, const double *x,
+                            const double *target, double *grad_params, double *grad_x) {
+    int64_t HW = (int64_t)H * W;
+    double *acts = (double *)malloc(sizeof(double) * or_net_act_count(H, W));
+    double *y = (double *)malloc(sizeof(double) * 3 * HW);
+    or_net_forward(H, W, periodic, params, x, y, acts);
+    double nout = 3.0 * (double)HW, L = 0.0;
+    double *gy = (double *)malloc(sizeof(double) * 32 * HW);
+    for (int64_t q = 0; q < 3 * HW; ++q) {
+        double d = y[q] - target[q];
+        L += d * d;
+        gy[q] = d / nout;
+    }
+    L /= 2.0 * nout;
+    const double *Wl[4], *bl[4];
+    double *gW[4], *gb[4];
+    {
+        const double *p = params;
+        double *gp = grad_params;
+        for (int l = 0; l < 4; ++l) {
+            int cin = NET_C[l], cout = NET_C[l + 1];
+            Wl[l] = p; bl[l] = p + (int64_t)cout * cin * 9; p = bl[l] + cout;
+            gW[l] = gp; gb[l] = gp + (int64_t)cout * cin * 9; gp = gb[l] + cout;
+        }
+        memset(grad_params, 0, sizeof(double) * or_net_param_count());
+    }
+    double *gin = (double *)malloc(sizeof(double) * 32 * HW);
+    double *hin = (double *)malloc(sizeof(double) * 32 * HW);
+    for (int l = 3; l >= 0; --l) {
+        int cin = NET_C[l], cout = NET_C[l + 1];
+        /* the layer's input: x for l == 0, relu(pre-activation of layer l-1) otherwise */
+        if (l == 0) memcpy(hin, x, sizeof(double) * 3 * HW);
+        else
+            for (int64_t q = 0; q < (int64_t)cin * HW; ++q) {
+                double a = acts[(int64_t)(l - 1) * 32 * HW + q];
+                hin[q] = a > 0.0 ? a : 0.0;
+            }
+        memset(gin, 0, sizeof(double) * (int64_t)cin * HW);
+        for (int co = 0; co < cout; ++co)
+            for (int i = 0; i < H; ++i)
+                for (int j = 0; j < W; ++j) {
+                    double d = gy[((int64_t)co * H + i) * W + j];
+                    if (d == 0.0) continue;
+                    gb[l][co] += d;
+                    for (int ci = 0; ci < cin; ++ci)
+                        for (int ky = 0; ky < 3; ++ky)
+                            for (int kx = 0; kx < 3; ++kx) {
+                                int ii = i + ky - 1, jj = j + kx - 1;
+                                int64_t widx = ((co * cin + ci) * 3 + ky) * 3 + kx;
+                                if (periodic) { ii = wrapi(ii, H); jj = wrapi(jj, W); }
+                                else if (ii < 0 || ii >= H || jj < 0 || jj >= W) continue;
+                                gW[l][widx] += d * hin[((int64_t)ci * H + ii) * W + jj];
+                                gin[((int64_t)ci * H + ii) * W + jj] += d * Wl[l][widx];
+                            }
+                }
+        if (l > 0) {
+            for (int64_t q = 0; q < (int64_t)cin * HW; ++q)
+                gy[q] = acts[(int64_t)(l - 1) * 32 * HW + q] > 0.0 ? gin[q] : 0.0;
+        } else if (grad_x) {
+            memcpy(grad_x, gin, sizeof(double) * 3 * HW);
+        }
+    }
+    free(acts); free(y); free(gy); free(gin); free(hin);
+    return L;
+}

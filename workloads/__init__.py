@@ -1,0 +1,243 @@
+"""Seeded synthetic plasma workloads (inputs only).
+
+This module is the one piece shared by the CUDA path's tests/benchmark and the
+CPU oracle: it draws particles and initial fields and holds none of the
+method's arithmetic (no deposit, solve or push).  Each workload stands in for a
+paper setup whose data are not available (the paper's runs need MHD-refined
+initial states and a reconnection setup from another paper); the shapes, sizes
+and distributions follow the configurations the project is measured on.
+
+Units: Gaussian with explicit c.  Unless a workload says otherwise c = 1, ions
+have q = 1, m = 1 and the reference density is n0 = 1/(4 pi), so that the ion
+plasma frequency and the ion inertial length are 1.  Electrons have q = -1 and
+m = 1 / mass_ratio.  A species of density n with ppc particles per cell gets
+weights w = n dV / ppc, so the charge density it deposits is q n.
+
+Random numbers: numpy Generator(Philox(seed + species index)).  Positions are
+uniform within each cell, velocities are a drifting Maxwellian with per-
+component standard deviation vth.  Positions are returned in float64 (global
+coordinates), velocities and weights in float32 (the particle precision of the
+GPU path; the oracle promotes the very same float32 values to float64).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+N0 = 1.0 / (4.0 * math.pi)
+
+
+@dataclass
+class Workload:
+    name: str
+    n: tuple                 # cells per axis (nx, ny, nz); nz == 1 -> 2D
+    dx: tuple
+    c: float
+    theta: float
+    dt: float
+    comoving: int
+    lf_on: int
+    lf_beta: float
+    lf_speed_c: int
+    ns_j: int
+    nsmooth_u: int
+    gmres_tol: float
+    species: list            # dicts: q, m, x, y, z (f64), vx, vy, vz, w (f32)
+    E0: np.ndarray           # (3, nz, ny, nx) at nodes
+    B0: np.ndarray           # (3, nz, ny, nx) at cell centres
+    steps: int = 10
+    notes: dict = field(default_factory=dict)
+
+    @property
+    def dim(self):
+        return 3 if self.n[2] > 1 else 2
+
+    @property
+    def n_particles(self):
+        return sum(len(s["x"]) for s in self.species)
+
+    def grid_kwargs(self):
+        return dict(c=self.c, theta=self.theta, dt=self.dt, comoving=self.comoving, lf_on=self.lf_on,
+                    lf_beta=self.lf_beta, lf_speed_c=self.lf_speed_c, ns_j=self.ns_j,
+                    nsmooth_u=self.nsmooth_u, gmres_tol=self.gmres_tol)
+
+
+def _rng(seed, k):
+    return np.random.Generator(np.random.Philox(seed + k))
+
+
+def _uniform_positions(rng, n, dx, ppc):
+    """ppc particles uniformly distributed inside every cell."""
+    nx, ny, nz = n
+    ncell = nx * ny * nz
+    cid = np.repeat(np.arange(ncell, dtype=np.int64), ppc)
+    i = cid % nx
+    j = (cid // nx) % ny
+    k = cid // (nx * ny)
+    off = rng.random((3, cid.size), dtype=np.float32).astype(np.float64)
+    x = (i + off[0]) * dx[0]
+    y = (j + off[1]) * dx[1]
+    z = (k + off[2]) * dx[2] if nz > 1 else np.zeros(cid.size)
+    return x, y, z
+
+
+def _maxwellian(rng, count, u, vth):
+    v = rng.standard_normal((3, count), dtype=np.float64) * vth
+    return [(v[d] + u[d]).astype(np.float32) for d in range(3)]
+
+
+def drifting_species(n, dx, ppc, *, q, m, density, u, vth, seed, k):
+    rng = _rng(seed, k)
+    x, y, z = _uniform_positions(rng, n, dx, ppc)
+    vx, vy, vz = _maxwellian(rng, x.size, u, vth)
+    dV = dx[0] * dx[1] * dx[2]
+    w = np.full(x.size, density * dV / ppc, np.float32)
+    return dict(q=float(q), m=float(m), x=x, y=y, z=z, vx=vx, vy=vy, vz=vz, w=w)
+
+
+def _uniform_fields(n, c, u, B):
+    nx, ny, nz = n
+    Bc = np.zeros((3, nz, ny, nx))
+    E = np.zeros((3, nz, ny, nx))
+    for d in range(3):
+        Bc[d] = B[d]
+    # initial electric field: the motional field -u x B / c of the drifting
+    # plasma, with u rounded to float32 exactly as the particles carry it
+    u32 = np.asarray(u, np.float32).astype(np.float64)
+    Em = -np.cross(u32, np.asarray(B, float)) / c
+    for d in range(3):
+        E[d] = Em[d]
+    return E, Bc
+
+
+def uniform_drift(n=(32, 32, 1), dx=(0.1, 0.1, 1.0), ppc=64, mass_ratio=25.0, vth_e=0.05, vth_i=0.01,
+                  u=(0.3, 0.0, 0.0), B=(0.0, 0.0, 0.1), dt=None, theta=0.5, comoving=1, lf_on=1,
+                  lf_beta=1.0, ns_j=0, nsmooth_u=5, gmres_tol=1e-8, seed=12345, name="uniform_drift",
+                  steps=10):
+    """Periodic drifting Maxwellian electron-ion plasma in a uniform B.
+
+    Defaults are the 2D 32x32 case: dx = 0.1 d_i, m_i/m_e = 25, 64 particles per
+    cell per species, vth_e = 0.05 c, vth_i = 0.01 c, bulk drift 0.3 c along x,
+    B = 0.1 along z, theta = 0.5, dt = 0.1 / omega_pe, comoving current and
+    limited LF on, GMRES to 1e-8.  With nz > 1 it is the 3D periodic cube.
+    """
+    n = tuple(n)
+    c = 1.0
+    wpe = math.sqrt(mass_ratio)          # omega_pi = 1 at n0 = 1/(4 pi)
+    if dt is None:
+        dt = 0.1 / wpe
+    ions = drifting_species(n, dx, ppc, q=1.0, m=1.0, density=N0, u=u, vth=vth_i, seed=seed, k=0)
+    elec = drifting_species(n, dx, ppc, q=-1.0, m=1.0 / mass_ratio, density=N0, u=u, vth=vth_e, seed=seed, k=1)
+    E, Bc = _uniform_fields(n, c, u, B)
+    return Workload(name=name, n=n, dx=tuple(dx), c=c, theta=theta, dt=dt, comoving=comoving, lf_on=lf_on,
+                    lf_beta=lf_beta, lf_speed_c=0, ns_j=ns_j, nsmooth_u=nsmooth_u, gmres_tol=gmres_tol,
+                    species=[elec, ions], E0=E, B0=Bc, steps=steps,
+                    notes=dict(mass_ratio=mass_ratio, ppc=ppc, u=list(u), B=list(B), vth_e=vth_e, vth_i=vth_i))
+
+
+def config_small(**kw):
+    """2D periodic 32x32 cells, 64 particles/cell/species, 10 steps."""
+    return uniform_drift(name="periodic_32x32_ppc64", **kw)
+
+
+def uniform_3d(ncell=128, ppc=64, **kw):
+    """3D periodic ncell^3 drifting Maxwellian (u = 0.3 c, vth_e = 0.05 c,
+    m_i/m_e = 25, B = 0.1 along z), ppc particles/cell/species."""
+    kw.setdefault("name", f"periodic3d_{ncell}^3_ppc{ppc}")
+    return uniform_drift(n=(ncell, ncell, ncell), dx=(0.1, 0.1, 0.1), ppc=ppc, **kw)
+
+
+def harris(nx=512, ny=256, dx=0.05, ppc=100, mass_ratio=100.0, Ti_over_Te=5.0, nb=0.1, lam=0.5,
+           B0=0.1, psi_frac=0.1, flow_vA=0.5, dt=0.02, theta=0.5, comoving=1, lf_on=1, lf_beta=1.0,
+           ns_j=1, nsmooth_u=5, gmres_tol=1e-8, seed=12345, name=None, steps=5000):
+    """Periodic double Harris sheet for reconnection (x-y plane, B along x).
+
+    Sheet half-width lam = 0.5 d_i, background density nb = 0.1 (in units of
+    n0), m_i/m_e = 100, T_i/T_e = 5 with pressure balance, psi perturbation of
+    10 %, a bulk flow of 0.5 v_A along x superposed on every particle, and
+    ppc particles per cell per species with weights proportional to the local
+    density.  The field amplitude is taken as B0 = 0.1 in units where c = 1 and
+    omega_pi(n0) = 1, i.e. v_A / c = 0.1.
+    """
+    n = (nx, ny, 1)
+    dxs = (dx, dx, 1.0)
+    c = 1.0
+    Lx, Ly = nx * dx, ny * dx
+    y1, y2 = 0.25 * Ly, 0.75 * Ly
+    T_tot = B0 ** 2 / (8 * math.pi * N0)          # n0 (Ti + Te) = B0^2 / 8 pi
+    Te = T_tot / (1.0 + Ti_over_Te)
+    Ti = T_tot - Te
+    vA = B0 / math.sqrt(4 * math.pi * N0 * 1.0)
+    ux = flow_vA * vA
+    psi0 = psi_frac * B0 * lam
+    dV = dxs[0] * dxs[1] * dxs[2]
+
+    def sech2(s):
+        return 1.0 / np.cosh(s) ** 2
+
+    species = []
+    for k, (q, m, T) in enumerate(((-1.0, 1.0 / mass_ratio, Te), (1.0, 1.0, Ti))):
+        rng = _rng(seed, k)
+        x, y, z = _uniform_positions(rng, n, dxs, ppc)
+        s1 = sech2((y - y1) / lam)
+        s2 = sech2((y - y2) / lam)
+        dens = nb + s1 + s2                              # in units of n0
+        w = (dens * N0 * dV / ppc).astype(np.float32)
+        vth = math.sqrt(T / m)
+        ud = 2.0 * c * T / (q * B0 * lam)                # Harris drift of the sheet population
+        pick = rng.random(x.size)
+        in1 = pick < s1 / dens
+        in2 = (~in1) & (pick < (s1 + s2) / dens)
+        uz = np.where(in1, ud, np.where(in2, -ud, 0.0))
+        v = rng.standard_normal((3, x.size)) * vth
+        species.append(dict(q=q, m=m, x=x, y=y, z=z,
+                            vx=(v[0] + ux).astype(np.float32), vy=v[1].astype(np.float32),
+                            vz=(v[2] + uz).astype(np.float32), w=w))
+
+    # fields: B at cell centres, E = -u x B / c at nodes (flow along x only)
+    xc = (np.arange(nx) + 0.5) * dx
+    yc = (np.arange(ny) + 0.5) * dx
+    xn = np.arange(nx) * dx
+    yn = np.arange(ny) * dx
+
+    def bfield(X, Y):
+        bx = B0 * (np.tanh((Y - y1) / lam) - np.tanh((Y - y2) / lam) - 1.0)
+        kx, ky = 2 * math.pi / Lx, 4 * math.pi / Ly
+        bx = bx + psi0 * ky * np.cos(kx * X) * np.sin(ky * Y)     # -d psi / dy
+        by = -psi0 * kx * np.sin(kx * X) * np.cos(ky * Y)          # d psi / dx
+        return bx, by
+
+    Xc, Yc = np.meshgrid(xc, yc)
+    bx, by = bfield(Xc, Yc)
+    Bc = np.zeros((3, 1, ny, nx))
+    Bc[0, 0], Bc[1, 0] = bx, by
+    Xn, Yn = np.meshgrid(xn, yn)
+    bxn, byn = bfield(Xn, Yn)
+    E = np.zeros((3, 1, ny, nx))
+    E[2, 0] = -(ux * byn) / c
+    return Workload(name=name or f"harris_{nx}x{ny}_ppc{ppc}", n=n, dx=dxs, c=c, theta=theta, dt=dt,
+                    comoving=comoving, lf_on=lf_on, lf_beta=lf_beta, lf_speed_c=0, ns_j=ns_j,
+                    nsmooth_u=nsmooth_u, gmres_tol=gmres_tol, species=species, E0=E, B0=Bc, steps=steps,
+                    notes=dict(mass_ratio=mass_ratio, ppc=ppc, Te=Te, Ti=Ti, vA=vA, ux=ux, lam=lam, nb=nb))
+
+
+def tophat_1d(n=80, dx=0.01, cfl=0.4, lf_on=1, lf_beta=1.0, theta=0.5):
+    """Vacuum light wave with a top-hat E_y = B_z = 1 for |x| < 0.2 on
+    [-0.4, 0.4) (shifted to [0, 0.8)), c = 1; the advection test of Sec. 3.1."""
+    c = 1.0
+    dt = cfl * dx / c
+    L = n * dx
+    xn = np.arange(n) * dx - 0.5 * L
+    xc = (np.arange(n) + 0.5) * dx - 0.5 * L
+    E = np.zeros((3, 1, 1, n))
+    B = np.zeros((3, 1, 1, n))
+    # B at cell centres is the cell value of the top-hat; a node sitting exactly
+    # on a jump takes the mean of the two sides, so E and B describe the same
+    # right-moving profile on the staggered mesh.
+    E[1, 0, 0] = np.where(np.isclose(np.abs(xn), 0.2), 0.5, (np.abs(xn) < 0.2).astype(float))
+    B[2, 0, 0] = (np.abs(xc) < 0.2).astype(float)
+    return Workload(name="tophat", n=(n, 1, 1), dx=(dx, 1.0, 1.0), c=c, theta=theta, dt=dt, comoving=0,
+                    lf_on=lf_on, lf_beta=lf_beta, lf_speed_c=1, ns_j=0, nsmooth_u=0, gmres_tol=1e-13,
+                    species=[], E0=E, B0=B, steps=25, notes=dict(xn=xn, xc=xc))
