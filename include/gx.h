@@ -1,0 +1,261 @@
+/*
+ * gx.h -- C ABI of the GB300 GL-ECSIM hot-path library (libgx.so).
+ *
+ * The library implements one time step of the semi-implicit particle-in-cell
+ * method of Chen, Zhou & Toth, "Suppressing spurious oscillations and particle
+ * noise in particle-in-cell simulations" (arXiv 2506.11320): the theta-implicit
+ * particle mover, the particle-to-grid moments it feeds (charge density, the
+ * comoving-frame current, the ECSIM mass matrices), and the implicit field solve
+ * with the limited Lax-Friedrichs terms.  Section and equation numbers below
+ * refer to that paper: Sec. 1.1 "Discretization of Maxwell's equations", Sec. 1.2
+ * "Suppressing spurious oscillations", Sec. 1.4 (the digital filter), Sec. 2.1
+ * "Calculating current in the comoving frame", Sec. 2.2 "Smoothing the current".
+ *
+ * Conventions shared by every entry point:
+ *   - Every function returns a status (GX_OK == 0) and never aborts or exits.
+ *     On failure gx_last_error() describes the cause; the context stays usable
+ *     unless the status is GX_ECUDA (a CUDA error: the device may need a reset).
+ *   - Pointers are borrowed: the library copies data in and out during the call
+ *     and keeps no caller pointer afterwards.  `ptr_is_device` says whether the
+ *     caller's arrays live in host memory (0, pageable or pinned) or device
+ *     memory of the context's GPU (1).  The library owns all of its device state.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *     stream).  Work is enqueued on it; calls that return host-visible results
+ *     synchronise it before returning.
+ *   - Units are Gaussian with an explicit speed of light c (Ampere's law
+ *     dE/dt = c curl B - 4 pi J, Lorentz force q (E + v x B / c)).
+ *   - Mesh (Sec. 1.1): collocated staggered grid, E at nodes, B at cell centres,
+ *     periodic in every axis.  Node (i,j,k) sits at (i dx, j dy, k dz); cell
+ *     (i,j,k) spans [i,i+1] x [j,j+1] x [k,k+1] cell widths.  Node and cell
+ *     (i,j,k) share the flat index g = i + nx (j + ny k).  Vector fields are
+ *     component-major FP64 arrays [3][nz][ny][nx].  n[2] == 1 selects the 2D
+ *     (x-y, three velocity components) path; 3D needs every n[d] >= 2.
+ */
+#ifndef GX_H
+#define GX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------- statuses */
+enum {
+    GX_OK = 0,
+    GX_EINVAL = 1,     /* bad argument or configuration */
+    GX_ENOMEM = 2,     /* device or host allocation failed */
+    GX_ECUDA = 3,      /* a CUDA runtime call or kernel failed */
+    GX_ENOCONV = 4,    /* GMRES stopped at gmres_maxit; the best iterate is kept */
+    GX_ECFL = 5,       /* a particle moved more than one cell in one step */
+    GX_ETIMEOUT = 6,   /* a bounded device-side wait gave up */
+    GX_ENOTIMPL = 7,   /* feature not available in this build */
+    GX_EOVERFLOW = 8,  /* a cell's particle bin overflowed (particles were lost) */
+    GX_ESTATE = 9      /* call out of order (e.g. push before a field solve) */
+};
+
+enum { GX_PRECOND_NONE = 0, GX_PRECOND_JACOBI = 1, GX_PRECOND_NET = 2 };
+
+typedef struct gx_ctx gx_ctx;
+
+/* Problem statement.  The method switches follow the paper:
+ *   comoving   1: the current is computed in the comoving frame (Sec. 2.1,
+ *                 Eq. 33-35): bulk velocity u first (mass-weighted plasma
+ *                 velocity smoothed by nsmooth_u passes of the digital filter of
+ *                 Eq. 26 with phi = 0.5 and strides 1,2,1,2,...), then the
+ *                 deposit of the deviations v - u(x_p).
+ *   lf_on      1: limited Lax-Friedrichs diffusion on B (explicit, Eq. 17-18)
+ *                 and E (implicit, Eq. 19-20) with the MC limiter of Eq. 21,
+ *                 parameter lf_beta; diffusion speed a = |u| (lf_speed_c = 0) or
+ *                 a = c (lf_speed_c = 1, vacuum tests).
+ *   ns_j          passes of the digital filter (phi = 0.5, d = 1) on the
+ *                 comoving current (Sec. 2.2).
+ *   theta         time centring of the theta scheme (Eq. 5-8), in [0.5, 1].
+ *   gmres_*       FGMRES(restart) on the field equation, stopping at relative
+ *                 residual gmres_tol or gmres_maxit matrix-vector products.
+ *   precond       GX_PRECOND_*: right preconditioner of the field solve.
+ *   track_ids     1: carry a 32-bit particle id through the bins (testing).
+ *   bin_slack     capacity of a cell's particle bin relative to the largest
+ *                 initial count (>= 1.2; the bins grow automatically when a
+ *                 step finds one filled above 90 %). */
+typedef struct {
+    int32_t n[3];
+    int32_t comoving;
+    int32_t lf_on;
+    int32_t lf_speed_c;
+    int32_t ns_j;
+    int32_t nsmooth_u;
+    int32_t gmres_restart;
+    int32_t gmres_maxit;
+    int32_t precond;
+    int32_t track_ids;
+    double dx[3];
+    double c;
+    double theta;
+    double dt;
+    double lf_beta;
+    double gmres_tol;
+    double bin_slack;
+} gx_config;
+
+typedef struct {
+    int32_t iters;        /* matrix-vector products of the last solve */
+    int32_t converged;    /* 1 if the relative residual reached gmres_tol */
+    double relres;        /* true relative residual ||b - A E|| / ||b||, FP64 */
+    double ms;            /* device time of the solve (CUDA events) */
+} gx_solve_stats;
+
+typedef struct {
+    double energy_E;      /* dV sum_nodes |E|^2 / 8 pi */
+    double energy_B;      /* dV sum_cells |B|^2 / 8 pi */
+    double kinetic;       /* sum_p m_p |v_p|^2 / 2 */
+    double momentum[3];   /* sum_p m_p v_p */
+    double charge;        /* sum_g rho_g dV of the current deposit */
+    double gauss_l2;      /* || div_C E - 4 pi rho_C ||_2 over cells (rho averaged to cells) */
+    double divB_l2;       /* || div_N B ||_2 over nodes */
+    int64_t n_particles;
+} gx_diag;
+
+/* ---------------------------------------------------------- life cycle */
+
+/* Create a context on the current CUDA device.  Validates cfg (GX_EINVAL with
+ * a message), allocates the field and solver state and sets E = B = 0. */
+int gx_create(const gx_config *cfg, gx_ctx **out);
+
+/* Free every device and host resource of ctx (NULL is ignored). */
+void gx_destroy(gx_ctx *ctx);
+
+const char *gx_status_string(int status);
+
+/* Description of the last failure on ctx (empty string if none); the pointer
+ * stays valid until the next call on ctx. */
+const char *gx_last_error(gx_ctx *ctx);
+
+/* ------------------------------------------------------------- set-up */
+
+/* Add a species of n macro-particles with charge q and mass m per unit weight
+ * (a particle of weight w carries q w and m w).  x, y, z are global positions
+ * (FP64; z is ignored in 2D) wrapped into the periodic box; vx, vy, vz, w are
+ * FP32.  Positions are x^{n+1/2} and velocities v^n of the ECSIM staggering.
+ * The particles are copied into cell-sorted bins.  *species_id receives the
+ * index of the new species (0, 1, ...; at most 4 species). */
+int gx_species_add(gx_ctx *ctx, double q, double m, int64_t n,
+                   const double *x, const double *y, const double *z,
+                   const float *vx, const float *vy, const float *vz, const float *w,
+                   int ptr_is_device, int *species_id);
+
+/* Set E (nodes) and B (cell centres), each FP64 [3][nz][ny][nx]. */
+int gx_fields_set(gx_ctx *ctx, const double *E, const double *B, int ptr_is_device);
+
+/* ------------------------------------------------------------- hot path */
+
+/* Deposit the moments of the current particle state (positions x^{n+1/2},
+ * velocities v^n, B^n): charge density, mass-weighted bulk velocity u
+ * (Sec. 2.1), the current (comoving, Eq. 34, or standard) smoothed by ns_j
+ * passes (Sec. 2.2), and the mass matrices M_gg' = sum_s beta_s sum_p q_p
+ * alpha_p W_pg W_pg' (Eq. 33) with alpha from Eq. 30.  Called implicitly by
+ * gx_field_solve when the moments are stale. */
+int gx_deposit(gx_ctx *ctx, void *stream);
+
+/* Solve the implicit field equation (Eq. 7 with the mass term and comoving
+ * right-hand side of Eq. 35 and the implicit LF term of Eq. 19) for
+ * E^{n+theta}, then form B^{n+1} = B^n - c dt curl E^{n+theta} (+ limited LF,
+ * Eq. 17-18) and E^{n+1} = (E^{n+theta} - (1-theta) E^n) / theta (Eq. 10).
+ * The new fields become current only at the next gx_push_and_deposit.
+ * Returns GX_ENOCONV (best iterate kept) if gmres_maxit was reached.
+ * stats may be NULL. */
+int gx_field_solve(gx_ctx *ctx, void *stream, gx_solve_stats *stats);
+
+/* Push every particle with the theta-implicit mover (Sec. 2.1, Eq. 29-30):
+ * vbar = alpha (v^n + beta_s E^{n+theta}(x^{n+1/2})), v^{n+1} = 2 vbar - v^n,
+ * x^{n+3/2} = x^{n+1/2} + dt v^{n+1} (periodic wrap), re-bin them by cell, and
+ * in the same pass deposit the moments of step n+1 with alpha built from
+ * B^{n+1}.  Requires a preceding gx_field_solve (GX_ESTATE otherwise); makes
+ * E^{n+1}, B^{n+1} current.  GX_ECFL if a particle moved more than one cell. */
+int gx_push_and_deposit(gx_ctx *ctx, void *stream);
+
+/* nsteps x (gx_field_solve + gx_push_and_deposit).  last (may be NULL)
+ * receives the statistics of the final solve. */
+int gx_step(gx_ctx *ctx, int nsteps, void *stream, gx_solve_stats *last);
+
+/* ------------------------------------------------------------- read-back */
+
+/* Current E (nodes) and B (cells), FP64 [3][nz][ny][nx]; either may be NULL. */
+int gx_get_fields(gx_ctx *ctx, double *E, double *B, int ptr_is_device);
+
+/* E^{n+theta} of the last solve (FP64 [3][nz][ny][nx]). */
+int gx_get_solution(gx_ctx *ctx, double *Etheta, int ptr_is_device);
+
+/* Moments of the current deposit (FP64): rho [nz][ny][nx] (charge density),
+ * J [3][nz][ny][nx] (comoving or standard current after ns_j smoothing passes),
+ * M [nz][ny][nx][27][3][3] (mass matrix block coupling node g to its
+ * neighbour at offset o = (ox+1) + 3 (oy+1) + 9 (oz+1); in 2D only oz = 0
+ * blocks are non-zero), u [3][nz][ny][nx] (smoothed bulk velocity).  Any
+ * pointer may be NULL. */
+int gx_get_moments(gx_ctx *ctx, double *rho, double *J, double *M, double *u, int ptr_is_device);
+
+/* Number of particles currently held by a species (-1 on a bad id). */
+int64_t gx_species_count(gx_ctx *ctx, int species);
+
+/* Copy a species' particles out in bin order: global positions (FP64),
+ * velocities and weights (FP32), ids (int32, only with track_ids, else may be
+ * NULL).  Each array holds gx_species_count() entries. */
+int gx_get_particles(gx_ctx *ctx, int species, double *x, double *y, double *z,
+                     float *vx, float *vy, float *vz, float *w, int32_t *id, int ptr_is_device);
+
+/* FP64 diagnostics of the current state (synchronises the stream). */
+int gx_diagnostics(gx_ctx *ctx, void *stream, gx_diag *out);
+
+/* Accumulated device time (CUDA events on the launching stream) of the fused
+ * push-and-deposit kernels, of the grid-side moment assembly, and of the
+ * field solves since the last reset, in ms; plus the number of library kernel
+ * launches.  reset != 0 clears the counters after reading. */
+int gx_timers(gx_ctx *ctx, double *push_ms, double *moments_ms, double *solve_ms,
+              int64_t *launches, int reset);
+
+/* ------------------------------------------- learned GMRES preconditioner
+ * An addition of this project (the paper has no learned preconditioner): a
+ * 2D convolutional network N with four 3x3 layers (3 -> 32 -> 32 -> 32 -> 3
+ * channels, ReLU between, periodic padding), BF16 weights and activations
+ * with FP32 accumulation, applied as z = s N(r / s), s = ||r||_2 / sqrt(3 N),
+ * as the right preconditioner of FGMRES.  2D only. */
+
+/* Number of FP32 parameters of the network (weights [Cout][Cin][3][3] then
+ * biases [Cout], per layer). */
+int64_t gx_precond_param_count(void);
+
+/* Load FP32 parameters (host or device); kept as an FP32 master copy and a
+ * BF16 inference copy. */
+int gx_precond_set_weights(gx_ctx *ctx, const float *params, int64_t n, int ptr_is_device);
+int gx_precond_get_weights(gx_ctx *ctx, float *params, int64_t n, int ptr_is_device);
+
+/* Keep up to `capacity` (residual, error) pairs from the solves that follow:
+ * each solve contributes r0 = b - A E^n and e = E^{n+theta} - E^n (so A e = r0
+ * to the solver tolerance).  capacity = 0 stops collecting. */
+int gx_precond_collect(gx_ctx *ctx, int capacity);
+int gx_precond_pairs(gx_ctx *ctx);
+
+/* Train the network on the device with Adam (lr) on `npairs` random crops of
+ * crop x crop nodes drawn from the collected pairs, in batches of `batch`, for
+ * `epochs` passes; loss = mean squared error of N(r/s) against e/s.  Forward,
+ * backward (data and weight gradients) and the update run in this library's
+ * kernels.  loss_out (may be NULL) receives the mean loss of each epoch. */
+int gx_precond_train(gx_ctx *ctx, int npairs, int crop, int batch, int epochs, float lr,
+                     uint64_t seed, float *loss_out, void *stream);
+
+/* One forward pass of the network on a [3][H][W] FP32 input (H = ny, W = nx
+ * of the context, or any H, W when called with ctx == NULL is not allowed):
+ * out = N(in) without the s-scaling.  Device pointers only.  For tests. */
+int gx_precond_forward(gx_ctx *ctx, int H, int W, const float *in, float *out, void *stream);
+
+/* Loss and gradients of one [3][H][W] sample: *loss = mean (N(in) - target)^2 / 2,
+ * grad (param_count FP32) = dloss/dparams.  Device pointers.  For tests. */
+int gx_precond_loss_grad(gx_ctx *ctx, int H, int W, const float *in, const float *target,
+                         float *loss, float *grad, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GX_H */

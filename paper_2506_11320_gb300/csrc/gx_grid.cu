@@ -1,0 +1,655 @@
+// gx_grid.cu -- grid kernels of the GL-ECSIM step (2D, FP64 fields).
+//
+// Mesh (Sec. 1.1): E at nodes, B at cell centres; node (i,j) at (i dx, j dy),
+// cell (i,j) spans [i,i+1] x [j,j+1]; periodic.  Derivatives of a node field at
+// a cell are differences of the face-averaged corner values, derivatives of a
+// cell field at a node are differences of the side-averaged neighbouring cells,
+// so that curl_N and curl_C are adjoint and div_C curl_N = 0 exactly.
+#include "gx_internal.cuh"
+
+namespace {
+
+constexpr int kB = 256;
+
+struct G2 {
+    int nx, ny;
+    double dx, dy;
+    __device__ __forceinline__ int64_t id(int i, int j) const {
+        return (int64_t)wrap_idx(i, nx) + (int64_t)nx * wrap_idx(j, ny);
+    }
+    __device__ __forceinline__ int64_t N() const { return (int64_t)nx * ny; }
+};
+
+inline int blocks_for(int64_t n) {
+    int64_t b = (n + kB - 1) / kB;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 32));
+}
+
+#define GRID_LOOP(i, n) for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (n); i += (int64_t)gridDim.x * blockDim.x)
+
+// ------------------------------------------------------ FP32 node copies
+// E^{n+theta} as float4 per node; B averaged from the 4 cells around a node.
+__global__ void k_node_fields(G2 g, const double *__restrict__ E, const double *__restrict__ B, float4 *outE,
+                              float4 *outB) {
+    const int64_t N = g.N();
+    GRID_LOOP(q, N) {
+        const int i = (int)(q % g.nx), j = (int)(q / g.nx);
+        if (outE) outE[q] = make_float4((float)E[q], (float)E[N + q], (float)E[2 * N + q], 0.f);
+        if (outB) {
+            const int64_t c0 = g.id(i - 1, j - 1), c1 = g.id(i, j - 1), c2 = g.id(i - 1, j), c3 = g.id(i, j);
+            double b[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) b[k] = 0.25 * (B[k * N + c0] + B[k * N + c1] + B[k * N + c2] + B[k * N + c3]);
+            outB[q] = make_float4((float)b[0], (float)b[1], (float)b[2], 0.f);
+        }
+    }
+}
+
+// ------------------------------------------------------ moment assembly
+struct SpecK {
+    int ns;
+    double q[GX_MAX_SPECIES], m[GX_MAX_SPECIES], bq[GX_MAX_SPECIES];   // bq = beta_s q_s
+};
+
+// rho, mass density, momentum and the raw plasma velocity at every node from
+// the per-species cell records of the 4 cells around it.
+__global__ void k_assemble_bulk(G2 g, SpecK sk, const float *__restrict__ rec, double dV, double *rho,
+                                double *rho_m, double *P, double *u) {
+    const int64_t N = g.N();
+    constexpr int R = Rec<2>::SIZE;
+    GRID_LOOP(q, N) {
+        const int i = (int)(q % g.nx), j = (int)(q / g.nx);
+        double r = 0, rm = 0, p[3] = {0, 0, 0};
+        for (int s = 0; s < sk.ns; ++s) {
+            const float *rs = rec + (size_t)s * N * R;
+            double w = 0, mv[3] = {0, 0, 0};
+#pragma unroll
+            for (int cy = -1; cy <= 0; ++cy)
+#pragma unroll
+                for (int cx = -1; cx <= 0; ++cx) {
+                    const float *rc = rs + (size_t)g.id(i + cx, j + cy) * R;
+                    const int a = (-cx) + 2 * (-cy);
+                    w += rc[Rec<2>::RHO + a];
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) mv[k] += rc[Rec<2>::MV + 3 * a + k];
+                }
+            r += sk.q[s] * w;
+            rm += sk.m[s] * w;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) p[k] += sk.m[s] * mv[k];
+        }
+        rho[q] = r / dV;
+        rho_m[q] = rm;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            P[k * N + q] = p[k];
+            u[k * N + q] = rm != 0.0 ? p[k] / rm : 0.0;
+        }
+    }
+}
+
+// One sweep of the digital filter (Sec. 1.4, Eq. 26) along one axis with
+// stride d on a 3-component node field: out = phi in + (1-phi)/2 (in[-d] + in[+d]).
+__global__ void k_filter_axis(G2 g, const double *__restrict__ in, double *out, int axis, int d, double phi) {
+    const int64_t N = g.N();
+    GRID_LOOP(q, 3 * N) {
+        const int64_t nd = q % N, base = q - nd;
+        const int i = (int)(nd % g.nx), j = (int)(nd / g.nx);
+        const int64_t m = axis == 0 ? g.id(i - d, j) : g.id(i, j - d);
+        const int64_t p = axis == 0 ? g.id(i + d, j) : g.id(i, j + d);
+        out[q] = phi * in[q] + 0.5 * (1.0 - phi) * (in[base + m] + in[base + p]);
+    }
+}
+
+// The comoving current (Sec. 2.1, Eq. 34) and the FP64 node rows of the mass
+// matrix (Eq. 33).  The particle kernels accumulate alpha (v - u_ref) with a
+// reference velocity u_ref (the bulk velocity of the previous deposit); the
+// exact correction to the smoothed u of this deposit is
+//   sum_p q alpha (u - u_ref)(x_p) W_pg = sum_g' M0_gg' (u - u_ref)_g',
+// with M0 the mass matrix without beta, so
+//   J_C = (1/dV) [sum_p q alpha (v - u_ref) W - sum_g' M0 (u - u_ref)].
+// With the comoving current off, u_ref = 0 and the correction is skipped.
+__global__ void k_assemble_main(G2 g, SpecK sk, const float *__restrict__ rec, double dV, int comoving,
+                                const double *__restrict__ u, const double *__restrict__ uref, double *J,
+                                double *M) {
+    const int64_t N = g.N();
+    constexpr int R = Rec<2>::SIZE;
+    GRID_LOOP(q, N) {
+        const int i = (int)(q % g.nx), j = (int)(q / g.nx);
+        // current: the 4 cells around the node, node g is corner a of each
+        double jc[3] = {0, 0, 0};
+        for (int cy = -1; cy <= 0; ++cy)
+            for (int cx = -1; cx <= 0; ++cx) {
+                const int64_t cell = g.id(i + cx, j + cy);
+                const int ax = -cx, ay = -cy, a = ax + 2 * ay;
+                double du[4][3];
+                if (comoving) {
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) {
+                        const int64_t nb = g.id(i + cx + (b & 1), j + cy + (b >> 1));
+#pragma unroll
+                        for (int k = 0; k < 3; ++k) du[b][k] = u[k * N + nb] - uref[k * N + nb];
+                    }
+                }
+                for (int s = 0; s < sk.ns; ++s) {
+                    const float *rc = rec + ((size_t)s * N + cell) * R;
+                    double js[3];
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) js[k] = rc[Rec<2>::J + 3 * a + k];
+                    if (comoving) {
+#pragma unroll
+                        for (int b = 0; b < 4; ++b) {
+                            const int bx = b & 1, by = b >> 1;
+                            const int jx = (ax == bx) ? 2 * ax : 1, jy = (ay == by) ? 2 * ay : 1;
+                            const float *mp = rc + Rec<2>::M + 9 * (jx + 3 * jy);
+#pragma unroll
+                            for (int r = 0; r < 3; ++r)
+                                js[r] -= (double)mp[3 * r] * du[b][0] + (double)mp[3 * r + 1] * du[b][1] +
+                                         (double)mp[3 * r + 2] * du[b][2];
+                        }
+                    }
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) jc[k] += sk.q[s] * js[k];
+                }
+            }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) J[k * N + q] = jc[k] / dV;
+        // mass-matrix row: block o = (ox,oy) collects every cell holding both g
+        // and g + o.  Along x: ox = 0 -> cells -1 (pair class 2) and 0 (class 0);
+        // ox = +1 -> cell 0 (class 1); ox = -1 -> cell -1 (class 1).  Same in y.
+        double *Mq = M + (size_t)q * 81;
+        for (int o = 0; o < 9; ++o) {
+            const int ox = o % 3 - 1, oy = o / 3 - 1;
+            double blk[9];
+#pragma unroll
+            for (int e = 0; e < 9; ++e) blk[e] = 0.0;
+            const int ncx = ox == 0 ? 2 : 1, ncy = oy == 0 ? 2 : 1;
+            for (int tyy = 0; tyy < ncy; ++tyy) {
+                const int cy = oy == 0 ? -tyy : (oy > 0 ? 0 : -1);
+                const int jy = oy == 0 ? (cy == -1 ? 2 : 0) : 1;
+                for (int txx = 0; txx < ncx; ++txx) {
+                    const int cx = ox == 0 ? -txx : (ox > 0 ? 0 : -1);
+                    const int jx = ox == 0 ? (cx == -1 ? 2 : 0) : 1;
+                    const int64_t cell = g.id(i + cx, j + cy);
+                    for (int s = 0; s < sk.ns; ++s) {
+                        const float *mp = rec + ((size_t)s * N + cell) * R + Rec<2>::M + 9 * (jx + 3 * jy);
+#pragma unroll
+                        for (int e = 0; e < 9; ++e) blk[e] += sk.bq[s] * (double)mp[e];
+                    }
+                }
+            }
+#pragma unroll
+            for (int e = 0; e < 9; ++e) Mq[o * 9 + e] = blk[e];
+        }
+    }
+}
+
+__global__ void k_copy_uref(int64_t N, const double *__restrict__ u, float4 *nU, double *u64, int zero) {
+    GRID_LOOP(q, N) {
+        float4 v = zero ? make_float4(0.f, 0.f, 0.f, 0.f)
+                        : make_float4((float)u[q], (float)u[N + q], (float)u[2 * N + q], 0.f);
+        nU[q] = v;
+        u64[q] = v.x; u64[N + q] = v.y; u64[2 * N + q] = v.z;
+    }
+}
+
+// ------------------------------------------------------------- operators
+// derivatives of a cell field at node (i,j)
+__device__ __forceinline__ double dNx(const G2 &g, const double *f, int i, int j) {
+    return ((f[g.id(i, j - 1)] + f[g.id(i, j)]) - (f[g.id(i - 1, j - 1)] + f[g.id(i - 1, j)])) / (2.0 * g.dx);
+}
+__device__ __forceinline__ double dNy(const G2 &g, const double *f, int i, int j) {
+    return ((f[g.id(i - 1, j)] + f[g.id(i, j)]) - (f[g.id(i - 1, j - 1)] + f[g.id(i, j - 1)])) / (2.0 * g.dy);
+}
+// derivatives of a node field at cell (i,j)
+__device__ __forceinline__ double dCx(const G2 &g, const double *f, int i, int j) {
+    return ((f[g.id(i + 1, j)] + f[g.id(i + 1, j + 1)]) - (f[g.id(i, j)] + f[g.id(i, j + 1)])) / (2.0 * g.dx);
+}
+__device__ __forceinline__ double dCy(const G2 &g, const double *f, int i, int j) {
+    return ((f[g.id(i, j + 1)] + f[g.id(i + 1, j + 1)]) - (f[g.id(i, j)] + f[g.id(i + 1, j)])) / (2.0 * g.dy);
+}
+
+// curl of node field x at cell (i,j) (2D: no z derivatives)
+__device__ __forceinline__ void curlC(const G2 &g, const double *x, int i, int j, double out[3]) {
+    const int64_t N = g.N();
+    const double *xx = x, *xy = x + N, *xz = x + 2 * N;
+    out[0] = dCy(g, xz, i, j);
+    out[1] = -dCx(g, xz, i, j);
+    out[2] = dCx(g, xy, i, j) - dCy(g, xx, i, j);
+}
+
+struct OpArgs {
+    G2 g;
+    double ct2;        // (c theta dt)^2
+    double mfac;       // 4 pi theta dt / dV
+    double lfx, lfy;   // theta dt / dx, theta dt / dy
+    const double *M;   // [N][9][9]
+    const double *kappa;   // [2][3][N] or null
+};
+
+// y = A x: x + (c theta dt)^2 curl_N curl_C x + (4 pi theta dt / dV) M x
+//        - theta dt sum_d (1/dx_d) [kappa_+ (x_+ - x) - kappa_- (x - x_-)]
+// (Eq. 7 with the mass term of Eq. 35 and the diffusive LF term of Eq. 19.)
+__global__ void k_matvec(OpArgs a, const double *__restrict__ x, double *__restrict__ y) {
+    const G2 &g = a.g;
+    const int64_t N = g.N();
+    GRID_LOOP(q, N) {
+        const int i = (int)(q % g.nx), j = (int)(q / g.nx);
+        // curl_C x at the 4 cells around node (i,j): cells (i-1+a, j-1+b)
+        double cc[2][2][3];
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int aa = 0; aa < 2; ++aa) curlC(g, x, i - 1 + aa, j - 1 + b, cc[b][aa]);
+        // curl_N of that cell field at the node
+        const double dxz = ((cc[0][1][2] + cc[1][1][2]) - (cc[0][0][2] + cc[1][0][2])) / (2.0 * g.dx);
+        const double dyz = ((cc[1][0][2] + cc[1][1][2]) - (cc[0][0][2] + cc[0][1][2])) / (2.0 * g.dy);
+        const double dxy = ((cc[0][1][1] + cc[1][1][1]) - (cc[0][0][1] + cc[1][0][1])) / (2.0 * g.dx);
+        const double dyx = ((cc[1][0][0] + cc[1][1][0]) - (cc[0][0][0] + cc[0][1][0])) / (2.0 * g.dy);
+        double out[3];
+        out[0] = x[q] + a.ct2 * dyz;
+        out[1] = x[N + q] + a.ct2 * (-dxz);
+        out[2] = x[2 * N + q] + a.ct2 * (dxy - dyx);
+        if (a.M) {
+            const double *Mq = a.M + (size_t)q * 81;
+#pragma unroll
+            for (int o = 0; o < 9; ++o) {
+                const int64_t nb = g.id(i + (o % 3) - 1, j + (o / 3) - 1);
+                const double x0 = x[nb], x1 = x[N + nb], x2 = x[2 * N + nb];
+#pragma unroll
+                for (int r = 0; r < 3; ++r)
+                    out[r] += a.mfac * (Mq[o * 9 + 3 * r] * x0 + Mq[o * 9 + 3 * r + 1] * x1 + Mq[o * 9 + 3 * r + 2] * x2);
+            }
+        }
+        if (a.kappa) {
+            const int64_t xp = g.id(i + 1, j), xm = g.id(i - 1, j), yp = g.id(i, j + 1), ym = g.id(i, j - 1);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const double *xc = x + c * N;
+                const double *kx = a.kappa + (0 * 3 + c) * N, *ky = a.kappa + (1 * 3 + c) * N;
+                if (g.nx > 1)
+                    out[c] -= a.lfx * (kx[q] * (xc[xp] - xc[q]) - kx[xm] * (xc[q] - xc[xm]));
+                if (g.ny > 1)
+                    out[c] -= a.lfy * (ky[q] * (xc[yp] - xc[q]) - ky[ym] * (xc[q] - xc[ym]));
+            }
+        }
+        y[q] = out[0];
+        y[N + q] = out[1];
+        y[2 * N + q] = out[2];
+    }
+}
+
+// 3x3 diagonal block of A at every node, inverted (block-Jacobi preconditioner).
+__global__ void k_jacobi(OpArgs a, double *jd) {
+    const G2 &g = a.g;
+    const int64_t N = g.N();
+    GRID_LOOP(q, N) {
+        // curl_N curl_C diagonal: for 2D the x and y components couple to their
+        // own node through the y- and x-second differences; derive by applying
+        // the stencil to unit vectors at this node.
+        // d2 terms: (curl curl x)_x = -d_yy x_x + d_xy x_y, etc.; on this mesh
+        // the self-coupling coefficients are 1/(2 dy^2), 1/(2 dx^2) and
+        // their sum for z (averaged second differences).
+        const double sx = g.nx > 1 ? 1.0 / (2.0 * g.dx * g.dx) : 0.0;
+        const double sy = g.ny > 1 ? 1.0 / (2.0 * g.dy * g.dy) : 0.0;
+        double A[9] = {1 + a.ct2 * 2 * sy, 0, 0, 0, 1 + a.ct2 * 2 * sx, 0, 0, 0, 1 + a.ct2 * 2 * (sx + sy)};
+        if (a.M) {
+            const double *Mc = a.M + (size_t)q * 81 + 4 * 9;   // centre offset
+#pragma unroll
+            for (int e = 0; e < 9; ++e) A[e] += a.mfac * Mc[e];
+        }
+        if (a.kappa) {
+            const int i = (int)(q % g.nx), j = (int)(q / g.nx);
+            const int64_t xm = g.id(i - 1, j), ym = g.id(i, j - 1);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                double d = 0;
+                if (g.nx > 1) d += a.lfx * (a.kappa[(0 * 3 + c) * N + q] + a.kappa[(0 * 3 + c) * N + xm]);
+                if (g.ny > 1) d += a.lfy * (a.kappa[(1 * 3 + c) * N + q] + a.kappa[(1 * 3 + c) * N + ym]);
+                A[4 * c] += d;
+            }
+        }
+        // invert the 3x3 block
+        const double c00 = A[4] * A[8] - A[5] * A[7], c01 = A[5] * A[6] - A[3] * A[8], c02 = A[3] * A[7] - A[4] * A[6];
+        const double det = A[0] * c00 + A[1] * c01 + A[2] * c02;
+        const double id = 1.0 / det;
+        double *o = jd + (size_t)q * 9;
+        o[0] = c00 * id; o[1] = (A[2] * A[7] - A[1] * A[8]) * id; o[2] = (A[1] * A[5] - A[2] * A[4]) * id;
+        o[3] = c01 * id; o[4] = (A[0] * A[8] - A[2] * A[6]) * id; o[5] = (A[2] * A[3] - A[0] * A[5]) * id;
+        o[6] = c02 * id; o[7] = (A[1] * A[6] - A[0] * A[7]) * id; o[8] = (A[0] * A[4] - A[1] * A[3]) * id;
+    }
+}
+
+__global__ void k_apply_jacobi(int64_t N, const double *__restrict__ jd, const double *__restrict__ x, double *y) {
+    GRID_LOOP(q, N) {
+        const double *o = jd + (size_t)q * 9;
+        const double x0 = x[q], x1 = x[N + q], x2 = x[2 * N + q];
+        y[q] = o[0] * x0 + o[1] * x1 + o[2] * x2;
+        y[N + q] = o[3] * x0 + o[4] * x1 + o[5] * x2;
+        y[2 * N + q] = o[6] * x0 + o[7] * x1 + o[8] * x2;
+    }
+}
+
+// E_M = -u x B^n / c at nodes (B averaged to nodes), the motional field of Sec. 2.1.
+__global__ void k_motional(G2 g, const double *__restrict__ u, const double *__restrict__ B, double c, double *EM) {
+    const int64_t N = g.N();
+    GRID_LOOP(q, N) {
+        const int i = (int)(q % g.nx), j = (int)(q / g.nx);
+        const int64_t c0 = g.id(i - 1, j - 1), c1 = g.id(i, j - 1), c2 = g.id(i - 1, j), c3 = g.id(i, j);
+        double b[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) b[k] = 0.25 * (B[k * N + c0] + B[k * N + c1] + B[k * N + c2] + B[k * N + c3]);
+        const double ux = u[q], uy = u[N + q], uz = u[2 * N + q];
+        EM[q] = -(uy * b[2] - uz * b[1]) / c;
+        EM[N + q] = -(uz * b[0] - ux * b[2]) / c;
+        EM[2 * N + q] = -(ux * b[1] - uy * b[0]) / c;
+    }
+}
+
+// b = E^n + c theta dt [curl_N B^n - (4 pi / c)(J - (1/dV) M E_M)]   (Eq. 35)
+__global__ void k_rhs(G2 g, const double *__restrict__ E, const double *__restrict__ B, const double *__restrict__ J,
+                      const double *__restrict__ M, const double *__restrict__ EM, double ctd, double jf, double mf,
+                      double *b) {
+    const int64_t N = g.N();
+    GRID_LOOP(q, N) {
+        const int i = (int)(q % g.nx), j = (int)(q / g.nx);
+        const double *Bx = B, *By = B + N, *Bz = B + 2 * N;
+        double cn[3];
+        cn[0] = dNy(g, Bz, i, j);
+        cn[1] = -dNx(g, Bz, i, j);
+        cn[2] = dNx(g, By, i, j) - dNy(g, Bx, i, j);
+        double out[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) out[k] = E[k * N + q] + ctd * cn[k] - jf * J[k * N + q];
+        if (EM) {
+            const double *Mq = M + (size_t)q * 81;
+#pragma unroll
+            for (int o = 0; o < 9; ++o) {
+                const int64_t nb = g.id(i + (o % 3) - 1, j + (o / 3) - 1);
+                const double e0 = EM[nb], e1 = EM[N + nb], e2 = EM[2 * N + nb];
+#pragma unroll
+                for (int r = 0; r < 3; ++r)
+                    out[r] += mf * (Mq[o * 9 + 3 * r] * e0 + Mq[o * 9 + 3 * r + 1] * e1 + Mq[o * 9 + 3 * r + 2] * e2);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) b[k * N + q] = out[k];
+    }
+}
+
+__device__ __forceinline__ double mc_limiter(double r, double beta) {
+    const double v = fmin(fmin(beta * r, 0.5 * (1.0 + r)), beta);
+    return v > 0.0 ? v : 0.0;
+}
+__device__ __forceinline__ double ratio(double prev, double cur) { return cur == 0.0 ? 0.0 : prev / cur; }
+__device__ __forceinline__ double umag(const double *u, int64_t N, int64_t q) {
+    return sqrt(u[q] * u[q] + u[N + q] * u[N + q] + u[2 * N + q] * u[2 * N + q]);
+}
+
+// kappa = (1 - phi_E) a / 2 on the edge from node g to g + e_d (Eq. 19-21),
+// phi_E from E^n (frozen, keeps the solve linear), a = |u| averaged over the
+// edge's two nodes or a = c.
+__global__ void k_kappa(G2 g, const double *__restrict__ E, const double *__restrict__ u, double beta, int speed_c,
+                        double c, double *kappa) {
+    const int64_t N = g.N();
+    GRID_LOOP(t, 6 * N) {
+        const int64_t q = t % N;
+        const int dc = (int)(t / N);       // d * 3 + comp
+        const int d = dc / 3, comp = dc % 3;
+        const int i = (int)(q % g.nx), j = (int)(q / g.nx);
+        const int64_t p = d == 0 ? g.id(i + 1, j) : g.id(i, j + 1);
+        const int64_t m = d == 0 ? g.id(i - 1, j) : g.id(i, j - 1);
+        const double *Ec = E + comp * N;
+        const double r = ratio(Ec[q] - Ec[m], Ec[p] - Ec[q]);
+        const double phi = mc_limiter(r, beta);
+        const double a = speed_c ? c : 0.5 * (umag(u, N, q) + umag(u, N, p));
+        kappa[t] = (1.0 - phi) * a / 2.0;
+    }
+}
+
+// B^{n+1} = B^n - c dt curl_C E^{n+theta} + dt/dx_d (F_{c+1/2} - F_{c-1/2}),
+// F = (1 - phi_B) a / 2 (B_{c+1} - B_c)  (Eq. 5, 17, 18, 22);  E^{n+1} from Eq. 10.
+__global__ void k_advance(G2 g, const double *__restrict__ E, const double *__restrict__ B,
+                          const double *__restrict__ Eth, const double *__restrict__ u, double c, double dt,
+                          double theta, int lf_on, double beta, int speed_c, double *Enew, double *Bnew) {
+    const int64_t N = g.N();
+    GRID_LOOP(q, N) {
+        const int i = (int)(q % g.nx), j = (int)(q / g.nx);
+        double cu[3];
+        curlC(g, Eth, i, j, cu);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) Bnew[k * N + q] = B[k * N + q] - c * dt * cu[k];
+        if (lf_on) {
+            for (int d = 0; d < 2; ++d) {
+                if ((d == 0 && g.nx == 1) || (d == 1 && g.ny == 1)) continue;
+                const double f = dt / (d == 0 ? g.dx : g.dy);
+                // faces c+1/2 (between c and c+e) and c-1/2 (between c-e and c)
+                for (int side = 0; side < 2; ++side) {
+                    const int ci = d == 0 ? i - side : i, cj = d == 0 ? j : j - side;   // face between cell (ci,cj) and +e
+                    const int64_t c0 = g.id(ci, cj);
+                    const int64_t cp = d == 0 ? g.id(ci + 1, cj) : g.id(ci, cj + 1);
+                    const int64_t cm = d == 0 ? g.id(ci - 1, cj) : g.id(ci, cj - 1);
+                    double a;
+                    if (speed_c) {
+                        a = c;
+                    } else {
+                        const int64_t n0 = d == 0 ? g.id(ci + 1, cj) : g.id(ci, cj + 1);
+                        const int64_t n1 = d == 0 ? g.id(ci + 1, cj + 1) : g.id(ci + 1, cj + 1);
+                        a = 0.5 * (umag(u, N, n0) + umag(u, N, n1));
+                    }
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) {
+                        const double *Bk = B + k * N;
+                        const double r = ratio(Bk[c0] - Bk[cm], Bk[cp] - Bk[c0]);
+                        const double F = (1.0 - mc_limiter(r, beta)) * a / 2.0 * (Bk[cp] - Bk[c0]);
+                        Bnew[k * N + q] += side == 0 ? f * F : -f * F;
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) Enew[k * N + q] = (Eth[k * N + q] - (1.0 - theta) * E[k * N + q]) / theta;
+    }
+}
+
+// ------------------------------------------------------------ diagnostics
+__global__ void k_diag_grid(G2 g, const double *__restrict__ E, const double *__restrict__ B,
+                            const double *__restrict__ rho, double *acc) {
+    const int64_t N = g.N();
+    double we = 0, wb = 0, ch = 0, gl = 0, db = 0;
+    GRID_LOOP(q, N) {
+        const int i = (int)(q % g.nx), j = (int)(q / g.nx);
+        for (int k = 0; k < 3; ++k) {
+            we += E[k * N + q] * E[k * N + q];
+            wb += B[k * N + q] * B[k * N + q];
+        }
+        ch += rho ? rho[q] : 0.0;
+        // Gauss residual at cell (i,j): div_C E - 4 pi (rho averaged to the cell)
+        const double divE = dCx(g, E, i, j) + dCy(g, E + N, i, j);
+        const double rc = rho ? 0.25 * (rho[g.id(i, j)] + rho[g.id(i + 1, j)] + rho[g.id(i, j + 1)] + rho[g.id(i + 1, j + 1)]) : 0.0;
+        const double gr = divE - 4.0 * GX_PI * rc;
+        gl += gr * gr;
+        const double divB = dNx(g, B, i, j) + dNy(g, B + N, i, j);
+        db += divB * divB;
+    }
+    double v[5] = {we, wb, ch, gl, db};
+    for (int k = 0; k < 5; ++k) {
+        double s = v[k];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if ((threadIdx.x & 31) == 0) atomicAdd(acc + k, s);
+    }
+}
+
+__global__ void k_diag_particles(int64_t ncell, int cap, const int *cnt, const float *vx, const float *vy,
+                                 const float *vz, const float *w, double mass, double *acc) {
+    double ke = 0, px = 0, py = 0, pz = 0;
+    double np = 0;
+    for (int64_t c = blockIdx.x; c < ncell; c += gridDim.x) {
+        const int m = min(cnt[c], cap);
+        if (threadIdx.x == 0) np += m;
+        for (int i = threadIdx.x; i < m; i += blockDim.x) {
+            const size_t s = (size_t)c * cap + i;
+            const double mw = mass * w[s];
+            const double a = vx[s], b = vy[s], d = vz[s];
+            ke += 0.5 * mw * (a * a + b * b + d * d);
+            px += mw * a; py += mw * b; pz += mw * d;
+        }
+    }
+    double v[5] = {ke, px, py, pz, np};
+    for (int k = 0; k < 5; ++k) {
+        double s = v[k];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if ((threadIdx.x & 31) == 0) atomicAdd(acc + k, s);
+    }
+}
+
+G2 geom(const gx_ctx *c) { return G2{c->n[0], c->n[1], c->cfg.dx[0], c->cfg.dx[1]}; }
+
+SpecK speck(const gx_ctx *c) {
+    SpecK sk{};
+    sk.ns = c->nspecies;
+    for (int s = 0; s < c->nspecies; ++s) {
+        sk.q[s] = c->sp[s].q;
+        sk.m[s] = c->sp[s].m;
+        sk.bq[s] = c->sp[s].q * c->cfg.dt / (2.0 * c->sp[s].m) * c->sp[s].q;
+    }
+    return sk;
+}
+
+OpArgs opargs(const gx_ctx *c) {
+    OpArgs a{};
+    a.g = geom(c);
+    const double ct = c->cfg.c * c->cfg.theta * c->cfg.dt;
+    a.ct2 = ct * ct;
+    a.mfac = 4.0 * GX_PI * c->cfg.theta * c->cfg.dt / c->dV;
+    a.lfx = c->cfg.theta * c->cfg.dt / c->cfg.dx[0];
+    a.lfy = c->cfg.theta * c->cfg.dt / c->cfg.dx[1];
+    a.M = c->nspecies > 0 ? c->M : nullptr;
+    a.kappa = c->cfg.lf_on ? c->kappa : nullptr;
+    return a;
+}
+
+// filter passes: ping-pong between f and the scratch buffer, result in f
+int filter_passes(gx_ctx *c, double *f, int passes, bool alternate, cudaStream_t st) {
+    const G2 g = geom(c);
+    for (int p = 0; p < passes; ++p) {
+        const int d = (alternate && (p % 2 == 1)) ? 2 : 1;
+        for (int axis = 0; axis < 2; ++axis) {
+            if ((axis == 0 && g.nx == 1) || (axis == 1 && g.ny == 1)) continue;
+            k_filter_axis<<<blocks_for(3 * c->N), kB, 0, st>>>(g, f, c->tmp3, axis, d, 0.5);
+            GX_LAUNCHED(c);
+            GX_CHECK(c, cudaMemcpyAsync(f, c->tmp3, 3 * c->N * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        }
+    }
+    return GX_OK;
+}
+
+}  // namespace
+
+int gx_node_fields(gx_ctx *c, const double *Eth, const double *Bcur, float4 *outE, float4 *outB, cudaStream_t st) {
+    k_node_fields<<<blocks_for(c->N), kB, 0, st>>>(geom(c), Eth, Bcur, outE, outB);
+    GX_LAUNCHED(c);
+    return GX_OK;
+}
+
+// records -> rho, u (smoothed), J (comoving or standard, smoothed), M; then
+// the reference velocity of the next deposit becomes this u.
+int gx_assemble_moments(gx_ctx *c, cudaStream_t st) {
+    const G2 g = geom(c);
+    const SpecK sk = speck(c);
+    k_assemble_bulk<<<blocks_for(c->N), kB, 0, st>>>(g, sk, c->rec, c->dV, c->rho, c->rho_m, c->P, c->u);
+    GX_LAUNCHED(c);
+    int rc = filter_passes(c, c->u, c->cfg.nsmooth_u, true, st);
+    if (rc) return rc;
+    k_assemble_main<<<blocks_for(c->N), kB, 0, st>>>(g, sk, c->rec, c->dV, c->cfg.comoving, c->u, c->uref64, c->J,
+                                                       c->M);
+    GX_LAUNCHED(c);
+    rc = filter_passes(c, c->J, c->cfg.ns_j, false, st);
+    if (rc) return rc;
+    // reference velocity of the next deposit: this u (comoving) or 0
+    k_copy_uref<<<blocks_for(c->N), kB, 0, st>>>(c->N, c->u, c->nUref, c->uref64, c->cfg.comoving ? 0 : 1);
+    GX_LAUNCHED(c);
+    c->have_u = 1;
+    return GX_OK;
+}
+
+int gx_build_rhs(gx_ctx *c, cudaStream_t st) {
+    const G2 g = geom(c);
+    const bool cm = c->cfg.comoving && c->nspecies > 0;
+    if (cm) {
+        k_motional<<<blocks_for(c->N), kB, 0, st>>>(g, c->u, c->B, c->cfg.c, c->EM);
+        GX_LAUNCHED(c);
+    }
+    const double ctd = c->cfg.c * c->cfg.theta * c->cfg.dt;
+    const double jf = 4.0 * GX_PI * c->cfg.theta * c->cfg.dt;
+    k_rhs<<<blocks_for(c->N), kB, 0, st>>>(g, c->E, c->B, c->J, c->M, cm ? c->EM : nullptr, ctd, jf, jf / c->dV,
+                                           c->rhs);
+    GX_LAUNCHED(c);
+    return GX_OK;
+}
+
+int gx_build_kappa(gx_ctx *c, cudaStream_t st) {
+    if (!c->cfg.lf_on) return GX_OK;
+    k_kappa<<<blocks_for(6 * c->N), kB, 0, st>>>(geom(c), c->E, c->u, c->cfg.lf_beta, c->cfg.lf_speed_c, c->cfg.c,
+                                                  c->kappa);
+    GX_LAUNCHED(c);
+    return GX_OK;
+}
+
+int gx_apply_A(gx_ctx *c, const double *x, double *y, cudaStream_t st) {
+    k_matvec<<<blocks_for(c->N), kB, 0, st>>>(opargs(c), x, y);
+    GX_LAUNCHED(c);
+    return GX_OK;
+}
+
+int gx_build_jacobi(gx_ctx *c, cudaStream_t st) {
+    k_jacobi<<<blocks_for(c->N), kB, 0, st>>>(opargs(c), c->jdiag);
+    GX_LAUNCHED(c);
+    return GX_OK;
+}
+
+int gx_apply_jacobi(gx_ctx *c, const double *x, double *y, cudaStream_t st) {
+    k_apply_jacobi<<<blocks_for(c->N), kB, 0, st>>>(c->N, c->jdiag, x, y);
+    GX_LAUNCHED(c);
+    return GX_OK;
+}
+
+int gx_advance(gx_ctx *c, cudaStream_t st) {
+    k_advance<<<blocks_for(c->N), kB, 0, st>>>(geom(c), c->E, c->B, c->Eth, c->u, c->cfg.c, c->cfg.dt, c->cfg.theta,
+                                               c->cfg.lf_on, c->cfg.lf_beta, c->cfg.lf_speed_c, c->Enew, c->Bnew);
+    GX_LAUNCHED(c);
+    return GX_OK;
+}
+
+int gx_copy_uref(gx_ctx *c, int zero, cudaStream_t st);
+int gx_copy_uref(gx_ctx *c, int zero, cudaStream_t st) {
+    k_copy_uref<<<blocks_for(c->N), kB, 0, st>>>(c->N, c->u, c->nUref, c->uref64, zero);
+    GX_LAUNCHED(c);
+    return GX_OK;
+}
+
+int gx_diag_run(gx_ctx *c, gx_diag *out, cudaStream_t st) {
+    double *acc = c->dred;
+    GX_CHECK(c, cudaMemsetAsync(acc, 0, 16 * sizeof(double), st));
+    k_diag_grid<<<blocks_for(c->N), kB, 0, st>>>(geom(c), c->E, c->B, c->moments_valid ? c->rho : nullptr, acc);
+    GX_LAUNCHED(c);
+    for (int s = 0; s < c->nspecies; ++s) {
+        const Species &S = c->sp[s];
+        k_diag_particles<<<(unsigned)std::min<int64_t>(c->N, 152 * 8), 128, 0, st>>>(
+            c->N, S.cap, S.cnt[c->cur], S.f[c->cur][PF_VX], S.f[c->cur][PF_VY], S.f[c->cur][PF_VZ],
+            S.f[c->cur][PF_W], S.m, acc + 5);
+        GX_LAUNCHED(c);
+    }
+    double h[16];
+    GX_CHECK(c, cudaMemcpyAsync(h, acc, 16 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    GX_CHECK(c, cudaStreamSynchronize(st));
+    out->energy_E = h[0] * c->dV / (8.0 * GX_PI);
+    out->energy_B = h[1] * c->dV / (8.0 * GX_PI);
+    out->charge = h[2] * c->dV;
+    out->gauss_l2 = sqrt(h[3]);
+    out->divB_l2 = sqrt(h[4]);
+    out->kinetic = h[5];
+    out->momentum[0] = h[6]; out->momentum[1] = h[7]; out->momentum[2] = h[8];
+    out->n_particles = (int64_t)llround(h[9]);
+    return GX_OK;
+}

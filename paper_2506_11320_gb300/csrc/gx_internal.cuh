@@ -1,0 +1,205 @@
+// gx_internal.cuh -- internal declarations of the GB300 GL-ECSIM library.
+//
+// Data layout in HBM (2D = x-y with three velocity components; 3D = x-y-z):
+//   * fields: FP64, component-major [3][N] with N = nx ny nz; E at nodes, B at
+//     cell centres (collocated staggered mesh, Sec. 1.1 of the paper);
+//   * particles: per species, cell bins of fixed capacity `cap` (a multiple of
+//     32).  Bin c holds cnt[c] particles in slots [c*cap, c*cap + cnt[c]) of
+//     SoA FP32 arrays: cell-local offsets ox, oy (, oz) in [0,1), velocities
+//     vx, vy, vz, weight w (and an optional int32 id).  Two copies (A, B): the
+//     push reads A and writes B, then they swap;
+//   * deposit records: per species and cell, FP32 partial sums over the cell's
+//     particles (see REC_* below), written by the particle kernels and folded
+//     into FP64 node moments by the grid kernels;
+//   * mass matrix: FP64 node rows M[g][o][3][3], o over the 3^d neighbour
+//     offsets (9 in 2D, 27 in 3D).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "../../include/gx.h"
+
+#define GX_MAX_SPECIES 4
+#define GX_PI 3.14159265358979323846
+
+// --------------------------------------------------------------- records
+// Per species s and cell c, sums over the particles p of s in c with cell-local
+// linear weights W_a (corner a = ax + 2 ay (+ 4 az)) and pair weights
+// P_j = X_jx Y_jy (Z_jz), X_0 = (1-ox)^2, X_1 = ox (1-ox), X_2 = ox^2:
+//   [REC_RHO + a]            sum w W_a
+//   [REC_MV + 3a + i]        sum w v_i W_a
+//   [REC_J + 3a + i]         sum w (alpha (v - u_ref(x_p)))_i W_a
+//   [REC_M + 9 j + e]        sum w alpha_e P_j          (alpha row-major, e = 3 r + c)
+// The species factors q_s, m_s, beta_s are applied when the records are folded.
+template <int DIM> struct Rec;
+template <> struct Rec<2> {
+    static constexpr int NC = 4, NPAIR = 9;
+    static constexpr int RHO = 0, MV = 4, J = 16, M = 28, USED = 109, SIZE = 112;
+};
+template <> struct Rec<3> {
+    static constexpr int NC = 8, NPAIR = 27;
+    static constexpr int RHO = 0, MV = 8, J = 32, M = 56, USED = 299, SIZE = 300;
+};
+
+// ------------------------------------------------------------- particles
+enum { PF_OX = 0, PF_OY, PF_OZ, PF_VX, PF_VY, PF_VZ, PF_W, PF_ID, PF_COUNT };
+
+struct Species {
+    double q = 0, m = 0;
+    int cap = 0;                        // bin capacity (particles per cell)
+    float *f[2][PF_COUNT] = {};         // [copy][field]; PF_ID holds int32 bits
+    int *cnt[2] = {};                   // particles per cell, per copy
+};
+
+struct DevFlags {                       // written by kernels, read by the host
+    int cfl;                            // a particle moved more than one cell
+    int overflow;                       // a bin overflowed (particle dropped)
+    int maxcount;                       // largest bin count after the last push
+    int pad;
+};
+
+// --------------------------------------------------------------- tiles
+// The particle kernels give each CTA a tile of TX x TY (x TZ) cells; the tile's
+// records plus a one-cell ring around it live in shared memory.  Contributions
+// of particles that leave the tile land in the ring and are written to a
+// per-tile ring buffer, folded into the neighbours' records afterwards.
+struct TileGeom {
+    int T[3];            // tile size per axis
+    int ntile[3];        // tiles per axis
+    int ntiles;
+    int ring;            // ring cells per tile
+    int local;           // (TX+2)(TY+2)(TZ+2) cells incl. ring
+};
+
+// --------------------------------------------------------------- context
+struct gx_ctx {
+    gx_config cfg{};
+    int dim = 2;
+    int n[3] = {1, 1, 1};
+    int64_t N = 0;
+    double dV = 1;
+    int noff = 9;                       // neighbour offsets per node (9 / 27)
+    std::string err;
+
+    // fields (FP64)
+    double *E = nullptr, *B = nullptr;          // E^n (nodes), B^n (cells)
+    double *Eth = nullptr, *Enew = nullptr, *Bnew = nullptr;
+    int pending = 0;                            // a solve is waiting for the push
+
+    // FP32 node copies used by the particle kernels (float4: x, y, z, pad)
+    float4 *nE = nullptr;        // E^{n+theta}
+    float4 *nB = nullptr;        // B^n averaged to nodes
+    float4 *nBnext = nullptr;    // B^{n+1} averaged to nodes
+    float4 *nUref = nullptr;     // reference velocity subtracted in the deposit
+
+    // particles
+    int nspecies = 0;
+    Species sp[GX_MAX_SPECIES];
+    int cur = 0;                                // which copy is current
+    int64_t np_total = 0;
+
+    // deposit records
+    TileGeom tg{};
+    int *ring_slot_of_local = nullptr;          // [local] -> ring slot, -1 = interior
+    int *ring_local_of_slot = nullptr;          // [ring]  -> local cell index
+    int rec_size = 112;
+    float *rec = nullptr;                       // [S][N][rec_size]
+    float *ring = nullptr;                      // [S][ntiles][ring][rec_size]
+
+    // node moments (FP64)
+    double *rho = nullptr, *rho_m = nullptr;    // [N]
+    double *P = nullptr, *u = nullptr;          // [3][N]
+    double *J = nullptr;                        // [3][N]
+    double *M = nullptr;                        // [N][noff][9]
+    double *tmp3 = nullptr;                     // [3][N] scratch for filters
+    double *uref64 = nullptr;                   // [3][N] FP64 copy of nUref values
+    int moments_valid = 0;
+    int have_u = 0;                             // u of a previous deposit exists
+
+    // field solve
+    double *kappa = nullptr;                    // [dim][3][N] LF-E coefficients
+    double *rhs = nullptr, *EM = nullptr;       // [3][N]
+    double *jdiag = nullptr;                    // [N][9] inverse 3x3 block diagonal
+    double *V = nullptr, *Z = nullptr;          // Krylov bases [(m+1)][3N], [m][3N]
+    double *w = nullptr, *r = nullptr;          // [3N]
+    double *dred = nullptr;                     // reduction scratch
+    int red_blocks = 0;
+    double *hcol = nullptr;                     // [m+2] device column
+    double *hpin = nullptr;                     // pinned host mirror of hcol
+    gx_solve_stats last{};
+
+    // learned preconditioner (allocated on demand)
+    struct Net *net = nullptr;
+
+    // flags, timers
+    DevFlags *dflags = nullptr;
+    DevFlags *hflags = nullptr;                 // pinned
+    std::vector<cudaEvent_t> evpool;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> evpend[3];   // push, moments, solve
+    double t_push = 0, t_mom = 0, t_solve = 0;
+    int64_t launches = 0;
+};
+
+// ------------------------------------------------------- shared helpers
+#define GX_CHECK(ctx, call)                                                              \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess) {                                                         \
+            (ctx)->err = std::string(#call) + ": " + cudaGetErrorString(e_);             \
+            return GX_ECUDA;                                                             \
+        }                                                                                \
+    } while (0)
+
+#define GX_LAUNCHED(ctx)                                                                 \
+    do {                                                                                 \
+        cudaError_t e_ = cudaGetLastError();                                             \
+        (ctx)->launches++;                                                               \
+        if (e_ != cudaSuccess) {                                                         \
+            (ctx)->err = std::string("kernel launch: ") + cudaGetErrorString(e_);        \
+            return GX_ECUDA;                                                             \
+        }                                                                                \
+    } while (0)
+
+__host__ __device__ inline int wrap_idx(int i, int n) {
+    i %= n;
+    return i < 0 ? i + n : i;
+}
+
+// ------------------------------------------------ entry points per module
+// particles (gx_particles.cu)
+int gx_bin_particles(gx_ctx *c, int s, int64_t n, const double *x, const double *y, const double *z,
+                     const float *vx, const float *vy, const float *vz, const float *w, const int32_t *id,
+                     cudaStream_t st);
+int gx_run_deposit(gx_ctx *c, cudaStream_t st);              // records from the current copy
+int gx_run_push_deposit(gx_ctx *c, cudaStream_t st);         // mover + re-bin + records
+int gx_particles_out(gx_ctx *c, int s, double *x, double *y, double *z, float *vx, float *vy, float *vz,
+                     float *w, int32_t *id, cudaStream_t st);
+int gx_choose_tiles(gx_ctx *c);
+int gx_regrow_bins(gx_ctx *c, int s, int newcap, cudaStream_t st);
+
+// grid (gx_grid.cu)
+int gx_node_fields(gx_ctx *c, const double *Eth, const double *Bcur, float4 *outE, float4 *outB,
+                   cudaStream_t st);
+int gx_assemble_moments(gx_ctx *c, cudaStream_t st);         // records -> rho, u, J, M
+int gx_build_rhs(gx_ctx *c, cudaStream_t st);
+int gx_build_kappa(gx_ctx *c, cudaStream_t st);
+int gx_apply_A(gx_ctx *c, const double *x, double *y, cudaStream_t st);
+int gx_build_jacobi(gx_ctx *c, cudaStream_t st);
+int gx_apply_jacobi(gx_ctx *c, const double *x, double *y, cudaStream_t st);
+int gx_advance(gx_ctx *c, cudaStream_t st);                  // Enew, Bnew from Eth
+int gx_diag_run(gx_ctx *c, gx_diag *out, cudaStream_t st);
+
+// solver (gx_gmres.cu)
+int gx_fgmres(gx_ctx *c, cudaStream_t st);
+double gx_norm_host(gx_ctx *c, const double *x, int64_t n, cudaStream_t st, int *status);
+
+// network (gx_net.cu)
+int gx_net_apply(gx_ctx *c, const double *r, double *z, cudaStream_t st);
+int gx_net_collect(gx_ctx *c, cudaStream_t st);
+void gx_net_free(gx_ctx *c);
