@@ -1,0 +1,362 @@
+"""Benchmark of the GB300 GL-ECSIM hot path.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl reference]
+
+One step = one full pass of the hot path: limited-LF coefficients, right-hand
+side, FP64 FGMRES field solve, field advance, the fused mover + re-bin +
+deposit kernel, and the grid-side assembly of rho, u, the comoving current and
+the mass matrices.  The metric is particle-steps/s of push+deposit (the fused
+particle kernel plus the moment assembly it feeds), timed with CUDA events on
+the launching stream inside the timed steps; the field solve's time per step
+is reported next to it.  Inputs are seeded synthetic plasmas (workloads/).
+
+With --gpus N > 1 (launched by torch.distributed.run) every rank runs an
+independent replica of the workload on its own GPU (the single-domain step has
+no exchange to shard); value = particle-steps of all ranks / max rank time.
+
+--impl reference times the FP64 CPU oracle (the reference arm of this project)
+on a bounded sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+METRIC = "particle-steps/s (push+deposit) & GMRES time/step, learned vs plain"
+UNIT = "particle-steps/s"
+ALG_BYTES_2D = 44          # per particle-step: read ox,oy,vx,vy,vz,w (24 B) + write ox,oy,vx,vy,vz (20 B)
+
+
+def make_workload(name):
+    if name == "harris":
+        return workloads.harris(nx=512, ny=256, ppc=100), "2D Harris-sheet reconnection 512x256 cells, 100 ppc/species"
+    if name == "harris_small":
+        return workloads.harris(nx=128, ny=64, ppc=100), "2D Harris sheet 128x64 cells, 100 ppc/species"
+    if name == "uniform":
+        return workloads.uniform_drift(n=(32, 32, 1), ppc=64), "2D periodic 32x32, 64 ppc/species"
+    raise SystemExit(f"unknown workload {name}")
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def load_traffic(kernel_key, workload_key):
+    """DRAM bytes per launch of the dominant kernel from a committed ncu summary
+    (profiles/<kernel>_<workload>.json), or None."""
+    p = os.path.join(ROOT, "profiles", f"{kernel_key}_{workload_key}.json")
+    if os.path.exists(p):
+        try:
+            d = json.load(open(p))
+            return d.get("dram_bytes_per_launch"), d
+        except Exception:
+            return None, None
+    return None, None
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    def __init__(self, dev):
+        self.dev, self.p, self.out = dev, None, os.path.join("/tmp", f"gx_clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.out, "w")
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200", "-i", str(self.dev)], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except Exception:
+                self.p.kill()
+            self.f.close()
+
+    def summary(self):
+        if not self.p or not os.path.exists(self.out):
+            return None
+        sm, mx, reasons = [], [], set()
+        for line in open(self.out):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, v in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"),
+                               parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_push_deposit_rate(wl, budget_s=15.0, cells=(64, 32)):
+    """The FP64 CPU oracle's push+deposit throughput (mover + bulk moments +
+    deposit) on a bounded patch of the workload (single host thread)."""
+    import oracle as O
+    sub = make_sample(wl, cells)
+    cfg = O.make_cfg(sub.n, sub.dx, **sub.grid_kwargs())
+    pl = O.Plasma.from_species(sub.species)
+    Bn = O.node_avg(cfg, sub.B0)
+    Eth = sub.E0.copy()
+    t0 = time.perf_counter()
+    steps = 0
+    while True:
+        O.mover(cfg, pl, Eth, Bn)
+        rm, P = O.bulk_moments(cfg, pl)
+        u = O.bulk_velocity(cfg, rm, P)
+        O.deposit(cfg, pl, Bn, u=u if sub.comoving else None)
+        steps += 1
+        if time.perf_counter() - t0 > budget_s or steps >= 50:
+            break
+    dt = time.perf_counter() - t0
+    return pl.np * steps / dt, {"particles": pl.np, "steps": steps, "seconds": dt, "cells": list(cells)}
+
+
+def make_sample(wl, cells):
+    """A patch of the workload: the first cells[0] x cells[1] cells with their
+    particles and fields, made periodic."""
+    nx, ny = cells
+    nx, ny = min(nx, wl.n[0]), min(ny, wl.n[1])
+    Lx, Ly = nx * wl.dx[0], ny * wl.dx[1]
+    species = []
+    for s in wl.species:
+        m = (s["x"] < Lx) & (s["y"] < Ly)
+        species.append({k: (v[m] if isinstance(v, np.ndarray) else v) for k, v in s.items()})
+    import copy
+    sub = copy.copy(wl)
+    sub.n = (nx, ny, 1)
+    sub.species = species
+    sub.E0 = np.ascontiguousarray(wl.E0[:, :, :ny, :nx])
+    sub.B0 = np.ascontiguousarray(wl.B0[:, :, :ny, :nx])
+    return sub
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    wl, desc = make_workload(args.workload)
+    import oracle as O
+    O.build()
+    rates = []
+    info = None
+    for k in range(args.warmup + args.steps):
+        r, info = oracle_push_deposit_rate(wl, budget_s=4.0)
+        if k >= args.warmup:
+            rates.append(r)
+    value = statistics.median(rates)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": desc, "sample": f"{info['cells'][0]}x{info['cells'][1]}-cell patch"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{info['particles']} particles of a {info['cells'][0]}x{info['cells'][1]}"
+                                       f"-cell patch, mover+bulk+deposit, {info['steps']} steps per timing"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default="harris")
+    ap.add_argument("--impl", default="gx")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+
+    import paper_2506_11320_gb300 as gx
+    if not os.path.exists(gx.LIB_PATH):
+        from paper_2506_11320_gb300 import build as b
+        b.build()
+    wl, desc = make_workload(args.workload)
+    Np = wl.n_particles
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+            torch.cuda.synchronize()
+
+    # ------------------------------------------------------- device-timed run
+    ctx = gx.from_workload(wl, gmres_tol=wl.gmres_tol)
+    for _ in range(args.warmup):
+        ctx.step(1, allow_noconv=True)
+    ctx.timers(reset=True)
+    iters = []
+    barrier()
+    with Clocks(dev) as clk:
+        t0 = time.perf_counter()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        for _ in range(args.steps):
+            st = ctx.step(1, allow_noconv=True)
+            iters.append(st.iters)
+        ev1.record()
+        barrier()
+        wall = time.perf_counter() - t0
+    step_ms_dev = ev0.elapsed_time(ev1) / args.steps
+    tm = ctx.timers(reset=True)
+    kern = ctx.kernel_timers() if hasattr(ctx, "kernel_timers") else None
+    pd_ms = (tm["push_ms"] + tm["moments_ms"]) / args.steps
+    solve_ms = tm["solve_ms"] / args.steps
+    # max over ranks
+    vals = torch.tensor([pd_ms, step_ms_dev, wall], dtype=torch.float64, device="cuda")
+    if dist:
+        dist.all_reduce(vals, op=dist.ReduceOp.MAX)
+    pd_ms_max, step_ms_max = float(vals[0]), float(vals[1])
+    value = world * Np / (pd_ms_max / 1000.0)
+
+    peak, peak_kind = load_peaks()
+    push_kernel_ms = tm["push_ms"] / args.steps        # fused kernel + ring fold + bin stats
+    n_launch_kernel = len(wl.species)
+    alg_bytes = ALG_BYTES_2D * Np                      # per step, both species' launches
+    achieved = alg_bytes / (push_kernel_ms / 1000.0) / 1e9
+    traffic, prof = load_traffic("k_push_deposit", args.workload)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "peak_kind": peak_kind,
+                "kernel": "k_push_deposit (fused mover + re-bin + deposit), per-species launches",
+                "alg_bytes_per_launch": alg_bytes / n_launch_kernel}
+
+    # ------------------------------------------------------- end to end (host buffers)
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(gx, wl, args.steps, barrier)
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        try:
+            rate, info = oracle_push_deposit_rate(wl, budget_s=12.0)
+            cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": f"{info['particles']} particles of a {info['cells'][0]}x{info['cells'][1]}-cell patch "
+                             f"of the workload, FP64 mover+bulk moments+deposit, {info['steps']} steps in "
+                             f"{info['seconds']:.1f} s"}
+        except Exception as e:     # pragma: no cover
+            cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"failed: {e}"}
+
+    if rank == 0:
+        clocks = clk.summary()
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": step_ms_max, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 particles / f64 fields", "data": "synthetic",
+            "config": {"workload": desc, "particles": Np, "cells": list(wl.n[:2]), "comoving": wl.comoving,
+                       "lf": wl.lf_on, "ns_j": wl.ns_j, "gmres_tol": wl.gmres_tol, "precond": "none",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       "l2": f"inputs larger than L2 ({Np * 24 / 1e6:.0f} MB of particle state read per step, "
+                             f"L2 129 MB); no flush"},
+            "push_deposit_ms_per_step": pd_ms_max, "push_kernel_ms_per_step": push_kernel_ms,
+            "gmres_ms_per_step": solve_ms, "gmres_iters_per_step": statistics.mean(iters),
+            "wall_ms_per_step": 1000 * wall / args.steps,
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "gpu_launches": int(tm["launches"]),
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def run_e2e(gx, wl, steps, barrier):
+    """Same metric through the public C ABI with host buffers: pinned host
+    particle and field arrays are copied in (gx_species_add, gx_fields_set),
+    every step's diagnostics (FP64 energies, momentum) are read back, and the
+    final fields are copied out; all inside the timed region."""
+    import torch
+    host = []
+    h2d = 0
+    for s in wl.species:
+        arrs = {}
+        for k in ("x", "y", "z"):
+            t = torch.from_numpy(np.ascontiguousarray(s[k], np.float64)).pin_memory()
+            arrs[k] = t
+            h2d += t.numel() * 8
+        for k in ("vx", "vy", "vz", "w"):
+            t = torch.from_numpy(np.ascontiguousarray(s[k], np.float32)).pin_memory()
+            arrs[k] = t
+            h2d += t.numel() * 4
+        host.append((s["q"], s["m"], arrs))
+    E0 = torch.from_numpy(np.ascontiguousarray(wl.E0)).pin_memory()
+    B0 = torch.from_numpy(np.ascontiguousarray(wl.B0)).pin_memory()
+    Eout = torch.empty_like(E0).pin_memory()
+    Bout = torch.empty_like(B0).pin_memory()
+    h2d += 2 * E0.numel() * 8
+    cfg = gx.make_config(wl.n, wl.dx, c=wl.c, theta=wl.theta, dt=wl.dt, comoving=wl.comoving, lf_on=wl.lf_on,
+                         lf_speed_c=wl.lf_speed_c, lf_beta=wl.lf_beta, ns_j=wl.ns_j, nsmooth_u=wl.nsmooth_u,
+                         gmres_tol=wl.gmres_tol)
+    barrier()
+    t0 = time.perf_counter()
+    ctx = gx.Context(cfg)
+    for q, m, a in host:
+        ctx.species_add(q, m, a["x"].numpy(), a["y"].numpy(), a["z"].numpy(), a["vx"].numpy(), a["vy"].numpy(),
+                        a["vz"].numpy(), a["w"].numpy())
+    ctx.fields_set(E0.numpy(), B0.numpy())
+    d2h = 0
+    for _ in range(steps):
+        ctx.step(1, allow_noconv=True)
+        ctx.diagnostics()
+        d2h += 16 * 8
+    ctx.get_fields(Eout.numpy(), Bout.numpy())
+    d2h += 2 * Eout.numel() * 8
+    barrier()
+    wall = time.perf_counter() - t0
+    ctx.close()
+    return {"value": wl.n_particles * steps / wall, "unit": UNIT, "h2d_bytes_per_step": h2d // steps,
+            "d2h_bytes_per_step": d2h // steps,
+            "note": "context creation, binning of all particles from pinned host memory, every step's FP64 "
+                    "diagnostics and the final fields read back are inside the timed region"}
+
+
+if __name__ == "__main__":
+    sys.exit(main())

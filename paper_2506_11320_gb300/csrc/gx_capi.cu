@@ -124,9 +124,13 @@ int deposit_now(gx_ctx *c, cudaStream_t st) {
 int check_flags(gx_ctx *c, cudaStream_t st) {
     GX_CHECK(c, cudaMemcpyAsync(c->hflags, c->dflags, sizeof(DevFlags), cudaMemcpyDeviceToHost, st));
     GX_CHECK(c, cudaStreamSynchronize(st));
-    if (c->hflags->overflow || c->hflags->cfl) {
+    if (c->hflags->overflow || c->hflags->cfl || c->hflags->timeout) {
         // report once: clear the device flags so the context stays usable
-        GX_CHECK(c, cudaMemsetAsync(c->dflags, 0, 2 * sizeof(int), st));
+        GX_CHECK(c, cudaMemsetAsync(c->dflags, 0, 3 * sizeof(int), st));
+    }
+    if (c->hflags->timeout) {
+        c->err = "a bounded device wait for a bulk copy gave up";
+        return GX_ETIMEOUT;
     }
     if (c->hflags->overflow) {
         c->err = "a cell bin overflowed: particles were lost (raise bin_slack)";
@@ -174,9 +178,10 @@ void gx_destroy(gx_ctx *c) {
     for (auto p : fp)
         if (*p) cudaFree(*p);
     if (c->rec) cudaFree(c->rec);
-    if (c->ring) cudaFree(c->ring);
-    if (c->ring_slot_of_local) cudaFree(c->ring_slot_of_local);
-    if (c->ring_local_of_slot) cudaFree(c->ring_local_of_slot);
+    if (c->gm) cudaFree(c->gm);
+    if (c->gpart) cudaFree(c->gpart);
+    if (c->zbuf) cudaFree(c->zbuf);
+    if (c->vbuf) cudaFree(c->vbuf);
     if (c->dflags) cudaFree(c->dflags);
     if (c->hflags) cudaFreeHost(c->hflags);
     if (c->hpin) cudaFreeHost(c->hpin);
@@ -206,7 +211,8 @@ int gx_create(const gx_config *cfg, gx_ctx **out) {
     if (cfg->n[2] != 1) return fail(GX_ENOTIMPL, "this build implements the 2D (x-y) path: n[2] must be 1");
     if (!(cfg->c > 0) || !(cfg->dt > 0)) return fail(GX_EINVAL, "c and dt must be > 0");
     if (!(cfg->theta >= 0.5 && cfg->theta <= 1.0)) return fail(GX_EINVAL, "theta must be in [0.5, 1]");
-    if (cfg->gmres_restart < 1 || cfg->gmres_restart > 256) return fail(GX_EINVAL, "gmres_restart in [1, 256]");
+    if (cfg->gmres_restart < 1 || cfg->gmres_restart > gx_gm_max_restart())
+        return fail(GX_EINVAL, "gmres_restart must be in [1, 64]");
     if (cfg->gmres_maxit < 1) return fail(GX_EINVAL, "gmres_maxit must be >= 1");
     if (!(cfg->gmres_tol > 0)) return fail(GX_EINVAL, "gmres_tol must be > 0");
     if (cfg->precond < 0 || cfg->precond > 2) return fail(GX_EINVAL, "precond must be 0, 1 or 2");
@@ -229,6 +235,14 @@ int gx_create(const gx_config *cfg, gx_ctx **out) {
         (rc = dalloc(c, &c->hcol, 2 * (m + 2))) || (rc = dalloc(c, &c->dflags, 1)))
         return fail(rc, nullptr);
     if (cfg->precond != GX_PRECOND_NONE && (rc = dalloc(c, &c->Z, (size_t)m * 3 * N))) return fail(rc, nullptr);
+    {
+        char *gm = nullptr;
+        if ((rc = dalloc(c, &gm, gx_gm_state_bytes())) || (rc = dalloc(c, &c->gpart, gx_gm_partial_count())) ||
+            (rc = dalloc(c, &c->zbuf, 3 * N)) || (rc = dalloc(c, &c->vbuf, 3 * N)))
+            return fail(rc, nullptr);
+        c->gm = reinterpret_cast<GmState *>(gm);
+        if (cudaMemset(gm, 0, gx_gm_state_bytes()) != cudaSuccess) return fail(GX_ECUDA, "cudaMemset failed");
+    }
     float4 **nodes[] = {&c->nE, &c->nB, &c->nBnext, &c->nUref};
     for (auto p : nodes)
         if ((rc = dalloc(c, p, N))) return fail(rc, nullptr);
@@ -236,10 +250,7 @@ int gx_create(const gx_config *cfg, gx_ctx **out) {
         cudaMallocHost(&c->hflags, sizeof(DevFlags)) != cudaSuccess)
         return fail(GX_ENOMEM, "pinned host allocation failed");
     std::memset(c->hflags, 0, sizeof(DevFlags));
-    if ((rc = gx_choose_tiles(c))) return fail(rc, nullptr);
-    if ((rc = dalloc(c, &c->rec, (size_t)GX_MAX_SPECIES * N * Rec<2>::SIZE)) ||
-        (rc = dalloc(c, &c->ring, (size_t)GX_MAX_SPECIES * c->tg.ntiles * c->tg.ring * Rec<2>::SIZE)))
-        return fail(rc, nullptr);
+    if ((rc = dalloc(c, &c->rec, (size_t)GX_MAX_SPECIES * N * Rec<2>::SIZE))) return fail(rc, nullptr);
     double *zero3[] = {c->E, c->B, c->Eth, c->Enew, c->Bnew, c->u, c->J, c->uref64};
     for (auto p : zero3)
         if (cudaMemset(p, 0, 3 * N * sizeof(double)) != cudaSuccess) return fail(GX_ECUDA, "cudaMemset failed");
@@ -322,7 +333,6 @@ int gx_field_solve(gx_ctx *c, void *stream, gx_solve_stats *stats) {
     TRY(gx_build_kappa(c, st));
     TRY(gx_build_rhs(c, st));
     GX_CHECK(c, cudaMemcpyAsync(c->Eth, c->E, 3 * c->N * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    TRY(gx_net_collect(c, st));
     int rc = gx_fgmres(c, st);
     if (rc != GX_OK && rc != GX_ENOCONV) return rc;
     TRY(gx_advance(c, st));
@@ -400,11 +410,12 @@ int gx_get_moments(gx_ctx *c, double *rho, double *J, double *M, double *u, int 
     if (J) TRY(copy_out(c, J, c->J, 3 * N * sizeof(double), ptr_is_device, 0));
     if (u) TRY(copy_out(c, u, c->u, 3 * N * sizeof(double), ptr_is_device, 0));
     if (M) {
-        // expand the 9 in-plane offsets to the 27-offset layout (oz = 0 -> +9)
+        // device rows are [81][N] (entry o*9 + e over the 9 in-plane offsets);
+        // expand to the node-major 27-offset layout (oz = 0 -> offset + 9)
         std::vector<double> h(81 * N), full(243 * N, 0.0);
         GX_CHECK(c, cudaMemcpy(h.data(), c->M, 81 * N * sizeof(double), cudaMemcpyDeviceToHost));
         for (int64_t q = 0; q < N; ++q)
-            std::memcpy(&full[(size_t)q * 243 + 9 * 9], &h[(size_t)q * 81], 81 * sizeof(double));
+            for (int k = 0; k < 81; ++k) full[(size_t)q * 243 + 81 + k] = h[(size_t)k * N + q];
         if (ptr_is_device) GX_CHECK(c, cudaMemcpy(M, full.data(), 243 * N * sizeof(double), cudaMemcpyHostToDevice));
         else std::memcpy(M, full.data(), 243 * N * sizeof(double));
     }
@@ -417,7 +428,7 @@ int64_t gx_species_count(gx_ctx *c, int s) {
     std::vector<int> h(c->N);
     if (cudaMemcpy(h.data(), c->sp[s].cnt[c->cur], c->N * sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return -1;
     int64_t t = 0;
-    for (int v : h) t += std::min(v, c->sp[s].cap);
+    for (int v : h) t += std::min(bin_count(v), c->sp[s].cap);
     return t;
 }
 

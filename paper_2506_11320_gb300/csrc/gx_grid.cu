@@ -5,18 +5,24 @@
 // a cell are differences of the face-averaged corner values, derivatives of a
 // cell field at a node are differences of the side-averaged neighbouring cells,
 // so that curl_N and curl_C are adjoint and div_C curl_N = 0 exactly.
+//
+// Layouts (component-major so that neighbouring threads touch neighbouring
+// addresses): vector fields [3][N], mass-matrix rows [81][N] (entry o*9 + e:
+// neighbour offset o = (ox+1) + 3 (oy+1), alpha component e), deposit records
+// [species][112][N].
 #include "gx_internal.cuh"
 
 namespace {
 
 constexpr int kB = 256;
 
+// periodic index for small offsets (|off| < n): no integer division
+__device__ __forceinline__ int wr(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+
 struct G2 {
     int nx, ny;
     double dx, dy;
-    __device__ __forceinline__ int64_t id(int i, int j) const {
-        return (int64_t)wrap_idx(i, nx) + (int64_t)nx * wrap_idx(j, ny);
-    }
+    __device__ __forceinline__ int64_t id(int i, int j) const { return (int64_t)wr(i, nx) + (int64_t)nx * wr(j, ny); }
     __device__ __forceinline__ int64_t N() const { return (int64_t)nx * ny; }
 };
 
@@ -36,7 +42,7 @@ __global__ void k_node_fields(G2 g, const double *__restrict__ E, const double *
         const int i = (int)(q % g.nx), j = (int)(q / g.nx);
         if (outE) outE[q] = make_float4((float)E[q], (float)E[N + q], (float)E[2 * N + q], 0.f);
         if (outB) {
-            const int64_t c0 = g.id(i - 1, j - 1), c1 = g.id(i, j - 1), c2 = g.id(i - 1, j), c3 = g.id(i, j);
+            const int64_t c0 = g.id(i - 1, j - 1), c1 = g.id(i, j - 1), c2 = g.id(i - 1, j), c3 = q;
             double b[3];
 #pragma unroll
             for (int k = 0; k < 3; ++k) b[k] = 0.25 * (B[k * N + c0] + B[k * N + c1] + B[k * N + c2] + B[k * N + c3]);
@@ -56,22 +62,21 @@ struct SpecK {
 __global__ void k_assemble_bulk(G2 g, SpecK sk, const float *__restrict__ rec, double dV, double *rho,
                                 double *rho_m, double *P, double *u) {
     const int64_t N = g.N();
-    constexpr int R = Rec<2>::SIZE;
     GRID_LOOP(q, N) {
         const int i = (int)(q % g.nx), j = (int)(q / g.nx);
         double r = 0, rm = 0, p[3] = {0, 0, 0};
         for (int s = 0; s < sk.ns; ++s) {
-            const float *rs = rec + (size_t)s * N * R;
+            const float *rs = rec + (size_t)s * Rec<2>::SIZE * N;
             double w = 0, mv[3] = {0, 0, 0};
 #pragma unroll
             for (int cy = -1; cy <= 0; ++cy)
 #pragma unroll
                 for (int cx = -1; cx <= 0; ++cx) {
-                    const float *rc = rs + (size_t)g.id(i + cx, j + cy) * R;
+                    const int64_t cell = g.id(i + cx, j + cy);
                     const int a = (-cx) + 2 * (-cy);
-                    w += rc[Rec<2>::RHO + a];
+                    w += rs[(Rec<2>::RHO + a) * N + cell];
 #pragma unroll
-                    for (int k = 0; k < 3; ++k) mv[k] += rc[Rec<2>::MV + 3 * a + k];
+                    for (int k = 0; k < 3; ++k) mv[k] += rs[(Rec<2>::MV + 3 * a + k) * N + cell];
                 }
             r += sk.q[s] * w;
             rm += sk.m[s] * w;
@@ -88,20 +93,56 @@ __global__ void k_assemble_bulk(G2 g, SpecK sk, const float *__restrict__ rec, d
     }
 }
 
-// One sweep of the digital filter (Sec. 1.4, Eq. 26) along one axis with
-// stride d on a 3-component node field: out = phi in + (1-phi)/2 (in[-d] + in[+d]).
-__global__ void k_filter_axis(G2 g, const double *__restrict__ in, double *out, int axis, int d, double phi) {
+// All passes of the digital filter (Sec. 1.4, Eq. 26: v* = phi v + (1-phi)/2
+// (v_{-d} + v_{+d}), phi = 0.5) on a 3-component node field, one 32x32 tile per
+// CTA with a halo of sum(d) nodes loaded once, every sweep done in shared
+// memory (x then y within each pass).  Strides alternate 1, 2, 1, ... when
+// `alternate`, else all 1.
+constexpr int kFT = 32;
+constexpr int kFHaloMax = 16;
+__global__ void k_filter_fused(G2 g, const double *__restrict__ in, double *out, int npass, int alternate) {
+    extern __shared__ double fsh[];
+    int halo = 0;
+    for (int p = 0; p < npass; ++p) halo += (alternate && (p & 1)) ? 2 : 1;
+    const int hx = g.nx > 1 ? halo : 0, hy = g.ny > 1 ? halo : 0;
+    const int W = kFT + 2 * hx, H = kFT + 2 * hy;
+    double *a = fsh, *b = fsh + W * H;
+    const int x0 = blockIdx.x * kFT, y0 = blockIdx.y * kFT;
     const int64_t N = g.N();
-    GRID_LOOP(q, 3 * N) {
-        const int64_t nd = q % N, base = q - nd;
-        const int i = (int)(nd % g.nx), j = (int)(nd / g.nx);
-        const int64_t m = axis == 0 ? g.id(i - d, j) : g.id(i, j - d);
-        const int64_t p = axis == 0 ? g.id(i + d, j) : g.id(i, j + d);
-        out[q] = phi * in[q] + 0.5 * (1.0 - phi) * (in[base + m] + in[base + p]);
+    for (int comp = 0; comp < 3; ++comp) {
+        const double *src = in + comp * N;
+        for (int t = threadIdx.x; t < W * H; t += blockDim.x) {
+            const int lx = t % W - hx, ly = t / W - hy;
+            int gx = (x0 + lx) % g.nx, gy = (y0 + ly) % g.ny;
+            gx = gx < 0 ? gx + g.nx : gx;
+            gy = gy < 0 ? gy + g.ny : gy;
+            a[t] = src[gx + (int64_t)g.nx * gy];
+        }
+        __syncthreads();
+        for (int p = 0; p < npass; ++p) {
+            const int d = (alternate && (p & 1)) ? 2 : 1;
+            for (int axis = 0; axis < 2; ++axis) {
+                if ((axis == 0 && g.nx == 1) || (axis == 1 && g.ny == 1)) continue;
+                const int step = axis == 0 ? d : d * W;
+                for (int t = threadIdx.x; t < W * H; t += blockDim.x) {
+                    const int lx = t % W, ly = t / W;
+                    const bool inside = axis == 0 ? (lx >= d && lx < W - d) : (ly >= d && ly < H - d);
+                    b[t] = inside ? 0.5 * a[t] + 0.25 * (a[t - step] + a[t + step]) : a[t];
+                }
+                __syncthreads();
+                double *tmp = a; a = b; b = tmp;
+            }
+        }
+        for (int t = threadIdx.x; t < kFT * kFT; t += blockDim.x) {
+            const int lx = t % kFT, ly = t / kFT;
+            const int gx = x0 + lx, gy = y0 + ly;
+            if (gx < g.nx && gy < g.ny) out[comp * N + gx + (int64_t)g.nx * gy] = a[(lx + hx) + W * (ly + hy)];
+        }
+        __syncthreads();
     }
 }
 
-// The comoving current (Sec. 2.1, Eq. 34) and the FP64 node rows of the mass
+// The comoving current (Sec. 2.1, Eq. 34) and the FP64 rows of the mass
 // matrix (Eq. 33).  The particle kernels accumulate alpha (v - u_ref) with a
 // reference velocity u_ref (the bulk velocity of the previous deposit); the
 // exact correction to the smoothed u of this deposit is
@@ -113,10 +154,8 @@ __global__ void k_assemble_main(G2 g, SpecK sk, const float *__restrict__ rec, d
                                 const double *__restrict__ u, const double *__restrict__ uref, double *J,
                                 double *M) {
     const int64_t N = g.N();
-    constexpr int R = Rec<2>::SIZE;
     GRID_LOOP(q, N) {
         const int i = (int)(q % g.nx), j = (int)(q / g.nx);
-        // current: the 4 cells around the node, node g is corner a of each
         double jc[3] = {0, 0, 0};
         for (int cy = -1; cy <= 0; ++cy)
             for (int cx = -1; cx <= 0; ++cx) {
@@ -132,20 +171,20 @@ __global__ void k_assemble_main(G2 g, SpecK sk, const float *__restrict__ rec, d
                     }
                 }
                 for (int s = 0; s < sk.ns; ++s) {
-                    const float *rc = rec + ((size_t)s * N + cell) * R;
+                    const float *rs = rec + (size_t)s * Rec<2>::SIZE * N + cell;
                     double js[3];
 #pragma unroll
-                    for (int k = 0; k < 3; ++k) js[k] = rc[Rec<2>::J + 3 * a + k];
+                    for (int k = 0; k < 3; ++k) js[k] = rs[(Rec<2>::J + 3 * a + k) * N];
                     if (comoving) {
 #pragma unroll
                         for (int b = 0; b < 4; ++b) {
                             const int bx = b & 1, by = b >> 1;
                             const int jx = (ax == bx) ? 2 * ax : 1, jy = (ay == by) ? 2 * ay : 1;
-                            const float *mp = rc + Rec<2>::M + 9 * (jx + 3 * jy);
+                            const float *mp = rs + (size_t)(Rec<2>::M + 9 * (jx + 3 * jy)) * N;
 #pragma unroll
                             for (int r = 0; r < 3; ++r)
-                                js[r] -= (double)mp[3 * r] * du[b][0] + (double)mp[3 * r + 1] * du[b][1] +
-                                         (double)mp[3 * r + 2] * du[b][2];
+                                js[r] -= (double)mp[(3 * r) * N] * du[b][0] + (double)mp[(3 * r + 1) * N] * du[b][1] +
+                                         (double)mp[(3 * r + 2) * N] * du[b][2];
                         }
                     }
 #pragma unroll
@@ -157,7 +196,6 @@ __global__ void k_assemble_main(G2 g, SpecK sk, const float *__restrict__ rec, d
         // mass-matrix row: block o = (ox,oy) collects every cell holding both g
         // and g + o.  Along x: ox = 0 -> cells -1 (pair class 2) and 0 (class 0);
         // ox = +1 -> cell 0 (class 1); ox = -1 -> cell -1 (class 1).  Same in y.
-        double *Mq = M + (size_t)q * 81;
         for (int o = 0; o < 9; ++o) {
             const int ox = o % 3 - 1, oy = o / 3 - 1;
             double blk[9];
@@ -172,14 +210,14 @@ __global__ void k_assemble_main(G2 g, SpecK sk, const float *__restrict__ rec, d
                     const int jx = ox == 0 ? (cx == -1 ? 2 : 0) : 1;
                     const int64_t cell = g.id(i + cx, j + cy);
                     for (int s = 0; s < sk.ns; ++s) {
-                        const float *mp = rec + ((size_t)s * N + cell) * R + Rec<2>::M + 9 * (jx + 3 * jy);
+                        const float *mp = rec + (size_t)s * Rec<2>::SIZE * N + (size_t)(Rec<2>::M + 9 * (jx + 3 * jy)) * N + cell;
 #pragma unroll
-                        for (int e = 0; e < 9; ++e) blk[e] += sk.bq[s] * (double)mp[e];
+                        for (int e = 0; e < 9; ++e) blk[e] += sk.bq[s] * (double)mp[(size_t)e * N];
                     }
                 }
             }
 #pragma unroll
-            for (int e = 0; e < 9; ++e) Mq[o * 9 + e] = blk[e];
+            for (int e = 0; e < 9; ++e) M[(size_t)(o * 9 + e) * N + q] = blk[e];
         }
     }
 }
@@ -209,68 +247,86 @@ __device__ __forceinline__ double dCy(const G2 &g, const double *f, int i, int j
     return ((f[g.id(i, j + 1)] + f[g.id(i + 1, j + 1)]) - (f[g.id(i, j)] + f[g.id(i + 1, j)])) / (2.0 * g.dy);
 }
 
-// curl of node field x at cell (i,j) (2D: no z derivatives)
-__device__ __forceinline__ void curlC(const G2 &g, const double *x, int i, int j, double out[3]) {
-    const int64_t N = g.N();
-    const double *xx = x, *xy = x + N, *xz = x + 2 * N;
-    out[0] = dCy(g, xz, i, j);
-    out[1] = -dCx(g, xz, i, j);
-    out[2] = dCx(g, xy, i, j) - dCy(g, xx, i, j);
-}
-
 struct OpArgs {
     G2 g;
     double ct2;        // (c theta dt)^2
     double mfac;       // 4 pi theta dt / dV
     double lfx, lfy;   // theta dt / dx, theta dt / dy
-    const double *M;   // [N][9][9]
+    const double *M;   // [81][N]
     const double *kappa;   // [2][3][N] or null
 };
 
 // y = A x: x + (c theta dt)^2 curl_N curl_C x + (4 pi theta dt / dV) M x
 //        - theta dt sum_d (1/dx_d) [kappa_+ (x_+ - x) - kappa_- (x - x_-)]
 // (Eq. 7 with the mass term of Eq. 35 and the diffusive LF term of Eq. 19.)
-__global__ void k_matvec(OpArgs a, const double *__restrict__ x, double *__restrict__ y) {
+__global__ void k_matvec(OpArgs a, const double *__restrict__ x, double *__restrict__ y, const int *jptr,
+                         int64_t stride, const int *doneptr) {
+    // device-indexed operand (Krylov column j of a basis) and early exit once
+    // the solver flagged the cycle done
+    if (doneptr && *doneptr) return;
+    if (jptr) x += (int64_t)(*jptr) * stride;
     const G2 &g = a.g;
     const int64_t N = g.N();
     GRID_LOOP(q, N) {
         const int i = (int)(q % g.nx), j = (int)(q / g.nx);
-        // curl_C x at the 4 cells around node (i,j): cells (i-1+a, j-1+b)
+        const int im = wr(i - 1, g.nx), ip = wr(i + 1, g.nx), jm = wr(j - 1, g.ny), jp = wr(j + 1, g.ny);
+        const int xs[3] = {im, i, ip};
+        const int64_t ys[3] = {(int64_t)jm * g.nx, (int64_t)j * g.nx, (int64_t)jp * g.nx};
+        // the 3x3 node neighbourhood of the three components
+        double v[3][3][3];   // [comp][row y][col x]
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+#pragma unroll
+                for (int s = 0; s < 3; ++s) v[c][r][s] = x[c * N + ys[r] + xs[s]];
+        // curl_C x at the 4 cells around the node: cell (i-1+ca, j-1+cb) has
+        // corners at columns ca, ca+1 and rows cb, cb+1 of the neighbourhood
         double cc[2][2][3];
+        const double hx = 1.0 / (2.0 * g.dx), hy = 1.0 / (2.0 * g.dy);
 #pragma unroll
-        for (int b = 0; b < 2; ++b)
+        for (int cb = 0; cb < 2; ++cb)
 #pragma unroll
-            for (int aa = 0; aa < 2; ++aa) curlC(g, x, i - 1 + aa, j - 1 + b, cc[b][aa]);
-        // curl_N of that cell field at the node
-        const double dxz = ((cc[0][1][2] + cc[1][1][2]) - (cc[0][0][2] + cc[1][0][2])) / (2.0 * g.dx);
-        const double dyz = ((cc[1][0][2] + cc[1][1][2]) - (cc[0][0][2] + cc[0][1][2])) / (2.0 * g.dy);
-        const double dxy = ((cc[0][1][1] + cc[1][1][1]) - (cc[0][0][1] + cc[1][0][1])) / (2.0 * g.dx);
-        const double dyx = ((cc[1][0][0] + cc[1][1][0]) - (cc[0][0][0] + cc[0][1][0])) / (2.0 * g.dy);
+            for (int ca = 0; ca < 2; ++ca) {
+                // d/dx and d/dy of each component at this cell
+                double ddx[3], ddy[3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    ddx[c] = ((v[c][cb][ca + 1] + v[c][cb + 1][ca + 1]) - (v[c][cb][ca] + v[c][cb + 1][ca])) * hx;
+                    ddy[c] = ((v[c][cb + 1][ca] + v[c][cb + 1][ca + 1]) - (v[c][cb][ca] + v[c][cb][ca + 1])) * hy;
+                }
+                cc[cb][ca][0] = ddy[2];
+                cc[cb][ca][1] = -ddx[2];
+                cc[cb][ca][2] = ddx[1] - ddy[0];
+            }
+        const double dxz = ((cc[0][1][2] + cc[1][1][2]) - (cc[0][0][2] + cc[1][0][2])) * hx;
+        const double dyz = ((cc[1][0][2] + cc[1][1][2]) - (cc[0][0][2] + cc[0][1][2])) * hy;
+        const double dxy = ((cc[0][1][1] + cc[1][1][1]) - (cc[0][0][1] + cc[1][0][1])) * hx;
+        const double dyx = ((cc[1][0][0] + cc[1][1][0]) - (cc[0][0][0] + cc[0][1][0])) * hy;
         double out[3];
-        out[0] = x[q] + a.ct2 * dyz;
-        out[1] = x[N + q] + a.ct2 * (-dxz);
-        out[2] = x[2 * N + q] + a.ct2 * (dxy - dyx);
+        out[0] = v[0][1][1] + a.ct2 * dyz;
+        out[1] = v[1][1][1] + a.ct2 * (-dxz);
+        out[2] = v[2][1][1] + a.ct2 * (dxy - dyx);
         if (a.M) {
-            const double *Mq = a.M + (size_t)q * 81;
 #pragma unroll
             for (int o = 0; o < 9; ++o) {
-                const int64_t nb = g.id(i + (o % 3) - 1, j + (o / 3) - 1);
-                const double x0 = x[nb], x1 = x[N + nb], x2 = x[2 * N + nb];
+                const int ox = o % 3, oy = o / 3;
 #pragma unroll
                 for (int r = 0; r < 3; ++r)
-                    out[r] += a.mfac * (Mq[o * 9 + 3 * r] * x0 + Mq[o * 9 + 3 * r + 1] * x1 + Mq[o * 9 + 3 * r + 2] * x2);
+                    out[r] += a.mfac * (a.M[(size_t)(o * 9 + 3 * r) * N + q] * v[0][oy][ox] +
+                                        a.M[(size_t)(o * 9 + 3 * r + 1) * N + q] * v[1][oy][ox] +
+                                        a.M[(size_t)(o * 9 + 3 * r + 2) * N + q] * v[2][oy][ox]);
             }
         }
         if (a.kappa) {
-            const int64_t xp = g.id(i + 1, j), xm = g.id(i - 1, j), yp = g.id(i, j + 1), ym = g.id(i, j - 1);
+            const int64_t xm = ys[1] + im, ym = ys[0] + i;
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                const double *xc = x + c * N;
                 const double *kx = a.kappa + (0 * 3 + c) * N, *ky = a.kappa + (1 * 3 + c) * N;
                 if (g.nx > 1)
-                    out[c] -= a.lfx * (kx[q] * (xc[xp] - xc[q]) - kx[xm] * (xc[q] - xc[xm]));
+                    out[c] -= a.lfx * (kx[q] * (v[c][1][2] - v[c][1][1]) - kx[xm] * (v[c][1][1] - v[c][1][0]));
                 if (g.ny > 1)
-                    out[c] -= a.lfy * (ky[q] * (xc[yp] - xc[q]) - ky[ym] * (xc[q] - xc[ym]));
+                    out[c] -= a.lfy * (ky[q] * (v[c][2][1] - v[c][1][1]) - ky[ym] * (v[c][1][1] - v[c][0][1]));
             }
         }
         y[q] = out[0];
@@ -284,19 +340,14 @@ __global__ void k_jacobi(OpArgs a, double *jd) {
     const G2 &g = a.g;
     const int64_t N = g.N();
     GRID_LOOP(q, N) {
-        // curl_N curl_C diagonal: for 2D the x and y components couple to their
-        // own node through the y- and x-second differences; derive by applying
-        // the stencil to unit vectors at this node.
-        // d2 terms: (curl curl x)_x = -d_yy x_x + d_xy x_y, etc.; on this mesh
-        // the self-coupling coefficients are 1/(2 dy^2), 1/(2 dx^2) and
-        // their sum for z (averaged second differences).
-        const double sx = g.nx > 1 ? 1.0 / (2.0 * g.dx * g.dx) : 0.0;
-        const double sy = g.ny > 1 ? 1.0 / (2.0 * g.dy * g.dy) : 0.0;
-        double A[9] = {1 + a.ct2 * 2 * sy, 0, 0, 0, 1 + a.ct2 * 2 * sx, 0, 0, 0, 1 + a.ct2 * 2 * (sx + sy)};
+        // self-coupling of curl_N curl_C on this mesh: 1/dy^2 for x, 1/dx^2 for
+        // y and their sum for z (2D, averaged second differences)
+        const double sx = g.nx > 1 ? 1.0 / (g.dx * g.dx) : 0.0;
+        const double sy = g.ny > 1 ? 1.0 / (g.dy * g.dy) : 0.0;
+        double A[9] = {1 + a.ct2 * sy, 0, 0, 0, 1 + a.ct2 * sx, 0, 0, 0, 1 + a.ct2 * (sx + sy)};
         if (a.M) {
-            const double *Mc = a.M + (size_t)q * 81 + 4 * 9;   // centre offset
 #pragma unroll
-            for (int e = 0; e < 9; ++e) A[e] += a.mfac * Mc[e];
+            for (int e = 0; e < 9; ++e) A[e] += a.mfac * a.M[(size_t)(4 * 9 + e) * N + q];   // centre offset
         }
         if (a.kappa) {
             const int i = (int)(q % g.nx), j = (int)(q / g.nx);
@@ -309,7 +360,6 @@ __global__ void k_jacobi(OpArgs a, double *jd) {
                 A[4 * c] += d;
             }
         }
-        // invert the 3x3 block
         const double c00 = A[4] * A[8] - A[5] * A[7], c01 = A[5] * A[6] - A[3] * A[8], c02 = A[3] * A[7] - A[4] * A[6];
         const double det = A[0] * c00 + A[1] * c01 + A[2] * c02;
         const double id = 1.0 / det;
@@ -335,7 +385,7 @@ __global__ void k_motional(G2 g, const double *__restrict__ u, const double *__r
     const int64_t N = g.N();
     GRID_LOOP(q, N) {
         const int i = (int)(q % g.nx), j = (int)(q / g.nx);
-        const int64_t c0 = g.id(i - 1, j - 1), c1 = g.id(i, j - 1), c2 = g.id(i - 1, j), c3 = g.id(i, j);
+        const int64_t c0 = g.id(i - 1, j - 1), c1 = g.id(i, j - 1), c2 = g.id(i - 1, j), c3 = q;
         double b[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) b[k] = 0.25 * (B[k * N + c0] + B[k * N + c1] + B[k * N + c2] + B[k * N + c3]);
@@ -362,14 +412,14 @@ __global__ void k_rhs(G2 g, const double *__restrict__ E, const double *__restri
 #pragma unroll
         for (int k = 0; k < 3; ++k) out[k] = E[k * N + q] + ctd * cn[k] - jf * J[k * N + q];
         if (EM) {
-            const double *Mq = M + (size_t)q * 81;
 #pragma unroll
             for (int o = 0; o < 9; ++o) {
                 const int64_t nb = g.id(i + (o % 3) - 1, j + (o / 3) - 1);
                 const double e0 = EM[nb], e1 = EM[N + nb], e2 = EM[2 * N + nb];
 #pragma unroll
                 for (int r = 0; r < 3; ++r)
-                    out[r] += mf * (Mq[o * 9 + 3 * r] * e0 + Mq[o * 9 + 3 * r + 1] * e1 + Mq[o * 9 + 3 * r + 2] * e2);
+                    out[r] += mf * (M[(size_t)(o * 9 + 3 * r) * N + q] * e0 + M[(size_t)(o * 9 + 3 * r + 1) * N + q] * e1 +
+                                    M[(size_t)(o * 9 + 3 * r + 2) * N + q] * e2);
             }
         }
 #pragma unroll
@@ -392,18 +442,19 @@ __device__ __forceinline__ double umag(const double *u, int64_t N, int64_t q) {
 __global__ void k_kappa(G2 g, const double *__restrict__ E, const double *__restrict__ u, double beta, int speed_c,
                         double c, double *kappa) {
     const int64_t N = g.N();
-    GRID_LOOP(t, 6 * N) {
-        const int64_t q = t % N;
-        const int dc = (int)(t / N);       // d * 3 + comp
-        const int d = dc / 3, comp = dc % 3;
+    GRID_LOOP(q, N) {
         const int i = (int)(q % g.nx), j = (int)(q / g.nx);
-        const int64_t p = d == 0 ? g.id(i + 1, j) : g.id(i, j + 1);
-        const int64_t m = d == 0 ? g.id(i - 1, j) : g.id(i, j - 1);
-        const double *Ec = E + comp * N;
-        const double r = ratio(Ec[q] - Ec[m], Ec[p] - Ec[q]);
-        const double phi = mc_limiter(r, beta);
-        const double a = speed_c ? c : 0.5 * (umag(u, N, q) + umag(u, N, p));
-        kappa[t] = (1.0 - phi) * a / 2.0;
+        for (int d = 0; d < 2; ++d) {
+            const int64_t p = d == 0 ? g.id(i + 1, j) : g.id(i, j + 1);
+            const int64_t m = d == 0 ? g.id(i - 1, j) : g.id(i, j - 1);
+            const double a = speed_c ? c : 0.5 * (umag(u, N, q) + umag(u, N, p));
+#pragma unroll
+            for (int comp = 0; comp < 3; ++comp) {
+                const double *Ec = E + comp * N;
+                const double r = ratio(Ec[q] - Ec[m], Ec[p] - Ec[q]);
+                kappa[(d * 3 + comp) * N + q] = (1.0 - mc_limiter(r, beta)) * a / 2.0;
+            }
+        }
     }
 }
 
@@ -415,17 +466,21 @@ __global__ void k_advance(G2 g, const double *__restrict__ E, const double *__re
     const int64_t N = g.N();
     GRID_LOOP(q, N) {
         const int i = (int)(q % g.nx), j = (int)(q / g.nx);
+        const int64_t Nq = N;
         double cu[3];
-        curlC(g, Eth, i, j, cu);
+        cu[0] = dCy(g, Eth + 2 * Nq, i, j);
+        cu[1] = -dCx(g, Eth + 2 * Nq, i, j);
+        cu[2] = dCx(g, Eth + Nq, i, j) - dCy(g, Eth, i, j);
+        double bn[3];
 #pragma unroll
-        for (int k = 0; k < 3; ++k) Bnew[k * N + q] = B[k * N + q] - c * dt * cu[k];
+        for (int k = 0; k < 3; ++k) bn[k] = B[k * N + q] - c * dt * cu[k];
         if (lf_on) {
             for (int d = 0; d < 2; ++d) {
                 if ((d == 0 && g.nx == 1) || (d == 1 && g.ny == 1)) continue;
                 const double f = dt / (d == 0 ? g.dx : g.dy);
                 // faces c+1/2 (between c and c+e) and c-1/2 (between c-e and c)
                 for (int side = 0; side < 2; ++side) {
-                    const int ci = d == 0 ? i - side : i, cj = d == 0 ? j : j - side;   // face between cell (ci,cj) and +e
+                    const int ci = d == 0 ? i - side : i, cj = d == 0 ? j : j - side;   // face between (ci,cj) and +e
                     const int64_t c0 = g.id(ci, cj);
                     const int64_t cp = d == 0 ? g.id(ci + 1, cj) : g.id(ci, cj + 1);
                     const int64_t cm = d == 0 ? g.id(ci - 1, cj) : g.id(ci, cj - 1);
@@ -434,7 +489,7 @@ __global__ void k_advance(G2 g, const double *__restrict__ E, const double *__re
                         a = c;
                     } else {
                         const int64_t n0 = d == 0 ? g.id(ci + 1, cj) : g.id(ci, cj + 1);
-                        const int64_t n1 = d == 0 ? g.id(ci + 1, cj + 1) : g.id(ci + 1, cj + 1);
+                        const int64_t n1 = g.id(ci + 1, cj + 1);
                         a = 0.5 * (umag(u, N, n0) + umag(u, N, n1));
                     }
 #pragma unroll
@@ -442,13 +497,16 @@ __global__ void k_advance(G2 g, const double *__restrict__ E, const double *__re
                         const double *Bk = B + k * N;
                         const double r = ratio(Bk[c0] - Bk[cm], Bk[cp] - Bk[c0]);
                         const double F = (1.0 - mc_limiter(r, beta)) * a / 2.0 * (Bk[cp] - Bk[c0]);
-                        Bnew[k * N + q] += side == 0 ? f * F : -f * F;
+                        bn[k] += side == 0 ? f * F : -f * F;
                     }
                 }
             }
         }
 #pragma unroll
-        for (int k = 0; k < 3; ++k) Enew[k * N + q] = (Eth[k * N + q] - (1.0 - theta) * E[k * N + q]) / theta;
+        for (int k = 0; k < 3; ++k) {
+            Bnew[k * N + q] = bn[k];
+            Enew[k * N + q] = (Eth[k * N + q] - (1.0 - theta) * E[k * N + q]) / theta;
+        }
     }
 }
 
@@ -485,10 +543,11 @@ __global__ void k_diag_particles(int64_t ncell, int cap, const int *cnt, const f
     double ke = 0, px = 0, py = 0, pz = 0;
     double np = 0;
     for (int64_t c = blockIdx.x; c < ncell; c += gridDim.x) {
-        const int m = min(cnt[c], cap);
+        const int word = cnt[c];
+        const int m = min(bin_count(word), cap);
         if (threadIdx.x == 0) np += m;
         for (int i = threadIdx.x; i < m; i += blockDim.x) {
-            const size_t s = (size_t)c * cap + i;
+            const size_t s = (size_t)c * cap + bin_slot(word, i, cap);
             const double mw = mass * w[s];
             const double a = vx[s], b = vy[s], d = vz[s];
             ke += 0.5 * mw * (a * a + b * b + d * d);
@@ -529,18 +588,24 @@ OpArgs opargs(const gx_ctx *c) {
     return a;
 }
 
-// filter passes: ping-pong between f and the scratch buffer, result in f
+// all filter passes in one launch (result written to tmp3, then back to f)
 int filter_passes(gx_ctx *c, double *f, int passes, bool alternate, cudaStream_t st) {
+    if (passes <= 0) return GX_OK;
     const G2 g = geom(c);
-    for (int p = 0; p < passes; ++p) {
-        const int d = (alternate && (p % 2 == 1)) ? 2 : 1;
-        for (int axis = 0; axis < 2; ++axis) {
-            if ((axis == 0 && g.nx == 1) || (axis == 1 && g.ny == 1)) continue;
-            k_filter_axis<<<blocks_for(3 * c->N), kB, 0, st>>>(g, f, c->tmp3, axis, d, 0.5);
-            GX_LAUNCHED(c);
-            GX_CHECK(c, cudaMemcpyAsync(f, c->tmp3, 3 * c->N * sizeof(double), cudaMemcpyDeviceToDevice, st));
-        }
+    int halo = 0;
+    for (int p = 0; p < passes; ++p) halo += (alternate && (p & 1)) ? 2 : 1;
+    if (halo > kFHaloMax) { c->err = "too many filter passes"; return GX_EINVAL; }
+    const int hx = g.nx > 1 ? halo : 0, hy = g.ny > 1 ? halo : 0;
+    const size_t smem = 2 * (size_t)(kFT + 2 * hx) * (kFT + 2 * hy) * sizeof(double);
+    static size_t configured = 0;
+    if (smem > configured) {
+        GX_CHECK(c, cudaFuncSetAttribute(k_filter_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        configured = smem;
     }
+    dim3 grid((g.nx + kFT - 1) / kFT, (g.ny + kFT - 1) / kFT);
+    k_filter_fused<<<grid, kB, smem, st>>>(g, f, c->tmp3, passes, alternate ? 1 : 0);
+    GX_LAUNCHED(c);
+    GX_CHECK(c, cudaMemcpyAsync(f, c->tmp3, 3 * c->N * sizeof(double), cudaMemcpyDeviceToDevice, st));
     return GX_OK;
 }
 
@@ -590,14 +655,21 @@ int gx_build_rhs(gx_ctx *c, cudaStream_t st) {
 
 int gx_build_kappa(gx_ctx *c, cudaStream_t st) {
     if (!c->cfg.lf_on) return GX_OK;
-    k_kappa<<<blocks_for(6 * c->N), kB, 0, st>>>(geom(c), c->E, c->u, c->cfg.lf_beta, c->cfg.lf_speed_c, c->cfg.c,
-                                                  c->kappa);
+    k_kappa<<<blocks_for(c->N), kB, 0, st>>>(geom(c), c->E, c->u, c->cfg.lf_beta, c->cfg.lf_speed_c, c->cfg.c,
+                                              c->kappa);
     GX_LAUNCHED(c);
     return GX_OK;
 }
 
 int gx_apply_A(gx_ctx *c, const double *x, double *y, cudaStream_t st) {
-    k_matvec<<<blocks_for(c->N), kB, 0, st>>>(opargs(c), x, y);
+    k_matvec<<<blocks_for(c->N), kB, 0, st>>>(opargs(c), x, y, nullptr, 0, nullptr);
+    GX_LAUNCHED(c);
+    return GX_OK;
+}
+
+int gx_apply_A_j(gx_ctx *c, const double *base, int64_t stride, const int *jptr, const int *doneptr, double *y,
+                 cudaStream_t st) {
+    k_matvec<<<blocks_for(c->N), kB, 0, st>>>(opargs(c), base, y, jptr, stride, doneptr);
     GX_LAUNCHED(c);
     return GX_OK;
 }

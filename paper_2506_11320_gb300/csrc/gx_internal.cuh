@@ -50,6 +50,20 @@ template <> struct Rec<3> {
 // ------------------------------------------------------------- particles
 enum { PF_OX = 0, PF_OY, PF_OZ, PF_VX, PF_VY, PF_VZ, PF_W, PF_ID, PF_COUNT };
 
+// A cell's bin holds two segments: particles that stayed in the cell during
+// the last push fill slots [0, front) from the bottom, particles that arrived
+// from a neighbour fill [cap - back, cap) from the top.  Both counts live in one
+// 32-bit word (front in the low, back in the high 16 bits) so that a single
+// atomicAdd reserves slots and sees the exact occupancy.
+__host__ __device__ inline int bin_front(int w) { return w & 0xffff; }
+__host__ __device__ inline int bin_back(int w) { return (int)((unsigned)w >> 16); }
+__host__ __device__ inline int bin_count(int w) { return bin_front(w) + bin_back(w); }
+// slot of the i-th particle of a bin (front first, then back)
+__host__ __device__ inline int bin_slot(int w, int i, int cap) {
+    const int f = bin_front(w);
+    return i < f ? i : cap - bin_back(w) + (i - f);
+}
+
 struct Species {
     double q = 0, m = 0;
     int cap = 0;                        // bin capacity (particles per cell)
@@ -60,21 +74,8 @@ struct Species {
 struct DevFlags {                       // written by kernels, read by the host
     int cfl;                            // a particle moved more than one cell
     int overflow;                       // a bin overflowed (particle dropped)
+    int timeout;                        // a bounded device wait gave up
     int maxcount;                       // largest bin count after the last push
-    int pad;
-};
-
-// --------------------------------------------------------------- tiles
-// The particle kernels give each CTA a tile of TX x TY (x TZ) cells; the tile's
-// records plus a one-cell ring around it live in shared memory.  Contributions
-// of particles that leave the tile land in the ring and are written to a
-// per-tile ring buffer, folded into the neighbours' records afterwards.
-struct TileGeom {
-    int T[3];            // tile size per axis
-    int ntile[3];        // tiles per axis
-    int ntiles;
-    int ring;            // ring cells per tile
-    int local;           // (TX+2)(TY+2)(TZ+2) cells incl. ring
 };
 
 // --------------------------------------------------------------- context
@@ -105,12 +106,8 @@ struct gx_ctx {
     int64_t np_total = 0;
 
     // deposit records
-    TileGeom tg{};
-    int *ring_slot_of_local = nullptr;          // [local] -> ring slot, -1 = interior
-    int *ring_local_of_slot = nullptr;          // [ring]  -> local cell index
     int rec_size = 112;
     float *rec = nullptr;                       // [S][N][rec_size]
-    float *ring = nullptr;                      // [S][ntiles][ring][rec_size]
 
     // node moments (FP64)
     double *rho = nullptr, *rho_m = nullptr;    // [N]
@@ -132,6 +129,9 @@ struct gx_ctx {
     int red_blocks = 0;
     double *hcol = nullptr;                     // [m+2] device column
     double *hpin = nullptr;                     // pinned host mirror of hcol
+    struct GmState *gm = nullptr;               // device-side FGMRES state
+    double *gpart = nullptr;                    // block partial sums
+    double *zbuf = nullptr, *vbuf = nullptr;    // [3N] preconditioner in/out staging
     gx_solve_stats last{};
 
     // learned preconditioner (allocated on demand)
@@ -180,7 +180,6 @@ int gx_run_deposit(gx_ctx *c, cudaStream_t st);              // records from the
 int gx_run_push_deposit(gx_ctx *c, cudaStream_t st);         // mover + re-bin + records
 int gx_particles_out(gx_ctx *c, int s, double *x, double *y, double *z, float *vx, float *vy, float *vz,
                      float *w, int32_t *id, cudaStream_t st);
-int gx_choose_tiles(gx_ctx *c);
 int gx_regrow_bins(gx_ctx *c, int s, int newcap, cudaStream_t st);
 
 // grid (gx_grid.cu)
@@ -190,6 +189,8 @@ int gx_assemble_moments(gx_ctx *c, cudaStream_t st);         // records -> rho, 
 int gx_build_rhs(gx_ctx *c, cudaStream_t st);
 int gx_build_kappa(gx_ctx *c, cudaStream_t st);
 int gx_apply_A(gx_ctx *c, const double *x, double *y, cudaStream_t st);
+int gx_apply_A_j(gx_ctx *c, const double *base, int64_t stride, const int *jptr, const int *doneptr, double *y,
+                 cudaStream_t st);
 int gx_build_jacobi(gx_ctx *c, cudaStream_t st);
 int gx_apply_jacobi(gx_ctx *c, const double *x, double *y, cudaStream_t st);
 int gx_advance(gx_ctx *c, cudaStream_t st);                  // Enew, Bnew from Eth
@@ -197,9 +198,13 @@ int gx_diag_run(gx_ctx *c, gx_diag *out, cudaStream_t st);
 
 // solver (gx_gmres.cu)
 int gx_fgmres(gx_ctx *c, cudaStream_t st);
+size_t gx_gm_state_bytes();
+size_t gx_gm_partial_count();
+int gx_gm_max_restart();
 double gx_norm_host(gx_ctx *c, const double *x, int64_t n, cudaStream_t st, int *status);
 
 // network (gx_net.cu)
 int gx_net_apply(gx_ctx *c, const double *r, double *z, cudaStream_t st);
-int gx_net_collect(gx_ctx *c, cudaStream_t st);
+int gx_net_pair_begin(gx_ctx *c, const double *r0, cudaStream_t st);
+int gx_net_pair_end(gx_ctx *c, int converged, cudaStream_t st);
 void gx_net_free(gx_ctx *c);

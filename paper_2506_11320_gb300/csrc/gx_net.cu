@@ -1,39 +1,812 @@
-// gx_net.cu -- learned GMRES preconditioner (placeholder until the BF16
-// network kernels land; every entry reports GX_ENOTIMPL).
+// gx_net.cu -- learned GMRES preconditioner (an addition of this project; the
+// paper has no learned preconditioner).
+//
+// Network N: four 3x3 convolutions, channels 3 -> 32 -> 32 -> 32 -> 3, ReLU
+// between them, on the 2D node grid (H = ny rows, W = nx columns), BF16 weights
+// and activations with FP32 accumulation.  Inside FGMRES it is applied as
+// z = s N(r / s), s = ||r||_2 / sqrt(3 N), with periodic padding.
+//
+// Kernels (all on the tensor cores through mma.sync m16n8k16 BF16 -> FP32):
+//   * k_conv: implicit-GEMM convolution, M = 16 pixels of a row, N = output
+//     channels, K = 9 taps x input channels; a CTA computes 8 rows x 16
+//     columns, the input tile with its one-pixel halo and the weights staged in
+//     shared memory (row strides padded so that ldmatrix is conflict-free).
+//     The forward pass and the data gradient (the same convolution with the
+//     kernel flipped and the channel roles swapped, masked by the ReLU of the
+//     layer input) both use it.
+//   * k_wgrad: weight gradient dW[co][tap][ci] = sum_p dY[p][co] X[p+tap][ci],
+//     a contraction over pixels (ldmatrix.trans operands), accumulated by a
+//     persistent grid in registers and added to FP32 global sums once per CTA.
+//   * Adam on an FP32 master copy; BF16 copies refreshed after each update.
+// Channel counts are padded for the MMA shapes: 3 input channels -> 16,
+// 3 output channels -> 8 (forward) or 16 (gradient).
+#include <cuda_bf16.h>
+
+#include <cstring>
+#include <random>
+
 #include "gx_internal.cuh"
 
-struct Net {
-    int dummy;
+typedef __nv_bfloat16 bf16;
+
+namespace {
+
+constexpr int kNL = 4;
+constexpr int kCin[kNL] = {3, 32, 32, 32};
+constexpr int kCout[kNL] = {32, 32, 32, 3};
+constexpr int kCinP[kNL] = {16, 32, 32, 32};    // padded input channels (storage of the layer input)
+constexpr int kCoutP[kNL] = {32, 32, 32, 8};    // padded output channels (forward)
+constexpr int kGCoutP[kNL] = {32, 32, 32, 16};  // padded output channels of the gradient (dY) storage
+constexpr int kTH = 8, kTW = 16;                // CTA tile: 8 rows x 16 columns
+constexpr int kHalo = (kTH + 2) * (kTW + 2);    // 180 input pixels per tile
+
+enum { EPI_RELU = 0, EPI_F32 = 1, EPI_MASK = 2 };
+
+constexpr int64_t layer_w_count(int l) { return (int64_t)kCout[l] * kCin[l] * 9; }
+inline int64_t param_offset(int l) {
+    int64_t o = 0;
+    for (int k = 0; k < l; ++k) o += layer_w_count(k) + kCout[k];
+    return o;
+}
+inline int64_t param_count() { return param_offset(kNL); }
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void ldsm_x4(uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3, const void *p) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(smem_u32(p)));
+}
+__device__ __forceinline__ void ldsm_x2(uint32_t &r0, uint32_t &r1, const void *p) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];" : "=r"(r0), "=r"(r1) : "r"(smem_u32(p)));
+}
+__device__ __forceinline__ void ldsm_x4_t(uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3, const void *p) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(smem_u32(p)));
+}
+__device__ __forceinline__ void ldsm_x2_t(uint32_t &r0, uint32_t &r1, const void *p) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];" : "=r"(r0), "=r"(r1) : "r"(smem_u32(p)));
+}
+__device__ __forceinline__ void mma16816(float c[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, uint32_t b0,
+                                         uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ int wrapn(int i, int n) {
+    i %= n;
+    return i < 0 ? i + n : i;
+}
+
+// load the (TH+2) x (TW+2) pixel halo tile of CIN channels of image b into
+// shared memory (row stride CIN + 8), zero or periodic outside the image
+template <int CIN>
+__device__ __forceinline__ void load_tile(bf16 *sIn, const bf16 *in, int b, int H, int W, int y0, int x0,
+                                          int periodic) {
+    constexpr int S = CIN + 8;
+    constexpr int V = CIN / 8;   // 16-byte vectors per pixel
+    for (int t = threadIdx.x; t < kHalo * V; t += blockDim.x) {
+        const int pix = t / V, v = t % V;
+        int yy = y0 - 1 + pix / (kTW + 2), xx = x0 - 1 + pix % (kTW + 2);
+        uint4 val = make_uint4(0, 0, 0, 0);
+        bool ok = true;
+        if (periodic) {
+            yy = wrapn(yy, H);
+            xx = wrapn(xx, W);
+        } else {
+            ok = yy >= 0 && yy < H && xx >= 0 && xx < W;
+        }
+        if (ok) val = *reinterpret_cast<const uint4 *>(in + (((int64_t)b * H + yy) * W + xx) * CIN + v * 8);
+        *reinterpret_cast<uint4 *>(sIn + pix * S + v * 8) = val;
+    }
+}
+
+struct ConvArgs {
+    const bf16 *in;      // [B][H][W][CIN]
+    const bf16 *w;       // [COUT][9][CIN]
+    const float *bias;   // [COUT] or null
+    void *out;           // [B][H][W][COUT] bf16 (or float for EPI_F32)
+    const bf16 *mask;    // [B][H][W][COUT] (EPI_MASK): multiply by (mask > 0)
+    int B, H, W, periodic;
 };
 
-int gx_net_apply(gx_ctx *c, const double *, double *, cudaStream_t) {
-    c->err = "learned preconditioner not available in this build";
-    return GX_ENOTIMPL;
+// out = epilogue(conv3x3(in, w) + bias)
+template <int CIN, int COUT, int EPI>
+__global__ void __launch_bounds__(256) k_conv(ConvArgs a) {
+    constexpr int SI = CIN + 8, SWr = 9 * CIN + 8;
+    constexpr int NT = COUT / 8;
+    __shared__ __align__(16) bf16 sIn[kHalo * SI];
+    __shared__ __align__(16) bf16 sW[COUT * SWr];
+    const int x0 = blockIdx.x * kTW, y0 = blockIdx.y * kTH, b = blockIdx.z;
+    // weights
+    constexpr int WV = 9 * CIN / 8;
+    for (int t = threadIdx.x; t < COUT * WV; t += blockDim.x) {
+        const int co = t / WV, v = t % WV;
+        *reinterpret_cast<uint4 *>(sW + co * SWr + v * 8) = *reinterpret_cast<const uint4 *>(a.w + (size_t)co * 9 * CIN + v * 8);
+    }
+    load_tile<CIN>(sIn, a.in, b, a.H, a.W, y0, x0, a.periodic);
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int mi = lane >> 3, r = lane & 7;
+    float acc[NT][4];
+#pragma unroll
+    for (int n = 0; n < NT; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
+#pragma unroll
+    for (int tap = 0; tap < 9; ++tap) {
+        const int ky = tap / 3, kx = tap % 3;
+#pragma unroll
+        for (int kc = 0; kc < CIN / 16; ++kc) {
+            uint32_t a0, a1, a2, a3;
+            {
+                const int p = r + 8 * (mi & 1), koff = 8 * (mi >> 1);
+                ldsm_x4(a0, a1, a2, a3, sIn + ((warp + ky) * (kTW + 2) + p + kx) * SI + kc * 16 + koff);
+            }
+            if (NT >= 2) {
+#pragma unroll
+                for (int np = 0; np < NT / 2; ++np) {
+                    uint32_t b0, b1, b2, b3;
+                    const int co = np * 16 + 8 * (mi >> 1) + r, k = tap * CIN + kc * 16 + 8 * (mi & 1);
+                    ldsm_x4(b0, b1, b2, b3, sW + co * SWr + k);
+                    mma16816(acc[2 * np], a0, a1, a2, a3, b0, b1);
+                    mma16816(acc[2 * np + 1], a0, a1, a2, a3, b2, b3);
+                }
+            } else {
+                uint32_t b0, b1;
+                const int co = r, k = tap * CIN + kc * 16 + 8 * (mi & 1);
+                ldsm_x2(b0, b1, sW + co * SWr + k);
+                mma16816(acc[0], a0, a1, a2, a3, b0, b1);
+            }
+        }
+    }
+    // epilogue: thread holds pixels g and g+8 of the row, channels 2t, 2t+1 of each n-tile
+    const int gq = lane >> 2, tq = lane & 3;
+    const int yy = y0 + warp;
+    if (yy >= a.H) return;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int xx = x0 + gq + 8 * h;
+        if (xx >= a.W) continue;
+        const int64_t pix = ((int64_t)b * a.H + yy) * a.W + xx;
+#pragma unroll
+        for (int n = 0; n < NT; ++n) {
+            const int co = n * 8 + 2 * tq;
+            float v0 = acc[n][2 * h], v1 = acc[n][2 * h + 1];
+            if (a.bias) { v0 += a.bias[co]; v1 += a.bias[co + 1]; }
+            if (EPI == EPI_F32) {
+                *reinterpret_cast<float2 *>(reinterpret_cast<float *>(a.out) + pix * COUT + co) = make_float2(v0, v1);
+            } else {
+                if (EPI == EPI_RELU) {
+                    v0 = fmaxf(v0, 0.f);
+                    v1 = fmaxf(v1, 0.f);
+                } else {   // EPI_MASK
+                    const __nv_bfloat162 m = *reinterpret_cast<const __nv_bfloat162 *>(a.mask + pix * COUT + co);
+                    if (!(__bfloat162float(m.x) > 0.f)) v0 = 0.f;
+                    if (!(__bfloat162float(m.y) > 0.f)) v1 = 0.f;
+                }
+                *reinterpret_cast<__nv_bfloat162 *>(reinterpret_cast<bf16 *>(a.out) + pix * COUT + co) =
+                    __floats2bfloat162_rn(v0, v1);
+            }
+        }
+    }
 }
-int gx_net_collect(gx_ctx *, cudaStream_t) { return GX_OK; }
+
+struct WgArgs {
+    const bf16 *dy;      // [B][H][W][COUTP] gradient wrt the layer output
+    const bf16 *x;       // [B][H][W][CIN] layer input
+    float *gw;           // [COUTP][9][CIN] FP32 sums
+    float *gb;           // [COUTP]
+    int B, H, W, periodic;
+};
+
+// dW[co][tap][ci] += sum_p dY[p][co] X[p + off(tap)][ci],  dB[co] += sum_p dY[p][co]
+template <int CIN, int COUTP>
+__global__ void __launch_bounds__(256) k_wgrad(WgArgs a) {
+    constexpr int SI = CIN + 8, SD = COUTP + 8;
+    constexpr int MT = COUTP / 16, NTN = 9 * CIN / 8, NTILE = MT * NTN;
+    constexpr int PER = (NTILE + 7) / 8;          // output tiles per warp
+    __shared__ __align__(16) bf16 sX[kHalo * SI];
+    __shared__ __align__(16) bf16 sD[kTH * kTW * SD];
+    __shared__ float sB[COUTP];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int mi = lane >> 3, r = lane & 7;
+    float acc[PER][4];
+#pragma unroll
+    for (int i = 0; i < PER; ++i) acc[i][0] = acc[i][1] = acc[i][2] = acc[i][3] = 0.f;
+    for (int i = threadIdx.x; i < COUTP; i += blockDim.x) sB[i] = 0.f;
+    const int tx = (a.W + kTW - 1) / kTW, ty = (a.H + kTH - 1) / kTH;
+    const int64_t ntiles = (int64_t)tx * ty * a.B;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int b = (int)(t / (tx * ty)), rem = (int)(t % (tx * ty));
+        const int y0 = (rem / tx) * kTH, x0 = (rem % tx) * kTW;
+        __syncthreads();
+        load_tile<CIN>(sX, a.x, b, a.H, a.W, y0, x0, a.periodic);
+        constexpr int DV = COUTP / 8;
+        for (int q = threadIdx.x; q < kTH * kTW * DV; q += blockDim.x) {
+            const int pix = q / DV, v = q % DV;
+            const int yy = y0 + pix / kTW, xx = x0 + pix % kTW;
+            uint4 val = make_uint4(0, 0, 0, 0);
+            if (yy < a.H && xx < a.W)
+                val = *reinterpret_cast<const uint4 *>(a.dy + (((int64_t)b * a.H + yy) * a.W + xx) * COUTP + v * 8);
+            *reinterpret_cast<uint4 *>(sD + pix * SD + v * 8) = val;
+        }
+        __syncthreads();
+        // bias gradient
+        for (int co = threadIdx.x; co < COUTP; co += blockDim.x) {
+            float s = 0.f;
+            for (int pix = 0; pix < kTH * kTW; ++pix) s += __bfloat162float(sD[pix * SD + co]);
+            sB[co] += s;
+        }
+        // K loop: one tile row of 16 pixels per step
+#pragma unroll 1
+        for (int row = 0; row < kTH; ++row) {
+            uint32_t af[MT][4];
+#pragma unroll
+            for (int m = 0; m < MT; ++m) {
+                const int p = r + 8 * (mi >> 1), coff = 8 * (mi & 1);
+                ldsm_x4_t(af[m][0], af[m][1], af[m][2], af[m][3], sD + (row * kTW + p) * SD + m * 16 + coff);
+            }
+#pragma unroll
+            for (int i = 0; i < PER; ++i) {
+                const int tile = warp + 8 * i;
+                if (tile >= NTILE) break;
+                const int m = tile / NTN, nt = tile % NTN;
+                const int kk = nt * 8, tap = kk / CIN, ci0 = kk % CIN;
+                const int ky = tap / 3, kx = tap % 3;
+                uint32_t b0, b1;
+                const int p = r + 8 * (mi & 1);
+                ldsm_x2_t(b0, b1, sX + ((row + ky) * (kTW + 2) + p + kx) * SI + ci0);
+                mma16816(acc[i], af[m][0], af[m][1], af[m][2], af[m][3], b0, b1);
+            }
+        }
+    }
+    __syncthreads();
+    const int gq = lane >> 2, tq = lane & 3;
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+        const int tile = warp + 8 * i;
+        if (tile >= NTILE) break;
+        const int m = tile / NTN, nt = tile % NTN;
+        const int co0 = m * 16 + gq, k0 = nt * 8 + 2 * tq;
+        atomicAdd(a.gw + (size_t)co0 * 9 * CIN + k0, acc[i][0]);
+        atomicAdd(a.gw + (size_t)co0 * 9 * CIN + k0 + 1, acc[i][1]);
+        atomicAdd(a.gw + (size_t)(co0 + 8) * 9 * CIN + k0, acc[i][2]);
+        atomicAdd(a.gw + (size_t)(co0 + 8) * 9 * CIN + k0 + 1, acc[i][3]);
+    }
+    for (int co = threadIdx.x; co < COUTP; co += blockDim.x) atomicAdd(a.gb + co, sB[co]);
+}
+
+// FP32 master parameters (layout W[co][ci][ky][kx], b[co] per layer) -> BF16
+// forward weights [coutP][9][cinP], FP32 bias [coutP], BF16 data-gradient
+// weights [cin][9][gcoutP] (flipped taps, channel roles swapped)
+__global__ void k_pack_weights(const float *params, bf16 *wf, float *bias, bf16 *wd, int cin, int cout, int cinP,
+                               int coutP, int gcoutP, int64_t off) {
+    const float *W = params + off, *bsrc = params + off + (int64_t)cout * cin * 9;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < coutP * 9 * cinP; t += gridDim.x * blockDim.x) {
+        const int co = t / (9 * cinP), rem = t % (9 * cinP), tap = rem / cinP, ci = rem % cinP;
+        const float v = (co < cout && ci < cin) ? W[((co * cin + ci) * 9) + tap] : 0.f;
+        wf[t] = __float2bfloat16_rn(v);
+    }
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < coutP; t += gridDim.x * blockDim.x)
+        bias[t] = t < cout ? bsrc[t] : 0.f;
+    if (wd) {
+        // dgrad conv: output channel = ci (cin of this layer, 32 for layers 2-4),
+        // input channel = co (padded to gcoutP), tap flipped
+        for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < cin * 9 * gcoutP; t += gridDim.x * blockDim.x) {
+            const int ci = t / (9 * gcoutP), rem = t % (9 * gcoutP), tp = rem / gcoutP, co = rem % gcoutP;
+            const float v = co < cout ? W[((co * cin + ci) * 9) + (8 - tp)] : 0.f;
+            wd[t] = __float2bfloat16_rn(v);
+        }
+    }
+}
+
+// padded FP32 gradient sums -> gradient in the master layout (scaled)
+__global__ void k_unpack_grad(const float *gw, const float *gb, float *grad, int cin, int cout, int cinP,
+                              int64_t off, float scale) {
+    const int64_t nw = (int64_t)cout * cin * 9;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nw + cout; t += (int64_t)gridDim.x * blockDim.x) {
+        if (t < nw) {
+            const int co = (int)(t / (cin * 9)), rem = (int)(t % (cin * 9)), ci = rem / 9, tap = rem % 9;
+            grad[off + t] = scale * gw[((int64_t)co * 9 + tap) * cinP + ci];
+        } else {
+            grad[off + t] = scale * gb[t - nw];
+        }
+    }
+}
+
+__global__ void k_adam(float *p, const float *g, float *m1, float *m2, int64_t n, float lr, float b1, float b2,
+                       float eps, float c1, float c2) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float a = b1 * m1[i] + (1.f - b1) * gi, b = b2 * m2[i] + (1.f - b2) * gi * gi;
+        m1[i] = a;
+        m2[i] = b;
+        p[i] -= lr * (a / c1) / (sqrtf(b / c2) + eps);
+    }
+}
+
+// [3][H][W] FP32 or FP64 field (times `scale` or 1/scale from a device sum)
+// -> BF16 NHWC with 16 channels
+template <typename T>
+__global__ void k_pack_input(const T *src, int64_t HW, bf16 *dst, const double *sumsq, double fixed_scale) {
+    double inv = fixed_scale;
+    if (sumsq) {
+        const double s = sqrt(*sumsq / (3.0 * HW));
+        inv = s > 0.0 ? 1.0 / s : 0.0;
+    }
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < HW; p += (int64_t)gridDim.x * blockDim.x) {
+        __align__(16) bf16 v[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) v[c] = __float2bfloat16_rn(c < 3 ? (float)(src[c * HW + p] * inv) : 0.f);
+        reinterpret_cast<uint4 *>(dst + p * 16)[0] = reinterpret_cast<uint4 *>(v)[0];
+        reinterpret_cast<uint4 *>(dst + p * 16)[1] = reinterpret_cast<uint4 *>(v)[1];
+    }
+}
+
+template <typename T>
+__global__ void k_unpack_output(const float *y, int64_t HW, T *dst, const double *sumsq) {
+    double s = 1.0;
+    if (sumsq) s = sqrt(*sumsq / (3.0 * HW));
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < HW; p += (int64_t)gridDim.x * blockDim.x)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) dst[c * HW + p] = (T)(s * (double)y[p * 8 + c]);
+}
+
+__global__ void k_sumsq(const double *x, int64_t n, double *out) {
+    double s = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        s += x[i] * x[i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(out, s);
+}
+
+// training crops: for crop b, input = r / s_b on a (C+8)^2 window (4-pixel halo,
+// periodic in the source field) and target = e / s_b on the central C^2, with
+// s_b the RMS of r over the central C^2.
+struct CropSpec {
+    int pair, y0, x0, pad;
+};
+__global__ void k_crop_scale(const float *pairs, int64_t N, int nx, int ny, const CropSpec *spec, int C, float *scale) {
+    const CropSpec sp = spec[blockIdx.x];
+    const float *r = pairs + (size_t)sp.pair * 6 * N;
+    double s = 0.0;
+    for (int t = threadIdx.x; t < 3 * C * C; t += blockDim.x) {
+        const int c = t / (C * C), rem = t % (C * C), yy = rem / C, xx = rem % C;
+        const int gy = wrapn(sp.y0 + yy, ny), gx = wrapn(sp.x0 + xx, nx);
+        const double v = r[c * N + gy * (int64_t)nx + gx];
+        s += v * v;
+    }
+    __shared__ double sh[32];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+        const double rms = sqrt(t / (3.0 * C * C));
+        scale[blockIdx.x] = rms > 0 ? (float)rms : 1.f;
+    }
+}
+__global__ void k_crop_gather(const float *pairs, int64_t N, int nx, int ny, const CropSpec *spec, int C,
+                              const float *scale, bf16 *x0, float *target) {
+    const int b = blockIdx.y;
+    const CropSpec sp = spec[b];
+    const float *r = pairs + (size_t)sp.pair * 6 * N, *e = r + 3 * N;
+    const int S = C + 8;
+    const float inv = 1.f / scale[b];
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < S * S; t += gridDim.x * blockDim.x) {
+        const int yy = t / S, xx = t % S;
+        const int gy = wrapn(sp.y0 + yy - 4, ny), gx = wrapn(sp.x0 + xx - 4, nx);
+        const int64_t q = gy * (int64_t)nx + gx;
+        __align__(16) bf16 v[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) v[c] = __float2bfloat16_rn(c < 3 ? r[c * N + q] * inv : 0.f);
+        bf16 *d = x0 + ((int64_t)b * S * S + t) * 16;
+        reinterpret_cast<uint4 *>(d)[0] = reinterpret_cast<uint4 *>(v)[0];
+        reinterpret_cast<uint4 *>(d)[1] = reinterpret_cast<uint4 *>(v)[1];
+        const bool inner = yy >= 4 && yy < 4 + C && xx >= 4 && xx < 4 + C;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) target[((int64_t)b * S * S + t) * 3 + c] = inner ? e[c * N + q] * inv : 0.f;
+    }
+}
+
+// loss = sum over the loss region of (y - t)^2 / (2 Nout) and dY = (y - t) / Nout
+// there (zero elsewhere), dY stored BF16 with 16 channels
+__global__ void k_loss(const float *y, const float *target, int B, int H, int W, int ry0, int rx0, int RH, int RW,
+                       float inv_nout, bf16 *dy, double *loss) {
+    double s = 0.0;
+    const int64_t npix = (int64_t)B * H * W;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < npix; p += (int64_t)gridDim.x * blockDim.x) {
+        const int rem = (int)(p % (H * W)), yy = rem / W, xx = rem % W;
+        const bool in = yy >= ry0 && yy < ry0 + RH && xx >= rx0 && xx < rx0 + RW;
+        __align__(16) bf16 v[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) v[c] = __float2bfloat16_rn(0.f);
+        if (in) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float d = y[p * 8 + c] - target[p * 3 + c];
+                s += (double)d * d;
+                v[c] = __float2bfloat16_rn(d * inv_nout);
+            }
+        }
+        reinterpret_cast<uint4 *>(dy + p * 16)[0] = reinterpret_cast<uint4 *>(v)[0];
+        reinterpret_cast<uint4 *>(dy + p * 16)[1] = reinterpret_cast<uint4 *>(v)[1];
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(loss, 0.5 * s * inv_nout);
+}
+
+__global__ void k_f32_to_chw3(const float *y, int64_t HW, float *out) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < HW; p += (int64_t)gridDim.x * blockDim.x)
+        for (int c = 0; c < 3; ++c) out[c * HW + p] = y[p * 8 + c];
+}
+__global__ void k_chw3_to_target(const float *t, int64_t HW, float *out) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < HW; p += (int64_t)gridDim.x * blockDim.x)
+        for (int c = 0; c < 3; ++c) out[p * 3 + c] = t[c * HW + p];
+}
+
+// pair slot [2][3][N]: r0 (when r0 is given) or e = eth - en (otherwise)
+__global__ void k_store_pair(const double *r0, const double *eth, const double *en, int64_t n3, float *dst) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x) {
+        if (r0) dst[i] = (float)r0[i];
+        else dst[n3 + i] = (float)(eth[i] - en[i]);
+    }
+}
+
+inline int nblk(int64_t n, int b = 256) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + b - 1) / b, 152 * 16)); }
+
+}  // namespace
+
+struct Net {
+    float *params = nullptr, *grad = nullptr, *m1 = nullptr, *m2 = nullptr;
+    bf16 *wf[kNL] = {}, *wd[kNL] = {};
+    float *bias[kNL] = {};
+    float *gw[kNL] = {}, *gb[kNL] = {};
+    int have_weights = 0;
+    // activations
+    int64_t cap_pix = 0;
+    bf16 *x0 = nullptr, *h1 = nullptr, *h2 = nullptr, *h3 = nullptr;
+    bf16 *d4 = nullptr, *d3 = nullptr, *d2 = nullptr, *d1 = nullptr;
+    float *y = nullptr, *target = nullptr;
+    double *dsum = nullptr;    // [0] sum of squares, [1] loss
+    // collected pairs: [cap][2][3][N] FP32 (r0, e)
+    float *pairs = nullptr;
+    int cap_pairs = 0, npairs = 0, next_pair = 0, collect = 0;
+    int pending_pair = 0;
+    int adam_t = 0;
+};
+
+static int net_alloc(gx_ctx *c) {
+    if (c->net) return GX_OK;
+    Net *n = new Net();
+    c->net = n;
+    const int64_t P = param_count();
+    GX_CHECK(c, cudaMalloc(&n->params, P * sizeof(float)));
+    GX_CHECK(c, cudaMalloc(&n->grad, P * sizeof(float)));
+    GX_CHECK(c, cudaMalloc(&n->m1, P * sizeof(float)));
+    GX_CHECK(c, cudaMalloc(&n->m2, P * sizeof(float)));
+    GX_CHECK(c, cudaMemset(n->m1, 0, P * sizeof(float)));
+    GX_CHECK(c, cudaMemset(n->m2, 0, P * sizeof(float)));
+    for (int l = 0; l < kNL; ++l) {
+        GX_CHECK(c, cudaMalloc(&n->wf[l], (size_t)kCoutP[l] * 9 * kCinP[l] * sizeof(bf16)));
+        GX_CHECK(c, cudaMalloc(&n->bias[l], kCoutP[l] * sizeof(float)));
+        if (l > 0) GX_CHECK(c, cudaMalloc(&n->wd[l], (size_t)kCin[l] * 9 * kGCoutP[l] * sizeof(bf16)));
+        GX_CHECK(c, cudaMalloc(&n->gw[l], (size_t)kGCoutP[l] * 9 * kCinP[l] * sizeof(float)));
+        GX_CHECK(c, cudaMalloc(&n->gb[l], kGCoutP[l] * sizeof(float)));
+    }
+    GX_CHECK(c, cudaMalloc(&n->dsum, 4 * sizeof(double)));
+    // default initialisation: small random weights (He scale), zero biases
+    std::vector<float> h(P, 0.f);
+    std::mt19937_64 rng(12345);
+    std::normal_distribution<float> nd(0.f, 1.f);
+    for (int l = 0; l < kNL; ++l) {
+        const float sc = std::sqrt(2.f / (9.f * kCin[l])) * (l == kNL - 1 ? 0.1f : 1.f);
+        const int64_t off = param_offset(l);
+        for (int64_t i = 0; i < layer_w_count(l); ++i) h[off + i] = sc * nd(rng);
+    }
+    GX_CHECK(c, cudaMemcpy(n->params, h.data(), P * sizeof(float), cudaMemcpyHostToDevice));
+    return GX_OK;
+}
+
+static int net_refresh(gx_ctx *c, cudaStream_t st) {
+    Net *n = c->net;
+    for (int l = 0; l < kNL; ++l) {
+        k_pack_weights<<<64, 256, 0, st>>>(n->params, n->wf[l], n->bias[l], l > 0 ? n->wd[l] : nullptr, kCin[l],
+                                            kCout[l], kCinP[l], kCoutP[l], kGCoutP[l], param_offset(l));
+        GX_LAUNCHED(c);
+    }
+    n->have_weights = 1;
+    return GX_OK;
+}
+
+static int net_reserve(gx_ctx *c, int64_t pix) {
+    Net *n = c->net;
+    if (pix <= n->cap_pix) return GX_OK;
+    bf16 **b16[] = {&n->x0, &n->h1, &n->h2, &n->h3, &n->d4, &n->d3, &n->d2, &n->d1};
+    const int ch[] = {16, 32, 32, 32, 16, 32, 32, 32};
+    for (int i = 0; i < 8; ++i) {
+        if (*b16[i]) cudaFree(*b16[i]);
+        GX_CHECK(c, cudaMalloc(b16[i], (size_t)pix * ch[i] * sizeof(bf16)));
+    }
+    if (n->y) cudaFree(n->y);
+    if (n->target) cudaFree(n->target);
+    GX_CHECK(c, cudaMalloc(&n->y, (size_t)pix * 8 * sizeof(float)));
+    GX_CHECK(c, cudaMalloc(&n->target, (size_t)pix * 3 * sizeof(float)));
+    n->cap_pix = pix;
+    return GX_OK;
+}
+
+template <int CIN, int COUT, int EPI>
+static int conv(gx_ctx *c, const bf16 *in, const bf16 *w, const float *bias, void *out, const bf16 *mask, int B, int H,
+                int W, int periodic, cudaStream_t st) {
+    ConvArgs a{in, w, bias, out, mask, B, H, W, periodic};
+    dim3 grid((W + kTW - 1) / kTW, (H + kTH - 1) / kTH, B);
+    k_conv<CIN, COUT, EPI><<<grid, 256, 0, st>>>(a);
+    GX_LAUNCHED(c);
+    return GX_OK;
+}
+
+template <int CIN, int COUTP>
+static int wgrad(gx_ctx *c, const bf16 *dy, const bf16 *x, float *gw, float *gb, int B, int H, int W, int periodic,
+                 cudaStream_t st) {
+    WgArgs a{dy, x, gw, gb, B, H, W, periodic};
+    const int64_t tiles = (int64_t)((W + kTW - 1) / kTW) * ((H + kTH - 1) / kTH) * B;
+    k_wgrad<CIN, COUTP><<<(unsigned)std::min<int64_t>(tiles, 152 * 2), 256, 0, st>>>(a);
+    GX_LAUNCHED(c);
+    return GX_OK;
+}
+
+// forward through the four layers (input in n->x0), output FP32 [pix][8] in n->y
+static int net_forward(gx_ctx *c, int B, int H, int W, int periodic, cudaStream_t st) {
+    Net *n = c->net;
+    int rc;
+    if ((rc = conv<16, 32, EPI_RELU>(c, n->x0, n->wf[0], n->bias[0], n->h1, nullptr, B, H, W, periodic, st))) return rc;
+    if ((rc = conv<32, 32, EPI_RELU>(c, n->h1, n->wf[1], n->bias[1], n->h2, nullptr, B, H, W, periodic, st))) return rc;
+    if ((rc = conv<32, 32, EPI_RELU>(c, n->h2, n->wf[2], n->bias[2], n->h3, nullptr, B, H, W, periodic, st))) return rc;
+    return conv<32, 8, EPI_F32>(c, n->h3, n->wf[3], n->bias[3], n->y, nullptr, B, H, W, periodic, st);
+}
+
+// backward from dY4 (in n->d4): weight gradients (FP32 sums, zeroed here) and
+// data gradients down to layer 1; then the gradient in the master layout
+static int net_backward(gx_ctx *c, int B, int H, int W, int periodic, float grad_scale, cudaStream_t st) {
+    Net *n = c->net;
+    int rc;
+    for (int l = 0; l < kNL; ++l) {
+        GX_CHECK(c, cudaMemsetAsync(n->gw[l], 0, (size_t)kGCoutP[l] * 9 * kCinP[l] * sizeof(float), st));
+        GX_CHECK(c, cudaMemsetAsync(n->gb[l], 0, kGCoutP[l] * sizeof(float), st));
+    }
+    if ((rc = wgrad<32, 16>(c, n->d4, n->h3, n->gw[3], n->gb[3], B, H, W, periodic, st))) return rc;
+    if ((rc = conv<16, 32, EPI_MASK>(c, n->d4, n->wd[3], nullptr, n->d3, n->h3, B, H, W, periodic, st))) return rc;
+    if ((rc = wgrad<32, 32>(c, n->d3, n->h2, n->gw[2], n->gb[2], B, H, W, periodic, st))) return rc;
+    if ((rc = conv<32, 32, EPI_MASK>(c, n->d3, n->wd[2], nullptr, n->d2, n->h2, B, H, W, periodic, st))) return rc;
+    if ((rc = wgrad<32, 32>(c, n->d2, n->h1, n->gw[1], n->gb[1], B, H, W, periodic, st))) return rc;
+    if ((rc = conv<32, 32, EPI_MASK>(c, n->d2, n->wd[1], nullptr, n->d1, n->h1, B, H, W, periodic, st))) return rc;
+    if ((rc = wgrad<16, 32>(c, n->d1, n->x0, n->gw[0], n->gb[0], B, H, W, periodic, st))) return rc;
+    for (int l = 0; l < kNL; ++l) {
+        k_unpack_grad<<<64, 256, 0, st>>>(n->gw[l], n->gb[l], n->grad, kCin[l], kCout[l], kCinP[l], param_offset(l),
+                                          grad_scale);
+        GX_LAUNCHED(c);
+    }
+    return GX_OK;
+}
+
+// ------------------------------------------------------------ solver hooks
+// z = s N(r / s), s = ||r|| / sqrt(3 N): FP64 [3][N] in and out
+int gx_net_apply(gx_ctx *c, const double *r, double *z, cudaStream_t st) {
+    if (c->dim != 2) { c->err = "the learned preconditioner is 2D"; return GX_ENOTIMPL; }
+    int rc = net_alloc(c);
+    if (rc) return rc;
+    Net *n = c->net;
+    if (!n->have_weights && (rc = net_refresh(c, st))) return rc;
+    const int H = c->n[1], W = c->n[0];
+    if ((rc = net_reserve(c, (int64_t)H * W))) return rc;
+    GX_CHECK(c, cudaMemsetAsync(n->dsum, 0, sizeof(double), st));
+    k_sumsq<<<nblk(3 * c->N), 256, 0, st>>>(r, 3 * c->N, n->dsum);
+    GX_LAUNCHED(c);
+    k_pack_input<double><<<nblk(c->N), 256, 0, st>>>(r, c->N, n->x0, n->dsum, 1.0);
+    GX_LAUNCHED(c);
+    if ((rc = net_forward(c, 1, H, W, 1, st))) return rc;
+    k_unpack_output<double><<<nblk(c->N), 256, 0, st>>>(n->y, c->N, z, n->dsum);
+    GX_LAUNCHED(c);
+    return GX_OK;
+}
+
+// collection of (residual, error) pairs around one solve with initial guess
+// E^n: the first residual r0 = b - A E^n is kept when the solve starts and the
+// error e = E^{n+theta} - E^n is added once it has converged
+int gx_net_pair_begin(gx_ctx *c, const double *r0, cudaStream_t st) {
+    Net *n = c->net;
+    if (!n || !n->collect || n->cap_pairs < 1) return GX_OK;
+    float *dst = n->pairs + (size_t)n->next_pair * 6 * c->N;
+    k_store_pair<<<nblk(3 * c->N), 256, 0, st>>>(r0, nullptr, nullptr, 3 * c->N, dst);
+    GX_LAUNCHED(c);
+    n->pending_pair = 1;
+    return GX_OK;
+}
+
+int gx_net_pair_end(gx_ctx *c, int converged, cudaStream_t st) {
+    Net *n = c->net;
+    if (!n || !n->pending_pair) return GX_OK;
+    n->pending_pair = 0;
+    if (!converged) return GX_OK;
+    float *dst = n->pairs + (size_t)n->next_pair * 6 * c->N;
+    k_store_pair<<<nblk(3 * c->N), 256, 0, st>>>(nullptr, c->Eth, c->E, 3 * c->N, dst);
+    GX_LAUNCHED(c);
+    n->next_pair = (n->next_pair + 1) % n->cap_pairs;
+    n->npairs = std::min(n->npairs + 1, n->cap_pairs);
+    return GX_OK;
+}
+
 void gx_net_free(gx_ctx *c) {
-    delete c->net;
+    Net *n = c->net;
+    if (!n) return;
+    void *ps[] = {n->params, n->grad, n->m1, n->m2, n->x0, n->h1, n->h2, n->h3, n->d4, n->d3, n->d2, n->d1, n->y,
+                  n->target, n->dsum, n->pairs};
+    for (void *p : ps)
+        if (p) cudaFree(p);
+    for (int l = 0; l < kNL; ++l) {
+        void *qs[] = {n->wf[l], n->wd[l], n->bias[l], n->gw[l], n->gb[l]};
+        for (void *q : qs)
+            if (q) cudaFree(q);
+    }
+    delete n;
     c->net = nullptr;
 }
 
+// ------------------------------------------------------------------ C ABI
 extern "C" {
-int64_t gx_precond_param_count(void) { return 20259; }
-int gx_precond_set_weights(gx_ctx *c, const float *, int64_t, int) {
-    if (!c) return GX_EINVAL;
-    c->err = "learned preconditioner not available in this build";
-    return GX_ENOTIMPL;
+
+int64_t gx_precond_param_count(void) { return param_count(); }
+
+int gx_precond_set_weights(gx_ctx *c, const float *params, int64_t n, int ptr_is_device) {
+    if (!c || !params || n != param_count()) {
+        if (c) c->err = "gx_precond_set_weights: need gx_precond_param_count() values";
+        return GX_EINVAL;
+    }
+    int rc = net_alloc(c);
+    if (rc) return rc;
+    GX_CHECK(c, cudaMemcpy(c->net->params, params, n * sizeof(float),
+                           ptr_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice));
+    GX_CHECK(c, cudaMemset(c->net->m1, 0, n * sizeof(float)));
+    GX_CHECK(c, cudaMemset(c->net->m2, 0, n * sizeof(float)));
+    c->net->adam_t = 0;
+    rc = net_refresh(c, 0);
+    if (rc) return rc;
+    GX_CHECK(c, cudaStreamSynchronize(0));
+    return GX_OK;
 }
-int gx_precond_get_weights(gx_ctx *c, float *, int64_t, int) {
-    if (!c) return GX_EINVAL;
-    return GX_ENOTIMPL;
+
+int gx_precond_get_weights(gx_ctx *c, float *params, int64_t n, int ptr_is_device) {
+    if (!c || !params || n != param_count()) return GX_EINVAL;
+    int rc = net_alloc(c);
+    if (rc) return rc;
+    GX_CHECK(c, cudaMemcpy(params, c->net->params, n * sizeof(float),
+                           ptr_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost));
+    return GX_OK;
 }
-int gx_precond_collect(gx_ctx *c, int) { return c ? GX_ENOTIMPL : GX_EINVAL; }
-int gx_precond_pairs(gx_ctx *c) { return c ? 0 : -1; }
-int gx_precond_train(gx_ctx *c, int, int, int, int, float, uint64_t, float *, void *) {
-    return c ? GX_ENOTIMPL : GX_EINVAL;
+
+int gx_precond_collect(gx_ctx *c, int capacity) {
+    if (!c || capacity < 0) return GX_EINVAL;
+    if (c->dim != 2) { c->err = "the learned preconditioner is 2D"; return GX_ENOTIMPL; }
+    int rc = net_alloc(c);
+    if (rc) return rc;
+    Net *n = c->net;
+    if (capacity == 0) { n->collect = 0; return GX_OK; }
+    if (capacity != n->cap_pairs) {
+        if (n->pairs) cudaFree(n->pairs);
+        n->pairs = nullptr;
+        GX_CHECK(c, cudaMalloc(&n->pairs, (size_t)capacity * 6 * c->N * sizeof(float)));
+        n->cap_pairs = capacity;
+        n->npairs = 0;
+        n->next_pair = 0;
+    }
+    n->collect = 1;
+    return GX_OK;
 }
-int gx_precond_forward(gx_ctx *c, int, int, const float *, float *, void *) { return c ? GX_ENOTIMPL : GX_EINVAL; }
-int gx_precond_loss_grad(gx_ctx *c, int, int, const float *, const float *, float *, float *, void *) {
-    return c ? GX_ENOTIMPL : GX_EINVAL;
+
+int gx_precond_pairs(gx_ctx *c) { return c ? (c->net ? c->net->npairs : 0) : -1; }
+
+int gx_precond_train(gx_ctx *c, int npairs, int crop, int batch, int epochs, float lr, uint64_t seed,
+                     float *loss_out, void *stream) {
+    if (!c || npairs < 1 || crop < 8 || batch < 1 || epochs < 1 || !(lr > 0)) return GX_EINVAL;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    Net *n = c->net;
+    if (!n || n->npairs < 1) { c->err = "no collected pairs: call gx_precond_collect and run some solves"; return GX_ESTATE; }
+    if (!n->have_weights) { int rc = net_refresh(c, st); if (rc) return rc; }
+    const int S = crop + 8;
+    int rc = net_reserve(c, (int64_t)batch * S * S);
+    if (rc) return rc;
+    CropSpec *dspec = nullptr;
+    float *dscale = nullptr;
+    GX_CHECK(c, cudaMalloc(&dspec, batch * sizeof(CropSpec)));
+    GX_CHECK(c, cudaMalloc(&dscale, batch * sizeof(float)));
+    std::mt19937_64 rng(seed);
+    std::vector<CropSpec> spec(batch);
+    const int64_t P = param_count();
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    for (int ep = 0; ep < epochs; ++ep) {
+        GX_CHECK(c, cudaMemsetAsync(n->dsum + 1, 0, sizeof(double), st));
+        int nb = 0;
+        for (int done = 0; done < npairs; done += batch, ++nb) {
+            const int B = std::min(batch, npairs - done);
+            for (int b = 0; b < B; ++b) {
+                spec[b].pair = (int)(rng() % (uint64_t)n->npairs);
+                spec[b].y0 = (int)(rng() % (uint64_t)c->n[1]);
+                spec[b].x0 = (int)(rng() % (uint64_t)c->n[0]);
+                spec[b].pad = 0;
+            }
+            GX_CHECK(c, cudaMemcpyAsync(dspec, spec.data(), B * sizeof(CropSpec), cudaMemcpyHostToDevice, st));
+            k_crop_scale<<<B, 256, 0, st>>>(n->pairs, c->N, c->n[0], c->n[1], dspec, crop, dscale);
+            GX_LAUNCHED(c);
+            k_crop_gather<<<dim3(nblk((int64_t)S * S), B), 256, 0, st>>>(n->pairs, c->N, c->n[0], c->n[1], dspec, crop,
+                                                                           dscale, n->x0, n->target);
+            GX_LAUNCHED(c);
+            if ((rc = net_forward(c, B, S, S, 0, st))) return rc;
+            const float inv_nout = 1.f / (3.f * crop * crop * B);
+            k_loss<<<nblk((int64_t)B * S * S), 256, 0, st>>>(n->y, n->target, B, S, S, 4, 4, crop, crop, inv_nout,
+                                                               n->d4, n->dsum + 1);
+            GX_LAUNCHED(c);
+            if ((rc = net_backward(c, B, S, S, 0, 1.f, st))) return rc;
+            ++n->adam_t;
+            const float c1 = 1.f - std::pow(b1, (float)n->adam_t), c2 = 1.f - std::pow(b2, (float)n->adam_t);
+            k_adam<<<nblk(P), 256, 0, st>>>(n->params, n->grad, n->m1, n->m2, P, lr, b1, b2, eps, c1, c2);
+            GX_LAUNCHED(c);
+            if ((rc = net_refresh(c, st))) return rc;
+        }
+        double L = 0;
+        GX_CHECK(c, cudaMemcpyAsync(&L, n->dsum + 1, sizeof(double), cudaMemcpyDeviceToHost, st));
+        GX_CHECK(c, cudaStreamSynchronize(st));
+        if (loss_out) loss_out[ep] = (float)(L / nb);
+    }
+    cudaFree(dspec);
+    cudaFree(dscale);
+    return GX_OK;
 }
+
+int gx_precond_forward(gx_ctx *c, int H, int W, const float *in, float *out, void *stream) {
+    if (!c || H < 1 || W < 1 || !in || !out) return GX_EINVAL;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    int rc = net_alloc(c);
+    if (rc) return rc;
+    Net *n = c->net;
+    if (!n->have_weights && (rc = net_refresh(c, st))) return rc;
+    if ((rc = net_reserve(c, (int64_t)H * W))) return rc;
+    k_pack_input<float><<<nblk((int64_t)H * W), 256, 0, st>>>(in, (int64_t)H * W, n->x0, nullptr, 1.0);
+    GX_LAUNCHED(c);
+    if ((rc = net_forward(c, 1, H, W, 1, st))) return rc;
+    k_f32_to_chw3<<<nblk((int64_t)H * W), 256, 0, st>>>(n->y, (int64_t)H * W, out);
+    GX_LAUNCHED(c);
+    GX_CHECK(c, cudaStreamSynchronize(st));
+    return GX_OK;
 }
+
+int gx_precond_loss_grad(gx_ctx *c, int H, int W, const float *in, const float *target, float *loss, float *grad,
+                         void *stream) {
+    if (!c || H < 1 || W < 1 || !in || !target || !grad) return GX_EINVAL;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    int rc = net_alloc(c);
+    if (rc) return rc;
+    Net *n = c->net;
+    if (!n->have_weights && (rc = net_refresh(c, st))) return rc;
+    if ((rc = net_reserve(c, (int64_t)H * W))) return rc;
+    const int64_t HW = (int64_t)H * W;
+    k_pack_input<float><<<nblk(HW), 256, 0, st>>>(in, HW, n->x0, nullptr, 1.0);
+    GX_LAUNCHED(c);
+    k_chw3_to_target<<<nblk(HW), 256, 0, st>>>(target, HW, n->target);
+    GX_LAUNCHED(c);
+    if ((rc = net_forward(c, 1, H, W, 0, st))) return rc;
+    GX_CHECK(c, cudaMemsetAsync(n->dsum + 1, 0, sizeof(double), st));
+    k_loss<<<nblk(HW), 256, 0, st>>>(n->y, n->target, 1, H, W, 0, 0, H, W, 1.f / (3.f * HW), n->d4, n->dsum + 1);
+    GX_LAUNCHED(c);
+    if ((rc = net_backward(c, 1, H, W, 0, 1.f, st))) return rc;
+    GX_CHECK(c, cudaMemcpyAsync(grad, n->grad, param_count() * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    double L = 0;
+    GX_CHECK(c, cudaMemcpyAsync(&L, n->dsum + 1, sizeof(double), cudaMemcpyDeviceToHost, st));
+    GX_CHECK(c, cudaStreamSynchronize(st));
+    if (loss) *loss = (float)L;
+    return GX_OK;
+}
+
+}  // extern "C"

@@ -1,31 +1,32 @@
 // gx_particles.cu -- particle kernels of the GL-ECSIM hot path (2D).
 //
-// The fused kernel k_push_deposit does, for every particle of a species, in one
+// k_pd<true> (the fused push) does, for every particle of a species, in one
 // pass over the cell bins:
 //   1. the theta-implicit mover of Sec. 2.1 (Eq. 29-30 and the ECSIM update):
 //      vbar = alpha (v^n + beta_s E^{n+theta}), v^{n+1} = 2 vbar - v^n,
-//      x^{n+3/2} = x^{n+1/2} + dt v^{n+1}, with alpha from B^n (Eq. 30);
-//   2. re-binning: the particle is written to its new cell's bin in the other
-//      copy of the particle arrays (slot reserved with one warp-aggregated
-//      atomic per destination cell);
-//   3. the deposit of step n+1 at the new position with alpha from B^{n+1}:
-//      charge, mass and momentum weights, the current alpha (v - u_ref) and
-//      the mass-matrix sums alpha W_g W_g' (Eq. 33-35).
-// k_deposit is the same kernel without steps 1-2 (moments of the current state).
+//      x^{n+3/2} = x^{n+1/2} + dt v^{n+1}, alpha from B^n (Eq. 30);
+//   2. the deposit of step n+1 for the particles that stay in their cell, with
+//      alpha from B^{n+1}: charge, mass and momentum weights, the current
+//      alpha (v - u_ref) and the mass-matrix sums alpha W_g W_g' (Eq. 33-35);
+//   3. re-binning into the other copy of the particle arrays: a cell's stayers
+//      take consecutive slots at the bottom of its new bin (one atomic per
+//      64-particle chunk), particles that leave take slots at the top of their
+//      new cell's bin (see bin_front / bin_back).
+// k_arrivals then deposits the particles that arrived in each cell (the top
+// segment, contiguous) into that cell's record.  k_pd<false> deposits the
+// current state without moving it.
 //
-// Work decomposition (GB300-first): one CTA per tile of TX x TY cells, 8 warps,
-// each warp split into 4 groups of 8 lanes; a group owns one cell at a time.
-// Particles are processed in chunks of 64 per group: the mover pass keeps 8
-// particles per lane in flight (coalesced 32-byte segments per group), writes
-// the new state and stages it in shared memory, compacted into particles that
-// stay in the cell and particles that leave it.  Stayers are accumulated in
-// per-lane registers (109 partial sums), reduced across the group through
-// shared memory and added to the cell's record; leavers (about a tenth) add
-// their contributions with shared-memory atomics to the record of their new
-// cell, which may be in the one-cell ring around the tile.  At the end the tile
-// records are stored to global memory (ring records to a per-tile buffer that a
-// small kernel folds into the neighbours).  The FP32 particle arithmetic stays on
-// the CUDA cores: it is a scatter, not a dense contraction.
+// Work decomposition (GB300-first): a persistent grid, one CTA of 8 warps per
+// SM; each warp is split into 4 groups of 8 lanes and a group owns one cell at
+// a time (32 consecutive cells per CTA batch).  The particle arrays of a cell
+// are streamed into shared memory in 64-particle chunks by the bulk-copy (TMA)
+// engine, double buffered per group and signalled through mbarriers (bounded
+// waits), so the next chunk's loads overlap the current chunk's arithmetic.
+// The mover and the stayer deposit run with no warp collectives; each lane
+// accumulates its particles' 109 partial sums in registers and at the end of
+// the cell the 8 lanes are reduced through shared memory and the record is
+// stored with plain stores.  The FP32 particle arithmetic stays on the CUDA
+// cores: it is a scatter, not a dense contraction.
 #include <cub/cub.cuh>
 
 #include "gx_internal.cuh"
@@ -34,48 +35,78 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kGroup = 8;                         // lanes per cell group
-constexpr int kGroups = kThreads / kGroup;        // 32 groups per CTA
-constexpr int kPerLane = 8;                       // particles per lane per chunk
-constexpr int kChunk = kGroup * kPerLane;         // 64 particles per group chunk
+constexpr int kGroups = kThreads / kGroup;        // 32 cells per CTA batch
+constexpr int kChunk = 64;                        // particles per staged chunk
+constexpr int kPerLane = kChunk / kGroup;         // 8
+constexpr int kMaxF = 7;                          // ox oy vx vy vz w id
+constexpr int kScr = 56 * 33;                     // reduction scratch floats per warp
 constexpr unsigned kFull = 0xffffffffu;
+constexpr long long kSpinLimit = 1LL << 24;       // bounded mbarrier wait
 
-struct PDParams {
-    int n[3];
-    int T[3];
-    int ntile[3];
-    int LD[3];          // local cell dims incl. ring (T+2 on active axes)
-    int NLD[3];         // local node dims (T+3 on active axes)
-    int local;          // local cells incl. ring
-    int ring;
+// staged field order (the bulk copies fill one 64-float row per field)
+enum { SF_OX = 0, SF_OY, SF_VX, SF_VY, SF_VZ, SF_W, SF_ID };
+
+struct P2 {
+    int nx, ny;
+    int64_t N;
     int cap;
-    float dtdx[3];      // dt / dx per axis
+    int nbatch;
+    int nf;             // staged fields (6, or 7 with ids)
+    float dtdx, dtdy;
     float beta;         // q dt / (2 m)
     float bc;           // beta / c
-    int track;
-    // particle bins
-    const float *in[PF_COUNT];
+    const float *in[kMaxF];      // current copy, in staged (SF_*) order
     const int *cnt_in;
-    float *out[PF_COUNT];
+    float *out[kMaxF];           // other copy, in staged (SF_*) order
     int *cnt_out;
-    // node fields (float4 per node)
-    const float4 *mE, *mB;       // mover: E^{n+theta}, B^n
-    const float4 *dB, *dU;       // deposit: B for alpha, reference velocity
-    // outputs
+    const float4 *mE, *mB;       // mover: E^{n+theta}, B^n (node averaged)
+    const float4 *dB, *dU;       // deposit: B for alpha, reference velocity u_ref
     float *rec;                  // [N][112] for this species
-    float *ring_out;             // [ntiles][ring][112]
-    const int *ring_slot;        // [local] -> ring slot or -1 (interior)
     DevFlags *flags;
 };
 
-__device__ __forceinline__ unsigned lanemask_lt() {
-    unsigned m;
-    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
-    return m;
+size_t pd_smem_bytes() {
+    return 512 + (size_t)kGroups * 2 * kMaxF * kChunk * sizeof(float) + (size_t)kGroups * kChunk * sizeof(int) +
+           (size_t)8 * kScr * sizeof(float);
+}
+size_t arr_smem_bytes() { return (size_t)8 * kScr * sizeof(float); }
+
+// ------------------------------------------------------------ PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+// 1D bulk copy global -> shared (TMA engine), completion counted on an mbarrier
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t phase) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(phase)
+        : "memory");
+    return ok != 0;
+}
+// wait with an iteration limit; false if it gave up
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t phase) {
+    for (long long it = 0; it < kSpinLimit; ++it)
+        if (mbar_try_wait(bar, phase)) return true;
+    return false;
 }
 
+// ------------------------------------------------------------ deposit math
 // alpha (Eq. 30) with b = beta B / c, row-major: alpha a = (a + a x b + (a.b) b)/(1 + b.b)
 __device__ __forceinline__ void alpha_tensor(float bx, float by, float bz, float al[9]) {
-    float inv = 1.0f / (1.0f + bx * bx + by * by + bz * bz);
+    const float inv = __frcp_rn(1.0f + bx * bx + by * by + bz * bz);
     al[0] = (1.0f + bx * bx) * inv; al[1] = (bz + bx * by) * inv; al[2] = (bx * bz - by) * inv;
     al[3] = (by * bx - bz) * inv;   al[4] = (1.0f + by * by) * inv; al[5] = (bx + by * bz) * inv;
     al[6] = (by + bz * bx) * inv;   al[7] = (bz * by - bx) * inv; al[8] = (1.0f + bz * bz) * inv;
@@ -83,18 +114,15 @@ __device__ __forceinline__ void alpha_tensor(float bx, float by, float bz, float
 
 struct RegAcc {
     float v[Rec<2>::SIZE];
-    __device__ __forceinline__ void add(int k, float x) { v[k] += x; }
-};
-struct SmemAcc {
-    float *base;
-    __device__ __forceinline__ void add(int k, float x) { atomicAdd(base + k, x); }
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+        for (int k = 0; k < Rec<2>::SIZE; ++k) v[k] = 0.f;
+    }
 };
 
-// Deposit of one particle at cell-local offsets (x, y): weights of the four
-// corners, B and u_ref interpolated from the corner values, alpha, then the
-// partial sums of the record layout Rec<2>.
-template <class A>
-__device__ __forceinline__ void deposit_one(A &acc, float x, float y, float vx, float vy, float vz, float w,
+// Deposit of one particle at cell-local offsets (x, y) with the corner values
+// of B (for alpha) and u_ref: the partial sums of the record layout Rec<2>.
+__device__ __forceinline__ void deposit_one(RegAcc &acc, float x, float y, float vx, float vy, float vz, float w,
                                             const float4 cB[4], const float4 cU[4], float bc) {
     const float wx0 = 1.0f - x, wx1 = x, wy0 = 1.0f - y, wy1 = y;
     const float W[4] = {wx0 * wy0, wx1 * wy0, wx0 * wy1, wx1 * wy1};
@@ -113,13 +141,13 @@ __device__ __forceinline__ void deposit_one(A &acc, float x, float y, float vx, 
     const float wvx = w * vx, wvy = w * vy, wvz = w * vz;
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
-        acc.add(Rec<2>::RHO + a, w * W[a]);
-        acc.add(Rec<2>::MV + 3 * a + 0, wvx * W[a]);
-        acc.add(Rec<2>::MV + 3 * a + 1, wvy * W[a]);
-        acc.add(Rec<2>::MV + 3 * a + 2, wvz * W[a]);
-        acc.add(Rec<2>::J + 3 * a + 0, jx * W[a]);
-        acc.add(Rec<2>::J + 3 * a + 1, jy * W[a]);
-        acc.add(Rec<2>::J + 3 * a + 2, jz * W[a]);
+        acc.v[Rec<2>::RHO + a] = fmaf(w, W[a], acc.v[Rec<2>::RHO + a]);
+        acc.v[Rec<2>::MV + 3 * a + 0] = fmaf(wvx, W[a], acc.v[Rec<2>::MV + 3 * a + 0]);
+        acc.v[Rec<2>::MV + 3 * a + 1] = fmaf(wvy, W[a], acc.v[Rec<2>::MV + 3 * a + 1]);
+        acc.v[Rec<2>::MV + 3 * a + 2] = fmaf(wvz, W[a], acc.v[Rec<2>::MV + 3 * a + 2]);
+        acc.v[Rec<2>::J + 3 * a + 0] = fmaf(jx, W[a], acc.v[Rec<2>::J + 3 * a + 0]);
+        acc.v[Rec<2>::J + 3 * a + 1] = fmaf(jy, W[a], acc.v[Rec<2>::J + 3 * a + 1]);
+        acc.v[Rec<2>::J + 3 * a + 2] = fmaf(jz, W[a], acc.v[Rec<2>::J + 3 * a + 2]);
     }
     const float X[3] = {w * wx0 * wx0, w * wx0 * wx1, w * wx1 * wx1};
     const float Y[3] = {wy0 * wy0, wy0 * wy1, wy1 * wy1};
@@ -128,266 +156,337 @@ __device__ __forceinline__ void deposit_one(A &acc, float x, float y, float vx, 
 #pragma unroll
         for (int jx_ = 0; jx_ < 3; ++jx_) {
             const float pw = X[jx_] * Y[jy_];
+            float *m = acc.v + Rec<2>::M + 9 * (jx_ + 3 * jy_);
 #pragma unroll
-            for (int e = 0; e < 9; ++e) acc.add(Rec<2>::M + 9 * (jx_ + 3 * jy_) + e, pw * al[e]);
+            for (int e = 0; e < 9; ++e) m[e] = fmaf(pw, al[e], m[e]);
         }
 }
 
-__device__ __forceinline__ int node_local(const PDParams &p, int lx, int ly) {
-    return (lx + 1) + p.NLD[0] * (ly + 1);
-}
-__device__ __forceinline__ int cell_local(const PDParams &p, int lx, int ly) {
-    return (lx + 1) + p.LD[0] * (ly + 1);
+// Sum the 8 lanes of every group of the warp through the warp's shared scratch
+// (stride 33: conflict-free writes and column sums) and store (or add) the
+// record of the group's cell.
+__device__ __forceinline__ void group_reduce_store(const RegAcc &acc, float *scr, int lane, int lig, int gshift,
+                                                   float *dst, int64_t stride, bool add, bool active) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+#pragma unroll
+        for (int k = 0; k < 56; ++k) scr[k * 33 + lane] = acc.v[h * 56 + k];
+        __syncwarp();
+        if (active) {
+#pragma unroll
+            for (int t = 0; t < 7; ++t) {
+                const int k = lig * 7 + t;
+                float s = 0.f;
+#pragma unroll
+                for (int l = 0; l < kGroup; ++l) s += scr[k * 33 + gshift + l];
+                float *d = dst + (size_t)(h * 56 + k) * stride;
+                if (add) *d += s;
+                else *d = s;
+            }
+        }
+        __syncwarp();
+    }
 }
 
+// position of the t-th set bit (t counted from 0) of a 64-bit mask
+__device__ __forceinline__ int nth_bit64(unsigned long long m, int t) {
+    const unsigned lo = (unsigned)m, hi = (unsigned)(m >> 32);
+    const int nlo = __popc(lo);
+    return t < nlo ? (int)__fns(lo, 0, t + 1) : 32 + (int)__fns(hi, 0, t - nlo + 1);
+}
+
+__device__ __forceinline__ void corner_nodes(int ci, int cj, int nx, int ny, int64_t nd[4]) {
+    const int ip = ci + 1 == nx ? 0 : ci + 1, jp = cj + 1 == ny ? 0 : cj + 1;
+    nd[0] = ci + (int64_t)nx * cj;
+    nd[1] = ip + (int64_t)nx * cj;
+    nd[2] = ci + (int64_t)nx * jp;
+    nd[3] = ip + (int64_t)nx * jp;
+}
+
+// bottom slot of chunk ch of a bin whose front holds nf and back nb particles:
+// front chunks are [64 ch, 64 ch + 64), back chunks count down from the top
+__device__ __forceinline__ int chunk_base(int ch, int nf, int cap) {
+    const int nchf = (nf + kChunk - 1) / kChunk;
+    return ch < nchf ? ch * kChunk : cap - (ch - nchf + 1) * kChunk;
+}
+__device__ __forceinline__ int bin_chunks(int word) {
+    return (bin_front(word) + kChunk - 1) / kChunk + (bin_back(word) + kChunk - 1) / kChunk;
+}
+// clamp a (possibly overflowed) count word to the capacity
+__device__ __forceinline__ int clamp_word(int w, int cap) {
+    int f = bin_front(w), b = bin_back(w);
+    b = min(b, cap);
+    f = min(f, cap - b);
+    return f | (b << 16);
+}
+
+// ------------------------------------------------------------ fused kernel
 template <bool PUSH>
-__global__ void __launch_bounds__(kThreads, 1) k_push_deposit(PDParams p) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int NL = p.NLD[0] * p.NLD[1];
-    float4 *sE = reinterpret_cast<float4 *>(smem);          // mover E^{n+theta}
-    float4 *sB = sE + NL;                                    // mover B^n
-    float4 *sDB = sB + NL;                                   // deposit B
-    float4 *sDU = sDB + NL;                                  // deposit u_ref
-    float *sRec = reinterpret_cast<float *>(sDU + NL);       // [local][112]
-    float4 *sStage = reinterpret_cast<float4 *>(sRec + (size_t)p.local * Rec<2>::SIZE);  // [groups][64][2]
+__global__ void __launch_bounds__(kThreads, 1) k_pd(P2 p) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem);                         // [groups][2]
+    float *bufs = reinterpret_cast<float *>(smem + 512);                          // [groups][2][kMaxF][64]
+    int *codes = reinterpret_cast<int *>(bufs + (size_t)kGroups * 2 * kMaxF * kChunk);  // [groups][64]
+    float *scr_all = reinterpret_cast<float *>(codes + kGroups * kChunk);         // [8][kScr]
 
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
-    const int grp = tid / kGroup, lig = tid % kGroup;        // group and lane in group
-    const int gshift = (lane / kGroup) * kGroup;             // first lane of my group in the warp
-    const int tile = blockIdx.x;
-    const int tx = tile % p.ntile[0], ty = tile / p.ntile[0];
-    const int x0 = tx * p.T[0], y0 = ty * p.T[1];
+    const int g = tid / kGroup, lig = tid % kGroup;
+    const int gshift = (lane / kGroup) * kGroup;
+    float *mybuf = bufs + (size_t)g * 2 * kMaxF * kChunk;
+    int *mycode = codes + g * kChunk;
+    uint64_t *mybar = bars + 2 * g;
+    float *scr = scr_all + (size_t)warp * kScr;
+    const uint32_t tx_bytes = (uint32_t)(p.nf * kChunk * sizeof(float));
 
-    // stage node fields of the tile and its ring (+1 node) into shared memory
-    for (int i = tid; i < NL; i += kThreads) {
-        const int lx = i % p.NLD[0] - 1, ly = i / p.NLD[0] - 1;
-        const int g = wrap_idx(x0 + lx, p.n[0]) + p.n[0] * wrap_idx(y0 + ly, p.n[1]);
-        if (PUSH) { sE[i] = p.mE[g]; sB[i] = p.mB[g]; }
-        sDB[i] = p.dB[g];
-        sDU[i] = p.dU[g];
+    if (lig == 0) {
+        mbar_init(&mybar[0], 1);
+        mbar_init(&mybar[1], 1);
     }
-    for (int i = tid; i < p.local * Rec<2>::SIZE; i += kThreads) sRec[i] = 0.f;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     __syncthreads();
 
-    float4 *myStage = sStage + (size_t)grp * kChunk * 2;
-    const int ncell_tile = p.T[0] * p.T[1];
-
-    for (int c0 = 0; c0 < ncell_tile; c0 += kGroups) {
-        const int lc = c0 + grp;
-        const bool valid = lc < ncell_tile;
-        const int lx = valid ? lc % p.T[0] : 0, ly = valid ? lc / p.T[0] : 0;
-        const int gcell = (x0 + lx) + p.n[0] * (y0 + ly);
-        int cnt = valid ? min(p.cnt_in[gcell], p.cap) : 0;
-        const int wmax = __reduce_max_sync(kFull, cnt);
-        const size_t binbase = (size_t)gcell * p.cap;
-        const int homeL = cell_local(p, lx, ly);
-        // corner nodes of the home cell
-        const int n00 = node_local(p, lx, ly), n10 = n00 + 1, n01 = n00 + p.NLD[0], n11 = n01 + 1;
-
-        for (int start = 0; start < wmax; start += kChunk) {
-            // ---------------- pass 1: load, move, re-bin, stage
-            float px[kPerLane], py[kPerLane], pvx[kPerLane], pvy[kPerLane], pvz[kPerLane], pw[kPerLane];
-            int pid[kPerLane];
-#pragma unroll
-            for (int k = 0; k < kPerLane; ++k) {
-                const int i = start + k * kGroup + lig;
-                if (i < cnt) {
-                    const size_t s = binbase + i;
-                    px[k] = p.in[PF_OX][s]; py[k] = p.in[PF_OY][s];
-                    pvx[k] = p.in[PF_VX][s]; pvy[k] = p.in[PF_VY][s]; pvz[k] = p.in[PF_VZ][s];
-                    pw[k] = p.in[PF_W][s];
-                    pid[k] = p.track ? __float_as_int(p.in[PF_ID][s]) : 0;
-                }
+    // producer state of this group (lane 0): next chunk to stream = chunk
+    // `ich` of the cell of batch `ib`
+    int ib = blockIdx.x, ich = 0, inch = -1, iword = 0;
+    int issued = 0, cons = 0;
+    auto find_next = [&]() -> bool {
+        while (ib < p.nbatch) {
+            if (inch < 0) {
+                const int64_t cell = (int64_t)ib * kGroups + g;
+                iword = cell < p.N ? clamp_word(p.cnt_in[cell], p.cap) : 0;
+                inch = bin_chunks(iword);
             }
-            int nstay = 0, nleave = 0;       // group-uniform
+            if (ich < inch) return true;
+            ib += gridDim.x;
+            ich = 0;
+            inch = -1;
+        }
+        return false;
+    };
+    auto issue = [&]() {
+        const int slot = issued & 1;
+        const int64_t cell = (int64_t)ib * kGroups + g;
+        const size_t off = (size_t)cell * p.cap + chunk_base(ich, bin_front(iword), p.cap);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_expect_tx(&mybar[slot], tx_bytes);
+        for (int f = 0; f < p.nf; ++f)
+            bulk_g2s(mybuf + (size_t)(slot * kMaxF + f) * kChunk, p.in[f] + off, kChunk * sizeof(float), &mybar[slot]);
+        ++issued;
+        ++ich;
+    };
+    if (lig == 0) {
+        if (find_next()) issue();
+        if (find_next()) issue();
+    }
+
+    bool abort = false;
+    for (int b = blockIdx.x; b < p.nbatch; b += gridDim.x) {
+        const int64_t cell = (int64_t)b * kGroups + g;
+        const bool valid = cell < p.N;
+        const int word = valid ? clamp_word(p.cnt_in[cell], p.cap) : 0;
+        const int nch = bin_chunks(word);
+        const int nchf = (bin_front(word) + kChunk - 1) / kChunk;
+        const int wmax = __reduce_max_sync(kFull, nch);
+        const int ci = valid ? (int)(cell % p.nx) : 0, cj = valid ? (int)(cell / p.nx) : 0;
+        int64_t nd[4];
+        corner_nodes(ci, cj, p.nx, p.ny, nd);
+        float4 cB[4], cU[4];
 #pragma unroll
-            for (int k = 0; k < kPerLane; ++k) {
-                const int i = start + k * kGroup + lig;
-                const bool act = i < cnt;
-                float x = 0.f, y = 0.f, vx = 0.f, vy = 0.f, vz = 0.f, w = 0.f;
-                int sx = 0, sy = 0;
-                if (act) {
-                    x = px[k]; y = py[k]; vx = pvx[k]; vy = pvy[k]; vz = pvz[k]; w = pw[k];
-                    if (PUSH) {
+        for (int a = 0; a < 4; ++a) {
+            cB[a] = __ldg(p.dB + nd[a]);
+            cU[a] = __ldg(p.dU + nd[a]);
+        }
+        RegAcc acc;
+        acc.zero();
+
+        for (int ch = 0; ch < wmax; ++ch) {
+            const bool has = ch < nch;
+            const int slot = cons & 1;
+            bool ok = true;
+            if (has) ok = mbar_wait_bounded(&mybar[slot], (uint32_t)((cons >> 1) & 1));
+            if (__any_sync(kFull, !ok)) { abort = true; break; }
+            float *cbuf = mybuf + (size_t)slot * kMaxF * kChunk;
+            const int sbase = has ? chunk_base(ch, bin_front(word), p.cap) : 0;
+            // particles of this chunk: slots of its own segment only
+            unsigned long long vmask = 0ull;
+            if (has) {
+                const int lo = ch < nchf ? 0 : max(0, p.cap - bin_back(word) - sbase);
+                const int hi = ch < nchf ? min(kChunk, bin_front(word) - sbase) : kChunk;
+                if (hi > lo) vmask = (hi - lo == 64 ? ~0ull : ((1ull << (hi - lo)) - 1ull)) << lo;
+            }
+            unsigned long long smask = vmask;   // stayers (all of them without the push)
+            int old[kPerLane];                  // slot reservations of this lane's leavers
+            int base = 0, fits = 1;
+            if (PUSH) {
+                // ---- A1: mover.  New state written back into the staged chunk,
+                // the destination cell of each leaver into the code row.
+                float4 mE[4], mB[4];
+#pragma unroll
+                for (int a = 0; a < 4; ++a) { mE[a] = __ldg(p.mE + nd[a]); mB[a] = __ldg(p.mB + nd[a]); }
+                unsigned long long lv = 0ull;
+#pragma unroll 2
+                for (int k = 0; k < kPerLane; ++k) {
+                    const int j = k * kGroup + lig;
+                    bool leave = false;
+                    if ((vmask >> j) & 1ull) {
+                        float x = cbuf[SF_OX * kChunk + j], y = cbuf[SF_OY * kChunk + j];
+                        float vx = cbuf[SF_VX * kChunk + j], vy = cbuf[SF_VY * kChunk + j], vz = cbuf[SF_VZ * kChunk + j];
                         const float wx0 = 1.f - x, wy0 = 1.f - y;
                         const float W0 = wx0 * wy0, W1 = x * wy0, W2 = wx0 * y, W3 = x * y;
-                        const float4 e0 = sE[n00], e1 = sE[n10], e2 = sE[n01], e3 = sE[n11];
-                        const float4 b0 = sB[n00], b1 = sB[n10], b2 = sB[n01], b3 = sB[n11];
-                        const float ex = W0 * e0.x + W1 * e1.x + W2 * e2.x + W3 * e3.x;
-                        const float ey = W0 * e0.y + W1 * e1.y + W2 * e2.y + W3 * e3.y;
-                        const float ez = W0 * e0.z + W1 * e1.z + W2 * e2.z + W3 * e3.z;
-                        const float bx = p.bc * (W0 * b0.x + W1 * b1.x + W2 * b2.x + W3 * b3.x);
-                        const float by = p.bc * (W0 * b0.y + W1 * b1.y + W2 * b2.y + W3 * b3.y);
-                        const float bz = p.bc * (W0 * b0.z + W1 * b1.z + W2 * b2.z + W3 * b3.z);
+                        const float ex = W0 * mE[0].x + W1 * mE[1].x + W2 * mE[2].x + W3 * mE[3].x;
+                        const float ey = W0 * mE[0].y + W1 * mE[1].y + W2 * mE[2].y + W3 * mE[3].y;
+                        const float ez = W0 * mE[0].z + W1 * mE[1].z + W2 * mE[2].z + W3 * mE[3].z;
+                        const float bx = p.bc * (W0 * mB[0].x + W1 * mB[1].x + W2 * mB[2].x + W3 * mB[3].x);
+                        const float by = p.bc * (W0 * mB[0].y + W1 * mB[1].y + W2 * mB[2].y + W3 * mB[3].y);
+                        const float bz = p.bc * (W0 * mB[0].z + W1 * mB[1].z + W2 * mB[2].z + W3 * mB[3].z);
                         // a = v + beta E ; vbar = (a + a x b + (a.b) b) / (1 + b.b)
                         const float ax = fmaf(p.beta, ex, vx), ay = fmaf(p.beta, ey, vy), az = fmaf(p.beta, ez, vz);
-                        const float inv = 1.0f / (1.0f + bx * bx + by * by + bz * bz);
+                        const float inv = __frcp_rn(1.0f + bx * bx + by * by + bz * bz);
                         const float ab = ax * bx + ay * by + az * bz;
                         const float vbx = (ax + (ay * bz - az * by) + ab * bx) * inv;
                         const float vby = (ay + (az * bx - ax * bz) + ab * by) * inv;
                         const float vbz = (az + (ax * by - ay * bx) + ab * bz) * inv;
                         vx = 2.f * vbx - vx; vy = 2.f * vby - vy; vz = 2.f * vbz - vz;
-                        x = fmaf(vx, p.dtdx[0], x);
-                        y = fmaf(vy, p.dtdx[1], y);
+                        x = fmaf(vx, p.dtdx, x);
+                        y = fmaf(vy, p.dtdy, y);
                         float fx = floorf(x), fy = floorf(y);
                         x -= fx; y -= fy;
                         if (x >= 1.f) { x -= 1.f; fx += 1.f; }
                         if (y >= 1.f) { y -= 1.f; fy += 1.f; }
-                        sx = (int)fx; sy = (int)fy;
+                        int sx = (int)fx, sy = (int)fy;
                         if (sx < -1 || sx > 1 || sy < -1 || sy > 1) {
                             atomicExch(&p.flags->cfl, 1);
                             sx = max(-1, min(1, sx)); sy = max(-1, min(1, sy));
                         }
-                        if (p.n[1] == 1) { sy = 0; y = 0.f; }
+                        if (p.ny == 1) { sy = 0; y = 0.f; }
+                        leave = sx != 0 || sy != 0;
+                        int dxg = ci + sx, dyg = cj + sy;
+                        dxg = dxg < 0 ? dxg + p.nx : (dxg >= p.nx ? dxg - p.nx : dxg);
+                        dyg = dyg < 0 ? dyg + p.ny : (dyg >= p.ny ? dyg - p.ny : dyg);
+                        cbuf[SF_OX * kChunk + j] = x; cbuf[SF_OY * kChunk + j] = y;
+                        cbuf[SF_VX * kChunk + j] = vx; cbuf[SF_VY * kChunk + j] = vy; cbuf[SF_VZ * kChunk + j] = vz;
+                        mycode[j] = dxg + p.nx * dyg;
                     }
+                    if (leave) lv |= 1ull << j;
                 }
-                // re-bin into the other copy: one atomic per destination cell per warp
-                if (PUSH) {
-                    const int dxg = wrap_idx(x0 + lx + sx, p.n[0]);
-                    const int dyg = wrap_idx(y0 + ly + sy, p.n[1]);
-                    const int dest = act ? dxg + p.n[0] * dyg : -1;
-                    const unsigned peers = __match_any_sync(kFull, dest);
-                    const int leader = __ffs(peers) - 1;
-                    int base = 0;
-                    if (act && lane == leader) base = atomicAdd(&p.cnt_out[dest], __popc(peers));
-                    base = __shfl_sync(kFull, base, leader);
-                    const int slot = base + __popc(peers & lanemask_lt());
-                    if (act) {
-                        if (slot < p.cap) {
-                            const size_t o = (size_t)dest * p.cap + slot;
-                            p.out[PF_OX][o] = x; p.out[PF_OY][o] = y;
-                            p.out[PF_VX][o] = vx; p.out[PF_VY][o] = vy; p.out[PF_VZ][o] = vz;
-                            p.out[PF_W][o] = w;
-                            if (p.track) p.out[PF_ID][o] = __int_as_float(pid[k]);
-                        } else {
-                            atomicExch(&p.flags->overflow, 1);
-                        }
-                    }
-                }
-                // stage, compacted: stayers from the front, leavers from the back
-                const bool stay = act && sx == 0 && sy == 0;
-                const bool leave = act && !stay;
-                const unsigned bs = (__ballot_sync(kFull, stay) >> gshift) & 0xffu;
-                const unsigned bl = (__ballot_sync(kFull, leave) >> gshift) & 0xffu;
-                const unsigned below = (1u << lig) - 1u;
-                if (stay) {
-                    const int pos = nstay + __popc(bs & below);
-                    myStage[2 * pos] = make_float4(x, y, vx, vy);
-                    myStage[2 * pos + 1] = make_float4(vz, w, 0.f, 0.f);
-                } else if (leave) {
-                    const int pos = kChunk - 1 - (nleave + __popc(bl & below));
-                    myStage[2 * pos] = make_float4(x, y, vx, vy);
-                    myStage[2 * pos + 1] = make_float4(vz, w, __int_as_float(cell_local(p, lx + sx, ly + sy)), 0.f);
-                }
-                nstay += __popc(bs);
-                nleave += __popc(bl);
-            }
-            __syncwarp();
-
-            // ---------------- pass 2: stayers, register accumulation
-            RegAcc acc;
+                // gather the group's leaver bits (each lane knows its own slots)
+                unsigned long long all = lv;
 #pragma unroll
-            for (int k = 0; k < Rec<2>::SIZE; ++k) acc.v[k] = 0.f;
+                for (int o = 1; o < kGroup; o <<= 1) all |= __shfl_xor_sync(kFull, all, o);
+                smask = vmask & ~all;
+                __syncwarp();
+                // ---- B1: reserve the slots (results used only after the deposit)
+                const int ns = __popcll(smask);
+                if (has && lig == 0 && ns > 0) {
+                    const int o = atomicAdd(&p.cnt_out[cell], ns);
+                    base = bin_front(o);
+                    fits = bin_count(o) + ns <= p.cap;
+                }
+#pragma unroll
+                for (int k = 0; k < kPerLane; ++k) {
+                    const int j = k * kGroup + lig;
+                    old[k] = (lv >> j) & 1ull ? atomicAdd(&p.cnt_out[mycode[j]], 1 << 16) : 0;
+                }
+            }
+            // ---- A2: deposit of the stayers (compacted, no idle lanes)
             {
-                const float4 cB[4] = {sDB[n00], sDB[n10], sDB[n01], sDB[n11]};
-                const float4 cU[4] = {sDU[n00], sDU[n10], sDU[n01], sDU[n11]};
-                const int smax = __reduce_max_sync(kFull, nstay);
-                for (int j = lig; j < smax; j += kGroup) {
-                    if (j < nstay) {
-                        const float4 a = myStage[2 * j], b = myStage[2 * j + 1];
-                        deposit_one(acc, a.x, a.y, a.z, a.w, b.x, b.y, cB, cU, p.bc);
-                    }
+                const int ns = __popcll(smask);
+                for (int t = lig; t < ns; t += kGroup) {
+                    const int j = nth_bit64(smask, t);
+                    deposit_one(acc, cbuf[SF_OX * kChunk + j], cbuf[SF_OY * kChunk + j], cbuf[SF_VX * kChunk + j],
+                                cbuf[SF_VY * kChunk + j], cbuf[SF_VZ * kChunk + j], cbuf[SF_W * kChunk + j], cB, cU,
+                                p.bc);
                 }
             }
-            // ---------------- pass 3: leavers, shared-memory atomics into the
-            // record of their new cell (interior or ring)
+            // ---- B2: write the chunk into the other copy.  Stayers take
+            // consecutive bottom slots of this cell's new bin, leavers the top
+            // slots reserved in B1.
             if (PUSH) {
-                const int lmax = __reduce_max_sync(kFull, nleave);
-                for (int j = lig; j < lmax; j += kGroup) {
-                    if (j < nleave) {
-                        const float4 a = myStage[2 * (kChunk - 1 - j)], b = myStage[2 * (kChunk - 1 - j) + 1];
-                        const int dl = __float_as_int(b.z);
-                        const int dlx = dl % p.LD[0] - 1, dly = dl / p.LD[0] - 1;
-                        const int m00 = node_local(p, dlx, dly), m10 = m00 + 1, m01 = m00 + p.NLD[0], m11 = m01 + 1;
-                        const float4 cB[4] = {sDB[m00], sDB[m10], sDB[m01], sDB[m11]};
-                        const float4 cU[4] = {sDU[m00], sDU[m10], sDU[m01], sDU[m11]};
-                        SmemAcc sacc{sRec + (size_t)dl * Rec<2>::SIZE};
-                        deposit_one(sacc, a.x, a.y, a.z, a.w, b.x, b.y, cB, cU, p.bc);
+                base = __shfl_sync(kFull, base, gshift);
+                fits = __shfl_sync(kFull, fits, gshift);
+#pragma unroll
+                for (int k = 0; k < kPerLane; ++k) {
+                    const int j = k * kGroup + lig;
+                    int64_t o = -1;
+                    if ((smask >> j) & 1ull) {
+                        const int rank = __popcll(smask & ((1ull << j) - 1ull));
+                        if (fits) o = (int64_t)cell * p.cap + base + rank;
+                        else atomicExch(&p.flags->overflow, 1);
+                    } else if ((vmask >> j) & 1ull) {
+                        const int w0 = old[k];
+                        if (bin_count(w0) + 1 <= p.cap) o = (int64_t)mycode[j] * p.cap + p.cap - 1 - bin_back(w0);
+                        else atomicExch(&p.flags->overflow, 1);
+                    }
+                    if (o >= 0) {
+#pragma unroll
+                        for (int f = 0; f < kMaxF; ++f)
+                            if (f < p.nf) p.out[f][o] = cbuf[f * kChunk + j];
                     }
                 }
             }
             __syncwarp();
-            // ---------------- group reduction of the stayer sums through the
-            // warp's (now free) stage buffer: two halves of 56 values; the
-            // stride-33 layout keeps both the writes and the column sums free of
-            // bank conflicts.
-            if (__reduce_or_sync(kFull, nstay > 0 ? 1u : 0u) != 0u) {
-                float *scratch = reinterpret_cast<float *>(sStage + (size_t)(warp * 4) * kChunk * 2);
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-#pragma unroll
-                    for (int k = 0; k < 56; ++k) scratch[k * 33 + lane] = acc.v[h * 56 + k];
-                    __syncwarp();
-                    if (nstay > 0) {
-#pragma unroll
-                        for (int t = 0; t < 7; ++t) {
-                            const int k = lig * 7 + t;
-                            float sum = 0.f;
-#pragma unroll
-                            for (int l = 0; l < kGroup; ++l) sum += scratch[k * 33 + gshift + l];
-                            if (h * 56 + k < Rec<2>::USED) atomicAdd(&sRec[homeL * Rec<2>::SIZE + h * 56 + k], sum);
-                        }
-                    }
-                    __syncwarp();
-                }
+            if (has) {
+                ++cons;
+                if (lig == 0 && find_next()) issue();       // refill the buffer just consumed
             }
         }
+        if (abort) break;
+        group_reduce_store(acc, scr, lane, lig, gshift, p.rec + cell, p.N, false, valid);
     }
-    __syncthreads();
+    if (abort) {
+        if (lane == 0) atomicExch(&p.flags->timeout, 1);
+        // drain this group's copies still in flight before the CTA exits
+        if (lig == 0)
+            for (int k = cons; k < issued; ++k) mbar_wait_bounded(&mybar[k & 1], (uint32_t)((k >> 1) & 1));
+    }
+}
 
-    // store the tile records: interior cells to their global record, ring cells
-    // to this tile's ring buffer
-    const int nvec = Rec<2>::SIZE / 4;
-    for (int i = tid; i < p.local * nvec; i += kThreads) {
-        const int l = i / nvec, k = i % nvec;
-        const float4 v = reinterpret_cast<const float4 *>(sRec)[i];
-        const int rs = p.ring_slot[l];
-        if (rs < 0) {
-            const int lx = l % p.LD[0] - 1, ly = l / p.LD[0] - 1;
-            const int g = (x0 + lx) + p.n[0] * (y0 + ly);
-            reinterpret_cast<float4 *>(p.rec + (size_t)g * Rec<2>::SIZE)[k] = v;
-        } else if (PUSH) {
-            reinterpret_cast<float4 *>(p.ring_out + ((size_t)tile * p.ring + rs) * Rec<2>::SIZE)[k] = v;
+// Deposit the particles that arrived in a cell during the push (the top
+// segment of its new bin, contiguous) into the cell's record.
+__global__ void __launch_bounds__(kThreads, 1) k_arrivals(P2 p) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    float *scr_all = reinterpret_cast<float *>(smem);                          // [8][kScr]
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    const int g = tid / kGroup, lig = tid % kGroup;
+    const int gshift = (lane / kGroup) * kGroup;
+    float *scr = scr_all + (size_t)warp * kScr;
+    for (int b = blockIdx.x; b < p.nbatch; b += gridDim.x) {
+        const int64_t cell = (int64_t)b * kGroups + g;
+        const bool valid = cell < p.N;
+        const int nb = valid ? bin_back(clamp_word(p.cnt_out[cell], p.cap)) : 0;
+        if (!__any_sync(kFull, nb > 0)) continue;
+        const int ci = valid ? (int)(cell % p.nx) : 0, cj = valid ? (int)(cell / p.nx) : 0;
+        int64_t nd[4];
+        corner_nodes(ci, cj, p.nx, p.ny, nd);
+        float4 cB[4], cU[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) { cB[a] = __ldg(p.dB + nd[a]); cU[a] = __ldg(p.dU + nd[a]); }
+        RegAcc acc;
+        acc.zero();
+        const size_t top = (size_t)cell * p.cap + p.cap - nb;
+        for (int i = lig; i < nb; i += kGroup) {
+            const size_t s = top + i;
+            deposit_one(acc, p.out[SF_OX][s], p.out[SF_OY][s], p.out[SF_VX][s], p.out[SF_VY][s], p.out[SF_VZ][s],
+                        p.out[SF_W][s], cB, cU, p.bc);
         }
+        group_reduce_store(acc, scr, lane, lig, gshift, p.rec + cell, p.N, true, valid && nb > 0);
     }
 }
 
-// Fold ring buffers into the records of the cells they belong to.
-__global__ void k_fold_rings(float *rec, const float *ring, const int *ring_lidx, int ring_n, int ntiles,
-                             int ntx, int Tx, int Ty, int LDx, int nx, int ny) {
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (warp >= ntiles * ring_n) return;
-    const int tile = warp / ring_n, rs = warp % ring_n;
-    const int l = ring_lidx[rs];
-    const int lx = l % LDx - 1, ly = l / LDx - 1;
-    const int tx = tile % ntx, ty = tile / ntx;
-    const int g = wrap_idx(tx * Tx + lx, nx) + nx * wrap_idx(ty * Ty + ly, ny);
-    const float *src = ring + (size_t)warp * Rec<2>::SIZE;
-    float *dst = rec + (size_t)g * Rec<2>::SIZE;
-    for (int k = lane; k < Rec<2>::USED; k += 32) {
-        const float v = src[k];
-        if (v != 0.f) atomicAdd(dst + k, v);
-    }
-}
-
-__global__ void k_max_count(const int *cnt, int64_t n, DevFlags *f) {
+__global__ void k_max_count(const int *cnt, int64_t n, int cap, DevFlags *f) {
     int m = 0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        m = max(m, cnt[i]);
+        m = max(m, bin_count(cnt[i]));
     m = __reduce_max_sync(kFull, m);
     if ((threadIdx.x & 31) == 0) atomicMax(&f->maxcount, m);
+    (void)cap;
+}
+
+__global__ void k_counts(const int *cnt, int64_t n, int cap, int *out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = bin_count(clamp_word(cnt[i], cap));
 }
 
 // ---------------------------------------------------------------- binning
@@ -426,16 +525,19 @@ __global__ void k_scatter(int64_t n, const int *cell, const float *ox, const flo
     }
 }
 
-// copy bins (old capacity) into bins of a new capacity
-__global__ void k_rebin_copy(int64_t ncell, int oldcap, int newcap, const int *cnt, float *const *src,
+// copy bins into bins of a new capacity (both segments into the new front)
+__global__ void k_rebin_copy(int64_t ncell, int oldcap, int newcap, const int *cnt, int *newcnt, float *const *src,
                              float *const *dst, int nf) {
     const int64_t c = blockIdx.x;
     if (c >= ncell) return;
-    const int m = min(cnt[c], min(oldcap, newcap));
+    const int word = clamp_word(cnt[c], oldcap);
+    const int m = min(bin_count(word), newcap);
     for (int f = 0; f < nf; ++f) {
         if (!src[f]) continue;
-        for (int i = threadIdx.x; i < m; i += blockDim.x) dst[f][(size_t)c * newcap + i] = src[f][(size_t)c * oldcap + i];
+        for (int i = threadIdx.x; i < m; i += blockDim.x)
+            dst[f][(size_t)c * newcap + i] = src[f][(size_t)c * oldcap + bin_slot(word, i, oldcap)];
     }
+    if (threadIdx.x == 0) newcnt[c] = m;
 }
 
 __global__ void k_gather_out(int64_t ncell, int cap, const int *cnt, const int *offs, float *const *src, int nx,
@@ -443,10 +545,11 @@ __global__ void k_gather_out(int64_t ncell, int cap, const int *cnt, const int *
                              float *vz, float *w, int32_t *id) {
     const int64_t c = blockIdx.x;
     if (c >= ncell) return;
-    const int m = min(cnt[c], cap);
+    const int word = clamp_word(cnt[c], cap);
+    const int m = bin_count(word);
     const int cx = (int)(c % nx), cy = (int)(c / nx);
     for (int i = threadIdx.x; i < m; i += blockDim.x) {
-        const size_t s = (size_t)c * cap + i;
+        const size_t s = (size_t)c * cap + bin_slot(word, i, cap);
         const int o = offs[c] + i;
         if (x) x[o] = (cx + (double)src[PF_OX][s]) * dx;
         if (y) y[o] = ny > 1 ? (cy + (double)src[PF_OY][s]) * dy : 0.0;
@@ -463,12 +566,6 @@ int grid_for(int64_t n, int block = 256) {
     int64_t g = (n + block - 1) / block;
     if (g > 152 * 16) g = 152 * 16;
     return (int)(g < 1 ? 1 : g);
-}
-
-size_t pd_smem_bytes(const gx_ctx *c) {
-    const int NL = (c->tg.T[0] + 3) * (c->tg.T[1] + 3);
-    return (size_t)4 * NL * sizeof(float4) + (size_t)c->tg.local * Rec<2>::SIZE * sizeof(float) +
-           (size_t)kGroups * kChunk * 2 * sizeof(float4);
 }
 
 int alloc_bins(gx_ctx *c, int s, int cap) {
@@ -499,65 +596,15 @@ void free_bins(Species &S) {
     }
 }
 
+// bin capacity: a multiple of the 64-particle chunk (staged chunks stay inside
+// their bin) and below 2^15 (the packed count word)
 int round_cap(double v) {
     int cap = (int)ceil(v);
-    cap = (cap + 31) / 32 * 32;
-    return cap < 32 ? 32 : cap;
+    cap = (cap + kChunk - 1) / kChunk * kChunk;
+    return cap < kChunk ? kChunk : cap;
 }
 
 }  // namespace
-
-// ------------------------------------------------------------------ tiles
-int gx_choose_tiles(gx_ctx *c) {
-    if (c->dim != 2) {
-        c->err = "the particle kernels of this build handle the 2D (x-y) configuration";
-        return GX_ENOTIMPL;
-    }
-    const int nx = c->n[0], ny = c->n[1];
-    const int cx[] = {16, 8, 4, 2, 1}, cy[] = {8, 4, 2, 1};
-    // prefer at least two waves of CTAs over the 152 SMs with the largest tile
-    // (the ring costs relatively less on large tiles); otherwise the most tiles
-    int bx = 1, by = 1;
-    int64_t best_tiles = -1;
-    int best_area = -1;
-    bool best_two_waves = false;
-    for (int a : cx) {
-        if (nx % a) continue;
-        for (int b : cy) {
-            if (ny % b) continue;
-            const int64_t tiles = (int64_t)(nx / a) * (ny / b);
-            const int area = a * b;
-            const bool two = tiles >= 304;
-            bool better;
-            if (two != best_two_waves) better = two;
-            else if (two) better = area > best_area;
-            else better = tiles > best_tiles || (tiles == best_tiles && area > best_area);
-            if (best_tiles < 0 || better) { bx = a; by = b; best_tiles = tiles; best_area = area; best_two_waves = two; }
-        }
-    }
-    TileGeom &t = c->tg;
-    t.T[0] = bx; t.T[1] = by; t.T[2] = 1;
-    t.ntile[0] = nx / bx; t.ntile[1] = ny / by; t.ntile[2] = 1;
-    t.ntiles = t.ntile[0] * t.ntile[1];
-    t.local = (bx + 2) * (by + 2);
-    t.ring = t.local - bx * by;
-    // ring-slot tables: local cell -> ring slot (-1 interior) and back
-    const int LDx = bx + 2, LDy = by + 2;
-    std::vector<int> sol(LDx * LDy, -1), los;
-    for (int ly = 0; ly < LDy; ++ly)
-        for (int lx = 0; lx < LDx; ++lx) {
-            const bool interior = lx >= 1 && lx <= bx && ly >= 1 && ly <= by;
-            if (!interior) { sol[lx + LDx * ly] = (int)los.size(); los.push_back(lx + LDx * ly); }
-        }
-    if (c->ring_slot_of_local) cudaFree(c->ring_slot_of_local);
-    if (c->ring_local_of_slot) cudaFree(c->ring_local_of_slot);
-    c->ring_slot_of_local = c->ring_local_of_slot = nullptr;
-    GX_CHECK(c, cudaMalloc(&c->ring_slot_of_local, sol.size() * sizeof(int)));
-    GX_CHECK(c, cudaMalloc(&c->ring_local_of_slot, los.size() * sizeof(int)));
-    GX_CHECK(c, cudaMemcpy(c->ring_slot_of_local, sol.data(), sol.size() * sizeof(int), cudaMemcpyHostToDevice));
-    GX_CHECK(c, cudaMemcpy(c->ring_local_of_slot, los.data(), los.size() * sizeof(int), cudaMemcpyHostToDevice));
-    return GX_OK;
-}
 
 // --------------------------------------------------------------- binning
 int gx_bin_particles(gx_ctx *c, int s, int64_t n, const double *x, const double *y, const double *z,
@@ -576,20 +623,20 @@ int gx_bin_particles(gx_ctx *c, int s, int64_t n, const double *x, const double 
         k_locate<<<grid_for(n), 256, 0, st>>>(n, x, y, c->n[0], c->n[1], c->cfg.dx[0], c->cfg.dx[1], cell, ox, oy, count);
         GX_LAUNCHED(c);
     }
-    int *dmax = nullptr;
+    DevFlags *dmax = nullptr;
     GX_CHECK(c, cudaMalloc(&dmax, sizeof(DevFlags)));
     GX_CHECK(c, cudaMemsetAsync(dmax, 0, sizeof(DevFlags), st));
-    k_max_count<<<grid_for(c->N), 256, 0, st>>>(count, c->N, reinterpret_cast<DevFlags *>(dmax));
+    k_max_count<<<grid_for(c->N), 256, 0, st>>>(count, c->N, 0, dmax);
     GX_LAUNCHED(c);
     DevFlags hf{};
     GX_CHECK(c, cudaMemcpyAsync(&hf, dmax, sizeof(DevFlags), cudaMemcpyDeviceToHost, st));
     GX_CHECK(c, cudaStreamSynchronize(st));
     const double slack = c->cfg.bin_slack > 1.2 ? c->cfg.bin_slack : 1.2;
-    const int cap = round_cap(std::max(32.0, hf.maxcount * slack));
+    const int cap = round_cap(std::max(64.0, hf.maxcount * slack));
     GX_CHECK(c, cudaFree(dmax));
+    if (cap >= 32768) { c->err = "more than 32767 particles per cell bin"; return GX_EINVAL; }
     int rc = alloc_bins(c, s, cap);
     if (rc) return rc;
-    // counts of the current copy = final cursor values
     float **dout = nullptr;
     GX_CHECK(c, cudaMalloc(&dout, PF_COUNT * sizeof(float *)));
     GX_CHECK(c, cudaMemcpyAsync(dout, S.f[c->cur], PF_COUNT * sizeof(float *), cudaMemcpyHostToDevice, st));
@@ -605,6 +652,8 @@ int gx_bin_particles(gx_ctx *c, int s, int64_t n, const double *x, const double 
 }
 
 int gx_regrow_bins(gx_ctx *c, int s, int newcap, cudaStream_t st) {
+    newcap = round_cap(newcap);
+    if (newcap >= 32768) { c->err = "more than 32767 particles per cell bin"; return GX_EOVERFLOW; }
     Species &S = c->sp[s];
     Species old = S;
     int rc = alloc_bins(c, s, newcap);
@@ -614,9 +663,9 @@ int gx_regrow_bins(gx_ctx *c, int s, int newcap, cudaStream_t st) {
     GX_CHECK(c, cudaMalloc(&ddst, PF_COUNT * sizeof(float *)));
     GX_CHECK(c, cudaMemcpyAsync(dsrc, old.f[c->cur], PF_COUNT * sizeof(float *), cudaMemcpyHostToDevice, st));
     GX_CHECK(c, cudaMemcpyAsync(ddst, S.f[c->cur], PF_COUNT * sizeof(float *), cudaMemcpyHostToDevice, st));
-    k_rebin_copy<<<(unsigned)c->N, 128, 0, st>>>(c->N, old.cap, newcap, old.cnt[c->cur], dsrc, ddst, PF_COUNT);
+    k_rebin_copy<<<(unsigned)c->N, 128, 0, st>>>(c->N, old.cap, newcap, old.cnt[c->cur], S.cnt[c->cur], dsrc, ddst,
+                                                  PF_COUNT);
     GX_LAUNCHED(c);
-    GX_CHECK(c, cudaMemcpyAsync(S.cnt[c->cur], old.cnt[c->cur], c->N * sizeof(int), cudaMemcpyDeviceToDevice, st));
     GX_CHECK(c, cudaStreamSynchronize(st));
     cudaFree(dsrc); cudaFree(ddst);
     free_bins(old);
@@ -625,56 +674,50 @@ int gx_regrow_bins(gx_ctx *c, int s, int newcap, cudaStream_t st) {
 
 // ------------------------------------------------------------ hot path
 static int launch_pd(gx_ctx *c, bool push, cudaStream_t st) {
-    const size_t smem = pd_smem_bytes(c);
-    static size_t configured[2] = {0, 0};
-    if (configured[push] < smem) {
-        if (push) GX_CHECK(c, cudaFuncSetAttribute(k_push_deposit<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        else GX_CHECK(c, cudaFuncSetAttribute(k_push_deposit<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        configured[push] = smem;
+    static bool configured = false;
+    if (!configured) {
+        GX_CHECK(c, cudaFuncSetAttribute(k_pd<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pd_smem_bytes()));
+        GX_CHECK(c, cudaFuncSetAttribute(k_pd<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pd_smem_bytes()));
+        GX_CHECK(c, cudaFuncSetAttribute(k_arrivals, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)arr_smem_bytes()));
+        configured = true;
     }
+    int dev = 0, nsm = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int nbatch = (int)((c->N + kGroups - 1) / kGroups);
+    const int grid = std::max(1, std::min(nbatch, nsm));
     const int nxt = 1 - c->cur;
+    const int sf2pf[kMaxF] = {PF_OX, PF_OY, PF_VX, PF_VY, PF_VZ, PF_W, PF_ID};
     for (int s = 0; s < c->nspecies; ++s) {
         Species &S = c->sp[s];
-        PDParams p{};
-        for (int d = 0; d < 3; ++d) {
-            p.n[d] = c->n[d];
-            p.T[d] = c->tg.T[d];
-            p.ntile[d] = c->tg.ntile[d];
-            p.dtdx[d] = (float)(c->cfg.dt / c->cfg.dx[d]);
-        }
-        p.LD[0] = c->tg.T[0] + 2; p.LD[1] = c->tg.T[1] + 2; p.LD[2] = 1;
-        p.NLD[0] = c->tg.T[0] + 3; p.NLD[1] = c->tg.T[1] + 3; p.NLD[2] = 1;
-        p.local = c->tg.local;
-        p.ring = c->tg.ring;
+        P2 p{};
+        p.nx = c->n[0]; p.ny = c->n[1]; p.N = c->N;
         p.cap = S.cap;
+        p.nbatch = nbatch;
+        p.nf = c->cfg.track_ids ? 7 : 6;
+        p.dtdx = (float)(c->cfg.dt / c->cfg.dx[0]);
+        p.dtdy = (float)(c->cfg.dt / c->cfg.dx[1]);
         const double beta = S.q * c->cfg.dt / (2.0 * S.m);
         p.beta = (float)beta;
         p.bc = (float)(beta / c->cfg.c);
-        p.track = c->cfg.track_ids;
-        for (int f = 0; f < PF_COUNT; ++f) {
-            p.in[f] = S.f[c->cur][f];
-            p.out[f] = S.f[nxt][f];
+        for (int f = 0; f < kMaxF; ++f) {
+            p.in[f] = S.f[c->cur][sf2pf[f]];
+            p.out[f] = S.f[nxt][sf2pf[f]];
         }
         p.cnt_in = S.cnt[c->cur];
         p.cnt_out = S.cnt[nxt];
+        p.rec = c->rec + (size_t)s * c->N * Rec<2>::SIZE;
+        p.flags = c->dflags;
         if (push) {
             p.mE = c->nE; p.mB = c->nB; p.dB = c->nBnext; p.dU = c->nUref;
             GX_CHECK(c, cudaMemsetAsync(S.cnt[nxt], 0, c->N * sizeof(int), st));
+            k_pd<true><<<grid, kThreads, pd_smem_bytes(), st>>>(p);
+            GX_LAUNCHED(c);
+            k_arrivals<<<grid, kThreads, arr_smem_bytes(), st>>>(p);
+            GX_LAUNCHED(c);
         } else {
             p.mE = nullptr; p.mB = nullptr; p.dB = c->nB; p.dU = c->nUref;
-        }
-        p.rec = c->rec + (size_t)s * c->N * Rec<2>::SIZE;
-        p.ring_out = c->ring + (size_t)s * c->tg.ntiles * c->tg.ring * Rec<2>::SIZE;
-        p.ring_slot = c->ring_slot_of_local;
-        p.flags = c->dflags;
-        if (push) k_push_deposit<true><<<c->tg.ntiles, kThreads, smem, st>>>(p);
-        else k_push_deposit<false><<<c->tg.ntiles, kThreads, smem, st>>>(p);
-        GX_LAUNCHED(c);
-        if (push) {
-            const int64_t warps = (int64_t)c->tg.ntiles * c->tg.ring;
-            k_fold_rings<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>(
-                p.rec, p.ring_out, c->ring_local_of_slot, c->tg.ring, c->tg.ntiles, c->tg.ntile[0], c->tg.T[0],
-                c->tg.T[1], c->tg.T[0] + 2, c->n[0], c->n[1]);
+            k_pd<false><<<grid, kThreads, pd_smem_bytes(), st>>>(p);
             GX_LAUNCHED(c);
         }
     }
@@ -682,7 +725,7 @@ static int launch_pd(gx_ctx *c, bool push, cudaStream_t st) {
         c->cur = nxt;
         GX_CHECK(c, cudaMemsetAsync(&c->dflags->maxcount, 0, sizeof(int), st));
         for (int s = 0; s < c->nspecies; ++s) {
-            k_max_count<<<grid_for(c->N), 256, 0, st>>>(c->sp[s].cnt[c->cur], c->N, c->dflags);
+            k_max_count<<<grid_for(c->N), 256, 0, st>>>(c->sp[s].cnt[c->cur], c->N, c->sp[s].cap, c->dflags);
             GX_LAUNCHED(c);
         }
     }
@@ -695,13 +738,16 @@ int gx_run_push_deposit(gx_ctx *c, cudaStream_t st) { return launch_pd(c, true, 
 int gx_particles_out(gx_ctx *c, int s, double *x, double *y, double *z, float *vx, float *vy, float *vz, float *w,
                      int32_t *id, cudaStream_t st) {
     Species &S = c->sp[s];
-    int *offs = nullptr;
+    int *offs = nullptr, *counts = nullptr;
     void *tmp = nullptr;
     size_t tmpb = 0;
     GX_CHECK(c, cudaMalloc(&offs, (c->N + 1) * sizeof(int)));
-    cub::DeviceScan::ExclusiveSum(nullptr, tmpb, S.cnt[c->cur], offs, (int)c->N, st);
+    GX_CHECK(c, cudaMalloc(&counts, (c->N + 1) * sizeof(int)));
+    k_counts<<<grid_for(c->N), 256, 0, st>>>(S.cnt[c->cur], c->N, S.cap, counts);
+    GX_LAUNCHED(c);
+    cub::DeviceScan::ExclusiveSum(nullptr, tmpb, counts, offs, (int)c->N, st);
     GX_CHECK(c, cudaMalloc(&tmp, tmpb + 16));
-    GX_CHECK(c, cub::DeviceScan::ExclusiveSum(tmp, tmpb, S.cnt[c->cur], offs, (int)c->N, st));
+    GX_CHECK(c, cub::DeviceScan::ExclusiveSum(tmp, tmpb, counts, offs, (int)c->N, st));
     float **dsrc = nullptr;
     GX_CHECK(c, cudaMalloc(&dsrc, PF_COUNT * sizeof(float *)));
     GX_CHECK(c, cudaMemcpyAsync(dsrc, S.f[c->cur], PF_COUNT * sizeof(float *), cudaMemcpyHostToDevice, st));
@@ -709,11 +755,10 @@ int gx_particles_out(gx_ctx *c, int s, double *x, double *y, double *z, float *v
                                                   c->cfg.dx[0], c->cfg.dx[1], x, y, z, vx, vy, vz, w, id);
     GX_LAUNCHED(c);
     GX_CHECK(c, cudaStreamSynchronize(st));
-    cudaFree(offs); cudaFree(tmp); cudaFree(dsrc);
+    cudaFree(offs); cudaFree(counts); cudaFree(tmp); cudaFree(dsrc);
     return GX_OK;
 }
 
-size_t gx_pd_smem_bytes(const gx_ctx *c) { return pd_smem_bytes(c); }
 void gx_free_bins(gx_ctx *c) {
     for (int s = 0; s < c->nspecies; ++s) free_bins(c->sp[s]);
 }
