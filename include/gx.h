@@ -218,8 +218,9 @@ int gx_timers(gx_ctx *ctx, double *push_ms, double *moments_ms, double *solve_ms
  * An addition of this project (the paper has no learned preconditioner): a
  * 2D convolutional network N with four 3x3 layers (3 -> 32 -> 32 -> 32 -> 3
  * channels, ReLU between, periodic padding), BF16 weights and activations
- * with FP32 accumulation, applied as z = s N(r / s), s = ||r||_2 / sqrt(3 N),
- * as the right preconditioner of FGMRES.  2D only. */
+ * with FP32 accumulation, applied with a skip connection as
+ * z = r + s N(r / s), s = ||r||_2 / sqrt(3 N), as the right preconditioner of
+ * FGMRES.  2D only. */
 
 /* Number of FP32 parameters of the network (weights [Cout][Cin][3][3] then
  * biases [Cout], per layer). */
@@ -230,27 +231,40 @@ int64_t gx_precond_param_count(void);
 int gx_precond_set_weights(gx_ctx *ctx, const float *params, int64_t n, int ptr_is_device);
 int gx_precond_get_weights(gx_ctx *ctx, float *params, int64_t n, int ptr_is_device);
 
-/* Keep up to `capacity` (residual, error) pairs from the solves that follow:
- * each solve contributes r0 = b - A E^n and e = E^{n+theta} - E^n (so A e = r0
- * to the solver tolerance).  capacity = 0 stops collecting. */
+/* Keep up to `capacity` (residual, error) pairs (a ring: the newest replace
+ * the oldest) from the converged solves that follow.  Each solve contributes
+ * r0 = b - A E^n with e = E^{n+theta} - E^n (A e = r0 to the solver
+ * tolerance), and (A V_j, V_j) for its first Krylov basis vectors V_j (up to
+ * 6, one matrix-vector product each), which resemble what the preconditioner
+ * is applied to.  capacity = 0 stops collecting. */
 int gx_precond_collect(gx_ctx *ctx, int capacity);
 int gx_precond_pairs(gx_ctx *ctx);
 
-/* Train the network on the device with Adam (lr) on `npairs` random crops of
- * crop x crop nodes drawn from the collected pairs, in batches of `batch`, for
- * `epochs` passes; loss = mean squared error of N(r/s) against e/s.  Forward,
- * backward (data and weight gradients) and the update run in this library's
- * kernels.  loss_out (may be NULL) receives the mean loss of each epoch. */
+/* Train the network on the device with Adam (lr, beta1 0.9, beta2 0.999,
+ * eps 1e-8, on an FP32 master copy) for `epochs` passes of `npairs` samples
+ * each, in batches of `batch`.  A sample is a crop x crop window (crop >= 8) at
+ * a random position (seeded by `seed`) of a random collected pair, cut from the
+ * periodic grid with a 4-node halo so that the four 3x3 layers see exactly the
+ * values they would see on the whole grid.  With s = ||r||_2 / sqrt(3 N) of the
+ * pair (the scale the solver applies), the network learns the remainder of the
+ * skip connection: loss = sum over the crop of (N(r/s) - (e - r)/s)^2 /
+ * (2 * 3 crop^2 * batch).
+ * Forward, backward (data and weight gradients) and the update run in this
+ * library's kernels.  loss_out (may be NULL) receives the mean batch loss of
+ * each epoch.  GX_ESTATE if no pair has been collected. */
 int gx_precond_train(gx_ctx *ctx, int npairs, int crop, int batch, int epochs, float lr,
                      uint64_t seed, float *loss_out, void *stream);
 
-/* One forward pass of the network on a [3][H][W] FP32 input (H = ny, W = nx
- * of the context, or any H, W when called with ctx == NULL is not allowed):
- * out = N(in) without the s-scaling.  Device pointers only.  For tests. */
+/* One forward pass of the network on a [3][H][W] FP32 input with periodic
+ * padding: out = N(in), without the s-scaling.  H, W >= 1 are free (they need
+ * not match the context's grid).  Device pointers; synchronises `stream`.
+ * For tests. */
 int gx_precond_forward(gx_ctx *ctx, int H, int W, const float *in, float *out, void *stream);
 
-/* Loss and gradients of one [3][H][W] sample: *loss = mean (N(in) - target)^2 / 2,
- * grad (param_count FP32) = dloss/dparams.  Device pointers.  For tests. */
+/* Loss and gradients of one [3][H][W] sample with zero padding:
+ * *loss = sum (N(in) - target)^2 / (2 * 3 H W), grad (param_count FP32, the
+ * layout of gx_precond_set_weights) = dloss/dparams.  Device pointers;
+ * synchronises `stream`.  For tests. */
 int gx_precond_loss_grad(gx_ctx *ctx, int H, int W, const float *in, const float *target,
                          float *loss, float *grad, void *stream);
 

@@ -268,6 +268,45 @@ class Context:
         self._check(lib().gx_timers(self.h, C.byref(a), C.byref(b), C.byref(s), C.byref(L), int(reset)))
         return {"push_ms": a.value, "moments_ms": b.value, "solve_ms": s.value, "launches": L.value}
 
+    # ------------------------------------------- learned preconditioner
+    @staticmethod
+    def precond_param_count():
+        return int(lib().gx_precond_param_count())
+
+    def precond_set_weights(self, params):
+        p, d = _ptr(params)
+        self._check(lib().gx_precond_set_weights(self.h, p, len(params), d))
+
+    def precond_get_weights(self):
+        out = np.zeros(self.precond_param_count(), np.float32)
+        self._check(lib().gx_precond_get_weights(self.h, out.ctypes.data, len(out), 0))
+        return out
+
+    def precond_collect(self, capacity):
+        self._check(lib().gx_precond_collect(self.h, int(capacity)))
+
+    def precond_pairs(self):
+        return int(lib().gx_precond_pairs(self.h))
+
+    def precond_train(self, npairs, crop, batch, epochs, lr, seed=0, stream=None):
+        losses = np.zeros(epochs, np.float32)
+        self._check(lib().gx_precond_train(self.h, int(npairs), int(crop), int(batch), int(epochs), float(lr),
+                                           int(seed), losses.ctypes.data, _stream(stream)))
+        return losses
+
+    def precond_forward(self, x, out, stream=None):
+        """x, out: CUDA float32 tensors of shape (3, H, W); out = N(x), periodic padding."""
+        _, H, W = x.shape
+        self._check(lib().gx_precond_forward(self.h, H, W, x.data_ptr(), out.data_ptr(), _stream(stream)))
+        return out
+
+    def precond_loss_grad(self, x, target, grad, stream=None):
+        """Loss and parameter gradient of one (3, H, W) sample, zero padding; grad: CUDA float32."""
+        _, H, W = x.shape
+        L = C.c_float()
+        self._check(lib().gx_precond_loss_grad(self.h, H, W, x.data_ptr(), target.data_ptr(), C.byref(L),
+                                               grad.data_ptr(), _stream(stream)))
+        return L.value
 
 def from_workload(wl, *, track_ids=0, precond=GX_PRECOND_NONE, gmres_tol=None, bin_slack=1.6, gmres_restart=50):
     """Create a context from a workloads.Workload (inputs copied from host)."""

@@ -388,7 +388,7 @@ int gx_fgmres(gx_ctx *c, cudaStream_t st) {
     c->last.iters = hf->total;
     c->last.relres = tail[0];
     c->last.converged = hf->conv;
-    if ((rc = gx_net_pair_end(c, hf->conv, st))) return rc;
+    if ((rc = gx_net_pair_end(c, hf->conv, std::min(hf->total, m), st))) return rc;
     if (!hf->conv) {
         c->err = "GMRES reached gmres_maxit without converging (best iterate kept)";
         return GX_ENOCONV;

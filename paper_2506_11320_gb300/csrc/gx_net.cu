@@ -3,8 +3,11 @@
 //
 // Network N: four 3x3 convolutions, channels 3 -> 32 -> 32 -> 32 -> 3, ReLU
 // between them, on the 2D node grid (H = ny rows, W = nx columns), BF16 weights
-// and activations with FP32 accumulation.  Inside FGMRES it is applied as
-// z = s N(r / s), s = ||r||_2 / sqrt(3 N), with periodic padding.
+// and activations with FP32 accumulation.  Inside FGMRES it is applied with a
+// skip connection, z = r + s N(r / s), s = ||r||_2 / sqrt(3 N), periodic
+// padding: the field operator is the identity plus terms of a few per cent at
+// the usual time steps, so the network only has to learn the small remainder
+// A^-1 r - r, and its BF16 rounding error is relative to that remainder.
 //
 // Kernels (all on the tensor cores through mma.sync m16n8k16 BF16 -> FP32):
 //   * k_conv: implicit-GEMM convolution, M = 16 pixels of a row, N = output
@@ -344,13 +347,12 @@ __global__ void k_pack_input(const T *src, int64_t HW, bf16 *dst, const double *
     }
 }
 
-template <typename T>
-__global__ void k_unpack_output(const float *y, int64_t HW, T *dst, const double *sumsq) {
-    double s = 1.0;
-    if (sumsq) s = sqrt(*sumsq / (3.0 * HW));
+// z = r + s y (the skip connection of the preconditioner)
+__global__ void k_unpack_output(const float *y, int64_t HW, const double *r, double *z, const double *sumsq) {
+    const double s = sqrt(*sumsq / (3.0 * HW));
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < HW; p += (int64_t)gridDim.x * blockDim.x)
 #pragma unroll
-        for (int c = 0; c < 3; ++c) dst[c * HW + p] = (T)(s * (double)y[p * 8 + c]);
+        for (int c = 0; c < 3; ++c) z[c * HW + p] = r[c * HW + p] + s * (double)y[p * 8 + c];
 }
 
 __global__ void k_sumsq(const double *x, int64_t n, double *out) {
@@ -362,19 +364,18 @@ __global__ void k_sumsq(const double *x, int64_t n, double *out) {
 }
 
 // training crops: for crop b, input = r / s_b on a (C+8)^2 window (4-pixel halo,
-// periodic in the source field) and target = e / s_b on the central C^2, with
-// s_b the RMS of r over the central C^2.
+// periodic in the source field) and target = (e - r) / s_b on the central C^2
+// (the network learns the remainder of the skip connection), with
+// s_b = ||r||_2 / sqrt(3 N) over the whole field, the scale the solver uses
 struct CropSpec {
     int pair, y0, x0, pad;
 };
-__global__ void k_crop_scale(const float *pairs, int64_t N, int nx, int ny, const CropSpec *spec, int C, float *scale) {
+__global__ void k_crop_scale(const float *pairs, int64_t N, const CropSpec *spec, float *scale) {
     const CropSpec sp = spec[blockIdx.x];
     const float *r = pairs + (size_t)sp.pair * 6 * N;
     double s = 0.0;
-    for (int t = threadIdx.x; t < 3 * C * C; t += blockDim.x) {
-        const int c = t / (C * C), rem = t % (C * C), yy = rem / C, xx = rem % C;
-        const int gy = wrapn(sp.y0 + yy, ny), gx = wrapn(sp.x0 + xx, nx);
-        const double v = r[c * N + gy * (int64_t)nx + gx];
+    for (int64_t t = threadIdx.x; t < 3 * N; t += blockDim.x) {
+        const double v = r[t];
         s += v * v;
     }
     __shared__ double sh[32];
@@ -384,7 +385,7 @@ __global__ void k_crop_scale(const float *pairs, int64_t N, int nx, int ny, cons
     if (threadIdx.x == 0) {
         double t = 0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
-        const double rms = sqrt(t / (3.0 * C * C));
+        const double rms = sqrt(t / (3.0 * N));
         scale[blockIdx.x] = rms > 0 ? (float)rms : 1.f;
     }
 }
@@ -407,7 +408,8 @@ __global__ void k_crop_gather(const float *pairs, int64_t N, int nx, int ny, con
         reinterpret_cast<uint4 *>(d)[1] = reinterpret_cast<uint4 *>(v)[1];
         const bool inner = yy >= 4 && yy < 4 + C && xx >= 4 && xx < 4 + C;
 #pragma unroll
-        for (int c = 0; c < 3; ++c) target[((int64_t)b * S * S + t) * 3 + c] = inner ? e[c * N + q] * inv : 0.f;
+        for (int c = 0; c < 3; ++c)
+            target[((int64_t)b * S * S + t) * 3 + c] = inner ? (e[c * N + q] - r[c * N + q]) * inv : 0.f;
     }
 }
 
@@ -452,6 +454,14 @@ __global__ void k_store_pair(const double *r0, const double *eth, const double *
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x) {
         if (r0) dst[i] = (float)r0[i];
         else dst[n3 + i] = (float)(eth[i] - en[i]);
+    }
+}
+
+// pair slot [2][3][N] = (r, e), both given
+__global__ void k_store_rv(const double *r, const double *e, int64_t n3, float *dst) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x) {
+        dst[i] = (float)r[i];
+        dst[n3 + i] = (float)e[i];
     }
 }
 
@@ -593,7 +603,7 @@ static int net_backward(gx_ctx *c, int B, int H, int W, int periodic, float grad
 }
 
 // ------------------------------------------------------------ solver hooks
-// z = s N(r / s), s = ||r|| / sqrt(3 N): FP64 [3][N] in and out
+// z = r + s N(r / s), s = ||r|| / sqrt(3 N): FP64 [3][N] in and out
 int gx_net_apply(gx_ctx *c, const double *r, double *z, cudaStream_t st) {
     if (c->dim != 2) { c->err = "the learned preconditioner is 2D"; return GX_ENOTIMPL; }
     int rc = net_alloc(c);
@@ -608,14 +618,20 @@ int gx_net_apply(gx_ctx *c, const double *r, double *z, cudaStream_t st) {
     k_pack_input<double><<<nblk(c->N), 256, 0, st>>>(r, c->N, n->x0, n->dsum, 1.0);
     GX_LAUNCHED(c);
     if ((rc = net_forward(c, 1, H, W, 1, st))) return rc;
-    k_unpack_output<double><<<nblk(c->N), 256, 0, st>>>(n->y, c->N, z, n->dsum);
+    k_unpack_output<<<nblk(c->N), 256, 0, st>>>(n->y, c->N, r, z, n->dsum);
     GX_LAUNCHED(c);
     return GX_OK;
 }
 
 // collection of (residual, error) pairs around one solve with initial guess
 // E^n: the first residual r0 = b - A E^n is kept when the solve starts and the
-// error e = E^{n+theta} - E^n is added once it has converged
+// error e = E^{n+theta} - E^n is added once it has converged.  The inputs the
+// preconditioner sees inside FGMRES are Krylov vectors, which carry far more
+// small-scale content than r0, so the first kKrylovPairs basis vectors V_j of
+// the solve are added too, as exact pairs (A V_j, V_j) at one matrix-vector
+// product each.
+constexpr int kKrylovPairs = 6;
+
 int gx_net_pair_begin(gx_ctx *c, const double *r0, cudaStream_t st) {
     Net *n = c->net;
     if (!n || !n->collect || n->cap_pairs < 1) return GX_OK;
@@ -626,16 +642,31 @@ int gx_net_pair_begin(gx_ctx *c, const double *r0, cudaStream_t st) {
     return GX_OK;
 }
 
-int gx_net_pair_end(gx_ctx *c, int converged, cudaStream_t st) {
+static void advance_slot(Net *n) {
+    n->next_pair = (n->next_pair + 1) % n->cap_pairs;
+    n->npairs = std::min(n->npairs + 1, n->cap_pairs);
+}
+
+int gx_net_pair_end(gx_ctx *c, int converged, int nbasis, cudaStream_t st) {
     Net *n = c->net;
     if (!n || !n->pending_pair) return GX_OK;
     n->pending_pair = 0;
     if (!converged) return GX_OK;
+    const int64_t n3 = 3 * c->N;
     float *dst = n->pairs + (size_t)n->next_pair * 6 * c->N;
-    k_store_pair<<<nblk(3 * c->N), 256, 0, st>>>(nullptr, c->Eth, c->E, 3 * c->N, dst);
+    k_store_pair<<<nblk(n3), 256, 0, st>>>(nullptr, c->Eth, c->E, n3, dst);
     GX_LAUNCHED(c);
-    n->next_pair = (n->next_pair + 1) % n->cap_pairs;
-    n->npairs = std::min(n->npairs + 1, n->cap_pairs);
+    advance_slot(n);
+    const int nv = std::min(nbasis, kKrylovPairs);
+    for (int j = 0; j < nv; ++j) {
+        const double *v = c->V + (size_t)j * n3;
+        int rc = gx_apply_A(c, v, c->w, st);
+        if (rc) return rc;
+        dst = n->pairs + (size_t)n->next_pair * 6 * c->N;
+        k_store_rv<<<nblk(n3), 256, 0, st>>>(c->w, v, n3, dst);
+        GX_LAUNCHED(c);
+        advance_slot(n);
+    }
     return GX_OK;
 }
 
@@ -738,7 +769,7 @@ int gx_precond_train(gx_ctx *c, int npairs, int crop, int batch, int epochs, flo
                 spec[b].pad = 0;
             }
             GX_CHECK(c, cudaMemcpyAsync(dspec, spec.data(), B * sizeof(CropSpec), cudaMemcpyHostToDevice, st));
-            k_crop_scale<<<B, 256, 0, st>>>(n->pairs, c->N, c->n[0], c->n[1], dspec, crop, dscale);
+            k_crop_scale<<<B, 1024, 0, st>>>(n->pairs, c->N, dspec, dscale);
             GX_LAUNCHED(c);
             k_crop_gather<<<dim3(nblk((int64_t)S * S), B), 256, 0, st>>>(n->pairs, c->N, c->n[0], c->n[1], dspec, crop,
                                                                            dscale, n->x0, n->target);

@@ -1,0 +1,226 @@
+"""GPU parity of the learned preconditioner's kernels (BF16 tensor-core 3x3
+convolutions with FP32 accumulation: forward, data gradient, weight gradient)
+against the FP64 oracle network, and the gain of the trained network inside
+FGMRES.
+
+Tolerances.  The oracle runs on the same BF16-rounded weights and inputs, so
+what remains is the BF16 rounding (relative 2^-9) of the three hidden
+activations and, backwards, of the propagated gradients, plus FP32
+accumulation.  Against the FP64 oracle: relative L2 <= 1e-2 for the network
+output and the loss; <= 5e-2 for every layer's weight and bias gradient (the
+first layer's weight gradient sums products of three times re-rounded
+back-propagated values over all pixels with cancellation; a BF16 emulation in
+plain PyTorch shows the same 2-4 % on these inputs).  Against that emulation,
+which rounds at the same points as the kernels, the kernels agree to 2e-3 in
+the output and 1e-2 in the gradients (FP32 against FP64 accumulation moves a
+few values across a BF16 rounding boundary, and the first layer's weight
+gradient amplifies that by the same cancellation).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+TOL_FWD = 1e-2
+TOL_GRAD = 5e-2
+TOL_EMU = 2e-3
+TOL_EMU_GRAD = 1e-2
+
+
+def rel(a, b):
+    nb = np.linalg.norm(b)
+    return float(np.linalg.norm(a - b) / (nb if nb > 0 else 1.0))
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2506_11320_gb300 as g
+    g.lib()
+    ctx = g.Context(g.make_config((16, 8, 1), (0.1, 0.1, 1.0)))
+    yield g, torch, ctx
+    ctx.close()
+
+
+def bf16(torch, a):
+    return torch.from_numpy(np.asarray(a, np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+
+
+def random_params(seed, bias_scale=0.1):
+    """He-scaled weights and small biases, in the oracle's layout."""
+    rng = np.random.default_rng(seed)
+    chans = [3, 32, 32, 32, 3]
+    out = []
+    for l in range(4):
+        cin, cout = chans[l], chans[l + 1]
+        out.append(rng.standard_normal(cout * cin * 9) * np.sqrt(2.0 / (9 * cin)))
+        out.append(rng.standard_normal(cout) * bias_scale)
+    p = np.concatenate(out)
+    assert p.size == O.net_param_count()
+    return p
+
+
+def weights_bf16(torch, p):
+    """Round every weight (not the biases, which stay FP32) to BF16."""
+    q = p.copy()
+    chans = [3, 32, 32, 32, 3]
+    off = 0
+    for l in range(4):
+        nw = chans[l + 1] * chans[l] * 9
+        q[off:off + nw] = bf16(torch, p[off:off + nw])
+        off += nw + chans[l + 1]
+    return q
+
+
+def layer_slices():
+    chans = [3, 32, 32, 32, 3]
+    off, out = 0, []
+    for l in range(4):
+        nw = chans[l + 1] * chans[l] * 9
+        out.append((f"W{l + 1}", slice(off, off + nw)))
+        out.append((f"b{l + 1}", slice(off + nw, off + nw + chans[l + 1])))
+        off += nw + chans[l + 1]
+    return out
+
+
+def emulate_bf16(torch, p, x, t=None, periodic=True):
+    """The network in plain PyTorch (CPU, FP64 arithmetic) rounding to BF16 at
+    the points where the kernels store BF16: the input, the hidden
+    activations, and backwards the output gradient and the propagated
+    gradients.  Returns y, or (y, grads by layer name) when t is given."""
+    F = torch.nn.functional
+    chans = [3, 32, 32, 32, 3]
+    off, Ws, bs = 0, [], []
+    for l in range(4):
+        nw = chans[l + 1] * chans[l] * 9
+        Ws.append(torch.tensor(p[off:off + nw], dtype=torch.float64).reshape(chans[l + 1], chans[l], 3, 3))
+        bs.append(torch.tensor(p[off + nw:off + nw + chans[l + 1]], dtype=torch.float64))
+        off += nw + chans[l + 1]
+
+    def rb(a):
+        return a.to(torch.bfloat16).to(torch.float64)
+
+    def pad(a):
+        return F.pad(a, (1, 1, 1, 1), mode="circular") if periodic else F.pad(a, (1, 1, 1, 1))
+
+    h = [rb(torch.tensor(x, dtype=torch.float64)[None])]
+    for l in range(4):
+        a = F.conv2d(pad(h[-1]), Ws[l]) + bs[l][None, :, None, None]
+        h.append(rb(torch.relu(a)) if l < 3 else a)
+    y = h[-1]
+    if t is None:
+        return y[0].numpy()
+    assert not periodic
+    H, W = x.shape[1:]
+    d = rb((y - torch.tensor(t, dtype=torch.float64)[None]) / y.numel())
+    grads = {}
+    for l in range(3, -1, -1):
+        hl = pad(h[l])
+        gw = torch.zeros_like(Ws[l])
+        for ky in range(3):
+            for kx in range(3):
+                gw[:, :, ky, kx] = torch.einsum("bohw,bihw->oi", d, hl[:, :, ky:ky + H, kx:kx + W])
+        grads[f"W{l + 1}"] = gw.reshape(-1).numpy()
+        grads[f"b{l + 1}"] = d.sum((0, 2, 3)).numpy()
+        if l > 0:
+            d = rb(F.conv_transpose2d(d, Ws[l], padding=1) * (h[l] > 0))
+    return y[0].numpy(), grads
+
+
+# (H, W): several 8x16 tiles with ragged tails, one exact tile, smaller than a tile
+SHAPES = [(24, 40), (8, 16), (5, 7), (33, 50)]
+
+
+@pytest.mark.parametrize("H,W", SHAPES)
+def test_forward_matches_oracle(env, H, W):
+    g, torch, ctx = env
+    p = random_params(11)
+    ctx.precond_set_weights(p.astype(np.float32))
+    x = np.random.default_rng(H * 1000 + W).standard_normal((3, H, W))
+    xb = bf16(torch, x)
+    y_ref = O.net_forward(weights_bf16(torch, p.astype(np.float32)), xb, periodic=True)
+    xd = torch.from_numpy(xb.astype(np.float32)).cuda()
+    yd = torch.zeros((3, H, W), dtype=torch.float32, device="cuda")
+    ctx.precond_forward(xd, yd)
+    y = yd.cpu().numpy().astype(np.float64)
+    assert np.all(np.isfinite(y))
+    assert rel(y, y_ref) <= TOL_FWD, rel(y, y_ref)
+    y_emu = emulate_bf16(torch, weights_bf16(torch, p.astype(np.float32)), xb)
+    assert rel(y, y_emu) <= TOL_EMU, rel(y, y_emu)
+
+
+@pytest.mark.parametrize("H,W", [(16, 24), (9, 13), (24, 40)])
+def test_loss_and_gradients_match_oracle(env, H, W):
+    g, torch, ctx = env
+    p = random_params(23)
+    ctx.precond_set_weights(p.astype(np.float32))
+    rng = np.random.default_rng(7 + H)
+    xb = bf16(torch, rng.standard_normal((3, H, W)))
+    t = rng.standard_normal((3, H, W)).astype(np.float32).astype(np.float64)
+    pb = weights_bf16(torch, p.astype(np.float32))
+    L_ref, g_ref, _ = O.net_loss_backward(pb, xb, t, periodic=False)
+    _, g_emu = emulate_bf16(torch, pb, xb, t, periodic=False)
+    xd = torch.from_numpy(xb.astype(np.float32)).cuda()
+    td = torch.from_numpy(t.astype(np.float32)).cuda()
+    gd = torch.zeros(O.net_param_count(), dtype=torch.float32, device="cuda")
+    L = ctx.precond_loss_grad(xd, td, gd)
+    grad = gd.cpu().numpy().astype(np.float64)
+    assert abs(L - L_ref) <= TOL_FWD * abs(L_ref), (L, L_ref)
+    for name, sl in layer_slices():
+        e = rel(grad[sl], g_ref[sl])
+        assert e <= TOL_GRAD, (name, e)
+        e = rel(grad[sl], g_emu[name])
+        assert e <= TOL_EMU_GRAD, (name, "vs BF16 emulation", e)
+
+
+def test_set_get_weights_roundtrip_and_errors(env):
+    g, torch, ctx = env
+    p = random_params(5).astype(np.float32)
+    ctx.precond_set_weights(p)
+    assert np.array_equal(ctx.precond_get_weights(), p)
+    L = g.lib()
+    assert L.gx_precond_set_weights(ctx.h, p.ctypes.data, p.size - 1, 0) == g.GX_EINVAL
+    # training without collected pairs is a state error, not a crash
+    assert L.gx_precond_train(ctx.h, 4, 8, 2, 1, 1e-3, 0, None, None) == g.GX_ESTATE
+
+
+def test_trained_network_reduces_gmres_iterations(env):
+    """Collect (r0, E^{n+theta} - E^n) pairs from the run's own solves, train on
+    the GPU, then compare FGMRES with the trained network against plain GMRES
+    on the same plasma: fewer matrix-vector products per solve, the same true
+    relative residual, the same fields."""
+    g, torch, _ = env
+    wl = workloads.harris(nx=64, ny=32, ppc=16, steps=40)
+    plain = g.from_workload(wl, precond=g.GX_PRECOND_NONE)
+    net = g.from_workload(wl, precond=g.GX_PRECOND_NET)
+    try:
+        net.precond_collect(256)
+        it_plain, it_untrained = [], []
+        for _ in range(24):
+            it_plain.append(plain.step(1).iters)
+            it_untrained.append(net.step(1).iters)
+        assert net.precond_pairs() >= 24
+        losses = net.precond_train(npairs=256, crop=16, batch=32, epochs=100, lr=2e-3, seed=3)
+        assert np.all(np.isfinite(losses))
+        assert losses[-1] < 0.5 * losses[0], losses
+        net.precond_collect(0)
+        it_plain2, it_net = [], []
+        for _ in range(8):
+            sp = plain.step(1)
+            sn = net.step(1)
+            assert sp.converged and sn.converged
+            assert sn.relres <= wl.gmres_tol
+            it_plain2.append(sp.iters)
+            it_net.append(sn.iters)
+        Ep, Bp = plain.get_fields()
+        En, Bn = net.get_fields()
+        assert rel(En, Ep) <= 1e-5 and rel(Bn, Bp) <= 1e-5
+        assert np.mean(it_net) < np.mean(it_plain2), (it_net, it_plain2, it_untrained, losses)
+    finally:
+        plain.close()
+        net.close()
