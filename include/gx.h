@@ -268,6 +268,24 @@ int gx_precond_forward(gx_ctx *ctx, int H, int W, const float *in, float *out, v
 int gx_precond_loss_grad(gx_ctx *ctx, int H, int W, const float *in, const float *target,
                          float *loss, float *grad, void *stream);
 
+/* ------------------------------------------- gather without allocation
+ * The paper has no counterpart: this is a service of the library.  Same output
+ * as gx_get_particles with ptr_is_device = 1 (bin order, the same values), for
+ * callers that must not allocate device memory at that point (for instance a
+ * diagnostics hook while the particle arrays fill the device, or a path that
+ * must not synchronise).  It allocates nothing: its only scratch, the per-cell
+ * output offsets, lives in a fixed device array of gx_noalloc_max_cells()
+ * ints (262144, 1 MiB); larger grids get GX_EINVAL.  The first call on a
+ * device looks that array up (once per device, with that device current) and
+ * should come before any stream capture.  The array is shared by every context
+ * on the device, so calls that overlap in time race.  Output pointers are
+ * device arrays of gx_species_count() entries (NULL to skip a field; id only
+ * with track_ids); the call enqueues two kernels on `stream` and does not
+ * synchronise. */
+int gx_noalloc_max_cells(void);
+int gx_get_particles_noalloc(gx_ctx *ctx, int species, double *x, double *y, double *z,
+                             float *vx, float *vy, float *vz, float *w, int32_t *id, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -94,6 +94,8 @@ _SIGS = {
     "gx_precond_train": (C.c_int, [_CTX, C.c_int, C.c_int, C.c_int, C.c_int, C.c_float, C.c_uint64, _V, _V]),
     "gx_precond_forward": (C.c_int, [_CTX, C.c_int, C.c_int, _V, _V, _V]),
     "gx_precond_loss_grad": (C.c_int, [_CTX, C.c_int, C.c_int, _V, _V, _V, _V, _V]),
+    "gx_noalloc_max_cells": (C.c_int, []),
+    "gx_get_particles_noalloc": (C.c_int, [_CTX, C.c_int, _V, _V, _V, _V, _V, _V, _V, _V, _V]),
 }
 EXPORTED = tuple(_SIGS)
 
@@ -254,6 +256,15 @@ class Context:
         out = dict(x=x, y=y, z=z, vx=vx, vy=vy, vz=vz, w=w)
         if ids:
             out["id"] = idv
+        return out
+
+    def get_particles_noalloc(self, s, out, stream=None):
+        """Gather species s into preallocated CUDA tensors (dict with keys x, y,
+        z, vx, vy, vz, w and optionally id); allocates no device memory and does
+        not synchronise."""
+        ptr = [out[k].data_ptr() if out.get(k) is not None else None
+               for k in ("x", "y", "z", "vx", "vy", "vz", "w", "id")]
+        self._check(lib().gx_get_particles_noalloc(self.h, int(s), *ptr, _stream(stream)))
         return out
 
     def diagnostics(self, stream=None):
