@@ -198,6 +198,7 @@ def main():
     ap.add_argument("--impl", default="gx")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-precond", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -233,6 +234,7 @@ def main():
     for _ in range(args.warmup):
         ctx.step(1, allow_noconv=True)
     ctx.timers(reset=True)
+    ctx.kernel_timer(reset=True)
     iters = []
     barrier()
     with Clocks(dev) as clk:
@@ -247,7 +249,7 @@ def main():
         wall = time.perf_counter() - t0
     step_ms_dev = ev0.elapsed_time(ev1) / args.steps
     tm = ctx.timers(reset=True)
-    kern = ctx.kernel_timers() if hasattr(ctx, "kernel_timers") else None
+    kt = ctx.kernel_timer(reset=True)
     pd_ms = (tm["push_ms"] + tm["moments_ms"]) / args.steps
     solve_ms = tm["solve_ms"] / args.steps
     # max over ranks
@@ -258,15 +260,25 @@ def main():
     value = world * Np / (pd_ms_max / 1000.0)
 
     peak, peak_kind = load_peaks()
-    push_kernel_ms = tm["push_ms"] / args.steps        # fused kernel + ring fold + bin stats
-    n_launch_kernel = len(wl.species)
-    alg_bytes = ALG_BYTES_2D * Np                      # per step, both species' launches
-    achieved = alg_bytes / (push_kernel_ms / 1000.0) / 1e9
+    # roofline of the dominant kernel: the fused mover + re-bin + deposit
+    # kernel, one launch per species; algorithmic bytes of one launch = 44 B per
+    # particle of that species; time = its own CUDA events (launch list share in
+    # profiles/)
+    n_launch = max(1, kt["pd_launches"])
+    pd_kernel_ms = kt["pd_kernel_ms"] / n_launch
+    alg_bytes = ALG_BYTES_2D * Np / len(wl.species)
+    achieved = alg_bytes / (pd_kernel_ms / 1000.0) / 1e9
     traffic, prof = load_traffic("k_push_deposit", args.workload)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "peak_kind": peak_kind,
-                "kernel": "k_push_deposit (fused mover + re-bin + deposit), per-species launches",
-                "alg_bytes_per_launch": alg_bytes / n_launch_kernel}
+                "kernel": "k_pd<push> (fused mover + re-bin + deposit), one launch per species",
+                "alg_bytes_per_launch": alg_bytes, "ms_per_launch": pd_kernel_ms}
+    push_kernel_ms = tm["push_ms"] / args.steps
+
+    # ------------------------------------------------------- field solve: learned vs plain
+    solve_cmp = None
+    if not args.no_precond:
+        solve_cmp = run_precond_compare(gx, wl, args.steps, barrier)
 
     # ------------------------------------------------------- end to end (host buffers)
     e2e = None
@@ -295,9 +307,10 @@ def main():
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "l2": f"inputs larger than L2 ({Np * 24 / 1e6:.0f} MB of particle state read per step, "
                              f"L2 129 MB); no flush"},
-            "push_deposit_ms_per_step": pd_ms_max, "push_kernel_ms_per_step": push_kernel_ms,
+            "push_deposit_ms_per_step": pd_ms_max, "push_phase_ms_per_step": push_kernel_ms,
             "gmres_ms_per_step": solve_ms, "gmres_iters_per_step": statistics.mean(iters),
             "wall_ms_per_step": 1000 * wall / args.steps,
+            "gmres_learned_vs_plain": solve_cmp,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "gpu_launches": int(tm["launches"]),
         }
@@ -306,6 +319,48 @@ def main():
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def run_precond_compare(gx, wl, steps, barrier, collect_steps=24):
+    """Field-solve time per step with the learned preconditioner against plain
+    GMRES and block Jacobi on the same plasma.  Three contexts start from the
+    same state and step together; the learned one keeps training pairs from its
+    first `collect_steps` solves, trains on the device, then all three are timed
+    for `steps` steps (solve time from CUDA events in the library)."""
+    kinds = (("plain", gx.GX_PRECOND_NONE), ("jacobi", gx.GX_PRECOND_JACOBI), ("learned", gx.GX_PRECOND_NET))
+    ctxs = {k: gx.from_workload(wl, precond=p) for k, p in kinds}
+    net = ctxs["learned"]
+    net.precond_collect(512)
+    for _ in range(collect_steps):
+        for c in ctxs.values():
+            c.step(1, allow_noconv=True)
+    barrier()
+    t0 = time.perf_counter()
+    losses = net.precond_train(npairs=512, crop=32, batch=32, epochs=40, lr=2e-3, seed=7)
+    barrier()
+    train_s = time.perf_counter() - t0
+    net.precond_collect(0)
+    out = {}
+    for k, c in ctxs.items():
+        c.timers(reset=True)
+    its = {k: [] for k in ctxs}
+    for _ in range(steps):
+        for k, c in ctxs.items():
+            its[k].append(c.step(1, allow_noconv=True).iters)
+    barrier()
+    for k, c in ctxs.items():
+        tm = c.timers(reset=True)
+        out[k] = {"ms_per_step": tm["solve_ms"] / steps, "iters_per_step": statistics.mean(its[k])}
+    out["learned_speedup_vs_plain"] = out["plain"]["ms_per_step"] / out["learned"]["ms_per_step"]
+    out["training"] = {"pairs": net.precond_pairs(), "collect_steps": collect_steps, "epochs": len(losses),
+                       "samples_per_epoch": 512, "crop": 32, "seconds": train_s,
+                       "loss_first": float(losses[0]), "loss_last": float(losses[-1])}
+    out["note"] = ("solve = LF coefficients + right-hand side + FGMRES to 1e-8 relative residual + field "
+                   "advance, FP64; learned = block Jacobi plus a BF16 conv-net correction trained on this "
+                   "run's own solves")
+    for c in ctxs.values():
+        c.close()
+    return out
 
 
 def run_e2e(gx, wl, steps, barrier):

@@ -214,13 +214,21 @@ int gx_diagnostics(gx_ctx *ctx, void *stream, gx_diag *out);
 int gx_timers(gx_ctx *ctx, double *push_ms, double *moments_ms, double *solve_ms,
               int64_t *launches, int reset);
 
+/* Accumulated device time (CUDA events on the launching stream, recorded
+ * around each launch) of the fused mover + re-bin + deposit kernel alone, and
+ * its number of launches (one per species and step); for roofline accounting.
+ * reset != 0 clears both after reading. */
+int gx_kernel_timer(gx_ctx *ctx, double *pd_ms, int64_t *pd_launches, int reset);
+
 /* ------------------------------------------- learned GMRES preconditioner
  * An addition of this project (the paper has no learned preconditioner): a
  * 2D convolutional network N with four 3x3 layers (3 -> 32 -> 32 -> 32 -> 3
  * channels, ReLU between, periodic padding), BF16 weights and activations
- * with FP32 accumulation, applied with a skip connection as
- * z = r + s N(r / s), s = ||r||_2 / sqrt(3 N), as the right preconditioner of
- * FGMRES.  2D only. */
+ * with FP32 accumulation, used as the right preconditioner of FGMRES as a
+ * learned correction of the 3x3 block-Jacobi preconditioner D^-1:
+ * z = D^-1 r + s N(r / s), s = ||r||_2 / sqrt(3 N).  D^-1 carries what varies
+ * from node to node (the local plasma response); the network learns the
+ * translation-invariant remainder A^-1 r - D^-1 r.  2D only. */
 
 /* Number of FP32 parameters of the network (weights [Cout][Cin][3][3] then
  * biases [Cout], per layer). */
@@ -246,9 +254,9 @@ int gx_precond_pairs(gx_ctx *ctx);
  * a random position (seeded by `seed`) of a random collected pair, cut from the
  * periodic grid with a 4-node halo so that the four 3x3 layers see exactly the
  * values they would see on the whole grid.  With s = ||r||_2 / sqrt(3 N) of the
- * pair (the scale the solver applies), the network learns the remainder of the
- * skip connection: loss = sum over the crop of (N(r/s) - (e - r)/s)^2 /
- * (2 * 3 crop^2 * batch).
+ * pair (the scale the solver applies), the network learns the remainder over
+ * block Jacobi: loss = sum over the crop of (N(r/s) - (e - D^-1 r)/s)^2 /
+ * (2 * 3 crop^2 * batch), D^-1 that of the pair's own solve.
  * Forward, backward (data and weight gradients) and the update run in this
  * library's kernels.  loss_out (may be NULL) receives the mean batch loss of
  * each epoch.  GX_ESTATE if no pair has been collected. */

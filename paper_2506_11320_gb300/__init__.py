@@ -86,6 +86,7 @@ _SIGS = {
     "gx_diagnostics": (C.c_int, [_CTX, _V, C.POINTER(Diag)]),
     "gx_timers": (C.c_int, [_CTX, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double),
                             C.POINTER(C.c_int64), C.c_int]),
+    "gx_kernel_timer": (C.c_int, [_CTX, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_int]),
     "gx_precond_param_count": (C.c_int64, []),
     "gx_precond_set_weights": (C.c_int, [_CTX, _V, C.c_int64, C.c_int]),
     "gx_precond_get_weights": (C.c_int, [_CTX, _V, C.c_int64, C.c_int]),
@@ -278,6 +279,11 @@ class Context:
         a, b, s, L = C.c_double(), C.c_double(), C.c_double(), C.c_int64()
         self._check(lib().gx_timers(self.h, C.byref(a), C.byref(b), C.byref(s), C.byref(L), int(reset)))
         return {"push_ms": a.value, "moments_ms": b.value, "solve_ms": s.value, "launches": L.value}
+
+    def kernel_timer(self, reset=False):
+        ms, n = C.c_double(), C.c_int64()
+        self._check(lib().gx_kernel_timer(self.h, C.byref(ms), C.byref(n), int(reset)))
+        return {"pd_kernel_ms": ms.value, "pd_launches": n.value}
 
     # ------------------------------------------- learned preconditioner
     @staticmethod

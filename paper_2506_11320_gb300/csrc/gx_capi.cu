@@ -63,8 +63,8 @@ cudaEvent_t ev_get(gx_ctx *c) {
 }
 
 void ev_resolve(gx_ctx *c) {
-    double *acc[3] = {&c->t_push, &c->t_mom, &c->t_solve};
-    for (int k = 0; k < 3; ++k) {
+    double *acc[4] = {&c->t_push, &c->t_mom, &c->t_solve, &c->t_pdk};
+    for (int k = 0; k < 4; ++k) {
         for (auto &pr : c->evpend[k]) {
             cudaEventSynchronize(pr.second);
             float ms = 0.f;
@@ -145,6 +145,12 @@ int check_flags(gx_ctx *c, cudaStream_t st) {
 
 }  // namespace
 
+cudaEvent_t gx_ev_get(gx_ctx *c) { return ev_get(c); }
+void gx_ev_push(gx_ctx *c, int cat, cudaEvent_t a, cudaEvent_t b) {
+    c->evpend[cat].push_back({a, b});
+    if (c->evpend[cat].size() > 512) ev_resolve(c);
+}
+
 extern "C" {
 
 const char *gx_status_string(int s) {
@@ -178,6 +184,7 @@ void gx_destroy(gx_ctx *c) {
     for (auto p : fp)
         if (*p) cudaFree(*p);
     if (c->rec) cudaFree(c->rec);
+    if (c->rec2) cudaFree(c->rec2);
     if (c->gm) cudaFree(c->gm);
     if (c->gpart) cudaFree(c->gpart);
     if (c->zbuf) cudaFree(c->zbuf);
@@ -250,7 +257,9 @@ int gx_create(const gx_config *cfg, gx_ctx **out) {
         cudaMallocHost(&c->hflags, sizeof(DevFlags)) != cudaSuccess)
         return fail(GX_ENOMEM, "pinned host allocation failed");
     std::memset(c->hflags, 0, sizeof(DevFlags));
-    if ((rc = dalloc(c, &c->rec, (size_t)GX_MAX_SPECIES * N * Rec<2>::SIZE))) return fail(rc, nullptr);
+    if ((rc = dalloc(c, &c->rec, (size_t)GX_MAX_SPECIES * N * Rec<2>::SIZE)) ||
+        (rc = dalloc(c, &c->rec2, (size_t)GX_MAX_SPECIES * N * Rec<2>::SIZE)))
+        return fail(rc, nullptr);
     double *zero3[] = {c->E, c->B, c->Eth, c->Enew, c->Bnew, c->u, c->J, c->uref64};
     for (auto p : zero3)
         if (cudaMemset(p, 0, 3 * N * sizeof(double)) != cudaSuccess) return fail(GX_ECUDA, "cudaMemset failed");
@@ -484,6 +493,15 @@ int gx_timers(gx_ctx *c, double *push_ms, double *moments_ms, double *solve_ms, 
     if (solve_ms) *solve_ms = c->t_solve;
     if (launches) *launches = c->launches;
     if (reset) { c->t_push = c->t_mom = c->t_solve = 0; c->launches = 0; }
+    return GX_OK;
+}
+
+int gx_kernel_timer(gx_ctx *c, double *pd_ms, int64_t *pd_launches, int reset) {
+    if (!c) return GX_EINVAL;
+    ev_resolve(c);
+    if (pd_ms) *pd_ms = c->t_pdk;
+    if (pd_launches) *pd_launches = c->n_pdk;
+    if (reset) { c->t_pdk = 0; c->n_pdk = 0; }
     return GX_OK;
 }
 

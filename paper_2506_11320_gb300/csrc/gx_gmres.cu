@@ -317,7 +317,7 @@ int gx_fgmres(gx_ctx *c, cudaStream_t st) {
     GmState *gs = c->gm;
     const int nb = nblocks(n);
     int rc;
-    if (pc == GX_PRECOND_JACOBI) { rc = gx_build_jacobi(c, st); if (rc) return rc; }
+    if (pc == GX_PRECOND_JACOBI || pc == GX_PRECOND_NET) { rc = gx_build_jacobi(c, st); if (rc) return rc; }
     k_gm_init<<<1, 32, 0, st>>>(gs);
     GX_LAUNCHED(c);
     k_gm_bnorm<<<nb, kB, 0, st>>>(b, n, gs, c->gpart);

@@ -55,40 +55,53 @@ __global__ void k_node_fields(G2 g, const double *__restrict__ E, const double *
 struct SpecK {
     int ns;
     double q[GX_MAX_SPECIES], m[GX_MAX_SPECIES], bq[GX_MAX_SPECIES];   // bq = beta_s q_s
+    float bqf[GX_MAX_SPECIES];
+};
+
+// Record value of species s, row k, cell: the push pass's record plus, after a
+// push, the arrivals pass's record (FP32, as the particle kernels wrote them).
+struct Recs {
+    const float *a, *b;       // [S][112][N]; b may be null
+    int64_t N;
+    __device__ __forceinline__ float get(int s, int k, int64_t cell) const {
+        const size_t o = ((size_t)s * Rec<2>::SIZE + k) * N + cell;
+        return b ? a[o] + b[o] : a[o];
+    }
 };
 
 // rho, mass density, momentum and the raw plasma velocity at every node from
-// the per-species cell records of the 4 cells around it.
-__global__ void k_assemble_bulk(G2 g, SpecK sk, const float *__restrict__ rec, double dV, double *rho,
-                                double *rho_m, double *P, double *u) {
+// the per-species cell records of the 4 cells around it.  The cell sums of
+// one species are FP32 (the records are FP32 partial sums); species are
+// combined in FP64.
+__global__ void k_assemble_bulk(G2 g, SpecK sk, Recs R, double inv_dV, double *rho, double *rho_m, double *P,
+                                double *u) {
     const int64_t N = g.N();
     GRID_LOOP(q, N) {
         const int i = (int)(q % g.nx), j = (int)(q / g.nx);
+        int64_t cell[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) cell[a] = g.id(i - (a & 1), j - (a >> 1));   // corner a of that cell is this node
         double r = 0, rm = 0, p[3] = {0, 0, 0};
         for (int s = 0; s < sk.ns; ++s) {
-            const float *rs = rec + (size_t)s * Rec<2>::SIZE * N;
-            double w = 0, mv[3] = {0, 0, 0};
+            float w = 0.f, mv[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-            for (int cy = -1; cy <= 0; ++cy)
+            for (int a = 0; a < 4; ++a) {
+                w += R.get(s, Rec<2>::RHO + a, cell[a]);
 #pragma unroll
-                for (int cx = -1; cx <= 0; ++cx) {
-                    const int64_t cell = g.id(i + cx, j + cy);
-                    const int a = (-cx) + 2 * (-cy);
-                    w += rs[(Rec<2>::RHO + a) * N + cell];
+                for (int k = 0; k < 3; ++k) mv[k] += R.get(s, Rec<2>::MV + 3 * a + k, cell[a]);
+            }
+            r += sk.q[s] * (double)w;
+            rm += sk.m[s] * (double)w;
 #pragma unroll
-                    for (int k = 0; k < 3; ++k) mv[k] += rs[(Rec<2>::MV + 3 * a + k) * N + cell];
-                }
-            r += sk.q[s] * w;
-            rm += sk.m[s] * w;
-#pragma unroll
-            for (int k = 0; k < 3; ++k) p[k] += sk.m[s] * mv[k];
+            for (int k = 0; k < 3; ++k) p[k] += sk.m[s] * (double)mv[k];
         }
-        rho[q] = r / dV;
+        rho[q] = r * inv_dV;
         rho_m[q] = rm;
+        const double irm = rm != 0.0 ? 1.0 / rm : 0.0;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             P[k * N + q] = p[k];
-            u[k * N + q] = rm != 0.0 ? p[k] / rm : 0.0;
+            u[k * N + q] = p[k] * irm;
         }
     }
 }
@@ -142,82 +155,89 @@ __global__ void k_filter_fused(G2 g, const double *__restrict__ in, double *out,
     }
 }
 
-// The comoving current (Sec. 2.1, Eq. 34) and the FP64 rows of the mass
-// matrix (Eq. 33).  The particle kernels accumulate alpha (v - u_ref) with a
-// reference velocity u_ref (the bulk velocity of the previous deposit); the
-// exact correction to the smoothed u of this deposit is
-//   sum_p q alpha (u - u_ref)(x_p) W_pg = sum_g' M0_gg' (u - u_ref)_g',
-// with M0 the mass matrix without beta, so
-//   J_C = (1/dV) [sum_p q alpha (v - u_ref) W - sum_g' M0 (u - u_ref)].
-// With the comoving current off, u_ref = 0 and the correction is skipped.
-__global__ void k_assemble_main(G2 g, SpecK sk, const float *__restrict__ rec, double dV, int comoving,
-                                const double *__restrict__ u, const double *__restrict__ uref, double *J,
-                                double *M) {
+// Comoving current and mass-matrix rows at every node (Sec. 2.1, Eq. 33-35).
+// J: the records hold sum w alpha (v - u_ref); the comoving current subtracts
+// the plasma velocity u of this deposit, so the difference u - u_ref is
+// removed through the mass-matrix sums (exactly: alpha is linear in the
+// velocity), J_C = sum_s q_s [sum w alpha (v - u_ref) W - sum_b M_b (u - u_ref)_b].
+// M: block o = (ox,oy) of node g collects every cell holding both g and g + o.
+// Along x: ox = 0 -> cells -1 (pair class 2) and 0 (class 0); ox = +1 -> cell 0
+// (class 1); ox = -1 -> cell -1 (class 1); the same in y.  Cell sums of one
+// species are FP32 (the records are FP32 partial sums); the current's species
+// are combined in FP64, the mass matrix (all species add with beta_s q_s > 0)
+// in FP32 and stored as FP64.
+__global__ void k_assemble_main(G2 g, SpecK sk, Recs R, double inv_dV, int comoving, const double *__restrict__ u,
+                                const double *__restrict__ uref, double *J, double *M) {
     const int64_t N = g.N();
     GRID_LOOP(q, N) {
         const int i = (int)(q % g.nx), j = (int)(q / g.nx);
         double jc[3] = {0, 0, 0};
-        for (int cy = -1; cy <= 0; ++cy)
-            for (int cx = -1; cx <= 0; ++cx) {
-                const int64_t cell = g.id(i + cx, j + cy);
-                const int ax = -cx, ay = -cy, a = ax + 2 * ay;
-                double du[4][3];
-                if (comoving) {
+        float du[3][3][3];          // (u - u_ref) at the 3x3 nodes around q: [dy+1][dx+1][k]
+        if (comoving) {
 #pragma unroll
-                    for (int b = 0; b < 4; ++b) {
-                        const int64_t nb = g.id(i + cx + (b & 1), j + cy + (b >> 1));
+            for (int dy = -1; dy <= 1; ++dy)
 #pragma unroll
-                        for (int k = 0; k < 3; ++k) du[b][k] = u[k * N + nb] - uref[k * N + nb];
-                    }
+                for (int dx = -1; dx <= 1; ++dx) {
+                    const int64_t nb = g.id(i + dx, j + dy);
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) du[dy + 1][dx + 1][k] = (float)(u[k * N + nb] - uref[k * N + nb]);
                 }
-                for (int s = 0; s < sk.ns; ++s) {
-                    const float *rs = rec + (size_t)s * Rec<2>::SIZE * N + cell;
-                    double js[3];
+        }
+        for (int s = 0; s < sk.ns; ++s) {
+            float js[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-                    for (int k = 0; k < 3; ++k) js[k] = rs[(Rec<2>::J + 3 * a + k) * N];
+            for (int cy = -1; cy <= 0; ++cy)
+#pragma unroll
+                for (int cx = -1; cx <= 0; ++cx) {
+                    const int64_t cell = g.id(i + cx, j + cy);
+                    const int ax = -cx, ay = -cy, a = ax + 2 * ay;
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) js[k] += R.get(s, Rec<2>::J + 3 * a + k, cell);
                     if (comoving) {
 #pragma unroll
                         for (int b = 0; b < 4; ++b) {
                             const int bx = b & 1, by = b >> 1;
                             const int jx = (ax == bx) ? 2 * ax : 1, jy = (ay == by) ? 2 * ay : 1;
-                            const float *mp = rs + (size_t)(Rec<2>::M + 9 * (jx + 3 * jy)) * N;
+                            const int mrow = Rec<2>::M + 9 * (jx + 3 * jy);
+                            const float *d = du[cy + by + 1][cx + bx + 1];
 #pragma unroll
                             for (int r = 0; r < 3; ++r)
-                                js[r] -= (double)mp[(3 * r) * N] * du[b][0] + (double)mp[(3 * r + 1) * N] * du[b][1] +
-                                         (double)mp[(3 * r + 2) * N] * du[b][2];
+                                js[r] -= R.get(s, mrow + 3 * r, cell) * d[0] + R.get(s, mrow + 3 * r + 1, cell) * d[1] +
+                                         R.get(s, mrow + 3 * r + 2, cell) * d[2];
                         }
                     }
-#pragma unroll
-                    for (int k = 0; k < 3; ++k) jc[k] += sk.q[s] * js[k];
                 }
-            }
 #pragma unroll
-        for (int k = 0; k < 3; ++k) J[k * N + q] = jc[k] / dV;
-        // mass-matrix row: block o = (ox,oy) collects every cell holding both g
-        // and g + o.  Along x: ox = 0 -> cells -1 (pair class 2) and 0 (class 0);
-        // ox = +1 -> cell 0 (class 1); ox = -1 -> cell -1 (class 1).  Same in y.
+            for (int k = 0; k < 3; ++k) jc[k] += sk.q[s] * (double)js[k];
+        }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) J[k * N + q] = jc[k] * inv_dV;
+#pragma unroll
         for (int o = 0; o < 9; ++o) {
             const int ox = o % 3 - 1, oy = o / 3 - 1;
-            double blk[9];
+            float blk[9];
 #pragma unroll
-            for (int e = 0; e < 9; ++e) blk[e] = 0.0;
+            for (int e = 0; e < 9; ++e) blk[e] = 0.f;
             const int ncx = ox == 0 ? 2 : 1, ncy = oy == 0 ? 2 : 1;
+#pragma unroll
             for (int tyy = 0; tyy < ncy; ++tyy) {
                 const int cy = oy == 0 ? -tyy : (oy > 0 ? 0 : -1);
                 const int jy = oy == 0 ? (cy == -1 ? 2 : 0) : 1;
+#pragma unroll
                 for (int txx = 0; txx < ncx; ++txx) {
                     const int cx = ox == 0 ? -txx : (ox > 0 ? 0 : -1);
                     const int jx = ox == 0 ? (cx == -1 ? 2 : 0) : 1;
                     const int64_t cell = g.id(i + cx, j + cy);
+                    const int mrow = Rec<2>::M + 9 * (jx + 3 * jy);
                     for (int s = 0; s < sk.ns; ++s) {
-                        const float *mp = rec + (size_t)s * Rec<2>::SIZE * N + (size_t)(Rec<2>::M + 9 * (jx + 3 * jy)) * N + cell;
+                        const float f = sk.bqf[s];
 #pragma unroll
-                        for (int e = 0; e < 9; ++e) blk[e] += sk.bq[s] * (double)mp[(size_t)e * N];
+                        for (int e = 0; e < 9; ++e) blk[e] = fmaf(f, R.get(s, mrow + e, cell), blk[e]);
                     }
                 }
             }
 #pragma unroll
-            for (int e = 0; e < 9; ++e) M[(size_t)(o * 9 + e) * N + q] = blk[e];
+            for (int e = 0; e < 9; ++e) M[(size_t)(o * 9 + e) * N + q] = (double)blk[e];
         }
     }
 }
@@ -571,6 +591,7 @@ SpecK speck(const gx_ctx *c) {
         sk.q[s] = c->sp[s].q;
         sk.m[s] = c->sp[s].m;
         sk.bq[s] = c->sp[s].q * c->cfg.dt / (2.0 * c->sp[s].m) * c->sp[s].q;
+        sk.bqf[s] = (float)sk.bq[s];
     }
     return sk;
 }
@@ -622,11 +643,12 @@ int gx_node_fields(gx_ctx *c, const double *Eth, const double *Bcur, float4 *out
 int gx_assemble_moments(gx_ctx *c, cudaStream_t st) {
     const G2 g = geom(c);
     const SpecK sk = speck(c);
-    k_assemble_bulk<<<blocks_for(c->N), kB, 0, st>>>(g, sk, c->rec, c->dV, c->rho, c->rho_m, c->P, c->u);
+    const Recs R{c->rec, c->rec2_valid ? c->rec2 : nullptr, c->N};
+    k_assemble_bulk<<<blocks_for(c->N), kB, 0, st>>>(g, sk, R, 1.0 / c->dV, c->rho, c->rho_m, c->P, c->u);
     GX_LAUNCHED(c);
     int rc = filter_passes(c, c->u, c->cfg.nsmooth_u, true, st);
     if (rc) return rc;
-    k_assemble_main<<<blocks_for(c->N), kB, 0, st>>>(g, sk, c->rec, c->dV, c->cfg.comoving, c->u, c->uref64, c->J,
+    k_assemble_main<<<blocks_for(c->N), kB, 0, st>>>(g, sk, R, 1.0 / c->dV, c->cfg.comoving, c->u, c->uref64, c->J,
                                                        c->M);
     GX_LAUNCHED(c);
     rc = filter_passes(c, c->J, c->cfg.ns_j, false, st);

@@ -4,15 +4,16 @@
 //   * fields: FP64, component-major [3][N] with N = nx ny nz; E at nodes, B at
 //     cell centres (collocated staggered mesh, Sec. 1.1 of the paper);
 //   * particles: per species, cell bins of fixed capacity `cap` (a multiple of
-//     32).  Bin c holds cnt[c] particles in slots [c*cap, c*cap + cnt[c]) of
-//     SoA FP32 arrays: cell-local offsets ox, oy (, oz) in [0,1), velocities
-//     vx, vy, vz, weight w (and an optional int32 id).  Two copies (A, B): the
-//     push reads A and writes B, then they swap;
+//     64) in SoA FP32 arrays: cell-local offsets ox, oy in [0,1), velocities
+//     vx, vy, vz, weight w (and an optional int32 id).  A bin holds a bottom
+//     and a top segment (see bin_front / bin_back).  Two copies: the push
+//     reads one and writes the other, then they swap;
 //   * deposit records: per species and cell, FP32 partial sums over the cell's
-//     particles (see REC_* below), written by the particle kernels and folded
-//     into FP64 node moments by the grid kernels;
-//   * mass matrix: FP64 node rows M[g][o][3][3], o over the 3^d neighbour
-//     offsets (9 in 2D, 27 in 3D).
+//     particles (see Rec below), [species][112][N]; after a push a second set
+//     holds the sums over the particles that arrived in each cell; the grid
+//     kernels fold both into the FP64 node moments;
+//   * mass matrix: FP64 rows [o*9 + e][N], o over the 9 neighbour offsets
+//     (o = (ox+1) + 3 (oy+1)), e the alpha component.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -107,7 +108,9 @@ struct gx_ctx {
 
     // deposit records
     int rec_size = 112;
-    float *rec = nullptr;                       // [S][N][rec_size]
+    float *rec = nullptr;                       // [S][112][N]: the deposit pass of each cell's bin
+    float *rec2 = nullptr;                      // [S][112][N]: particles that arrived during the push
+    int rec2_valid = 0;                         // rec2 belongs to the current deposit
 
     // node moments (FP64)
     double *rho = nullptr, *rho_m = nullptr;    // [N]
@@ -141,8 +144,10 @@ struct gx_ctx {
     DevFlags *dflags = nullptr;
     DevFlags *hflags = nullptr;                 // pinned
     std::vector<cudaEvent_t> evpool;
-    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> evpend[3];   // push, moments, solve
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> evpend[4];   // push, moments, solve, push kernel
     double t_push = 0, t_mom = 0, t_solve = 0;
+    double t_pdk = 0;                           // the fused push kernel's launches alone
+    int64_t n_pdk = 0;
     int64_t launches = 0;
 };
 
@@ -170,6 +175,12 @@ __host__ __device__ inline int wrap_idx(int i, int n) {
     i %= n;
     return i < 0 ? i + n : i;
 }
+
+// event timing without host round trips (gx_capi.cu): an interval between two
+// events recorded on the launching stream, resolved later into a category's sum
+enum { GX_T_PUSH = 0, GX_T_MOM = 1, GX_T_SOLVE = 2, GX_T_PDK = 3 };
+cudaEvent_t gx_ev_get(gx_ctx *c);
+void gx_ev_push(gx_ctx *c, int cat, cudaEvent_t a, cudaEvent_t b);
 
 // ------------------------------------------------ entry points per module
 // particles (gx_particles.cu)

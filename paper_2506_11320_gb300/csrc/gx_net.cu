@@ -3,11 +3,13 @@
 //
 // Network N: four 3x3 convolutions, channels 3 -> 32 -> 32 -> 32 -> 3, ReLU
 // between them, on the 2D node grid (H = ny rows, W = nx columns), BF16 weights
-// and activations with FP32 accumulation.  Inside FGMRES it is applied with a
-// skip connection, z = r + s N(r / s), s = ||r||_2 / sqrt(3 N), periodic
-// padding: the field operator is the identity plus terms of a few per cent at
-// the usual time steps, so the network only has to learn the small remainder
-// A^-1 r - r, and its BF16 rounding error is relative to that remainder.
+// and activations with FP32 accumulation.  Inside FGMRES it corrects the 3x3
+// block-Jacobi preconditioner D^-1 of the field operator A:
+//     z = D^-1 r + s N(r / s),   s = ||r||_2 / sqrt(3 N),  periodic padding.
+// D^-1 carries what varies from node to node (the plasma's mass-matrix block,
+// which the network, seeing only r, could not know); the network learns the
+// translation-invariant remainder A^-1 r - D^-1 r, a few per cent of z at the
+// usual time steps, so its BF16 rounding error is relative to that remainder.
 //
 // Kernels (all on the tensor cores through mma.sync m16n8k16 BF16 -> FP32):
 //   * k_conv: implicit-GEMM convolution, M = 16 pixels of a row, N = output
@@ -347,12 +349,17 @@ __global__ void k_pack_input(const T *src, int64_t HW, bf16 *dst, const double *
     }
 }
 
-// z = r + s y (the skip connection of the preconditioner)
-__global__ void k_unpack_output(const float *y, int64_t HW, const double *r, double *z, const double *sumsq) {
+// z = D^-1 r + s y, jd = the 3x3 inverse diagonal blocks [N][9]
+__global__ void k_unpack_output(const float *y, int64_t HW, const double *jd, const double *r, double *z,
+                                const double *sumsq) {
     const double s = sqrt(*sumsq / (3.0 * HW));
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < HW; p += (int64_t)gridDim.x * blockDim.x)
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < HW; p += (int64_t)gridDim.x * blockDim.x) {
+        const double *o = jd + (size_t)p * 9;
+        const double r0 = r[p], r1 = r[HW + p], r2 = r[2 * HW + p];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) z[c * HW + p] = r[c * HW + p] + s * (double)y[p * 8 + c];
+        for (int c = 0; c < 3; ++c)
+            z[c * HW + p] = o[3 * c] * r0 + o[3 * c + 1] * r1 + o[3 * c + 2] * r2 + s * (double)y[p * 8 + c];
+    }
 }
 
 __global__ void k_sumsq(const double *x, int64_t n, double *out) {
@@ -364,8 +371,8 @@ __global__ void k_sumsq(const double *x, int64_t n, double *out) {
 }
 
 // training crops: for crop b, input = r / s_b on a (C+8)^2 window (4-pixel halo,
-// periodic in the source field) and target = (e - r) / s_b on the central C^2
-// (the network learns the remainder of the skip connection), with
+// periodic in the source field) and target = t / s_b on the central C^2, where
+// the pair stores t = e - D^-1 r (the remainder the network learns), with
 // s_b = ||r||_2 / sqrt(3 N) over the whole field, the scale the solver uses
 struct CropSpec {
     int pair, y0, x0, pad;
@@ -408,8 +415,7 @@ __global__ void k_crop_gather(const float *pairs, int64_t N, int nx, int ny, con
         reinterpret_cast<uint4 *>(d)[1] = reinterpret_cast<uint4 *>(v)[1];
         const bool inner = yy >= 4 && yy < 4 + C && xx >= 4 && xx < 4 + C;
 #pragma unroll
-        for (int c = 0; c < 3; ++c)
-            target[((int64_t)b * S * S + t) * 3 + c] = inner ? (e[c * N + q] - r[c * N + q]) * inv : 0.f;
+        for (int c = 0; c < 3; ++c) target[((int64_t)b * S * S + t) * 3 + c] = inner ? e[c * N + q] * inv : 0.f;
     }
 }
 
@@ -449,19 +455,33 @@ __global__ void k_chw3_to_target(const float *t, int64_t HW, float *out) {
         for (int c = 0; c < 3; ++c) out[p * 3 + c] = t[c * HW + p];
 }
 
-// pair slot [2][3][N]: r0 (when r0 is given) or e = eth - en (otherwise)
-__global__ void k_store_pair(const double *r0, const double *eth, const double *en, int64_t n3, float *dst) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x) {
-        if (r0) dst[i] = (float)r0[i];
-        else dst[n3 + i] = (float)(eth[i] - en[i]);
+// pair slot [2][3][N] = (r, t) with t = e - D^-1 r, jd = [N][9] inverse blocks.
+// k_store_r: r (FP64) -> slot; k_store_t: t from e = eth - en and the slot's
+// FP32 r; k_store_rt: both from FP64 r and e.
+__global__ void k_store_r(const double *r, int64_t n3, float *dst) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = (float)r[i];
+}
+__global__ void k_store_t(const double *jd, const double *eth, const double *en, int64_t N, float *dst) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < N; q += (int64_t)gridDim.x * blockDim.x) {
+        const double *o = jd + (size_t)q * 9;
+        const double r0 = dst[q], r1 = dst[N + q], r2 = dst[2 * N + q];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const double e = eth[c * N + q] - en[c * N + q];
+            dst[3 * N + c * N + q] = (float)(e - (o[3 * c] * r0 + o[3 * c + 1] * r1 + o[3 * c + 2] * r2));
+        }
     }
 }
-
-// pair slot [2][3][N] = (r, e), both given
-__global__ void k_store_rv(const double *r, const double *e, int64_t n3, float *dst) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x) {
-        dst[i] = (float)r[i];
-        dst[n3 + i] = (float)e[i];
+__global__ void k_store_rt(const double *jd, const double *r, const double *e, int64_t N, float *dst) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < N; q += (int64_t)gridDim.x * blockDim.x) {
+        const double *o = jd + (size_t)q * 9;
+        const double r0 = r[q], r1 = r[N + q], r2 = r[2 * N + q];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            dst[c * N + q] = (float)r[c * N + q];
+            dst[3 * N + c * N + q] = (float)(e[c * N + q] - (o[3 * c] * r0 + o[3 * c + 1] * r1 + o[3 * c + 2] * r2));
+        }
     }
 }
 
@@ -603,7 +623,8 @@ static int net_backward(gx_ctx *c, int B, int H, int W, int periodic, float grad
 }
 
 // ------------------------------------------------------------ solver hooks
-// z = r + s N(r / s), s = ||r|| / sqrt(3 N): FP64 [3][N] in and out
+// z = D^-1 r + s N(r / s), s = ||r|| / sqrt(3 N): FP64 [3][N] in and out; the
+// block-Jacobi inverse c->jdiag must be current
 int gx_net_apply(gx_ctx *c, const double *r, double *z, cudaStream_t st) {
     if (c->dim != 2) { c->err = "the learned preconditioner is 2D"; return GX_ENOTIMPL; }
     int rc = net_alloc(c);
@@ -618,7 +639,7 @@ int gx_net_apply(gx_ctx *c, const double *r, double *z, cudaStream_t st) {
     k_pack_input<double><<<nblk(c->N), 256, 0, st>>>(r, c->N, n->x0, n->dsum, 1.0);
     GX_LAUNCHED(c);
     if ((rc = net_forward(c, 1, H, W, 1, st))) return rc;
-    k_unpack_output<<<nblk(c->N), 256, 0, st>>>(n->y, c->N, r, z, n->dsum);
+    k_unpack_output<<<nblk(c->N), 256, 0, st>>>(n->y, c->N, c->jdiag, r, z, n->dsum);
     GX_LAUNCHED(c);
     return GX_OK;
 }
@@ -635,8 +656,13 @@ constexpr int kKrylovPairs = 6;
 int gx_net_pair_begin(gx_ctx *c, const double *r0, cudaStream_t st) {
     Net *n = c->net;
     if (!n || !n->collect || n->cap_pairs < 1) return GX_OK;
+    // the targets need D^-1 of this solve's operator
+    if (c->cfg.precond == GX_PRECOND_NONE) {
+        int rc = gx_build_jacobi(c, st);
+        if (rc) return rc;
+    }
     float *dst = n->pairs + (size_t)n->next_pair * 6 * c->N;
-    k_store_pair<<<nblk(3 * c->N), 256, 0, st>>>(r0, nullptr, nullptr, 3 * c->N, dst);
+    k_store_r<<<nblk(3 * c->N), 256, 0, st>>>(r0, 3 * c->N, dst);
     GX_LAUNCHED(c);
     n->pending_pair = 1;
     return GX_OK;
@@ -654,7 +680,7 @@ int gx_net_pair_end(gx_ctx *c, int converged, int nbasis, cudaStream_t st) {
     if (!converged) return GX_OK;
     const int64_t n3 = 3 * c->N;
     float *dst = n->pairs + (size_t)n->next_pair * 6 * c->N;
-    k_store_pair<<<nblk(n3), 256, 0, st>>>(nullptr, c->Eth, c->E, n3, dst);
+    k_store_t<<<nblk(c->N), 256, 0, st>>>(c->jdiag, c->Eth, c->E, c->N, dst);
     GX_LAUNCHED(c);
     advance_slot(n);
     const int nv = std::min(nbasis, kKrylovPairs);
@@ -663,7 +689,7 @@ int gx_net_pair_end(gx_ctx *c, int converged, int nbasis, cudaStream_t st) {
         int rc = gx_apply_A(c, v, c->w, st);
         if (rc) return rc;
         dst = n->pairs + (size_t)n->next_pair * 6 * c->N;
-        k_store_rv<<<nblk(n3), 256, 0, st>>>(c->w, v, n3, dst);
+        k_store_rt<<<nblk(c->N), 256, 0, st>>>(c->jdiag, c->w, v, c->N, dst);
         GX_LAUNCHED(c);
         advance_slot(n);
     }

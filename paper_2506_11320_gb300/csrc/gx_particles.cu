@@ -12,9 +12,10 @@
 //      take consecutive slots at the bottom of its new bin (one atomic per
 //      64-particle chunk), particles that leave take slots at the top of their
 //      new cell's bin (see bin_front / bin_back).
-// k_arrivals then deposits the particles that arrived in each cell (the top
-// segment, contiguous) into that cell's record.  k_pd<false> deposits the
-// current state without moving it.
+// k_pd<false> deposits without moving: the whole state (the deposit before
+// the first step), or, right after the push, only the particles that arrived
+// in each cell (the back segments of the new bins) into a second set of
+// records that the grid kernels add to the first.
 //
 // Work decomposition (GB300-first): a persistent grid, one CTA of 8 warps per
 // SM; each warp is split into 4 groups of 8 lanes and a group owns one cell at
@@ -63,13 +64,13 @@ struct P2 {
     const float4 *dB, *dU;       // deposit: B for alpha, reference velocity u_ref
     float *rec;                  // [N][112] for this species
     DevFlags *flags;
+    int arrivals;                // deposit only the back segments (the particles that arrived)
 };
 
 size_t pd_smem_bytes() {
     return 512 + (size_t)kGroups * 2 * kMaxF * kChunk * sizeof(float) + (size_t)kGroups * kChunk * sizeof(int) +
            (size_t)8 * kScr * sizeof(float);
 }
-size_t arr_smem_bytes() { return (size_t)8 * kScr * sizeof(float); }
 
 // ------------------------------------------------------------ PTX helpers
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -219,6 +220,11 @@ __device__ __forceinline__ int clamp_word(int w, int cap) {
     f = min(f, cap - b);
     return f | (b << 16);
 }
+// the segments a pass visits: the whole bin, or only the arrivals (back)
+__device__ __forceinline__ int seg_word(int w, int cap, int arrivals_only) {
+    const int c = clamp_word(w, cap);
+    return arrivals_only ? (int)((unsigned)c & 0xffff0000u) : c;
+}
 
 // ------------------------------------------------------------ fused kernel
 template <bool PUSH>
@@ -237,7 +243,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_pd(P2 p) {
     int *mycode = codes + g * kChunk;
     uint64_t *mybar = bars + 2 * g;
     float *scr = scr_all + (size_t)warp * kScr;
-    const uint32_t tx_bytes = (uint32_t)(p.nf * kChunk * sizeof(float));
 
     if (lig == 0) {
         mbar_init(&mybar[0], 1);
@@ -254,7 +259,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_pd(P2 p) {
         while (ib < p.nbatch) {
             if (inch < 0) {
                 const int64_t cell = (int64_t)ib * kGroups + g;
-                iword = cell < p.N ? clamp_word(p.cnt_in[cell], p.cap) : 0;
+                iword = cell < p.N ? seg_word(p.cnt_in[cell], p.cap, p.arrivals) : 0;
                 inch = bin_chunks(iword);
             }
             if (ich < inch) return true;
@@ -264,14 +269,24 @@ __global__ void __launch_bounds__(kThreads, 1) k_pd(P2 p) {
         }
         return false;
     };
+    // stream chunk `ich` of the cell: only the slots of its own segment,
+    // widened to 16-byte boundaries (4 slots), into the same positions of the
+    // staging row
     auto issue = [&]() {
         const int slot = issued & 1;
         const int64_t cell = (int64_t)ib * kGroups + g;
-        const size_t off = (size_t)cell * p.cap + chunk_base(ich, bin_front(iword), p.cap);
+        const int fr = bin_front(iword), sbase = chunk_base(ich, fr, p.cap);
+        int lo = 0, hi = kChunk;
+        if (ich < (fr + kChunk - 1) / kChunk) hi = min(kChunk, fr - sbase);
+        else lo = max(0, p.cap - bin_back(iword) - sbase);
+        lo &= ~3;
+        hi = (hi + 3) & ~3;
+        const uint32_t bytes = (uint32_t)((hi - lo) * sizeof(float));
+        const size_t off = (size_t)cell * p.cap + sbase + lo;
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_expect_tx(&mybar[slot], tx_bytes);
+        mbar_expect_tx(&mybar[slot], bytes * (uint32_t)p.nf);
         for (int f = 0; f < p.nf; ++f)
-            bulk_g2s(mybuf + (size_t)(slot * kMaxF + f) * kChunk, p.in[f] + off, kChunk * sizeof(float), &mybar[slot]);
+            bulk_g2s(mybuf + (size_t)(slot * kMaxF + f) * kChunk + lo, p.in[f] + off, bytes, &mybar[slot]);
         ++issued;
         ++ich;
     };
@@ -284,7 +299,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_pd(P2 p) {
     for (int b = blockIdx.x; b < p.nbatch; b += gridDim.x) {
         const int64_t cell = (int64_t)b * kGroups + g;
         const bool valid = cell < p.N;
-        const int word = valid ? clamp_word(p.cnt_in[cell], p.cap) : 0;
+        const int word = valid ? seg_word(p.cnt_in[cell], p.cap, p.arrivals) : 0;
         const int nch = bin_chunks(word);
         const int nchf = (bin_front(word) + kChunk - 1) / kChunk;
         const int wmax = __reduce_max_sync(kFull, nch);
@@ -439,39 +454,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_pd(P2 p) {
         // drain this group's copies still in flight before the CTA exits
         if (lig == 0)
             for (int k = cons; k < issued; ++k) mbar_wait_bounded(&mybar[k & 1], (uint32_t)((k >> 1) & 1));
-    }
-}
-
-// Deposit the particles that arrived in a cell during the push (the top
-// segment of its new bin, contiguous) into the cell's record.
-__global__ void __launch_bounds__(kThreads, 1) k_arrivals(P2 p) {
-    extern __shared__ __align__(128) unsigned char smem[];
-    float *scr_all = reinterpret_cast<float *>(smem);                          // [8][kScr]
-    const int tid = threadIdx.x;
-    const int lane = tid & 31, warp = tid >> 5;
-    const int g = tid / kGroup, lig = tid % kGroup;
-    const int gshift = (lane / kGroup) * kGroup;
-    float *scr = scr_all + (size_t)warp * kScr;
-    for (int b = blockIdx.x; b < p.nbatch; b += gridDim.x) {
-        const int64_t cell = (int64_t)b * kGroups + g;
-        const bool valid = cell < p.N;
-        const int nb = valid ? bin_back(clamp_word(p.cnt_out[cell], p.cap)) : 0;
-        if (!__any_sync(kFull, nb > 0)) continue;
-        const int ci = valid ? (int)(cell % p.nx) : 0, cj = valid ? (int)(cell / p.nx) : 0;
-        int64_t nd[4];
-        corner_nodes(ci, cj, p.nx, p.ny, nd);
-        float4 cB[4], cU[4];
-#pragma unroll
-        for (int a = 0; a < 4; ++a) { cB[a] = __ldg(p.dB + nd[a]); cU[a] = __ldg(p.dU + nd[a]); }
-        RegAcc acc;
-        acc.zero();
-        const size_t top = (size_t)cell * p.cap + p.cap - nb;
-        for (int i = lig; i < nb; i += kGroup) {
-            const size_t s = top + i;
-            deposit_one(acc, p.out[SF_OX][s], p.out[SF_OY][s], p.out[SF_VX][s], p.out[SF_VY][s], p.out[SF_VZ][s],
-                        p.out[SF_W][s], cB, cU, p.bc);
-        }
-        group_reduce_store(acc, scr, lane, lig, gshift, p.rec + cell, p.N, true, valid && nb > 0);
     }
 }
 
@@ -678,7 +660,6 @@ static int launch_pd(gx_ctx *c, bool push, cudaStream_t st) {
     if (!configured) {
         GX_CHECK(c, cudaFuncSetAttribute(k_pd<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pd_smem_bytes()));
         GX_CHECK(c, cudaFuncSetAttribute(k_pd<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pd_smem_bytes()));
-        GX_CHECK(c, cudaFuncSetAttribute(k_arrivals, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)arr_smem_bytes()));
         configured = true;
     }
     int dev = 0, nsm = 152;
@@ -711,9 +692,23 @@ static int launch_pd(gx_ctx *c, bool push, cudaStream_t st) {
         if (push) {
             p.mE = c->nE; p.mB = c->nB; p.dB = c->nBnext; p.dU = c->nUref;
             GX_CHECK(c, cudaMemsetAsync(S.cnt[nxt], 0, c->N * sizeof(int), st));
+            cudaEvent_t e0 = gx_ev_get(c), e1 = gx_ev_get(c);
+            GX_CHECK(c, cudaEventRecord(e0, st));
             k_pd<true><<<grid, kThreads, pd_smem_bytes(), st>>>(p);
             GX_LAUNCHED(c);
-            k_arrivals<<<grid, kThreads, arr_smem_bytes(), st>>>(p);
+            GX_CHECK(c, cudaEventRecord(e1, st));
+            gx_ev_push(c, GX_T_PDK, e0, e1);
+            c->n_pdk++;
+            // the particles that arrived in each cell: the same pipelined
+            // deposit over the back segments of the new bins, into the
+            // second set of records (every cell written, zero if none arrived)
+            P2 q = p;
+            q.arrivals = 1;
+            for (int f = 0; f < kMaxF; ++f) q.in[f] = p.out[f];
+            q.cnt_in = p.cnt_out;
+            q.mE = nullptr; q.mB = nullptr;
+            q.rec = c->rec2 + (size_t)s * c->N * Rec<2>::SIZE;
+            k_pd<false><<<grid, kThreads, pd_smem_bytes(), st>>>(q);
             GX_LAUNCHED(c);
         } else {
             p.mE = nullptr; p.mB = nullptr; p.dB = c->nB; p.dU = c->nUref;
@@ -721,6 +716,7 @@ static int launch_pd(gx_ctx *c, bool push, cudaStream_t st) {
             GX_LAUNCHED(c);
         }
     }
+    c->rec2_valid = push ? 1 : 0;
     if (push) {
         c->cur = nxt;
         GX_CHECK(c, cudaMemsetAsync(&c->dflags->maxcount, 0, sizeof(int), st));
