@@ -8,81 +8,338 @@
 // variant that stores the preconditioned vectors).  Orthogonalisation is
 // classical Gram-Schmidt applied twice; every inner product and norm is FP64.
 //
-// The iteration is driven from the device: the Krylov column index, the
-// Hessenberg matrix, the Givens rotations and the residual estimate live in a
-// device-side state; reductions finish in the last CTA to arrive (no memsets,
-// no host round trip); every kernel of an iteration returns at once when the
-// state says the cycle is done.  The host enqueues iterations in batches and
-// looks at the state only between batches and at restarts, so a solve costs a
-// few host synchronisations instead of one per iteration.  The true residual
-// ||b - A x|| / ||b|| is recomputed at every restart and decides convergence.
-#include "gx_internal.cuh"
+// GB300-first design: the whole solve is one cooperative persistent kernel.
+// Each thread owns a fixed set of nodes for every vector operation, so
+// node-local steps need no synchronisation; a grid-wide barrier separates the
+// steps that read other nodes (the matrix-vector product reads the 3x3
+// neighbourhood) or need a global sum.  Global sums: every CTA writes its
+// partial, and after the barrier every CTA adds all partials in the same
+// order, so all CTAs hold bit-identical sums and take identical decisions (the
+// Givens rotations, the convergence test) without another barrier.  An
+// Arnoldi step costs four barriers.  The true residual ||b - A x|| / ||b|| is
+// recomputed at every restart and decides convergence.  With the learned
+// preconditioner the kernel returns whenever it needs the next preconditioned
+// vector, which the network kernels produce between launches.
+#include <cooperative_groups.h>
+
+#include "gx_op.cuh"
+
+namespace cg = cooperative_groups;
 
 constexpr int kMaxM = 64;
 
 struct GmState {
     int j;             // current Krylov column
-    int done;          // the current cycle has ended
+    int done;          // the current cycle has ended (a restart is due)
     int finished;      // the solve has ended
     int conv;          // converged (true residual <= tol)
-    int total;         // matrix-vector products so far
+    int total;         // Arnoldi steps (matrix-vector products on Krylov vectors) so far
     int jend;          // last column of the ended cycle
     int breakdown;
     int pad;
-    unsigned cnt[4];   // last-CTA counters of the reductions
-    double bnorm, beta, relres, hn2, est;
-    double h[2][kMaxM + 2];
-    double H[(kMaxM + 1) * kMaxM];
-    double cs[kMaxM], sn[kMaxM], g[kMaxM + 1], y[kMaxM];
+    double bnorm, beta, relres, est;
+    double H[(kMaxM + 1) * kMaxM];     // rotated Hessenberg (upper triangular R), row-major [i][col]
+    double cs[kMaxM], sn[kMaxM], g[kMaxM + 1];
 };
 
 namespace {
 
 constexpr int kB = 256;
-constexpr int kRedBlocks = 152 * 2;
+constexpr int kWarps = kB / 32;
+constexpr int kMaxGrid = 152 * 8;
 constexpr int kPartStride = kMaxM + 2;
 
-inline int nblocks(int64_t n) {
-    int64_t b = (n + kB - 1) / kB;
-    return (int)std::max<int64_t>(1, std::min<int64_t>(b, kRedBlocks));
-}
+struct CoArgs {
+    OpArgs op;
+    const double *b;
+    double *x;          // solution (initial guess on entry)
+    double *V;          // Krylov basis [(m+1)][3N]
+    double *Z;          // preconditioned vectors [m][3N] (== V without a preconditioner)
+    double *w, *r;      // [3N]
+    const double *jd;   // block-Jacobi inverse [N][9], or null
+    GmState *st;
+    double *part;       // [2][kMaxGrid][kPartStride] CTA partial sums
+    int64_t N;
+    int m, maxit;
+    double tol;
+    int net;            // the preconditioned vectors come from the host between launches
+};
 
-__device__ __forceinline__ double block_sum(double v, double *sh) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+// every thread's node set: q = tid, tid + nthreads, ...
+#define NODE_LOOP(q) \
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < N; q += (int64_t)gridDim.x * blockDim.x)
+
+// CTA sums of up to 8 thread values -> dst[0..kk) (global partial row)
+__device__ __forceinline__ void cta_partials(double acc[8], int kk, double *sred, double *dst) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    __syncthreads();
-    if (lane == 0) sh[warp] = v;
-    __syncthreads();
-    double s = 0.0;
-    if (threadIdx.x < 32) {
-        s = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    }
-    return s;   // valid in thread 0
-}
-
-// true in every thread of the last CTA to finish (after its partials were
-// published); resets the counter for the next use
-__device__ __forceinline__ bool last_block(unsigned *counter) {
-    __shared__ bool last;
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const unsigned t = atomicAdd(counter, 1u);
-        last = (t == gridDim.x - 1);
-        if (last) *counter = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        double v = acc[i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) sred[warp * 8 + i] = v;
     }
     __syncthreads();
-    if (last) __threadfence();
-    return last;
-}
-
-// sum of the CTA partials of k values, by the last CTA
-__device__ __forceinline__ void finish_sums(const double *partial, int k, double *out) {
-    for (int i = threadIdx.x; i < k; i += blockDim.x) {
+    if (threadIdx.x < kk) {
         double s = 0.0;
-        for (int b = 0; b < (int)gridDim.x; ++b) s += partial[(size_t)b * kPartStride + i];
-        out[i] = s;
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) s += sred[w * 8 + threadIdx.x];
+        dst[threadIdx.x] = s;
+    }
+    __syncthreads();
+}
+
+// sum over all CTAs of partial rows [0, k) -> out (shared), same order in every CTA
+__device__ __forceinline__ void grid_sums(const double *part, int k, double *out) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = warp; i < k; i += kWarps) {
+        double s = 0.0;
+        for (int b = lane; b < (int)gridDim.x; b += 32) s += __ldcg(part + (size_t)b * kPartStride + i);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) out[i] = s;
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ double *prow(const CoArgs &a, int ph) {
+    return a.part + ((size_t)(ph & 1) * kMaxGrid + blockIdx.x) * kPartStride;
+}
+__device__ __forceinline__ const double *pbuf(const CoArgs &a, int ph) {
+    return a.part + (size_t)(ph & 1) * kMaxGrid * kPartStride;
+}
+
+// z = D^-1 v at node q (3x3 block)
+__device__ __forceinline__ void jacobi_node(const double *jd, const double *v, double *z, int64_t N, int64_t q) {
+    const double *o = jd + (size_t)q * 9;
+    const double x0 = v[q], x1 = v[N + q], x2 = v[2 * N + q];
+    z[q] = o[0] * x0 + o[1] * x1 + o[2] * x2;
+    z[N + q] = o[3] * x0 + o[4] * x1 + o[5] * x2;
+    z[2 * N + q] = o[6] * x0 + o[7] * x1 + o[8] * x2;
+}
+
+__global__ void __launch_bounds__(kB) k_fgmres(CoArgs a) {
+    cg::grid_group grid = cg::this_grid();
+    __shared__ double sred[kWarps * 8];
+    __shared__ double hs[2][kMaxM + 2];
+    __shared__ double s_cs[kMaxM], s_sn[kMaxM], s_g[kMaxM + 1], s_y[kMaxM];
+    __shared__ double s_scalar[2];
+    GmState *st = a.st;
+    const int64_t N = a.N, n = 3 * N;
+    const int m = a.m;
+    const bool flex = a.Z != a.V;
+    int j = st->j, done = st->done, total = st->total, breakdown = st->breakdown;
+    double bnorm = st->bnorm;
+    if (st->finished) return;
+    for (int i = threadIdx.x; i < kMaxM; i += blockDim.x) { s_cs[i] = st->cs[i]; s_sn[i] = st->sn[i]; }
+    for (int i = threadIdx.x; i <= kMaxM; i += blockDim.x) s_g[i] = st->g[i];
+    int ph = 0;
+    __syncthreads();
+    const bool writer = blockIdx.x == 0 && threadIdx.x == 0;
+
+    if (bnorm < 0.0) {                              // first launch of a solve: ||b||
+        double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        NODE_LOOP(q) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) acc[0] += a.b[c * N + q] * a.b[c * N + q];
+        }
+        cta_partials(acc, 1, sred, prow(a, ph));
+        grid.sync();
+        grid_sums(pbuf(a, ph), 1, s_scalar);
+        ++ph;
+        bnorm = sqrt(s_scalar[0]);
+        if (writer) st->bnorm = bnorm;
+    }
+
+    for (;;) {
+        if (done) {
+            // ---- restart: r = b - A x, beta = ||r||, convergence on the true residual
+            double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            NODE_LOOP(q) {
+                double ax[3];
+                gx_apply_A_node<true>(a.op, a.x, q, ax);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const double rv = a.b[c * N + q] - ax[c];
+                    a.r[c * N + q] = rv;
+                    acc[0] += rv * rv;
+                }
+            }
+            cta_partials(acc, 1, sred, prow(a, ph));
+            grid.sync();
+            grid_sums(pbuf(a, ph), 1, s_scalar);
+            ++ph;
+            const double beta = sqrt(s_scalar[0]);
+            const double relres = bnorm > 0.0 ? beta / bnorm : 0.0;
+            if (writer) { st->beta = beta; st->relres = relres; }
+            if (relres <= a.tol || total >= a.maxit || breakdown) {
+                if (writer) {
+                    st->finished = 1;
+                    st->conv = relres <= a.tol;
+                    st->done = 1;
+                    st->total = total;
+                }
+                return;
+            }
+            j = 0;
+            done = 0;
+            for (int i = threadIdx.x; i <= kMaxM; i += blockDim.x) s_g[i] = i == 0 ? beta : 0.0;
+            const double inv = 1.0 / beta;
+            NODE_LOOP(q) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) a.V[c * N + q] = a.r[c * N + q] * inv;
+                if (a.jd) jacobi_node(a.jd, a.V, a.Z, N, q);
+            }
+            __syncthreads();
+            if (writer) {
+                st->j = 0; st->done = 0; st->jend = -1;
+                for (int i = 0; i <= kMaxM; ++i) st->g[i] = i == 0 ? beta : 0.0;
+            }
+            if (a.net) return;                      // the network preconditions V_0 next
+            grid.sync();
+        }
+
+        // ---- Arnoldi step j: w = A z_j, two classical Gram-Schmidt passes
+        const int k = j + 1;
+        const double *zj = (flex ? a.Z : a.V) + (size_t)j * n;
+        // pass 1: w = A z_j, partial h0_i = V_i . w
+        for (int i0 = 0; i0 < k; i0 += 8) {
+            double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            NODE_LOOP(q) {
+                double wq[3];
+                if (i0 == 0) {
+                    gx_apply_A_node<true>(a.op, zj, q, wq);
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) a.w[c * N + q] = wq[c];
+                } else {
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) wq[c] = a.w[c * N + q];
+                }
+#pragma unroll
+                for (int ii = 0; ii < 8; ++ii)
+                    if (i0 + ii < k) {
+                        const double *vi = a.V + (size_t)(i0 + ii) * n;
+                        acc[ii] += vi[q] * wq[0] + vi[N + q] * wq[1] + vi[2 * N + q] * wq[2];
+                    }
+            }
+            cta_partials(acc, min(8, k - i0), sred, prow(a, ph) + i0);
+        }
+        grid.sync();
+        grid_sums(pbuf(a, ph), k, hs[0]);
+        ++ph;
+        // pass 2: w -= sum h0_i V_i, partial h1_i = V_i . w
+        NODE_LOOP(q) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                double v = a.w[c * N + q];
+                for (int i = 0; i < k; ++i) v -= hs[0][i] * a.V[(size_t)i * n + c * N + q];
+                a.w[c * N + q] = v;
+            }
+        }
+        for (int i0 = 0; i0 < k; i0 += 8) {
+            double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            NODE_LOOP(q) {
+                const double w0 = a.w[q], w1 = a.w[N + q], w2 = a.w[2 * N + q];
+#pragma unroll
+                for (int ii = 0; ii < 8; ++ii)
+                    if (i0 + ii < k) {
+                        const double *vi = a.V + (size_t)(i0 + ii) * n;
+                        acc[ii] += vi[q] * w0 + vi[N + q] * w1 + vi[2 * N + q] * w2;
+                    }
+            }
+            cta_partials(acc, min(8, k - i0), sred, prow(a, ph) + i0);
+        }
+        grid.sync();
+        grid_sums(pbuf(a, ph), k, hs[1]);
+        ++ph;
+        // pass 3: w -= sum h1_i V_i, partial ||w||^2
+        {
+            double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            NODE_LOOP(q) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    double v = a.w[c * N + q];
+                    for (int i = 0; i < k; ++i) v -= hs[1][i] * a.V[(size_t)i * n + c * N + q];
+                    a.w[c * N + q] = v;
+                    acc[0] += v * v;
+                }
+            }
+            cta_partials(acc, 1, sred, prow(a, ph));
+        }
+        grid.sync();
+        grid_sums(pbuf(a, ph), 1, s_scalar);
+        ++ph;
+        const double hn = sqrt(s_scalar[0]);
+        // Givens update of column j (identical in every CTA)
+        if (threadIdx.x == 0) {
+            double col[kMaxM + 1];
+            for (int i = 0; i <= j; ++i) col[i] = hs[0][i] + hs[1][i];
+            col[j + 1] = hn;
+            for (int i = 0; i < j; ++i) {
+                const double p = col[i], q2 = col[i + 1];
+                col[i] = s_cs[i] * p + s_sn[i] * q2;
+                col[i + 1] = -s_sn[i] * p + s_cs[i] * q2;
+            }
+            const double p = col[j], q2 = col[j + 1];
+            const double den = sqrt(p * p + q2 * q2);
+            const double cj = den == 0.0 ? 1.0 : p / den, sj = den == 0.0 ? 0.0 : q2 / den;
+            s_cs[j] = cj;
+            s_sn[j] = sj;
+            col[j] = cj * p + sj * q2;
+            s_g[j + 1] = -sj * s_g[j];
+            s_g[j] = cj * s_g[j];
+            s_scalar[1] = fabs(s_g[j + 1]) / bnorm;
+            if (blockIdx.x == 0) {
+                for (int i = 0; i <= j; ++i) st->H[i * kMaxM + j] = col[i];
+                st->cs[j] = cj;
+                st->sn[j] = sj;
+                st->g[j] = s_g[j];
+                st->g[j + 1] = s_g[j + 1];
+            }
+        }
+        __syncthreads();
+        total += 1;
+        if (hn == 0.0) breakdown = 1;
+        const double est = s_scalar[1];
+        const bool ended = est <= a.tol || total >= a.maxit || hn == 0.0 || j + 1 == m;
+        if (writer) { st->total = total; st->est = est; st->breakdown = breakdown; }
+        if (!ended) {
+            // V_{j+1} = w / hn (and its block-Jacobi image)
+            const double inv = 1.0 / hn;
+            double *v1 = a.V + (size_t)(j + 1) * n;
+            NODE_LOOP(q) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) v1[c * N + q] = a.w[c * N + q] * inv;
+                if (a.jd) jacobi_node(a.jd, v1, a.Z + (size_t)(j + 1) * n, N, q);
+            }
+            ++j;
+            if (writer) st->j = j;
+            if (a.net) return;                      // the network preconditions V_j next
+            grid.sync();
+            continue;
+        }
+        // ---- cycle end: y = R^-1 g, x += sum y_i z_i
+        grid.sync();                                // R columns written by CTA 0
+        if (threadIdx.x == 0) {
+            for (int i = j; i >= 0; --i) {
+                double s = s_g[i];
+                for (int kk = i + 1; kk <= j; ++kk) s -= __ldcg(&st->H[i * kMaxM + kk]) * s_y[kk];
+                s_y[i] = s / __ldcg(&st->H[i * kMaxM + i]);
+            }
+        }
+        __syncthreads();
+        const double *Zb = flex ? a.Z : a.V;
+        NODE_LOOP(q) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                double v = a.x[c * N + q];
+                for (int i = 0; i <= j; ++i) v += s_y[i] * Zb[(size_t)i * n + c * N + q];
+                a.x[c * N + q] = v;
+            }
+        }
+        done = 1;
+        if (writer) { st->done = 1; st->jend = j; }
+        grid.sync();                                // x complete before the restart reads it
     }
 }
 
@@ -90,305 +347,153 @@ __global__ void k_gm_init(GmState *st) {
     if (threadIdx.x == 0) {
         st->j = 0; st->done = 1; st->finished = 0; st->conv = 0; st->total = 0; st->jend = -1;
         st->breakdown = 0;
-        for (int i = 0; i < 4; ++i) st->cnt[i] = 0;
+        st->bnorm = -1.0;
+        for (int i = 0; i < kMaxM; ++i) { st->cs[i] = 1.0; st->sn[i] = 0.0; }
+        for (int i = 0; i <= kMaxM; ++i) st->g[i] = 0.0;
     }
 }
 
-// ||b||
-__global__ void k_gm_bnorm(const double *__restrict__ b, int64_t n, GmState *st, double *partial) {
-    __shared__ double sh[32];
-    double s = 0.0;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
-        s += b[t] * b[t];
-    s = block_sum(s, sh);
-    if (threadIdx.x == 0) partial[(size_t)blockIdx.x * kPartStride] = s;
-    if (last_block(&st->cnt[0]) && threadIdx.x == 0) {
-        double v = 0.0;
-        for (int k = 0; k < (int)gridDim.x; ++k) v += partial[(size_t)k * kPartStride];
-        st->bnorm = sqrt(v);
-    }
-}
-
-// r = b - Ax (r holds Ax on entry); start a cycle or finish the solve
-__global__ void k_gm_restart(const double *__restrict__ b, double *r, int64_t n, GmState *st, double *partial,
-                             double tol, int maxit) {
-    __shared__ double sh[32];
-    if (st->finished) return;
-    double s = 0.0;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
-        const double v = b[t] - r[t];
-        r[t] = v;
-        s += v * v;
-    }
-    s = block_sum(s, sh);
-    if (threadIdx.x == 0) partial[(size_t)blockIdx.x * kPartStride] = s;
-    if (last_block(&st->cnt[0]) && threadIdx.x == 0) {
-        double v = 0.0;
-        for (int k = 0; k < (int)gridDim.x; ++k) v += partial[(size_t)k * kPartStride];
-        const double beta = sqrt(v);
-        st->beta = beta;
-        st->relres = st->bnorm > 0.0 ? beta / st->bnorm : 0.0;
-        if (st->relres <= tol) { st->finished = 1; st->conv = 1; st->done = 1; }
-        else if (st->total >= maxit || st->breakdown) { st->finished = 1; st->done = 1; }
-        else {
-            st->done = 0;
-            st->j = 0;
-            st->jend = -1;
-            for (int i = 0; i <= kMaxM; ++i) st->g[i] = 0.0;
-            st->g[0] = beta;
-        }
-    }
-}
-
-// V_0 = r / beta
-__global__ void k_gm_v0(const double *__restrict__ r, double *V, int64_t n, const GmState *st) {
-    if (st->done) return;
-    const double inv = 1.0 / st->beta;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
-        V[t] = r[t] * inv;
-}
-
-// h[pass][i] = V_i . w for i <= j
-__global__ void k_gm_mdot(const double *__restrict__ V, int64_t n, const double *__restrict__ w, GmState *st,
-                          double *partial, int pass) {
-    __shared__ double sh[32];
-    if (st->done) return;
-    const int k = st->j + 1;
-    for (int i = 0; i < k; ++i) {
-        const double *v = V + (size_t)i * n;
-        double s = 0.0;
-        for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
-            s += v[t] * w[t];
-        s = block_sum(s, sh);
-        if (threadIdx.x == 0) partial[(size_t)blockIdx.x * kPartStride + i] = s;
-    }
-    if (last_block(&st->cnt[1])) finish_sums(partial, k, st->h[pass]);
-}
-
-// w -= sum_i h[pass][i] V_i; for the second pass also ||w||^2 and the update
-// of the Hessenberg column with Givens rotations (by the last CTA)
-__global__ void k_gm_axpy(const double *__restrict__ V, int64_t n, double *w, GmState *st, double *partial, int pass,
-                          int m, double tol, int maxit) {
-    __shared__ double sh[32];
-    __shared__ double coef[kMaxM + 2];
-    if (st->done) return;
-    const int k = st->j + 1;
-    for (int i = threadIdx.x; i < k; i += blockDim.x) coef[i] = st->h[pass][i];
-    __syncthreads();
-    double s = 0.0;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
-        double acc = w[t];
-        for (int i = 0; i < k; ++i) acc -= coef[i] * V[(size_t)i * n + t];
-        w[t] = acc;
-        s += acc * acc;
-    }
-    if (pass == 0) return;
-    s = block_sum(s, sh);
-    if (threadIdx.x == 0) partial[(size_t)blockIdx.x * kPartStride] = s;
-    if (last_block(&st->cnt[2]) && threadIdx.x == 0) {
-        double v = 0.0;
-        for (int b = 0; b < (int)gridDim.x; ++b) v += partial[(size_t)b * kPartStride];
-        const int j = st->j;
-        const double hn = sqrt(v);
-        st->hn2 = v;
-        double *H = st->H;
-        for (int i = 0; i <= j; ++i) H[i * kMaxM + j] = st->h[0][i] + st->h[1][i];
-        H[(j + 1) * kMaxM + j] = hn;
-        for (int i = 0; i < j; ++i) {
-            const double a = H[i * kMaxM + j], bb = H[(i + 1) * kMaxM + j];
-            H[i * kMaxM + j] = st->cs[i] * a + st->sn[i] * bb;
-            H[(i + 1) * kMaxM + j] = -st->sn[i] * a + st->cs[i] * bb;
-        }
-        const double a = H[j * kMaxM + j], bb = H[(j + 1) * kMaxM + j];
-        const double den = sqrt(a * a + bb * bb);
-        const double c = den == 0.0 ? 1.0 : a / den, sn = den == 0.0 ? 0.0 : bb / den;
-        st->cs[j] = c;
-        st->sn[j] = sn;
-        H[j * kMaxM + j] = c * a + sn * bb;
-        H[(j + 1) * kMaxM + j] = 0.0;
-        st->g[j + 1] = -sn * st->g[j];
-        st->g[j] = c * st->g[j];
-        st->total += 1;
-        st->est = fabs(st->g[j + 1]) / st->bnorm;
-        if (hn == 0.0) st->breakdown = 1;
-        if (st->est <= tol || st->total >= maxit || hn == 0.0 || j + 1 == m) {
-            st->done = 1;
-            st->jend = j;
-        } else {
-            st->j = j + 1;
-        }
-    }
-}
-
-// V_j = w / ||w|| (j already advanced by the Hessenberg update)
-__global__ void k_gm_normalize(const double *__restrict__ w, double *V, int64_t n, const GmState *st) {
-    if (st->done) return;
-    const double inv = 1.0 / sqrt(st->hn2);
-    double *v = V + (size_t)st->j * n;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
-        v[t] = w[t] * inv;
-}
-
-// y = H^{-1} g (upper triangular, jend+1 columns)
-__global__ void k_gm_solve(GmState *st) {
-    if (threadIdx.x != 0 || st->finished) return;
-    const int je = st->jend;
-    for (int i = je; i >= 0; --i) {
-        double s = st->g[i];
-        for (int k = i + 1; k <= je; ++k) s -= st->H[i * kMaxM + k] * st->y[k];
-        st->y[i] = s / st->H[i * kMaxM + i];
-    }
-}
-
-// x += sum_{i <= jend} y_i Z_i
-__global__ void k_gm_xupdate(const double *__restrict__ Z, int64_t n, double *x, const GmState *st) {
-    __shared__ double y[kMaxM];
-    if (st->finished) return;
-    const int k = st->jend + 1;
-    for (int i = threadIdx.x; i < k; i += blockDim.x) y[i] = st->y[i];
-    __syncthreads();
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
-        double acc = x[t];
-        for (int i = 0; i < k; ++i) acc += y[i] * Z[(size_t)i * n + t];
-        x[t] = acc;
-    }
-}
-
-// staging of column j for preconditioners that take plain pointers
+// staging of column j for the network (which takes plain pointers); nothing
+// to do once the solve has finished
 __global__ void k_gm_get_col(const double *__restrict__ V, int64_t n, const GmState *st, double *out) {
-    if (st->done) return;
+    if (st->finished) return;
     const double *v = V + (size_t)st->j * n;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
         out[t] = v[t];
 }
 __global__ void k_gm_put_col(const double *__restrict__ in, double *Z, int64_t n, const GmState *st) {
-    if (st->done) return;
+    if (st->finished) return;
     double *z = Z + (size_t)st->j * n;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
         z[t] = in[t];
 }
 
-__global__ void k_gm_jacobi_col(const double *__restrict__ jd, const double *__restrict__ V, double *Z, int64_t N,
-                                const GmState *st) {
-    if (st->done) return;
-    const double *v = V + (size_t)st->j * 3 * N;
-    double *z = Z + (size_t)st->j * 3 * N;
-    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < N; q += (int64_t)gridDim.x * blockDim.x) {
-        const double *o = jd + (size_t)q * 9;
-        const double x0 = v[q], x1 = v[N + q], x2 = v[2 * N + q];
-        z[q] = o[0] * x0 + o[1] * x1 + o[2] * x2;
-        z[N + q] = o[3] * x0 + o[4] * x1 + o[5] * x2;
-        z[2 * N + q] = o[6] * x0 + o[7] * x1 + o[8] * x2;
+__global__ void k_norm2(const double *__restrict__ x, int64_t n, double *out) {
+    __shared__ double sh[kWarps];
+    double s = 0.0;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+        s += x[t] * x[t];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < kWarps; ++w) t += sh[w];
+        atomicAdd(out, t);
     }
+}
+
+__global__ void k_sub(const double *__restrict__ b, const double *__restrict__ ax, double *r, int64_t n) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+        r[t] = b[t] - ax[t];
+}
+
+inline int nblocks(int64_t n) {
+    return (int)std::max<int64_t>(1, std::min<int64_t>((n + kB - 1) / kB, 152 * 4));
 }
 
 }  // namespace
 
 size_t gx_gm_state_bytes() { return sizeof(GmState); }
-size_t gx_gm_partial_count() { return (size_t)kRedBlocks * kPartStride; }
+size_t gx_gm_partial_count() { return (size_t)2 * kMaxGrid * kPartStride; }
 int gx_gm_max_restart() { return kMaxM; }
 
 // ||x||_2 computed on the device, read back (synchronises st)
 double gx_norm_host(gx_ctx *c, const double *x, int64_t n, cudaStream_t st, int *status) {
     *status = GX_OK;
-    k_gm_init<<<1, 32, 0, st>>>(c->gm);
-    k_gm_bnorm<<<nblocks(n), kB, 0, st>>>(x, n, c->gm, c->gpart);
-    c->launches += 2;
+    double *acc = c->gpart;
     double h = 0;
-    if (cudaMemcpyAsync(&h, &c->gm->bnorm, sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+    if (cudaMemsetAsync(acc, 0, sizeof(double), st) != cudaSuccess) { *status = GX_ECUDA; return 0; }
+    k_norm2<<<nblocks(n), kB, 0, st>>>(x, n, acc);
+    c->launches += 1;
+    if (cudaMemcpyAsync(&h, acc, sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess) {
         *status = GX_ECUDA;
         c->err = "norm: CUDA error";
         return 0;
     }
-    return h;
+    return sqrt(h);
 }
 
 // Solve A x = rhs for x = Eth (initial guess already in Eth).
 int gx_fgmres(gx_ctx *c, cudaStream_t st) {
     const int64_t n = 3 * c->N;
-    const int m = c->cfg.gmres_restart;
-    const int maxit = c->cfg.gmres_maxit;
-    const double tol = c->cfg.gmres_tol;
     const int pc = c->cfg.precond;
-    const bool flex = pc != GX_PRECOND_NONE;
-    double *x = c->Eth, *b = c->rhs, *w = c->w, *r = c->r;
-    double *V = c->V, *Z = flex ? c->Z : c->V;
-    GmState *gs = c->gm;
-    const int nb = nblocks(n);
     int rc;
     if (pc == GX_PRECOND_JACOBI || pc == GX_PRECOND_NET) { rc = gx_build_jacobi(c, st); if (rc) return rc; }
-    k_gm_init<<<1, 32, 0, st>>>(gs);
+    static int grid = 0;
+    if (!grid) {
+        int dev = 0, nsm = 0, per = 0;
+        GX_CHECK(c, cudaGetDevice(&dev));
+        GX_CHECK(c, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        GX_CHECK(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fgmres, kB, 0));
+        grid = std::max(1, std::min(per * nsm, kMaxGrid));
+    }
+    CoArgs a{};
+    a.op = gx_opargs(c);
+    a.b = c->rhs;
+    a.x = c->Eth;
+    a.V = c->V;
+    a.Z = pc == GX_PRECOND_NONE ? c->V : c->Z;
+    a.w = c->w;
+    a.r = c->r;
+    a.jd = pc == GX_PRECOND_JACOBI ? c->jdiag : nullptr;
+    a.st = c->gm;
+    a.part = c->gpart;
+    a.N = c->N;
+    a.m = c->cfg.gmres_restart;
+    a.maxit = c->cfg.gmres_maxit;
+    a.tol = c->cfg.gmres_tol;
+    a.net = pc == GX_PRECOND_NET;
+    if (gx_net_collecting(c)) {
+        // training pair of this solve: r0 = b - A E^n (the initial guess)
+        if ((rc = gx_apply_A(c, c->Eth, c->w, st))) return rc;
+        k_sub<<<nblocks(n), kB, 0, st>>>(c->rhs, c->w, c->r, n);
+        GX_LAUNCHED(c);
+        if ((rc = gx_net_pair_begin(c, c->r, st))) return rc;
+    }
+    k_gm_init<<<1, 32, 0, st>>>(c->gm);
     GX_LAUNCHED(c);
-    k_gm_bnorm<<<nb, kB, 0, st>>>(b, n, gs, c->gpart);
-    GX_LAUNCHED(c);
+    void *args[] = {&a};
+    auto launch = [&]() -> int {
+        GX_CHECK(c, cudaLaunchCooperativeKernel((const void *)k_fgmres, dim3(grid), dim3(kB), args, 0, st));
+        c->launches++;
+        return GX_OK;
+    };
     struct Flags { int j, done, finished, conv, total; };
     Flags *hf = reinterpret_cast<Flags *>(c->hpin);
-    auto read_flags = [&]() -> int {
-        GX_CHECK(c, cudaMemcpyAsync(hf, gs, sizeof(Flags), cudaMemcpyDeviceToHost, st));
-        GX_CHECK(c, cudaStreamSynchronize(st));
-        return GX_OK;
-    };
-    auto enqueue_iteration = [&]() -> int {
-        if (pc == GX_PRECOND_JACOBI) {
-            k_gm_jacobi_col<<<nblocks(c->N), kB, 0, st>>>(c->jdiag, V, Z, c->N, gs);
-            GX_LAUNCHED(c);
-        } else if (pc == GX_PRECOND_NET) {
-            k_gm_get_col<<<nb, kB, 0, st>>>(V, n, gs, c->vbuf);
-            GX_LAUNCHED(c);
-            int r2 = gx_net_apply(c, c->vbuf, c->zbuf, st);
-            if (r2) return r2;
-            k_gm_put_col<<<nb, kB, 0, st>>>(c->zbuf, Z, n, gs);
-            GX_LAUNCHED(c);
+    if (!a.net) {
+        if ((rc = launch())) return rc;             // the whole solve
+    } else {
+        // the network between launches: V_j -> Z_j, then the Arnoldi step;
+        // batches sized by the previous solve, state checked between batches
+        if ((rc = launch())) return rc;             // ||b||, first residual, V_0
+        int batch = std::max(2, std::min(16, c->last.iters > 0 ? c->last.iters + 2 : 6));
+        const int nb = nblocks(n);
+        for (int guard = 0; guard < 100000; ++guard) {
+            for (int k = 0; k < batch; ++k) {
+                k_gm_get_col<<<nb, kB, 0, st>>>(c->V, n, c->gm, c->vbuf);
+                GX_LAUNCHED(c);
+                if ((rc = gx_net_apply(c, c->vbuf, c->zbuf, st))) return rc;
+                k_gm_put_col<<<nb, kB, 0, st>>>(c->zbuf, c->Z, n, c->gm);
+                GX_LAUNCHED(c);
+                if ((rc = launch())) return rc;
+            }
+            GX_CHECK(c, cudaMemcpyAsync(hf, c->gm, sizeof(Flags), cudaMemcpyDeviceToHost, st));
+            GX_CHECK(c, cudaStreamSynchronize(st));
+            if (hf->finished) break;
+            batch = std::min(2 * batch, 32);
         }
-        int r2 = gx_apply_A_j(c, Z, n, &gs->j, &gs->done, w, st);
-        if (r2) return r2;
-        k_gm_mdot<<<nb, kB, 0, st>>>(V, n, w, gs, c->gpart, 0);
-        GX_LAUNCHED(c);
-        k_gm_axpy<<<nb, kB, 0, st>>>(V, n, w, gs, c->gpart, 0, m, tol, maxit);
-        GX_LAUNCHED(c);
-        k_gm_mdot<<<nb, kB, 0, st>>>(V, n, w, gs, c->gpart, 1);
-        GX_LAUNCHED(c);
-        k_gm_axpy<<<nb, kB, 0, st>>>(V, n, w, gs, c->gpart, 1, m, tol, maxit);
-        GX_LAUNCHED(c);
-        k_gm_normalize<<<nb, kB, 0, st>>>(w, V, n, gs);
-        GX_LAUNCHED(c);
-        return GX_OK;
-    };
-    // first batch sized by the previous solve (consecutive steps need similar
-    // iteration counts), so most solves need one look at the device state
-    int batch = std::max(2, std::min(16, c->last.iters > 0 ? c->last.iters : 4));
-    for (int cycle = 0;; ++cycle) {
-        // r = b - A x, decide, V_0 = r / beta
-        rc = gx_apply_A(c, x, r, st);
-        if (rc) return rc;
-        k_gm_restart<<<nb, kB, 0, st>>>(b, r, n, gs, c->gpart, tol, maxit);
-        GX_LAUNCHED(c);
-        k_gm_v0<<<nb, kB, 0, st>>>(r, V, n, gs);
-        GX_LAUNCHED(c);
-        if (cycle == 0 && (rc = gx_net_pair_begin(c, r, st))) return rc;
-        // iterate in batches until the cycle ends (kernels are no-ops after)
-        for (;;) {
-            for (int k = 0; k < batch; ++k)
-                if ((rc = enqueue_iteration())) return rc;
-            if ((rc = read_flags())) return rc;
-            if (hf->done) break;
-            batch = std::min(2 * batch, 16);
-        }
-        if (hf->finished) break;
-        k_gm_solve<<<1, 32, 0, st>>>(gs);
-        GX_LAUNCHED(c);
-        k_gm_xupdate<<<nb, kB, 0, st>>>(Z, n, x, gs);
-        GX_LAUNCHED(c);
-        if (cycle > maxit + 2) break;
     }
-    double tail[3];
-    GX_CHECK(c, cudaMemcpyAsync(tail, &gs->relres, sizeof(double), cudaMemcpyDeviceToHost, st));
+    double tail[4];
+    GX_CHECK(c, cudaMemcpyAsync(hf, c->gm, sizeof(Flags), cudaMemcpyDeviceToHost, st));
+    GX_CHECK(c, cudaMemcpyAsync(tail, &c->gm->bnorm, sizeof(tail), cudaMemcpyDeviceToHost, st));
     GX_CHECK(c, cudaStreamSynchronize(st));
+    if (!hf->finished) { c->err = "FGMRES: the solve did not finish"; return GX_ECUDA; }
     c->last.iters = hf->total;
-    c->last.relres = tail[0];
+    c->last.relres = tail[2];
     c->last.converged = hf->conv;
-    if ((rc = gx_net_pair_end(c, hf->conv, std::min(hf->total, m), st))) return rc;
+    if ((rc = gx_net_pair_end(c, hf->conv, std::min(hf->total, a.m), st))) return rc;
     if (!hf->conv) {
         c->err = "GMRES reached gmres_maxit without converging (best iterate kept)";
         return GX_ENOCONV;

@@ -10,21 +10,13 @@
 // addresses): vector fields [3][N], mass-matrix rows [81][N] (entry o*9 + e:
 // neighbour offset o = (ox+1) + 3 (oy+1), alpha component e), deposit records
 // [species][112][N].
-#include "gx_internal.cuh"
+#include "gx_op.cuh"
 
 namespace {
 
 constexpr int kB = 256;
 
-// periodic index for small offsets (|off| < n): no integer division
-__device__ __forceinline__ int wr(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
-
-struct G2 {
-    int nx, ny;
-    double dx, dy;
-    __device__ __forceinline__ int64_t id(int i, int j) const { return (int64_t)wr(i, nx) + (int64_t)nx * wr(j, ny); }
-    __device__ __forceinline__ int64_t N() const { return (int64_t)nx * ny; }
-};
+__device__ __forceinline__ int wr(int i, int n) { return gx_wr(i, n); }
 
 inline int blocks_for(int64_t n) {
     int64_t b = (n + kB - 1) / kB;
@@ -267,88 +259,16 @@ __device__ __forceinline__ double dCy(const G2 &g, const double *f, int i, int j
     return ((f[g.id(i, j + 1)] + f[g.id(i + 1, j + 1)]) - (f[g.id(i, j)] + f[g.id(i + 1, j)])) / (2.0 * g.dy);
 }
 
-struct OpArgs {
-    G2 g;
-    double ct2;        // (c theta dt)^2
-    double mfac;       // 4 pi theta dt / dV
-    double lfx, lfy;   // theta dt / dx, theta dt / dy
-    const double *M;   // [81][N]
-    const double *kappa;   // [2][3][N] or null
-};
-
-// y = A x: x + (c theta dt)^2 curl_N curl_C x + (4 pi theta dt / dV) M x
-//        - theta dt sum_d (1/dx_d) [kappa_+ (x_+ - x) - kappa_- (x - x_-)]
-// (Eq. 7 with the mass term of Eq. 35 and the diffusive LF term of Eq. 19.)
 __global__ void k_matvec(OpArgs a, const double *__restrict__ x, double *__restrict__ y, const int *jptr,
                          int64_t stride, const int *doneptr) {
     // device-indexed operand (Krylov column j of a basis) and early exit once
     // the solver flagged the cycle done
     if (doneptr && *doneptr) return;
     if (jptr) x += (int64_t)(*jptr) * stride;
-    const G2 &g = a.g;
-    const int64_t N = g.N();
+    const int64_t N = a.g.N();
     GRID_LOOP(q, N) {
-        const int i = (int)(q % g.nx), j = (int)(q / g.nx);
-        const int im = wr(i - 1, g.nx), ip = wr(i + 1, g.nx), jm = wr(j - 1, g.ny), jp = wr(j + 1, g.ny);
-        const int xs[3] = {im, i, ip};
-        const int64_t ys[3] = {(int64_t)jm * g.nx, (int64_t)j * g.nx, (int64_t)jp * g.nx};
-        // the 3x3 node neighbourhood of the three components
-        double v[3][3][3];   // [comp][row y][col x]
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-#pragma unroll
-            for (int r = 0; r < 3; ++r)
-#pragma unroll
-                for (int s = 0; s < 3; ++s) v[c][r][s] = x[c * N + ys[r] + xs[s]];
-        // curl_C x at the 4 cells around the node: cell (i-1+ca, j-1+cb) has
-        // corners at columns ca, ca+1 and rows cb, cb+1 of the neighbourhood
-        double cc[2][2][3];
-        const double hx = 1.0 / (2.0 * g.dx), hy = 1.0 / (2.0 * g.dy);
-#pragma unroll
-        for (int cb = 0; cb < 2; ++cb)
-#pragma unroll
-            for (int ca = 0; ca < 2; ++ca) {
-                // d/dx and d/dy of each component at this cell
-                double ddx[3], ddy[3];
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    ddx[c] = ((v[c][cb][ca + 1] + v[c][cb + 1][ca + 1]) - (v[c][cb][ca] + v[c][cb + 1][ca])) * hx;
-                    ddy[c] = ((v[c][cb + 1][ca] + v[c][cb + 1][ca + 1]) - (v[c][cb][ca] + v[c][cb][ca + 1])) * hy;
-                }
-                cc[cb][ca][0] = ddy[2];
-                cc[cb][ca][1] = -ddx[2];
-                cc[cb][ca][2] = ddx[1] - ddy[0];
-            }
-        const double dxz = ((cc[0][1][2] + cc[1][1][2]) - (cc[0][0][2] + cc[1][0][2])) * hx;
-        const double dyz = ((cc[1][0][2] + cc[1][1][2]) - (cc[0][0][2] + cc[0][1][2])) * hy;
-        const double dxy = ((cc[0][1][1] + cc[1][1][1]) - (cc[0][0][1] + cc[1][0][1])) * hx;
-        const double dyx = ((cc[1][0][0] + cc[1][1][0]) - (cc[0][0][0] + cc[0][1][0])) * hy;
         double out[3];
-        out[0] = v[0][1][1] + a.ct2 * dyz;
-        out[1] = v[1][1][1] + a.ct2 * (-dxz);
-        out[2] = v[2][1][1] + a.ct2 * (dxy - dyx);
-        if (a.M) {
-#pragma unroll
-            for (int o = 0; o < 9; ++o) {
-                const int ox = o % 3, oy = o / 3;
-#pragma unroll
-                for (int r = 0; r < 3; ++r)
-                    out[r] += a.mfac * (a.M[(size_t)(o * 9 + 3 * r) * N + q] * v[0][oy][ox] +
-                                        a.M[(size_t)(o * 9 + 3 * r + 1) * N + q] * v[1][oy][ox] +
-                                        a.M[(size_t)(o * 9 + 3 * r + 2) * N + q] * v[2][oy][ox]);
-            }
-        }
-        if (a.kappa) {
-            const int64_t xm = ys[1] + im, ym = ys[0] + i;
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const double *kx = a.kappa + (0 * 3 + c) * N, *ky = a.kappa + (1 * 3 + c) * N;
-                if (g.nx > 1)
-                    out[c] -= a.lfx * (kx[q] * (v[c][1][2] - v[c][1][1]) - kx[xm] * (v[c][1][1] - v[c][1][0]));
-                if (g.ny > 1)
-                    out[c] -= a.lfy * (ky[q] * (v[c][2][1] - v[c][1][1]) - ky[ym] * (v[c][1][1] - v[c][0][1]));
-            }
-        }
+        gx_apply_A_node(a, x, q, out);
         y[q] = out[0];
         y[N + q] = out[1];
         y[2 * N + q] = out[2];
@@ -631,6 +551,8 @@ int filter_passes(gx_ctx *c, double *f, int passes, bool alternate, cudaStream_t
 }
 
 }  // namespace
+
+OpArgs gx_opargs(const gx_ctx *c) { return opargs(c); }
 
 int gx_node_fields(gx_ctx *c, const double *Eth, const double *Bcur, float4 *outE, float4 *outB, cudaStream_t st) {
     k_node_fields<<<blocks_for(c->N), kB, 0, st>>>(geom(c), Eth, Bcur, outE, outB);

@@ -216,6 +216,7 @@ double gx_norm_host(gx_ctx *c, const double *x, int64_t n, cudaStream_t st, int 
 
 // network (gx_net.cu)
 int gx_net_apply(gx_ctx *c, const double *r, double *z, cudaStream_t st);
+int gx_net_collecting(const gx_ctx *c);
 int gx_net_pair_begin(gx_ctx *c, const double *r0, cudaStream_t st);
 int gx_net_pair_end(gx_ctx *c, int converged, int nbasis, cudaStream_t st);
 void gx_net_free(gx_ctx *c);

@@ -362,12 +362,20 @@ __global__ void k_unpack_output(const float *y, int64_t HW, const double *jd, co
     }
 }
 
+// one atomic per CTA (256 threads)
 __global__ void k_sumsq(const double *x, int64_t n, double *out) {
+    __shared__ double sh[8];
     double s = 0.0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         s += x[i] * x[i];
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if ((threadIdx.x & 31) == 0) atomicAdd(out, s);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < 8; ++w) t += sh[w];
+        atomicAdd(out, t);
+    }
 }
 
 // training crops: for crop b, input = r / s_b on a (C+8)^2 window (4-pixel halo,
@@ -634,7 +642,7 @@ int gx_net_apply(gx_ctx *c, const double *r, double *z, cudaStream_t st) {
     const int H = c->n[1], W = c->n[0];
     if ((rc = net_reserve(c, (int64_t)H * W))) return rc;
     GX_CHECK(c, cudaMemsetAsync(n->dsum, 0, sizeof(double), st));
-    k_sumsq<<<nblk(3 * c->N), 256, 0, st>>>(r, 3 * c->N, n->dsum);
+    k_sumsq<<<std::min(nblk(3 * c->N), 152 * 2), 256, 0, st>>>(r, 3 * c->N, n->dsum);
     GX_LAUNCHED(c);
     k_pack_input<double><<<nblk(c->N), 256, 0, st>>>(r, c->N, n->x0, n->dsum, 1.0);
     GX_LAUNCHED(c);
@@ -652,6 +660,8 @@ int gx_net_apply(gx_ctx *c, const double *r, double *z, cudaStream_t st) {
 // the solve are added too, as exact pairs (A V_j, V_j) at one matrix-vector
 // product each.
 constexpr int kKrylovPairs = 6;
+
+int gx_net_collecting(const gx_ctx *c) { return c->net && c->net->collect && c->net->cap_pairs > 0; }
 
 int gx_net_pair_begin(gx_ctx *c, const double *r0, cudaStream_t st) {
     Net *n = c->net;

@@ -1,0 +1,108 @@
+// gx_op.cuh -- the implicit field operator of the GL-ECSIM step (2D), shared
+// by the grid kernels and the solver.
+//
+//   A x = x + (c theta dt)^2 curl_N curl_C x + (4 pi theta dt / dV) M x
+//         - theta dt sum_d (1/dx_d) [kappa_+ (x_+ - x) - kappa_- (x - x_-)]
+//
+// (Eq. 7 with the mass term of Eq. 35 and the diffusive LF term of Eq. 19.)
+// Mesh (Sec. 1.1): E at nodes, B at cell centres, periodic.  With the cell
+// curl taken from face-averaged corner differences and the node curl from
+// side-averaged cell differences, curl_N curl_C acts on the 3x3 node
+// neighbourhood v[r][s] (row r along y, column s along x, centre (1,1)) as
+//   (curl curl x)_x = hy^2 Dyy(x_x) + hx hy Dxy(x_y)
+//   (curl curl x)_y = hx hy Dxy(x_x) + hx^2 Dxx(x_y)
+//   (curl curl x)_z = hx^2 Dxx(x_z) + hy^2 Dyy(x_z)
+// with hx = 1/(2 dx), hy = 1/(2 dy), Sx(r) = v[r][0] + 2 v[r][1] + v[r][2],
+// Sy(s) = v[0][s] + 2 v[1][s] + v[2][s],
+//   Dyy = 2 Sx(1) - Sx(0) - Sx(2),  Dxx = 2 Sy(1) - Sy(0) - Sy(2),
+//   Dxy = v[0][0] - v[0][2] - v[2][0] + v[2][2]
+// (the composition of the two averaged differences, expanded once).
+#pragma once
+
+#include "gx_internal.cuh"
+
+// periodic index for small offsets (|off| < n): no integer division
+__device__ __forceinline__ int gx_wr(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+
+struct G2 {
+    int nx, ny;
+    double dx, dy;
+    __device__ __forceinline__ int64_t id(int i, int j) const {
+        return (int64_t)gx_wr(i, nx) + (int64_t)nx * gx_wr(j, ny);
+    }
+    __device__ __forceinline__ int64_t N() const { return (int64_t)nx * ny; }
+};
+
+struct OpArgs {
+    G2 g;
+    double ct2;            // (c theta dt)^2
+    double mfac;           // 4 pi theta dt / dV
+    double lfx, lfy;       // theta dt / dx, theta dt / dy
+    const double *M;       // [81][N] or null
+    const double *kappa;   // [2][3][N] or null
+};
+
+// operator arguments of a context (its current M, kappa and step parameters)
+OpArgs gx_opargs(const gx_ctx *c);
+
+// (A x) at node q, x component-major [3][N].  With CG the neighbourhood of x
+// is read through L2 only (x was written by other CTAs of the same launch).
+template <bool CG = false>
+__device__ __forceinline__ void gx_apply_A_node(const OpArgs &a, const double *__restrict__ x, int64_t q,
+                                                double out[3]) {
+    const G2 &g = a.g;
+    const int64_t N = g.N();
+    const int i = (int)(q % g.nx), j = (int)(q / g.nx);
+    const int im = gx_wr(i - 1, g.nx), ip = gx_wr(i + 1, g.nx), jm = gx_wr(j - 1, g.ny), jp = gx_wr(j + 1, g.ny);
+    const int xs[3] = {im, i, ip};
+    const int64_t ys[3] = {(int64_t)jm * g.nx, (int64_t)j * g.nx, (int64_t)jp * g.nx};
+    double v[3][3][3];   // [comp][row y][col x]
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int s = 0; s < 3; ++s) v[c][r][s] = CG ? __ldcg(x + c * N + ys[r] + xs[s]) : x[c * N + ys[r] + xs[s]];
+    const double hx = 0.5 / g.dx, hy = 0.5 / g.dy;
+    const double hxx = hx * hx, hyy = hy * hy, hxy = hx * hy;
+    auto Dyy = [&](int c) {
+        const double s0 = v[c][0][0] + 2.0 * v[c][0][1] + v[c][0][2];
+        const double s1 = v[c][1][0] + 2.0 * v[c][1][1] + v[c][1][2];
+        const double s2 = v[c][2][0] + 2.0 * v[c][2][1] + v[c][2][2];
+        return 2.0 * s1 - s0 - s2;
+    };
+    auto Dxx = [&](int c) {
+        const double s0 = v[c][0][0] + 2.0 * v[c][1][0] + v[c][2][0];
+        const double s1 = v[c][0][1] + 2.0 * v[c][1][1] + v[c][2][1];
+        const double s2 = v[c][0][2] + 2.0 * v[c][1][2] + v[c][2][2];
+        return 2.0 * s1 - s0 - s2;
+    };
+    auto Dxy = [&](int c) { return (v[c][0][0] - v[c][0][2]) - (v[c][2][0] - v[c][2][2]); };
+    out[0] = v[0][1][1] + a.ct2 * (hyy * Dyy(0) + hxy * Dxy(1));
+    out[1] = v[1][1][1] + a.ct2 * (hxy * Dxy(0) + hxx * Dxx(1));
+    out[2] = v[2][1][1] + a.ct2 * (hxx * Dxx(2) + hyy * Dyy(2));
+    if (a.M) {
+        double m[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+        for (int o = 0; o < 9; ++o) {
+            const int ox = o % 3, oy = o / 3;
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+#pragma unroll
+                for (int e = 0; e < 3; ++e) m[r] = fma(a.M[(size_t)(o * 9 + 3 * r + e) * N + q], v[e][oy][ox], m[r]);
+        }
+#pragma unroll
+        for (int r = 0; r < 3; ++r) out[r] = fma(a.mfac, m[r], out[r]);
+    }
+    if (a.kappa) {
+        const int64_t xm = ys[1] + im, ym = ys[0] + i;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const double *kx = a.kappa + (0 * 3 + c) * N, *ky = a.kappa + (1 * 3 + c) * N;
+            if (g.nx > 1)
+                out[c] -= a.lfx * (kx[q] * (v[c][1][2] - v[c][1][1]) - kx[xm] * (v[c][1][1] - v[c][1][0]));
+            if (g.ny > 1)
+                out[c] -= a.lfy * (ky[q] * (v[c][2][1] - v[c][1][1]) - ky[ym] * (v[c][1][1] - v[c][0][1]));
+        }
+    }
+}
