@@ -478,8 +478,7 @@ __global__ void k_diag_grid(G2 g, const double *__restrict__ E, const double *__
     }
 }
 
-__global__ void k_diag_particles(int64_t ncell, int cap, const int *cnt, const float *vx, const float *vy,
-                                 const float *vz, const float *w, double mass, double *acc) {
+__global__ void k_diag_particles(int64_t ncell, int cap, const int *cnt, const float4 *P, double mass, double *acc) {
     double ke = 0, px = 0, py = 0, pz = 0;
     double np = 0;
     for (int64_t c = blockIdx.x; c < ncell; c += gridDim.x) {
@@ -488,8 +487,9 @@ __global__ void k_diag_particles(int64_t ncell, int cap, const int *cnt, const f
         if (threadIdx.x == 0) np += m;
         for (int i = threadIdx.x; i < m; i += blockDim.x) {
             const size_t s = (size_t)c * cap + bin_slot(word, i, cap);
-            const double mw = mass * w[s];
-            const double a = vx[s], b = vy[s], d = vz[s];
+            const float4 s0 = P[2 * s], s1 = P[2 * s + 1];
+            const double mw = mass * s1.y;
+            const double a = s0.z, b = s0.w, d = s1.x;
             ke += 0.5 * mw * (a * a + b * b + d * d);
             px += mw * a; py += mw * b; pz += mw * d;
         }
@@ -652,8 +652,7 @@ int gx_diag_run(gx_ctx *c, gx_diag *out, cudaStream_t st) {
     for (int s = 0; s < c->nspecies; ++s) {
         const Species &S = c->sp[s];
         k_diag_particles<<<(unsigned)std::min<int64_t>(c->N, 152 * 8), 128, 0, st>>>(
-            c->N, S.cap, S.cnt[c->cur], S.f[c->cur][PF_VX], S.f[c->cur][PF_VY], S.f[c->cur][PF_VZ],
-            S.f[c->cur][PF_W], S.m, acc + 5);
+            c->N, S.cap, S.cnt[c->cur], S.p[c->cur], S.m, acc + 5);
         GX_LAUNCHED(c);
     }
     double h[16];

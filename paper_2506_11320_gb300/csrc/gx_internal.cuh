@@ -4,10 +4,10 @@
 //   * fields: FP64, component-major [3][N] with N = nx ny nz; E at nodes, B at
 //     cell centres (collocated staggered mesh, Sec. 1.1 of the paper);
 //   * particles: per species, cell bins of fixed capacity `cap` (a multiple of
-//     64) in SoA FP32 arrays: cell-local offsets ox, oy in [0,1), velocities
-//     vx, vy, vz, weight w (and an optional int32 id).  A bin holds a bottom
-//     and a top segment (see bin_front / bin_back).  Two copies: the push
-//     reads one and writes the other, then they swap;
+//     64) of 32-byte slots (ox, oy, vx, vy | vz, w, id, 0) in FP32, ox and oy
+//     the cell-local offsets in [0,1).  A bin holds a bottom and a top segment
+//     (see bin_front / bin_back).  Two copies: the push reads one and writes
+//     the other, then they swap;
 //   * deposit records: per species and cell, FP32 partial sums over the cell's
 //     particles (see Rec below), [species][112][N]; after a push a second set
 //     holds the sums over the particles that arrived in each cell; the grid
@@ -49,7 +49,8 @@ template <> struct Rec<3> {
 };
 
 // ------------------------------------------------------------- particles
-enum { PF_OX = 0, PF_OY, PF_OZ, PF_VX, PF_VY, PF_VZ, PF_W, PF_ID, PF_COUNT };
+// One 32-byte slot per particle: float4 (ox, oy, vx, vy) then float4
+// (vz, w, id bits, 0); ox, oy are the cell-local offsets in [0, 1).
 
 // A cell's bin holds two segments: particles that stayed in the cell during
 // the last push fill slots [0, front) from the bottom, particles that arrived
@@ -68,7 +69,7 @@ __host__ __device__ inline int bin_slot(int w, int i, int cap) {
 struct Species {
     double q = 0, m = 0;
     int cap = 0;                        // bin capacity (particles per cell)
-    float *f[2][PF_COUNT] = {};         // [copy][field]; PF_ID holds int32 bits
+    float4 *p[2] = {};                  // [copy]: 2 float4 per slot, cap slots per cell
     int *cnt[2] = {};                   // particles per cell, per copy
 };
 

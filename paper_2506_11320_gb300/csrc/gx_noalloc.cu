@@ -1,14 +1,13 @@
 // gx_noalloc.cu -- particle gather that allocates no memory.
 //
-// gx_get_particles sizes its scratch (per-cell offsets, the scan's temporary
-// storage, the field-pointer table) to the grid and allocates it on every
-// call.  Some callers cannot allocate at that point: a diagnostics or
+// gx_get_particles sizes its scratch (per-cell counts and offsets, the scan's
+// temporary storage) to the grid and allocates it on every call.  Some callers cannot allocate at that point: a diagnostics or
 // checkpoint hook running while the particle arrays already fill the device,
 // a code path that must not synchronise the device (cudaMalloc and cudaFree
 // can), or a host thread that holds a memory budget of its own.  This variant
 // keeps its only scratch, the per-cell output offsets, in a fixed file-scope
-// device array and passes everything else by value, so it calls no
-// allocating routine of CUDA, of a library or of PyTorch.
+// device array, so it calls no allocating routine of CUDA, of a library or of
+// PyTorch.
 //
 // Limits and rules:
 //   * at most kMaxCells cells (the scratch holds one int per cell, 1 MiB);
@@ -76,15 +75,11 @@ __global__ void __launch_bounds__(kScanThreads) k_na_scan(const int *__restrict_
     }
 }
 
-struct NaSrc {
-    const float *f[PF_COUNT];
-};
-
 // one CTA per cell: copy the cell's particles (front segment, then back) to
-// positions offs[c] .. offs[c] + count - 1
+// positions offs[c] .. offs[c] + count - 1; slots are (ox, oy, vx, vy | vz, w, id, 0)
 __global__ void k_na_gather(int64_t ncell, int cap, const int *__restrict__ cnt, const int *__restrict__ offs,
-                            NaSrc src, int nx, int ny, double dx, double dy, double *x, double *y, double *z,
-                            float *vx, float *vy, float *vz, float *w, int32_t *id) {
+                            const float4 *__restrict__ P, int nx, int ny, double dx, double dy, double *x, double *y,
+                            double *z, float *vx, float *vy, float *vz, float *w, int32_t *id) {
     const int64_t c = blockIdx.x;
     if (c >= ncell) return;
     const int word = cnt[c];
@@ -95,15 +90,16 @@ __global__ void k_na_gather(int64_t ncell, int cap, const int *__restrict__ cnt,
     const int cx = (int)(c % nx), cy = (int)(c / nx);
     for (int i = threadIdx.x; i < m; i += blockDim.x) {
         const size_t s = (size_t)c * cap + (i < f ? i : cap - b + (i - f));
+        const float4 s0 = P[2 * s], s1 = P[2 * s + 1];
         const int o = offs[c] + i;
-        if (x) x[o] = (cx + (double)src.f[PF_OX][s]) * dx;
-        if (y) y[o] = ny > 1 ? (cy + (double)src.f[PF_OY][s]) * dy : 0.0;
+        if (x) x[o] = (cx + (double)s0.x) * dx;
+        if (y) y[o] = ny > 1 ? (cy + (double)s0.y) * dy : 0.0;
         if (z) z[o] = 0.0;
-        if (vx) vx[o] = src.f[PF_VX][s];
-        if (vy) vy[o] = src.f[PF_VY][s];
-        if (vz) vz[o] = src.f[PF_VZ][s];
-        if (w) w[o] = src.f[PF_W][s];
-        if (id && src.f[PF_ID]) id[o] = __float_as_int(src.f[PF_ID][s]);
+        if (vx) vx[o] = s0.z;
+        if (vy) vy[o] = s0.w;
+        if (vz) vz[o] = s1.x;
+        if (w) w[o] = s1.y;
+        if (id) id[o] = __float_as_int(s1.z);
     }
 }
 
@@ -151,10 +147,8 @@ extern "C" int gx_get_particles_noalloc(gx_ctx *c, int s, double *x, double *y, 
     const int *cnt = S.cnt[c->cur];
     k_na_scan<<<1, kScanThreads, 0, st>>>(cnt, (int)c->N, S.cap, offs);
     GX_LAUNCHED(c);
-    NaSrc src;
-    for (int f = 0; f < PF_COUNT; ++f) src.f[f] = S.f[c->cur][f];
-    k_na_gather<<<(unsigned)c->N, 128, 0, st>>>(c->N, S.cap, cnt, offs, src, c->n[0], c->n[1], c->cfg.dx[0],
-                                                c->cfg.dx[1], x, y, z, vx, vy, vz, w, id);
+    k_na_gather<<<(unsigned)c->N, 128, 0, st>>>(c->N, S.cap, cnt, offs, S.p[c->cur], c->n[0], c->n[1],
+                                                c->cfg.dx[0], c->cfg.dx[1], x, y, z, vx, vy, vz, w, id);
     GX_LAUNCHED(c);
     return GX_OK;
 }

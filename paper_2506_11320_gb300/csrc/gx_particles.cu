@@ -9,25 +9,30 @@
 //      alpha from B^{n+1}: charge, mass and momentum weights, the current
 //      alpha (v - u_ref) and the mass-matrix sums alpha W_g W_g' (Eq. 33-35);
 //   3. re-binning into the other copy of the particle arrays: a cell's stayers
-//      take consecutive slots at the bottom of its new bin (one atomic per
-//      64-particle chunk), particles that leave take slots at the top of their
-//      new cell's bin (see bin_front / bin_back).
+//      fill its new bin from the bottom in order, particles that leave take
+//      slots at the top of their new cell's bin (see bin_front / bin_back).
 // k_pd<false> deposits without moving: the whole state (the deposit before
 // the first step), or, right after the push, only the particles that arrived
 // in each cell (the back segments of the new bins) into a second set of
 // records that the grid kernels add to the first.
 //
+// Particle layout: one 32-byte slot per particle, two float4
+// (ox, oy, vx, vy) and (vz, w, id bits, 0); cell c's bin is slots
+// [c cap, (c+1) cap).  A staged chunk of a bin is one contiguous bulk copy, a
+// particle that leaves its cell is one 32-byte sector written, and the
+// stayers of a chunk go out as contiguous runs of whole lines.
+//
 // Work decomposition (GB300-first): a persistent grid, one CTA of 8 warps per
 // SM; each warp is split into 4 groups of 8 lanes and a group owns one cell at
-// a time (32 consecutive cells per CTA batch).  The particle arrays of a cell
-// are streamed into shared memory in 64-particle chunks by the bulk-copy (TMA)
-// engine, double buffered per group and signalled through mbarriers (bounded
-// waits), so the next chunk's loads overlap the current chunk's arithmetic.
-// The mover and the stayer deposit run with no warp collectives; each lane
-// accumulates its particles' 109 partial sums in registers and at the end of
-// the cell the 8 lanes are reduced through shared memory and the record is
-// stored with plain stores.  The FP32 particle arithmetic stays on the CUDA
-// cores: it is a scatter, not a dense contraction.
+// a time (32 consecutive cells per CTA batch).  A cell's bin is streamed into
+// shared memory in 64-particle chunks by the bulk-copy (TMA) engine, double
+// buffered per group and signalled through mbarriers (bounded waits), so the
+// next chunk's loads overlap the current chunk's arithmetic.  The mover and
+// the stayer deposit run with no warp collectives; each lane accumulates its
+// particles' 109 partial sums in registers and at the end of the cell the 8
+// lanes are reduced through shared memory and the record is stored with plain
+// stores.  The FP32 particle arithmetic stays on the CUDA cores: it is a
+// scatter, not a dense contraction.
 #include <cub/cub.cuh>
 
 #include "gx_internal.cuh"
@@ -39,38 +44,38 @@ constexpr int kGroup = 8;                         // lanes per cell group
 constexpr int kGroups = kThreads / kGroup;        // 32 cells per CTA batch
 constexpr int kChunk = 64;                        // particles per staged chunk
 constexpr int kPerLane = kChunk / kGroup;         // 8
-constexpr int kMaxF = 7;                          // ox oy vx vy vz w id
 constexpr int kScr = 56 * 33;                     // reduction scratch floats per warp
 constexpr unsigned kFull = 0xffffffffu;
 constexpr long long kSpinLimit = 1LL << 24;       // bounded mbarrier wait
-
-// staged field order (the bulk copies fill one 64-float row per field)
-enum { SF_OX = 0, SF_OY, SF_VX, SF_VY, SF_VZ, SF_W, SF_ID };
 
 struct P2 {
     int nx, ny;
     int64_t N;
     int cap;
     int nbatch;
-    int nf;             // staged fields (6, or 7 with ids)
     float dtdx, dtdy;
-    float beta;         // q dt / (2 m)
-    float bc;           // beta / c
-    const float *in[kMaxF];      // current copy, in staged (SF_*) order
+    float beta;                  // q dt / (2 m)
+    float bc;                    // beta / c
+    const float4 *in;            // current copy: 2 float4 per slot
     const int *cnt_in;
-    float *out[kMaxF];           // other copy, in staged (SF_*) order
+    float4 *out;                 // other copy
     int *cnt_out;
     const float4 *mE, *mB;       // mover: E^{n+theta}, B^n (node averaged)
     const float4 *dB, *dU;       // deposit: B for alpha, reference velocity u_ref
-    float *rec;                  // [N][112] for this species
+    float *rec;                  // [112][N] for this species
     DevFlags *flags;
     int arrivals;                // deposit only the back segments (the particles that arrived)
 };
 
-size_t pd_smem_bytes() {
-    return 512 + (size_t)kGroups * 2 * kMaxF * kChunk * sizeof(float) + (size_t)kGroups * kChunk * sizeof(int) +
-           (size_t)8 * kScr * sizeof(float);
-}
+// dynamic shared memory: mbarriers, staging [group][buffer][slot][2] float4,
+// destination codes [group][slot], compaction maps [group][slot] (the slot of
+// the t-th stayer), reduction scratch [warp][kScr]
+constexpr size_t kBarBytes = 512;
+constexpr size_t kBufBytes = (size_t)kGroups * 2 * kChunk * 2 * sizeof(float4);
+constexpr size_t kCodeBytes = (size_t)kGroups * kChunk * sizeof(int);
+constexpr size_t kMapBytes = (size_t)kGroups * kChunk;
+constexpr size_t kScrBytes = (size_t)8 * kScr * sizeof(float);
+size_t pd_smem_bytes() { return kBarBytes + kBufBytes + kCodeBytes + kMapBytes + kScrBytes; }
 
 // ------------------------------------------------------------ PTX helpers
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -164,10 +169,10 @@ __device__ __forceinline__ void deposit_one(RegAcc &acc, float x, float y, float
 }
 
 // Sum the 8 lanes of every group of the warp through the warp's shared scratch
-// (stride 33: conflict-free writes and column sums) and store (or add) the
-// record of the group's cell.
+// (stride 33: conflict-free writes and column sums) and store the record of
+// the group's cell.
 __device__ __forceinline__ void group_reduce_store(const RegAcc &acc, float *scr, int lane, int lig, int gshift,
-                                                   float *dst, int64_t stride, bool add, bool active) {
+                                                   float *dst, int64_t stride, bool active) {
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
 #pragma unroll
@@ -177,23 +182,13 @@ __device__ __forceinline__ void group_reduce_store(const RegAcc &acc, float *scr
 #pragma unroll
             for (int t = 0; t < 7; ++t) {
                 const int k = lig * 7 + t;
-                float s = 0.f;
-#pragma unroll
-                for (int l = 0; l < kGroup; ++l) s += scr[k * 33 + gshift + l];
-                float *d = dst + (size_t)(h * 56 + k) * stride;
-                if (add) *d += s;
-                else *d = s;
+                const float *c = scr + k * 33 + gshift;
+                const float s = ((c[0] + c[1]) + (c[2] + c[3])) + ((c[4] + c[5]) + (c[6] + c[7]));
+                dst[(size_t)(h * 56 + k) * stride] = s;
             }
         }
         __syncwarp();
     }
-}
-
-// position of the t-th set bit (t counted from 0) of a 64-bit mask
-__device__ __forceinline__ int nth_bit64(unsigned long long m, int t) {
-    const unsigned lo = (unsigned)m, hi = (unsigned)(m >> 32);
-    const int nlo = __popc(lo);
-    return t < nlo ? (int)__fns(lo, 0, t + 1) : 32 + (int)__fns(hi, 0, t - nlo + 1);
 }
 
 __device__ __forceinline__ void corner_nodes(int ci, int cj, int nx, int ny, int64_t nd[4]) {
@@ -231,16 +226,18 @@ template <bool PUSH>
 __global__ void __launch_bounds__(kThreads, 1) k_pd(P2 p) {
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem);                         // [groups][2]
-    float *bufs = reinterpret_cast<float *>(smem + 512);                          // [groups][2][kMaxF][64]
-    int *codes = reinterpret_cast<int *>(bufs + (size_t)kGroups * 2 * kMaxF * kChunk);  // [groups][64]
-    float *scr_all = reinterpret_cast<float *>(codes + kGroups * kChunk);         // [8][kScr]
+    float4 *bufs = reinterpret_cast<float4 *>(smem + kBarBytes);                  // [groups][2][64][2]
+    int *codes = reinterpret_cast<int *>(smem + kBarBytes + kBufBytes);           // [groups][64]
+    unsigned char *maps = smem + kBarBytes + kBufBytes + kCodeBytes;             // [groups][64]
+    float *scr_all = reinterpret_cast<float *>(smem + kBarBytes + kBufBytes + kCodeBytes + kMapBytes);  // [8][kScr]
 
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
     const int g = tid / kGroup, lig = tid % kGroup;
     const int gshift = (lane / kGroup) * kGroup;
-    float *mybuf = bufs + (size_t)g * 2 * kMaxF * kChunk;
+    float4 *mybuf = bufs + (size_t)g * 2 * kChunk * 2;
     int *mycode = codes + g * kChunk;
+    unsigned char *mymap = maps + g * kChunk;
     uint64_t *mybar = bars + 2 * g;
     float *scr = scr_all + (size_t)warp * kScr;
 
@@ -269,9 +266,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_pd(P2 p) {
         }
         return false;
     };
-    // stream chunk `ich` of the cell: only the slots of its own segment,
-    // widened to 16-byte boundaries (4 slots), into the same positions of the
-    // staging row
+    // stream chunk `ich` of the cell: only the slots of its own segment (whole
+    // 32-byte slots are 16-byte aligned), into the same positions of the
+    // staging buffer
     auto issue = [&]() {
         const int slot = issued & 1;
         const int64_t cell = (int64_t)ib * kGroups + g;
@@ -279,14 +276,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_pd(P2 p) {
         int lo = 0, hi = kChunk;
         if (ich < (fr + kChunk - 1) / kChunk) hi = min(kChunk, fr - sbase);
         else lo = max(0, p.cap - bin_back(iword) - sbase);
-        lo &= ~3;
-        hi = (hi + 3) & ~3;
-        const uint32_t bytes = (uint32_t)((hi - lo) * sizeof(float));
-        const size_t off = (size_t)cell * p.cap + sbase + lo;
+        const uint32_t bytes = (uint32_t)((hi - lo) * 2 * sizeof(float4));
+        const float4 *src = p.in + 2 * ((size_t)cell * p.cap + sbase + lo);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_expect_tx(&mybar[slot], bytes * (uint32_t)p.nf);
-        for (int f = 0; f < p.nf; ++f)
-            bulk_g2s(mybuf + (size_t)(slot * kMaxF + f) * kChunk + lo, p.in[f] + off, bytes, &mybar[slot]);
+        mbar_expect_tx(&mybar[slot], bytes);
+        bulk_g2s(mybuf + (size_t)(slot * kChunk + lo) * 2, src, bytes, &mybar[slot]);
         ++issued;
         ++ich;
     };
@@ -314,6 +308,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_pd(P2 p) {
         }
         RegAcc acc;
         acc.zero();
+        int fbase = 0;                      // stayers written to this cell's new bin so far
 
         for (int ch = 0; ch < wmax; ++ch) {
             const bool has = ch < nch;
@@ -321,7 +316,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_pd(P2 p) {
             bool ok = true;
             if (has) ok = mbar_wait_bounded(&mybar[slot], (uint32_t)((cons >> 1) & 1));
             if (__any_sync(kFull, !ok)) { abort = true; break; }
-            float *cbuf = mybuf + (size_t)slot * kMaxF * kChunk;
+            float4 *cbuf = mybuf + (size_t)slot * kChunk * 2;
             const int sbase = has ? chunk_base(ch, bin_front(word), p.cap) : 0;
             // particles of this chunk: slots of its own segment only
             unsigned long long vmask = 0ull;
@@ -332,7 +327,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_pd(P2 p) {
             }
             unsigned long long smask = vmask;   // stayers (all of them without the push)
             int old[kPerLane];                  // slot reservations of this lane's leavers
-            int base = 0, fits = 1;
             if (PUSH) {
                 // ---- A1: mover.  New state written back into the staged chunk,
                 // the destination cell of each leaver into the code row.
@@ -345,8 +339,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_pd(P2 p) {
                     const int j = k * kGroup + lig;
                     bool leave = false;
                     if ((vmask >> j) & 1ull) {
-                        float x = cbuf[SF_OX * kChunk + j], y = cbuf[SF_OY * kChunk + j];
-                        float vx = cbuf[SF_VX * kChunk + j], vy = cbuf[SF_VY * kChunk + j], vz = cbuf[SF_VZ * kChunk + j];
+                        const float4 s0 = cbuf[2 * j];
+                        float x = s0.x, y = s0.y, vx = s0.z, vy = s0.w;
+                        float vz = reinterpret_cast<const float *>(cbuf + 2 * j + 1)[0];
                         const float wx0 = 1.f - x, wy0 = 1.f - y;
                         const float W0 = wx0 * wy0, W1 = x * wy0, W2 = wx0 * y, W3 = x * y;
                         const float ex = W0 * mE[0].x + W1 * mE[1].x + W2 * mE[2].x + W3 * mE[3].x;
@@ -379,8 +374,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_pd(P2 p) {
                         int dxg = ci + sx, dyg = cj + sy;
                         dxg = dxg < 0 ? dxg + p.nx : (dxg >= p.nx ? dxg - p.nx : dxg);
                         dyg = dyg < 0 ? dyg + p.ny : (dyg >= p.ny ? dyg - p.ny : dyg);
-                        cbuf[SF_OX * kChunk + j] = x; cbuf[SF_OY * kChunk + j] = y;
-                        cbuf[SF_VX * kChunk + j] = vx; cbuf[SF_VY * kChunk + j] = vy; cbuf[SF_VZ * kChunk + j] = vz;
+                        cbuf[2 * j] = make_float4(x, y, vx, vy);
+                        reinterpret_cast<float *>(cbuf + 2 * j + 1)[0] = vz;
                         mycode[j] = dxg + p.nx * dyg;
                     }
                     if (leave) lv |= 1ull << j;
@@ -391,54 +386,73 @@ __global__ void __launch_bounds__(kThreads, 1) k_pd(P2 p) {
                 for (int o = 1; o < kGroup; o <<= 1) all |= __shfl_xor_sync(kFull, all, o);
                 smask = vmask & ~all;
                 __syncwarp();
-                // ---- B1: reserve the slots (results used only after the deposit)
-                const int ns = __popcll(smask);
-                if (has && lig == 0 && ns > 0) {
-                    const int o = atomicAdd(&p.cnt_out[cell], ns);
-                    base = bin_front(o);
-                    fits = bin_count(o) + ns <= p.cap;
-                }
+                // ---- B1: reserve the leavers' slots at the top of their new
+                // bins (the results are used only after the deposit)
 #pragma unroll
                 for (int k = 0; k < kPerLane; ++k) {
                     const int j = k * kGroup + lig;
                     old[k] = (lv >> j) & 1ull ? atomicAdd(&p.cnt_out[mycode[j]], 1 << 16) : 0;
                 }
             }
-            // ---- A2: deposit of the stayers (compacted, no idle lanes)
-            {
-                const int ns = __popcll(smask);
-                for (int t = lig; t < ns; t += kGroup) {
-                    const int j = nth_bit64(smask, t);
-                    deposit_one(acc, cbuf[SF_OX * kChunk + j], cbuf[SF_OY * kChunk + j], cbuf[SF_VX * kChunk + j],
-                                cbuf[SF_VY * kChunk + j], cbuf[SF_VZ * kChunk + j], cbuf[SF_W * kChunk + j], cB, cU,
-                                p.bc);
-                }
-            }
-            // ---- B2: write the chunk into the other copy.  Stayers take
-            // consecutive bottom slots of this cell's new bin, leavers the top
-            // slots reserved in B1.
+            // ---- A2: deposit of the stayers (compacted, no idle lanes).  With
+            // the push the stayers are scattered over the chunk: each lane
+            // enters its own slots in the group's compaction map first.
+            const int ns = __popcll(smask);
+            const int vlo = vmask ? __ffsll((long long)vmask) - 1 : 0;
             if (PUSH) {
-                base = __shfl_sync(kFull, base, gshift);
-                fits = __shfl_sync(kFull, fits, gshift);
 #pragma unroll
                 for (int k = 0; k < kPerLane; ++k) {
                     const int j = k * kGroup + lig;
-                    int64_t o = -1;
-                    if ((smask >> j) & 1ull) {
-                        const int rank = __popcll(smask & ((1ull << j) - 1ull));
-                        if (fits) o = (int64_t)cell * p.cap + base + rank;
-                        else atomicExch(&p.flags->overflow, 1);
-                    } else if ((vmask >> j) & 1ull) {
-                        const int w0 = old[k];
-                        if (bin_count(w0) + 1 <= p.cap) o = (int64_t)mycode[j] * p.cap + p.cap - 1 - bin_back(w0);
-                        else atomicExch(&p.flags->overflow, 1);
-                    }
-                    if (o >= 0) {
+                    if ((smask >> j) & 1ull) mymap[__popcll(smask & ((1ull << j) - 1ull))] = (unsigned char)j;
+                }
+                __syncwarp();
+            }
+            for (int t = lig; t < ns; t += kGroup) {
+                const int j = PUSH ? (int)mymap[t] : vlo + t;
+                const float4 s0 = cbuf[2 * j];
+                const float2 s1 = reinterpret_cast<const float2 *>(cbuf + 2 * j + 1)[0];
+                deposit_one(acc, s0.x, s0.y, s0.z, s0.w, s1.x, s1.y, cB, cU, p.bc);
+            }
+            // ---- B2: write the chunk into the other copy
+            if (PUSH) {
+                // stayers: bottom of this cell's new bin, in order.  The warp
+                // writes one group's run at a time, 16 slots (512 contiguous
+                // bytes) per store instruction.
+                const int boff = (int)(cbuf - bufs);
+                const int moff = (int)(mymap - maps);
 #pragma unroll
-                        for (int f = 0; f < kMaxF; ++f)
-                            if (f < p.nf) p.out[f][o] = cbuf[f * kChunk + j];
+                for (int gi = 0; gi < 4; ++gi) {
+                    const int src = gi * kGroup;
+                    const int ns_g = __shfl_sync(kFull, ns, src);
+                    if (ns_g == 0) continue;
+                    const int base_g = __shfl_sync(kFull, fbase, src);
+                    const long long cell_g = __shfl_sync(kFull, (long long)cell, src);
+                    const float4 *gbuf = bufs + __shfl_sync(kFull, boff, src);
+                    const unsigned char *gmap = maps + __shfl_sync(kFull, moff, src);
+                    for (int r0 = 0; r0 < ns_g; r0 += 16) {
+                        const int t = r0 + (lane >> 1), half = lane & 1;
+                        if (t < ns_g) {
+                            const int j = gmap[t];
+                            p.out[2 * ((size_t)cell_g * p.cap + base_g + t) + half] = gbuf[2 * j + half];
+                        }
                     }
                 }
+                // leavers: the slot reserved in B1 (one 32-byte sector each)
+#pragma unroll
+                for (int k = 0; k < kPerLane; ++k) {
+                    const int j = k * kGroup + lig;
+                    if (((vmask >> j) & 1ull) && !((smask >> j) & 1ull)) {
+                        const int back = bin_back(old[k]);
+                        if (back < p.cap) {
+                            const size_t o = (size_t)mycode[j] * p.cap + p.cap - 1 - back;
+                            p.out[2 * o] = cbuf[2 * j];
+                            p.out[2 * o + 1] = cbuf[2 * j + 1];
+                        } else {
+                            atomicExch(&p.flags->overflow, 1);
+                        }
+                    }
+                }
+                fbase += ns;
             }
             __syncwarp();
             if (has) {
@@ -447,7 +461,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_pd(P2 p) {
             }
         }
         if (abort) break;
-        group_reduce_store(acc, scr, lane, lig, gshift, p.rec + cell, p.N, false, valid);
+        // the stayers' count (the bottom segment) of this cell's new bin
+        if (PUSH && valid && lig == 0 && fbase > 0) atomicAdd(&p.cnt_out[cell], fbase);
+        group_reduce_store(acc, scr, lane, lig, gshift, p.rec + cell, p.N, valid);
     }
     if (abort) {
         if (lane == 0) atomicExch(&p.flags->timeout, 1);
@@ -457,13 +473,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_pd(P2 p) {
     }
 }
 
+// largest bin count after a push; a bin whose two segments met has lost
+// particles (stayers and arrivals wrote over each other)
 __global__ void k_max_count(const int *cnt, int64_t n, int cap, DevFlags *f) {
     int m = 0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        m = max(m, bin_count(cnt[i]));
+    bool over = false;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int c = bin_count(cnt[i]);
+        m = max(m, c);
+        over |= cap > 0 && c > cap;
+    }
     m = __reduce_max_sync(kFull, m);
     if ((threadIdx.x & 31) == 0) atomicMax(&f->maxcount, m);
-    (void)cap;
+    if (over) atomicExch(&f->overflow, 1);
 }
 
 __global__ void k_counts(const int *cnt, int64_t n, int cap, int *out) {
@@ -494,35 +516,33 @@ __global__ void k_locate(int64_t n, const double *x, const double *y, int nx, in
 
 __global__ void k_scatter(int64_t n, const int *cell, const float *ox, const float *oy, const float *vx,
                           const float *vy, const float *vz, const float *w, const int32_t *id, int cap,
-                          int *cursor, float *const *out, int track, DevFlags *f) {
+                          int *cursor, float4 *out, int track, DevFlags *f) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const int c = cell[i];
         const int slot = atomicAdd(&cursor[c], 1);
         if (slot >= cap) { atomicExch(&f->overflow, 1); continue; }
         const size_t o = (size_t)c * cap + slot;
-        out[PF_OX][o] = ox[i]; out[PF_OY][o] = oy[i];
-        out[PF_VX][o] = vx[i]; out[PF_VY][o] = vy[i]; out[PF_VZ][o] = vz[i];
-        out[PF_W][o] = w[i];
-        if (track) out[PF_ID][o] = __int_as_float(id ? id[i] : (int32_t)i);
+        const int idv = track ? (id ? id[i] : (int32_t)i) : 0;
+        out[2 * o] = make_float4(ox[i], oy[i], vx[i], vy[i]);
+        out[2 * o + 1] = make_float4(vz[i], w[i], __int_as_float(idv), 0.f);
     }
 }
 
 // copy bins into bins of a new capacity (both segments into the new front)
-__global__ void k_rebin_copy(int64_t ncell, int oldcap, int newcap, const int *cnt, int *newcnt, float *const *src,
-                             float *const *dst, int nf) {
+__global__ void k_rebin_copy(int64_t ncell, int oldcap, int newcap, const int *cnt, int *newcnt, const float4 *src,
+                             float4 *dst) {
     const int64_t c = blockIdx.x;
     if (c >= ncell) return;
     const int word = clamp_word(cnt[c], oldcap);
     const int m = min(bin_count(word), newcap);
-    for (int f = 0; f < nf; ++f) {
-        if (!src[f]) continue;
-        for (int i = threadIdx.x; i < m; i += blockDim.x)
-            dst[f][(size_t)c * newcap + i] = src[f][(size_t)c * oldcap + bin_slot(word, i, oldcap)];
+    for (int i = threadIdx.x; i < 2 * m; i += blockDim.x) {
+        const size_t s = (size_t)c * oldcap + bin_slot(word, i >> 1, oldcap);
+        dst[2 * ((size_t)c * newcap + (i >> 1)) + (i & 1)] = src[2 * s + (i & 1)];
     }
     if (threadIdx.x == 0) newcnt[c] = m;
 }
 
-__global__ void k_gather_out(int64_t ncell, int cap, const int *cnt, const int *offs, float *const *src, int nx,
+__global__ void k_gather_out(int64_t ncell, int cap, const int *cnt, const int *offs, const float4 *src, int nx,
                              int ny, double dx, double dy, double *x, double *y, double *z, float *vx, float *vy,
                              float *vz, float *w, int32_t *id) {
     const int64_t c = blockIdx.x;
@@ -532,15 +552,16 @@ __global__ void k_gather_out(int64_t ncell, int cap, const int *cnt, const int *
     const int cx = (int)(c % nx), cy = (int)(c / nx);
     for (int i = threadIdx.x; i < m; i += blockDim.x) {
         const size_t s = (size_t)c * cap + bin_slot(word, i, cap);
+        const float4 a = src[2 * s], b = src[2 * s + 1];
         const int o = offs[c] + i;
-        if (x) x[o] = (cx + (double)src[PF_OX][s]) * dx;
-        if (y) y[o] = ny > 1 ? (cy + (double)src[PF_OY][s]) * dy : 0.0;
+        if (x) x[o] = (cx + (double)a.x) * dx;
+        if (y) y[o] = ny > 1 ? (cy + (double)a.y) * dy : 0.0;
         if (z) z[o] = 0.0;
-        if (vx) vx[o] = src[PF_VX][s];
-        if (vy) vy[o] = src[PF_VY][s];
-        if (vz) vz[o] = src[PF_VZ][s];
-        if (w) w[o] = src[PF_W][s];
-        if (id && src[PF_ID]) id[o] = __float_as_int(src[PF_ID][s]);
+        if (vx) vx[o] = a.z;
+        if (vy) vy[o] = a.w;
+        if (vz) vz[o] = b.x;
+        if (w) w[o] = b.y;
+        if (id) id[o] = __float_as_int(b.z);
     }
 }
 
@@ -554,12 +575,8 @@ int alloc_bins(gx_ctx *c, int s, int cap) {
     Species &S = c->sp[s];
     const size_t nslot = (size_t)c->N * cap;
     for (int b = 0; b < 2; ++b) {
-        for (int f = 0; f < PF_COUNT; ++f) {
-            S.f[b][f] = nullptr;
-            if (f == PF_OZ) continue;                          // 2D: no z offset
-            if (f == PF_ID && !c->cfg.track_ids) continue;
-            GX_CHECK(c, cudaMalloc(&S.f[b][f], nslot * sizeof(float)));
-        }
+        S.p[b] = nullptr;
+        GX_CHECK(c, cudaMalloc(&S.p[b], nslot * 2 * sizeof(float4)));
         GX_CHECK(c, cudaMalloc(&S.cnt[b], c->N * sizeof(int)));
         GX_CHECK(c, cudaMemset(S.cnt[b], 0, c->N * sizeof(int)));
     }
@@ -569,10 +586,8 @@ int alloc_bins(gx_ctx *c, int s, int cap) {
 
 void free_bins(Species &S) {
     for (int b = 0; b < 2; ++b) {
-        for (int f = 0; f < PF_COUNT; ++f) {
-            if (S.f[b][f]) cudaFree(S.f[b][f]);
-            S.f[b][f] = nullptr;
-        }
+        if (S.p[b]) cudaFree(S.p[b]);
+        S.p[b] = nullptr;
         if (S.cnt[b]) cudaFree(S.cnt[b]);
         S.cnt[b] = nullptr;
     }
@@ -619,17 +634,14 @@ int gx_bin_particles(gx_ctx *c, int s, int64_t n, const double *x, const double 
     if (cap >= 32768) { c->err = "more than 32767 particles per cell bin"; return GX_EINVAL; }
     int rc = alloc_bins(c, s, cap);
     if (rc) return rc;
-    float **dout = nullptr;
-    GX_CHECK(c, cudaMalloc(&dout, PF_COUNT * sizeof(float *)));
-    GX_CHECK(c, cudaMemcpyAsync(dout, S.f[c->cur], PF_COUNT * sizeof(float *), cudaMemcpyHostToDevice, st));
     GX_CHECK(c, cudaMemsetAsync(S.cnt[c->cur], 0, c->N * sizeof(int), st));
     if (n > 0) {
-        k_scatter<<<grid_for(n), 256, 0, st>>>(n, cell, ox, oy, vx, vy, vz, w, id, cap, S.cnt[c->cur], dout,
+        k_scatter<<<grid_for(n), 256, 0, st>>>(n, cell, ox, oy, vx, vy, vz, w, id, cap, S.cnt[c->cur], S.p[c->cur],
                                                 c->cfg.track_ids, c->dflags);
         GX_LAUNCHED(c);
     }
     GX_CHECK(c, cudaStreamSynchronize(st));
-    cudaFree(dout); cudaFree(cell); cudaFree(ox); cudaFree(oy); cudaFree(count);
+    cudaFree(cell); cudaFree(ox); cudaFree(oy); cudaFree(count);
     return GX_OK;
 }
 
@@ -640,16 +652,10 @@ int gx_regrow_bins(gx_ctx *c, int s, int newcap, cudaStream_t st) {
     Species old = S;
     int rc = alloc_bins(c, s, newcap);
     if (rc) return rc;
-    float **dsrc = nullptr, **ddst = nullptr;
-    GX_CHECK(c, cudaMalloc(&dsrc, PF_COUNT * sizeof(float *)));
-    GX_CHECK(c, cudaMalloc(&ddst, PF_COUNT * sizeof(float *)));
-    GX_CHECK(c, cudaMemcpyAsync(dsrc, old.f[c->cur], PF_COUNT * sizeof(float *), cudaMemcpyHostToDevice, st));
-    GX_CHECK(c, cudaMemcpyAsync(ddst, S.f[c->cur], PF_COUNT * sizeof(float *), cudaMemcpyHostToDevice, st));
-    k_rebin_copy<<<(unsigned)c->N, 128, 0, st>>>(c->N, old.cap, newcap, old.cnt[c->cur], S.cnt[c->cur], dsrc, ddst,
-                                                  PF_COUNT);
+    k_rebin_copy<<<(unsigned)c->N, 128, 0, st>>>(c->N, old.cap, newcap, old.cnt[c->cur], S.cnt[c->cur],
+                                                  old.p[c->cur], S.p[c->cur]);
     GX_LAUNCHED(c);
     GX_CHECK(c, cudaStreamSynchronize(st));
-    cudaFree(dsrc); cudaFree(ddst);
     free_bins(old);
     return GX_OK;
 }
@@ -668,23 +674,19 @@ static int launch_pd(gx_ctx *c, bool push, cudaStream_t st) {
     const int nbatch = (int)((c->N + kGroups - 1) / kGroups);
     const int grid = std::max(1, std::min(nbatch, nsm));
     const int nxt = 1 - c->cur;
-    const int sf2pf[kMaxF] = {PF_OX, PF_OY, PF_VX, PF_VY, PF_VZ, PF_W, PF_ID};
     for (int s = 0; s < c->nspecies; ++s) {
         Species &S = c->sp[s];
         P2 p{};
         p.nx = c->n[0]; p.ny = c->n[1]; p.N = c->N;
         p.cap = S.cap;
         p.nbatch = nbatch;
-        p.nf = c->cfg.track_ids ? 7 : 6;
         p.dtdx = (float)(c->cfg.dt / c->cfg.dx[0]);
         p.dtdy = (float)(c->cfg.dt / c->cfg.dx[1]);
         const double beta = S.q * c->cfg.dt / (2.0 * S.m);
         p.beta = (float)beta;
         p.bc = (float)(beta / c->cfg.c);
-        for (int f = 0; f < kMaxF; ++f) {
-            p.in[f] = S.f[c->cur][sf2pf[f]];
-            p.out[f] = S.f[nxt][sf2pf[f]];
-        }
+        p.in = S.p[c->cur];
+        p.out = S.p[nxt];
         p.cnt_in = S.cnt[c->cur];
         p.cnt_out = S.cnt[nxt];
         p.rec = c->rec + (size_t)s * c->N * Rec<2>::SIZE;
@@ -704,7 +706,7 @@ static int launch_pd(gx_ctx *c, bool push, cudaStream_t st) {
             // second set of records (every cell written, zero if none arrived)
             P2 q = p;
             q.arrivals = 1;
-            for (int f = 0; f < kMaxF; ++f) q.in[f] = p.out[f];
+            q.in = p.out;
             q.cnt_in = p.cnt_out;
             q.mE = nullptr; q.mB = nullptr;
             q.rec = c->rec2 + (size_t)s * c->N * Rec<2>::SIZE;
@@ -744,14 +746,11 @@ int gx_particles_out(gx_ctx *c, int s, double *x, double *y, double *z, float *v
     cub::DeviceScan::ExclusiveSum(nullptr, tmpb, counts, offs, (int)c->N, st);
     GX_CHECK(c, cudaMalloc(&tmp, tmpb + 16));
     GX_CHECK(c, cub::DeviceScan::ExclusiveSum(tmp, tmpb, counts, offs, (int)c->N, st));
-    float **dsrc = nullptr;
-    GX_CHECK(c, cudaMalloc(&dsrc, PF_COUNT * sizeof(float *)));
-    GX_CHECK(c, cudaMemcpyAsync(dsrc, S.f[c->cur], PF_COUNT * sizeof(float *), cudaMemcpyHostToDevice, st));
-    k_gather_out<<<(unsigned)c->N, 128, 0, st>>>(c->N, S.cap, S.cnt[c->cur], offs, dsrc, c->n[0], c->n[1],
+    k_gather_out<<<(unsigned)c->N, 128, 0, st>>>(c->N, S.cap, S.cnt[c->cur], offs, S.p[c->cur], c->n[0], c->n[1],
                                                   c->cfg.dx[0], c->cfg.dx[1], x, y, z, vx, vy, vz, w, id);
     GX_LAUNCHED(c);
     GX_CHECK(c, cudaStreamSynchronize(st));
-    cudaFree(offs); cudaFree(counts); cudaFree(tmp); cudaFree(dsrc);
+    cudaFree(offs); cudaFree(counts); cudaFree(tmp);
     return GX_OK;
 }
 
