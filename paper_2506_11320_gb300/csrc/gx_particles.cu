@@ -118,13 +118,38 @@ __device__ __forceinline__ void alpha_tensor(float bx, float by, float bz, float
     al[6] = (by + bz * bx) * inv;   al[7] = (bz * by - bx) * inv; al[8] = (1.0f + bz * bz) * inv;
 }
 
+// The 109 partial sums of one lane, held as 55 register pairs so that the
+// deposit can use the paired FP32 FMA (two rounded FMAs per instruction,
+// bit-identical to two fmaf):
+//   p[0..1]    RHO corner pairs (a0,a1), (a2,a3)
+//   p[2..7]    MV  [component][corner pair]
+//   p[8..13]   J   [component][corner pair]
+//   p[14..49]  M   [pair class j][alpha entries (0,1) (2,3) (4,5) (6,7)]
+//   p[50..54]  M   alpha entry 8 for pair classes (0,1) (2,3) (4,5) (6,7) (8,-)
 struct RegAcc {
-    float v[Rec<2>::SIZE];
+    float2 p[55];
     __device__ __forceinline__ void zero() {
 #pragma unroll
-        for (int k = 0; k < Rec<2>::SIZE; ++k) v[k] = 0.f;
+        for (int k = 0; k < 55; ++k) p[k] = make_float2(0.f, 0.f);
+    }
+    // record entry k (Rec<2> layout); k is a compile-time constant after unrolling
+    __device__ __forceinline__ float get(int k) const {
+        int idx, comp;
+        if (k < Rec<2>::MV) { idx = k >> 1; comp = k & 1; }
+        else if (k < Rec<2>::J) { const int t = k - Rec<2>::MV, a = t / 3, c = t % 3; idx = 2 + 2 * c + (a >> 1); comp = a & 1; }
+        else if (k < Rec<2>::M) { const int t = k - Rec<2>::J, a = t / 3, c = t % 3; idx = 8 + 2 * c + (a >> 1); comp = a & 1; }
+        else if (k < Rec<2>::USED) {
+            const int t = k - Rec<2>::M, j = t / 9, e = t % 9;
+            if (e < 8) { idx = 14 + 4 * j + (e >> 1); comp = e & 1; }
+            else { idx = 50 + (j >> 1); comp = j & 1; }
+        } else {
+            return 0.f;
+        }
+        return comp ? p[idx].y : p[idx].x;
     }
 };
+
+__device__ __forceinline__ float2 dup2(float v) { return make_float2(v, v); }
 
 // Deposit of one particle at cell-local offsets (x, y) with the corner values
 // of B (for alpha) and u_ref: the partial sums of the record layout Rec<2>.
@@ -144,28 +169,33 @@ __device__ __forceinline__ void deposit_one(RegAcc &acc, float x, float y, float
     const float jx = w * (al[0] * dx_ + al[1] * dy_ + al[2] * dz_);
     const float jy = w * (al[3] * dx_ + al[4] * dy_ + al[5] * dz_);
     const float jz = w * (al[6] * dx_ + al[7] * dy_ + al[8] * dz_);
-    const float wvx = w * vx, wvy = w * vy, wvz = w * vz;
+    const float wv[3] = {w * vx, w * vy, w * vz};
+    const float jv[3] = {jx, jy, jz};
+    const float2 W01 = make_float2(W[0], W[1]), W23 = make_float2(W[2], W[3]);
+    acc.p[0] = __ffma2_rn(dup2(w), W01, acc.p[0]);
+    acc.p[1] = __ffma2_rn(dup2(w), W23, acc.p[1]);
 #pragma unroll
-    for (int a = 0; a < 4; ++a) {
-        acc.v[Rec<2>::RHO + a] = fmaf(w, W[a], acc.v[Rec<2>::RHO + a]);
-        acc.v[Rec<2>::MV + 3 * a + 0] = fmaf(wvx, W[a], acc.v[Rec<2>::MV + 3 * a + 0]);
-        acc.v[Rec<2>::MV + 3 * a + 1] = fmaf(wvy, W[a], acc.v[Rec<2>::MV + 3 * a + 1]);
-        acc.v[Rec<2>::MV + 3 * a + 2] = fmaf(wvz, W[a], acc.v[Rec<2>::MV + 3 * a + 2]);
-        acc.v[Rec<2>::J + 3 * a + 0] = fmaf(jx, W[a], acc.v[Rec<2>::J + 3 * a + 0]);
-        acc.v[Rec<2>::J + 3 * a + 1] = fmaf(jy, W[a], acc.v[Rec<2>::J + 3 * a + 1]);
-        acc.v[Rec<2>::J + 3 * a + 2] = fmaf(jz, W[a], acc.v[Rec<2>::J + 3 * a + 2]);
+    for (int c = 0; c < 3; ++c) {
+        acc.p[2 + 2 * c] = __ffma2_rn(dup2(wv[c]), W01, acc.p[2 + 2 * c]);
+        acc.p[3 + 2 * c] = __ffma2_rn(dup2(wv[c]), W23, acc.p[3 + 2 * c]);
+        acc.p[8 + 2 * c] = __ffma2_rn(dup2(jv[c]), W01, acc.p[8 + 2 * c]);
+        acc.p[9 + 2 * c] = __ffma2_rn(dup2(jv[c]), W23, acc.p[9 + 2 * c]);
     }
     const float X[3] = {w * wx0 * wx0, w * wx0 * wx1, w * wx1 * wx1};
     const float Y[3] = {wy0 * wy0, wy0 * wy1, wy1 * wy1};
+    float pw[9];
 #pragma unroll
-    for (int jy_ = 0; jy_ < 3; ++jy_)
+    for (int j = 0; j < 9; ++j) pw[j] = X[j % 3] * Y[j / 3];
+    const float2 al2[4] = {make_float2(al[0], al[1]), make_float2(al[2], al[3]), make_float2(al[4], al[5]),
+                           make_float2(al[6], al[7])};
 #pragma unroll
-        for (int jx_ = 0; jx_ < 3; ++jx_) {
-            const float pw = X[jx_] * Y[jy_];
-            float *m = acc.v + Rec<2>::M + 9 * (jx_ + 3 * jy_);
+    for (int j = 0; j < 9; ++j)
 #pragma unroll
-            for (int e = 0; e < 9; ++e) m[e] = fmaf(pw, al[e], m[e]);
-        }
+        for (int q = 0; q < 4; ++q) acc.p[14 + 4 * j + q] = __ffma2_rn(dup2(pw[j]), al2[q], acc.p[14 + 4 * j + q]);
+#pragma unroll
+    for (int j = 0; j < 8; j += 2)
+        acc.p[50 + j / 2] = __ffma2_rn(make_float2(pw[j], pw[j + 1]), dup2(al[8]), acc.p[50 + j / 2]);
+    acc.p[54].x = fmaf(pw[8], al[8], acc.p[54].x);
 }
 
 // Sum the 8 lanes of every group of the warp through the warp's shared scratch
@@ -176,7 +206,7 @@ __device__ __forceinline__ void group_reduce_store(const RegAcc &acc, float *scr
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
 #pragma unroll
-        for (int k = 0; k < 56; ++k) scr[k * 33 + lane] = acc.v[h * 56 + k];
+        for (int k = 0; k < 56; ++k) scr[k * 33 + lane] = acc.get(h * 56 + k);
         __syncwarp();
         if (active) {
 #pragma unroll
