@@ -70,9 +70,14 @@ struct P2 {
 // dynamic shared memory: mbarriers, staging [group][buffer][slot][2] float4,
 // destination codes [group][slot], compaction maps [group][slot] (the slot of
 // the t-th stayer), reduction scratch [warp][kScr]
+// The per-group strides are padded (16 bytes, 4 bytes) so that the 4 groups of
+// a warp, which touch the same slot positions of their own buffers, land on
+// different shared-memory banks.
+constexpr int kGroupBuf = 2 * kChunk * 2 + 1;     // float4 per group: 2 buffers of 64 slots + pad
+constexpr int kCodeStride = kChunk + 1;
 constexpr size_t kBarBytes = 512;
-constexpr size_t kBufBytes = (size_t)kGroups * 2 * kChunk * 2 * sizeof(float4);
-constexpr size_t kCodeBytes = (size_t)kGroups * kChunk * sizeof(int);
+constexpr size_t kBufBytes = (size_t)kGroups * kGroupBuf * sizeof(float4);
+constexpr size_t kCodeBytes = (size_t)kGroups * kCodeStride * sizeof(int);
 constexpr size_t kMapBytes = (size_t)kGroups * kChunk;
 constexpr size_t kScrBytes = (size_t)8 * kScr * sizeof(float);
 size_t pd_smem_bytes() { return kBarBytes + kBufBytes + kCodeBytes + kMapBytes + kScrBytes; }
@@ -265,8 +270,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_pd(P2 p) {
     const int lane = tid & 31, warp = tid >> 5;
     const int g = tid / kGroup, lig = tid % kGroup;
     const int gshift = (lane / kGroup) * kGroup;
-    float4 *mybuf = bufs + (size_t)g * 2 * kChunk * 2;
-    int *mycode = codes + g * kChunk;
+    float4 *mybuf = bufs + (size_t)g * kGroupBuf;
+    int *mycode = codes + g * kCodeStride;
     unsigned char *mymap = maps + g * kChunk;
     uint64_t *mybar = bars + 2 * g;
     float *scr = scr_all + (size_t)warp * kScr;
@@ -330,11 +335,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_pd(P2 p) {
         const int ci = valid ? (int)(cell % p.nx) : 0, cj = valid ? (int)(cell / p.nx) : 0;
         int64_t nd[4];
         corner_nodes(ci, cj, p.nx, p.ny, nd);
-        float4 cB[4], cU[4];
+        float4 cB[4], cU[4], mE[4], mB[4];
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
             cB[a] = __ldg(p.dB + nd[a]);
             cU[a] = __ldg(p.dU + nd[a]);
+            if (PUSH) { mE[a] = __ldg(p.mE + nd[a]); mB[a] = __ldg(p.mB + nd[a]); }
         }
         RegAcc acc;
         acc.zero();
@@ -360,9 +366,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_pd(P2 p) {
             if (PUSH) {
                 // ---- A1: mover.  New state written back into the staged chunk,
                 // the destination cell of each leaver into the code row.
-                float4 mE[4], mB[4];
-#pragma unroll
-                for (int a = 0; a < 4; ++a) { mE[a] = __ldg(p.mE + nd[a]); mB[a] = __ldg(p.mB + nd[a]); }
                 unsigned long long lv = 0ull;
 #pragma unroll 2
                 for (int k = 0; k < kPerLane; ++k) {
