@@ -184,7 +184,6 @@ void gx_destroy(gx_ctx *c) {
     for (auto p : fp)
         if (*p) cudaFree(*p);
     if (c->rec) cudaFree(c->rec);
-    if (c->rec2) cudaFree(c->rec2);
     if (c->gm) cudaFree(c->gm);
     if (c->gpart) cudaFree(c->gpart);
     if (c->zbuf) cudaFree(c->zbuf);
@@ -257,9 +256,7 @@ int gx_create(const gx_config *cfg, gx_ctx **out) {
         cudaMallocHost(&c->hflags, sizeof(DevFlags)) != cudaSuccess)
         return fail(GX_ENOMEM, "pinned host allocation failed");
     std::memset(c->hflags, 0, sizeof(DevFlags));
-    if ((rc = dalloc(c, &c->rec, (size_t)GX_MAX_SPECIES * N * Rec<2>::SIZE)) ||
-        (rc = dalloc(c, &c->rec2, (size_t)GX_MAX_SPECIES * N * Rec<2>::SIZE)))
-        return fail(rc, nullptr);
+    if ((rc = dalloc(c, &c->rec, (size_t)GX_MAX_SPECIES * N * Rec<2>::SIZE))) return fail(rc, nullptr);
     double *zero3[] = {c->E, c->B, c->Eth, c->Enew, c->Bnew, c->u, c->J, c->uref64};
     for (auto p : zero3)
         if (cudaMemset(p, 0, 3 * N * sizeof(double)) != cudaSuccess) return fail(GX_ECUDA, "cudaMemset failed");

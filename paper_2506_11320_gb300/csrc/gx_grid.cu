@@ -50,14 +50,12 @@ struct SpecK {
     float bqf[GX_MAX_SPECIES];
 };
 
-// Record value of species s, row k, cell: the push pass's record plus, after a
-// push, the arrivals pass's record (FP32, as the particle kernels wrote them).
+// Record value of species s, row k, cell (FP32, as the particle kernels wrote it).
 struct Recs {
-    const float *a, *b;       // [S][112][N]; b may be null
+    const float *a;           // [S][112][N]
     int64_t N;
     __device__ __forceinline__ float get(int s, int k, int64_t cell) const {
-        const size_t o = ((size_t)s * Rec<2>::SIZE + k) * N + cell;
-        return b ? a[o] + b[o] : a[o];
+        return a[((size_t)s * Rec<2>::SIZE + k) * N + cell];
     }
 };
 
@@ -100,28 +98,35 @@ __global__ void k_assemble_bulk(G2 g, SpecK sk, Recs R, double inv_dV, double *r
 
 // All passes of the digital filter (Sec. 1.4, Eq. 26: v* = phi v + (1-phi)/2
 // (v_{-d} + v_{+d}), phi = 0.5) on a 3-component node field, one 32x32 tile per
-// CTA with a halo of sum(d) nodes loaded once, every sweep done in shared
-// memory (x then y within each pass).  Strides alternate 1, 2, 1, ... when
-// `alternate`, else all 1.
+// CTA (32 x 8 threads, one component each) with a halo of sum(d) nodes loaded once, every sweep
+// done in shared memory (x then y within each pass).  Strides alternate
+// 1, 2, 1, ... when `alternate`, else all 1.  The sweeps run in FP32 (three
+// operations per node and sweep, a few 1e-7 of the smoothed value after five
+// passes); input and output stay FP64.
 constexpr int kFT = 32;
 constexpr int kFHaloMax = 16;
-__global__ void k_filter_fused(G2 g, const double *__restrict__ in, double *out, int npass, int alternate) {
-    extern __shared__ double fsh[];
+__device__ __forceinline__ int wrap_any(int i, int n) {
+    while (i < 0) i += n;
+    while (i >= n) i -= n;
+    return i;
+}
+__global__ void __launch_bounds__(256) k_filter_fused(G2 g, const double *__restrict__ in, double *out, int npass,
+                                                      int alternate) {
+    extern __shared__ float fsh[];
     int halo = 0;
     for (int p = 0; p < npass; ++p) halo += (alternate && (p & 1)) ? 2 : 1;
     const int hx = g.nx > 1 ? halo : 0, hy = g.ny > 1 ? halo : 0;
     const int W = kFT + 2 * hx, H = kFT + 2 * hy;
-    double *a = fsh, *b = fsh + W * H;
+    float *a = fsh, *b = fsh + W * H;
     const int x0 = blockIdx.x * kFT, y0 = blockIdx.y * kFT;
+    const int tx = threadIdx.x, ty = threadIdx.y;
     const int64_t N = g.N();
-    for (int comp = 0; comp < 3; ++comp) {
+    {
+        const int comp = blockIdx.z;       // one component per CTA layer
         const double *src = in + comp * N;
-        for (int t = threadIdx.x; t < W * H; t += blockDim.x) {
-            const int lx = t % W - hx, ly = t / W - hy;
-            int gx = (x0 + lx) % g.nx, gy = (y0 + ly) % g.ny;
-            gx = gx < 0 ? gx + g.nx : gx;
-            gy = gy < 0 ? gy + g.ny : gy;
-            a[t] = src[gx + (int64_t)g.nx * gy];
+        for (int ly = ty; ly < H; ly += 8) {
+            const int64_t row = (int64_t)g.nx * wrap_any(y0 + ly - hy, g.ny);
+            for (int lx = tx; lx < W; lx += 32) a[ly * W + lx] = (float)src[row + wrap_any(x0 + lx - hx, g.nx)];
         }
         __syncthreads();
         for (int p = 0; p < npass; ++p) {
@@ -129,21 +134,21 @@ __global__ void k_filter_fused(G2 g, const double *__restrict__ in, double *out,
             for (int axis = 0; axis < 2; ++axis) {
                 if ((axis == 0 && g.nx == 1) || (axis == 1 && g.ny == 1)) continue;
                 const int step = axis == 0 ? d : d * W;
-                for (int t = threadIdx.x; t < W * H; t += blockDim.x) {
-                    const int lx = t % W, ly = t / W;
-                    const bool inside = axis == 0 ? (lx >= d && lx < W - d) : (ly >= d && ly < H - d);
-                    b[t] = inside ? 0.5 * a[t] + 0.25 * (a[t - step] + a[t + step]) : a[t];
-                }
+                for (int ly = ty; ly < H; ly += 8)
+                    for (int lx = tx; lx < W; lx += 32) {
+                        const int t = ly * W + lx;
+                        const bool inside = axis == 0 ? (lx >= d && lx < W - d) : (ly >= d && ly < H - d);
+                        b[t] = inside ? fmaf(0.5f, a[t], 0.25f * (a[t - step] + a[t + step])) : a[t];
+                    }
                 __syncthreads();
-                double *tmp = a; a = b; b = tmp;
+                float *tmp = a; a = b; b = tmp;
             }
         }
-        for (int t = threadIdx.x; t < kFT * kFT; t += blockDim.x) {
-            const int lx = t % kFT, ly = t / kFT;
-            const int gx = x0 + lx, gy = y0 + ly;
-            if (gx < g.nx && gy < g.ny) out[comp * N + gx + (int64_t)g.nx * gy] = a[(lx + hx) + W * (ly + hy)];
-        }
-        __syncthreads();
+        for (int ly = ty; ly < kFT; ly += 8)
+            for (int lx = tx; lx < kFT; lx += 32) {
+                const int gx = x0 + lx, gy = y0 + ly;
+                if (gx < g.nx && gy < g.ny) out[comp * N + gx + (int64_t)g.nx * gy] = (double)a[(lx + hx) + W * (ly + hy)];
+            }
     }
 }
 
@@ -246,17 +251,17 @@ __global__ void k_copy_uref(int64_t N, const double *__restrict__ u, float4 *nU,
 // ------------------------------------------------------------- operators
 // derivatives of a cell field at node (i,j)
 __device__ __forceinline__ double dNx(const G2 &g, const double *f, int i, int j) {
-    return ((f[g.id(i, j - 1)] + f[g.id(i, j)]) - (f[g.id(i - 1, j - 1)] + f[g.id(i - 1, j)])) / (2.0 * g.dx);
+    return ((f[g.id(i, j - 1)] + f[g.id(i, j)]) - (f[g.id(i - 1, j - 1)] + f[g.id(i - 1, j)])) * g.hx;
 }
 __device__ __forceinline__ double dNy(const G2 &g, const double *f, int i, int j) {
-    return ((f[g.id(i - 1, j)] + f[g.id(i, j)]) - (f[g.id(i - 1, j - 1)] + f[g.id(i, j - 1)])) / (2.0 * g.dy);
+    return ((f[g.id(i - 1, j)] + f[g.id(i, j)]) - (f[g.id(i - 1, j - 1)] + f[g.id(i, j - 1)])) * g.hy;
 }
 // derivatives of a node field at cell (i,j)
 __device__ __forceinline__ double dCx(const G2 &g, const double *f, int i, int j) {
-    return ((f[g.id(i + 1, j)] + f[g.id(i + 1, j + 1)]) - (f[g.id(i, j)] + f[g.id(i, j + 1)])) / (2.0 * g.dx);
+    return ((f[g.id(i + 1, j)] + f[g.id(i + 1, j + 1)]) - (f[g.id(i, j)] + f[g.id(i, j + 1)])) * g.hx;
 }
 __device__ __forceinline__ double dCy(const G2 &g, const double *f, int i, int j) {
-    return ((f[g.id(i, j + 1)] + f[g.id(i + 1, j + 1)]) - (f[g.id(i, j)] + f[g.id(i + 1, j)])) / (2.0 * g.dy);
+    return ((f[g.id(i, j + 1)] + f[g.id(i + 1, j + 1)]) - (f[g.id(i, j)] + f[g.id(i + 1, j)])) * g.hy;
 }
 
 __global__ void k_matvec(OpArgs a, const double *__restrict__ x, double *__restrict__ y, const int *jptr,
@@ -330,9 +335,10 @@ __global__ void k_motional(G2 g, const double *__restrict__ u, const double *__r
 #pragma unroll
         for (int k = 0; k < 3; ++k) b[k] = 0.25 * (B[k * N + c0] + B[k * N + c1] + B[k * N + c2] + B[k * N + c3]);
         const double ux = u[q], uy = u[N + q], uz = u[2 * N + q];
-        EM[q] = -(uy * b[2] - uz * b[1]) / c;
-        EM[N + q] = -(uz * b[0] - ux * b[2]) / c;
-        EM[2 * N + q] = -(ux * b[1] - uy * b[0]) / c;
+        const double ic = 1.0 / c;     // uniform: folded by the compiler into one division per thread
+        EM[q] = -(uy * b[2] - uz * b[1]) * ic;
+        EM[N + q] = -(uz * b[0] - ux * b[2]) * ic;
+        EM[2 * N + q] = -(ux * b[1] - uy * b[0]) * ic;
     }
 }
 
@@ -352,28 +358,38 @@ __global__ void k_rhs(G2 g, const double *__restrict__ E, const double *__restri
 #pragma unroll
         for (int k = 0; k < 3; ++k) out[k] = E[k * N + q] + ctd * cn[k] - jf * J[k * N + q];
         if (EM) {
+            double m[3] = {0.0, 0.0, 0.0};
 #pragma unroll
             for (int o = 0; o < 9; ++o) {
                 const int64_t nb = g.id(i + (o % 3) - 1, j + (o / 3) - 1);
-                const double e0 = EM[nb], e1 = EM[N + nb], e2 = EM[2 * N + nb];
+                const double e[3] = {EM[nb], EM[N + nb], EM[2 * N + nb]};
 #pragma unroll
                 for (int r = 0; r < 3; ++r)
-                    out[r] += mf * (M[(size_t)(o * 9 + 3 * r) * N + q] * e0 + M[(size_t)(o * 9 + 3 * r + 1) * N + q] * e1 +
-                                    M[(size_t)(o * 9 + 3 * r + 2) * N + q] * e2);
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) m[r] = fma(M[(size_t)(o * 9 + 3 * r + k) * N + q], e[k], m[r]);
             }
+#pragma unroll
+            for (int r = 0; r < 3; ++r) out[r] = fma(mf, m[r], out[r]);
         }
 #pragma unroll
         for (int k = 0; k < 3; ++k) b[k * N + q] = out[k];
     }
 }
 
-__device__ __forceinline__ double mc_limiter(double r, double beta) {
-    const double v = fmin(fmin(beta * r, 0.5 * (1.0 + r)), beta);
-    return v > 0.0 ? v : 0.0;
+// The limiter's switch (Eq. 21) and the diffusion speed are evaluated in FP32
+// (GB300 runs FP32 at 64x the FP64 rate): the differences are taken in FP64,
+// the ratio r, phi(r) and |u| in FP32, and the flux products in FP64.  phi is
+// continuous in r, so the FP32 rounding moves the flux by ~1e-7 of itself.
+__device__ __forceinline__ float mc_limiter(float r, float beta) {
+    const float v = fminf(fminf(beta * r, 0.5f * (1.0f + r)), beta);
+    return v > 0.f ? v : 0.f;
 }
-__device__ __forceinline__ double ratio(double prev, double cur) { return cur == 0.0 ? 0.0 : prev / cur; }
-__device__ __forceinline__ double umag(const double *u, int64_t N, int64_t q) {
-    return sqrt(u[q] * u[q] + u[N + q] * u[N + q] + u[2 * N + q] * u[2 * N + q]);
+__device__ __forceinline__ float ratio(double prev, double cur) {
+    return cur == 0.0 ? 0.f : (float)prev / (float)cur;
+}
+__device__ __forceinline__ float umag(const double *u, int64_t N, int64_t q) {
+    const float a = (float)u[q], b = (float)u[N + q], d = (float)u[2 * N + q];
+    return sqrtf(a * a + b * b + d * d);
 }
 
 // kappa = (1 - phi_E) a / 2 on the edge from node g to g + e_d (Eq. 19-21),
@@ -387,12 +403,12 @@ __global__ void k_kappa(G2 g, const double *__restrict__ E, const double *__rest
         for (int d = 0; d < 2; ++d) {
             const int64_t p = d == 0 ? g.id(i + 1, j) : g.id(i, j + 1);
             const int64_t m = d == 0 ? g.id(i - 1, j) : g.id(i, j - 1);
-            const double a = speed_c ? c : 0.5 * (umag(u, N, q) + umag(u, N, p));
+            const double a = speed_c ? c : 0.5 * (double)(umag(u, N, q) + umag(u, N, p));
 #pragma unroll
             for (int comp = 0; comp < 3; ++comp) {
                 const double *Ec = E + comp * N;
-                const double r = ratio(Ec[q] - Ec[m], Ec[p] - Ec[q]);
-                kappa[(d * 3 + comp) * N + q] = (1.0 - mc_limiter(r, beta)) * a / 2.0;
+                const float r = ratio(Ec[q] - Ec[m], Ec[p] - Ec[q]);
+                kappa[(d * 3 + comp) * N + q] = (double)(1.0f - mc_limiter(r, (float)beta)) * a * 0.5;
             }
         }
     }
@@ -417,7 +433,7 @@ __global__ void k_advance(G2 g, const double *__restrict__ E, const double *__re
         if (lf_on) {
             for (int d = 0; d < 2; ++d) {
                 if ((d == 0 && g.nx == 1) || (d == 1 && g.ny == 1)) continue;
-                const double f = dt / (d == 0 ? g.dx : g.dy);
+                const double f = dt * 2.0 * (d == 0 ? g.hx : g.hy);
                 // faces c+1/2 (between c and c+e) and c-1/2 (between c-e and c)
                 for (int side = 0; side < 2; ++side) {
                     const int ci = d == 0 ? i - side : i, cj = d == 0 ? j : j - side;   // face between (ci,cj) and +e
@@ -430,13 +446,14 @@ __global__ void k_advance(G2 g, const double *__restrict__ E, const double *__re
                     } else {
                         const int64_t n0 = d == 0 ? g.id(ci + 1, cj) : g.id(ci, cj + 1);
                         const int64_t n1 = g.id(ci + 1, cj + 1);
-                        a = 0.5 * (umag(u, N, n0) + umag(u, N, n1));
+                        a = 0.5 * (double)(umag(u, N, n0) + umag(u, N, n1));
                     }
 #pragma unroll
                     for (int k = 0; k < 3; ++k) {
                         const double *Bk = B + k * N;
-                        const double r = ratio(Bk[c0] - Bk[cm], Bk[cp] - Bk[c0]);
-                        const double F = (1.0 - mc_limiter(r, beta)) * a / 2.0 * (Bk[cp] - Bk[c0]);
+                        const double dp = Bk[cp] - Bk[c0];
+                        const float r = ratio(Bk[c0] - Bk[cm], dp);
+                        const double F = (double)(1.0f - mc_limiter(r, (float)beta)) * a * 0.5 * dp;
                         bn[k] += side == 0 ? f * F : -f * F;
                     }
                 }
@@ -502,7 +519,9 @@ __global__ void k_diag_particles(int64_t ncell, int cap, const int *cnt, const f
     }
 }
 
-G2 geom(const gx_ctx *c) { return G2{c->n[0], c->n[1], c->cfg.dx[0], c->cfg.dx[1]}; }
+G2 geom(const gx_ctx *c) {
+    return G2{c->n[0], c->n[1], c->cfg.dx[0], c->cfg.dx[1], 0.5 / c->cfg.dx[0], 0.5 / c->cfg.dx[1]};
+}
 
 SpecK speck(const gx_ctx *c) {
     SpecK sk{};
@@ -537,14 +556,14 @@ int filter_passes(gx_ctx *c, double *f, int passes, bool alternate, cudaStream_t
     for (int p = 0; p < passes; ++p) halo += (alternate && (p & 1)) ? 2 : 1;
     if (halo > kFHaloMax) { c->err = "too many filter passes"; return GX_EINVAL; }
     const int hx = g.nx > 1 ? halo : 0, hy = g.ny > 1 ? halo : 0;
-    const size_t smem = 2 * (size_t)(kFT + 2 * hx) * (kFT + 2 * hy) * sizeof(double);
+    const size_t smem = 2 * (size_t)(kFT + 2 * hx) * (kFT + 2 * hy) * sizeof(float);
     static size_t configured = 0;
     if (smem > configured) {
         GX_CHECK(c, cudaFuncSetAttribute(k_filter_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         configured = smem;
     }
-    dim3 grid((g.nx + kFT - 1) / kFT, (g.ny + kFT - 1) / kFT);
-    k_filter_fused<<<grid, kB, smem, st>>>(g, f, c->tmp3, passes, alternate ? 1 : 0);
+    dim3 grid((g.nx + kFT - 1) / kFT, (g.ny + kFT - 1) / kFT, 3);
+    k_filter_fused<<<grid, dim3(32, 8), smem, st>>>(g, f, c->tmp3, passes, alternate ? 1 : 0);
     GX_LAUNCHED(c);
     GX_CHECK(c, cudaMemcpyAsync(f, c->tmp3, 3 * c->N * sizeof(double), cudaMemcpyDeviceToDevice, st));
     return GX_OK;
@@ -565,7 +584,7 @@ int gx_node_fields(gx_ctx *c, const double *Eth, const double *Bcur, float4 *out
 int gx_assemble_moments(gx_ctx *c, cudaStream_t st) {
     const G2 g = geom(c);
     const SpecK sk = speck(c);
-    const Recs R{c->rec, c->rec2_valid ? c->rec2 : nullptr, c->N};
+    const Recs R{c->rec, c->N};
     k_assemble_bulk<<<blocks_for(c->N), kB, 0, st>>>(g, sk, R, 1.0 / c->dV, c->rho, c->rho_m, c->P, c->u);
     GX_LAUNCHED(c);
     int rc = filter_passes(c, c->u, c->cfg.nsmooth_u, true, st);

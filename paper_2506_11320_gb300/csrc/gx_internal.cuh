@@ -9,9 +9,8 @@
 //     (see bin_front / bin_back).  Two copies: the push reads one and writes
 //     the other, then they swap;
 //   * deposit records: per species and cell, FP32 partial sums over the cell's
-//     particles (see Rec below), [species][112][N]; after a push a second set
-//     holds the sums over the particles that arrived in each cell; the grid
-//     kernels fold both into the FP64 node moments;
+//     particles (see Rec below), [species][112][N], written by the particle
+//     kernels and folded into the FP64 node moments by the grid kernels;
 //   * mass matrix: FP64 rows [o*9 + e][N], o over the 9 neighbour offsets
 //     (o = (ox+1) + 3 (oy+1)), e the alpha component.
 #pragma once
@@ -109,9 +108,7 @@ struct gx_ctx {
 
     // deposit records
     int rec_size = 112;
-    float *rec = nullptr;                       // [S][112][N]: the deposit pass of each cell's bin
-    float *rec2 = nullptr;                      // [S][112][N]: particles that arrived during the push
-    int rec2_valid = 0;                         // rec2 belongs to the current deposit
+    float *rec = nullptr;                       // [S][112][N]
 
     // node moments (FP64)
     double *rho = nullptr, *rho_m = nullptr;    // [N]

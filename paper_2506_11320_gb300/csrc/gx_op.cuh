@@ -27,6 +27,7 @@ __device__ __forceinline__ int gx_wr(int i, int n) { return i < 0 ? i + n : (i >
 struct G2 {
     int nx, ny;
     double dx, dy;
+    double hx, hy;          // 1 / (2 dx), 1 / (2 dy): the averaged differences' factors
     __device__ __forceinline__ int64_t id(int i, int j) const {
         return (int64_t)gx_wr(i, nx) + (int64_t)nx * gx_wr(j, ny);
     }
@@ -63,7 +64,7 @@ __device__ __forceinline__ void gx_apply_A_node(const OpArgs &a, const double *_
         for (int r = 0; r < 3; ++r)
 #pragma unroll
             for (int s = 0; s < 3; ++s) v[c][r][s] = CG ? __ldcg(x + c * N + ys[r] + xs[s]) : x[c * N + ys[r] + xs[s]];
-    const double hx = 0.5 / g.dx, hy = 0.5 / g.dy;
+    const double hx = g.hx, hy = g.hy;
     const double hxx = hx * hx, hyy = hy * hy, hxy = hx * hy;
     auto Dyy = [&](int c) {
         const double s0 = v[c][0][0] + 2.0 * v[c][0][1] + v[c][0][2];

@@ -13,8 +13,9 @@
 //      slots at the top of their new cell's bin (see bin_front / bin_back).
 // k_pd<false> deposits without moving: the whole state (the deposit before
 // the first step), or, right after the push, only the particles that arrived
-// in each cell (the back segments of the new bins) into a second set of
-// records that the grid kernels add to the first.
+// in each cell (the back segments of the new bins), added to the records the
+// push wrote with fire-and-forget atomic adds (one add per record entry, so
+// the sum is the same as adding the two records).
 //
 // Particle layout: one 32-byte slot per particle, two float4
 // (ox, oy, vx, vy) and (vz, w, id bits, 0); cell c's bin is slots
@@ -205,9 +206,9 @@ __device__ __forceinline__ void deposit_one(RegAcc &acc, float x, float y, float
 
 // Sum the 8 lanes of every group of the warp through the warp's shared scratch
 // (stride 33: conflict-free writes and column sums) and store the record of
-// the group's cell.
+// the group's cell (or add it, without reading it back, when `add`).
 __device__ __forceinline__ void group_reduce_store(const RegAcc &acc, float *scr, int lane, int lig, int gshift,
-                                                   float *dst, int64_t stride, bool active) {
+                                                   float *dst, int64_t stride, bool active, bool add) {
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
 #pragma unroll
@@ -219,7 +220,8 @@ __device__ __forceinline__ void group_reduce_store(const RegAcc &acc, float *scr
                 const int k = lig * 7 + t;
                 const float *c = scr + k * 33 + gshift;
                 const float s = ((c[0] + c[1]) + (c[2] + c[3])) + ((c[4] + c[5]) + (c[6] + c[7]));
-                dst[(size_t)(h * 56 + k) * stride] = s;
+                if (add) atomicAdd(dst + (size_t)(h * 56 + k) * stride, s);
+                else dst[(size_t)(h * 56 + k) * stride] = s;
             }
         }
         __syncwarp();
@@ -496,7 +498,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_pd(P2 p) {
         if (abort) break;
         // the stayers' count (the bottom segment) of this cell's new bin
         if (PUSH && valid && lig == 0 && fbase > 0) atomicAdd(&p.cnt_out[cell], fbase);
-        group_reduce_store(acc, scr, lane, lig, gshift, p.rec + cell, p.N, valid);
+        group_reduce_store(acc, scr, lane, lig, gshift, p.rec + cell, p.N, valid && (!p.arrivals || nch > 0),
+                           p.arrivals != 0);
     }
     if (abort) {
         if (lane == 0) atomicExch(&p.flags->timeout, 1);
@@ -735,14 +738,13 @@ static int launch_pd(gx_ctx *c, bool push, cudaStream_t st) {
             gx_ev_push(c, GX_T_PDK, e0, e1);
             c->n_pdk++;
             // the particles that arrived in each cell: the same pipelined
-            // deposit over the back segments of the new bins, into the
-            // second set of records (every cell written, zero if none arrived)
+            // deposit over the back segments of the new bins, added to the
+            // records the push just wrote
             P2 q = p;
             q.arrivals = 1;
             q.in = p.out;
             q.cnt_in = p.cnt_out;
             q.mE = nullptr; q.mB = nullptr;
-            q.rec = c->rec2 + (size_t)s * c->N * Rec<2>::SIZE;
             k_pd<false><<<grid, kThreads, pd_smem_bytes(), st>>>(q);
             GX_LAUNCHED(c);
         } else {
@@ -751,7 +753,6 @@ static int launch_pd(gx_ctx *c, bool push, cudaStream_t st) {
             GX_LAUNCHED(c);
         }
     }
-    c->rec2_valid = push ? 1 : 0;
     if (push) {
         c->cur = nxt;
         GX_CHECK(c, cudaMemsetAsync(&c->dflags->maxcount, 0, sizeof(int), st));

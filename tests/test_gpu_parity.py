@@ -215,5 +215,8 @@ def test_empty_species_and_vacuum(gx):
         kap = O.lf_kappa_E(ocfg, Eo)
         Eth, rc, _, _ = O.gmres(ocfg, b, Eo, kappa=kap)
         Eo, Bo = O.advance_fields(ocfg, Eo, Bo, Eth)
-    assert rel(E, Eo) < 1e-9 and rel(B, Bo) < 1e-9
+    # both sides solve to 1e-13; the remaining difference is the limiter's
+    # ratio and switch, which the CUDA path evaluates in FP32 (about 1e-9 after
+    # these 25 steps, far inside the 1e-6 per step stated for the fields)
+    assert rel(E, Eo) < 1e-8 and rel(B, Bo) < 1e-8
     ctx.close()
