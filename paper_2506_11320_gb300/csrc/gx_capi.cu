@@ -186,8 +186,6 @@ void gx_destroy(gx_ctx *c) {
     if (c->rec) cudaFree(c->rec);
     if (c->gm) cudaFree(c->gm);
     if (c->gpart) cudaFree(c->gpart);
-    if (c->zbuf) cudaFree(c->zbuf);
-    if (c->vbuf) cudaFree(c->vbuf);
     if (c->dflags) cudaFree(c->dflags);
     if (c->hflags) cudaFreeHost(c->hflags);
     if (c->hpin) cudaFreeHost(c->hpin);
@@ -243,8 +241,7 @@ int gx_create(const gx_config *cfg, gx_ctx **out) {
     if (cfg->precond != GX_PRECOND_NONE && (rc = dalloc(c, &c->Z, (size_t)m * 3 * N))) return fail(rc, nullptr);
     {
         char *gm = nullptr;
-        if ((rc = dalloc(c, &gm, gx_gm_state_bytes())) || (rc = dalloc(c, &c->gpart, gx_gm_partial_count())) ||
-            (rc = dalloc(c, &c->zbuf, 3 * N)) || (rc = dalloc(c, &c->vbuf, 3 * N)))
+        if ((rc = dalloc(c, &gm, gx_gm_state_bytes())) || (rc = dalloc(c, &c->gpart, gx_gm_partial_count())))
             return fail(rc, nullptr);
         c->gm = reinterpret_cast<GmState *>(gm);
         if (cudaMemset(gm, 0, gx_gm_state_bytes()) != cudaSuccess) return fail(GX_ECUDA, "cudaMemset failed");

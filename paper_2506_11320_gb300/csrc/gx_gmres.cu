@@ -17,11 +17,14 @@
 // order, so all CTAs hold bit-identical sums and take identical decisions (the
 // Givens rotations, the convergence test) without another barrier.  An
 // Arnoldi step costs four barriers.  The true residual ||b - A x|| / ||b|| is
-// recomputed at every restart and decides convergence.  With the learned
-// preconditioner the kernel returns whenever it needs the next preconditioned
-// vector, which the network kernels produce between launches.
+// recomputed at every restart and decides convergence.  The learned
+// preconditioner also runs inside the kernel: the Krylov column is packed to
+// BF16, the four convolution layers run on the tensor cores over the whole
+// grid (a barrier between layers), and the correction is added to the block
+// Jacobi image, so a solve is one launch with every preconditioner.
 #include <cooperative_groups.h>
 
+#include "gx_conv.cuh"
 #include "gx_op.cuh"
 
 namespace cg = cooperative_groups;
@@ -62,8 +65,13 @@ struct CoArgs {
     int64_t N;
     int m, maxit;
     double tol;
-    int net;            // the preconditioned vectors come from the host between launches
+    int net;            // apply the learned preconditioner (the fields below)
+    NetSolverArgs nn;
+    double ns;          // its scale s = 1 / sqrt(3 N) (the Krylov columns have unit norm)
 };
+
+// shared memory of the in-kernel network (bf16 elements): the largest layer
+constexpr int kNetSmemElems = gxc::conv_smem_elems<32, 32>();
 
 // every thread's node set: q = tid, tid + nthreads, ...
 #define NODE_LOOP(q) \
@@ -118,7 +126,50 @@ __device__ __forceinline__ void jacobi_node(const double *jd, const double *v, d
     z[2 * N + q] = o[6] * x0 + o[7] * x1 + o[8] * x2;
 }
 
+// Z_j = D^-1 V_j + s N(V_j / s), every CTA of the cooperative grid taking part
+__device__ void net_apply(const CoArgs &a, cg::grid_group &grid, int j, gxc::bf16 *sm) {
+    using namespace gxc;
+    const int64_t N = a.N, n = 3 * N;
+    const double *vj = a.V + (size_t)j * n;
+    double *zj = a.Z + (size_t)j * n;
+    bf16 *x0 = static_cast<bf16 *>(a.nn.x0);
+    const double inv_s = 1.0 / a.ns;
+    NODE_LOOP(q) {
+        __align__(16) bf16 v[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) v[c] = __float2bfloat16_rn(c < 3 ? (float)(vj[c * N + q] * inv_s) : 0.f);
+        reinterpret_cast<uint4 *>(x0 + q * 16)[0] = reinterpret_cast<uint4 *>(v)[0];
+        reinterpret_cast<uint4 *>(x0 + q * 16)[1] = reinterpret_cast<uint4 *>(v)[1];
+    }
+    const int H = a.op.g.ny, W = a.op.g.nx;
+    ConvArgs c1{x0, static_cast<const bf16 *>(a.nn.w[0]), a.nn.b[0], a.nn.h1, nullptr, nullptr, 1, H, W, 1};
+    ConvArgs c2{static_cast<const bf16 *>(a.nn.h1), static_cast<const bf16 *>(a.nn.w[1]), a.nn.b[1], a.nn.h2,
+                nullptr, nullptr, 1, H, W, 1};
+    ConvArgs c3{static_cast<const bf16 *>(a.nn.h2), static_cast<const bf16 *>(a.nn.w[2]), a.nn.b[2], a.nn.h3,
+                nullptr, nullptr, 1, H, W, 1};
+    ConvArgs c4{static_cast<const bf16 *>(a.nn.h3), static_cast<const bf16 *>(a.nn.w[3]), a.nn.b[3], a.nn.y,
+                nullptr, nullptr, 1, H, W, 1};
+    grid.sync();
+    conv_tiles<16, 32, EPI_RELU>(c1, sm, blockIdx.x, gridDim.x);
+    grid.sync();
+    conv_tiles<32, 32, EPI_RELU>(c2, sm, blockIdx.x, gridDim.x);
+    grid.sync();
+    conv_tiles<32, 32, EPI_RELU>(c3, sm, blockIdx.x, gridDim.x);
+    grid.sync();
+    conv_tiles<32, 8, EPI_F32>(c4, sm, blockIdx.x, gridDim.x);
+    grid.sync();
+    NODE_LOOP(q) {
+        const double *o = a.jd + (size_t)q * 9;
+        const double r0 = vj[q], r1 = vj[N + q], r2 = vj[2 * N + q];
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            zj[c * N + q] = o[3 * c] * r0 + o[3 * c + 1] * r1 + o[3 * c + 2] * r2 +
+                            a.ns * (double)__ldcg(a.nn.y + q * 8 + c);
+    }
+}
+
 __global__ void __launch_bounds__(kB) k_fgmres(CoArgs a) {
+    extern __shared__ __align__(16) unsigned char gsm[];
     cg::grid_group grid = cg::this_grid();
     __shared__ double sred[kWarps * 8];
     __shared__ double hs[2][kMaxM + 2];
@@ -188,14 +239,14 @@ __global__ void __launch_bounds__(kB) k_fgmres(CoArgs a) {
             NODE_LOOP(q) {
 #pragma unroll
                 for (int c = 0; c < 3; ++c) a.V[c * N + q] = a.r[c * N + q] * inv;
-                if (a.jd) jacobi_node(a.jd, a.V, a.Z, N, q);
+                if (a.jd && !a.net) jacobi_node(a.jd, a.V, a.Z, N, q);
             }
             __syncthreads();
             if (writer) {
                 st->j = 0; st->done = 0; st->jend = -1;
                 for (int i = 0; i <= kMaxM; ++i) st->g[i] = i == 0 ? beta : 0.0;
             }
-            if (a.net) return;                      // the network preconditions V_0 next
+            if (a.net) net_apply(a, grid, 0, reinterpret_cast<gxc::bf16 *>(gsm));
             grid.sync();
         }
 
@@ -310,11 +361,11 @@ __global__ void __launch_bounds__(kB) k_fgmres(CoArgs a) {
             NODE_LOOP(q) {
 #pragma unroll
                 for (int c = 0; c < 3; ++c) v1[c * N + q] = a.w[c * N + q] * inv;
-                if (a.jd) jacobi_node(a.jd, v1, a.Z + (size_t)(j + 1) * n, N, q);
+                if (a.jd && !a.net) jacobi_node(a.jd, v1, a.Z + (size_t)(j + 1) * n, N, q);
             }
             ++j;
             if (writer) st->j = j;
-            if (a.net) return;                      // the network preconditions V_j next
+            if (a.net) net_apply(a, grid, j, reinterpret_cast<gxc::bf16 *>(gsm));
             grid.sync();
             continue;
         }
@@ -351,21 +402,6 @@ __global__ void k_gm_init(GmState *st) {
         for (int i = 0; i < kMaxM; ++i) { st->cs[i] = 1.0; st->sn[i] = 0.0; }
         for (int i = 0; i <= kMaxM; ++i) st->g[i] = 0.0;
     }
-}
-
-// staging of column j for the network (which takes plain pointers); nothing
-// to do once the solve has finished
-__global__ void k_gm_get_col(const double *__restrict__ V, int64_t n, const GmState *st, double *out) {
-    if (st->finished) return;
-    const double *v = V + (size_t)st->j * n;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
-        out[t] = v[t];
-}
-__global__ void k_gm_put_col(const double *__restrict__ in, double *Z, int64_t n, const GmState *st) {
-    if (st->finished) return;
-    double *z = Z + (size_t)st->j * n;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
-        z[t] = in[t];
 }
 
 __global__ void k_norm2(const double *__restrict__ x, int64_t n, double *out) {
@@ -421,12 +457,17 @@ int gx_fgmres(gx_ctx *c, cudaStream_t st) {
     const int pc = c->cfg.precond;
     int rc;
     if (pc == GX_PRECOND_JACOBI || pc == GX_PRECOND_NET) { rc = gx_build_jacobi(c, st); if (rc) return rc; }
-    static int grid = 0;
+    const bool use_net = pc == GX_PRECOND_NET;
+    const size_t smem = use_net ? (size_t)kNetSmemElems * sizeof(gxc::bf16) : 0;
+    static int grids[2] = {0, 0};
+    int &grid = grids[use_net ? 1 : 0];
     if (!grid) {
         int dev = 0, nsm = 0, per = 0;
         GX_CHECK(c, cudaGetDevice(&dev));
         GX_CHECK(c, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-        GX_CHECK(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fgmres, kB, 0));
+        if (smem > 0)
+            GX_CHECK(c, cudaFuncSetAttribute(k_fgmres, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        GX_CHECK(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fgmres, kB, smem));
         grid = std::max(1, std::min(per * nsm, kMaxGrid));
     }
     CoArgs a{};
@@ -437,14 +478,18 @@ int gx_fgmres(gx_ctx *c, cudaStream_t st) {
     a.Z = pc == GX_PRECOND_NONE ? c->V : c->Z;
     a.w = c->w;
     a.r = c->r;
-    a.jd = pc == GX_PRECOND_JACOBI ? c->jdiag : nullptr;
+    a.jd = pc == GX_PRECOND_NONE ? nullptr : c->jdiag;
     a.st = c->gm;
     a.part = c->gpart;
     a.N = c->N;
     a.m = c->cfg.gmres_restart;
     a.maxit = c->cfg.gmres_maxit;
     a.tol = c->cfg.gmres_tol;
-    a.net = pc == GX_PRECOND_NET;
+    a.net = use_net;
+    if (use_net) {
+        if ((rc = gx_net_solver_args(c, &a.nn, st))) return rc;
+        a.ns = 1.0 / std::sqrt(3.0 * (double)c->N);
+    }
     if (gx_net_collecting(c)) {
         // training pair of this solve: r0 = b - A E^n (the initial guess)
         if ((rc = gx_apply_A(c, c->Eth, c->w, st))) return rc;
@@ -455,36 +500,10 @@ int gx_fgmres(gx_ctx *c, cudaStream_t st) {
     k_gm_init<<<1, 32, 0, st>>>(c->gm);
     GX_LAUNCHED(c);
     void *args[] = {&a};
-    auto launch = [&]() -> int {
-        GX_CHECK(c, cudaLaunchCooperativeKernel((const void *)k_fgmres, dim3(grid), dim3(kB), args, 0, st));
-        c->launches++;
-        return GX_OK;
-    };
+    GX_CHECK(c, cudaLaunchCooperativeKernel((const void *)k_fgmres, dim3(grid), dim3(kB), args, smem, st));
+    c->launches++;
     struct Flags { int j, done, finished, conv, total; };
     Flags *hf = reinterpret_cast<Flags *>(c->hpin);
-    if (!a.net) {
-        if ((rc = launch())) return rc;             // the whole solve
-    } else {
-        // the network between launches: V_j -> Z_j, then the Arnoldi step;
-        // batches sized by the previous solve, state checked between batches
-        if ((rc = launch())) return rc;             // ||b||, first residual, V_0
-        int batch = std::max(2, std::min(16, c->last.iters > 0 ? c->last.iters + 2 : 6));
-        const int nb = nblocks(n);
-        for (int guard = 0; guard < 100000; ++guard) {
-            for (int k = 0; k < batch; ++k) {
-                k_gm_get_col<<<nb, kB, 0, st>>>(c->V, n, c->gm, c->vbuf);
-                GX_LAUNCHED(c);
-                if ((rc = gx_net_apply(c, c->vbuf, c->zbuf, st))) return rc;
-                k_gm_put_col<<<nb, kB, 0, st>>>(c->zbuf, c->Z, n, c->gm);
-                GX_LAUNCHED(c);
-                if ((rc = launch())) return rc;
-            }
-            GX_CHECK(c, cudaMemcpyAsync(hf, c->gm, sizeof(Flags), cudaMemcpyDeviceToHost, st));
-            GX_CHECK(c, cudaStreamSynchronize(st));
-            if (hf->finished) break;
-            batch = std::min(2 * batch, 32);
-        }
-    }
     double tail[4];
     GX_CHECK(c, cudaMemcpyAsync(hf, c->gm, sizeof(Flags), cudaMemcpyDeviceToHost, st));
     GX_CHECK(c, cudaMemcpyAsync(tail, &c->gm->bnorm, sizeof(tail), cudaMemcpyDeviceToHost, st));

@@ -132,7 +132,6 @@ struct gx_ctx {
     double *hpin = nullptr;                     // pinned host mirror of hcol
     struct GmState *gm = nullptr;               // device-side FGMRES state
     double *gpart = nullptr;                    // block partial sums
-    double *zbuf = nullptr, *vbuf = nullptr;    // [3N] preconditioner in/out staging
     gx_solve_stats last{};
 
     // learned preconditioner (allocated on demand)
@@ -213,7 +212,16 @@ int gx_gm_max_restart();
 double gx_norm_host(gx_ctx *c, const double *x, int64_t n, cudaStream_t st, int *status);
 
 // network (gx_net.cu)
-int gx_net_apply(gx_ctx *c, const double *r, double *z, cudaStream_t st);
+// device pointers the solver kernel needs to apply the network itself: BF16
+// forward weights [coutP][9][cinP] and FP32 biases of the 4 layers, the NHWC
+// BF16 activation buffers (16, 32, 32, 32 channels) and the FP32 output [pix][8]
+struct NetSolverArgs {
+    const void *w[4];
+    const float *b[4];
+    void *x0, *h1, *h2, *h3;
+    float *y;
+};
+int gx_net_solver_args(gx_ctx *c, NetSolverArgs *out, cudaStream_t st);
 int gx_net_collecting(const gx_ctx *c);
 int gx_net_pair_begin(gx_ctx *c, const double *r0, cudaStream_t st);
 int gx_net_pair_end(gx_ctx *c, int converged, int nbasis, cudaStream_t st);

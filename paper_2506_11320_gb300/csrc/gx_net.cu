@@ -12,13 +12,11 @@
 // usual time steps, so its BF16 rounding error is relative to that remainder.
 //
 // Kernels (all on the tensor cores through mma.sync m16n8k16 BF16 -> FP32):
-//   * k_conv: implicit-GEMM convolution, M = 16 pixels of a row, N = output
-//     channels, K = 9 taps x input channels; a CTA computes 8 rows x 16
-//     columns, the input tile with its one-pixel halo and the weights staged in
-//     shared memory (row strides padded so that ldmatrix is conflict-free).
-//     The forward pass and the data gradient (the same convolution with the
-//     kernel flipped and the channel roles swapped, masked by the ReLU of the
-//     layer input) both use it.
+//   * k_conv: the implicit-GEMM convolution of gx_conv.cuh.  The forward pass
+//     and the data gradient (the same convolution with the kernel flipped and
+//     the channel roles swapped, masked by the ReLU of the layer input) both
+//     use it; inside the solver the forward pass runs in the solver's own
+//     kernel.
 //   * k_wgrad: weight gradient dW[co][tap][ci] = sum_p dY[p][co] X[p+tap][ci],
 //     a contraction over pixels (ldmatrix.trans operands), accumulated by a
 //     persistent grid in registers and added to FP32 global sums once per CTA.
@@ -30,9 +28,9 @@
 #include <cstring>
 #include <random>
 
-#include "gx_internal.cuh"
+#include "gx_conv.cuh"
 
-typedef __nv_bfloat16 bf16;
+using namespace gxc;
 
 namespace {
 
@@ -42,10 +40,6 @@ constexpr int kCout[kNL] = {32, 32, 32, 3};
 constexpr int kCinP[kNL] = {16, 32, 32, 32};    // padded input channels (storage of the layer input)
 constexpr int kCoutP[kNL] = {32, 32, 32, 8};    // padded output channels (forward)
 constexpr int kGCoutP[kNL] = {32, 32, 32, 16};  // padded output channels of the gradient (dY) storage
-constexpr int kTH = 8, kTW = 16;                // CTA tile: 8 rows x 16 columns
-constexpr int kHalo = (kTH + 2) * (kTW + 2);    // 180 input pixels per tile
-
-enum { EPI_RELU = 0, EPI_F32 = 1, EPI_MASK = 2 };
 
 constexpr int64_t layer_w_count(int l) { return (int64_t)kCout[l] * kCin[l] * 9; }
 inline int64_t param_offset(int l) {
@@ -55,146 +49,12 @@ inline int64_t param_offset(int l) {
 }
 inline int64_t param_count() { return param_offset(kNL); }
 
-__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-__device__ __forceinline__ void ldsm_x4(uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3, const void *p) {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-                 : "r"(smem_u32(p)));
-}
-__device__ __forceinline__ void ldsm_x2(uint32_t &r0, uint32_t &r1, const void *p) {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];" : "=r"(r0), "=r"(r1) : "r"(smem_u32(p)));
-}
-__device__ __forceinline__ void ldsm_x4_t(uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3, const void *p) {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-                 : "r"(smem_u32(p)));
-}
-__device__ __forceinline__ void ldsm_x2_t(uint32_t &r0, uint32_t &r1, const void *p) {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];" : "=r"(r0), "=r"(r1) : "r"(smem_u32(p)));
-}
-__device__ __forceinline__ void mma16816(float c[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, uint32_t b0,
-                                         uint32_t b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-}
-
-__device__ __forceinline__ int wrapn(int i, int n) {
-    i %= n;
-    return i < 0 ? i + n : i;
-}
-
-// load the (TH+2) x (TW+2) pixel halo tile of CIN channels of image b into
-// shared memory (row stride CIN + 8), zero or periodic outside the image
-template <int CIN>
-__device__ __forceinline__ void load_tile(bf16 *sIn, const bf16 *in, int b, int H, int W, int y0, int x0,
-                                          int periodic) {
-    constexpr int S = CIN + 8;
-    constexpr int V = CIN / 8;   // 16-byte vectors per pixel
-    for (int t = threadIdx.x; t < kHalo * V; t += blockDim.x) {
-        const int pix = t / V, v = t % V;
-        int yy = y0 - 1 + pix / (kTW + 2), xx = x0 - 1 + pix % (kTW + 2);
-        uint4 val = make_uint4(0, 0, 0, 0);
-        bool ok = true;
-        if (periodic) {
-            yy = wrapn(yy, H);
-            xx = wrapn(xx, W);
-        } else {
-            ok = yy >= 0 && yy < H && xx >= 0 && xx < W;
-        }
-        if (ok) val = *reinterpret_cast<const uint4 *>(in + (((int64_t)b * H + yy) * W + xx) * CIN + v * 8);
-        *reinterpret_cast<uint4 *>(sIn + pix * S + v * 8) = val;
-    }
-}
-
-struct ConvArgs {
-    const bf16 *in;      // [B][H][W][CIN]
-    const bf16 *w;       // [COUT][9][CIN]
-    const float *bias;   // [COUT] or null
-    void *out;           // [B][H][W][COUT] bf16 (or float for EPI_F32)
-    const bf16 *mask;    // [B][H][W][COUT] (EPI_MASK): multiply by (mask > 0)
-    int B, H, W, periodic;
-};
-
-// out = epilogue(conv3x3(in, w) + bias)
+// the forward/data-gradient convolution as a kernel (a persistent grid)
 template <int CIN, int COUT, int EPI>
 __global__ void __launch_bounds__(256) k_conv(ConvArgs a) {
-    constexpr int SI = CIN + 8, SWr = 9 * CIN + 8;
-    constexpr int NT = COUT / 8;
-    __shared__ __align__(16) bf16 sIn[kHalo * SI];
-    __shared__ __align__(16) bf16 sW[COUT * SWr];
-    const int x0 = blockIdx.x * kTW, y0 = blockIdx.y * kTH, b = blockIdx.z;
-    // weights
-    constexpr int WV = 9 * CIN / 8;
-    for (int t = threadIdx.x; t < COUT * WV; t += blockDim.x) {
-        const int co = t / WV, v = t % WV;
-        *reinterpret_cast<uint4 *>(sW + co * SWr + v * 8) = *reinterpret_cast<const uint4 *>(a.w + (size_t)co * 9 * CIN + v * 8);
-    }
-    load_tile<CIN>(sIn, a.in, b, a.H, a.W, y0, x0, a.periodic);
-    __syncthreads();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int mi = lane >> 3, r = lane & 7;
-    float acc[NT][4];
-#pragma unroll
-    for (int n = 0; n < NT; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
-#pragma unroll
-    for (int tap = 0; tap < 9; ++tap) {
-        const int ky = tap / 3, kx = tap % 3;
-#pragma unroll
-        for (int kc = 0; kc < CIN / 16; ++kc) {
-            uint32_t a0, a1, a2, a3;
-            {
-                const int p = r + 8 * (mi & 1), koff = 8 * (mi >> 1);
-                ldsm_x4(a0, a1, a2, a3, sIn + ((warp + ky) * (kTW + 2) + p + kx) * SI + kc * 16 + koff);
-            }
-            if (NT >= 2) {
-#pragma unroll
-                for (int np = 0; np < NT / 2; ++np) {
-                    uint32_t b0, b1, b2, b3;
-                    const int co = np * 16 + 8 * (mi >> 1) + r, k = tap * CIN + kc * 16 + 8 * (mi & 1);
-                    ldsm_x4(b0, b1, b2, b3, sW + co * SWr + k);
-                    mma16816(acc[2 * np], a0, a1, a2, a3, b0, b1);
-                    mma16816(acc[2 * np + 1], a0, a1, a2, a3, b2, b3);
-                }
-            } else {
-                uint32_t b0, b1;
-                const int co = r, k = tap * CIN + kc * 16 + 8 * (mi & 1);
-                ldsm_x2(b0, b1, sW + co * SWr + k);
-                mma16816(acc[0], a0, a1, a2, a3, b0, b1);
-            }
-        }
-    }
-    // epilogue: thread holds pixels g and g+8 of the row, channels 2t, 2t+1 of each n-tile
-    const int gq = lane >> 2, tq = lane & 3;
-    const int yy = y0 + warp;
-    if (yy >= a.H) return;
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const int xx = x0 + gq + 8 * h;
-        if (xx >= a.W) continue;
-        const int64_t pix = ((int64_t)b * a.H + yy) * a.W + xx;
-#pragma unroll
-        for (int n = 0; n < NT; ++n) {
-            const int co = n * 8 + 2 * tq;
-            float v0 = acc[n][2 * h], v1 = acc[n][2 * h + 1];
-            if (a.bias) { v0 += a.bias[co]; v1 += a.bias[co + 1]; }
-            if (EPI == EPI_F32) {
-                *reinterpret_cast<float2 *>(reinterpret_cast<float *>(a.out) + pix * COUT + co) = make_float2(v0, v1);
-            } else {
-                if (EPI == EPI_RELU) {
-                    v0 = fmaxf(v0, 0.f);
-                    v1 = fmaxf(v1, 0.f);
-                } else {   // EPI_MASK
-                    const __nv_bfloat162 m = *reinterpret_cast<const __nv_bfloat162 *>(a.mask + pix * COUT + co);
-                    if (!(__bfloat162float(m.x) > 0.f)) v0 = 0.f;
-                    if (!(__bfloat162float(m.y) > 0.f)) v1 = 0.f;
-                }
-                *reinterpret_cast<__nv_bfloat162 *>(reinterpret_cast<bf16 *>(a.out) + pix * COUT + co) =
-                    __floats2bfloat162_rn(v0, v1);
-            }
-        }
-    }
+    __shared__ __align__(16) bf16 sm[conv_smem_elems<CIN, COUT>()];
+    if (a.skip && *a.skip) return;
+    conv_tiles<CIN, COUT, EPI>(a, sm, blockIdx.x, gridDim.x);
 }
 
 struct WgArgs {
@@ -349,34 +209,8 @@ __global__ void k_pack_input(const T *src, int64_t HW, bf16 *dst, const double *
     }
 }
 
-// z = D^-1 r + s y, jd = the 3x3 inverse diagonal blocks [N][9]
-__global__ void k_unpack_output(const float *y, int64_t HW, const double *jd, const double *r, double *z,
-                                const double *sumsq) {
-    const double s = sqrt(*sumsq / (3.0 * HW));
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < HW; p += (int64_t)gridDim.x * blockDim.x) {
-        const double *o = jd + (size_t)p * 9;
-        const double r0 = r[p], r1 = r[HW + p], r2 = r[2 * HW + p];
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-            z[c * HW + p] = o[3 * c] * r0 + o[3 * c + 1] * r1 + o[3 * c + 2] * r2 + s * (double)y[p * 8 + c];
-    }
-}
 
-// one atomic per CTA (256 threads)
-__global__ void k_sumsq(const double *x, int64_t n, double *out) {
-    __shared__ double sh[8];
-    double s = 0.0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        s += x[i] * x[i];
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int w = 0; w < 8; ++w) t += sh[w];
-        atomicAdd(out, t);
-    }
-}
+
 
 // training crops: for crop b, input = r / s_b on a (C+8)^2 window (4-pixel halo,
 // periodic in the source field) and target = t / s_b on the central C^2, where
@@ -578,10 +412,10 @@ static int net_reserve(gx_ctx *c, int64_t pix) {
 
 template <int CIN, int COUT, int EPI>
 static int conv(gx_ctx *c, const bf16 *in, const bf16 *w, const float *bias, void *out, const bf16 *mask, int B, int H,
-                int W, int periodic, cudaStream_t st) {
-    ConvArgs a{in, w, bias, out, mask, B, H, W, periodic};
-    dim3 grid((W + kTW - 1) / kTW, (H + kTH - 1) / kTH, B);
-    k_conv<CIN, COUT, EPI><<<grid, 256, 0, st>>>(a);
+                int W, int periodic, cudaStream_t st, const int *skip = nullptr) {
+    ConvArgs a{in, w, bias, out, mask, skip, B, H, W, periodic};
+    const int64_t tiles = (int64_t)((W + kTW - 1) / kTW) * ((H + kTH - 1) / kTH) * B;
+    k_conv<CIN, COUT, EPI><<<(unsigned)std::min<int64_t>(tiles, 152 * 4), 256, 0, st>>>(a);
     GX_LAUNCHED(c);
     return GX_OK;
 }
@@ -597,13 +431,16 @@ static int wgrad(gx_ctx *c, const bf16 *dy, const bf16 *x, float *gw, float *gb,
 }
 
 // forward through the four layers (input in n->x0), output FP32 [pix][8] in n->y
-static int net_forward(gx_ctx *c, int B, int H, int W, int periodic, cudaStream_t st) {
+static int net_forward(gx_ctx *c, int B, int H, int W, int periodic, cudaStream_t st, const int *skip = nullptr) {
     Net *n = c->net;
     int rc;
-    if ((rc = conv<16, 32, EPI_RELU>(c, n->x0, n->wf[0], n->bias[0], n->h1, nullptr, B, H, W, periodic, st))) return rc;
-    if ((rc = conv<32, 32, EPI_RELU>(c, n->h1, n->wf[1], n->bias[1], n->h2, nullptr, B, H, W, periodic, st))) return rc;
-    if ((rc = conv<32, 32, EPI_RELU>(c, n->h2, n->wf[2], n->bias[2], n->h3, nullptr, B, H, W, periodic, st))) return rc;
-    return conv<32, 8, EPI_F32>(c, n->h3, n->wf[3], n->bias[3], n->y, nullptr, B, H, W, periodic, st);
+    if ((rc = conv<16, 32, EPI_RELU>(c, n->x0, n->wf[0], n->bias[0], n->h1, nullptr, B, H, W, periodic, st, skip)))
+        return rc;
+    if ((rc = conv<32, 32, EPI_RELU>(c, n->h1, n->wf[1], n->bias[1], n->h2, nullptr, B, H, W, periodic, st, skip)))
+        return rc;
+    if ((rc = conv<32, 32, EPI_RELU>(c, n->h2, n->wf[2], n->bias[2], n->h3, nullptr, B, H, W, periodic, st, skip)))
+        return rc;
+    return conv<32, 8, EPI_F32>(c, n->h3, n->wf[3], n->bias[3], n->y, nullptr, B, H, W, periodic, st, skip);
 }
 
 // backward from dY4 (in n->d4): weight gradients (FP32 sums, zeroed here) and
@@ -631,24 +468,18 @@ static int net_backward(gx_ctx *c, int B, int H, int W, int periodic, float grad
 }
 
 // ------------------------------------------------------------ solver hooks
-// z = D^-1 r + s N(r / s), s = ||r|| / sqrt(3 N): FP64 [3][N] in and out; the
-// block-Jacobi inverse c->jdiag must be current
-int gx_net_apply(gx_ctx *c, const double *r, double *z, cudaStream_t st) {
+// pointers for the solver kernel, which applies the network to its Krylov
+// columns itself (weights refreshed, activations sized for the grid)
+int gx_net_solver_args(gx_ctx *c, NetSolverArgs *out, cudaStream_t st) {
     if (c->dim != 2) { c->err = "the learned preconditioner is 2D"; return GX_ENOTIMPL; }
     int rc = net_alloc(c);
     if (rc) return rc;
     Net *n = c->net;
     if (!n->have_weights && (rc = net_refresh(c, st))) return rc;
-    const int H = c->n[1], W = c->n[0];
-    if ((rc = net_reserve(c, (int64_t)H * W))) return rc;
-    GX_CHECK(c, cudaMemsetAsync(n->dsum, 0, sizeof(double), st));
-    k_sumsq<<<std::min(nblk(3 * c->N), 152 * 2), 256, 0, st>>>(r, 3 * c->N, n->dsum);
-    GX_LAUNCHED(c);
-    k_pack_input<double><<<nblk(c->N), 256, 0, st>>>(r, c->N, n->x0, n->dsum, 1.0);
-    GX_LAUNCHED(c);
-    if ((rc = net_forward(c, 1, H, W, 1, st))) return rc;
-    k_unpack_output<<<nblk(c->N), 256, 0, st>>>(n->y, c->N, c->jdiag, r, z, n->dsum);
-    GX_LAUNCHED(c);
+    if ((rc = net_reserve(c, c->N))) return rc;
+    for (int l = 0; l < kNL; ++l) { out->w[l] = n->wf[l]; out->b[l] = n->bias[l]; }
+    out->x0 = n->x0; out->h1 = n->h1; out->h2 = n->h2; out->h3 = n->h3;
+    out->y = n->y;
     return GX_OK;
 }
 
@@ -793,6 +624,8 @@ int gx_precond_train(gx_ctx *c, int npairs, int crop, int batch, int epochs, flo
     std::vector<CropSpec> spec(batch);
     const int64_t P = param_count();
     const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    const int total_steps = epochs * ((npairs + batch - 1) / batch);
+    int step_i = 0;
     for (int ep = 0; ep < epochs; ++ep) {
         GX_CHECK(c, cudaMemsetAsync(n->dsum + 1, 0, sizeof(double), st));
         int nb = 0;
@@ -818,7 +651,10 @@ int gx_precond_train(gx_ctx *c, int npairs, int crop, int batch, int epochs, flo
             if ((rc = net_backward(c, B, S, S, 0, 1.f, st))) return rc;
             ++n->adam_t;
             const float c1 = 1.f - std::pow(b1, (float)n->adam_t), c2 = 1.f - std::pow(b2, (float)n->adam_t);
-            k_adam<<<nblk(P), 256, 0, st>>>(n->params, n->grad, n->m1, n->m2, P, lr, b1, b2, eps, c1, c2);
+            // cosine decay of the step size over the call, down to lr / 20
+            const double prog = (double)(step_i++) / std::max(1, total_steps - 1);
+            const float lr_t = (float)(lr * (0.05 + 0.95 * 0.5 * (1.0 + std::cos(3.141592653589793 * prog))));
+            k_adam<<<nblk(P), 256, 0, st>>>(n->params, n->grad, n->m1, n->m2, P, lr_t, b1, b2, eps, c1, c2);
             GX_LAUNCHED(c);
             if ((rc = net_refresh(c, st))) return rc;
         }

@@ -206,7 +206,7 @@ def test_trained_network_reduces_gmres_iterations(env):
             for k, c in ctxs.items():
                 its[k].append(c.step(1).iters)
         assert net.precond_pairs() >= 24
-        losses = net.precond_train(npairs=256, crop=16, batch=32, epochs=100, lr=2e-3, seed=3)
+        losses = net.precond_train(npairs=256, crop=16, batch=32, epochs=300, lr=3e-3, seed=3)
         assert np.all(np.isfinite(losses))
         assert losses[-1] < 0.5 * losses[0], losses
         net.precond_collect(0)
