@@ -58,17 +58,31 @@ def load_peaks():
     return 6800.0, "fallback"
 
 
-def load_traffic(kernel_key, workload_key):
-    """DRAM bytes per launch of the dominant kernel from a committed ncu summary
-    (profiles/<kernel>_<workload>.json), or None."""
-    p = os.path.join(ROOT, "profiles", f"{kernel_key}_{workload_key}.json")
-    if os.path.exists(p):
-        try:
-            d = json.load(open(p))
-            return d.get("dram_bytes_per_launch"), d
-        except Exception:
-            return None, None
-    return None, None
+def load_traffic(summary_name, source):
+    """DRAM bytes per launch of the dominant kernel from its committed ncu
+    summary (profiles/<summary_name>.md, lines "- dram_bytes_per_launch: N" and
+    "- kernel_source_sha256: H"), or None when there is none or the kernel's
+    source has changed since the counters were taken."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", summary_name + ".md")
+    if not os.path.exists(p):
+        return None
+    vals = {}
+    for line in open(p):
+        line = line.strip()
+        if line.startswith("- ") and ":" in line:
+            k, v = line[2:].split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    try:
+        sha = hashlib.sha256(open(os.path.join(ROOT, source), "rb").read()).hexdigest()
+    except OSError:
+        return None
+    if vals.get("kernel_source_sha256") != sha:
+        return None
+    try:
+        return int(float(vals["dram_bytes_per_launch"]))
+    except (KeyError, ValueError):
+        return None
 
 
 class Clocks:
@@ -268,7 +282,7 @@ def main():
     pd_kernel_ms = kt["pd_kernel_ms"] / n_launch
     alg_bytes = ALG_BYTES_2D * Np / len(wl.species)
     achieved = alg_bytes / (pd_kernel_ms / 1000.0) / 1e9
-    traffic, prof = load_traffic("k_push_deposit", args.workload)
+    traffic = load_traffic(f"k_pd_push_{args.workload}", "paper_2506_11320_gb300/csrc/gx_particles.cu")
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "peak_kind": peak_kind,
                 "kernel": "k_pd<push> (fused mover + re-bin + deposit), one launch per species",
@@ -336,7 +350,7 @@ def run_precond_compare(gx, wl, steps, barrier, collect_steps=24):
             c.step(1, allow_noconv=True)
     barrier()
     t0 = time.perf_counter()
-    losses = net.precond_train(npairs=512, crop=32, batch=32, epochs=40, lr=2e-3, seed=7)
+    losses = net.precond_train(npairs=512, crop=32, batch=32, epochs=200, lr=2e-3, seed=7)
     barrier()
     train_s = time.perf_counter() - t0
     net.precond_collect(0)
