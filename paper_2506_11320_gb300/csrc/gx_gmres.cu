@@ -168,7 +168,10 @@ __device__ void net_apply(const CoArgs &a, cg::grid_group &grid, int j, gxc::bf1
     }
 }
 
-__global__ void __launch_bounds__(kB) k_fgmres(CoArgs a) {
+// NET: the learned preconditioner is applied in the kernel (the plain and
+// Jacobi instantiation is smaller and fits two CTAs per SM)
+template <bool NET>
+__global__ void __launch_bounds__(kB, NET ? 1 : 2) k_fgmres(CoArgs a) {
     extern __shared__ __align__(16) unsigned char gsm[];
     cg::grid_group grid = cg::this_grid();
     __shared__ double sred[kWarps * 8];
@@ -239,14 +242,14 @@ __global__ void __launch_bounds__(kB) k_fgmres(CoArgs a) {
             NODE_LOOP(q) {
 #pragma unroll
                 for (int c = 0; c < 3; ++c) a.V[c * N + q] = a.r[c * N + q] * inv;
-                if (a.jd && !a.net) jacobi_node(a.jd, a.V, a.Z, N, q);
+                if (a.jd && !NET) jacobi_node(a.jd, a.V, a.Z, N, q);
             }
             __syncthreads();
             if (writer) {
                 st->j = 0; st->done = 0; st->jend = -1;
                 for (int i = 0; i <= kMaxM; ++i) st->g[i] = i == 0 ? beta : 0.0;
             }
-            if (a.net) net_apply(a, grid, 0, reinterpret_cast<gxc::bf16 *>(gsm));
+            if (NET) net_apply(a, grid, 0, reinterpret_cast<gxc::bf16 *>(gsm));
             grid.sync();
         }
 
@@ -361,11 +364,11 @@ __global__ void __launch_bounds__(kB) k_fgmres(CoArgs a) {
             NODE_LOOP(q) {
 #pragma unroll
                 for (int c = 0; c < 3; ++c) v1[c * N + q] = a.w[c * N + q] * inv;
-                if (a.jd && !a.net) jacobi_node(a.jd, v1, a.Z + (size_t)(j + 1) * n, N, q);
+                if (a.jd && !NET) jacobi_node(a.jd, v1, a.Z + (size_t)(j + 1) * n, N, q);
             }
             ++j;
             if (writer) st->j = j;
-            if (a.net) net_apply(a, grid, j, reinterpret_cast<gxc::bf16 *>(gsm));
+            if (NET) net_apply(a, grid, j, reinterpret_cast<gxc::bf16 *>(gsm));
             grid.sync();
             continue;
         }
@@ -461,13 +464,14 @@ int gx_fgmres(gx_ctx *c, cudaStream_t st) {
     const size_t smem = use_net ? (size_t)kNetSmemElems * sizeof(gxc::bf16) : 0;
     static int grids[2] = {0, 0};
     int &grid = grids[use_net ? 1 : 0];
+    const void *kfn = use_net ? (const void *)k_fgmres<true> : (const void *)k_fgmres<false>;
     if (!grid) {
         int dev = 0, nsm = 0, per = 0;
         GX_CHECK(c, cudaGetDevice(&dev));
         GX_CHECK(c, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
         if (smem > 0)
-            GX_CHECK(c, cudaFuncSetAttribute(k_fgmres, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        GX_CHECK(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fgmres, kB, smem));
+            GX_CHECK(c, cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        GX_CHECK(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kfn, kB, smem));
         grid = std::max(1, std::min(per * nsm, kMaxGrid));
     }
     CoArgs a{};
@@ -500,7 +504,7 @@ int gx_fgmres(gx_ctx *c, cudaStream_t st) {
     k_gm_init<<<1, 32, 0, st>>>(c->gm);
     GX_LAUNCHED(c);
     void *args[] = {&a};
-    GX_CHECK(c, cudaLaunchCooperativeKernel((const void *)k_fgmres, dim3(grid), dim3(kB), args, smem, st));
+    GX_CHECK(c, cudaLaunchCooperativeKernel(kfn, dim3(grid), dim3(kB), args, smem, st));
     c->launches++;
     struct Flags { int j, done, finished, conv, total; };
     Flags *hf = reinterpret_cast<Flags *>(c->hpin);
