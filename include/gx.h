@@ -74,6 +74,10 @@ typedef struct gx_ctx gx_ctx;
  *   theta         time centring of the theta scheme (Eq. 5-8), in [0.5, 1].
  *   gmres_*       FGMRES(restart) on the field equation, stopping at relative
  *                 residual gmres_tol or gmres_maxit matrix-vector products.
+ *                 The solve starts from E^{n+theta} extrapolated linearly from
+ *                 the previous step's solution and E^n (from E^n on the first
+ *                 step and after gx_fields_set); the result does not depend on
+ *                 the starting point beyond the tolerance.
  *   precond       GX_PRECOND_*: right preconditioner of the field solve.
  *   track_ids     1: carry a 32-bit particle id through the bins (testing).
  *   bin_slack     capacity of a cell's particle bin relative to the largest

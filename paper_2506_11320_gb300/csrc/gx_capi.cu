@@ -312,6 +312,7 @@ int gx_fields_set(gx_ctx *c, const double *E, const double *B, int ptr_is_device
     GX_CHECK(c, cudaStreamSynchronize(0));
     c->moments_valid = 0;
     c->pending = 0;
+    c->have_eth = 0;
     return GX_OK;
 }
 
@@ -335,7 +336,7 @@ int gx_field_solve(gx_ctx *c, void *stream, gx_solve_stats *stats) {
     EvTimer t(c, st, 2);
     TRY(gx_build_kappa(c, st));
     TRY(gx_build_rhs(c, st));
-    GX_CHECK(c, cudaMemcpyAsync(c->Eth, c->E, 3 * c->N * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    TRY(gx_initial_guess(c, st));
     int rc = gx_fgmres(c, st);
     if (rc != GX_OK && rc != GX_ENOCONV) return rc;
     TRY(gx_advance(c, st));
@@ -366,6 +367,7 @@ int gx_push_and_deposit(gx_ctx *c, void *stream) {
     std::swap(c->E, c->Enew);
     std::swap(c->B, c->Bnew);
     std::swap(c->nB, c->nBnext);
+    c->have_eth = 1;
     {
         EvTimer t(c, st, 1);
         TRY(gx_assemble_moments(c, st));

@@ -454,7 +454,7 @@ double gx_norm_host(gx_ctx *c, const double *x, int64_t n, cudaStream_t st, int 
     return sqrt(h);
 }
 
-// Solve A x = rhs for x = Eth (initial guess already in Eth).
+// Solve A x = rhs for x = Eth (the starting point already in Eth).
 int gx_fgmres(gx_ctx *c, cudaStream_t st) {
     const int64_t n = 3 * c->N;
     const int pc = c->cfg.precond;
@@ -495,8 +495,8 @@ int gx_fgmres(gx_ctx *c, cudaStream_t st) {
         a.ns = 1.0 / std::sqrt(3.0 * (double)c->N);
     }
     if (gx_net_collecting(c)) {
-        // training pair of this solve: r0 = b - A E^n (the initial guess)
-        if ((rc = gx_apply_A(c, c->Eth, c->w, st))) return rc;
+        // training pair of this solve: r0 = b - A E^n, so that A (E^{n+theta} - E^n) = r0
+        if ((rc = gx_apply_A(c, c->E, c->w, st))) return rc;
         k_sub<<<nblocks(n), kB, 0, st>>>(c->rhs, c->w, c->r, n);
         GX_LAUNCHED(c);
         if ((rc = gx_net_pair_begin(c, c->r, st))) return rc;

@@ -239,6 +239,13 @@ __global__ void k_assemble_main(G2 g, SpecK sk, Recs R, double inv_dV, int comov
     }
 }
 
+// starting point of the field solve: E^{n+theta} extrapolated linearly from
+// E^{n-1+theta} (the previous solution, in x) and E^n:
+// x = E^n + theta/(1-theta) (E^n - x), or E^n itself when there is no previous solution
+__global__ void k_guess(int64_t n, const double *__restrict__ E, double *x, double f) {
+    GRID_LOOP(t, n) { x[t] = f != 0.0 ? E[t] + f * (E[t] - x[t]) : E[t]; }
+}
+
 __global__ void k_copy_uref(int64_t N, const double *__restrict__ u, float4 *nU, double *u64, int zero) {
     GRID_LOOP(q, N) {
         float4 v = zero ? make_float4(0.f, 0.f, 0.f, 0.f)
@@ -645,6 +652,14 @@ int gx_build_jacobi(gx_ctx *c, cudaStream_t st) {
 
 int gx_apply_jacobi(gx_ctx *c, const double *x, double *y, cudaStream_t st) {
     k_apply_jacobi<<<blocks_for(c->N), kB, 0, st>>>(c->N, c->jdiag, x, y);
+    GX_LAUNCHED(c);
+    return GX_OK;
+}
+
+int gx_initial_guess(gx_ctx *c, cudaStream_t st) {
+    const double th = c->cfg.theta;
+    const double f = (c->have_eth && th < 1.0) ? th / (1.0 - th) : 0.0;
+    k_guess<<<blocks_for(3 * c->N), kB, 0, st>>>(3 * c->N, c->E, c->Eth, f);
     GX_LAUNCHED(c);
     return GX_OK;
 }

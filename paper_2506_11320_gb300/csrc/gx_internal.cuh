@@ -93,6 +93,7 @@ struct gx_ctx {
     double *E = nullptr, *B = nullptr;          // E^n (nodes), B^n (cells)
     double *Eth = nullptr, *Enew = nullptr, *Bnew = nullptr;
     int pending = 0;                            // a solve is waiting for the push
+    int have_eth = 0;                           // Eth holds E^{n-1+theta} of the step that produced E
 
     // FP32 node copies used by the particle kernels (float4: x, y, z, pad)
     float4 *nE = nullptr;        // E^{n+theta}
@@ -202,6 +203,7 @@ int gx_apply_A_j(gx_ctx *c, const double *base, int64_t stride, const int *jptr,
 int gx_build_jacobi(gx_ctx *c, cudaStream_t st);
 int gx_apply_jacobi(gx_ctx *c, const double *x, double *y, cudaStream_t st);
 int gx_advance(gx_ctx *c, cudaStream_t st);                  // Enew, Bnew from Eth
+int gx_initial_guess(gx_ctx *c, cudaStream_t st);            // Eth <- starting point of the solve
 int gx_diag_run(gx_ctx *c, gx_diag *out, cudaStream_t st);
 
 // solver (gx_gmres.cu)
