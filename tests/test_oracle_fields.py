@@ -6,6 +6,7 @@ advection test of Sec. 3.1 (no new extrema with the limited LF term,
 overshoot without it, beta = 0 more diffusive than beta = 1), and GMRES
 against dense Gaussian elimination."""
 import math
+import os
 
 import numpy as np
 import pytest
@@ -131,7 +132,36 @@ def test_fourier_mode_crank_nicolson_phase():
     assert np.allclose(B[2, 0, 0], np.cos(k * xc - ph), atol=1e-11)
 
 
-def _tophat(lf_on, beta, cfl=0.4):
+def _golden(name):
+    # key = value pairs of a fixture under tests/golden/ (comments after #)
+    out = {}
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", name)
+    for line in open(path):
+        line = line.split("#", 1)[0].strip()
+        if "=" in line:
+            k, v = (x.strip() for x in line.split("=", 1))
+            out[k] = v
+    return out
+
+
+TOPHAT = _golden("tophat_sec3_1.txt")
+
+
+def test_tophat_workload_follows_the_printed_setup():
+    # Sec. 3.1: domain [-0.4, 0.4], spacing 0.01, top-hat of half-width 0.2,
+    # c = 1, CFL 0.4, 25 steps to t = 0.1
+    wl = workloads.tophat_1d(cfl=float(TOPHAT["cfl"]))
+    lo, hi, dx = float(TOPHAT["domain_lo"]), float(TOPHAT["domain_hi"]), float(TOPHAT["dx"])
+    assert wl.n[0] == round((hi - lo) / dx) and wl.dx[0] == dx and wl.c == float(TOPHAT["c"])
+    assert wl.steps == int(TOPHAT["steps"])
+    assert math.isclose(wl.steps * wl.dt, float(TOPHAT["t_end"]), rel_tol=1e-12)
+    xc = wl.notes["xc"]
+    hw = float(TOPHAT["half_width"])
+    assert np.array_equal(wl.B0[2, 0, 0], (np.abs(xc) < hw).astype(float))
+    assert xc.min() > lo and xc.max() < hi
+
+
+def _tophat(lf_on, beta, cfl=float(TOPHAT["cfl"])):
     wl = workloads.tophat_1d(lf_on=lf_on, lf_beta=beta, cfl=cfl)
     cfg = O.make_cfg(wl.n, wl.dx, **wl.grid_kwargs())
     E, B = _vacuum_steps(cfg, wl.E0, wl.B0, wl.steps)
@@ -139,7 +169,7 @@ def _tophat(lf_on, beta, cfl=0.4):
     L = wl.n[0] * wl.dx[0]
     xn = wl.notes["xn"]
     shifted = ((xn - t + 0.5 * L) % L) - 0.5 * L
-    exact = (np.abs(shifted) < 0.2).astype(float)
+    exact = (np.abs(shifted) < float(TOPHAT["half_width"])).astype(float)
     return E[1, 0, 0], exact, wl
 
 
