@@ -81,7 +81,9 @@ constexpr size_t kBufBytes = (size_t)kGroups * kGroupBuf * sizeof(float4);
 constexpr size_t kCodeBytes = (size_t)kGroups * kCodeStride * sizeof(int);
 constexpr size_t kMapBytes = (size_t)kGroups * kChunk;
 constexpr size_t kScrBytes = (size_t)8 * kScr * sizeof(float);
-size_t pd_smem_bytes() { return kBarBytes + kBufBytes + kCodeBytes + kMapBytes + kScrBytes; }
+// leaver counts per group and direction (8 neighbours)
+constexpr size_t kDirBytes = (size_t)kGroups * 8 * sizeof(int);
+size_t pd_smem_bytes() { return kBarBytes + kBufBytes + kCodeBytes + kMapBytes + kScrBytes + kDirBytes; }
 
 // ------------------------------------------------------------ PTX helpers
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -267,6 +269,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_pd(P2 p) {
     int *codes = reinterpret_cast<int *>(smem + kBarBytes + kBufBytes);           // [groups][64]
     unsigned char *maps = smem + kBarBytes + kBufBytes + kCodeBytes;             // [groups][64]
     float *scr_all = reinterpret_cast<float *>(smem + kBarBytes + kBufBytes + kCodeBytes + kMapBytes);  // [8][kScr]
+    int *dircnt = reinterpret_cast<int *>(smem + kBarBytes + kBufBytes + kCodeBytes + kMapBytes + kScrBytes);
 
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
@@ -277,6 +280,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_pd(P2 p) {
     unsigned char *mymap = maps + g * kChunk;
     uint64_t *mybar = bars + 2 * g;
     float *scr = scr_all + (size_t)warp * kScr;
+    int *mydir = dircnt + g * 8;
 
     if (lig == 0) {
         mbar_init(&mybar[0], 1);
@@ -364,7 +368,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_pd(P2 p) {
                 if (hi > lo) vmask = (hi - lo == 64 ? ~0ull : ((1ull << (hi - lo)) - 1ull)) << lo;
             }
             unsigned long long smask = vmask;   // stayers (all of them without the push)
-            int old[kPerLane];                  // slot reservations of this lane's leavers
+            int old[kPerLane];                  // ranks of this lane's leavers within their (group, neighbour)
+            int ddest = 0, dbase = 0;           // lane d: neighbour d's cell and its count word before the run
             if (PUSH) {
                 // ---- A1: mover.  New state written back into the staged chunk,
                 // the destination cell of each leaver into the code row.
@@ -406,12 +411,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_pd(P2 p) {
                         }
                         if (p.ny == 1) { sy = 0; y = 0.f; }
                         leave = sx != 0 || sy != 0;
-                        int dxg = ci + sx, dyg = cj + sy;
-                        dxg = dxg < 0 ? dxg + p.nx : (dxg >= p.nx ? dxg - p.nx : dxg);
-                        dyg = dyg < 0 ? dyg + p.ny : (dyg >= p.ny ? dyg - p.ny : dyg);
+                        const int code = (sx + 1) + 3 * (sy + 1);          // 4 = stays
                         cbuf[2 * j] = make_float4(x, y, vx, vy);
                         reinterpret_cast<float *>(cbuf + 2 * j + 1)[0] = vz;
-                        mycode[j] = dxg + p.nx * dyg;
+                        mycode[j] = code < 4 ? code : code - 1;            // neighbour 0..7
                     }
                     if (leave) lv |= 1ull << j;
                 }
@@ -422,11 +425,26 @@ __global__ void __launch_bounds__(kThreads, 1) k_pd(P2 p) {
                 smask = vmask & ~all;
                 __syncwarp();
                 // ---- B1: reserve the leavers' slots at the top of their new
-                // bins (the results are used only after the deposit)
+                // bins: each leaver takes a rank within its (group, neighbour)
+                // from a shared-memory counter, then lane d reserves the whole
+                // run of neighbour d with one global atomic (results used only
+                // after the deposit)
+                mydir[lig] = 0;
+                __syncwarp();
 #pragma unroll
                 for (int k = 0; k < kPerLane; ++k) {
                     const int j = k * kGroup + lig;
-                    old[k] = (lv >> j) & 1ull ? atomicAdd(&p.cnt_out[mycode[j]], 1 << 16) : 0;
+                    old[k] = (lv >> j) & 1ull ? atomicAdd(&mydir[mycode[j]], 1) : 0;
+                }
+                __syncwarp();
+                {
+                    const int cntd = mydir[lig];
+                    const int code = lig < 4 ? lig : lig + 1;
+                    int dxg = ci + code % 3 - 1, dyg = cj + code / 3 - 1;
+                    dxg = dxg < 0 ? dxg + p.nx : (dxg >= p.nx ? dxg - p.nx : dxg);
+                    dyg = dyg < 0 ? dyg + p.ny : (dyg >= p.ny ? dyg - p.ny : dyg);
+                    ddest = dxg + p.nx * dyg;
+                    dbase = cntd > 0 ? atomicAdd(&p.cnt_out[ddest], cntd << 16) : 0;
                 }
             }
             // ---- A2: deposit of the stayers (compacted, no idle lanes).  With
@@ -476,10 +494,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_pd(P2 p) {
 #pragma unroll
                 for (int k = 0; k < kPerLane; ++k) {
                     const int j = k * kGroup + lig;
-                    if (((vmask >> j) & 1ull) && !((smask >> j) & 1ull)) {
-                        const int back = bin_back(old[k]);
+                    const bool lvj = ((vmask >> j) & 1ull) && !((smask >> j) & 1ull);
+                    const int d = lvj ? mycode[j] : 0;
+                    const int dest = __shfl_sync(kFull, ddest, gshift + d);
+                    const int w0 = __shfl_sync(kFull, dbase, gshift + d);
+                    if (lvj) {
+                        const int back = bin_back(w0) + old[k];
                         if (back < p.cap) {
-                            const size_t o = (size_t)mycode[j] * p.cap + p.cap - 1 - back;
+                            const size_t o = (size_t)dest * p.cap + p.cap - 1 - back;
                             p.out[2 * o] = cbuf[2 * j];
                             p.out[2 * o + 1] = cbuf[2 * j + 1];
                         } else {
