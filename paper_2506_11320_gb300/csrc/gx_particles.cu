@@ -482,12 +482,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_pd(P2 p) {
                     const long long cell_g = __shfl_sync(kFull, (long long)cell, src);
                     const float4 *gbuf = bufs + __shfl_sync(kFull, boff, src);
                     const unsigned char *gmap = maps + __shfl_sync(kFull, moff, src);
-                    for (int r0 = 0; r0 < ns_g; r0 += 16) {
-                        const int t = r0 + (lane >> 1), half = lane & 1;
-                        if (t < ns_g) {
-                            const int j = gmap[t];
-                            p.out[2 * ((size_t)cell_g * p.cap + base_g + t) + half] = gbuf[2 * j + half];
-                        }
+                    float4 *dst = p.out + 2 * ((size_t)cell_g * p.cap + base_g);
+                    const int half = lane & 1;
+                    // two runs of 16 slots per round: both loads before both stores
+                    for (int r0 = 0; r0 < ns_g; r0 += 32) {
+                        const int t0 = r0 + (lane >> 1), t1 = t0 + 16;
+                        const bool v0 = t0 < ns_g, v1 = t1 < ns_g;
+                        const int j0 = v0 ? gmap[t0] : 0, j1 = v1 ? gmap[t1] : 0;
+                        const float4 a0 = gbuf[2 * j0 + half], a1 = gbuf[2 * j1 + half];
+                        if (v0) dst[2 * t0 + half] = a0;
+                        if (v1) dst[2 * t1 + half] = a1;
                     }
                 }
                 // leavers: the slot reserved in B1 (one 32-byte sector each)
