@@ -117,6 +117,13 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t phase)
     return false;
 }
 
+// one 32-byte particle slot written with a single 256-bit store (dst 32-byte aligned)
+__device__ __forceinline__ void st_slot(float4 *dst, float4 a, float4 b) {
+    asm volatile("st.global.v8.f32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(dst), "f"(a.x), "f"(a.y), "f"(a.z),
+                 "f"(a.w), "f"(b.x), "f"(b.y), "f"(b.z), "f"(b.w)
+                 : "memory");
+}
+
 // ------------------------------------------------------------ deposit math
 // alpha (Eq. 30) with b = beta B / c, row-major: alpha a = (a + a x b + (a.b) b)/(1 + b.b)
 __device__ __forceinline__ void alpha_tensor(float bx, float by, float bz, float al[9]) {
@@ -483,15 +490,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_pd(P2 p) {
                     const float4 *gbuf = bufs + __shfl_sync(kFull, boff, src);
                     const unsigned char *gmap = maps + __shfl_sync(kFull, moff, src);
                     float4 *dst = p.out + 2 * ((size_t)cell_g * p.cap + base_g);
-                    const int half = lane & 1;
-                    // two runs of 16 slots per round: both loads before both stores
+                    // 32 slots (1 KB contiguous) per round, one 256-bit store per lane
                     for (int r0 = 0; r0 < ns_g; r0 += 32) {
-                        const int t0 = r0 + (lane >> 1), t1 = t0 + 16;
-                        const bool v0 = t0 < ns_g, v1 = t1 < ns_g;
-                        const int j0 = v0 ? gmap[t0] : 0, j1 = v1 ? gmap[t1] : 0;
-                        const float4 a0 = gbuf[2 * j0 + half], a1 = gbuf[2 * j1 + half];
-                        if (v0) dst[2 * t0 + half] = a0;
-                        if (v1) dst[2 * t1 + half] = a1;
+                        const int t = r0 + lane;
+                        if (t < ns_g) {
+                            const int j = gmap[t];
+                            st_slot(dst + 2 * t, gbuf[2 * j], gbuf[2 * j + 1]);
+                        }
                     }
                 }
                 // leavers: the slot reserved in B1 (one 32-byte sector each)
@@ -506,8 +511,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_pd(P2 p) {
                         const int back = bin_back(w0) + old[k];
                         if (back < p.cap) {
                             const size_t o = (size_t)dest * p.cap + p.cap - 1 - back;
-                            p.out[2 * o] = cbuf[2 * j];
-                            p.out[2 * o + 1] = cbuf[2 * j + 1];
+                            st_slot(p.out + 2 * o, cbuf[2 * j], cbuf[2 * j + 1]);
                         } else {
                             atomicExch(&p.flags->overflow, 1);
                         }
