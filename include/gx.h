@@ -273,6 +273,15 @@ int gx_precond_train(gx_ctx *ctx, int npairs, int crop, int batch, int epochs, f
  * For tests. */
 int gx_precond_forward(gx_ctx *ctx, int H, int W, const float *in, float *out, void *stream);
 
+/* Apply the context's field-solve preconditioner to v ([3][N] FP64, device)
+ * exactly as FGMRES applies it to a Krylov column: z = v (none), z = D^-1 v
+ * (block Jacobi), z = D^-1 v + s N(v / s) with s = ||v||_2 / sqrt(3 N) (the
+ * network on the tensor cores, its last layer adding its output to the block
+ * Jacobi image).  D^-1 is rebuilt from the current operator (moments and LF
+ * coefficients of the last solve).  z must not alias v.  Synchronises
+ * `stream` (the norm is read back).  For tests. */
+int gx_precond_apply(gx_ctx *ctx, const double *v, double *z, void *stream);
+
 /* Loss and gradients of one [3][H][W] sample with zero padding:
  * *loss = sum (N(in) - target)^2 / (2 * 3 H W), grad (param_count FP32, the
  * layout of gx_precond_set_weights) = dloss/dparams.  Device pointers;

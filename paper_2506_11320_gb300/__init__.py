@@ -95,6 +95,7 @@ _SIGS = {
     "gx_precond_train": (C.c_int, [_CTX, C.c_int, C.c_int, C.c_int, C.c_int, C.c_float, C.c_uint64, _V, _V]),
     "gx_precond_forward": (C.c_int, [_CTX, C.c_int, C.c_int, _V, _V, _V]),
     "gx_precond_loss_grad": (C.c_int, [_CTX, C.c_int, C.c_int, _V, _V, _V, _V, _V]),
+    "gx_precond_apply": (C.c_int, [_CTX, _V, _V, _V]),
     "gx_noalloc_max_cells": (C.c_int, []),
     "gx_get_particles_noalloc": (C.c_int, [_CTX, C.c_int, _V, _V, _V, _V, _V, _V, _V, _V, _V]),
 }
@@ -316,6 +317,11 @@ class Context:
         _, H, W = x.shape
         self._check(lib().gx_precond_forward(self.h, H, W, x.data_ptr(), out.data_ptr(), _stream(stream)))
         return out
+
+    def precond_apply(self, v, z, stream=None):
+        """v, z: CUDA float64 tensors of 3 N entries; z = the solver's preconditioner applied to v."""
+        self._check(lib().gx_precond_apply(self.h, v.data_ptr(), z.data_ptr(), _stream(stream)))
+        return z
 
     def precond_loss_grad(self, x, target, grad, stream=None):
         """Loss and parameter gradient of one (3, H, W) sample, zero padding; grad: CUDA float32."""

@@ -129,7 +129,7 @@ int check_flags(gx_ctx *c, cudaStream_t st) {
         GX_CHECK(c, cudaMemsetAsync(c->dflags, 0, 3 * sizeof(int), st));
     }
     if (c->hflags->timeout) {
-        c->err = "a bounded device wait for a bulk copy gave up";
+        c->err = "a bounded device wait (bulk copy or tensor-core step) gave up";
         return GX_ETIMEOUT;
     }
     if (c->hflags->overflow) {

@@ -1,0 +1,325 @@
+// gx_convtc.cuh -- the 3x3 convolution of the learned preconditioner on the
+// fifth-generation tensor cores (tcgen05.mma kind::f16, BF16 operands, FP32
+// accumulation in tensor memory), fed by the TMA engine.
+//
+// Implicit GEMM, one MMA per (output row, tap, 16 input channels):
+//     D[128 pixels][N] += A_tap[128 pixels][16] * W_tap[N][16]^T
+// Activations live in global memory as NHWC BF16 images with a one-pixel halo
+// ring, [B][H + 2][W + 2][C]: the producer of a layer writes every edge pixel
+// a second time into the ring (its periodic image, or zero for zero padding),
+// so a tile needs no index arithmetic.  A unit of work is R image rows x 128
+// columns; its input tile, (R + 2) rows x 130 columns, arrives in shared
+// memory as C/8 channel slabs -- slab g holds channels 8g .. 8g + 7 of every
+// tile pixel, one 16-byte chunk per pixel, pixels in row-major order -- by one
+// TMA tensor copy per slab (a 5-D map: 8 channels, channel group, x, y, image;
+// box 8 x 1 x 130 x (R + 2) x 1; reads past the padded image fill zeros, and
+// those pixels feed no output).  The A operand of tap (ky, kx) for output row
+// r is then the 128 consecutive chunks starting at tile pixel
+// (r + ky) * 130 + kx: one descriptor with a start moved by whole chunks (no
+// im2col copy), LBO = slab size (next 8 channels), SBO = 128 bytes.  The
+// weights come pre-packed in the same form (slab = 8 input channels of one
+// tap for all N outputs) by one 1-D bulk copy.
+//
+// Warp roles of the 256-thread CTA, synchronised by mbarriers only:
+//   warp 0 lane 0: TMA producer, a ring of kStages tiles;
+//   warp 1 lane 0: MMA issuer, R * 9 * CIN / 16 MMAs per unit into one of two
+//                  accumulator sets, then commits (stage free, accumulators full);
+//   warps 4..7:    epilogue, warp w reading TMEM lane quarter w - 4 (pixels
+//                  32 (w - 4) .. + 31 of the unit's 128 columns), all R rows,
+//                  releasing the accumulator set before the global stores.
+// So tile loads, MMAs and epilogue stores of consecutive units overlap.
+//
+// Epilogues: ReLU to BF16 (halo ring included), FP32 without halo (padded
+// output channels), the ReLU mask of the data gradient, and -- inside the
+// solver -- the preconditioned vector z = D^-1 v + s N(v / s) written straight
+// to FP64.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include "gx_tc.cuh"
+
+namespace gxv {
+
+typedef __nv_bfloat16 bf16;
+
+constexpr int kTW = 128;            // output columns of a unit (the MMA's M)
+constexpr int kRowPix = kTW + 2;    // tile row with its halo
+constexpr int kThreads = 256;       // eight warps
+constexpr int kStages = 3;          // tiles in flight
+constexpr int kWaitLimit = 1 << 22; // mbarrier polls before a wait gives up
+
+enum { EPI_RELU = 0, EPI_F32 = 1, EPI_MASK = 2, EPI_Z = 3 };
+
+struct Args {
+    const bf16 *wtc;      // weights packed [9 CIN / 8][N][8] (zero rows beyond COUTG)
+    const float *bias;    // [COUTG] or null
+    void *out;            // EPI_RELU / EPI_MASK: bf16 [B][H+2][W+2][N]; EPI_F32: float [B][H][W][COUTG]
+    const bf16 *mask;     // EPI_MASK: bf16 [B][H+2][W+2][N], keep where > 0
+    const double *v;      // EPI_Z: Krylov vector [3][H*W] (B = 1)
+    const double *jd;     // EPI_Z: block-Jacobi inverse [H*W][9]
+    double *z;            // EPI_Z: [3][H*W]
+    double s;             // EPI_Z: output scale s
+    int *err;             // set when a bounded wait gives up
+    int B, H, W, periodic;
+};
+
+template <int CIN, int N, int R>
+struct Shape {
+    static_assert(CIN % 16 == 0 && N % 16 == 0 && N <= 32 && R >= 1 && R <= 4, "supported shapes");
+    static constexpr int kBoxPix = (R + 2) * kRowPix;                    // pixels one TMA box writes
+    static constexpr int kBoxBytes = kBoxPix * 16;
+    static constexpr int kSlabBytes = (kBoxBytes + 127) / 128 * 128;     // TMA destinations 128-byte aligned
+    static constexpr int kTileBytes = (CIN / 8) * kSlabBytes;
+    static constexpr int kTileTx = (CIN / 8) * kBoxBytes;                // bytes the tile's copies deliver
+    static constexpr int kWSlabBytes = N * 16;
+    static constexpr int kWBytes = 9 * (CIN / 8) * kWSlabBytes;
+    static constexpr int kAccCols = R * N;                               // one unit's accumulators
+    static constexpr int kTmemCols = 2 * kAccCols <= 32 ? 32 : 2 * kAccCols <= 64 ? 64 : 2 * kAccCols <= 128 ? 128 : 256;
+    // [weights][kStages tiles][bias 32 floats][barriers][tmem address, abort flag, units issued]
+    static constexpr int kBiasOff = kWBytes + kStages * kTileBytes;
+    static constexpr int kBarOff = kBiasOff + 4 * 32;
+    static constexpr int kNumBars = 1 + 2 * kStages + 4;                 // weights, full/empty, acc full/empty
+    static constexpr int kMiscOff = kBarOff + 8 * kNumBars;
+    static constexpr int kSmemBytes = kMiscOff + 16;
+};
+
+// shared memory a conv of this shape needs (bytes, from a 128-byte aligned base)
+template <int CIN, int N, int R>
+__host__ __device__ constexpr int smem_bytes() { return Shape<CIN, N, R>::kSmemBytes; }
+
+// decode a unit index into (image, first row, first column)
+template <int R>
+__device__ __forceinline__ void unit_pos(int64_t u, int nseg, int nblk, int &b, int &y0, int &x0) {
+    const int seg = (int)(u % nseg);
+    const int64_t t = u / nseg;
+    y0 = (int)(t % nblk) * R;
+    b = (int)(t / nblk);
+    x0 = seg * kTW;
+}
+
+// offset (in pixels of C channels) of pixel (b, y, x) of an image with a halo
+// ring; y in [-1, H], x in [-1, W]
+__host__ __device__ __forceinline__ int64_t halo_pix(int b, int y, int x, int H, int W) {
+    return ((int64_t)b * (H + 2) + (y + 1)) * (W + 2) + (x + 1);
+}
+
+// store the C-channel value `val` (C/8 uint4) of pixel (b, y, x) into an image
+// with a halo ring, and into the ring positions that image the pixel (its
+// periodic copies, or zeros for zero padding); every ring position images
+// exactly one pixel, so each is written once
+template <int C>
+__device__ __forceinline__ void store_with_halo(bf16 *img, int b, int y, int x, int H, int W, int periodic,
+                                                const uint4 (&val)[C / 8]) {
+    const uint4 zero = make_uint4(0, 0, 0, 0);
+    auto put = [&](int yy, int xx, bool copy) {
+        uint4 *d = reinterpret_cast<uint4 *>(img + halo_pix(b, yy, xx, H, W) * C);
+#pragma unroll
+        for (int i = 0; i < C / 8; ++i) d[i] = copy ? val[i] : zero;
+    };
+    put(y, x, true);
+    const bool p = periodic != 0;
+    const int ey = y == 0 ? H : (y == H - 1 ? -1 : -2);      // ring row imaging this pixel, or none
+    const int ex = x == 0 ? W : (x == W - 1 ? -1 : -2);
+    if (ey != -2) put(ey, x, p);
+    if (ex != -2) put(y, ex, p);
+    if (ey != -2 && ex != -2) put(ey, ex, p);
+    // a one-row or one-column image is its own neighbour on both sides
+    if (H == 1) {
+        put(-1, x, p);
+        if (ex != -2) put(-1, ex, p);
+    }
+    if (W == 1) {
+        put(y, -1, p);
+        if (ey != -2) put(ey, -1, p);
+        if (H == 1) put(-1, -1, p);
+    }
+}
+
+// out = epilogue(conv3x3(in, w) + bias) over the units cta, cta + ncta, ...
+// Every thread of the CTA calls it (blockDim.x == kThreads); sm: smem_bytes()
+// bytes, 128-byte aligned; tmap: the input's tensor map (a __grid_constant__
+// kernel parameter).  N: MMA width (output channels padded to 16 or 32);
+// COUTG: output channels of w / bias (<= N).
+template <int CIN, int N, int COUTG, int R, int EPI>
+__device__ void conv_tc(const Args &a, const CUtensorMap *tmap, unsigned char *sm, int cta, int ncta) {
+    using namespace gxt;
+    using S = Shape<CIN, N, R>;
+    static_assert(COUTG <= N && (EPI != EPI_Z || COUTG >= 3), "output channels");
+    unsigned char *sW = sm;
+    float *sBias = reinterpret_cast<float *>(sm + S::kBiasOff);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + S::kBarOff);
+    uint64_t *wfull = bars, *full = bars + 1, *empty = bars + 1 + kStages, *accfull = bars + 1 + 2 * kStages,
+             *accempty = accfull + 2;
+    uint32_t *sTm = reinterpret_cast<uint32_t *>(sm + S::kMiscOff);
+    volatile int *abort = reinterpret_cast<volatile int *>(sm + S::kMiscOff + 4);
+    volatile int *s_issued = reinterpret_cast<volatile int *>(sm + S::kMiscOff + 8);   // units the MMA thread issued
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    const int nseg = (a.W + kTW - 1) / kTW, nblk = (a.H + R - 1) / R;
+    const int64_t nunits = (int64_t)a.B * nblk * nseg;
+    if (cta >= nunits) return;
+    const int nmine = (int)((nunits - 1 - cta) / ncta) + 1;    // units of this CTA
+
+    if (tid < 32) sBias[tid] = (a.bias && tid < COUTG) ? a.bias[tid] : 0.f;
+    if (tid == 0) {
+        for (int i = 0; i < S::kNumBars; ++i) mbar_init(&bars[i], i >= 1 + 2 * kStages + 2 ? 4 * 32 : 1);
+        *abort = 0;
+        *s_issued = 0;
+    }
+    __syncwarp();
+    if (warp == 0) tmem_alloc<S::kTmemCols>(sTm);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tm = *sTm;
+
+    int nloaded = 0;    // (producer thread)
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---- TMA producer
+            mbar_arrive_expect_tx(wfull, S::kWBytes);
+            bulk_load(smem_addr(sW), a.wtc, S::kWBytes, wfull);
+            int i = 0;
+            for (; i < nmine; ++i) {
+                const int st = i % kStages, n = i / kStages;
+                if (n > 0 && !mbar_wait_or_abort(&empty[st], (n - 1) & 1, kWaitLimit, abort)) break;
+                int b, y0, x0;
+                unit_pos<R>(cta + (int64_t)i * ncta, nseg, nblk, b, y0, x0);
+                const uint32_t dst = smem_addr(sm + S::kWBytes + st * S::kTileBytes);
+                mbar_arrive_expect_tx(&full[st], S::kTileTx);
+#pragma unroll
+                for (int g = 0; g < CIN / 8; ++g)
+                    tma_load_5d(dst + g * S::kSlabBytes, tmap, 0, g, x0, y0, b, &full[st]);
+            }
+            nloaded = i;
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---- MMA issuer
+            constexpr uint32_t idesc = idesc_bf16_f32(kTW, N);
+            const uint64_t bdesc = sdesc(smem_addr(sW), S::kWSlabBytes, 128);
+            bool ok = mbar_wait_or_abort(wfull, 0, kWaitLimit, abort);
+            int i = 0;
+            for (; ok && i < nmine; ++i) {
+                const int st = i % kStages, n = i / kStages, k = i & 1, m = i >> 1;
+                if (!mbar_wait_or_abort(&full[st], n & 1, kWaitLimit, abort)) break;
+                if (m > 0 && !mbar_wait_or_abort(&accempty[k], (m - 1) & 1, kWaitLimit, abort)) break;
+                tc_fence_after();
+                const uint64_t ad = sdesc(smem_addr(sm + S::kWBytes + st * S::kTileBytes), S::kSlabBytes, 128);
+                const uint32_t dacc = tm + k * S::kAccCols;
+#pragma unroll
+                for (int tap = 0; tap < 9; ++tap) {
+#pragma unroll
+                    for (int kc = 0; kc < CIN / 16; ++kc) {
+#pragma unroll
+                        for (int r = 0; r < R; ++r) {
+                            const uint32_t aoff = ((r + tap / 3) * kRowPix + tap % 3) + 2 * kc * (S::kSlabBytes / 16);
+                            const uint32_t boff = (tap * (CIN / 8) + 2 * kc) * (S::kWSlabBytes / 16);
+                            mma_bf16(dacc + r * N, ad + aoff, bdesc + boff, idesc, tap > 0 || kc > 0);
+                        }
+                    }
+                }
+                mma_commit(&empty[st]);
+                mma_commit(&accfull[k]);
+            }
+            *s_issued = i;
+        }
+    } else if (warp >= 4) {
+        // ---- epilogue
+        const int q4 = warp - 4;
+        for (int i = 0; i < nmine; ++i) {
+            const int k = i & 1, m = i >> 1;
+            // one lane polls; the warp reads tensor memory together (.sync.aligned)
+            int ok = 0;
+            if (lane == 0) ok = mbar_wait_or_abort(&accfull[k], m & 1, kWaitLimit, abort);
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (!ok) break;
+            tc_fence_after();
+            float acc[R][N];
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+#pragma unroll
+                for (int j = 0; j < N / 16; ++j)
+                    tmem_ld16(tm + ((uint32_t)(32 * q4) << 16) + k * S::kAccCols + r * N + 16 * j,
+                              *reinterpret_cast<float(*)[16]>(&acc[r][16 * j]));
+            tc_fence_before();
+            mbar_arrive(&accempty[k]);
+            int b, y0, x0;
+            unit_pos<R>(cta + (int64_t)i * ncta, nseg, nblk, b, y0, x0);
+            const int xx = x0 + 32 * q4 + lane;
+            if (xx >= a.W) continue;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int yy = y0 + r;
+                if (yy >= a.H) break;
+                if (EPI == EPI_RELU || EPI == EPI_MASK) {
+                    uint4 packed[N / 8];
+                    uint32_t *pw = reinterpret_cast<uint32_t *>(packed);
+                    if (EPI == EPI_MASK) {
+                        const uint4 *mk = reinterpret_cast<const uint4 *>(a.mask + halo_pix(b, yy, xx, a.H, a.W) * N);
+#pragma unroll
+                        for (int c8 = 0; c8 < N / 8; ++c8) {
+                            const uint4 m4 = mk[c8];
+                            const uint32_t mw[4] = {m4.x, m4.y, m4.z, m4.w};
+#pragma unroll
+                            for (int h = 0; h < 4; ++h) {
+                                const __nv_bfloat162 m2 = *reinterpret_cast<const __nv_bfloat162 *>(&mw[h]);
+                                const int c = 8 * c8 + 2 * h;
+                                const float v0 = __bfloat162float(m2.x) > 0.f ? acc[r][c] : 0.f;
+                                const float v1 = __bfloat162float(m2.y) > 0.f ? acc[r][c + 1] : 0.f;
+                                const __nv_bfloat162 o = __floats2bfloat162_rn(v0, v1);
+                                pw[c / 2] = *reinterpret_cast<const uint32_t *>(&o);
+                            }
+                        }
+                    } else {
+#pragma unroll
+                        for (int c = 0; c < N; c += 2) {
+                            const __nv_bfloat162 o = __floats2bfloat162_rn(fmaxf(acc[r][c] + sBias[c], 0.f),
+                                                                           fmaxf(acc[r][c + 1] + sBias[c + 1], 0.f));
+                            pw[c / 2] = *reinterpret_cast<const uint32_t *>(&o);
+                        }
+                    }
+                    store_with_halo<N>(static_cast<bf16 *>(a.out), b, yy, xx, a.H, a.W, a.periodic, packed);
+                } else if (EPI == EPI_F32) {
+                    const int64_t pix = ((int64_t)b * a.H + yy) * a.W + xx;
+                    float4 *o4 = reinterpret_cast<float4 *>(static_cast<float *>(a.out) + pix * COUTG);
+#pragma unroll
+                    for (int c = 0; c < COUTG; c += 4)
+                        o4[c / 4] = make_float4(acc[r][c] + sBias[c], acc[r][c + 1] + sBias[c + 1],
+                                                acc[r][c + 2] + sBias[c + 2], acc[r][c + 3] + sBias[c + 3]);
+                } else {   // EPI_Z: z = D^-1 v + s y  (B = 1)
+                    const int64_t HW = (int64_t)a.H * a.W, q = (int64_t)yy * a.W + xx;
+                    const double v0 = __ldcg(a.v + q), v1 = __ldcg(a.v + HW + q), v2 = __ldcg(a.v + 2 * HW + q);
+                    const double *o = a.jd + q * 9;
+#pragma unroll
+                    for (int c = 0; c < 3; ++c)
+                        a.z[c * HW + q] = o[3 * c] * v0 + o[3 * c + 1] * v1 + o[3 * c + 2] * v2 +
+                                          a.s * (double)(acc[r][c] + sBias[c]);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        // drain before the barriers and buffers are reused: every copy issued
+        // has landed and every MMA issued has completed (normally all consumed
+        // already; after an abort these are the operations still in flight)
+        const int nissued = *s_issued;
+        for (int j = nloaded > kStages ? nloaded - kStages : 0; j < nloaded; ++j) {
+            mbar_wait(&full[j % kStages], (j / kStages) & 1, kWaitLimit);
+            if (j < nissued) mbar_wait(&empty[j % kStages], (j / kStages) & 1, kWaitLimit);
+        }
+        if (*abort && a.err) atomicExch(a.err, 1);
+    }
+    __syncthreads();
+    if (warp == 0) {
+        __syncwarp();
+        tc_fence_after();
+        tmem_dealloc<S::kTmemCols>(tm);
+    }
+    __syncthreads();     // shared memory (barriers included) is reused by the caller's next step
+}
+
+}  // namespace gxv

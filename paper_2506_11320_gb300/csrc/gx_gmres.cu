@@ -18,13 +18,15 @@
 // Givens rotations, the convergence test) without another barrier.  An
 // Arnoldi step costs four barriers.  The true residual ||b - A x|| / ||b|| is
 // recomputed at every restart and decides convergence.  The learned
-// preconditioner also runs inside the kernel: the Krylov column is packed to
-// BF16, the four convolution layers run on the tensor cores over the whole
-// grid (a barrier between layers), and the correction is added to the block
-// Jacobi image, so a solve is one launch with every preconditioner.
+// preconditioner also runs inside the kernel: the thread that forms a Krylov
+// column also packs it to BF16 for the network, the four convolution layers
+// run on the fifth-generation tensor cores (TMA-fed tcgen05, accumulators in
+// tensor memory) over the whole grid with a barrier before each layer, and the
+// last adds the correction to the block-Jacobi image, so a solve is one launch
+// with every preconditioner.
 #include <cooperative_groups.h>
 
-#include "gx_conv.cuh"
+#include "gx_convtc.cuh"
 #include "gx_op.cuh"
 
 namespace cg = cooperative_groups;
@@ -68,10 +70,14 @@ struct CoArgs {
     int net;            // apply the learned preconditioner (the fields below)
     NetSolverArgs nn;
     double ns;          // its scale s = 1 / sqrt(3 N) (the Krylov columns have unit norm)
+    int *err;           // set when a bounded wait of the network's tensor-core steps gives up
 };
 
-// shared memory of the in-kernel network (bf16 elements): the largest layer
-constexpr int kNetSmemElems = gxc::conv_smem_elems<32, 32>();
+// in-kernel network: image rows per convolution unit, shared memory of the
+// largest layer (+ alignment slack)
+constexpr int kNetRows = 2;
+constexpr int kNetSmemBytes = gxv::smem_bytes<32, 32, kNetRows>() + 128;
+static_assert(kB == gxv::kThreads, "the convolution runs on the solver's 256-thread CTAs");
 
 // every thread's node set: q = tid, tid + nthreads, ...
 #define NODE_LOOP(q) \
@@ -126,53 +132,65 @@ __device__ __forceinline__ void jacobi_node(const double *jd, const double *v, d
     z[2 * N + q] = o[6] * x0 + o[7] * x1 + o[8] * x2;
 }
 
-// Z_j = D^-1 V_j + s N(V_j / s), every CTA of the cooperative grid taking part
-__device__ void net_apply(const CoArgs &a, cg::grid_group &grid, int j, gxc::bf16 *sm) {
-    using namespace gxc;
-    const int64_t N = a.N, n = 3 * N;
-    const double *vj = a.V + (size_t)j * n;
-    double *zj = a.Z + (size_t)j * n;
-    bf16 *x0 = static_cast<bf16 *>(a.nn.x0);
-    const double inv_s = 1.0 / a.ns;
-    NODE_LOOP(q) {
-        __align__(16) bf16 v[16];
-#pragma unroll
-        for (int c = 0; c < 16; ++c) v[c] = __float2bfloat16_rn(c < 3 ? (float)(vj[c * N + q] * inv_s) : 0.f);
-        reinterpret_cast<uint4 *>(x0 + q * 16)[0] = reinterpret_cast<uint4 *>(v)[0];
-        reinterpret_cast<uint4 *>(x0 + q * 16)[1] = reinterpret_cast<uint4 *>(v)[1];
-    }
-    const int H = a.op.g.ny, W = a.op.g.nx;
-    ConvArgs c1{x0, static_cast<const bf16 *>(a.nn.w[0]), a.nn.b[0], a.nn.h1, nullptr, nullptr, 1, H, W, 1};
-    ConvArgs c2{static_cast<const bf16 *>(a.nn.h1), static_cast<const bf16 *>(a.nn.w[1]), a.nn.b[1], a.nn.h2,
-                nullptr, nullptr, 1, H, W, 1};
-    ConvArgs c3{static_cast<const bf16 *>(a.nn.h2), static_cast<const bf16 *>(a.nn.w[2]), a.nn.b[2], a.nn.h3,
-                nullptr, nullptr, 1, H, W, 1};
-    ConvArgs c4{static_cast<const bf16 *>(a.nn.h3), static_cast<const bf16 *>(a.nn.w[3]), a.nn.b[3], a.nn.y,
-                nullptr, nullptr, 1, H, W, 1};
+// the network input of node q: (V_j at q) / s in BF16, 16 channels, into the
+// halo-ring image x0 (periodic copies included); written by the thread that
+// computes V_j at q, so the layer-1 tiles see it after the next grid barrier
+__device__ __forceinline__ void net_pack_node(const CoArgs &a, int64_t q, double v0, double v1, double v2) {
+    const double inv = 1.0 / a.ns;
+    const __nv_bfloat162 p01 = __floats2bfloat162_rn((float)(v0 * inv), (float)(v1 * inv));
+    const __nv_bfloat162 p2 = __floats2bfloat162_rn((float)(v2 * inv), 0.f);
+    const uint4 val[2] = {make_uint4(*reinterpret_cast<const uint32_t *>(&p01), *reinterpret_cast<const uint32_t *>(&p2),
+                                     0, 0),
+                          make_uint4(0, 0, 0, 0)};
+    const int W = a.op.g.nx;
+    gxv::store_with_halo<16>(static_cast<gxv::bf16 *>(a.nn.x0), 0, (int)(q / W), (int)(q % W), a.op.g.ny, W, 1, val);
+}
+
+// Z_j = D^-1 V_j + s N(V_j / s), every CTA of the cooperative grid taking part:
+// four tensor-core convolutions (gx_convtc.cuh) with a grid barrier before
+// each layer (a layer reads its neighbours' inputs); the first reads the
+// packed V_j, the last writes Z_j itself (the caller's barrier follows)
+__device__ void net_apply(const CoArgs &a, cg::grid_group &grid, int j, unsigned char *sm) {
+    using namespace gxv;
+    const int64_t n = 3 * a.N;
+    Args c{};
+    c.err = a.err;
+    c.B = 1;
+    c.H = a.op.g.ny;
+    c.W = a.op.g.nx;
+    c.periodic = 1;
     grid.sync();
-    conv_tiles<16, 32, EPI_RELU>(c1, sm, blockIdx.x, gridDim.x);
+    c.wtc = static_cast<const bf16 *>(a.nn.w[0]);
+    c.bias = a.nn.b[0];
+    c.out = a.nn.h1;
+    conv_tc<16, 32, 32, kNetRows, EPI_RELU>(c, &a.nn.tm[0], sm, blockIdx.x, gridDim.x);
     grid.sync();
-    conv_tiles<32, 32, EPI_RELU>(c2, sm, blockIdx.x, gridDim.x);
+    c.wtc = static_cast<const bf16 *>(a.nn.w[1]);
+    c.bias = a.nn.b[1];
+    c.out = a.nn.h2;
+    conv_tc<32, 32, 32, kNetRows, EPI_RELU>(c, &a.nn.tm[1], sm, blockIdx.x, gridDim.x);
     grid.sync();
-    conv_tiles<32, 32, EPI_RELU>(c3, sm, blockIdx.x, gridDim.x);
+    c.wtc = static_cast<const bf16 *>(a.nn.w[2]);
+    c.bias = a.nn.b[2];
+    c.out = a.nn.h3;
+    conv_tc<32, 32, 32, kNetRows, EPI_RELU>(c, &a.nn.tm[2], sm, blockIdx.x, gridDim.x);
     grid.sync();
-    conv_tiles<32, 8, EPI_F32>(c4, sm, blockIdx.x, gridDim.x);
-    grid.sync();
-    NODE_LOOP(q) {
-        const double *o = a.jd + (size_t)q * 9;
-        const double r0 = vj[q], r1 = vj[N + q], r2 = vj[2 * N + q];
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-            zj[c * N + q] = o[3 * c] * r0 + o[3 * c + 1] * r1 + o[3 * c + 2] * r2 +
-                            a.ns * (double)__ldcg(a.nn.y + q * 8 + c);
-    }
+    c.wtc = static_cast<const bf16 *>(a.nn.w[3]);
+    c.bias = a.nn.b[3];
+    c.out = nullptr;
+    c.v = a.V + (size_t)j * n;
+    c.jd = a.jd;
+    c.z = a.Z + (size_t)j * n;
+    c.s = a.ns;
+    conv_tc<32, 16, 8, kNetRows, EPI_Z>(c, &a.nn.tm[3], sm, blockIdx.x, gridDim.x);
 }
 
 // NET: the learned preconditioner is applied in the kernel (the plain and
 // Jacobi instantiation is smaller and fits two CTAs per SM)
 template <bool NET>
-__global__ void __launch_bounds__(kB, NET ? 1 : 2) k_fgmres(CoArgs a) {
-    extern __shared__ __align__(16) unsigned char gsm[];
+__global__ void __launch_bounds__(kB, NET ? 1 : 2) k_fgmres(const __grid_constant__ CoArgs a) {
+    extern __shared__ __align__(128) unsigned char gsm_raw[];
+    unsigned char *gsm = gsm_raw + ((128 - (gxt::smem_addr(gsm_raw) & 127)) & 127);
     cg::grid_group grid = cg::this_grid();
     __shared__ double sred[kWarps * 8];
     __shared__ double hs[2][kMaxM + 2];
@@ -243,13 +261,14 @@ __global__ void __launch_bounds__(kB, NET ? 1 : 2) k_fgmres(CoArgs a) {
 #pragma unroll
                 for (int c = 0; c < 3; ++c) a.V[c * N + q] = a.r[c * N + q] * inv;
                 if (a.jd && !NET) jacobi_node(a.jd, a.V, a.Z, N, q);
+                if (NET) net_pack_node(a, q, a.V[q], a.V[N + q], a.V[2 * N + q]);
             }
             __syncthreads();
             if (writer) {
                 st->j = 0; st->done = 0; st->jend = -1;
                 for (int i = 0; i <= kMaxM; ++i) st->g[i] = i == 0 ? beta : 0.0;
             }
-            if (NET) net_apply(a, grid, 0, reinterpret_cast<gxc::bf16 *>(gsm));
+            if (NET) net_apply(a, grid, 0, gsm);
             grid.sync();
         }
 
@@ -365,10 +384,11 @@ __global__ void __launch_bounds__(kB, NET ? 1 : 2) k_fgmres(CoArgs a) {
 #pragma unroll
                 for (int c = 0; c < 3; ++c) v1[c * N + q] = a.w[c * N + q] * inv;
                 if (a.jd && !NET) jacobi_node(a.jd, v1, a.Z + (size_t)(j + 1) * n, N, q);
+                if (NET) net_pack_node(a, q, v1[q], v1[N + q], v1[2 * N + q]);
             }
             ++j;
             if (writer) st->j = j;
-            if (NET) net_apply(a, grid, j, reinterpret_cast<gxc::bf16 *>(gsm));
+            if (NET) net_apply(a, grid, j, gsm);
             grid.sync();
             continue;
         }
@@ -461,7 +481,7 @@ int gx_fgmres(gx_ctx *c, cudaStream_t st) {
     int rc;
     if (pc == GX_PRECOND_JACOBI || pc == GX_PRECOND_NET) { rc = gx_build_jacobi(c, st); if (rc) return rc; }
     const bool use_net = pc == GX_PRECOND_NET;
-    const size_t smem = use_net ? (size_t)kNetSmemElems * sizeof(gxc::bf16) : 0;
+    const size_t smem = use_net ? (size_t)kNetSmemBytes : 0;
     static int grids[2] = {0, 0};
     int &grid = grids[use_net ? 1 : 0];
     const void *kfn = use_net ? (const void *)k_fgmres<true> : (const void *)k_fgmres<false>;
@@ -493,6 +513,7 @@ int gx_fgmres(gx_ctx *c, cudaStream_t st) {
     if (use_net) {
         if ((rc = gx_net_solver_args(c, &a.nn, st))) return rc;
         a.ns = 1.0 / std::sqrt(3.0 * (double)c->N);
+        a.err = &c->dflags->timeout;
     }
     if (gx_net_collecting(c)) {
         // training pair of this solve: r0 = b - A E^n, so that A (E^{n+theta} - E^n) = r0

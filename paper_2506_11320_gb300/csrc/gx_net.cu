@@ -11,24 +11,28 @@
 // translation-invariant remainder A^-1 r - D^-1 r, a few per cent of z at the
 // usual time steps, so its BF16 rounding error is relative to that remainder.
 //
-// Kernels (all on the tensor cores through mma.sync m16n8k16 BF16 -> FP32):
-//   * k_conv: the implicit-GEMM convolution of gx_conv.cuh.  The forward pass
-//     and the data gradient (the same convolution with the kernel flipped and
-//     the channel roles swapped, masked by the ReLU of the layer input) both
-//     use it; inside the solver the forward pass runs in the solver's own
-//     kernel.
+// Kernels:
+//   * k_convtc: the implicit-GEMM convolution of gx_convtc.cuh on the tcgen05
+//     tensor cores (TMA-fed, BF16 operands, FP32 accumulators in tensor
+//     memory).  The forward pass and the data gradient (the same convolution
+//     with the kernel flipped and the channel roles swapped, masked by the
+//     ReLU of the layer input) both use it; inside the solver the forward pass
+//     runs in the solver's own kernel.
 //   * k_wgrad: weight gradient dW[co][tap][ci] = sum_p dY[p][co] X[p+tap][ci],
-//     a contraction over pixels (ldmatrix.trans operands), accumulated by a
-//     persistent grid in registers and added to FP32 global sums once per CTA.
+//     a contraction over pixels (mma.sync m16n8k16 with ldmatrix.trans
+//     operands), accumulated by a persistent grid in registers and added to
+//     FP32 global sums once per CTA.
 //   * Adam on an FP32 master copy; BF16 copies refreshed after each update.
 // Channel counts are padded for the MMA shapes: 3 input channels -> 16,
-// 3 output channels -> 8 (forward) or 16 (gradient).
+// 3 output channels -> 8 (stored forward output; 16 in the MMA) or 16
+// (gradient).  BF16 activations are images with a one-pixel halo ring.
 #include <cuda_bf16.h>
 
 #include <cstring>
 #include <random>
 
 #include "gx_conv.cuh"
+#include "gx_convtc.cuh"
 
 using namespace gxc;
 
@@ -38,7 +42,8 @@ constexpr int kNL = 4;
 constexpr int kCin[kNL] = {3, 32, 32, 32};
 constexpr int kCout[kNL] = {32, 32, 32, 3};
 constexpr int kCinP[kNL] = {16, 32, 32, 32};    // padded input channels (storage of the layer input)
-constexpr int kCoutP[kNL] = {32, 32, 32, 8};    // padded output channels (forward)
+constexpr int kCoutP[kNL] = {32, 32, 32, 8};    // padded output channels (forward storage)
+constexpr int kNmma[kNL] = {32, 32, 32, 16};    // output channels of the forward MMA (N)
 constexpr int kGCoutP[kNL] = {32, 32, 32, 16};  // padded output channels of the gradient (dY) storage
 
 constexpr int64_t layer_w_count(int l) { return (int64_t)kCout[l] * kCin[l] * 9; }
@@ -49,17 +54,22 @@ inline int64_t param_offset(int l) {
 }
 inline int64_t param_count() { return param_offset(kNL); }
 
-// the forward/data-gradient convolution as a kernel (a persistent grid)
-template <int CIN, int COUT, int EPI>
-__global__ void __launch_bounds__(256) k_conv(ConvArgs a) {
-    __shared__ __align__(16) bf16 sm[conv_smem_elems<CIN, COUT>()];
-    if (a.skip && *a.skip) return;
-    conv_tiles<CIN, COUT, EPI>(a, sm, blockIdx.x, gridDim.x);
+// the forward/data-gradient convolution as a kernel (a persistent grid of
+// tensor-core CTAs, gx_convtc.cuh); R image rows per unit of work
+constexpr int kConvRows = 2;
+
+template <int CIN, int N, int COUTG, int EPI>
+__global__ void __launch_bounds__(gxv::kThreads) k_convtc(const __grid_constant__ CUtensorMap tmap, gxv::Args a,
+                                                          const int *skip) {
+    extern __shared__ __align__(128) unsigned char dsm[];
+    if (skip && *skip) return;
+    unsigned char *sm = dsm + ((128 - (gxt::smem_addr(dsm) & 127)) & 127);
+    gxv::conv_tc<CIN, N, COUTG, kConvRows, EPI>(a, &tmap, sm, blockIdx.x, gridDim.x);
 }
 
 struct WgArgs {
-    const bf16 *dy;      // [B][H][W][COUTP] gradient wrt the layer output
-    const bf16 *x;       // [B][H][W][CIN] layer input
+    const bf16 *dy;      // [B][H+2][W+2][COUTP] gradient wrt the layer output (halo ring)
+    const bf16 *x;       // [B][H+2][W+2][CIN] layer input (halo ring: periodic copies or zeros)
     float *gw;           // [COUTP][9][CIN] FP32 sums
     float *gb;           // [COUTP]
     int B, H, W, periodic;
@@ -86,14 +96,14 @@ __global__ void __launch_bounds__(256) k_wgrad(WgArgs a) {
         const int b = (int)(t / (tx * ty)), rem = (int)(t % (tx * ty));
         const int y0 = (rem / tx) * kTH, x0 = (rem % tx) * kTW;
         __syncthreads();
-        load_tile<CIN>(sX, a.x, b, a.H, a.W, y0, x0, a.periodic);
+        load_tile_halo<CIN>(sX, a.x, b, a.H, a.W, y0, x0);
         constexpr int DV = COUTP / 8;
         for (int q = threadIdx.x; q < kTH * kTW * DV; q += blockDim.x) {
             const int pix = q / DV, v = q % DV;
             const int yy = y0 + pix / kTW, xx = x0 + pix % kTW;
             uint4 val = make_uint4(0, 0, 0, 0);
             if (yy < a.H && xx < a.W)
-                val = *reinterpret_cast<const uint4 *>(a.dy + (((int64_t)b * a.H + yy) * a.W + xx) * COUTP + v * 8);
+                val = *reinterpret_cast<const uint4 *>(a.dy + gxv::halo_pix(b, yy, xx, a.H, a.W) * COUTP + v * 8);
             *reinterpret_cast<uint4 *>(sD + pix * SD + v * 8) = val;
         }
         __syncthreads();
@@ -145,22 +155,29 @@ __global__ void __launch_bounds__(256) k_wgrad(WgArgs a) {
 // FP32 master parameters (layout W[co][ci][ky][kx], b[co] per layer) -> BF16
 // forward weights [coutP][9][cinP], FP32 bias [coutP], BF16 data-gradient
 // weights [cin][9][gcoutP] (flipped taps, channel roles swapped)
+// FP32 master weights -> BF16 operands of the tensor-core convolution, packed
+// as its weight slabs: element (n, k) of W_l viewed as [N][9 CINP] (k = tap *
+// CINP + ci) at ((k / 8) * NP + n) * 8 + k % 8, zero for padded n or ci.
+//   wf: the forward kernel, n = output channel (NP = nP);
+//   wd: the data-gradient kernel (flipped taps, channel roles swapped),
+//       n = input channel of the layer (NP = cin), k over (tap, output channel
+//       padded to gcoutP).
 __global__ void k_pack_weights(const float *params, bf16 *wf, float *bias, bf16 *wd, int cin, int cout, int cinP,
-                               int coutP, int gcoutP, int64_t off) {
+                               int nP, int coutP, int gcoutP, int64_t off) {
     const float *W = params + off, *bsrc = params + off + (int64_t)cout * cin * 9;
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < coutP * 9 * cinP; t += gridDim.x * blockDim.x) {
-        const int co = t / (9 * cinP), rem = t % (9 * cinP), tap = rem / cinP, ci = rem % cinP;
-        const float v = (co < cout && ci < cin) ? W[((co * cin + ci) * 9) + tap] : 0.f;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < 9 * cinP * nP; t += gridDim.x * blockDim.x) {
+        const int kg = t / (nP * 8), n = (t / 8) % nP, k = kg * 8 + t % 8;
+        const int tap = k / cinP, ci = k % cinP;
+        const float v = (n < cout && ci < cin) ? W[((n * cin + ci) * 9) + tap] : 0.f;
         wf[t] = __float2bfloat16_rn(v);
     }
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < coutP; t += gridDim.x * blockDim.x)
         bias[t] = t < cout ? bsrc[t] : 0.f;
     if (wd) {
-        // dgrad conv: output channel = ci (cin of this layer, 32 for layers 2-4),
-        // input channel = co (padded to gcoutP), tap flipped
-        for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < cin * 9 * gcoutP; t += gridDim.x * blockDim.x) {
-            const int ci = t / (9 * gcoutP), rem = t % (9 * gcoutP), tp = rem / gcoutP, co = rem % gcoutP;
-            const float v = co < cout ? W[((co * cin + ci) * 9) + (8 - tp)] : 0.f;
+        for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < 9 * gcoutP * cin; t += gridDim.x * blockDim.x) {
+            const int kg = t / (cin * 8), n = (t / 8) % cin, k = kg * 8 + t % 8;
+            const int tp = k / gcoutP, co = k % gcoutP;
+            const float v = co < cout ? W[((co * cin + n) * 9) + (8 - tp)] : 0.f;
             wd[t] = __float2bfloat16_rn(v);
         }
     }
@@ -191,26 +208,20 @@ __global__ void k_adam(float *p, const float *g, float *m1, float *m2, int64_t n
     }
 }
 
-// [3][H][W] FP32 or FP64 field (times `scale` or 1/scale from a device sum)
-// -> BF16 NHWC with 16 channels
+// [3][H][W] FP32 or FP64 field times `scale` -> BF16 NHWC image with 16
+// channels (3 used) and a halo ring (periodic copies or zeros)
 template <typename T>
-__global__ void k_pack_input(const T *src, int64_t HW, bf16 *dst, const double *sumsq, double fixed_scale) {
-    double inv = fixed_scale;
-    if (sumsq) {
-        const double s = sqrt(*sumsq / (3.0 * HW));
-        inv = s > 0.0 ? 1.0 / s : 0.0;
-    }
+__global__ void k_pack_input(const T *src, int H, int W, double scale, int periodic, bf16 *dst) {
+    const int64_t HW = (int64_t)H * W;
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < HW; p += (int64_t)gridDim.x * blockDim.x) {
-        __align__(16) bf16 v[16];
-#pragma unroll
-        for (int c = 0; c < 16; ++c) v[c] = __float2bfloat16_rn(c < 3 ? (float)(src[c * HW + p] * inv) : 0.f);
-        reinterpret_cast<uint4 *>(dst + p * 16)[0] = reinterpret_cast<uint4 *>(v)[0];
-        reinterpret_cast<uint4 *>(dst + p * 16)[1] = reinterpret_cast<uint4 *>(v)[1];
+        const __nv_bfloat162 p01 = __floats2bfloat162_rn((float)(src[p] * scale), (float)(src[HW + p] * scale));
+        const __nv_bfloat162 p2 = __floats2bfloat162_rn((float)(src[2 * HW + p] * scale), 0.f);
+        const uint4 val[2] = {make_uint4(*reinterpret_cast<const uint32_t *>(&p01),
+                                         *reinterpret_cast<const uint32_t *>(&p2), 0, 0),
+                              make_uint4(0, 0, 0, 0)};
+        gxv::store_with_halo<16>(dst, 0, (int)(p / W), (int)(p % W), H, W, periodic, val);
     }
 }
-
-
-
 
 // training crops: for crop b, input = r / s_b on a (C+8)^2 window (4-pixel halo,
 // periodic in the source field) and target = t / s_b on the central C^2, where
@@ -249,12 +260,12 @@ __global__ void k_crop_gather(const float *pairs, int64_t N, int nx, int ny, con
         const int yy = t / S, xx = t % S;
         const int gy = wrapn(sp.y0 + yy - 4, ny), gx = wrapn(sp.x0 + xx - 4, nx);
         const int64_t q = gy * (int64_t)nx + gx;
-        __align__(16) bf16 v[16];
-#pragma unroll
-        for (int c = 0; c < 16; ++c) v[c] = __float2bfloat16_rn(c < 3 ? r[c * N + q] * inv : 0.f);
-        bf16 *d = x0 + ((int64_t)b * S * S + t) * 16;
-        reinterpret_cast<uint4 *>(d)[0] = reinterpret_cast<uint4 *>(v)[0];
-        reinterpret_cast<uint4 *>(d)[1] = reinterpret_cast<uint4 *>(v)[1];
+        const __nv_bfloat162 p01 = __floats2bfloat162_rn(r[q] * inv, r[N + q] * inv);
+        const __nv_bfloat162 p2 = __floats2bfloat162_rn(r[2 * N + q] * inv, 0.f);
+        const uint4 val[2] = {make_uint4(*reinterpret_cast<const uint32_t *>(&p01),
+                                         *reinterpret_cast<const uint32_t *>(&p2), 0, 0),
+                              make_uint4(0, 0, 0, 0)};
+        gxv::store_with_halo<16>(x0, b, yy, xx, S, S, 0, val);
         const bool inner = yy >= 4 && yy < 4 + C && xx >= 4 && xx < 4 + C;
 #pragma unroll
         for (int c = 0; c < 3; ++c) target[((int64_t)b * S * S + t) * 3 + c] = inner ? e[c * N + q] * inv : 0.f;
@@ -262,7 +273,7 @@ __global__ void k_crop_gather(const float *pairs, int64_t N, int nx, int ny, con
 }
 
 // loss = sum over the loss region of (y - t)^2 / (2 Nout) and dY = (y - t) / Nout
-// there (zero elsewhere), dY stored BF16 with 16 channels
+// there (zero elsewhere), dY stored BF16 with 16 channels and a zero halo ring
 __global__ void k_loss(const float *y, const float *target, int B, int H, int W, int ry0, int rx0, int RH, int RW,
                        float inv_nout, bf16 *dy, double *loss) {
     double s = 0.0;
@@ -281,8 +292,8 @@ __global__ void k_loss(const float *y, const float *target, int B, int H, int W,
                 v[c] = __float2bfloat16_rn(d * inv_nout);
             }
         }
-        reinterpret_cast<uint4 *>(dy + p * 16)[0] = reinterpret_cast<uint4 *>(v)[0];
-        reinterpret_cast<uint4 *>(dy + p * 16)[1] = reinterpret_cast<uint4 *>(v)[1];
+        const uint4 val[2] = {reinterpret_cast<uint4 *>(v)[0], reinterpret_cast<uint4 *>(v)[1]};
+        gxv::store_with_halo<16>(dy, (int)(p / (H * W)), yy, xx, H, W, 0, val);
     }
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if ((threadIdx.x & 31) == 0) atomicAdd(loss, 0.5 * s * inv_nout);
@@ -337,8 +348,8 @@ struct Net {
     float *bias[kNL] = {};
     float *gw[kNL] = {}, *gb[kNL] = {};
     int have_weights = 0;
-    // activations
-    int64_t cap_pix = 0;
+    // activations: BF16 images with a halo ring [B][H+2][W+2][C]; y, target [B][H][W][*]
+    int64_t cap_pix = 0, cap_halo = 0;
     bf16 *x0 = nullptr, *h1 = nullptr, *h2 = nullptr, *h3 = nullptr;
     bf16 *d4 = nullptr, *d3 = nullptr, *d2 = nullptr, *d1 = nullptr;
     float *y = nullptr, *target = nullptr;
@@ -362,7 +373,7 @@ static int net_alloc(gx_ctx *c) {
     GX_CHECK(c, cudaMemset(n->m1, 0, P * sizeof(float)));
     GX_CHECK(c, cudaMemset(n->m2, 0, P * sizeof(float)));
     for (int l = 0; l < kNL; ++l) {
-        GX_CHECK(c, cudaMalloc(&n->wf[l], (size_t)kCoutP[l] * 9 * kCinP[l] * sizeof(bf16)));
+        GX_CHECK(c, cudaMalloc(&n->wf[l], (size_t)kNmma[l] * 9 * kCinP[l] * sizeof(bf16)));
         GX_CHECK(c, cudaMalloc(&n->bias[l], kCoutP[l] * sizeof(float)));
         if (l > 0) GX_CHECK(c, cudaMalloc(&n->wd[l], (size_t)kCin[l] * 9 * kGCoutP[l] * sizeof(bf16)));
         GX_CHECK(c, cudaMalloc(&n->gw[l], (size_t)kGCoutP[l] * 9 * kCinP[l] * sizeof(float)));
@@ -386,38 +397,106 @@ static int net_refresh(gx_ctx *c, cudaStream_t st) {
     Net *n = c->net;
     for (int l = 0; l < kNL; ++l) {
         k_pack_weights<<<64, 256, 0, st>>>(n->params, n->wf[l], n->bias[l], l > 0 ? n->wd[l] : nullptr, kCin[l],
-                                            kCout[l], kCinP[l], kCoutP[l], kGCoutP[l], param_offset(l));
+                                            kCout[l], kCinP[l], kNmma[l], kCoutP[l], kGCoutP[l], param_offset(l));
         GX_LAUNCHED(c);
     }
     n->have_weights = 1;
     return GX_OK;
 }
 
-static int net_reserve(gx_ctx *c, int64_t pix) {
+// activation buffers for B images of H x W
+static int net_reserve(gx_ctx *c, int B, int H, int W) {
     Net *n = c->net;
-    if (pix <= n->cap_pix) return GX_OK;
+    const int64_t pix = (int64_t)B * H * W, halo = (int64_t)B * (H + 2) * (W + 2);
+    if (pix <= n->cap_pix && halo <= n->cap_halo) return GX_OK;
     bf16 **b16[] = {&n->x0, &n->h1, &n->h2, &n->h3, &n->d4, &n->d3, &n->d2, &n->d1};
     const int ch[] = {16, 32, 32, 32, 16, 32, 32, 32};
     for (int i = 0; i < 8; ++i) {
         if (*b16[i]) cudaFree(*b16[i]);
-        GX_CHECK(c, cudaMalloc(b16[i], (size_t)pix * ch[i] * sizeof(bf16)));
+        *b16[i] = nullptr;
+        GX_CHECK(c, cudaMalloc(b16[i], (size_t)halo * ch[i] * sizeof(bf16)));
     }
     if (n->y) cudaFree(n->y);
     if (n->target) cudaFree(n->target);
     GX_CHECK(c, cudaMalloc(&n->y, (size_t)pix * 8 * sizeof(float)));
     GX_CHECK(c, cudaMalloc(&n->target, (size_t)pix * 3 * sizeof(float)));
     n->cap_pix = pix;
+    n->cap_halo = halo;
     return GX_OK;
 }
 
-template <int CIN, int COUT, int EPI>
-static int conv(gx_ctx *c, const bf16 *in, const bf16 *w, const float *bias, void *out, const bf16 *mask, int B, int H,
-                int W, int periodic, cudaStream_t st, const int *skip = nullptr) {
-    ConvArgs a{in, w, bias, out, mask, skip, B, H, W, periodic};
-    const int64_t tiles = (int64_t)((W + kTW - 1) / kTW) * ((H + kTH - 1) / kTH) * B;
-    k_conv<CIN, COUT, EPI><<<(unsigned)std::min<int64_t>(tiles, 152 * 4), 256, 0, st>>>(a);
+// TMA map of an activation image [B][H+2][W+2][C] (BF16) for the tile boxes of
+// the tensor-core convolution: dims (8 channels, C/8 groups, W+2, H+2, B),
+// box (8, 1, 130, R+2, 1), zero fill outside
+static int encode_act_map(gx_ctx *c, CUtensorMap *m, const void *base, int B, int H, int W, int C) {
+    typedef CUresult (*EncodeFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    static EncodeFn encode = nullptr;
+    if (!encode) {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        GX_CHECK(c, cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q));
+        if (q != cudaDriverEntryPointSuccess || !fn) {
+            c->err = "cuTensorMapEncodeTiled is not available from the driver";
+            return GX_ECUDA;
+        }
+        encode = reinterpret_cast<EncodeFn>(fn);
+    }
+    const cuuint64_t dims[5] = {8, (cuuint64_t)C / 8, (cuuint64_t)W + 2, (cuuint64_t)H + 2, (cuuint64_t)B};
+    const cuuint64_t strides[4] = {16, (cuuint64_t)C * 2, (cuuint64_t)(W + 2) * C * 2,
+                                   (cuuint64_t)(H + 2) * (W + 2) * C * 2};
+    const cuuint32_t box[5] = {8, 1, gxv::kRowPix, kConvRows + 2, 1};
+    const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    const CUresult r = encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void *>(base), dims, strides, box, estr,
+                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        c->err = "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")";
+        return GX_ECUDA;
+    }
+    return GX_OK;
+}
+
+// one persistent wave of k_convtc over the units of a, input `in` with CIN channels
+template <int CIN, int N, int COUTG, int EPI>
+static int launch_conv(gx_ctx *c, const bf16 *in, gxv::Args a, cudaStream_t st, const int *skip = nullptr) {
+    constexpr int smem = gxv::smem_bytes<CIN, N, kConvRows>() + 128;   // + alignment slack
+    const void *kfn = (const void *)k_convtc<CIN, N, COUTG, EPI>;
+    static int cap = 0;     // resident CTAs on the device
+    if (!cap) {
+        int dev = 0, nsm = 0, per = 0;
+        GX_CHECK(c, cudaGetDevice(&dev));
+        GX_CHECK(c, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        GX_CHECK(c, cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        GX_CHECK(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kfn, gxv::kThreads, smem));
+        // tensor memory: 512 columns per SM, kTmemCols per resident CTA
+        per = std::min(per, 512 / gxv::Shape<CIN, N, kConvRows>::kTmemCols);
+        cap = std::max(1, per * nsm);
+    }
+    CUtensorMap tm;
+    int rc = encode_act_map(c, &tm, in, a.B, a.H, a.W, CIN);
+    if (rc) return rc;
+    a.err = &c->dflags->timeout;
+    const int64_t units = (int64_t)a.B * ((a.H + kConvRows - 1) / kConvRows) * ((a.W + gxv::kTW - 1) / gxv::kTW);
+    k_convtc<CIN, N, COUTG, EPI><<<(unsigned)std::min<int64_t>(units, cap), gxv::kThreads, smem, st>>>(tm, a, skip);
     GX_LAUNCHED(c);
     return GX_OK;
+}
+
+template <int CIN, int N, int COUTG, int EPI>
+static int conv(gx_ctx *c, const bf16 *in, const bf16 *w, const float *bias, void *out, const bf16 *mask, int B, int H,
+                int W, int periodic, cudaStream_t st, const int *skip = nullptr) {
+    gxv::Args a{};
+    a.wtc = w;
+    a.bias = bias;
+    a.out = out;
+    a.mask = mask;
+    a.B = B;
+    a.H = H;
+    a.W = W;
+    a.periodic = periodic;
+    return launch_conv<CIN, N, COUTG, EPI>(c, in, a, st, skip);
 }
 
 template <int CIN, int COUTP>
@@ -432,15 +511,16 @@ static int wgrad(gx_ctx *c, const bf16 *dy, const bf16 *x, float *gw, float *gb,
 
 // forward through the four layers (input in n->x0), output FP32 [pix][8] in n->y
 static int net_forward(gx_ctx *c, int B, int H, int W, int periodic, cudaStream_t st, const int *skip = nullptr) {
+    using gxv::EPI_RELU;
     Net *n = c->net;
     int rc;
-    if ((rc = conv<16, 32, EPI_RELU>(c, n->x0, n->wf[0], n->bias[0], n->h1, nullptr, B, H, W, periodic, st, skip)))
+    if ((rc = conv<16, 32, 32, EPI_RELU>(c, n->x0, n->wf[0], n->bias[0], n->h1, nullptr, B, H, W, periodic, st, skip)))
         return rc;
-    if ((rc = conv<32, 32, EPI_RELU>(c, n->h1, n->wf[1], n->bias[1], n->h2, nullptr, B, H, W, periodic, st, skip)))
+    if ((rc = conv<32, 32, 32, EPI_RELU>(c, n->h1, n->wf[1], n->bias[1], n->h2, nullptr, B, H, W, periodic, st, skip)))
         return rc;
-    if ((rc = conv<32, 32, EPI_RELU>(c, n->h2, n->wf[2], n->bias[2], n->h3, nullptr, B, H, W, periodic, st, skip)))
+    if ((rc = conv<32, 32, 32, EPI_RELU>(c, n->h2, n->wf[2], n->bias[2], n->h3, nullptr, B, H, W, periodic, st, skip)))
         return rc;
-    return conv<32, 8, EPI_F32>(c, n->h3, n->wf[3], n->bias[3], n->y, nullptr, B, H, W, periodic, st, skip);
+    return conv<32, 16, 8, gxv::EPI_F32>(c, n->h3, n->wf[3], n->bias[3], n->y, nullptr, B, H, W, periodic, st, skip);
 }
 
 // backward from dY4 (in n->d4): weight gradients (FP32 sums, zeroed here) and
@@ -453,11 +533,14 @@ static int net_backward(gx_ctx *c, int B, int H, int W, int periodic, float grad
         GX_CHECK(c, cudaMemsetAsync(n->gb[l], 0, kGCoutP[l] * sizeof(float), st));
     }
     if ((rc = wgrad<32, 16>(c, n->d4, n->h3, n->gw[3], n->gb[3], B, H, W, periodic, st))) return rc;
-    if ((rc = conv<16, 32, EPI_MASK>(c, n->d4, n->wd[3], nullptr, n->d3, n->h3, B, H, W, periodic, st))) return rc;
+    if ((rc = conv<16, 32, 32, gxv::EPI_MASK>(c, n->d4, n->wd[3], nullptr, n->d3, n->h3, B, H, W, periodic, st)))
+        return rc;
     if ((rc = wgrad<32, 32>(c, n->d3, n->h2, n->gw[2], n->gb[2], B, H, W, periodic, st))) return rc;
-    if ((rc = conv<32, 32, EPI_MASK>(c, n->d3, n->wd[2], nullptr, n->d2, n->h2, B, H, W, periodic, st))) return rc;
+    if ((rc = conv<32, 32, 32, gxv::EPI_MASK>(c, n->d3, n->wd[2], nullptr, n->d2, n->h2, B, H, W, periodic, st)))
+        return rc;
     if ((rc = wgrad<32, 32>(c, n->d2, n->h1, n->gw[1], n->gb[1], B, H, W, periodic, st))) return rc;
-    if ((rc = conv<32, 32, EPI_MASK>(c, n->d2, n->wd[1], nullptr, n->d1, n->h1, B, H, W, periodic, st))) return rc;
+    if ((rc = conv<32, 32, 32, gxv::EPI_MASK>(c, n->d2, n->wd[1], nullptr, n->d1, n->h1, B, H, W, periodic, st)))
+        return rc;
     if ((rc = wgrad<16, 32>(c, n->d1, n->x0, n->gw[0], n->gb[0], B, H, W, periodic, st))) return rc;
     for (int l = 0; l < kNL; ++l) {
         k_unpack_grad<<<64, 256, 0, st>>>(n->gw[l], n->gb[l], n->grad, kCin[l], kCout[l], kCinP[l], param_offset(l),
@@ -476,10 +559,13 @@ int gx_net_solver_args(gx_ctx *c, NetSolverArgs *out, cudaStream_t st) {
     if (rc) return rc;
     Net *n = c->net;
     if (!n->have_weights && (rc = net_refresh(c, st))) return rc;
-    if ((rc = net_reserve(c, c->N))) return rc;
+    const int H = c->n[1], W = c->n[0];
+    if ((rc = net_reserve(c, 1, H, W))) return rc;
     for (int l = 0; l < kNL; ++l) { out->w[l] = n->wf[l]; out->b[l] = n->bias[l]; }
     out->x0 = n->x0; out->h1 = n->h1; out->h2 = n->h2; out->h3 = n->h3;
-    out->y = n->y;
+    const void *ins[4] = {n->x0, n->h1, n->h2, n->h3};
+    for (int l = 0; l < kNL; ++l)
+        if ((rc = encode_act_map(c, &out->tm[l], ins[l], 1, H, W, kCinP[l]))) return rc;
     return GX_OK;
 }
 
@@ -614,7 +700,7 @@ int gx_precond_train(gx_ctx *c, int npairs, int crop, int batch, int epochs, flo
     if (!n || n->npairs < 1) { c->err = "no collected pairs: call gx_precond_collect and run some solves"; return GX_ESTATE; }
     if (!n->have_weights) { int rc = net_refresh(c, st); if (rc) return rc; }
     const int S = crop + 8;
-    int rc = net_reserve(c, (int64_t)batch * S * S);
+    int rc = net_reserve(c, batch, S, S);
     if (rc) return rc;
     CropSpec *dspec = nullptr;
     float *dscale = nullptr;
@@ -675,12 +761,72 @@ int gx_precond_forward(gx_ctx *c, int H, int W, const float *in, float *out, voi
     if (rc) return rc;
     Net *n = c->net;
     if (!n->have_weights && (rc = net_refresh(c, st))) return rc;
-    if ((rc = net_reserve(c, (int64_t)H * W))) return rc;
-    k_pack_input<float><<<nblk((int64_t)H * W), 256, 0, st>>>(in, (int64_t)H * W, n->x0, nullptr, 1.0);
+    if ((rc = net_reserve(c, 1, H, W))) return rc;
+    k_pack_input<float><<<nblk((int64_t)H * W), 256, 0, st>>>(in, H, W, 1.0, 1, n->x0);
     GX_LAUNCHED(c);
     if ((rc = net_forward(c, 1, H, W, 1, st))) return rc;
     k_f32_to_chw3<<<nblk((int64_t)H * W), 256, 0, st>>>(n->y, (int64_t)H * W, out);
     GX_LAUNCHED(c);
+    GX_CHECK(c, cudaStreamSynchronize(st));
+    return GX_OK;
+}
+
+int gx_precond_apply(gx_ctx *c, const double *v, double *z, void *stream) {
+    if (!c || !v || !z || v == z) return GX_EINVAL;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const int64_t N = c->N;
+    const int pc = c->cfg.precond;
+    if (pc == GX_PRECOND_NONE) {
+        GX_CHECK(c, cudaMemcpyAsync(z, v, 3 * N * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        GX_CHECK(c, cudaStreamSynchronize(st));
+        return GX_OK;
+    }
+    int rc = gx_build_jacobi(c, st);
+    if (rc) return rc;
+    if (pc == GX_PRECOND_JACOBI) {
+        if ((rc = gx_apply_jacobi(c, v, z, st))) return rc;
+        GX_CHECK(c, cudaStreamSynchronize(st));
+        return GX_OK;
+    }
+    NetSolverArgs nn;
+    if ((rc = gx_net_solver_args(c, &nn, st))) return rc;
+    const double vn = gx_norm_host(c, v, 3 * N, st, &rc);
+    if (rc) return rc;
+    if (vn == 0.0) {
+        GX_CHECK(c, cudaMemsetAsync(z, 0, 3 * N * sizeof(double), st));
+        GX_CHECK(c, cudaStreamSynchronize(st));
+        return GX_OK;
+    }
+    const double s = vn / std::sqrt(3.0 * (double)N);
+    const int H = c->n[1], W = c->n[0];
+    k_pack_input<double><<<nblk(N), 256, 0, st>>>(v, H, W, 1.0 / s, 1, static_cast<bf16 *>(nn.x0));
+    GX_LAUNCHED(c);
+    using namespace gxv;
+    Args a{};
+    a.B = 1;
+    a.H = H;
+    a.W = W;
+    a.periodic = 1;
+    a.wtc = static_cast<const bf16 *>(nn.w[0]);
+    a.bias = nn.b[0];
+    a.out = nn.h1;
+    if ((rc = launch_conv<16, 32, 32, EPI_RELU>(c, static_cast<const bf16 *>(nn.x0), a, st))) return rc;
+    a.wtc = static_cast<const bf16 *>(nn.w[1]);
+    a.bias = nn.b[1];
+    a.out = nn.h2;
+    if ((rc = launch_conv<32, 32, 32, EPI_RELU>(c, static_cast<const bf16 *>(nn.h1), a, st))) return rc;
+    a.wtc = static_cast<const bf16 *>(nn.w[2]);
+    a.bias = nn.b[2];
+    a.out = nn.h3;
+    if ((rc = launch_conv<32, 32, 32, EPI_RELU>(c, static_cast<const bf16 *>(nn.h2), a, st))) return rc;
+    a.wtc = static_cast<const bf16 *>(nn.w[3]);
+    a.bias = nn.b[3];
+    a.out = nullptr;
+    a.v = v;
+    a.jd = c->jdiag;
+    a.z = z;
+    a.s = s;
+    if ((rc = launch_conv<32, 16, 8, EPI_Z>(c, static_cast<const bf16 *>(nn.h3), a, st))) return rc;
     GX_CHECK(c, cudaStreamSynchronize(st));
     return GX_OK;
 }
@@ -693,9 +839,9 @@ int gx_precond_loss_grad(gx_ctx *c, int H, int W, const float *in, const float *
     if (rc) return rc;
     Net *n = c->net;
     if (!n->have_weights && (rc = net_refresh(c, st))) return rc;
-    if ((rc = net_reserve(c, (int64_t)H * W))) return rc;
+    if ((rc = net_reserve(c, 1, H, W))) return rc;
     const int64_t HW = (int64_t)H * W;
-    k_pack_input<float><<<nblk(HW), 256, 0, st>>>(in, HW, n->x0, nullptr, 1.0);
+    k_pack_input<float><<<nblk(HW), 256, 0, st>>>(in, H, W, 1.0, 0, n->x0);
     GX_LAUNCHED(c);
     k_chw3_to_target<<<nblk(HW), 256, 0, st>>>(target, HW, n->target);
     GX_LAUNCHED(c);

@@ -132,8 +132,11 @@ def emulate_bf16(torch, p, x, t=None, periodic=True):
     return y[0].numpy(), grads
 
 
-# (H, W): several 8x16 tiles with ragged tails, one exact tile, smaller than a tile
-SHAPES = [(24, 40), (8, 16), (5, 7), (33, 50)]
+# (H, W): the convolution works on units of 2 rows x 128 columns.  Narrow
+# images (one partial unit per row pair, odd heights), one exact unit, and
+# rows of several units with a ragged last one (the periodic halo crossing
+# unit and image edges).
+SHAPES = [(24, 40), (8, 16), (5, 7), (33, 50), (2, 128), (7, 300), (4, 256)]
 
 
 @pytest.mark.parametrize("H,W", SHAPES)
@@ -176,6 +179,50 @@ def test_loss_and_gradients_match_oracle(env, H, W):
         assert e <= TOL_GRAD, (name, e)
         e = rel(grad[sl], g_emu[name])
         assert e <= TOL_EMU_GRAD, (name, "vs BF16 emulation", e)
+
+
+def test_solver_application_matches_oracle(env):
+    """The network as FGMRES applies it to a Krylov column v (unit norm): the
+    input is v / s (s = 1/sqrt(3N)) rounded to BF16, the last layer writes
+    z = D^-1 v + s N(v/s) itself.  With zero weights N = 0, so that call gives
+    D^-1 v, which must equal the block-Jacobi preconditioner's output; the
+    difference of the two calls, divided by s, is N(v/s), compared with the
+    oracle's forward pass.  The grid (160 x 13) has rows of two units (the
+    second ragged) and an odd number of rows."""
+    g, torch, _ = env
+    wl = workloads.harris(nx=160, ny=13, ppc=4, steps=1)
+    net = g.from_workload(wl, precond=g.GX_PRECOND_NET)
+    jac = g.from_workload(wl, precond=g.GX_PRECOND_JACOBI)
+    try:
+        for c in (net, jac):
+            assert c.step(1).converged
+        H, W = 13, 160
+        N = H * W
+        v = np.random.default_rng(5).standard_normal(3 * N)
+        v /= np.linalg.norm(v)
+        s = 1.0 / np.sqrt(3 * N)
+        vd = torch.from_numpy(v).cuda()
+        z1 = torch.zeros_like(vd)
+        z0 = torch.zeros_like(vd)
+        zj = torch.zeros_like(vd)
+        p = random_params(11)
+        net.precond_set_weights(p.astype(np.float32))
+        net.precond_apply(vd, z1)
+        net.precond_set_weights(np.zeros(O.net_param_count(), np.float32))
+        net.precond_apply(vd, z0)
+        jac.precond_apply(vd, zj)
+        z0h, zjh = z0.cpu().numpy(), zj.cpu().numpy()
+        assert np.all(np.isfinite(z0h)) and rel(z0h, zjh) <= 1e-6, rel(z0h, zjh)
+        y = ((z1.cpu().numpy() - z0h) / s).reshape(3, H, W)
+        xb = bf16(torch, (v / s).reshape(3, H, W))
+        pb = weights_bf16(torch, p.astype(np.float32))
+        y_ref = O.net_forward(pb, xb, periodic=True)
+        assert rel(y, y_ref) <= TOL_FWD, rel(y, y_ref)
+        y_emu = emulate_bf16(torch, pb, xb)
+        assert rel(y, y_emu) <= TOL_EMU, rel(y, y_emu)
+    finally:
+        net.close()
+        jac.close()
 
 
 def test_set_get_weights_roundtrip_and_errors(env):
