@@ -7,8 +7,9 @@
 //
 // Tile: 8 rows x 16 columns of pixels with a one-pixel halo, staged in shared
 // memory with row strides padded by 8 elements so that ldmatrix is
-// conflict-free.  Activations are NHWC BF16 images with a one-pixel halo ring
-// ([B][H+2][W+2][C]) and the channel count padded to the MMA shapes.
+// conflict-free.  Activations are channel-blocked BF16 images with a
+// one-pixel halo ring ([B][C/8][H+2][W+2][8]), the channel count padded to the
+// MMA shapes.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -55,19 +56,20 @@ __device__ __forceinline__ int wrapn(int i, int n) {
 
 // load the (TH+2) x (TW+2) pixel tile of CIN channels of image b (rows
 // y0-1 .. y0+TH, columns x0-1 .. x0+TW) into shared memory (row stride CIN +
-// 8) from an image stored with a one-pixel halo ring, [B][H+2][W+2][CIN]
-// (the ring holds the periodic copies or zeros); zero beyond the ring
+// 8) from a channel-blocked image with a one-pixel halo ring,
+// [B][CIN/8][H+2][W+2][8] (the ring holds the periodic copies or zeros); zero
+// beyond the ring
 template <int CIN>
 __device__ __forceinline__ void load_tile_halo(bf16 *sIn, const bf16 *in, int b, int H, int W, int y0, int x0) {
     constexpr int S = CIN + 8;
-    constexpr int V = CIN / 8;   // 16-byte vectors per pixel
+    constexpr int V = CIN / 8;   // 16-byte chunks per pixel
     for (int t = threadIdx.x; t < kHalo * V; t += blockDim.x) {
-        const int pix = t / V, v = t % V;
+        const int v = t / kHalo, pix = t % kHalo;     // consecutive threads: consecutive pixels of one chunk
         const int yy = y0 - 1 + pix / (kTW + 2), xx = x0 - 1 + pix % (kTW + 2);
         uint4 val = make_uint4(0, 0, 0, 0);
         if (yy <= H && xx <= W)
             val = *reinterpret_cast<const uint4 *>(
-                in + ((((int64_t)b * (H + 2) + yy + 1) * (W + 2)) + xx + 1) * CIN + v * 8);
+                in + ((((int64_t)b * V + v) * (H + 2) + yy + 1) * (W + 2) + xx + 1) * 8);
         *reinterpret_cast<uint4 *>(sIn + pix * S + v * 8) = val;
     }
 }

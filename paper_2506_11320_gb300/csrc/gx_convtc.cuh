@@ -1,27 +1,27 @@
 // gx_convtc.cuh -- the 3x3 convolution of the learned preconditioner on the
 // fifth-generation tensor cores (tcgen05.mma kind::f16, BF16 operands, FP32
-// accumulation in tensor memory), fed by the TMA engine.
+// accumulation in tensor memory), fed by TMA bulk copies.
 //
 // Implicit GEMM, one MMA per (output row, tap, 16 input channels):
 //     D[128 pixels][N] += A_tap[128 pixels][16] * W_tap[N][16]^T
-// Activations live in global memory as NHWC BF16 images with a one-pixel halo
-// ring, [B][H + 2][W + 2][C]: the producer of a layer writes every edge pixel
-// a second time into the ring (its periodic image, or zero for zero padding),
-// so a tile needs no index arithmetic.  A unit of work is R image rows x 128
-// columns; its input tile, (R + 2) rows x 130 columns, arrives in shared
-// memory as C/8 channel slabs -- slab g holds channels 8g .. 8g + 7 of every
-// tile pixel, one 16-byte chunk per pixel, pixels in row-major order -- by one
-// TMA tensor copy per slab (a 5-D map: 8 channels, channel group, x, y, image;
-// box 8 x 1 x 130 x (R + 2) x 1; reads past the padded image fill zeros, and
-// those pixels feed no output).  The A operand of tap (ky, kx) for output row
-// r is then the 128 consecutive chunks starting at tile pixel
-// (r + ky) * 130 + kx: one descriptor with a start moved by whole chunks (no
-// im2col copy), LBO = slab size (next 8 channels), SBO = 128 bytes.  The
-// weights come pre-packed in the same form (slab = 8 input channels of one
-// tap for all N outputs) by one 1-D bulk copy.
+// Activations live in global memory as channel-blocked BF16 images with a
+// one-pixel halo ring, [B][C/8][H + 2][W + 2][8]: the producer of a layer
+// writes every edge pixel a second time into the ring (its periodic image, or
+// zero for zero padding), so a tile needs no index arithmetic.  A unit of
+// work is R image rows x 128 columns; its input tile, (R + 2) rows x 130
+// columns, arrives in shared memory as C/8 channel slabs -- slab g holds
+// channels 8g .. 8g + 7 of every tile pixel, one 16-byte chunk per pixel,
+// pixels in row-major order.  In the blocked layout one tile row of one slab
+// is 130 x 16 = 2080 contiguous bytes, so the tile is (R + 2) * C/8 bulk
+// copies (TMA, cp.async.bulk), one per lane of the producer warp.  The A
+// operand of tap (ky, kx) for output row r is then the 128 consecutive chunks
+// starting at tile pixel (r + ky) * 130 + kx: one descriptor with a start
+// moved by whole chunks (no im2col copy), LBO = slab size (next 8 channels),
+// SBO = 128 bytes.  The weights come pre-packed in the same form (slab = 8
+// input channels of one tap for all N outputs) by one more bulk copy.
 //
 // Warp roles of the 256-thread CTA, synchronised by mbarriers only:
-//   warp 0 lane 0: TMA producer, a ring of kStages tiles;
+//   warp 0:        producer (bulk copies), a ring of kStages tiles;
 //   warp 1 lane 0: MMA issuer, R * 9 * CIN / 16 MMAs per unit into one of two
 //                  accumulator sets, then commits (stage free, accumulators full);
 //   warps 4..7:    epilogue, warp w reading TMEM lane quarter w - 4 (pixels
@@ -35,7 +35,6 @@
 // to FP64.
 #pragma once
 
-#include <cuda.h>
 #include <cuda_bf16.h>
 
 #include "gx_tc.cuh"
@@ -45,7 +44,7 @@ namespace gxv {
 typedef __nv_bfloat16 bf16;
 
 constexpr int kTW = 128;            // output columns of a unit (the MMA's M)
-constexpr int kRowPix = kTW + 2;    // tile row with its halo
+constexpr int kTileRow = kTW + 2;   // tile row with its halo (pixels)
 constexpr int kThreads = 256;       // eight warps
 constexpr int kStages = 3;          // tiles in flight
 constexpr int kWaitLimit = 1 << 22; // mbarrier polls before a wait gives up
@@ -55,8 +54,8 @@ enum { EPI_RELU = 0, EPI_F32 = 1, EPI_MASK = 2, EPI_Z = 3 };
 struct Args {
     const bf16 *wtc;      // weights packed [9 CIN / 8][N][8] (zero rows beyond COUTG)
     const float *bias;    // [COUTG] or null
-    void *out;            // EPI_RELU / EPI_MASK: bf16 [B][H+2][W+2][N]; EPI_F32: float [B][H][W][COUTG]
-    const bf16 *mask;     // EPI_MASK: bf16 [B][H+2][W+2][N], keep where > 0
+    void *out;            // EPI_RELU / EPI_MASK: bf16 [B][N/8][H+2][W+2][8]; EPI_F32: float [B][H][W][COUTG]
+    const bf16 *mask;     // EPI_MASK: bf16 [B][N/8][H+2][W+2][8], keep where > 0
     const double *v;      // EPI_Z: Krylov vector [3][H*W] (B = 1)
     const double *jd;     // EPI_Z: block-Jacobi inverse [H*W][9]
     double *z;            // EPI_Z: [3][H*W]
@@ -68,16 +67,16 @@ struct Args {
 template <int CIN, int N, int R>
 struct Shape {
     static_assert(CIN % 16 == 0 && N % 16 == 0 && N <= 32 && R >= 1 && R <= 4, "supported shapes");
-    static constexpr int kBoxPix = (R + 2) * kRowPix;                    // pixels one TMA box writes
-    static constexpr int kBoxBytes = kBoxPix * 16;
-    static constexpr int kSlabBytes = (kBoxBytes + 127) / 128 * 128;     // TMA destinations 128-byte aligned
+    static constexpr int kSlabBytes = (R + 2) * kTileRow * 16;
     static constexpr int kTileBytes = (CIN / 8) * kSlabBytes;
-    static constexpr int kTileTx = (CIN / 8) * kBoxBytes;                // bytes the tile's copies deliver
+    static constexpr int kLoads = (CIN / 8) * (R + 2);                   // bulk copies per tile (one row of one slab)
+    static_assert(kLoads <= 32, "one copy per lane of the producer warp");
     static constexpr int kWSlabBytes = N * 16;
     static constexpr int kWBytes = 9 * (CIN / 8) * kWSlabBytes;
     static constexpr int kAccCols = R * N;                               // one unit's accumulators
     static constexpr int kTmemCols = 2 * kAccCols <= 32 ? 32 : 2 * kAccCols <= 64 ? 64 : 2 * kAccCols <= 128 ? 128 : 256;
     // [weights][kStages tiles][bias 32 floats][barriers][tmem address, abort flag, units issued]
+    // (tile pixels beyond the padded image are never written: they feed no valid output)
     static constexpr int kBiasOff = kWBytes + kStages * kTileBytes;
     static constexpr int kBarOff = kBiasOff + 4 * 32;
     static constexpr int kNumBars = 1 + 2 * kStages + 4;                 // weights, full/empty, acc full/empty
@@ -99,10 +98,11 @@ __device__ __forceinline__ void unit_pos(int64_t u, int nseg, int nblk, int &b, 
     x0 = seg * kTW;
 }
 
-// offset (in pixels of C channels) of pixel (b, y, x) of an image with a halo
-// ring; y in [-1, H], x in [-1, W]
-__host__ __device__ __forceinline__ int64_t halo_pix(int b, int y, int x, int H, int W) {
-    return ((int64_t)b * (H + 2) + (y + 1)) * (W + 2) + (x + 1);
+// offset (elements) of the 8-channel chunk g of pixel (b, y, x) of a
+// channel-blocked image with a halo ring and G chunks per pixel; y in
+// [-1, H], x in [-1, W]
+__host__ __device__ __forceinline__ int64_t blk_off(int b, int g, int y, int x, int H, int W, int G) {
+    return ((((int64_t)b * G + g) * (H + 2) + (y + 1)) * (W + 2) + (x + 1)) * 8;
 }
 
 // store the C-channel value `val` (C/8 uint4) of pixel (b, y, x) into an image
@@ -114,9 +114,9 @@ __device__ __forceinline__ void store_with_halo(bf16 *img, int b, int y, int x, 
                                                 const uint4 (&val)[C / 8]) {
     const uint4 zero = make_uint4(0, 0, 0, 0);
     auto put = [&](int yy, int xx, bool copy) {
-        uint4 *d = reinterpret_cast<uint4 *>(img + halo_pix(b, yy, xx, H, W) * C);
 #pragma unroll
-        for (int i = 0; i < C / 8; ++i) d[i] = copy ? val[i] : zero;
+        for (int g = 0; g < C / 8; ++g)
+            *reinterpret_cast<uint4 *>(img + blk_off(b, g, yy, xx, H, W, C / 8)) = copy ? val[g] : zero;
     };
     put(y, x, true);
     const bool p = periodic != 0;
@@ -139,11 +139,11 @@ __device__ __forceinline__ void store_with_halo(bf16 *img, int b, int y, int x, 
 
 // out = epilogue(conv3x3(in, w) + bias) over the units cta, cta + ncta, ...
 // Every thread of the CTA calls it (blockDim.x == kThreads); sm: smem_bytes()
-// bytes, 128-byte aligned; tmap: the input's tensor map (a __grid_constant__
-// kernel parameter).  N: MMA width (output channels padded to 16 or 32);
-// COUTG: output channels of w / bias (<= N).
+// bytes, 128-byte aligned; in: the input image [B][CIN/8][H+2][W+2][8].  N: MMA
+// width (output channels padded to 16 or 32); COUTG: output channels of w /
+// bias (<= N).
 template <int CIN, int N, int COUTG, int R, int EPI>
-__device__ void conv_tc(const Args &a, const CUtensorMap *tmap, unsigned char *sm, int cta, int ncta) {
+__device__ void conv_tc(const Args &a, const bf16 *in, unsigned char *sm, int cta, int ncta) {
     using namespace gxt;
     using S = Shape<CIN, N, R>;
     static_assert(COUTG <= N && (EPI != EPI_Z || COUTG >= 3), "output channels");
@@ -175,26 +175,35 @@ __device__ void conv_tc(const Args &a, const CUtensorMap *tmap, unsigned char *s
     tc_fence_after();
     const uint32_t tm = *sTm;
 
-    int nloaded = 0;    // (producer thread)
+    int nloaded = 0;    // (producer warp)
     if (warp == 0) {
+        // ---- producer: lane 0 waits for the stage and announces the bytes, lanes issue the row copies
         if (lane == 0) {
-            // ---- TMA producer
             mbar_arrive_expect_tx(wfull, S::kWBytes);
             bulk_load(smem_addr(sW), a.wtc, S::kWBytes, wfull);
-            int i = 0;
-            for (; i < nmine; ++i) {
-                const int st = i % kStages, n = i / kStages;
-                if (n > 0 && !mbar_wait_or_abort(&empty[st], (n - 1) & 1, kWaitLimit, abort)) break;
-                int b, y0, x0;
-                unit_pos<R>(cta + (int64_t)i * ncta, nseg, nblk, b, y0, x0);
-                const uint32_t dst = smem_addr(sm + S::kWBytes + st * S::kTileBytes);
-                mbar_arrive_expect_tx(&full[st], S::kTileTx);
-#pragma unroll
-                for (int g = 0; g < CIN / 8; ++g)
-                    tma_load_5d(dst + g * S::kSlabBytes, tmap, 0, g, x0, y0, b, &full[st]);
-            }
-            nloaded = i;
         }
+        int i = 0;
+        for (; i < nmine; ++i) {
+            const int st = i % kStages, n = i / kStages;
+            int b, y0, x0;
+            unit_pos<R>(cta + (int64_t)i * ncta, nseg, nblk, b, y0, x0);
+            // rows y0-1 .. y0+R of the padded image that exist (up to row H), and the
+            // pixels of each from padded column x0 (= image column x0 - 1) that exist
+            const int rows = min(R + 2, a.H + 2 - y0), npx = min(kTileRow, a.W + 2 - x0);
+            int ok = 1;
+            if (lane == 0) {
+                if (n > 0) ok = mbar_wait_or_abort(&empty[st], (n - 1) & 1, kWaitLimit, abort);
+                if (ok) mbar_arrive_expect_tx(&full[st], (uint32_t)(rows * (CIN / 8) * npx * 16));
+            }
+            if (!__shfl_sync(0xffffffffu, ok, 0)) break;
+            if (lane < S::kLoads) {
+                const int r = lane % (R + 2), g = lane / (R + 2);
+                if (r < rows)
+                    bulk_load(smem_addr(sm + S::kWBytes + st * S::kTileBytes + g * S::kSlabBytes + r * kTileRow * 16),
+                              in + blk_off(b, g, y0 - 1 + r, x0 - 1, a.H, a.W, CIN / 8), npx * 16, &full[st]);
+            }
+        }
+        nloaded = i;
     } else if (warp == 1) {
         if (lane == 0) {
             // ---- MMA issuer
@@ -215,7 +224,7 @@ __device__ void conv_tc(const Args &a, const CUtensorMap *tmap, unsigned char *s
                     for (int kc = 0; kc < CIN / 16; ++kc) {
 #pragma unroll
                         for (int r = 0; r < R; ++r) {
-                            const uint32_t aoff = ((r + tap / 3) * kRowPix + tap % 3) + 2 * kc * (S::kSlabBytes / 16);
+                            const uint32_t aoff = ((r + tap / 3) * kTileRow + tap % 3) + 2 * kc * (S::kSlabBytes / 16);
                             const uint32_t boff = (tap * (CIN / 8) + 2 * kc) * (S::kWSlabBytes / 16);
                             mma_bf16(dacc + r * N, ad + aoff, bdesc + boff, idesc, tap > 0 || kc > 0);
                         }
@@ -258,10 +267,10 @@ __device__ void conv_tc(const Args &a, const CUtensorMap *tmap, unsigned char *s
                     uint4 packed[N / 8];
                     uint32_t *pw = reinterpret_cast<uint32_t *>(packed);
                     if (EPI == EPI_MASK) {
-                        const uint4 *mk = reinterpret_cast<const uint4 *>(a.mask + halo_pix(b, yy, xx, a.H, a.W) * N);
 #pragma unroll
                         for (int c8 = 0; c8 < N / 8; ++c8) {
-                            const uint4 m4 = mk[c8];
+                            const uint4 m4 =
+                                *reinterpret_cast<const uint4 *>(a.mask + blk_off(b, c8, yy, xx, a.H, a.W, N / 8));
                             const uint32_t mw[4] = {m4.x, m4.y, m4.z, m4.w};
 #pragma unroll
                             for (int h = 0; h < 4; ++h) {

@@ -20,10 +20,10 @@
 // recomputed at every restart and decides convergence.  The learned
 // preconditioner also runs inside the kernel: the thread that forms a Krylov
 // column also packs it to BF16 for the network, the four convolution layers
-// run on the fifth-generation tensor cores (TMA-fed tcgen05, accumulators in
-// tensor memory) over the whole grid with a barrier before each layer, and the
-// last adds the correction to the block-Jacobi image, so a solve is one launch
-// with every preconditioner.
+// run on the fifth-generation tensor cores (tcgen05 fed by TMA bulk copies,
+// accumulators in tensor memory) over the whole grid with a barrier before
+// each layer, and the last adds the correction to the block-Jacobi image, so a
+// solve is one launch with every preconditioner.
 #include <cooperative_groups.h>
 
 #include "gx_convtc.cuh"
@@ -163,17 +163,17 @@ __device__ void net_apply(const CoArgs &a, cg::grid_group &grid, int j, unsigned
     c.wtc = static_cast<const bf16 *>(a.nn.w[0]);
     c.bias = a.nn.b[0];
     c.out = a.nn.h1;
-    conv_tc<16, 32, 32, kNetRows, EPI_RELU>(c, &a.nn.tm[0], sm, blockIdx.x, gridDim.x);
+    conv_tc<16, 32, 32, kNetRows, EPI_RELU>(c, static_cast<const bf16 *>(a.nn.x0), sm, blockIdx.x, gridDim.x);
     grid.sync();
     c.wtc = static_cast<const bf16 *>(a.nn.w[1]);
     c.bias = a.nn.b[1];
     c.out = a.nn.h2;
-    conv_tc<32, 32, 32, kNetRows, EPI_RELU>(c, &a.nn.tm[1], sm, blockIdx.x, gridDim.x);
+    conv_tc<32, 32, 32, kNetRows, EPI_RELU>(c, static_cast<const bf16 *>(a.nn.h1), sm, blockIdx.x, gridDim.x);
     grid.sync();
     c.wtc = static_cast<const bf16 *>(a.nn.w[2]);
     c.bias = a.nn.b[2];
     c.out = a.nn.h3;
-    conv_tc<32, 32, 32, kNetRows, EPI_RELU>(c, &a.nn.tm[2], sm, blockIdx.x, gridDim.x);
+    conv_tc<32, 32, 32, kNetRows, EPI_RELU>(c, static_cast<const bf16 *>(a.nn.h2), sm, blockIdx.x, gridDim.x);
     grid.sync();
     c.wtc = static_cast<const bf16 *>(a.nn.w[3]);
     c.bias = a.nn.b[3];
@@ -182,7 +182,7 @@ __device__ void net_apply(const CoArgs &a, cg::grid_group &grid, int j, unsigned
     c.jd = a.jd;
     c.z = a.Z + (size_t)j * n;
     c.s = a.ns;
-    conv_tc<32, 16, 8, kNetRows, EPI_Z>(c, &a.nn.tm[3], sm, blockIdx.x, gridDim.x);
+    conv_tc<32, 16, 8, kNetRows, EPI_Z>(c, static_cast<const bf16 *>(a.nn.h3), sm, blockIdx.x, gridDim.x);
 }
 
 // NET: the learned preconditioner is applied in the kernel (the plain and

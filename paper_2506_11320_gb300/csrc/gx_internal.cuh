@@ -15,7 +15,6 @@
 //     (o = (ox+1) + 3 (oy+1)), e the alpha component.
 #pragma once
 
-#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -219,10 +218,9 @@ double gx_norm_host(gx_ctx *c, const double *x, int64_t n, cudaStream_t st, int 
 // forward weights [coutP][9][cinP] and FP32 biases of the 4 layers, the NHWC
 // BF16 activation buffers (16, 32, 32, 32 channels) and the FP32 output [pix][8]
 struct NetSolverArgs {
-    CUtensorMap tm[4];      // TMA maps of the layer inputs x0, h1, h2, h3 (halo-ring images)
     const void *w[4];       // weights in the tensor-core operand layout
     const float *b[4];
-    void *x0, *h1, *h2, *h3;
+    void *x0, *h1, *h2, *h3; // layer inputs: channel-blocked images with a halo ring
 };
 int gx_net_solver_args(gx_ctx *c, NetSolverArgs *out, cudaStream_t st);
 int gx_net_collecting(const gx_ctx *c);

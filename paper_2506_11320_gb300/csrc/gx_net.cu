@@ -13,8 +13,8 @@
 //
 // Kernels:
 //   * k_convtc: the implicit-GEMM convolution of gx_convtc.cuh on the tcgen05
-//     tensor cores (TMA-fed, BF16 operands, FP32 accumulators in tensor
-//     memory).  The forward pass and the data gradient (the same convolution
+//     tensor cores (fed by TMA bulk copies, BF16 operands, FP32 accumulators
+//     in tensor memory).  The forward pass and the data gradient (the same convolution
 //     with the kernel flipped and the channel roles swapped, masked by the
 //     ReLU of the layer input) both use it; inside the solver the forward pass
 //     runs in the solver's own kernel.
@@ -25,7 +25,8 @@
 //   * Adam on an FP32 master copy; BF16 copies refreshed after each update.
 // Channel counts are padded for the MMA shapes: 3 input channels -> 16,
 // 3 output channels -> 8 (stored forward output; 16 in the MMA) or 16
-// (gradient).  BF16 activations are images with a one-pixel halo ring.
+// (gradient).  BF16 activations are channel-blocked images with a one-pixel
+// halo ring, [B][C/8][H+2][W+2][8].
 #include <cuda_bf16.h>
 
 #include <cstring>
@@ -59,17 +60,16 @@ inline int64_t param_count() { return param_offset(kNL); }
 constexpr int kConvRows = 2;
 
 template <int CIN, int N, int COUTG, int EPI>
-__global__ void __launch_bounds__(gxv::kThreads) k_convtc(const __grid_constant__ CUtensorMap tmap, gxv::Args a,
-                                                          const int *skip) {
+__global__ void __launch_bounds__(gxv::kThreads) k_convtc(const gxv::bf16 *in, gxv::Args a, const int *skip) {
     extern __shared__ __align__(128) unsigned char dsm[];
     if (skip && *skip) return;
     unsigned char *sm = dsm + ((128 - (gxt::smem_addr(dsm) & 127)) & 127);
-    gxv::conv_tc<CIN, N, COUTG, kConvRows, EPI>(a, &tmap, sm, blockIdx.x, gridDim.x);
+    gxv::conv_tc<CIN, N, COUTG, kConvRows, EPI>(a, in, sm, blockIdx.x, gridDim.x);
 }
 
 struct WgArgs {
-    const bf16 *dy;      // [B][H+2][W+2][COUTP] gradient wrt the layer output (halo ring)
-    const bf16 *x;       // [B][H+2][W+2][CIN] layer input (halo ring: periodic copies or zeros)
+    const bf16 *dy;      // [B][COUTP/8][H+2][W+2][8] gradient wrt the layer output (halo ring)
+    const bf16 *x;       // [B][CIN/8][H+2][W+2][8] layer input (halo ring: periodic copies or zeros)
     float *gw;           // [COUTP][9][CIN] FP32 sums
     float *gb;           // [COUTP]
     int B, H, W, periodic;
@@ -99,11 +99,11 @@ __global__ void __launch_bounds__(256) k_wgrad(WgArgs a) {
         load_tile_halo<CIN>(sX, a.x, b, a.H, a.W, y0, x0);
         constexpr int DV = COUTP / 8;
         for (int q = threadIdx.x; q < kTH * kTW * DV; q += blockDim.x) {
-            const int pix = q / DV, v = q % DV;
+            const int v = q / (kTH * kTW), pix = q % (kTH * kTW);   // consecutive threads: consecutive pixels
             const int yy = y0 + pix / kTW, xx = x0 + pix % kTW;
             uint4 val = make_uint4(0, 0, 0, 0);
             if (yy < a.H && xx < a.W)
-                val = *reinterpret_cast<const uint4 *>(a.dy + gxv::halo_pix(b, yy, xx, a.H, a.W) * COUTP + v * 8);
+                val = *reinterpret_cast<const uint4 *>(a.dy + gxv::blk_off(b, v, yy, xx, a.H, a.W, DV));
             *reinterpret_cast<uint4 *>(sD + pix * SD + v * 8) = val;
         }
         __syncthreads();
@@ -348,7 +348,7 @@ struct Net {
     float *bias[kNL] = {};
     float *gw[kNL] = {}, *gb[kNL] = {};
     int have_weights = 0;
-    // activations: BF16 images with a halo ring [B][H+2][W+2][C]; y, target [B][H][W][*]
+    // activations: channel-blocked BF16 images with a halo ring [B][C/8][H+2][W+2][8]; y, target [B][H][W][*]
     int64_t cap_pix = 0, cap_halo = 0;
     bf16 *x0 = nullptr, *h1 = nullptr, *h2 = nullptr, *h3 = nullptr;
     bf16 *d4 = nullptr, *d3 = nullptr, *d2 = nullptr, *d1 = nullptr;
@@ -425,39 +425,6 @@ static int net_reserve(gx_ctx *c, int B, int H, int W) {
     return GX_OK;
 }
 
-// TMA map of an activation image [B][H+2][W+2][C] (BF16) for the tile boxes of
-// the tensor-core convolution: dims (8 channels, C/8 groups, W+2, H+2, B),
-// box (8, 1, 130, R+2, 1), zero fill outside
-static int encode_act_map(gx_ctx *c, CUtensorMap *m, const void *base, int B, int H, int W, int C) {
-    typedef CUresult (*EncodeFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
-                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
-                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-    static EncodeFn encode = nullptr;
-    if (!encode) {
-        void *fn = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        GX_CHECK(c, cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q));
-        if (q != cudaDriverEntryPointSuccess || !fn) {
-            c->err = "cuTensorMapEncodeTiled is not available from the driver";
-            return GX_ECUDA;
-        }
-        encode = reinterpret_cast<EncodeFn>(fn);
-    }
-    const cuuint64_t dims[5] = {8, (cuuint64_t)C / 8, (cuuint64_t)W + 2, (cuuint64_t)H + 2, (cuuint64_t)B};
-    const cuuint64_t strides[4] = {16, (cuuint64_t)C * 2, (cuuint64_t)(W + 2) * C * 2,
-                                   (cuuint64_t)(H + 2) * (W + 2) * C * 2};
-    const cuuint32_t box[5] = {8, 1, gxv::kRowPix, kConvRows + 2, 1};
-    const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
-    const CUresult r = encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void *>(base), dims, strides, box, estr,
-                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) {
-        c->err = "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")";
-        return GX_ECUDA;
-    }
-    return GX_OK;
-}
-
 // one persistent wave of k_convtc over the units of a, input `in` with CIN channels
 template <int CIN, int N, int COUTG, int EPI>
 static int launch_conv(gx_ctx *c, const bf16 *in, gxv::Args a, cudaStream_t st, const int *skip = nullptr) {
@@ -474,12 +441,9 @@ static int launch_conv(gx_ctx *c, const bf16 *in, gxv::Args a, cudaStream_t st, 
         per = std::min(per, 512 / gxv::Shape<CIN, N, kConvRows>::kTmemCols);
         cap = std::max(1, per * nsm);
     }
-    CUtensorMap tm;
-    int rc = encode_act_map(c, &tm, in, a.B, a.H, a.W, CIN);
-    if (rc) return rc;
     a.err = &c->dflags->timeout;
     const int64_t units = (int64_t)a.B * ((a.H + kConvRows - 1) / kConvRows) * ((a.W + gxv::kTW - 1) / gxv::kTW);
-    k_convtc<CIN, N, COUTG, EPI><<<(unsigned)std::min<int64_t>(units, cap), gxv::kThreads, smem, st>>>(tm, a, skip);
+    k_convtc<CIN, N, COUTG, EPI><<<(unsigned)std::min<int64_t>(units, cap), gxv::kThreads, smem, st>>>(in, a, skip);
     GX_LAUNCHED(c);
     return GX_OK;
 }
@@ -563,9 +527,6 @@ int gx_net_solver_args(gx_ctx *c, NetSolverArgs *out, cudaStream_t st) {
     if ((rc = net_reserve(c, 1, H, W))) return rc;
     for (int l = 0; l < kNL; ++l) { out->w[l] = n->wf[l]; out->b[l] = n->bias[l]; }
     out->x0 = n->x0; out->h1 = n->h1; out->h2 = n->h2; out->h3 = n->h3;
-    const void *ins[4] = {n->x0, n->h1, n->h2, n->h3};
-    for (int l = 0; l < kNL; ++l)
-        if ((rc = encode_act_map(c, &out->tm[l], ins[l], 1, H, W, kCinP[l]))) return rc;
     return GX_OK;
 }
 

@@ -1,7 +1,7 @@
 // gx_tc.cuh -- fifth-generation tensor-core primitives (tcgen05) and the TMA
-// copies that feed them, for sm_103a: tensor-memory allocation, shared-memory
-// matrix descriptors, the BF16 MMA with FP32 accumulation in tensor memory,
-// its completion through an mbarrier, bulk and tiled tensor copies, and the
+// bulk copies that feed them, for sm_103a: tensor-memory allocation,
+// shared-memory matrix descriptors, the BF16 MMA with FP32 accumulation in
+// tensor memory, its completion through an mbarrier, bulk copies, and the
 // tensor-memory loads of an epilogue.  Inline PTX only.
 //
 // Operand layout used here ("K-major, no swizzle"): a matrix of rows (M or N)
@@ -124,22 +124,12 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t by
                  : "memory");
 }
 
-// ---- TMA: 1D bulk copy and 5D tiled tensor copy global -> shared, counted on
-// an mbarrier (bulk: addresses 16-byte aligned, bytes a multiple of 16; tensor:
-// destination 128-byte aligned, tmap the address of a CUtensorMap kernel
-// parameter declared __grid_constant__)
+// ---- TMA bulk copy global -> shared, counted on an mbarrier (both addresses
+// 16-byte aligned, bytes a multiple of 16)
 __device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes, uint64_t *bar) {
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
                  "l"(src), "r"(bytes), "r"(smem_addr(bar))
                  : "memory");
-}
-__device__ __forceinline__ void tma_load_5d(uint32_t dst, const void *tmap, int c0, int c1, int c2, int c3, int c4,
-                                            uint64_t *bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, "
-        "%6}], [%7];" ::"r"(dst),
-        "l"(tmap), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(smem_addr(bar))
-        : "memory");
 }
 
 // ---- tensor memory -> registers: lane quarter of the calling warp, 32-bit columns
