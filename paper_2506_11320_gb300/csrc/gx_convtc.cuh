@@ -2,8 +2,18 @@
 // fifth-generation tensor cores (tcgen05.mma kind::f16, BF16 operands, FP32
 // accumulation in tensor memory), fed by TMA bulk copies.
 //
-// Implicit GEMM, one MMA per (output row, tap, 16 input channels):
-//     D[128 pixels][N] += A_tap[128 pixels][16] * W_tap[N][16]^T
+// Implicit GEMM with the three kernel rows folded into N: one MMA per (input
+// row rho, kernel column kx, 16 input channels),
+//     D[128 pixels][3 NB] += A_{rho,kx}[128 pixels][16] * W_kx[3 NB][16]^T,
+// where W_kx stacks the weights of kernel rows ky = 2, 1, 0 (NB output
+// channels each).  D starts at the accumulator block of output row rho - 2,
+// so its three NB-column blocks land on output rows rho - 2, rho - 1, rho with
+// ky = 2, 1, 0 -- exactly the contributions of input row rho -- and tensor
+// memory adds them up across rows.  A unit of R rows takes 3 (R + 2) CIN / 16
+// MMAs instead of 9 R CIN / 16 (the tensor core accepts a narrow MMA no
+// faster than a wide one).  Accumulators start at zero: the epilogue clears
+// each output row's block after reading it (the two blocks on either side of
+// the unit receive out-of-unit terms and are never read).
 // Activations live in global memory as channel-blocked BF16 images with a
 // one-pixel halo ring, [B][C/8][H + 2][W + 2][8]: the producer of a layer
 // writes every edge pixel a second time into the ring (its periodic image, or
@@ -22,11 +32,11 @@
 //
 // Warp roles of the 256-thread CTA, synchronised by mbarriers only:
 //   warp 0:        producer (bulk copies), a ring of kStages tiles;
-//   warp 1 lane 0: MMA issuer, R * 9 * CIN / 16 MMAs per unit into one of two
-//                  accumulator sets, then commits (stage free, accumulators full);
+//   warp 1 lane 0: MMA issuer, 3 (R + 2) CIN / 16 MMAs per unit into one of
+//                  two accumulator sets, then commits (stage free, accumulators full);
 //   warps 4..7:    epilogue, warp w reading TMEM lane quarter w - 4 (pixels
-//                  32 (w - 4) .. + 31 of the unit's 128 columns), all R rows,
-//                  releasing the accumulator set before the global stores.
+//                  32 (w - 4) .. + 31 of the unit's 128 columns), row by row,
+//                  clearing each row's block, then releasing the set.
 // So tile loads, MMAs and epilogue stores of consecutive units overlap.
 //
 // Epilogues: ReLU to BF16 (halo ring included), FP32 without halo (padded
@@ -46,13 +56,13 @@ typedef __nv_bfloat16 bf16;
 constexpr int kTW = 128;            // output columns of a unit (the MMA's M)
 constexpr int kTileRow = kTW + 2;   // tile row with its halo (pixels)
 constexpr int kThreads = 256;       // eight warps
-constexpr int kStages = 3;          // tiles in flight
+constexpr int kStages = 2;          // tiles in flight
 constexpr int kWaitLimit = 1 << 22; // mbarrier polls before a wait gives up
 
 enum { EPI_RELU = 0, EPI_F32 = 1, EPI_MASK = 2, EPI_Z = 3 };
 
 struct Args {
-    const bf16 *wtc;      // weights packed [9 CIN / 8][N][8] (zero rows beyond COUTG)
+    const bf16 *wtc;      // weights packed [3 kx][CIN / 8][3 N (ky = 2, 1, 0)][8] (zero rows beyond COUTG)
     const float *bias;    // [COUTG] or null
     void *out;            // EPI_RELU / EPI_MASK: bf16 [B][N/8][H+2][W+2][8]; EPI_F32: float [B][H][W][COUTG]
     const bf16 *mask;     // EPI_MASK: bf16 [B][N/8][H+2][W+2][8], keep where > 0
@@ -64,17 +74,18 @@ struct Args {
     int B, H, W, periodic;
 };
 
-template <int CIN, int N, int R>
+template <int CIN, int N, int R>   // N: output channels of one row block (NB)
 struct Shape {
     static_assert(CIN % 16 == 0 && N % 16 == 0 && N <= 32 && R >= 1 && R <= 4, "supported shapes");
     static constexpr int kSlabBytes = (R + 2) * kTileRow * 16;
     static constexpr int kTileBytes = (CIN / 8) * kSlabBytes;
     static constexpr int kLoads = (CIN / 8) * (R + 2);                   // bulk copies per tile (one row of one slab)
     static_assert(kLoads <= 32, "one copy per lane of the producer warp");
-    static constexpr int kWSlabBytes = N * 16;
-    static constexpr int kWBytes = 9 * (CIN / 8) * kWSlabBytes;
-    static constexpr int kAccCols = R * N;                               // one unit's accumulators
-    static constexpr int kTmemCols = 2 * kAccCols <= 32 ? 32 : 2 * kAccCols <= 64 ? 64 : 2 * kAccCols <= 128 ? 128 : 256;
+    static constexpr int kWSlabBytes = 3 * N * 16;                       // 8 input channels x 3 NB rows of W_kx
+    static constexpr int kWBytes = 3 * (CIN / 8) * kWSlabBytes;
+    static constexpr int kAccCols = (R + 4) * N;                         // blocks of output rows -2 .. R+1
+    static constexpr int kTmemCols = 2 * kAccCols <= 128 ? 128 : 2 * kAccCols <= 256 ? 256 : 512;
+    static_assert(2 * kAccCols <= 512, "two accumulator sets in tensor memory");
     // [weights][kStages tiles][bias 32 floats][barriers][tmem address, abort flag, units issued]
     // (tile pixels beyond the padded image are never written: they feed no valid output)
     static constexpr int kBiasOff = kWBytes + kStages * kTileBytes;
@@ -207,26 +218,26 @@ __device__ void conv_tc(const Args &a, const bf16 *in, unsigned char *sm, int ct
     } else if (warp == 1) {
         if (lane == 0) {
             // ---- MMA issuer
-            constexpr uint32_t idesc = idesc_bf16_f32(kTW, N);
+            constexpr uint32_t idesc = idesc_bf16_f32(kTW, 3 * N);
             const uint64_t bdesc = sdesc(smem_addr(sW), S::kWSlabBytes, 128);
             bool ok = mbar_wait_or_abort(wfull, 0, kWaitLimit, abort);
             int i = 0;
             for (; ok && i < nmine; ++i) {
                 const int st = i % kStages, n = i / kStages, k = i & 1, m = i >> 1;
                 if (!mbar_wait_or_abort(&full[st], n & 1, kWaitLimit, abort)) break;
-                if (m > 0 && !mbar_wait_or_abort(&accempty[k], (m - 1) & 1, kWaitLimit, abort)) break;
+                if (!mbar_wait_or_abort(&accempty[k], m & 1, kWaitLimit, abort)) break;
                 tc_fence_after();
                 const uint64_t ad = sdesc(smem_addr(sm + S::kWBytes + st * S::kTileBytes), S::kSlabBytes, 128);
                 const uint32_t dacc = tm + k * S::kAccCols;
 #pragma unroll
-                for (int tap = 0; tap < 9; ++tap) {
+                for (int rho = 0; rho < R + 2; ++rho) {
 #pragma unroll
-                    for (int kc = 0; kc < CIN / 16; ++kc) {
+                    for (int kx = 0; kx < 3; ++kx) {
 #pragma unroll
-                        for (int r = 0; r < R; ++r) {
-                            const uint32_t aoff = ((r + tap / 3) * kTileRow + tap % 3) + 2 * kc * (S::kSlabBytes / 16);
-                            const uint32_t boff = (tap * (CIN / 8) + 2 * kc) * (S::kWSlabBytes / 16);
-                            mma_bf16(dacc + r * N, ad + aoff, bdesc + boff, idesc, tap > 0 || kc > 0);
+                        for (int kc = 0; kc < CIN / 16; ++kc) {
+                            const uint32_t aoff = (rho * kTileRow + kx) + 2 * kc * (S::kSlabBytes / 16);
+                            const uint32_t boff = (kx * (CIN / 8) + 2 * kc) * (S::kWSlabBytes / 16);
+                            mma_bf16(dacc + rho * N, ad + aoff, bdesc + boff, idesc, true);
                         }
                     }
                 }
@@ -238,6 +249,15 @@ __device__ void conv_tc(const Args &a, const bf16 *in, unsigned char *sm, int ct
     } else if (warp >= 4) {
         // ---- epilogue
         const int q4 = warp - 4;
+        const uint32_t lane_base = tm + ((uint32_t)(32 * q4) << 16);
+        // both accumulator sets start at zero (output-row blocks 2 .. R+1)
+#pragma unroll 1
+        for (int k = 0; k < 2; ++k) {
+            for (int c = 2 * N; c < (R + 2) * N; c += 16) tmem_zero16(lane_base + k * S::kAccCols + c);
+            tmem_wait_st();
+            tc_fence_before();
+            mbar_arrive(&accempty[k]);
+        }
         for (int i = 0; i < nmine; ++i) {
             const int k = i & 1, m = i >> 1;
             // one lane polls; the warp reads tensor memory together (.sync.aligned)
@@ -246,23 +266,19 @@ __device__ void conv_tc(const Args &a, const bf16 *in, unsigned char *sm, int ct
             ok = __shfl_sync(0xffffffffu, ok, 0);
             if (!ok) break;
             tc_fence_after();
-            float acc[R][N];
-#pragma unroll
-            for (int r = 0; r < R; ++r)
-#pragma unroll
-                for (int j = 0; j < N / 16; ++j)
-                    tmem_ld16(tm + ((uint32_t)(32 * q4) << 16) + k * S::kAccCols + r * N + 16 * j,
-                              *reinterpret_cast<float(*)[16]>(&acc[r][16 * j]));
-            tc_fence_before();
-            mbar_arrive(&accempty[k]);
             int b, y0, x0;
             unit_pos<R>(cta + (int64_t)i * ncta, nseg, nblk, b, y0, x0);
             const int xx = x0 + 32 * q4 + lane;
-            if (xx >= a.W) continue;
-#pragma unroll
+#pragma unroll 1
             for (int r = 0; r < R; ++r) {
                 const int yy = y0 + r;
-                if (yy >= a.H) break;
+                const uint32_t blk = lane_base + k * S::kAccCols + (r + 2) * N;
+                float acc[N];
+#pragma unroll
+                for (int j = 0; j < N / 16; ++j) tmem_ld16(blk + 16 * j, *reinterpret_cast<float(*)[16]>(&acc[16 * j]));
+#pragma unroll
+                for (int j = 0; j < N / 16; ++j) tmem_zero16(blk + 16 * j);
+                if (yy >= a.H || xx >= a.W) continue;
                 if (EPI == EPI_RELU || EPI == EPI_MASK) {
                     uint4 packed[N / 8];
                     uint32_t *pw = reinterpret_cast<uint32_t *>(packed);
@@ -276,8 +292,8 @@ __device__ void conv_tc(const Args &a, const bf16 *in, unsigned char *sm, int ct
                             for (int h = 0; h < 4; ++h) {
                                 const __nv_bfloat162 m2 = *reinterpret_cast<const __nv_bfloat162 *>(&mw[h]);
                                 const int c = 8 * c8 + 2 * h;
-                                const float v0 = __bfloat162float(m2.x) > 0.f ? acc[r][c] : 0.f;
-                                const float v1 = __bfloat162float(m2.y) > 0.f ? acc[r][c + 1] : 0.f;
+                                const float v0 = __bfloat162float(m2.x) > 0.f ? acc[c] : 0.f;
+                                const float v1 = __bfloat162float(m2.y) > 0.f ? acc[c + 1] : 0.f;
                                 const __nv_bfloat162 o = __floats2bfloat162_rn(v0, v1);
                                 pw[c / 2] = *reinterpret_cast<const uint32_t *>(&o);
                             }
@@ -285,8 +301,8 @@ __device__ void conv_tc(const Args &a, const bf16 *in, unsigned char *sm, int ct
                     } else {
 #pragma unroll
                         for (int c = 0; c < N; c += 2) {
-                            const __nv_bfloat162 o = __floats2bfloat162_rn(fmaxf(acc[r][c] + sBias[c], 0.f),
-                                                                           fmaxf(acc[r][c + 1] + sBias[c + 1], 0.f));
+                            const __nv_bfloat162 o = __floats2bfloat162_rn(fmaxf(acc[c] + sBias[c], 0.f),
+                                                                           fmaxf(acc[c + 1] + sBias[c + 1], 0.f));
                             pw[c / 2] = *reinterpret_cast<const uint32_t *>(&o);
                         }
                     }
@@ -296,8 +312,8 @@ __device__ void conv_tc(const Args &a, const bf16 *in, unsigned char *sm, int ct
                     float4 *o4 = reinterpret_cast<float4 *>(static_cast<float *>(a.out) + pix * COUTG);
 #pragma unroll
                     for (int c = 0; c < COUTG; c += 4)
-                        o4[c / 4] = make_float4(acc[r][c] + sBias[c], acc[r][c + 1] + sBias[c + 1],
-                                                acc[r][c + 2] + sBias[c + 2], acc[r][c + 3] + sBias[c + 3]);
+                        o4[c / 4] = make_float4(acc[c] + sBias[c], acc[c + 1] + sBias[c + 1],
+                                                acc[c + 2] + sBias[c + 2], acc[c + 3] + sBias[c + 3]);
                 } else {   // EPI_Z: z = D^-1 v + s y  (B = 1)
                     const int64_t HW = (int64_t)a.H * a.W, q = (int64_t)yy * a.W + xx;
                     const double v0 = __ldcg(a.v + q), v1 = __ldcg(a.v + HW + q), v2 = __ldcg(a.v + 2 * HW + q);
@@ -305,9 +321,13 @@ __device__ void conv_tc(const Args &a, const bf16 *in, unsigned char *sm, int ct
 #pragma unroll
                     for (int c = 0; c < 3; ++c)
                         a.z[c * HW + q] = o[3 * c] * v0 + o[3 * c + 1] * v1 + o[3 * c + 2] * v2 +
-                                          a.s * (double)(acc[r][c] + sBias[c]);
+                                          a.s * (double)(acc[c] + sBias[c]);
                 }
             }
+            // this set's output blocks are read and cleared: hand it back to the MMA thread
+            tmem_wait_st();
+            tc_fence_before();
+            mbar_arrive(&accempty[k]);
         }
     }
     __syncthreads();

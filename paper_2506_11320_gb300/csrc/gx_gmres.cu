@@ -75,7 +75,7 @@ struct CoArgs {
 
 // in-kernel network: image rows per convolution unit, shared memory of the
 // largest layer (+ alignment slack)
-constexpr int kNetRows = 2;
+constexpr int kNetRows = 4;
 constexpr int kNetSmemBytes = gxv::smem_bytes<32, 32, kNetRows>() + 128;
 static_assert(kB == gxv::kThreads, "the convolution runs on the solver's 256-thread CTAs");
 

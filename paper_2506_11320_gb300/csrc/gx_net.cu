@@ -57,7 +57,7 @@ inline int64_t param_count() { return param_offset(kNL); }
 
 // the forward/data-gradient convolution as a kernel (a persistent grid of
 // tensor-core CTAs, gx_convtc.cuh); R image rows per unit of work
-constexpr int kConvRows = 2;
+constexpr int kConvRows = 4;
 
 template <int CIN, int N, int COUTG, int EPI>
 __global__ void __launch_bounds__(gxv::kThreads) k_convtc(const gxv::bf16 *in, gxv::Args a, const int *skip) {
@@ -156,28 +156,32 @@ __global__ void __launch_bounds__(256) k_wgrad(WgArgs a) {
 // forward weights [coutP][9][cinP], FP32 bias [coutP], BF16 data-gradient
 // weights [cin][9][gcoutP] (flipped taps, channel roles swapped)
 // FP32 master weights -> BF16 operands of the tensor-core convolution, packed
-// as its weight slabs: element (n, k) of W_l viewed as [N][9 CINP] (k = tap *
-// CINP + ci) at ((k / 8) * NP + n) * 8 + k % 8, zero for padded n or ci.
+// as its weight slabs: for kernel column kx and 8-input-channel group kg, the
+// 3 NP rows (kernel rows ky = 2, 1, 0, NP output channels each) of 8 channels,
+// element (kx, kg, (2 - ky) NP + n, j) at ((kx CINP/8 + kg) 3 NP + (2 - ky) NP
+// + n) 8 + j, zero for padded n or channels.
 //   wf: the forward kernel, n = output channel (NP = nP);
 //   wd: the data-gradient kernel (flipped taps, channel roles swapped),
-//       n = input channel of the layer (NP = cin), k over (tap, output channel
-//       padded to gcoutP).
+//       n = input channel of the layer (NP = cin), channels = output channels
+//       of the layer padded to gcoutP.
 __global__ void k_pack_weights(const float *params, bf16 *wf, float *bias, bf16 *wd, int cin, int cout, int cinP,
                                int nP, int coutP, int gcoutP, int64_t off) {
     const float *W = params + off, *bsrc = params + off + (int64_t)cout * cin * 9;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < 9 * cinP * nP; t += gridDim.x * blockDim.x) {
-        const int kg = t / (nP * 8), n = (t / 8) % nP, k = kg * 8 + t % 8;
-        const int tap = k / cinP, ci = k % cinP;
-        const float v = (n < cout && ci < cin) ? W[((n * cin + ci) * 9) + tap] : 0.f;
+        const int j = t % 8, n3 = (t / 8) % (3 * nP), kgx = t / (8 * 3 * nP);
+        const int kx = kgx / (cinP / 8), ci = (kgx % (cinP / 8)) * 8 + j;
+        const int ky = 2 - n3 / nP, n = n3 % nP;
+        const float v = (n < cout && ci < cin) ? W[((n * cin + ci) * 9) + ky * 3 + kx] : 0.f;
         wf[t] = __float2bfloat16_rn(v);
     }
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < coutP; t += gridDim.x * blockDim.x)
         bias[t] = t < cout ? bsrc[t] : 0.f;
     if (wd) {
         for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < 9 * gcoutP * cin; t += gridDim.x * blockDim.x) {
-            const int kg = t / (cin * 8), n = (t / 8) % cin, k = kg * 8 + t % 8;
-            const int tp = k / gcoutP, co = k % gcoutP;
-            const float v = co < cout ? W[((co * cin + n) * 9) + (8 - tp)] : 0.f;
+            const int j = t % 8, n3 = (t / 8) % (3 * cin), kgx = t / (8 * 3 * cin);
+            const int kx = kgx / (gcoutP / 8), co = (kgx % (gcoutP / 8)) * 8 + j;
+            const int ky = 2 - n3 / cin, n = n3 % cin;
+            const float v = co < cout ? W[((co * cin + n) * 9) + (8 - (ky * 3 + kx))] : 0.f;
             wd[t] = __float2bfloat16_rn(v);
         }
     }

@@ -132,6 +132,17 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_
                  : "memory");
 }
 
+// ---- registers -> tensor memory: zeros into 16 columns of the calling warp's
+// lane quarter (tcgen05_wait_st before the columns are handed to an MMA)
+__device__ __forceinline__ void tmem_zero16(uint32_t taddr) {
+    const uint32_t z = 0;
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1};" ::"r"(taddr),
+        "r"(z)
+        : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
 // ---- tensor memory -> registers: lane quarter of the calling warp, 32-bit columns
 // (thread t of warp w reads TMEM lane 32 (w % 4) + t; register i = column col + i)
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {

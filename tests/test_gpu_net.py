@@ -132,7 +132,7 @@ def emulate_bf16(torch, p, x, t=None, periodic=True):
     return y[0].numpy(), grads
 
 
-# (H, W): the convolution works on units of 2 rows x 128 columns.  Narrow
+# (H, W): the convolution works on units of 4 rows x 128 columns.  Narrow
 # images (one partial unit per row pair, odd heights), one exact unit, and
 # rows of several units with a ragged last one (the periodic halo crossing
 # unit and image edges).
