@@ -34,9 +34,11 @@
 //   warp 0:        producer (bulk copies), a ring of kStages tiles;
 //   warp 1 lane 0: MMA issuer, 3 (R + 2) CIN / 16 MMAs per unit into one of
 //                  two accumulator sets, then commits (stage free, accumulators full);
-//   warps 4..7:    epilogue, warp w reading TMEM lane quarter w - 4 (pixels
-//                  32 (w - 4) .. + 31 of the unit's 128 columns), row by row,
-//                  clearing each row's block, then releasing the set.
+//   warps 4..7:    epilogue, warp w reading TMEM lane quarter w % 4 (pixels
+//                  32 (w % 4) .. + 31 of the unit's 128 columns), row by row,
+//                  clearing each row's block, then releasing the set.  A
+//                  512-thread CTA has a second epilogue group, warps 12..15,
+//                  and the two groups take alternate rows.
 // So tile loads, MMAs and epilogue stores of consecutive units overlap.
 //
 // Epilogues: ReLU to BF16 (halo ring included), FP32 without halo (padded
@@ -55,7 +57,7 @@ typedef __nv_bfloat16 bf16;
 
 constexpr int kTW = 128;            // output columns of a unit (the MMA's M)
 constexpr int kTileRow = kTW + 2;   // tile row with its halo (pixels)
-constexpr int kThreads = 256;       // eight warps
+constexpr int kThreads = 256;       // eight warps: one role group (a CTA may run 1 or 2 groups)
 constexpr int kStages = 2;          // tiles in flight
 constexpr int kWaitLimit = 1 << 22; // mbarrier polls before a wait gives up
 
@@ -149,7 +151,7 @@ __device__ __forceinline__ void store_with_halo(bf16 *img, int b, int y, int x, 
 }
 
 // out = epilogue(conv3x3(in, w) + bias) over the units cta, cta + ncta, ...
-// Every thread of the CTA calls it (blockDim.x == kThreads); sm: smem_bytes()
+// Every thread of the CTA calls it (blockDim.x == 256 or 512); sm: smem_bytes()
 // bytes, 128-byte aligned; in: the input image [B][CIN/8][H+2][W+2][8].  N: MMA
 // width (output channels padded to 16 or 32); COUTG: output channels of w /
 // bias (<= N).
@@ -167,6 +169,7 @@ __device__ void conv_tc(const Args &a, const bf16 *in, unsigned char *sm, int ct
     volatile int *abort = reinterpret_cast<volatile int *>(sm + S::kMiscOff + 4);
     volatile int *s_issued = reinterpret_cast<volatile int *>(sm + S::kMiscOff + 8);   // units the MMA thread issued
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int ngroups = blockDim.x >> 8, group = warp >> 3;    // epilogue groups, this warp's
 
     const int nseg = (a.W + kTW - 1) / kTW, nblk = (a.H + R - 1) / R;
     const int64_t nunits = (int64_t)a.B * nblk * nseg;
@@ -175,7 +178,7 @@ __device__ void conv_tc(const Args &a, const bf16 *in, unsigned char *sm, int ct
 
     if (tid < 32) sBias[tid] = (a.bias && tid < COUTG) ? a.bias[tid] : 0.f;
     if (tid == 0) {
-        for (int i = 0; i < S::kNumBars; ++i) mbar_init(&bars[i], i >= 1 + 2 * kStages + 2 ? 4 * 32 : 1);
+        for (int i = 0; i < S::kNumBars; ++i) mbar_init(&bars[i], i >= 1 + 2 * kStages + 2 ? 4 * 32 * ngroups : 1);
         *abort = 0;
         *s_issued = 0;
     }
@@ -246,14 +249,15 @@ __device__ void conv_tc(const Args &a, const bf16 *in, unsigned char *sm, int ct
             }
             *s_issued = i;
         }
-    } else if (warp >= 4) {
+    } else if ((warp & 7) >= 4) {
         // ---- epilogue
-        const int q4 = warp - 4;
+        const int q4 = warp & 3;
         const uint32_t lane_base = tm + ((uint32_t)(32 * q4) << 16);
         // both accumulator sets start at zero (output-row blocks 2 .. R+1)
 #pragma unroll 1
         for (int k = 0; k < 2; ++k) {
-            for (int c = 2 * N; c < (R + 2) * N; c += 16) tmem_zero16(lane_base + k * S::kAccCols + c);
+            for (int r = group; r < R; r += ngroups)
+                for (int c = 0; c < N; c += 16) tmem_zero16(lane_base + k * S::kAccCols + (r + 2) * N + c);
             tmem_wait_st();
             tc_fence_before();
             mbar_arrive(&accempty[k]);
@@ -270,7 +274,7 @@ __device__ void conv_tc(const Args &a, const bf16 *in, unsigned char *sm, int ct
             unit_pos<R>(cta + (int64_t)i * ncta, nseg, nblk, b, y0, x0);
             const int xx = x0 + 32 * q4 + lane;
 #pragma unroll 1
-            for (int r = 0; r < R; ++r) {
+            for (int r = group; r < R; r += ngroups) {
                 const int yy = y0 + r;
                 const uint32_t blk = lane_base + k * S::kAccCols + (r + 2) * N;
                 float acc[N];

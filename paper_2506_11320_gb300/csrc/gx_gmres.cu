@@ -49,8 +49,10 @@ struct GmState {
 
 namespace {
 
-constexpr int kB = 256;
+constexpr int kB = 256;               // threads per CTA (plain / block Jacobi: two CTAs per SM)
+constexpr int kBNet = 512;            // with the network: one CTA per SM (its shared and tensor memory)
 constexpr int kWarps = kB / 32;
+constexpr int kMaxWarps = kBNet / 32;
 constexpr int kMaxGrid = 152 * 8;
 constexpr int kPartStride = kMaxM + 2;
 
@@ -77,7 +79,7 @@ struct CoArgs {
 // largest layer (+ alignment slack)
 constexpr int kNetRows = 4;
 constexpr int kNetSmemBytes = gxv::smem_bytes<32, 32, kNetRows>() + 128;
-static_assert(kB == gxv::kThreads, "the convolution runs on the solver's 256-thread CTAs");
+static_assert(kBNet % gxv::kThreads == 0 && kBNet / gxv::kThreads <= 2, "the convolution's role groups");
 
 // every thread's node set: q = tid, tid + nthreads, ...
 #define NODE_LOOP(q) \
@@ -96,8 +98,7 @@ __device__ __forceinline__ void cta_partials(double acc[8], int kk, double *sred
     __syncthreads();
     if (threadIdx.x < kk) {
         double s = 0.0;
-#pragma unroll
-        for (int w = 0; w < kWarps; ++w) s += sred[w * 8 + threadIdx.x];
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sred[w * 8 + threadIdx.x];
         dst[threadIdx.x] = s;
     }
     __syncthreads();
@@ -106,7 +107,7 @@ __device__ __forceinline__ void cta_partials(double acc[8], int kk, double *sred
 // sum over all CTAs of partial rows [0, k) -> out (shared), same order in every CTA
 __device__ __forceinline__ void grid_sums(const double *part, int k, double *out) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int i = warp; i < k; i += kWarps) {
+    for (int i = warp; i < k; i += (int)(blockDim.x >> 5)) {
         double s = 0.0;
         for (int b = lane; b < (int)gridDim.x; b += 32) s += __ldcg(part + (size_t)b * kPartStride + i);
 #pragma unroll
@@ -188,11 +189,11 @@ __device__ void net_apply(const CoArgs &a, cg::grid_group &grid, int j, unsigned
 // NET: the learned preconditioner is applied in the kernel (the plain and
 // Jacobi instantiation is smaller and fits two CTAs per SM)
 template <bool NET>
-__global__ void __launch_bounds__(kB, NET ? 1 : 2) k_fgmres(const __grid_constant__ CoArgs a) {
+__global__ void __launch_bounds__(NET ? kBNet : kB, NET ? 1 : 2) k_fgmres(const __grid_constant__ CoArgs a) {
     extern __shared__ __align__(128) unsigned char gsm_raw[];
     unsigned char *gsm = gsm_raw + ((128 - (gxt::smem_addr(gsm_raw) & 127)) & 127);
     cg::grid_group grid = cg::this_grid();
-    __shared__ double sred[kWarps * 8];
+    __shared__ double sred[kMaxWarps * 8];
     __shared__ double hs[2][kMaxM + 2];
     __shared__ double s_cs[kMaxM], s_sn[kMaxM], s_g[kMaxM + 1], s_y[kMaxM];
     __shared__ double s_scalar[2];
@@ -491,7 +492,7 @@ int gx_fgmres(gx_ctx *c, cudaStream_t st) {
         GX_CHECK(c, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
         if (smem > 0)
             GX_CHECK(c, cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        GX_CHECK(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kfn, kB, smem));
+        GX_CHECK(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kfn, use_net ? kBNet : kB, smem));
         grid = std::max(1, std::min(per * nsm, kMaxGrid));
     }
     CoArgs a{};
@@ -525,7 +526,7 @@ int gx_fgmres(gx_ctx *c, cudaStream_t st) {
     k_gm_init<<<1, 32, 0, st>>>(c->gm);
     GX_LAUNCHED(c);
     void *args[] = {&a};
-    GX_CHECK(c, cudaLaunchCooperativeKernel(kfn, dim3(grid), dim3(kB), args, smem, st));
+    GX_CHECK(c, cudaLaunchCooperativeKernel(kfn, dim3(grid), dim3(use_net ? kBNet : kB), args, smem, st));
     c->launches++;
     struct Flags { int j, done, finished, conv, total; };
     Flags *hf = reinterpret_cast<Flags *>(c->hpin);

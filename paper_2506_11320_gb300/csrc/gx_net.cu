@@ -60,7 +60,7 @@ inline int64_t param_count() { return param_offset(kNL); }
 constexpr int kConvRows = 4;
 
 template <int CIN, int N, int COUTG, int EPI>
-__global__ void __launch_bounds__(gxv::kThreads) k_convtc(const gxv::bf16 *in, gxv::Args a, const int *skip) {
+__global__ void __launch_bounds__(2 * gxv::kThreads) k_convtc(const gxv::bf16 *in, gxv::Args a, const int *skip) {
     extern __shared__ __align__(128) unsigned char dsm[];
     if (skip && *skip) return;
     unsigned char *sm = dsm + ((128 - (gxt::smem_addr(dsm) & 127)) & 127);
@@ -440,14 +440,14 @@ static int launch_conv(gx_ctx *c, const bf16 *in, gxv::Args a, cudaStream_t st, 
         GX_CHECK(c, cudaGetDevice(&dev));
         GX_CHECK(c, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
         GX_CHECK(c, cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        GX_CHECK(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kfn, gxv::kThreads, smem));
+        GX_CHECK(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kfn, 2 * gxv::kThreads, smem));
         // tensor memory: 512 columns per SM, kTmemCols per resident CTA
         per = std::min(per, 512 / gxv::Shape<CIN, N, kConvRows>::kTmemCols);
         cap = std::max(1, per * nsm);
     }
     a.err = &c->dflags->timeout;
     const int64_t units = (int64_t)a.B * ((a.H + kConvRows - 1) / kConvRows) * ((a.W + gxv::kTW - 1) / gxv::kTW);
-    k_convtc<CIN, N, COUTG, EPI><<<(unsigned)std::min<int64_t>(units, cap), gxv::kThreads, smem, st>>>(in, a, skip);
+    k_convtc<CIN, N, COUTG, EPI><<<(unsigned)std::min<int64_t>(units, cap), 2 * gxv::kThreads, smem, st>>>(in, a, skip);
     GX_LAUNCHED(c);
     return GX_OK;
 }
