@@ -213,6 +213,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-precond", action="store_true")
+    ap.add_argument("--precond-workload", default="harris_1024x512",
+                    help="plasma of the learned-vs-plain GMRES comparison: harris_1024x512 (the learned-"
+                         "preconditioner configuration: Harris reconnection, 1024x512 cells, 100 ppc/species) "
+                         "or 'same' (the main workload)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -292,7 +296,16 @@ def main():
     # ------------------------------------------------------- field solve: learned vs plain
     solve_cmp = None
     if not args.no_precond:
-        solve_cmp = run_precond_compare(gx, wl, args.steps, barrier)
+        if args.precond_workload == "same":
+            pwl, pdesc = wl, desc
+        else:
+            pwl = workloads.harris(nx=1024, ny=512, ppc=100)
+            pdesc = ("Harris double current sheet 1024x512 cells, dx 0.05 d_i, 100 particles/cell/species "
+                     f"({pwl.n_particles / 1e6:.1f} M particles), mass ratio 100, Ti/Te 5, flow 0.5 v_A")
+        solve_cmp = run_precond_compare(gx, pwl, args.steps, barrier)
+        solve_cmp["workload"] = pdesc
+        solve_cmp["cells"] = list(pwl.n[:2])
+        del pwl
 
     # ------------------------------------------------------- end to end (host buffers)
     e2e = None
