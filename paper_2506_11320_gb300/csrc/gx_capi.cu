@@ -180,6 +180,7 @@ void gx_destroy(gx_ctx *c) {
                      &c->w, &c->r, &c->dred, &c->hcol};
     for (auto p : dp)
         if (*p) cudaFree(*p);
+    if (c->jdiag32) cudaFree(c->jdiag32);
     float4 **fp[] = {&c->nE, &c->nB, &c->nBnext, &c->nUref};
     for (auto p : fp)
         if (*p) cudaFree(*p);
@@ -234,7 +235,7 @@ int gx_create(const gx_config *cfg, gx_ctx **out) {
     for (auto p : vec3)
         if ((rc = dalloc(c, p, 3 * N))) return fail(rc, nullptr);
     if ((rc = dalloc(c, &c->rho, N)) || (rc = dalloc(c, &c->rho_m, N)) || (rc = dalloc(c, &c->M, 81 * N)) ||
-        (rc = dalloc(c, &c->kappa, 6 * N)) || (rc = dalloc(c, &c->jdiag, 9 * N)) ||
+        (rc = dalloc(c, &c->kappa, 6 * N)) || (rc = dalloc(c, &c->jdiag, 9 * N)) || (rc = dalloc(c, &c->jdiag32, 9 * N)) ||
         (rc = dalloc(c, &c->V, (size_t)(m + 1) * 3 * N)) || (rc = dalloc(c, &c->dred, 64)) ||
         (rc = dalloc(c, &c->hcol, 2 * (m + 2))) || (rc = dalloc(c, &c->dflags, 1)))
         return fail(rc, nullptr);

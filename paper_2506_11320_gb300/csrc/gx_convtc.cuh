@@ -43,8 +43,9 @@
 //
 // Epilogues: ReLU to BF16 (halo ring included), FP32 without halo (padded
 // output channels), the ReLU mask of the data gradient, and -- inside the
-// solver -- the preconditioned vector z = D^-1 v + s N(v / s) written straight
-// to FP64.
+// solver -- the preconditioned vector z = D^-1 v + s N(v / s), evaluated in
+// FP32 (a preconditioner needs no FP64: FGMRES judges the FP64 residual) and
+// stored as FP64.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -69,7 +70,7 @@ struct Args {
     void *out;            // EPI_RELU / EPI_MASK: bf16 [B][N/8][H+2][W+2][8]; EPI_F32: float [B][H][W][COUTG]
     const bf16 *mask;     // EPI_MASK: bf16 [B][N/8][H+2][W+2][8], keep where > 0
     const double *v;      // EPI_Z: Krylov vector [3][H*W] (B = 1)
-    const double *jd;     // EPI_Z: block-Jacobi inverse [H*W][9]
+    const float *jd;      // EPI_Z: block-Jacobi inverse [H*W][9], FP32
     double *z;            // EPI_Z: [3][H*W]
     double s;             // EPI_Z: output scale s
     int *err;             // set when a bounded wait gives up
@@ -103,12 +104,11 @@ __host__ __device__ constexpr int smem_bytes() { return Shape<CIN, N, R>::kSmemB
 
 // decode a unit index into (image, first row, first column)
 template <int R>
-__device__ __forceinline__ void unit_pos(int64_t u, int nseg, int nblk, int &b, int &y0, int &x0) {
-    const int seg = (int)(u % nseg);
-    const int64_t t = u / nseg;
-    y0 = (int)(t % nblk) * R;
-    b = (int)(t / nblk);
-    x0 = seg * kTW;
+__device__ __forceinline__ void unit_pos(int u, int nseg, int nblk, int &b, int &y0, int &x0) {
+    const int t = u / nseg;
+    x0 = (u - t * nseg) * kTW;
+    b = t / nblk;
+    y0 = (t - b * nblk) * R;
 }
 
 // offset (elements) of the 8-channel chunk g of pixel (b, y, x) of a
@@ -156,8 +156,19 @@ __device__ __forceinline__ void store_with_halo(bf16 *img, int b, int y, int x, 
 // width (output channels padded to 16 or 32); COUTG: output channels of w /
 // bias (<= N).
 template <int CIN, int N, int COUTG, int R, int EPI>
-__device__ void conv_tc(const Args &a, const bf16 *in, unsigned char *sm, int cta, int ncta) {
+__device__ void conv_tc(const Args &args, const bf16 *in, unsigned char *sm, int cta, int ncta) {
     using namespace gxt;
+    // register copies of the arguments: the inline assembly below clobbers
+    // memory, which would otherwise force a reload of every field after it
+    const int H = args.H, W = args.W, periodic = args.periodic;
+    const bf16 *const wtc = args.wtc, *const mask = args.mask;
+    const float *const bias = args.bias;
+    void *const out = args.out;
+    const double *const vz = args.v;
+    const float *const jd = args.jd;
+    double *const z = args.z;
+    const double s_out = args.s;
+    int *const err = args.err;
     using S = Shape<CIN, N, R>;
     static_assert(COUTG <= N && (EPI != EPI_Z || COUTG >= 3), "output channels");
     unsigned char *sW = sm;
@@ -171,12 +182,12 @@ __device__ void conv_tc(const Args &a, const bf16 *in, unsigned char *sm, int ct
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int ngroups = blockDim.x >> 8, group = warp >> 3;    // epilogue groups, this warp's
 
-    const int nseg = (a.W + kTW - 1) / kTW, nblk = (a.H + R - 1) / R;
-    const int64_t nunits = (int64_t)a.B * nblk * nseg;
+    const int nseg = (W + kTW - 1) / kTW, nblk = (H + R - 1) / R;
+    const int nunits = args.B * nblk * nseg;
     if (cta >= nunits) return;
-    const int nmine = (int)((nunits - 1 - cta) / ncta) + 1;    // units of this CTA
+    const int nmine = (nunits - 1 - cta) / ncta + 1;    // units of this CTA
 
-    if (tid < 32) sBias[tid] = (a.bias && tid < COUTG) ? a.bias[tid] : 0.f;
+    if (tid < 32) sBias[tid] = (bias && tid < COUTG) ? bias[tid] : 0.f;
     if (tid == 0) {
         for (int i = 0; i < S::kNumBars; ++i) mbar_init(&bars[i], i >= 1 + 2 * kStages + 2 ? 4 * 32 * ngroups : 1);
         *abort = 0;
@@ -194,16 +205,16 @@ __device__ void conv_tc(const Args &a, const bf16 *in, unsigned char *sm, int ct
         // ---- producer: lane 0 waits for the stage and announces the bytes, lanes issue the row copies
         if (lane == 0) {
             mbar_arrive_expect_tx(wfull, S::kWBytes);
-            bulk_load(smem_addr(sW), a.wtc, S::kWBytes, wfull);
+            bulk_load(smem_addr(sW), wtc, S::kWBytes, wfull);
         }
         int i = 0;
         for (; i < nmine; ++i) {
             const int st = i % kStages, n = i / kStages;
             int b, y0, x0;
-            unit_pos<R>(cta + (int64_t)i * ncta, nseg, nblk, b, y0, x0);
+            unit_pos<R>(cta + i * ncta, nseg, nblk, b, y0, x0);
             // rows y0-1 .. y0+R of the padded image that exist (up to row H), and the
             // pixels of each from padded column x0 (= image column x0 - 1) that exist
-            const int rows = min(R + 2, a.H + 2 - y0), npx = min(kTileRow, a.W + 2 - x0);
+            const int rows = min(R + 2, H + 2 - y0), npx = min(kTileRow, W + 2 - x0);
             int ok = 1;
             if (lane == 0) {
                 if (n > 0) ok = mbar_wait_or_abort(&empty[st], (n - 1) & 1, kWaitLimit, abort);
@@ -214,7 +225,7 @@ __device__ void conv_tc(const Args &a, const bf16 *in, unsigned char *sm, int ct
                 const int r = lane % (R + 2), g = lane / (R + 2);
                 if (r < rows)
                     bulk_load(smem_addr(sm + S::kWBytes + st * S::kTileBytes + g * S::kSlabBytes + r * kTileRow * 16),
-                              in + blk_off(b, g, y0 - 1 + r, x0 - 1, a.H, a.W, CIN / 8), npx * 16, &full[st]);
+                              in + blk_off(b, g, y0 - 1 + r, x0 - 1, H, W, CIN / 8), npx * 16, &full[st]);
             }
         }
         nloaded = i;
@@ -253,6 +264,9 @@ __device__ void conv_tc(const Args &a, const bf16 *in, unsigned char *sm, int ct
         // ---- epilogue
         const int q4 = warp & 3;
         const uint32_t lane_base = tm + ((uint32_t)(32 * q4) << 16);
+        float bz[N];                   // the bias, in registers for the whole call
+#pragma unroll
+        for (int c = 0; c < N; ++c) bz[c] = sBias[c];
         // both accumulator sets start at zero (output-row blocks 2 .. R+1)
 #pragma unroll 1
         for (int k = 0; k < 2; ++k) {
@@ -271,7 +285,7 @@ __device__ void conv_tc(const Args &a, const bf16 *in, unsigned char *sm, int ct
             if (!ok) break;
             tc_fence_after();
             int b, y0, x0;
-            unit_pos<R>(cta + (int64_t)i * ncta, nseg, nblk, b, y0, x0);
+            unit_pos<R>(cta + i * ncta, nseg, nblk, b, y0, x0);
             const int xx = x0 + 32 * q4 + lane;
 #pragma unroll 1
             for (int r = group; r < R; r += ngroups) {
@@ -282,7 +296,7 @@ __device__ void conv_tc(const Args &a, const bf16 *in, unsigned char *sm, int ct
                 for (int j = 0; j < N / 16; ++j) tmem_ld16(blk + 16 * j, *reinterpret_cast<float(*)[16]>(&acc[16 * j]));
 #pragma unroll
                 for (int j = 0; j < N / 16; ++j) tmem_zero16(blk + 16 * j);
-                if (yy >= a.H || xx >= a.W) continue;
+                if (yy >= H || xx >= W) continue;
                 if (EPI == EPI_RELU || EPI == EPI_MASK) {
                     uint4 packed[N / 8];
                     uint32_t *pw = reinterpret_cast<uint32_t *>(packed);
@@ -290,7 +304,7 @@ __device__ void conv_tc(const Args &a, const bf16 *in, unsigned char *sm, int ct
 #pragma unroll
                         for (int c8 = 0; c8 < N / 8; ++c8) {
                             const uint4 m4 =
-                                *reinterpret_cast<const uint4 *>(a.mask + blk_off(b, c8, yy, xx, a.H, a.W, N / 8));
+                                *reinterpret_cast<const uint4 *>(mask + blk_off(b, c8, yy, xx, H, W, N / 8));
                             const uint32_t mw[4] = {m4.x, m4.y, m4.z, m4.w};
 #pragma unroll
                             for (int h = 0; h < 4; ++h) {
@@ -305,27 +319,28 @@ __device__ void conv_tc(const Args &a, const bf16 *in, unsigned char *sm, int ct
                     } else {
 #pragma unroll
                         for (int c = 0; c < N; c += 2) {
-                            const __nv_bfloat162 o = __floats2bfloat162_rn(fmaxf(acc[c] + sBias[c], 0.f),
-                                                                           fmaxf(acc[c + 1] + sBias[c + 1], 0.f));
+                            const __nv_bfloat162 o = __floats2bfloat162_rn(fmaxf(acc[c] + bz[c], 0.f),
+                                                                           fmaxf(acc[c + 1] + bz[c + 1], 0.f));
                             pw[c / 2] = *reinterpret_cast<const uint32_t *>(&o);
                         }
                     }
-                    store_with_halo<N>(static_cast<bf16 *>(a.out), b, yy, xx, a.H, a.W, a.periodic, packed);
+                    store_with_halo<N>(static_cast<bf16 *>(out), b, yy, xx, H, W, periodic, packed);
                 } else if (EPI == EPI_F32) {
-                    const int64_t pix = ((int64_t)b * a.H + yy) * a.W + xx;
-                    float4 *o4 = reinterpret_cast<float4 *>(static_cast<float *>(a.out) + pix * COUTG);
+                    const int64_t pix = ((int64_t)b * H + yy) * W + xx;
+                    float4 *o4 = reinterpret_cast<float4 *>(static_cast<float *>(out) + pix * COUTG);
 #pragma unroll
                     for (int c = 0; c < COUTG; c += 4)
-                        o4[c / 4] = make_float4(acc[c] + sBias[c], acc[c + 1] + sBias[c + 1],
-                                                acc[c + 2] + sBias[c + 2], acc[c + 3] + sBias[c + 3]);
+                        o4[c / 4] = make_float4(acc[c] + bz[c], acc[c + 1] + bz[c + 1],
+                                                acc[c + 2] + bz[c + 2], acc[c + 3] + bz[c + 3]);
                 } else {   // EPI_Z: z = D^-1 v + s y  (B = 1)
-                    const int64_t HW = (int64_t)a.H * a.W, q = (int64_t)yy * a.W + xx;
-                    const double v0 = __ldcg(a.v + q), v1 = __ldcg(a.v + HW + q), v2 = __ldcg(a.v + 2 * HW + q);
-                    const double *o = a.jd + q * 9;
+                    const int64_t HW = (int64_t)H * W, q = (int64_t)yy * W + xx;
+                    const float v0 = (float)__ldcg(vz + q), v1 = (float)__ldcg(vz + HW + q),
+                                v2 = (float)__ldcg(vz + 2 * HW + q);
+                    const float *o = jd + q * 9, s = (float)s_out;
 #pragma unroll
                     for (int c = 0; c < 3; ++c)
-                        a.z[c * HW + q] = o[3 * c] * v0 + o[3 * c + 1] * v1 + o[3 * c + 2] * v2 +
-                                          a.s * (double)(acc[c] + sBias[c]);
+                        z[c * HW + q] =
+                            (double)fmaf(s, acc[c] + bz[c], o[3 * c] * v0 + o[3 * c + 1] * v1 + o[3 * c + 2] * v2);
                 }
             }
             // this set's output blocks are read and cleared: hand it back to the MMA thread
@@ -344,7 +359,7 @@ __device__ void conv_tc(const Args &a, const bf16 *in, unsigned char *sm, int ct
             mbar_wait(&full[j % kStages], (j / kStages) & 1, kWaitLimit);
             if (j < nissued) mbar_wait(&empty[j % kStages], (j / kStages) & 1, kWaitLimit);
         }
-        if (*abort && a.err) atomicExch(a.err, 1);
+        if (*abort && err) atomicExch(err, 1);
     }
     __syncthreads();
     if (warp == 0) {

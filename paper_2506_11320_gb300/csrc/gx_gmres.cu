@@ -64,6 +64,7 @@ struct CoArgs {
     double *Z;          // preconditioned vectors [m][3N] (== V without a preconditioner)
     double *w, *r;      // [3N]
     const double *jd;   // block-Jacobi inverse [N][9], or null
+    const float *jd32;  // the same in FP32 (the learned preconditioner's base)
     GmState *st;
     double *part;       // [2][kMaxGrid][kPartStride] CTA partial sums
     int64_t N;
@@ -72,6 +73,7 @@ struct CoArgs {
     int net;            // apply the learned preconditioner (the fields below)
     NetSolverArgs nn;
     double ns;          // its scale s = 1 / sqrt(3 N) (the Krylov columns have unit norm)
+    float inv_ns;       // 1 / s
     int *err;           // set when a bounded wait of the network's tensor-core steps gives up
 };
 
@@ -137,9 +139,9 @@ __device__ __forceinline__ void jacobi_node(const double *jd, const double *v, d
 // halo-ring image x0 (periodic copies included); written by the thread that
 // computes V_j at q, so the layer-1 tiles see it after the next grid barrier
 __device__ __forceinline__ void net_pack_node(const CoArgs &a, int64_t q, double v0, double v1, double v2) {
-    const double inv = 1.0 / a.ns;
-    const __nv_bfloat162 p01 = __floats2bfloat162_rn((float)(v0 * inv), (float)(v1 * inv));
-    const __nv_bfloat162 p2 = __floats2bfloat162_rn((float)(v2 * inv), 0.f);
+    const float inv = a.inv_ns;
+    const __nv_bfloat162 p01 = __floats2bfloat162_rn((float)v0 * inv, (float)v1 * inv);
+    const __nv_bfloat162 p2 = __floats2bfloat162_rn((float)v2 * inv, 0.f);
     const uint4 val[2] = {make_uint4(*reinterpret_cast<const uint32_t *>(&p01), *reinterpret_cast<const uint32_t *>(&p2),
                                      0, 0),
                           make_uint4(0, 0, 0, 0)};
@@ -180,7 +182,7 @@ __device__ void net_apply(const CoArgs &a, cg::grid_group &grid, int j, unsigned
     c.bias = a.nn.b[3];
     c.out = nullptr;
     c.v = a.V + (size_t)j * n;
-    c.jd = a.jd;
+    c.jd = a.jd32;
     c.z = a.Z + (size_t)j * n;
     c.s = a.ns;
     conv_tc<32, 16, 8, kNetRows, EPI_Z>(c, static_cast<const bf16 *>(a.nn.h3), sm, blockIdx.x, gridDim.x);
@@ -504,6 +506,7 @@ int gx_fgmres(gx_ctx *c, cudaStream_t st) {
     a.w = c->w;
     a.r = c->r;
     a.jd = pc == GX_PRECOND_NONE ? nullptr : c->jdiag;
+    a.jd32 = c->jdiag32;
     a.st = c->gm;
     a.part = c->gpart;
     a.N = c->N;
@@ -514,6 +517,7 @@ int gx_fgmres(gx_ctx *c, cudaStream_t st) {
     if (use_net) {
         if ((rc = gx_net_solver_args(c, &a.nn, st))) return rc;
         a.ns = 1.0 / std::sqrt(3.0 * (double)c->N);
+        a.inv_ns = (float)std::sqrt(3.0 * (double)c->N);
         a.err = &c->dflags->timeout;
     }
     if (gx_net_collecting(c)) {

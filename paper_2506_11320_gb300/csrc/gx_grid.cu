@@ -287,8 +287,9 @@ __global__ void k_matvec(OpArgs a, const double *__restrict__ x, double *__restr
     }
 }
 
-// 3x3 diagonal block of A at every node, inverted (block-Jacobi preconditioner).
-__global__ void k_jacobi(OpArgs a, double *jd) {
+// 3x3 diagonal block of A at every node, inverted (block-Jacobi preconditioner),
+// in FP64 and in FP32
+__global__ void k_jacobi(OpArgs a, double *jd, float *jd32) {
     const G2 &g = a.g;
     const int64_t N = g.N();
     GRID_LOOP(q, N) {
@@ -319,6 +320,11 @@ __global__ void k_jacobi(OpArgs a, double *jd) {
         o[0] = c00 * id; o[1] = (A[2] * A[7] - A[1] * A[8]) * id; o[2] = (A[1] * A[5] - A[2] * A[4]) * id;
         o[3] = c01 * id; o[4] = (A[0] * A[8] - A[2] * A[6]) * id; o[5] = (A[2] * A[3] - A[0] * A[5]) * id;
         o[6] = c02 * id; o[7] = (A[1] * A[6] - A[0] * A[7]) * id; o[8] = (A[0] * A[4] - A[1] * A[3]) * id;
+        if (jd32) {
+            float *o32 = jd32 + (size_t)q * 9;
+#pragma unroll
+            for (int e = 0; e < 9; ++e) o32[e] = (float)o[e];
+        }
     }
 }
 
@@ -645,7 +651,7 @@ int gx_apply_A_j(gx_ctx *c, const double *base, int64_t stride, const int *jptr,
 }
 
 int gx_build_jacobi(gx_ctx *c, cudaStream_t st) {
-    k_jacobi<<<blocks_for(c->N), kB, 0, st>>>(opargs(c), c->jdiag);
+    k_jacobi<<<blocks_for(c->N), kB, 0, st>>>(opargs(c), c->jdiag, c->jdiag32);
     GX_LAUNCHED(c);
     return GX_OK;
 }

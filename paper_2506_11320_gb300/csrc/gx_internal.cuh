@@ -125,6 +125,7 @@ struct gx_ctx {
     double *kappa = nullptr;                    // [dim][3][N] LF-E coefficients
     double *rhs = nullptr, *EM = nullptr;       // [3][N]
     double *jdiag = nullptr;                    // [N][9] inverse 3x3 block diagonal
+    float *jdiag32 = nullptr;                   // the same in FP32 (applied with the learned correction)
     double *V = nullptr, *Z = nullptr;          // Krylov bases [(m+1)][3N], [m][3N]
     double *w = nullptr, *r = nullptr;          // [3N]
     double *dred = nullptr;                     // reduction scratch

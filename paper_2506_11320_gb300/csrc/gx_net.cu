@@ -788,7 +788,7 @@ int gx_precond_apply(gx_ctx *c, const double *v, double *z, void *stream) {
     a.bias = nn.b[3];
     a.out = nullptr;
     a.v = v;
-    a.jd = c->jdiag;
+    a.jd = c->jdiag32;
     a.z = z;
     a.s = s;
     if ((rc = launch_conv<32, 16, 8, EPI_Z>(c, static_cast<const bf16 *>(nn.h3), a, st))) return rc;
