@@ -26,7 +26,7 @@
 // solve is one launch with every preconditioner.
 #include <cooperative_groups.h>
 
-#include "gx_convtc.cuh"
+#include "gx_netpipe.cuh"
 #include "gx_op.cuh"
 
 namespace cg = cooperative_groups;
@@ -77,10 +77,8 @@ struct CoArgs {
     int *err;           // set when a bounded wait of the network's tensor-core steps gives up
 };
 
-// in-kernel network: image rows per convolution unit, shared memory of the
-// largest layer (+ alignment slack)
-constexpr int kNetRows = 4;
-constexpr int kNetSmemBytes = gxv::smem_bytes<32, 32, kNetRows>() + 128;
+// in-kernel network: shared memory of the pipeline (+ alignment slack)
+constexpr int kNetSmemBytes = gxn::kSmemBytes + 128;
 static_assert(kBNet % gxv::kThreads == 0 && kBNet / gxv::kThreads <= 2, "the convolution's role groups");
 
 // every thread's node set: q = tid, tid + nthreads, ...
@@ -150,42 +148,36 @@ __device__ __forceinline__ void net_pack_node(const CoArgs &a, int64_t q, double
 }
 
 // Z_j = D^-1 V_j + s N(V_j / s), every CTA of the cooperative grid taking part:
-// four tensor-core convolutions (gx_convtc.cuh) with a grid barrier before
-// each layer (a layer reads its neighbours' inputs); the first reads the
-// packed V_j, the last writes Z_j itself (the caller's barrier follows)
+// the four layers as one persistent tensor-core pipeline (gx_netpipe.cuh),
+// after a grid barrier that completes the packed input V_j / s and the
+// clearing of the pipeline's completion flags; the last layer writes Z_j
+// itself (the caller's barrier follows)
 __device__ void net_apply(const CoArgs &a, cg::grid_group &grid, int j, unsigned char *sm) {
-    using namespace gxv;
     const int64_t n = 3 * a.N;
-    Args c{};
-    c.err = a.err;
-    c.B = 1;
-    c.H = a.op.g.ny;
-    c.W = a.op.g.nx;
-    c.periodic = 1;
+    const int H = a.op.g.ny, W = a.op.g.nx;
+    gxn::pipe_clear_flags(a.nn.flags, H, W, blockIdx.x, gridDim.x);
     grid.sync();
-    c.wtc = static_cast<const bf16 *>(a.nn.w[0]);
-    c.bias = a.nn.b[0];
-    c.out = a.nn.h1;
-    conv_tc<16, 32, 32, kNetRows, EPI_RELU>(c, static_cast<const bf16 *>(a.nn.x0), sm, blockIdx.x, gridDim.x);
-    grid.sync();
-    c.wtc = static_cast<const bf16 *>(a.nn.w[1]);
-    c.bias = a.nn.b[1];
-    c.out = a.nn.h2;
-    conv_tc<32, 32, 32, kNetRows, EPI_RELU>(c, static_cast<const bf16 *>(a.nn.h1), sm, blockIdx.x, gridDim.x);
-    grid.sync();
-    c.wtc = static_cast<const bf16 *>(a.nn.w[2]);
-    c.bias = a.nn.b[2];
-    c.out = a.nn.h3;
-    conv_tc<32, 32, 32, kNetRows, EPI_RELU>(c, static_cast<const bf16 *>(a.nn.h2), sm, blockIdx.x, gridDim.x);
-    grid.sync();
-    c.wtc = static_cast<const bf16 *>(a.nn.w[3]);
-    c.bias = a.nn.b[3];
-    c.out = nullptr;
-    c.v = a.V + (size_t)j * n;
-    c.jd = a.jd32;
-    c.z = a.Z + (size_t)j * n;
-    c.s = a.ns;
-    conv_tc<32, 16, 8, kNetRows, EPI_Z>(c, static_cast<const bf16 *>(a.nn.h3), sm, blockIdx.x, gridDim.x);
+    gxn::PipeArgs p;
+    p.in[0] = static_cast<const gxv::bf16 *>(a.nn.x0);
+    p.in[1] = static_cast<const gxv::bf16 *>(a.nn.h1);
+    p.in[2] = static_cast<const gxv::bf16 *>(a.nn.h2);
+    p.in[3] = static_cast<const gxv::bf16 *>(a.nn.h3);
+    p.out[0] = static_cast<gxv::bf16 *>(a.nn.h1);
+    p.out[1] = static_cast<gxv::bf16 *>(a.nn.h2);
+    p.out[2] = static_cast<gxv::bf16 *>(a.nn.h3);
+    for (int l = 0; l < 4; ++l) {
+        p.w[l] = static_cast<const gxv::bf16 *>(a.nn.w[l]);
+        p.bias[l] = a.nn.b[l];
+    }
+    p.v = a.V + (size_t)j * n;
+    p.jd = a.jd32;
+    p.z = a.Z + (size_t)j * n;
+    p.s = (float)a.ns;
+    p.flags = a.nn.flags;
+    p.err = a.err;
+    p.H = H;
+    p.W = W;
+    gxn::net_pipeline(p, sm, blockIdx.x, gridDim.x);
 }
 
 // NET: the learned preconditioner is applied in the kernel (the plain and

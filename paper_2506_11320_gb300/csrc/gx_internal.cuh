@@ -222,6 +222,7 @@ struct NetSolverArgs {
     const void *w[4];       // weights in the tensor-core operand layout
     const float *b[4];
     void *x0, *h1, *h2, *h3; // layer inputs: channel-blocked images with a halo ring
+    unsigned *flags;        // per-unit completion flags of the network pipeline
 };
 int gx_net_solver_args(gx_ctx *c, NetSolverArgs *out, cudaStream_t st);
 int gx_net_collecting(const gx_ctx *c);

@@ -24,7 +24,7 @@
 //     FP32 global sums once per CTA.
 //   * Adam on an FP32 master copy; BF16 copies refreshed after each update.
 // Channel counts are padded for the MMA shapes: 3 input channels -> 16,
-// 3 output channels -> 8 (stored forward output; 16 in the MMA) or 16
+// 3 output channels -> 8 (stored forward output; 32 in the MMA) or 16
 // (gradient).  BF16 activations are channel-blocked images with a one-pixel
 // halo ring, [B][C/8][H+2][W+2][8].
 #include <cuda_bf16.h>
@@ -34,6 +34,9 @@
 
 #include "gx_conv.cuh"
 #include "gx_convtc.cuh"
+#include "gx_netpipe.cuh"
+
+#include <cooperative_groups.h>
 
 using namespace gxc;
 
@@ -44,7 +47,7 @@ constexpr int kCin[kNL] = {3, 32, 32, 32};
 constexpr int kCout[kNL] = {32, 32, 32, 3};
 constexpr int kCinP[kNL] = {16, 32, 32, 32};    // padded input channels (storage of the layer input)
 constexpr int kCoutP[kNL] = {32, 32, 32, 8};    // padded output channels (forward storage)
-constexpr int kNmma[kNL] = {32, 32, 32, 16};    // output channels of the forward MMA (N)
+constexpr int kNmma[kNL] = {32, 32, 32, 32};    // output channels of the forward MMA (one row block)
 constexpr int kGCoutP[kNL] = {32, 32, 32, 16};  // padded output channels of the gradient (dY) storage
 
 constexpr int64_t layer_w_count(int l) { return (int64_t)kCout[l] * kCin[l] * 9; }
@@ -58,6 +61,27 @@ inline int64_t param_count() { return param_offset(kNL); }
 // the forward/data-gradient convolution as a kernel (a persistent grid of
 // tensor-core CTAs, gx_convtc.cuh); R image rows per unit of work
 constexpr int kConvRows = 4;
+
+// the solver's application of the network to one vector, as one cooperative
+// kernel running the same pipeline as the solver: pack v / s into the layer-0
+// image, clear the completion flags, grid barrier, four layers
+__global__ void __launch_bounds__(2 * gxv::kThreads, 1) k_net_apply(gxn::PipeArgs p, gxv::bf16 *x0, float inv_s) {
+    extern __shared__ __align__(128) unsigned char dsm[];
+    unsigned char *sm = dsm + ((128 - (gxt::smem_addr(dsm) & 127)) & 127);
+    cooperative_groups::grid_group grid = cooperative_groups::this_grid();
+    const int64_t HW = (int64_t)p.H * p.W;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < HW; q += (int64_t)gridDim.x * blockDim.x) {
+        const __nv_bfloat162 p01 = __floats2bfloat162_rn((float)p.v[q] * inv_s, (float)p.v[HW + q] * inv_s);
+        const __nv_bfloat162 p2 = __floats2bfloat162_rn((float)p.v[2 * HW + q] * inv_s, 0.f);
+        const uint4 val[2] = {make_uint4(*reinterpret_cast<const uint32_t *>(&p01),
+                                         *reinterpret_cast<const uint32_t *>(&p2), 0, 0),
+                              make_uint4(0, 0, 0, 0)};
+        gxv::store_with_halo<16>(x0, 0, (int)(q / p.W), (int)(q % p.W), p.H, p.W, 1, val);
+    }
+    gxn::pipe_clear_flags(p.flags, p.H, p.W, blockIdx.x, gridDim.x);
+    grid.sync();
+    gxn::net_pipeline(p, sm, blockIdx.x, gridDim.x);
+}
 
 template <int CIN, int N, int COUTG, int EPI>
 __global__ void __launch_bounds__(2 * gxv::kThreads) k_convtc(const gxv::bf16 *in, gxv::Args a, const int *skip) {
@@ -358,6 +382,8 @@ struct Net {
     bf16 *d4 = nullptr, *d3 = nullptr, *d2 = nullptr, *d1 = nullptr;
     float *y = nullptr, *target = nullptr;
     double *dsum = nullptr;    // [0] sum of squares, [1] loss
+    unsigned *flags = nullptr; // completion flags of the network pipeline [3][units]
+    int cap_flags = 0;
     // collected pairs: [cap][2][3][N] FP32 (r0, e)
     float *pairs = nullptr;
     int cap_pairs = 0, npairs = 0, next_pair = 0, collect = 0;
@@ -488,7 +514,7 @@ static int net_forward(gx_ctx *c, int B, int H, int W, int periodic, cudaStream_
         return rc;
     if ((rc = conv<32, 32, 32, EPI_RELU>(c, n->h2, n->wf[2], n->bias[2], n->h3, nullptr, B, H, W, periodic, st, skip)))
         return rc;
-    return conv<32, 16, 8, gxv::EPI_F32>(c, n->h3, n->wf[3], n->bias[3], n->y, nullptr, B, H, W, periodic, st, skip);
+    return conv<32, 32, 8, gxv::EPI_F32>(c, n->h3, n->wf[3], n->bias[3], n->y, nullptr, B, H, W, periodic, st, skip);
 }
 
 // backward from dY4 (in n->d4): weight gradients (FP32 sums, zeroed here) and
@@ -531,6 +557,14 @@ int gx_net_solver_args(gx_ctx *c, NetSolverArgs *out, cudaStream_t st) {
     if ((rc = net_reserve(c, 1, H, W))) return rc;
     for (int l = 0; l < kNL; ++l) { out->w[l] = n->wf[l]; out->b[l] = n->bias[l]; }
     out->x0 = n->x0; out->h1 = n->h1; out->h2 = n->h2; out->h3 = n->h3;
+    const int nflags = 3 * gxn::pipe_units(H, W);
+    if (nflags > n->cap_flags) {
+        if (n->flags) cudaFree(n->flags);
+        n->flags = nullptr;
+        GX_CHECK(c, cudaMalloc(&n->flags, (size_t)nflags * sizeof(unsigned)));
+        n->cap_flags = nflags;
+    }
+    out->flags = n->flags;
     return GX_OK;
 }
 
@@ -592,7 +626,7 @@ void gx_net_free(gx_ctx *c) {
     Net *n = c->net;
     if (!n) return;
     void *ps[] = {n->params, n->grad, n->m1, n->m2, n->x0, n->h1, n->h2, n->h3, n->d4, n->d3, n->d2, n->d1, n->y,
-                  n->target, n->dsum, n->pairs};
+                  n->target, n->dsum, n->pairs, n->flags};
     for (void *p : ps)
         if (p) cudaFree(p);
     for (int l = 0; l < kNL; ++l) {
@@ -764,34 +798,43 @@ int gx_precond_apply(gx_ctx *c, const double *v, double *z, void *stream) {
     }
     const double s = vn / std::sqrt(3.0 * (double)N);
     const int H = c->n[1], W = c->n[0];
-    k_pack_input<double><<<nblk(N), 256, 0, st>>>(v, H, W, 1.0 / s, 1, static_cast<bf16 *>(nn.x0));
+    gxn::PipeArgs p;
+    p.in[0] = static_cast<const bf16 *>(nn.x0);
+    p.in[1] = static_cast<const bf16 *>(nn.h1);
+    p.in[2] = static_cast<const bf16 *>(nn.h2);
+    p.in[3] = static_cast<const bf16 *>(nn.h3);
+    p.out[0] = static_cast<bf16 *>(nn.h1);
+    p.out[1] = static_cast<bf16 *>(nn.h2);
+    p.out[2] = static_cast<bf16 *>(nn.h3);
+    for (int l = 0; l < kNL; ++l) {
+        p.w[l] = static_cast<const bf16 *>(nn.w[l]);
+        p.bias[l] = nn.b[l];
+    }
+    p.v = v;
+    p.jd = c->jdiag32;
+    p.z = z;
+    p.s = (float)s;
+    p.flags = nn.flags;
+    p.err = &c->dflags->timeout;
+    p.H = H;
+    p.W = W;
+    constexpr int smem = gxn::kSmemBytes + 128;
+    static int grid = 0;
+    if (!grid) {
+        int dev = 0, nsm = 0, per = 0;
+        GX_CHECK(c, cudaGetDevice(&dev));
+        GX_CHECK(c, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        GX_CHECK(c, cudaFuncSetAttribute((const void *)k_net_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        GX_CHECK(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, (const void *)k_net_apply, 2 * gxv::kThreads,
+                                                                  smem));
+        grid = std::max(1, std::min(per, 1) * nsm);   // one CTA per SM: its tensor memory
+    }
+    bf16 *x0 = static_cast<bf16 *>(nn.x0);
+    float inv_s = (float)(1.0 / s);
+    void *kargs[] = {&p, &x0, &inv_s};
+    GX_CHECK(c, cudaLaunchCooperativeKernel((const void *)k_net_apply, dim3(grid), dim3(2 * gxv::kThreads), kargs, smem,
+                                            st));
     GX_LAUNCHED(c);
-    using namespace gxv;
-    Args a{};
-    a.B = 1;
-    a.H = H;
-    a.W = W;
-    a.periodic = 1;
-    a.wtc = static_cast<const bf16 *>(nn.w[0]);
-    a.bias = nn.b[0];
-    a.out = nn.h1;
-    if ((rc = launch_conv<16, 32, 32, EPI_RELU>(c, static_cast<const bf16 *>(nn.x0), a, st))) return rc;
-    a.wtc = static_cast<const bf16 *>(nn.w[1]);
-    a.bias = nn.b[1];
-    a.out = nn.h2;
-    if ((rc = launch_conv<32, 32, 32, EPI_RELU>(c, static_cast<const bf16 *>(nn.h1), a, st))) return rc;
-    a.wtc = static_cast<const bf16 *>(nn.w[2]);
-    a.bias = nn.b[2];
-    a.out = nn.h3;
-    if ((rc = launch_conv<32, 32, 32, EPI_RELU>(c, static_cast<const bf16 *>(nn.h2), a, st))) return rc;
-    a.wtc = static_cast<const bf16 *>(nn.w[3]);
-    a.bias = nn.b[3];
-    a.out = nullptr;
-    a.v = v;
-    a.jd = c->jdiag32;
-    a.z = z;
-    a.s = s;
-    if ((rc = launch_conv<32, 16, 8, EPI_Z>(c, static_cast<const bf16 *>(nn.h3), a, st))) return rc;
     GX_CHECK(c, cudaStreamSynchronize(st));
     return GX_OK;
 }
