@@ -11,8 +11,9 @@
 // cta, cta + ncta, ...  A tile of layer l >= 1 needs the layer l-1 outputs of
 // its unit and of the 8 units around it (rows and columns wrap: periodic
 // field), so before copying it the producer waits for their completion flags
-// (ld.acquire, bounded); the epilogue publishes a unit's flag (st.release)
-// after all its stores are fenced.  Waits only point to earlier layers, and
+// (ld.acquire, bounded); once a named barrier has ordered the epilogue's
+// stores of a unit, a publisher warp fences them and releases the unit's flag
+// (st.release), off the epilogue's path.  Waits only point to earlier layers, and
 // every item of an earlier layer completes without outside help once it is
 // loaded, so the walk cannot deadlock; all waits are bounded anyway, and an
 // expired wait aborts the CTA's pipeline (the error flag is set, copies and
@@ -90,12 +91,47 @@ __device__ __forceinline__ void pipe_clear_flags(unsigned *flags, int H, int W, 
         for (int l = 0; l < kLayers - 1; ++l) flags[l * nunits + u] = 0;
 }
 
+// one unit's MMAs of a layer with CIN input channels (fully unrolled: the
+// tensor core then sees them back to back)
+template <int CIN>
+__device__ __forceinline__ void issue_unit(uint32_t dacc, uint64_t ad, uint64_t bd) {
+    constexpr uint32_t idesc = gxt::idesc_bf16_f32(kTW, 3 * kNB);
+    constexpr uint32_t kWSlab16 = 3 * kNB;                 // one 8-channel slab of W_kx, in 16-byte units
+#pragma unroll
+    for (int rho = 0; rho < kR + 2; ++rho)
+#pragma unroll
+        for (int kx = 0; kx < 3; ++kx)
+#pragma unroll
+            for (int kc = 0; kc < CIN / 16; ++kc)
+                gxt::mma_bf16(dacc + rho * kNB, ad + (uint32_t)(rho * kTileRow + kx + 2 * kc * (kSlabBytes / 16)),
+                              bd + (uint32_t)((kx * (CIN / 8) + 2 * kc) * kWSlab16), idesc, true);
+}
+
+// unit of item t: layer l walks the CTA's units cta + i ncta for i = l, l + 1,
+// ..., nmine - 1, 0, ..., l - 1.  On the periodic field any walk has a seam
+// where its first units neighbour its last ones; starting each layer one unit
+// further on puts the units that neighbour the previous layer's late units at
+// the end of the layer, so a layer's first units depend only on units the
+// previous layer finished early
+__device__ __forceinline__ int item_unit(int t, int nmine, int cta, int ncta) {
+    const int l = t / nmine, i = (t % nmine + l) % nmine;
+    return cta + i * ncta;
+}
+
 // the four layers over this CTA's units (every thread of the CTA calls it;
-// blockDim.x == 256 or 512; sm: kSmemBytes bytes, 128-byte aligned)
+// blockDim.x == 512: two epilogue groups of four warps, two rows each; sm:
+// kSmemBytes bytes, 128-byte aligned)
 static __device__ void net_pipeline(const PipeArgs &args, unsigned char *sm, int cta, int ncta) {
     using namespace gxt;
+    // register copies of the arguments (the inline assembly clobbers memory)
     const int H = args.H, W = args.W;
     unsigned *const flags = args.flags;
+    bf16 *const out0 = args.out[0], *const out1 = args.out[1], *const out2 = args.out[2];
+    const bf16 *const in0 = args.in[0], *const in1 = args.in[1], *const in2 = args.in[2], *const in3 = args.in[3];
+    const double *const vin = args.v;
+    const float *const jd = args.jd;
+    double *const zout = args.z;
+    const float s_out = args.s;
     float *sBias = reinterpret_cast<float *>(sm + kBiasOff);
     uint64_t *bars = reinterpret_cast<uint64_t *>(sm + kBarOff);
     uint64_t *wfull = bars, *full = bars + 1, *empty = bars + 1 + kStagesP, *accfull = bars + 1 + 2 * kStagesP,
@@ -108,6 +144,10 @@ static __device__ void net_pipeline(const PipeArgs &args, unsigned char *sm, int
 
     const int nseg = (W + kTW - 1) / kTW, nblk = (H + kR - 1) / kR, nunits = nblk * nseg;
     if (cta >= nunits) return;
+    if (ngroups != 2) {    // launch-configuration error: report it, touch nothing
+        if (tid == 0 && args.err) atomicExch(args.err, 1);
+        return;
+    }
     const int nmine = (nunits - 1 - cta) / ncta + 1;
     const int nitems = kLayers * nmine;     // item t: layer t / nmine, unit cta + (t % nmine) ncta
 
@@ -137,7 +177,7 @@ static __device__ void net_pipeline(const PipeArgs &args, unsigned char *sm, int
         }
         int t = 0;
         for (; t < nitems; ++t) {
-            const int l = t / nmine, u = cta + (t % nmine) * ncta;
+            const int l = t / nmine, u = item_unit(t, nmine, cta, ncta);
             const int st = t % kStagesP, n = t / kStagesP, cin = layer_cin(l);
             int b, y0, x0;
             unit_pos<kR>(u, nseg, nblk, b, y0, x0);
@@ -169,14 +209,14 @@ static __device__ void net_pipeline(const PipeArgs &args, unsigned char *sm, int
                 const int r = lane % (kR + 2), g = lane / (kR + 2);
                 if (r < rows)
                     bulk_load(smem_addr(sm + kTileOff + st * kTileBytes + g * kSlabBytes + r * kTileRow * 16),
-                              args.in[l] + blk_off(b, g, y0 - 1 + r, x0 - 1, H, W, cin / 8), npx * 16, &full[st]);
+                              (l == 0 ? in0 : l == 1 ? in1 : l == 2 ? in2 : in3) + blk_off(b, g, y0 - 1 + r, x0 - 1, H, W, cin / 8),
+                              npx * 16, &full[st]);
             }
         }
         nloaded = t;
     } else if (warp == 1) {
         if (lane == 0) {
             // ---- MMA issuer
-            constexpr uint32_t idesc = idesc_bf16_f32(kTW, 3 * kNB);
             constexpr uint32_t kWSlab = 3 * kNB * 16;          // bytes of one 8-channel slab of W_kx
             bool ok = mbar_wait_or_abort(wfull, 0, kWaitLimit, abort);
             int t = 0;
@@ -187,20 +227,30 @@ static __device__ void net_pipeline(const PipeArgs &args, unsigned char *sm, int
                 tc_fence_after();
                 const uint64_t ad = sdesc(smem_addr(sm + kTileOff + st * kTileBytes), kSlabBytes, 128);
                 const uint64_t bd = sdesc(smem_addr(sm + woff(l)), kWSlab, 128);
-                const uint32_t dacc = tm + k * kAccCols;
-                const int kcs = layer_cin(l) / 16, cg8 = layer_cin(l) / 8;
-#pragma unroll 1
-                for (int rho = 0; rho < kR + 2; ++rho)
-#pragma unroll
-                    for (int kx = 0; kx < 3; ++kx)
-#pragma unroll 1
-                        for (int kc = 0; kc < kcs; ++kc)
-                            mma_bf16(dacc + rho * kNB, ad + (uint32_t)(rho * kTileRow + kx + 2 * kc * (kSlabBytes / 16)),
-                                     bd + (uint32_t)((kx * cg8 + 2 * kc) * (kWSlab / 16)), idesc, true);
+                if (l == 0)
+                    issue_unit<16>(tm + k * kAccCols, ad, bd);
+                else
+                    issue_unit<32>(tm + k * kAccCols, ad, bd);
                 mma_commit(&empty[st]);
                 mma_commit(&accfull[k]);
             }
             *s_issued = t;
+        }
+    } else if (warp == 2) {
+        // ---- publisher: once the epilogue has stored a unit of layers 0..2 (named
+        // barrier: their stores are ordered before it), one gpu-scope fence and a
+        // release store of the unit's completion flag
+        const int nepi = 4 * 32 * ngroups;
+        for (int t = 0; t < nitems; ++t) {
+            const int l = t / nmine;
+            if (l >= kLayers - 1) break;
+            named_sync(1, nepi + 32);
+            if (lane == 0 && !*abort) {
+                __threadfence();
+                fence_proxy_async_global();
+                st_release(flags + l * nunits + item_unit(t, nmine, cta, ncta), 1u);
+            }
+            __syncwarp();
         }
     } else if ((warp & 7) >= 4) {
         // ---- epilogue: groups of four warps (TMEM lane quarters), alternate rows
@@ -218,7 +268,7 @@ static __device__ void net_pipeline(const PipeArgs &args, unsigned char *sm, int
         float bz[kNB];
         int lcur = -1;
         for (int t = 0; t < nitems; ++t) {
-            const int l = t / nmine, u = cta + (t % nmine) * ncta, k = t & 1, m = t >> 1;
+            const int l = t / nmine, u = item_unit(t, nmine, cta, ncta), k = t & 1, m = t >> 1;
             if (l != lcur) {
 #pragma unroll
                 for (int c = 0; c < kNB; ++c) bz[c] = sBias[l * kNB + c];
@@ -234,7 +284,7 @@ static __device__ void net_pipeline(const PipeArgs &args, unsigned char *sm, int
                 unit_pos<kR>(u, nseg, nblk, b, y0, x0);
                 const int xx = x0 + 32 * q4 + lane;
 #pragma unroll 1
-                for (int r = group; r < kR; r += ngroups) {
+                for (int r = group; r < kR; r += 2) {
                     const int yy = y0 + r;
                     const uint32_t blk = lane_base + k * kAccCols + (r + 2) * kNB;
                     float acc[kNB];
@@ -252,31 +302,26 @@ static __device__ void net_pipeline(const PipeArgs &args, unsigned char *sm, int
                                                                            fmaxf(acc[c + 1] + bz[c + 1], 0.f));
                             pw[c / 2] = *reinterpret_cast<const uint32_t *>(&o);
                         }
-                        store_with_halo<kNB>(args.out[l], 0, yy, xx, H, W, 1, packed);
+                        store_with_halo<kNB>(l == 0 ? out0 : (l == 1 ? out1 : out2), 0, yy, xx, H, W, 1, packed);
                     } else {   // z = D^-1 v + s y
                         const int64_t HW = (int64_t)H * W, q = (int64_t)yy * W + xx;
-                        const float v0 = (float)__ldcg(args.v + q), v1 = (float)__ldcg(args.v + HW + q),
-                                    v2 = (float)__ldcg(args.v + 2 * HW + q);
-                        const float *o = args.jd + q * 9;
+                        const float v0 = (float)__ldcg(vin + q), v1 = (float)__ldcg(vin + HW + q),
+                                    v2 = (float)__ldcg(vin + 2 * HW + q);
+                        const float *o = jd + q * 9;
 #pragma unroll
                         for (int c = 0; c < 3; ++c)
-                            args.z[c * HW + q] = (double)fmaf(args.s, acc[c] + bz[c],
-                                                              o[3 * c] * v0 + o[3 * c + 1] * v1 + o[3 * c + 2] * v2);
+                            zout[c * HW + q] = (double)fmaf(s_out, acc[c] + bz[c],
+                                                            o[3 * c] * v0 + o[3 * c + 1] * v1 + o[3 * c + 2] * v2);
                     }
                 }
                 tmem_wait_st();
                 tc_fence_before();
                 mbar_arrive(&accempty[k]);
             }
-            if (l < kLayers - 1) {
-                // publish the unit (all epilogue threads take part, also after an abort)
-                __threadfence();
-                named_sync(1, nepi);
-                if (warp == 4 && lane == 0 && !*abort) {
-                    fence_proxy_async_global();
-                    st_release(flags + l * nunits + u, 1u);
-                }
-            }
+            // hand the unit to the publisher (warp 2), which then fences and releases
+            // it while the epilogue goes on (both sides synchronise at every item,
+            // also after an abort, so the barrier's phases never mix)
+            if (l < kLayers - 1) named_sync(1, nepi + 32);
         }
     }
     __syncthreads();
