@@ -50,7 +50,8 @@ class Cfg(C.Structure):
         ("nsmooth_u", C.c_int32),
         ("gmres_restart", C.c_int32),
         ("gmres_maxit", C.c_int32),
-        ("_pad", C.c_int32 * 2),
+        ("divb_clean", C.c_int32),
+        ("_pad", C.c_int32),
         ("dx", C.c_double * 3),
         ("c", C.c_double),
         ("theta", C.c_double),
@@ -69,7 +70,7 @@ class Cfg(C.Structure):
 
 
 def make_cfg(n, dx, *, c=1.0, theta=0.5, dt=0.02, comoving=0, lf_on=0, lf_speed_c=0, lf_beta=1.0,
-             ns_j=0, nsmooth_u=5, gmres_tol=1e-12, gmres_restart=50, gmres_maxit=5000) -> Cfg:
+             ns_j=0, nsmooth_u=5, gmres_tol=1e-12, gmres_restart=50, gmres_maxit=5000, divb_clean=0) -> Cfg:
     n = list(n) + [1] * (3 - len(n))
     dx = list(dx) + [1.0] * (3 - len(dx))
     cfg = Cfg()
@@ -80,6 +81,7 @@ def make_cfg(n, dx, *, c=1.0, theta=0.5, dt=0.02, comoving=0, lf_on=0, lf_speed_
     cfg.comoving, cfg.lf_on, cfg.lf_speed_c = int(comoving), int(lf_on), int(lf_speed_c)
     cfg.lf_beta, cfg.ns_j, cfg.nsmooth_u = float(lf_beta), int(ns_j), int(nsmooth_u)
     cfg.gmres_tol, cfg.gmres_restart, cfg.gmres_maxit = float(gmres_tol), int(gmres_restart), int(gmres_maxit)
+    cfg.divb_clean = int(divb_clean)
     return cfg
 
 
@@ -110,8 +112,9 @@ _SIGS = {
     "or_advance_fields": (None, [_P, _D, _D, _D, _D, _D, _D]),
     "or_mover": (C.c_double, [_P, _D, _D, C.c_int64, _I32, _D, _D, _D, _D, _D, _D, _D, _D, _D]),
     "or_energy": (None, [_P, _D, C.c_int64, _I32, _D, _D, _D, _D, _D, _D, _D]),
-    "or_step": (C.c_int, [_P, _D, _D, C.c_int64, _I32, _D, _D, _D, _D, _D, _D, _D, _D, _D,
+    "or_step": (C.c_int, [_P, _D, _D, C.c_int64, _I32, _D, _D, _D, _D, _D, _D, _D, _D, _D, _D,
                           _D, _D, _D, _D, _D, _D]),
+    "or_divb_clean": (None, [_P, _D, _D]),
     "or_net_param_count": (C.c_int64, []),
     "or_net_act_count": (C.c_int64, [C.c_int, C.c_int]),
     "or_net_forward": (None, [C.c_int, C.c_int, C.c_int, _D, _D, _D, _D]),
@@ -323,9 +326,18 @@ def energy(cfg, pl: Plasma, E, Bc):
             "total": out[0] + out[1] + out[2]}
 
 
-def step(cfg, pl: Plasma, E, B, want=()):
-    """One full step, in place on pl, E and B (float64 contiguous arrays)."""
+def divb_clean(cfg, B, phi):
+    """Divergence cleaning of a cell-centred B [3][N] and phi [N], in place (Sec. 1.3)."""
+    assert B.dtype == np.float64 and phi.dtype == np.float64 and B.flags.c_contiguous and phi.flags.c_contiguous
+    lib().or_divb_clean(C.byref(cfg), _d(B), _d(phi))
+
+
+def step(cfg, pl: Plasma, E, B, want=(), phi=None):
+    """One full step, in place on pl, E and B (float64 contiguous arrays); with
+    cfg.divb_clean, phi (cell-centred, float64) is the cleaning potential, in place."""
     assert E.dtype == np.float64 and B.dtype == np.float64
+    if cfg.divb_clean:
+        assert phi is not None and phi.dtype == np.float64 and phi.flags.c_contiguous
     outs = {
         "Eth": vec(cfg) if "Eth" in want else None,
         "J": vec(cfg) if "J" in want else None,
@@ -334,7 +346,7 @@ def step(cfg, pl: Plasma, E, B, want=()):
         "vbar": np.zeros((pl.np, 3)) if "vbar" in want else None,
     }
     stats = np.zeros(3)
-    rc = lib().or_step(C.byref(cfg), *pl.args(), _d(pl.w), _d(E), _d(B),
+    rc = lib().or_step(C.byref(cfg), *pl.args(), _d(pl.w), _d(E), _d(B), _d(phi),
                        _d(outs["Eth"]), _d(outs["J"]), _d(outs["M"]), _d(outs["u"]), _d(outs["vbar"]), _d(stats))
     res = {k: v for k, v in outs.items() if v is not None}
     res.update(rc=rc, iters=int(stats[0]), relres=stats[1], maxdisp=stats[2])

@@ -70,7 +70,8 @@ typedef struct {
     int32_t nsmooth_u;     /* passes of the digital filter on the bulk velocity (Sec. 2.1) */
     int32_t gmres_restart;
     int32_t gmres_maxit;
-    int32_t _pad[2];
+    int32_t divb_clean;    /* 1: hyperbolic/parabolic divergence cleaning of B (Sec. 1.3) */
+    int32_t _pad;
     double dx[3];
     double c;              /* speed of light */
     double theta;          /* time centring of the theta scheme (Eq. 5-6) */
@@ -713,6 +714,56 @@ void or_advance_fields(const or_cfg *g, const double *En, const double *Bc, cons
     free(cc);
 }
 
+/* ------------------------------------------------------ div B correction */
+
+/* Hyperbolic/parabolic divergence cleaning (Sec. 1.3, "div B correction",
+ * after Dedner et al.): a scalar phi at the cell centres with
+ *   d phi / dt + c_h^2 div B = -(c_h^2 / c_p^2) phi,   dB/dt = -c curl E - grad phi,
+ * c_h = 0.8 dx / dt and dt c_h^2 / c_p^2 = 0.1 (the paper's settings; dx is the
+ * smallest cell width of the non-collapsed axes).  The paper takes its
+ * discretisation from a reference that is not available here; reading: B and
+ * phi at cell centres, divergence and gradient as central differences over the
+ * neighbouring cells (so that grad = -div^T), and within a step
+ *   B^{n+1} = (B^{n+1} of the field advance) - dt grad phi^n,
+ *   phi^{n+1} = exp(-dt c_h^2 / c_p^2) (phi^n - dt c_h^2 div B^{n+1}),
+ * the damping integrated exactly.  In place on Bnew [3][N] and phi [N]. */
+void or_divb_clean(const or_cfg *g, double *Bnew, double *phi) {
+    int64_t N = n_nodes(g);
+    double dxmin = 0.0;
+    for (int d = 0; d < 3; ++d)
+        if (g->n[d] > 1 && (dxmin == 0.0 || g->dx[d] < dxmin)) dxmin = g->dx[d];
+    if (dxmin == 0.0) return;                       /* no resolved axis: nothing to clean */
+    const double ch = 0.8 * dxmin / g->dt;
+    const double decay = exp(-0.1);
+    for (int64_t c = 0; c < N; ++c) {
+        int i, j, k;
+        unix3(g, c, &i, &j, &k);
+        for (int d = 0; d < 3; ++d) {
+            if (g->n[d] == 1) continue;
+            int p[3] = {i, j, k}, m[3] = {i, j, k};
+            p[d] += 1;
+            m[d] -= 1;
+            Bnew[d * N + c] -= g->dt * (phi[ix(g, p[0], p[1], p[2])] - phi[ix(g, m[0], m[1], m[2])]) / (2.0 * g->dx[d]);
+        }
+    }
+    double *div = (double *)malloc(sizeof(double) * N);
+    for (int64_t c = 0; c < N; ++c) {
+        int i, j, k;
+        unix3(g, c, &i, &j, &k);
+        double s = 0.0;
+        for (int d = 0; d < 3; ++d) {
+            if (g->n[d] == 1) continue;
+            int p[3] = {i, j, k}, m[3] = {i, j, k};
+            p[d] += 1;
+            m[d] -= 1;
+            s += (Bnew[d * N + ix(g, p[0], p[1], p[2])] - Bnew[d * N + ix(g, m[0], m[1], m[2])]) / (2.0 * g->dx[d]);
+        }
+        div[c] = s;
+    }
+    for (int64_t c = 0; c < N; ++c) phi[c] = decay * (phi[c] - g->dt * ch * ch * div[c]);
+    free(div);
+}
+
 /* ------------------------------------------------------------------- mover */
 
 /* theta-implicit mover (Sec. 2.1, Eq. 29-30 and the ECSIM update they cite):
@@ -787,7 +838,8 @@ void or_energy(const or_cfg *g, const double *ms, int64_t np, const int32_t *sp,
  *  4. ns_j filter passes on J;
  *  5. LF coefficients from E^n;
  *  6. right-hand side, GMRES from x0 = E^n -> E^{n+theta};
- *  7. B^{n+1}, E^{n+1};
+ *  7. B^{n+1}, E^{n+1}; with divb_clean, the divergence cleaning of B^{n+1}
+ *     and of the cell-centred phi (in/out, may be NULL without it);
  *  8. mover with E^{n+theta} and B^n.
  * E and B are updated in place; particles too.  Optional outputs (may be NULL):
  * Eth_out (3 Nn), J_out (3 Nn), M_out (Nn 27 9), u_out (3 Nn), vbar_out (3 np).
@@ -795,7 +847,7 @@ void or_energy(const or_cfg *g, const double *ms, int64_t np, const int32_t *sp,
  * stats[2] = max displacement in cells.  Returns 0 or 1 (GMRES not converged). */
 int or_step(const or_cfg *g, const double *qs, const double *ms, int64_t np, const int32_t *sp,
             double *x, double *y, double *z, double *vx, double *vy, double *vz, const double *w,
-            double *E, double *Bc, double *Eth_out, double *J_out, double *M_out, double *u_out,
+            double *E, double *Bc, double *phi, double *Eth_out, double *J_out, double *M_out, double *u_out,
             double *vbar_out, double *stats) {
     int64_t N = n_nodes(g);
     double *Bn = (double *)malloc(sizeof(double) * 3 * N);
@@ -822,6 +874,7 @@ int or_step(const or_cfg *g, const double *qs, const double *ms, int64_t np, con
     int iters = 0;
     int rc = or_gmres(g, M, g->lf_on ? kappa : NULL, b, Eth, &relres, &iters);
     or_advance_fields(g, E, Bc, Eth, u, En1, Bn1);
+    if (g->divb_clean && phi) or_divb_clean(g, Bn1, phi);
     double md = or_mover(g, qs, ms, np, sp, x, y, z, vx, vy, vz, Eth, Bn, vbar_out);
     memcpy(E, En1, sizeof(double) * 3 * N);
     memcpy(Bc, Bn1, sizeof(double) * 3 * N);
