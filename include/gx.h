@@ -80,6 +80,15 @@ typedef struct gx_ctx gx_ctx;
  *                 the starting point beyond the tolerance.
  *   precond       GX_PRECOND_*: right preconditioner of the field solve.
  *   track_ids     1: carry a 32-bit particle id through the bins (testing).
+ *   divb_clean 1: hyperbolic/parabolic cleaning of div B (Sec. 1.3): a scalar
+ *                 phi at cell centres with d phi/dt + c_h^2 div B = -(c_h^2 /
+ *                 c_p^2) phi and dB/dt = ... - grad phi, c_h = 0.8 dx/dt (dx:
+ *                 the smaller cell width), dt c_h^2/c_p^2 = 0.1 (the paper's
+ *                 settings).  Discretisation (the paper cites it from elsewhere):
+ *                 central differences over neighbouring cells for div and grad,
+ *                 B^{n+1} -= dt grad phi^n after the field advance, then
+ *                 phi^{n+1} = exp(-0.1) (phi^n - dt c_h^2 div B^{n+1}).  phi
+ *                 starts at zero and is reset by gx_fields_set.
  *   bin_slack     capacity of a cell's particle bin relative to the largest
  *                 initial count (>= 1.2; the bins grow automatically when a
  *                 step finds one filled above 90 %). */
@@ -101,6 +110,8 @@ typedef struct {
     double lf_beta;
     double gmres_tol;
     double bin_slack;
+    int32_t divb_clean;
+    int32_t reserved;
 } gx_config;
 
 typedef struct {

@@ -44,6 +44,8 @@ class Config(C.Structure):
         ("lf_beta", C.c_double),
         ("gmres_tol", C.c_double),
         ("bin_slack", C.c_double),
+        ("divb_clean", C.c_int32),
+        ("reserved", C.c_int32),
     ]
 
 
@@ -147,7 +149,7 @@ def _stream(stream):
 
 def make_config(n, dx, *, c=1.0, theta=0.5, dt=0.02, comoving=1, lf_on=1, lf_speed_c=0, lf_beta=1.0, ns_j=0,
                 nsmooth_u=5, gmres_tol=1e-8, gmres_restart=50, gmres_maxit=2000, precond=GX_PRECOND_NONE,
-                track_ids=0, bin_slack=1.6) -> Config:
+                track_ids=0, bin_slack=1.6, divb_clean=0) -> Config:
     n = list(n) + [1] * (3 - len(n))
     dx = list(dx) + [1.0] * (3 - len(dx))
     cfg = Config()
@@ -159,6 +161,7 @@ def make_config(n, dx, *, c=1.0, theta=0.5, dt=0.02, comoving=1, lf_on=1, lf_spe
     cfg.ns_j, cfg.nsmooth_u = int(ns_j), int(nsmooth_u)
     cfg.gmres_tol, cfg.gmres_restart, cfg.gmres_maxit = float(gmres_tol), int(gmres_restart), int(gmres_maxit)
     cfg.precond, cfg.track_ids, cfg.bin_slack = int(precond), int(track_ids), float(bin_slack)
+    cfg.divb_clean = int(divb_clean)
     return cfg
 
 
@@ -331,12 +334,14 @@ class Context:
                                                grad.data_ptr(), _stream(stream)))
         return L.value
 
-def from_workload(wl, *, track_ids=0, precond=GX_PRECOND_NONE, gmres_tol=None, bin_slack=1.6, gmres_restart=50):
+def from_workload(wl, *, track_ids=0, precond=GX_PRECOND_NONE, gmres_tol=None, bin_slack=1.6, gmres_restart=50,
+                  divb_clean=0):
     """Create a context from a workloads.Workload (inputs copied from host)."""
     cfg = make_config(wl.n, wl.dx, c=wl.c, theta=wl.theta, dt=wl.dt, comoving=wl.comoving, lf_on=wl.lf_on,
                       lf_speed_c=wl.lf_speed_c, lf_beta=wl.lf_beta, ns_j=wl.ns_j, nsmooth_u=wl.nsmooth_u,
                       gmres_tol=wl.gmres_tol if gmres_tol is None else gmres_tol, precond=precond,
-                      track_ids=track_ids, bin_slack=bin_slack, gmres_restart=gmres_restart)
+                      track_ids=track_ids, bin_slack=bin_slack, gmres_restart=gmres_restart,
+                      divb_clean=divb_clean)
     ctx = Context(cfg)
     for s in wl.species:
         ctx.species_add(s["q"], s["m"], np.ascontiguousarray(s["x"], np.float64),

@@ -181,6 +181,7 @@ void gx_destroy(gx_ctx *c) {
     for (auto p : dp)
         if (*p) cudaFree(*p);
     if (c->jdiag32) cudaFree(c->jdiag32);
+    if (c->phi) cudaFree(c->phi);
     float4 **fp[] = {&c->nE, &c->nB, &c->nBnext, &c->nUref};
     for (auto p : fp)
         if (*p) cudaFree(*p);
@@ -240,6 +241,10 @@ int gx_create(const gx_config *cfg, gx_ctx **out) {
         (rc = dalloc(c, &c->hcol, 2 * (m + 2))) || (rc = dalloc(c, &c->dflags, 1)))
         return fail(rc, nullptr);
     if (cfg->precond != GX_PRECOND_NONE && (rc = dalloc(c, &c->Z, (size_t)m * 3 * N))) return fail(rc, nullptr);
+    if (cfg->divb_clean) {
+        if ((rc = dalloc(c, &c->phi, N))) return fail(rc, nullptr);
+        if (cudaMemset(c->phi, 0, N * sizeof(double)) != cudaSuccess) return fail(GX_ECUDA, "cudaMemset failed");
+    }
     {
         char *gm = nullptr;
         if ((rc = dalloc(c, &gm, gx_gm_state_bytes())) || (rc = dalloc(c, &c->gpart, gx_gm_partial_count())))
@@ -310,6 +315,7 @@ int gx_fields_set(gx_ctx *c, const double *E, const double *B, int ptr_is_device
     const size_t bytes = 3 * c->N * sizeof(double);
     if (E) TRY(copy_in(c, c->E, E, bytes, ptr_is_device, 0));
     if (B) TRY(copy_in(c, c->B, B, bytes, ptr_is_device, 0));
+    if (B && c->phi) GX_CHECK(c, cudaMemsetAsync(c->phi, 0, c->N * sizeof(double), 0));
     GX_CHECK(c, cudaStreamSynchronize(0));
     c->moments_valid = 0;
     c->pending = 0;

@@ -287,6 +287,19 @@ __global__ void k_matvec(OpArgs a, const double *__restrict__ x, double *__restr
     }
 }
 
+// div B cleaning (Sec. 1.3): phi = decay (phi - dtch2 div B), the central
+// divergence of the cell-centred B^{n+1} over neighbouring cells
+__global__ void k_divb_phi(G2 g, const double *__restrict__ B, double dtch2, double decay, double *phi) {
+    const int64_t N = g.N();
+    GRID_LOOP(q, N) {
+        const int i = (int)(q % g.nx), j = (int)(q / g.nx);
+        double d = 0.0;
+        if (g.nx > 1) d += (B[g.id(i + 1, j)] - B[g.id(i - 1, j)]) * g.hx;
+        if (g.ny > 1) d += (B[N + g.id(i, j + 1)] - B[N + g.id(i, j - 1)]) * g.hy;
+        phi[q] = decay * (phi[q] - dtch2 * d);
+    }
+}
+
 // 3x3 diagonal block of A at every node, inverted (block-Jacobi preconditioner),
 // in FP64 and in FP32
 __global__ void k_jacobi(OpArgs a, double *jd, float *jd32) {
@@ -431,7 +444,8 @@ __global__ void k_kappa(G2 g, const double *__restrict__ E, const double *__rest
 // F = (1 - phi_B) a / 2 (B_{c+1} - B_c)  (Eq. 5, 17, 18, 22);  E^{n+1} from Eq. 10.
 __global__ void k_advance(G2 g, const double *__restrict__ E, const double *__restrict__ B,
                           const double *__restrict__ Eth, const double *__restrict__ u, double c, double dt,
-                          double theta, int lf_on, double beta, int speed_c, double *Enew, double *Bnew) {
+                          double theta, int lf_on, double beta, int speed_c, const double *__restrict__ phi,
+                          double *Enew, double *Bnew) {
     const int64_t N = g.N();
     GRID_LOOP(q, N) {
         const int i = (int)(q % g.nx), j = (int)(q / g.nx);
@@ -471,6 +485,10 @@ __global__ void k_advance(G2 g, const double *__restrict__ E, const double *__re
                     }
                 }
             }
+        }
+        if (phi) {   // div B cleaning (Sec. 1.3): - dt grad phi^n, central over cells (hx = 1 / (2 dx))
+            if (g.nx > 1) bn[0] -= dt * (phi[g.id(i + 1, j)] - phi[g.id(i - 1, j)]) * g.hx;
+            if (g.ny > 1) bn[1] -= dt * (phi[g.id(i, j + 1)] - phi[g.id(i, j - 1)]) * g.hy;
         }
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
@@ -672,8 +690,18 @@ int gx_initial_guess(gx_ctx *c, cudaStream_t st) {
 
 int gx_advance(gx_ctx *c, cudaStream_t st) {
     k_advance<<<blocks_for(c->N), kB, 0, st>>>(geom(c), c->E, c->B, c->Eth, c->u, c->cfg.c, c->cfg.dt, c->cfg.theta,
-                                               c->cfg.lf_on, c->cfg.lf_beta, c->cfg.lf_speed_c, c->Enew, c->Bnew);
+                                               c->cfg.lf_on, c->cfg.lf_beta, c->cfg.lf_speed_c, c->phi, c->Enew,
+                                               c->Bnew);
     GX_LAUNCHED(c);
+    if (c->phi) {
+        // phi^{n+1} = exp(-dt c_h^2 / c_p^2) (phi^n - dt c_h^2 div B^{n+1}), c_h = 0.8 dx / dt
+        const double dxmin = std::min(c->n[0] > 1 ? c->cfg.dx[0] : 1e300, c->n[1] > 1 ? c->cfg.dx[1] : 1e300);
+        if (dxmin < 1e300) {
+            const double ch = 0.8 * dxmin / c->cfg.dt;
+            k_divb_phi<<<blocks_for(c->N), kB, 0, st>>>(geom(c), c->Bnew, c->cfg.dt * ch * ch, std::exp(-0.1), c->phi);
+            GX_LAUNCHED(c);
+        }
+    }
     return GX_OK;
 }
 
