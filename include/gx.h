@@ -89,6 +89,10 @@ typedef struct gx_ctx gx_ctx;
  *                 B^{n+1} -= dt grad phi^n after the field advance, then
  *                 phi^{n+1} = exp(-0.1) (phi^n - dt c_h^2 div B^{n+1}).  phi
  *                 starts at zero and is reset by gx_fields_set.
+ *   nsmooth_e     passes of the digital filter of Eq. 26 (phi = 0.5, strides
+ *                 1, 2, 1, ...) on E^{n+1} after every step, in place of the
+ *                 implicit LF term on E (the comparison of Sec. 3.1); the LF
+ *                 term on B stays as lf_on says.  0: off.  At most 10 passes.
  *   bin_slack     capacity of a cell's particle bin relative to the largest
  *                 initial count (>= 1.2; the bins grow automatically when a
  *                 step finds one filled above 90 %). */
@@ -111,7 +115,7 @@ typedef struct {
     double gmres_tol;
     double bin_slack;
     int32_t divb_clean;
-    int32_t reserved;
+    int32_t nsmooth_e;
 } gx_config;
 
 typedef struct {

@@ -51,7 +51,7 @@ class Cfg(C.Structure):
         ("gmres_restart", C.c_int32),
         ("gmres_maxit", C.c_int32),
         ("divb_clean", C.c_int32),
-        ("_pad", C.c_int32),
+        ("nsmooth_e", C.c_int32),
         ("dx", C.c_double * 3),
         ("c", C.c_double),
         ("theta", C.c_double),
@@ -70,7 +70,8 @@ class Cfg(C.Structure):
 
 
 def make_cfg(n, dx, *, c=1.0, theta=0.5, dt=0.02, comoving=0, lf_on=0, lf_speed_c=0, lf_beta=1.0,
-             ns_j=0, nsmooth_u=5, gmres_tol=1e-12, gmres_restart=50, gmres_maxit=5000, divb_clean=0) -> Cfg:
+             ns_j=0, nsmooth_u=5, gmres_tol=1e-12, gmres_restart=50, gmres_maxit=5000, divb_clean=0,
+             nsmooth_e=0) -> Cfg:
     n = list(n) + [1] * (3 - len(n))
     dx = list(dx) + [1.0] * (3 - len(dx))
     cfg = Cfg()
@@ -82,6 +83,7 @@ def make_cfg(n, dx, *, c=1.0, theta=0.5, dt=0.02, comoving=0, lf_on=0, lf_speed_
     cfg.lf_beta, cfg.ns_j, cfg.nsmooth_u = float(lf_beta), int(ns_j), int(nsmooth_u)
     cfg.gmres_tol, cfg.gmres_restart, cfg.gmres_maxit = float(gmres_tol), int(gmres_restart), int(gmres_maxit)
     cfg.divb_clean = int(divb_clean)
+    cfg.nsmooth_e = int(nsmooth_e)
     return cfg
 
 
@@ -93,6 +95,7 @@ _SIGS = {
     "or_alpha": (None, [_D, _D]),
     "or_node_avg": (None, [_P, _D, _D]),
     "or_filter": (None, [_P, _D, C.c_int, C.c_int, C.c_double]),
+    "or_lf_b_increment": (None, [_P, _D, _D, _D]),
     "or_bulk_moments": (None, [_P, _D, _D, C.c_int64, _I32, _D, _D, _D, _D, _D, _D, _D, _D, _D]),
     "or_bulk_velocity": (None, [_P, _D, _D, _D]),
     "or_deposit": (None, [_P, _D, _D, C.c_int64, _I32, _D, _D, _D, _D, _D, _D, _D, _D, _D, _D, _D, _D]),
@@ -303,6 +306,14 @@ def dense_solve(cfg, b, M=None, kappa=None):
     rc = lib().or_dense_solve(C.byref(cfg), None if M is None else _d(_f64(M)),
                               None if kappa is None else _d(_f64(kappa)), _d(_f64(b)), _d(x))
     return x, rc
+
+
+def lf_b_increment(cfg, Bc, u=None):
+    """The LF increment D that B^{n+1} receives (Eq. 17-18); zero without lf_on."""
+    D = vec(cfg)
+    u = vec(cfg) if u is None else _f64(u)
+    lib().or_lf_b_increment(C.byref(cfg), _d(_f64(Bc)), _d(u), _d(D))
+    return D
 
 
 def advance_fields(cfg, En, Bc, Eth, u=None):

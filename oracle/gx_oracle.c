@@ -71,7 +71,7 @@ typedef struct {
     int32_t gmres_restart;
     int32_t gmres_maxit;
     int32_t divb_clean;    /* 1: hyperbolic/parabolic divergence cleaning of B (Sec. 1.3) */
-    int32_t _pad;
+    int32_t nsmooth_e;     /* passes of the digital filter on E^{n+1} instead of LF on E (Sec. 3.1) */
     double dx[3];
     double c;              /* speed of light */
     double theta;          /* time centring of the theta scheme (Eq. 5-6) */
@@ -485,16 +485,33 @@ void or_apply_A(const or_cfg *g, const double *M, const double *kappa, const dou
     free(cc);
 }
 
+void or_lf_b_increment(const or_cfg *g, const double *Bc, const double *u, double *D);
+
 /* Right-hand side of the E solve (Eq. 7; comoving form Eq. 35):
- *   b = E^n + c theta dt [curl_N B^n - (4 pi / c)(J - (1/dV) M E_M)]
+ *   b = E^n + c theta dt [curl_N B~ - (4 pi / c)(J - (1/dV) M E_M)]
  * with J the comoving current and E_M = -u x B^n / c the motional field at
  * nodes (B^n node averaged) when comoving != 0, and J the standard predicted-
- * current part without the E_M term otherwise. */
+ * current part without the E_M term otherwise.  B~ = B^n, or with lf_on
+ * B^n + theta D, D the LF increment that B^{n+1} receives (Eq. 17-18):
+ * Eq. 7 comes from substituting B^{n+theta} = (1-theta) B^n + theta B^{n+1}
+ * into Eq. 6, and B^{n+1} carries D besides - c dt curl E^{n+theta}.
+ * (Left out, the explicit D at level n amplifies the modes that the theta = 1/2
+ * scheme flips in sign every step when c dt / dx >> 1.) */
 void or_rhs(const or_cfg *g, const double *En, const double *Bc, const double *J, const double *M,
             const double *u, const double *Bn, double *b) {
     int64_t N = n_nodes(g);
     double *cn = (double *)malloc(sizeof(double) * 3 * N);
-    or_curl_N(g, Bc, cn);
+    if (g->lf_on) {
+        /* B^{n+theta} = (1 - theta) B^n + theta B^{n+1} holds the LF increment D
+         * of B^{n+1} too, so the curl on the right acts on B^n + theta D */
+        double *Bt = (double *)malloc(sizeof(double) * 3 * N);
+        or_lf_b_increment(g, Bc, u, Bt);
+        for (int64_t q = 0; q < 3 * N; ++q) Bt[q] = Bc[q] + g->theta * Bt[q];
+        or_curl_N(g, Bt, cn);
+        free(Bt);
+    } else {
+        or_curl_N(g, Bc, cn);
+    }
     double ct = g->c * g->theta * g->dt;
     double jf = 4.0 * OR_PI * g->theta * g->dt;
     for (int64_t q = 0; q < 3 * N; ++q) b[q] = En[q] + ct * cn[q] - jf * J[q];
@@ -652,66 +669,75 @@ int or_dense_solve(const or_cfg *g, const double *M, const double *kappa, const 
 
 /* ---------------------------------------------------------- field advance */
 
-/* B^{n+1} = B^n - c dt curl_C E^{n+theta} + (limited LF diffusion), Eq. 5 and
- * Eq. 17-18 (read with c dt, not c theta dt, see Eq. 8), and
- * E^{n+1} = (E^{n+theta} - (1-theta) E^n) / theta (Eq. 10).
- * The LF term adds dt/dx_d (F_{c+1/2} - F_{c-1/2}) to every component along
- * every axis, F = (1 - phi_B) a / 2 (B_{c+1} - B_c), phi_B = MC(r, beta) with
- * r = (B_c - B_{c-1}) / (B_{c+1} - B_c) (Eq. 22), a = |u| averaged over the
- * face's 4 nodes (or c).  u may be NULL when lf_speed_c != 0. */
+/* Increment of the limited LF diffusion on B over one step (Eq. 17-18), per
+ * component along every resolved axis:
+ *   D_c = dt/dx_d (F_{c+1/2} - F_{c-1/2}),  F = (1 - phi_B) a / 2 (B_{c+1} - B_c),
+ * phi_B = MC(r, beta) with r = (B_c - B_{c-1}) / (B_{c+1} - B_c) (Eq. 22),
+ * a = |u| averaged over the face's 4 nodes (or c).  D = 0 without lf_on.  u may
+ * be NULL when lf_speed_c != 0.  D [3][N]. */
+void or_lf_b_increment(const or_cfg *g, const double *Bc, const double *u, double *D) {
+    int64_t N = n_nodes(g);
+    memset(D, 0, sizeof(double) * 3 * N);
+    if (!g->lf_on) return;
+    double *F = (double *)malloc(sizeof(double) * N);
+    for (int d = 0; d < 3; ++d) {
+        if (g->n[d] == 1) continue;
+        double f = g->dt / g->dx[d];
+        for (int comp = 0; comp < 3; ++comp) {
+            const double *B = Bc + comp * N;
+            for (int64_t c = 0; c < N; ++c) {
+                int i, j, k;
+                unix3(g, c, &i, &j, &k);
+                int p[3] = {i, j, k}, m[3] = {i, j, k};
+                p[d] += 1;
+                m[d] -= 1;
+                int64_t cp = ix(g, p[0], p[1], p[2]), cm = ix(g, m[0], m[1], m[2]);
+                double r = ratio(B[c] - B[cm], B[cp] - B[c]);
+                double phi = or_mc_limiter(r, g->lf_beta);
+                double a;
+                if (g->lf_speed_c) {
+                    a = g->c;
+                } else {
+                    /* face between cell c and c+e_d: nodes with index_d = c_d + 1 */
+                    double s = 0.0;
+                    for (int t = 0; t < 4; ++t) {
+                        int o[3] = {0, 0, 0};
+                        int e1 = (d + 1) % 3, e2 = (d + 2) % 3;
+                        o[d] = 1;
+                        o[e1] = t & 1;
+                        o[e2] = (t >> 1) & 1;
+                        s += umag(g, u, ix(g, i + o[0], j + o[1], k + o[2]));
+                    }
+                    a = s / 4.0;
+                }
+                F[c] = (1.0 - phi) * a / 2.0 * (B[cp] - B[c]);
+            }
+            for (int64_t c = 0; c < N; ++c) {
+                int i, j, k;
+                unix3(g, c, &i, &j, &k);
+                int m[3] = {i, j, k};
+                m[d] -= 1;
+                D[comp * N + c] += f * (F[c] - F[ix(g, m[0], m[1], m[2])]);
+            }
+        }
+    }
+    free(F);
+}
+
+/* B^{n+1} = B^n - c dt curl_C E^{n+theta} + D (Eq. 5 read with c dt, not
+ * c theta dt, see Eq. 8; D the LF increment of or_lf_b_increment, Eq. 17-18),
+ * and E^{n+1} = (E^{n+theta} - (1-theta) E^n) / theta (Eq. 10). */
 void or_advance_fields(const or_cfg *g, const double *En, const double *Bc, const double *Eth,
                        const double *u, double *Enew, double *Bnew) {
     int64_t N = n_nodes(g);
     double *cc = (double *)malloc(sizeof(double) * 3 * N);
+    double *D = (double *)malloc(sizeof(double) * 3 * N);
     or_curl_C(g, Eth, cc);
-    for (int64_t q = 0; q < 3 * N; ++q) Bnew[q] = Bc[q] - g->c * g->dt * cc[q];
-    if (g->lf_on) {
-        double *F = (double *)malloc(sizeof(double) * N);
-        for (int d = 0; d < 3; ++d) {
-            if (g->n[d] == 1) continue;
-            double f = g->dt / g->dx[d];
-            for (int comp = 0; comp < 3; ++comp) {
-                const double *B = Bc + comp * N;
-                for (int64_t c = 0; c < N; ++c) {
-                    int i, j, k;
-                    unix3(g, c, &i, &j, &k);
-                    int p[3] = {i, j, k}, m[3] = {i, j, k};
-                    p[d] += 1;
-                    m[d] -= 1;
-                    int64_t cp = ix(g, p[0], p[1], p[2]), cm = ix(g, m[0], m[1], m[2]);
-                    double r = ratio(B[c] - B[cm], B[cp] - B[c]);
-                    double phi = or_mc_limiter(r, g->lf_beta);
-                    double a;
-                    if (g->lf_speed_c) {
-                        a = g->c;
-                    } else {
-                        /* face between cell c and c+e_d: nodes with index_d = c_d + 1 */
-                        double s = 0.0;
-                        for (int t = 0; t < 4; ++t) {
-                            int o[3] = {0, 0, 0};
-                            int e1 = (d + 1) % 3, e2 = (d + 2) % 3;
-                            o[d] = 1;
-                            o[e1] = t & 1;
-                            o[e2] = (t >> 1) & 1;
-                            s += umag(g, u, ix(g, i + o[0], j + o[1], k + o[2]));
-                        }
-                        a = s / 4.0;
-                    }
-                    F[c] = (1.0 - phi) * a / 2.0 * (B[cp] - B[c]);
-                }
-                for (int64_t c = 0; c < N; ++c) {
-                    int i, j, k;
-                    unix3(g, c, &i, &j, &k);
-                    int m[3] = {i, j, k};
-                    m[d] -= 1;
-                    Bnew[comp * N + c] += f * (F[c] - F[ix(g, m[0], m[1], m[2])]);
-                }
-            }
-        }
-        free(F);
-    }
+    or_lf_b_increment(g, Bc, u, D);
+    for (int64_t q = 0; q < 3 * N; ++q) Bnew[q] = Bc[q] - g->c * g->dt * cc[q] + D[q];
     for (int64_t q = 0; q < 3 * N; ++q) Enew[q] = (Eth[q] - (1.0 - g->theta) * En[q]) / g->theta;
     free(cc);
+    free(D);
 }
 
 /* ------------------------------------------------------ div B correction */
@@ -836,10 +862,11 @@ void or_energy(const or_cfg *g, const double *ms, int64_t np, const int32_t *sp,
  *  2. bulk velocity u (needed for the comoving current and for a = |u|);
  *  3. deposit rho, J (comoving or standard), M with alpha from B^n;
  *  4. ns_j filter passes on J;
- *  5. LF coefficients from E^n;
+ *  5. LF coefficients from E^n (skipped with nsmooth_e > 0);
  *  6. right-hand side, GMRES from x0 = E^n -> E^{n+theta};
  *  7. B^{n+1}, E^{n+1}; with divb_clean, the divergence cleaning of B^{n+1}
  *     and of the cell-centred phi (in/out, may be NULL without it);
+ *     with nsmooth_e, nsmooth_e filter passes on E^{n+1} (strides 1, 2, 1, ...);
  *  8. mover with E^{n+theta} and B^n.
  * E and B are updated in place; particles too.  Optional outputs (may be NULL):
  * Eth_out (3 Nn), J_out (3 Nn), M_out (Nn 27 9), u_out (3 Nn), vbar_out (3 np).
@@ -867,14 +894,19 @@ int or_step(const or_cfg *g, const double *qs, const double *ms, int64_t np, con
     }
     or_deposit(g, qs, ms, np, sp, x, y, z, vx, vy, vz, w, Bn, g->comoving ? u : NULL, rho, J, M);
     or_smooth_current(g, J, g->ns_j);
-    if (g->lf_on) or_lf_kappa_E(g, E, u, kappa);
+    /* with nsmooth_e > 0 the digital filter on E replaces the implicit LF term
+     * on E; the LF term on B stays as lf_on says (the comparison of Sec. 3.1) */
+    const int lf_e = g->lf_on && g->nsmooth_e == 0;
+    if (lf_e) or_lf_kappa_E(g, E, u, kappa);
     or_rhs(g, E, Bc, J, M, u, Bn, b);
     memcpy(Eth, E, sizeof(double) * 3 * N);
     double relres = 0.0;
     int iters = 0;
-    int rc = or_gmres(g, M, g->lf_on ? kappa : NULL, b, Eth, &relres, &iters);
+    int rc = or_gmres(g, M, lf_e ? kappa : NULL, b, Eth, &relres, &iters);
     or_advance_fields(g, E, Bc, Eth, u, En1, Bn1);
     if (g->divb_clean && phi) or_divb_clean(g, Bn1, phi);
+    /* E^{n+1} smoothed by nsmooth_e passes of Eq. 26, phi = 0.5, strides 1, 2, 1, ... */
+    for (int pass = 0; pass < g->nsmooth_e; ++pass) or_filter(g, En1, 3, (pass % 2 == 0) ? 1 : 2, 0.5);
     double md = or_mover(g, qs, ms, np, sp, x, y, z, vx, vy, vz, Eth, Bn, vbar_out);
     memcpy(E, En1, sizeof(double) * 3 * N);
     memcpy(Bc, Bn1, sizeof(double) * 3 * N);

@@ -45,7 +45,7 @@ class Config(C.Structure):
         ("gmres_tol", C.c_double),
         ("bin_slack", C.c_double),
         ("divb_clean", C.c_int32),
-        ("reserved", C.c_int32),
+        ("nsmooth_e", C.c_int32),
     ]
 
 
@@ -149,7 +149,7 @@ def _stream(stream):
 
 def make_config(n, dx, *, c=1.0, theta=0.5, dt=0.02, comoving=1, lf_on=1, lf_speed_c=0, lf_beta=1.0, ns_j=0,
                 nsmooth_u=5, gmres_tol=1e-8, gmres_restart=50, gmres_maxit=2000, precond=GX_PRECOND_NONE,
-                track_ids=0, bin_slack=1.6, divb_clean=0) -> Config:
+                track_ids=0, bin_slack=1.6, divb_clean=0, nsmooth_e=0) -> Config:
     n = list(n) + [1] * (3 - len(n))
     dx = list(dx) + [1.0] * (3 - len(dx))
     cfg = Config()
@@ -162,6 +162,7 @@ def make_config(n, dx, *, c=1.0, theta=0.5, dt=0.02, comoving=1, lf_on=1, lf_spe
     cfg.gmres_tol, cfg.gmres_restart, cfg.gmres_maxit = float(gmres_tol), int(gmres_restart), int(gmres_maxit)
     cfg.precond, cfg.track_ids, cfg.bin_slack = int(precond), int(track_ids), float(bin_slack)
     cfg.divb_clean = int(divb_clean)
+    cfg.nsmooth_e = int(nsmooth_e)
     return cfg
 
 

@@ -177,7 +177,7 @@ void gx_destroy(gx_ctx *c) {
     gx_free_bins(c);
     double **dp[] = {&c->E, &c->B, &c->Eth, &c->Enew, &c->Bnew, &c->rho, &c->rho_m, &c->P, &c->u, &c->J,
                      &c->M, &c->tmp3, &c->uref64, &c->kappa, &c->rhs, &c->EM, &c->jdiag, &c->V, &c->Z,
-                     &c->w, &c->r, &c->dred, &c->hcol};
+                     &c->w, &c->r, &c->dred, &c->hcol, &c->dBlf};
     for (auto p : dp)
         if (*p) cudaFree(*p);
     if (c->jdiag32) cudaFree(c->jdiag32);
@@ -222,7 +222,9 @@ int gx_create(const gx_config *cfg, gx_ctx **out) {
     if (cfg->gmres_maxit < 1) return fail(GX_EINVAL, "gmres_maxit must be >= 1");
     if (!(cfg->gmres_tol > 0)) return fail(GX_EINVAL, "gmres_tol must be > 0");
     if (cfg->precond < 0 || cfg->precond > 2) return fail(GX_EINVAL, "precond must be 0, 1 or 2");
-    if (cfg->nsmooth_u < 0 || cfg->ns_j < 0) return fail(GX_EINVAL, "smoothing passes must be >= 0");
+    if (cfg->nsmooth_u < 0 || cfg->ns_j < 0 || cfg->nsmooth_e < 0)
+        return fail(GX_EINVAL, "smoothing passes must be >= 0");
+    if (cfg->nsmooth_e > 10) return fail(GX_EINVAL, "nsmooth_e must be <= 10");
     if (cfg->lf_on && cfg->lf_beta < 0) return fail(GX_EINVAL, "lf_beta must be >= 0");
     c->dim = 2;
     c->N = (int64_t)c->n[0] * c->n[1] * c->n[2];
@@ -241,6 +243,7 @@ int gx_create(const gx_config *cfg, gx_ctx **out) {
         (rc = dalloc(c, &c->hcol, 2 * (m + 2))) || (rc = dalloc(c, &c->dflags, 1)))
         return fail(rc, nullptr);
     if (cfg->precond != GX_PRECOND_NONE && (rc = dalloc(c, &c->Z, (size_t)m * 3 * N))) return fail(rc, nullptr);
+    if (cfg->lf_on && (rc = dalloc(c, &c->dBlf, 3 * N))) return fail(rc, nullptr);
     if (cfg->divb_clean) {
         if ((rc = dalloc(c, &c->phi, N))) return fail(rc, nullptr);
         if (cudaMemset(c->phi, 0, N * sizeof(double)) != cudaSuccess) return fail(GX_ECUDA, "cudaMemset failed");

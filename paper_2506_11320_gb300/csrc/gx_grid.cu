@@ -370,8 +370,8 @@ __global__ void k_motional(G2 g, const double *__restrict__ u, const double *__r
 
 // b = E^n + c theta dt [curl_N B^n - (4 pi / c)(J - (1/dV) M E_M)]   (Eq. 35)
 __global__ void k_rhs(G2 g, const double *__restrict__ E, const double *__restrict__ B, const double *__restrict__ J,
-                      const double *__restrict__ M, const double *__restrict__ EM, double ctd, double jf, double mf,
-                      double *b) {
+                      const double *__restrict__ M, const double *__restrict__ EM, const double *__restrict__ D,
+                      double theta, double ctd, double jf, double mf, double *b) {
     const int64_t N = g.N();
     GRID_LOOP(q, N) {
         const int i = (int)(q % g.nx), j = (int)(q / g.nx);
@@ -380,6 +380,12 @@ __global__ void k_rhs(G2 g, const double *__restrict__ E, const double *__restri
         cn[0] = dNy(g, Bz, i, j);
         cn[1] = -dNx(g, Bz, i, j);
         cn[2] = dNx(g, By, i, j) - dNy(g, Bx, i, j);
+        if (D) {   // B^{n+theta} holds theta D of the LF increment: curl (B^n + theta D)
+            const double *Dx = D, *Dy = D + N, *Dz = D + 2 * N;
+            cn[0] += theta * dNy(g, Dz, i, j);
+            cn[1] -= theta * dNx(g, Dz, i, j);
+            cn[2] += theta * (dNx(g, Dy, i, j) - dNy(g, Dx, i, j));
+        }
         double out[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) out[k] = E[k * N + q] + ctd * cn[k] - jf * J[k * N + q];
@@ -442,10 +448,55 @@ __global__ void k_kappa(G2 g, const double *__restrict__ E, const double *__rest
 
 // B^{n+1} = B^n - c dt curl_C E^{n+theta} + dt/dx_d (F_{c+1/2} - F_{c-1/2}),
 // F = (1 - phi_B) a / 2 (B_{c+1} - B_c)  (Eq. 5, 17, 18, 22);  E^{n+1} from Eq. 10.
+// Increment of the limited LF diffusion on B over one step (Eq. 17-18): per
+// component along every resolved axis D = dt/dx (F_{c+1/2} - F_{c-1/2}),
+// F = (1 - phi_B) a / 2 (B_{c+1} - B_c), phi_B = MC(r, beta), r = (B_c -
+// B_{c-1}) / (B_{c+1} - B_c), a = |u| averaged over the face (or c).  Computed
+// once per step: B^{n+1} receives D, and the E solve curls B^n + theta D (the
+// B^{n+theta} that holds it).
+__global__ void k_lf_b(G2 g, const double *__restrict__ B, const double *__restrict__ u, double c, double dt,
+                       double beta, int speed_c, double *D) {
+    const int64_t N = g.N();
+    GRID_LOOP(q, N) {
+        const int i = (int)(q % g.nx), j = (int)(q / g.nx);
+        double dn[3] = {0.0, 0.0, 0.0};
+        for (int d = 0; d < 2; ++d) {
+            if ((d == 0 && g.nx == 1) || (d == 1 && g.ny == 1)) continue;
+            const double f = dt * 2.0 * (d == 0 ? g.hx : g.hy);
+            // faces c+1/2 (between c and c+e) and c-1/2 (between c-e and c)
+            for (int side = 0; side < 2; ++side) {
+                const int ci = d == 0 ? i - side : i, cj = d == 0 ? j : j - side;   // face between (ci,cj) and +e
+                const int64_t c0 = g.id(ci, cj);
+                const int64_t cp = d == 0 ? g.id(ci + 1, cj) : g.id(ci, cj + 1);
+                const int64_t cm = d == 0 ? g.id(ci - 1, cj) : g.id(ci, cj - 1);
+                double a;
+                if (speed_c) {
+                    a = c;
+                } else {
+                    const int64_t n0 = d == 0 ? g.id(ci + 1, cj) : g.id(ci, cj + 1);
+                    const int64_t n1 = g.id(ci + 1, cj + 1);
+                    a = 0.5 * (double)(umag(u, N, n0) + umag(u, N, n1));
+                }
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    const double *Bk = B + k * N;
+                    const double dp = Bk[cp] - Bk[c0];
+                    const float r = ratio(Bk[c0] - Bk[cm], dp);
+                    const double F = (double)(1.0f - mc_limiter(r, (float)beta)) * a * 0.5 * dp;
+                    dn[k] += side == 0 ? f * F : -f * F;
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) D[k * N + q] = dn[k];
+    }
+}
+
+// B^{n+1} = B^n - c dt curl_C E^{n+theta} (+ the LF increment D, - dt grad phi^n)
+// and E^{n+1} = (E^{n+theta} - (1 - theta) E^n) / theta
 __global__ void k_advance(G2 g, const double *__restrict__ E, const double *__restrict__ B,
-                          const double *__restrict__ Eth, const double *__restrict__ u, double c, double dt,
-                          double theta, int lf_on, double beta, int speed_c, const double *__restrict__ phi,
-                          double *Enew, double *Bnew) {
+                          const double *__restrict__ Eth, double c, double dt, double theta,
+                          const double *__restrict__ D, const double *__restrict__ phi, double *Enew, double *Bnew) {
     const int64_t N = g.N();
     GRID_LOOP(q, N) {
         const int i = (int)(q % g.nx), j = (int)(q / g.nx);
@@ -457,34 +508,9 @@ __global__ void k_advance(G2 g, const double *__restrict__ E, const double *__re
         double bn[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) bn[k] = B[k * N + q] - c * dt * cu[k];
-        if (lf_on) {
-            for (int d = 0; d < 2; ++d) {
-                if ((d == 0 && g.nx == 1) || (d == 1 && g.ny == 1)) continue;
-                const double f = dt * 2.0 * (d == 0 ? g.hx : g.hy);
-                // faces c+1/2 (between c and c+e) and c-1/2 (between c-e and c)
-                for (int side = 0; side < 2; ++side) {
-                    const int ci = d == 0 ? i - side : i, cj = d == 0 ? j : j - side;   // face between (ci,cj) and +e
-                    const int64_t c0 = g.id(ci, cj);
-                    const int64_t cp = d == 0 ? g.id(ci + 1, cj) : g.id(ci, cj + 1);
-                    const int64_t cm = d == 0 ? g.id(ci - 1, cj) : g.id(ci, cj - 1);
-                    double a;
-                    if (speed_c) {
-                        a = c;
-                    } else {
-                        const int64_t n0 = d == 0 ? g.id(ci + 1, cj) : g.id(ci, cj + 1);
-                        const int64_t n1 = g.id(ci + 1, cj + 1);
-                        a = 0.5 * (double)(umag(u, N, n0) + umag(u, N, n1));
-                    }
+        if (D) {
 #pragma unroll
-                    for (int k = 0; k < 3; ++k) {
-                        const double *Bk = B + k * N;
-                        const double dp = Bk[cp] - Bk[c0];
-                        const float r = ratio(Bk[c0] - Bk[cm], dp);
-                        const double F = (double)(1.0f - mc_limiter(r, (float)beta)) * a * 0.5 * dp;
-                        bn[k] += side == 0 ? f * F : -f * F;
-                    }
-                }
-            }
+            for (int k = 0; k < 3; ++k) bn[k] += D[k * N + q];
         }
         if (phi) {   // div B cleaning (Sec. 1.3): - dt grad phi^n, central over cells (hx = 1 / (2 dx))
             if (g.nx > 1) bn[0] -= dt * (phi[g.id(i + 1, j)] - phi[g.id(i - 1, j)]) * g.hx;
@@ -575,7 +601,7 @@ OpArgs opargs(const gx_ctx *c) {
     a.lfx = c->cfg.theta * c->cfg.dt / c->cfg.dx[0];
     a.lfy = c->cfg.theta * c->cfg.dt / c->cfg.dx[1];
     a.M = c->nspecies > 0 ? c->M : nullptr;
-    a.kappa = c->cfg.lf_on ? c->kappa : nullptr;
+    a.kappa = (c->cfg.lf_on && c->cfg.nsmooth_e == 0) ? c->kappa : nullptr;   // the E filter replaces LF on E
     return a;
 }
 
@@ -641,14 +667,21 @@ int gx_build_rhs(gx_ctx *c, cudaStream_t st) {
     }
     const double ctd = c->cfg.c * c->cfg.theta * c->cfg.dt;
     const double jf = 4.0 * GX_PI * c->cfg.theta * c->cfg.dt;
-    k_rhs<<<blocks_for(c->N), kB, 0, st>>>(g, c->E, c->B, c->J, c->M, cm ? c->EM : nullptr, ctd, jf, jf / c->dV,
-                                           c->rhs);
+    const double *D = nullptr;
+    if (c->cfg.lf_on) {
+        k_lf_b<<<blocks_for(c->N), kB, 0, st>>>(g, c->B, c->u, c->cfg.c, c->cfg.dt, c->cfg.lf_beta, c->cfg.lf_speed_c,
+                                                c->dBlf);
+        GX_LAUNCHED(c);
+        D = c->dBlf;
+    }
+    k_rhs<<<blocks_for(c->N), kB, 0, st>>>(g, c->E, c->B, c->J, c->M, cm ? c->EM : nullptr, D, c->cfg.theta, ctd,
+                                           jf, jf / c->dV, c->rhs);
     GX_LAUNCHED(c);
     return GX_OK;
 }
 
 int gx_build_kappa(gx_ctx *c, cudaStream_t st) {
-    if (!c->cfg.lf_on) return GX_OK;
+    if (!c->cfg.lf_on || c->cfg.nsmooth_e > 0) return GX_OK;
     k_kappa<<<blocks_for(c->N), kB, 0, st>>>(geom(c), c->E, c->u, c->cfg.lf_beta, c->cfg.lf_speed_c, c->cfg.c,
                                               c->kappa);
     GX_LAUNCHED(c);
@@ -689,9 +722,9 @@ int gx_initial_guess(gx_ctx *c, cudaStream_t st) {
 }
 
 int gx_advance(gx_ctx *c, cudaStream_t st) {
-    k_advance<<<blocks_for(c->N), kB, 0, st>>>(geom(c), c->E, c->B, c->Eth, c->u, c->cfg.c, c->cfg.dt, c->cfg.theta,
-                                               c->cfg.lf_on, c->cfg.lf_beta, c->cfg.lf_speed_c, c->phi, c->Enew,
-                                               c->Bnew);
+    // the LF increment D was computed from B^n and u when the right-hand side was built
+    k_advance<<<blocks_for(c->N), kB, 0, st>>>(geom(c), c->E, c->B, c->Eth, c->cfg.c, c->cfg.dt, c->cfg.theta,
+                                               c->cfg.lf_on ? c->dBlf : nullptr, c->phi, c->Enew, c->Bnew);
     GX_LAUNCHED(c);
     if (c->phi) {
         // phi^{n+1} = exp(-dt c_h^2 / c_p^2) (phi^n - dt c_h^2 div B^{n+1}), c_h = 0.8 dx / dt
@@ -702,7 +735,8 @@ int gx_advance(gx_ctx *c, cudaStream_t st) {
             GX_LAUNCHED(c);
         }
     }
-    return GX_OK;
+    // E^{n+1} smoothed by nsmooth_e filter passes (strides 1, 2, 1, ...) in place of LF on E
+    return filter_passes(c, c->Enew, c->cfg.nsmooth_e, true, st);
 }
 
 int gx_copy_uref(gx_ctx *c, int zero, cudaStream_t st);

@@ -223,6 +223,44 @@ def harris(nx=512, ny=256, dx=0.05, ppc=100, mass_ratio=100.0, Ti_over_Te=5.0, n
                     notes=dict(mass_ratio=mass_ratio, ppc=ppc, Te=Te, Ti=Ti, vA=vA, ux=ux, lam=lam, nb=nb))
 
 
+def fast_flow_1d(ppc=100, comoving=1, ns_j=1, lf_on=1, lf_beta=1.0, nsmooth_u=5, gmres_tol=1e-8, seed=12345,
+                 steps=1000):
+    """Uniform fast flow of Sec. 3.2 (solar wind at 1 AU) in the normalised
+    units of this package (c = 1, omega_pi = 1 at the flow density, q_i = m_i = 1).
+
+    Physical inputs as printed: n = 5 cm^-3, u = (400, 0, 0) km/s, B = (0, 0, 5)
+    nT, T_i = 72,000 K, T_e = 2 T_i, m_i/m_e = 100 (proton ion mass), domain
+    160 km in cells of 8 km (20 cells, periodic), dt = 0.0038 s.  Converted with
+    the ion inertial length d_i = c / omega_pi (about 102 km) and 1/omega_pi:
+    lengths / d_i, velocities / c, times * omega_pi, B as v_A / c (v_A = B /
+    sqrt(mu0 n m_p)), per-component thermal spreads sqrt(k T / m) / c.  The
+    particle count per cell is not printed (default 100 per species).  The
+    cell depth along y and z is 1 d_i; it enters only the cell volume.
+    """
+    c_si, mp, kB, e, eps0 = 299792458.0, 1.67262192e-27, 1.380649e-23, 1.602176634e-19, 8.8541878128e-12
+    mu0 = 1.0 / (eps0 * c_si ** 2)
+    n_si, u_si, B_si, Ti, dx_si, L_si, dt_si = 5e6, 4.0e5, 5e-9, 72000.0, 8e3, 160e3, 0.0038
+    Te, mass_ratio = 2.0 * Ti, 100.0
+    wpi = math.sqrt(n_si * e * e / (eps0 * mp))
+    di = c_si / wpi
+    nx = int(round(L_si / dx_si))
+    dx = (dx_si / di, 1.0, 1.0)
+    n = (nx, 1, 1)
+    u = (u_si / c_si, 0.0, 0.0)
+    B = (0.0, 0.0, B_si / math.sqrt(mu0 * n_si * mp) / c_si)
+    vth_i = math.sqrt(kB * Ti / mp) / c_si
+    vth_e = math.sqrt(kB * Te / (mp / mass_ratio)) / c_si
+    dt = dt_si * wpi
+    ions = drifting_species(n, dx, ppc, q=1.0, m=1.0, density=N0, u=u, vth=vth_i, seed=seed, k=0)
+    elec = drifting_species(n, dx, ppc, q=-1.0, m=1.0 / mass_ratio, density=N0, u=u, vth=vth_e, seed=seed, k=1)
+    E, Bc = _uniform_fields(n, 1.0, u, B)
+    return Workload(name=f"fast_flow_{nx}x1_ppc{ppc}", n=n, dx=dx, c=1.0, theta=0.5, dt=dt, comoving=comoving,
+                    lf_on=lf_on, lf_beta=lf_beta, lf_speed_c=0, ns_j=ns_j, nsmooth_u=nsmooth_u,
+                    gmres_tol=gmres_tol, species=[elec, ions], E0=E, B0=Bc, steps=steps,
+                    notes=dict(d_i_km=di / 1e3, omega_pi=wpi, u=list(u), B=list(B), vth_e=vth_e, vth_i=vth_i,
+                               v_A=B[2], mass_ratio=mass_ratio, ppc=ppc))
+
+
 def tophat_1d(n=80, dx=0.01, cfl=0.4, lf_on=1, lf_beta=1.0, theta=0.5):
     """Vacuum light wave with a top-hat E_y = B_z = 1 for |x| < 0.2 on
     [-0.4, 0.4) (shifted to [0, 0.8)), c = 1; the advection test of Sec. 3.1."""
