@@ -58,6 +58,8 @@ class Cfg(C.Structure):
         ("dt", C.c_double),
         ("lf_beta", C.c_double),
         ("gmres_tol", C.c_double),
+        ("bc_cells", C.c_int32),
+        ("_pad", C.c_int32),
     ]
 
     @property
@@ -71,7 +73,7 @@ class Cfg(C.Structure):
 
 def make_cfg(n, dx, *, c=1.0, theta=0.5, dt=0.02, comoving=0, lf_on=0, lf_speed_c=0, lf_beta=1.0,
              ns_j=0, nsmooth_u=5, gmres_tol=1e-12, gmres_restart=50, gmres_maxit=5000, divb_clean=0,
-             nsmooth_e=0) -> Cfg:
+             nsmooth_e=0, bc_cells=0) -> Cfg:
     n = list(n) + [1] * (3 - len(n))
     dx = list(dx) + [1.0] * (3 - len(dx))
     cfg = Cfg()
@@ -84,6 +86,9 @@ def make_cfg(n, dx, *, c=1.0, theta=0.5, dt=0.02, comoving=0, lf_on=0, lf_speed_
     cfg.gmres_tol, cfg.gmres_restart, cfg.gmres_maxit = float(gmres_tol), int(gmres_restart), int(gmres_maxit)
     cfg.divb_clean = int(divb_clean)
     cfg.nsmooth_e = int(nsmooth_e)
+    cfg.bc_cells = int(bc_cells)
+    if cfg.bc_cells and (cfg.divb_clean or 2 * cfg.bc_cells >= cfg.n[0]):
+        raise ValueError("open boundaries: no divergence cleaning, and 2 bc_cells < nx")
     return cfg
 
 
@@ -96,6 +101,9 @@ _SIGS = {
     "or_node_avg": (None, [_P, _D, _D]),
     "or_filter": (None, [_P, _D, C.c_int, C.c_int, C.c_double]),
     "or_lf_b_increment": (None, [_P, _D, _D, _D]),
+    "or_philox4x64": (None, [C.POINTER(C.c_uint64), C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]),
+    "or_bc_sample": (None, [_P, C.c_uint64, C.c_int, C.c_int64, C.c_int, C.c_int, C.c_int, _D, C.c_double,
+                            _D, _D, _D, _D, _D]),
     "or_bulk_moments": (None, [_P, _D, _D, C.c_int64, _I32, _D, _D, _D, _D, _D, _D, _D, _D, _D]),
     "or_bulk_velocity": (None, [_P, _D, _D, _D]),
     "or_deposit": (None, [_P, _D, _D, C.c_int64, _I32, _D, _D, _D, _D, _D, _D, _D, _D, _D, _D, _D, _D]),
@@ -362,6 +370,50 @@ def step(cfg, pl: Plasma, E, B, want=(), phi=None):
     res = {k: v for k, v in outs.items() if v is not None}
     res.update(rc=rc, iters=int(stats[0]), relres=stats[1], maxdisp=stats[2])
     return res
+
+
+def philox4x64(key, ctr):
+    """Philox4x64-10 of (key[2], counter[4]) -> four uint64 words."""
+    k = (C.c_uint64 * 2)(*[int(v) for v in key])
+    c = (C.c_uint64 * 4)(*[int(v) for v in ctr])
+    o = (C.c_uint64 * 4)()
+    lib().or_philox4x64(k, c, o)
+    return [int(o[i]) for i in range(4)]
+
+
+def bc_sample(cfg, seed, species, step, i, j, ppc, u, vth):
+    """The ppc particles that refill boundary cell (i, j) after the push of `step`."""
+    x, y, vx, vy, vz = (np.zeros(ppc) for _ in range(5))
+    lib().or_bc_sample(C.byref(cfg), int(seed), int(species), int(step), int(i), int(j), int(ppc),
+                       _d(_f64(np.asarray(u, float))), float(vth), _d(x), _d(y), _d(vx), _d(vy), _d(vz))
+    return x, y, vx, vy, vz
+
+
+def refill_boundaries(cfg, pl: Plasma, sources, step, seed):
+    """Open x boundaries (cfg.bc_cells per end): drop every particle in a
+    boundary cell and put in fresh ones from each side's plasma state.
+
+    sources[side][s] = dict(n=density, u=(ux, uy, uz), vth=thermal speed, ppc=count) for side 0 (low x)
+    and 1 (high x) and species s; weights n dV / ppc.  Returns the new Plasma; cells are visited in
+    index order (j, then i), species in order, so the result matches the device's bins as a set."""
+    nx, ny, G = cfg.n[0], cfg.n[1], cfg.bc_cells
+    ci = np.floor(pl.x / cfg.dx[0]).astype(np.int64) % nx
+    keep = ~((ci < G) | (ci >= nx - G))
+    parts = {k: [getattr(pl, k)[keep]] for k in ("x", "y", "z", "vx", "vy", "vz", "w")}
+    sp = [pl.sp[keep]]
+    dV = cfg.dx[0] * cfg.dx[1] * cfg.dx[2]
+    for s in range(len(pl.q)):
+        for j in range(ny):
+            for i in list(range(G)) + list(range(nx - G, nx)):
+                src = sources[0 if i < G else 1][s]
+                x, y, vx, vy, vz = bc_sample(cfg, seed, s, step, i, j, src["ppc"], src["u"], src["vth"])
+                for k, v in (("x", x), ("y", y), ("z", np.zeros_like(x)), ("vx", vx), ("vy", vy), ("vz", vz),
+                             ("w", np.full(len(x), src["n"] * dV / src["ppc"]))):
+                    parts[k].append(v)
+                sp.append(np.full(len(x), s, np.int32))
+    cat = {k: np.concatenate(v) for k, v in parts.items()}
+    return Plasma(pl.q, pl.m, np.concatenate(sp), cat["x"], cat["y"], cat["z"], cat["vx"], cat["vy"], cat["vz"],
+                  cat["w"])
 
 
 NET_CHANNELS = (3, 32, 32, 32, 3)

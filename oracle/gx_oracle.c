@@ -78,6 +78,8 @@ typedef struct {
     double dt;
     double lf_beta;        /* MC limiter parameter beta (Eq. 21) */
     double gmres_tol;      /* relative residual target */
+    int32_t bc_cells;      /* open x boundaries: cells per end held at a fixed plasma state (0: periodic) */
+    int32_t _pad;
 } or_cfg;
 
 /* ---------------------------------------------------------------- indexing */
@@ -99,6 +101,21 @@ static inline void unix3(const or_cfg *g, int64_t idx, int *i, int *j, int *k) {
 }
 
 static inline double cell_volume(const or_cfg *g) { return g->dx[0] * g->dx[1] * g->dx[2]; }
+
+/* Open boundaries along x (the shock runs of Sec. 3.3; the paper does not print
+ * the boundary treatment, this is the reading): bc_cells = G cells at each end
+ * hold a fixed plasma state.  Boundary cells: i < G or i >= nx - G.  Boundary
+ * nodes: i <= G - 1 or i >= nx - G + 1, the nodes whose two x-neighbouring
+ * cells are both boundary cells.  E at boundary nodes and B in boundary cells
+ * keep their values; the particles of boundary cells are replaced after every
+ * push (or_bc_sample).  Everything else keeps the periodic indexing: with
+ * G >= 8 no stencil or filter of an interior node reaches across the seam. */
+static inline int bcell(const or_cfg *g, int i) {
+    return g->bc_cells > 0 && (i < g->bc_cells || i >= g->n[0] - g->bc_cells);
+}
+static inline int bnode(const or_cfg *g, int i) {
+    return g->bc_cells > 0 && (i <= g->bc_cells - 1 || i >= g->n[0] - g->bc_cells + 1);
+}
 
 /* ----------------------------------------------------------- shape function */
 
@@ -483,6 +500,14 @@ void or_apply_A(const or_cfg *g, const double *M, const double *kappa, const dou
     }
     free(cC);
     free(cc);
+    if (g->bc_cells) {           /* Dirichlet rows: E stays at its boundary value */
+        for (int64_t nd = 0; nd < N; ++nd) {
+            int i, j, k;
+            unix3(g, nd, &i, &j, &k);
+            if (bnode(g, i))
+                for (int c = 0; c < 3; ++c) out[c * N + nd] = E[c * N + nd];
+        }
+    }
 }
 
 void or_lf_b_increment(const or_cfg *g, const double *Bc, const double *u, double *D);
@@ -538,6 +563,14 @@ void or_rhs(const or_cfg *g, const double *En, const double *Bc, const double *J
         free(EM);
     }
     free(cn);
+    if (g->bc_cells) {           /* Dirichlet rows of the operator: b = E^n there */
+        for (int64_t nd = 0; nd < N; ++nd) {
+            int i, j, k;
+            unix3(g, nd, &i, &j, &k);
+            if (bnode(g, i))
+                for (int c = 0; c < 3; ++c) b[c * N + nd] = En[c * N + nd];
+        }
+    }
 }
 
 /* ------------------------------------------------------------------ solvers */
@@ -722,6 +755,14 @@ void or_lf_b_increment(const or_cfg *g, const double *Bc, const double *u, doubl
         }
     }
     free(F);
+    if (g->bc_cells) {           /* boundary cells keep B: no increment there */
+        for (int64_t c = 0; c < N; ++c) {
+            int i, j, k;
+            unix3(g, c, &i, &j, &k);
+            if (bcell(g, i))
+                for (int comp = 0; comp < 3; ++comp) D[comp * N + c] = 0.0;
+        }
+    }
 }
 
 /* B^{n+1} = B^n - c dt curl_C E^{n+theta} + D (Eq. 5 read with c dt, not
@@ -735,6 +776,14 @@ void or_advance_fields(const or_cfg *g, const double *En, const double *Bc, cons
     or_curl_C(g, Eth, cc);
     or_lf_b_increment(g, Bc, u, D);
     for (int64_t q = 0; q < 3 * N; ++q) Bnew[q] = Bc[q] - g->c * g->dt * cc[q] + D[q];
+    if (g->bc_cells) {           /* boundary cells keep their B */
+        for (int64_t c = 0; c < N; ++c) {
+            int i, j, k;
+            unix3(g, c, &i, &j, &k);
+            if (bcell(g, i))
+                for (int comp = 0; comp < 3; ++comp) Bnew[comp * N + c] = Bc[comp * N + c];
+        }
+    }
     for (int64_t q = 0; q < 3 * N; ++q) Enew[q] = (Eth[q] - (1.0 - g->theta) * En[q]) / g->theta;
     free(cc);
     free(D);
@@ -917,6 +966,66 @@ int or_step(const or_cfg *g, const double *qs, const double *ms, int64_t np, con
     if (stats) { stats[0] = iters; stats[1] = relres; stats[2] = md; }
     free(Bn); free(u); free(rho); free(J); free(M); free(kappa); free(b); free(Eth); free(En1); free(Bn1);
     return rc;
+}
+
+/* ------------------------------------------------ boundary particle source */
+
+/* Philox4x64-10 (Salmon, Moraes, Dror and Shaw, "Parallel random numbers: as
+ * easy as 1, 2, 3", SC 2011): a counter-based generator, the same on the host
+ * and the device, so that both inject identical particles.  Ten rounds of
+ *   (x0, x1, x2, x3) <- (hi(M1 x2) ^ x1 ^ k0, lo(M1 x2), hi(M0 x0) ^ x3 ^ k1, lo(M0 x0))
+ * with the key bumped by the Weyl constants between rounds. */
+static void mulhilo64(uint64_t a, uint64_t b, uint64_t *hi, uint64_t *lo) {
+    const uint64_t a0 = a & 0xffffffffu, a1 = a >> 32, b0 = b & 0xffffffffu, b1 = b >> 32;
+    const uint64_t p00 = a0 * b0, p01 = a0 * b1, p10 = a1 * b0, p11 = a1 * b1;
+    const uint64_t mid = (p00 >> 32) + (p01 & 0xffffffffu) + (p10 & 0xffffffffu);
+    *lo = a * b;
+    *hi = p11 + (p01 >> 32) + (p10 >> 32) + (mid >> 32);
+}
+
+void or_philox4x64(const uint64_t key[2], const uint64_t ctr[4], uint64_t out[4]) {
+    const uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+    const uint64_t W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
+    uint64_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3], k0 = key[0], k1 = key[1];
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) { k0 += W0; k1 += W1; }
+        uint64_t hi0, lo0, hi1, lo1;
+        mulhilo64(M0, x0, &hi0, &lo0);
+        mulhilo64(M1, x2, &hi1, &lo1);
+        const uint64_t y0 = hi1 ^ x1 ^ k0, y2 = hi0 ^ x3 ^ k1;
+        x0 = y0; x1 = lo1; x2 = y2; x3 = lo0;
+    }
+    out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+/* The ppc particles that refill boundary cell (i, j) after the push of step
+ * `step` (reading of the open boundaries): key (seed, species), counter
+ * (step, cell index j nx + i, particle k, 0).  From the four 64-bit words:
+ * offsets in the cell ox = (r0 >> 40) 2^-24, oy = (r1 >> 40) 2^-24 (exact in
+ * FP32), and three normals by the Box-Muller transform of the 24-bit uniforms
+ * u1 = ((r2 >> 40) + 1) 2^-24, u2 = ((r2 >> 16) & 0xffffff) 2^-24,
+ * u3 = ((r3 >> 40) + 1) 2^-24, u4 = ((r3 >> 16) & 0xffffff) 2^-24:
+ *   n0 = sqrt(-2 ln u1) cos(2 pi u2), n1 = sqrt(-2 ln u1) sin(2 pi u2),
+ *   n2 = sqrt(-2 ln u3) cos(2 pi u4);
+ * v = u + vth (n0, n1, n2).  Positions are global: x = (i + ox) dx, y = (j + oy) dy. */
+void or_bc_sample(const or_cfg *g, uint64_t seed, int species, int64_t step, int i, int j, int ppc,
+                  const double u[3], double vth, double *x, double *y, double *vx, double *vy, double *vz) {
+    const uint64_t key[2] = {seed, (uint64_t)species};
+    const double s24 = 1.0 / 16777216.0, twopi = 2.0 * OR_PI;
+    for (int k = 0; k < ppc; ++k) {
+        const uint64_t ctr[4] = {(uint64_t)step, (uint64_t)j * (uint64_t)g->n[0] + (uint64_t)i, (uint64_t)k, 0};
+        uint64_t r[4];
+        or_philox4x64(key, ctr, r);
+        const double ox = (double)(r[0] >> 40) * s24, oy = (double)(r[1] >> 40) * s24;
+        const double u1 = (double)((r[2] >> 40) + 1) * s24, u2 = (double)((r[2] >> 16) & 0xffffffu) * s24;
+        const double u3 = (double)((r[3] >> 40) + 1) * s24, u4 = (double)((r[3] >> 16) & 0xffffffu) * s24;
+        const double ra = sqrt(-2.0 * log(u1)), rb = sqrt(-2.0 * log(u3));
+        x[k] = (i + ox) * g->dx[0];
+        y[k] = g->n[1] > 1 ? (j + oy) * g->dx[1] : 0.0;
+        vx[k] = u[0] + vth * ra * cos(twopi * u2);
+        vy[k] = u[1] + vth * ra * sin(twopi * u2);
+        vz[k] = u[2] + vth * rb * cos(twopi * u4);
+    }
 }
 
 /* ------------------------------------------------- learned preconditioner net */

@@ -261,6 +261,85 @@ def fast_flow_1d(ppc=100, comoving=1, ns_j=1, lf_on=1, lf_beta=1.0, nsmooth_u=5,
                                v_A=B[2], mass_ratio=mass_ratio, ppc=ppc))
 
 
+def _state(rho_amu_cc, u_kms, B_nT, pe_npa, pi_npa, c_kms, mass_ratio):
+    """One plasma state of the shock runs in the units of this package with the
+    reduced light speed c_kms as velocity unit and the upstream ion inertial
+    length as length unit (density unit: the upstream density)."""
+    mp, kB = 1.67262192e-27, 1.380649e-23
+    n_si = rho_amu_cc * 1e6                     # protons: 1 amu each
+    te = pe_npa * 1e-9 / n_si                   # k T_e in J
+    ti = pi_npa * 1e-9 / n_si
+    return dict(n_si=n_si, u=[v / c_kms for v in u_kms],
+                vth_e=math.sqrt(te / (mp / mass_ratio)) / (c_kms * 1e3),
+                vth_i=math.sqrt(ti / mp) / (c_kms * 1e3), B_nT=list(B_nT))
+
+
+def shock_1d(dx=0.4, length=None, ppc=100, bc_cells=8, seed=12345, cfl=0.2, steps=200, comoving=1, ns_j=1,
+             lf_on=1, lf_beta=1.0, gmres_tol=1e-8):
+    """1D quasi-parallel shock of Sec. 3.3 from the printed upstream and
+    downstream states (theta_Bn = 30 deg, p_e/p_i = 2), m_i/m_e = 25, reduced
+    light speed c = 3000 km/s, domain [-1.8e4, 3.2e4] km with the shock at x = 0
+    (downstream on the low-x side; the upstream flows in along -x).
+
+    Units: the upstream ion inertial length d_i = 133 km, velocities over the
+    reduced c, densities over the upstream density (omega_pi = c / d_i there).
+    B is v_A / c with v_A = |B| / sqrt(mu0 n m_p) per component.  dt from
+    CFL 0.2 on the fastest speed of the two states, |u| + 3 vth_e (the paper
+    quotes CFL 0.2 without the speed it uses).  `length` (in d_i) shortens the
+    domain around the shock for tests, keeping the printed proportion of the
+    two sides.  bc_cells cells at each end hold the two states (open
+    boundaries, refilled after every push from counter-based draws keyed by
+    seed); ppc per species (not printed)."""
+    c_kms, mass_ratio, di_km = 3000.0, 25.0, 133.0
+    up = _state(3.0, (-440.6, 0.0, 0.0), (4.33, 2.5, 0.0), 0.00995, 0.004975, c_kms, mass_ratio)
+    dn = _state(10.9, (-121.3, -10.86, 0.0), (4.33, 9.47, 0.0), 0.4588, 0.2294, c_kms, mass_ratio)
+    mu0, mp = 4e-7 * math.pi, 1.67262192e-27
+    n_up = up["n_si"]
+    for st in (up, dn):
+        st["n"] = st["n_si"] / n_up * N0
+        st["B"] = [b * 1e-9 / math.sqrt(mu0 * n_up * mp) / (c_kms * 1e3) for b in st["B_nT"]]
+    L_full = (3.2e4 + 1.8e4) / di_km
+    L = L_full if length is None else float(length)
+    nx = int(round(L / dx))
+    x_shock = 1.8e4 / 5.0e4 * nx * dx
+    vmax = max(abs(up["u"][0]) + 3 * up["vth_e"], math.hypot(dn["u"][0], dn["u"][1]) + 3 * dn["vth_e"])
+    dt = cfl * dx / vmax
+    n = (nx, 1, 1)
+    dxs = (dx, 1.0, 1.0)
+    rng_e, rng_i = _rng(seed, 1), _rng(seed, 0)
+    xc = (np.arange(nx) + 0.5) * dx
+    down_cell = xc < x_shock
+    species = []
+    for k, (rng, q, m, key) in enumerate(((rng_e, -1.0, 1.0 / mass_ratio, "vth_e"), (rng_i, 1.0, 1.0, "vth_i"))):
+        x, y, z = _uniform_positions(rng, n, dxs, ppc)
+        cell = np.floor(x / dx).astype(np.int64)
+        v = rng.standard_normal((3, x.size))
+        w = np.empty(x.size, np.float32)
+        vel = []
+        for d in range(3):
+            ud = np.where(down_cell[cell], dn["u"][d], up["u"][d])
+            vt = np.where(down_cell[cell], dn[key], up[key])
+            vel.append((ud + vt * v[d]).astype(np.float32))
+        w[:] = np.where(down_cell[cell], dn["n"], up["n"]) * dx / ppc
+        species.append(dict(q=q, m=m, x=x, y=np.zeros_like(x), z=z, vx=vel[0], vy=vel[1], vz=vel[2], w=w))
+    Bc = np.zeros((3, 1, 1, nx))
+    E = np.zeros((3, 1, 1, nx))
+    xn = np.arange(nx) * dx
+    for d in range(3):
+        Bc[d, 0, 0] = np.where(down_cell, dn["B"][d], up["B"][d])
+    for st, sel in ((dn, xn < x_shock), (up, xn >= x_shock)):
+        u32 = np.asarray(st["u"], np.float32).astype(np.float64)
+        Em = -np.cross(u32, np.asarray(st["B"]))
+        for d in range(3):
+            E[d, 0, 0, sel] = Em[d]
+    sources = [[dict(n=st["n"], u=st["u"], vth=st[key], ppc=ppc) for key in ("vth_e", "vth_i")] for st in (dn, up)]
+    return Workload(name=f"shock_1d_{nx}x1_dx{dx}", n=n, dx=dxs, c=1.0, theta=0.5, dt=dt, comoving=comoving,
+                    lf_on=lf_on, lf_beta=lf_beta, lf_speed_c=0, ns_j=ns_j, nsmooth_u=5, gmres_tol=gmres_tol,
+                    species=species, E0=E, B0=Bc, steps=steps,
+                    notes=dict(bc=dict(cells=bc_cells, seed=seed, sources=sources), up=up, down=dn,
+                               x_shock=x_shock, mass_ratio=mass_ratio))
+
+
 def tophat_1d(n=80, dx=0.01, cfl=0.4, lf_on=1, lf_beta=1.0, theta=0.5):
     """Vacuum light wave with a top-hat E_y = B_z = 1 for |x| < 0.2 on
     [-0.4, 0.4) (shifted to [0, 0.8)), c = 1; the advection test of Sec. 3.1."""
