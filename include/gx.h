@@ -95,7 +95,18 @@ typedef struct gx_ctx gx_ctx;
  *                 term on B stays as lf_on says.  0: off.  At most 10 passes.
  *   bin_slack     capacity of a cell's particle bin relative to the largest
  *                 initial count (>= 1.2; the bins grow automatically when a
- *                 step finds one filled above 90 %). */
+ *                 step finds one filled above 90 %).
+ *   bc_cells      0: periodic along x.  G >= 8: open x boundaries (the shock
+ *                 runs of Sec. 3.3): the G cells at each end hold a fixed
+ *                 plasma state.  E at the nodes whose two x-neighbouring cells
+ *                 are boundary cells and B in boundary cells keep their values
+ *                 (Dirichlet rows in the E solve); after every push the
+ *                 particles of every boundary cell are replaced by ppc fresh
+ *                 particles per species drawn from that side's source (see
+ *                 gx_boundary_source).  y stays periodic.  Not with divb_clean;
+ *                 2 G < nx.
+ *   bc_seed       key of the boundary draws: Philox4x64-10 with key (bc_seed,
+ *                 species) and counter (step, cell index, particle, 0). */
 typedef struct {
     int32_t n[3];
     int32_t comoving;
@@ -116,6 +127,9 @@ typedef struct {
     double bin_slack;
     int32_t divb_clean;
     int32_t nsmooth_e;
+    int32_t bc_cells;
+    int32_t reserved;
+    uint64_t bc_seed;
 } gx_config;
 
 typedef struct {
@@ -166,6 +180,18 @@ int gx_species_add(gx_ctx *ctx, double q, double m, int64_t n,
 
 /* Set E (nodes) and B (cell centres), each FP64 [3][nz][ny][nx]. */
 int gx_fields_set(gx_ctx *ctx, const double *E, const double *B, int ptr_is_device);
+
+/* Plasma state of an open boundary (cfg.bc_cells > 0): side 0 is low x, side
+ * 1 high x; for species `species` (already added): density n (particles of
+ * weight n dV / ppc), bulk velocity u[3], per-component thermal speed vth, and
+ * ppc particles per boundary cell (1 <= ppc <= 4096).  Every species needs a
+ * source on both sides before the first push (GX_ESTATE otherwise).  The draw
+ * of particle k of cell (i, j) after push number t (1, 2, ...) takes the four
+ * Philox words r of counter (t, j nx + i, k, 0): cell offsets (r0 >> 40) 2^-24
+ * and (r1 >> 40) 2^-24 (0 along y in 1D), and v = u + vth (n0, n1, n2) from the
+ * Box-Muller transform of the 24-bit uniforms ((r2 >> 40) + 1) 2^-24,
+ * ((r2 >> 16) & 0xffffff) 2^-24 (n0, n1) and the same of r3 (n2). */
+int gx_boundary_source(gx_ctx *ctx, int side, int species, double n, const double *u, double vth, int ppc);
 
 /* ------------------------------------------------------------- hot path */
 

@@ -46,6 +46,9 @@ class Config(C.Structure):
         ("bin_slack", C.c_double),
         ("divb_clean", C.c_int32),
         ("nsmooth_e", C.c_int32),
+        ("bc_cells", C.c_int32),
+        ("reserved", C.c_int32),
+        ("bc_seed", C.c_uint64),
     ]
 
 
@@ -76,6 +79,7 @@ _SIGS = {
     "gx_species_add": (C.c_int, [_CTX, C.c_double, C.c_double, C.c_int64, _V, _V, _V, _V, _V, _V, _V, C.c_int,
                                  C.POINTER(C.c_int)]),
     "gx_fields_set": (C.c_int, [_CTX, _V, _V, C.c_int]),
+    "gx_boundary_source": (C.c_int, [_CTX, C.c_int, C.c_int, C.c_double, C.POINTER(C.c_double), C.c_double, C.c_int]),
     "gx_deposit": (C.c_int, [_CTX, _V]),
     "gx_field_solve": (C.c_int, [_CTX, _V, C.POINTER(SolveStats)]),
     "gx_push_and_deposit": (C.c_int, [_CTX, _V]),
@@ -149,7 +153,8 @@ def _stream(stream):
 
 def make_config(n, dx, *, c=1.0, theta=0.5, dt=0.02, comoving=1, lf_on=1, lf_speed_c=0, lf_beta=1.0, ns_j=0,
                 nsmooth_u=5, gmres_tol=1e-8, gmres_restart=50, gmres_maxit=2000, precond=GX_PRECOND_NONE,
-                track_ids=0, bin_slack=1.6, divb_clean=0, nsmooth_e=0) -> Config:
+                track_ids=0, bin_slack=1.6, divb_clean=0, nsmooth_e=0, bc_cells=0,
+                bc_seed=0) -> Config:
     n = list(n) + [1] * (3 - len(n))
     dx = list(dx) + [1.0] * (3 - len(dx))
     cfg = Config()
@@ -163,6 +168,8 @@ def make_config(n, dx, *, c=1.0, theta=0.5, dt=0.02, comoving=1, lf_on=1, lf_spe
     cfg.precond, cfg.track_ids, cfg.bin_slack = int(precond), int(track_ids), float(bin_slack)
     cfg.divb_clean = int(divb_clean)
     cfg.nsmooth_e = int(nsmooth_e)
+    cfg.bc_cells = int(bc_cells)
+    cfg.bc_seed = int(bc_seed)
     return cfg
 
 
@@ -207,6 +214,11 @@ class Context:
     def fields_set(self, E, B):
         (pe, de), (pb, db) = _ptr(E), _ptr(B)
         self._check(lib().gx_fields_set(self.h, pe, pb, max(de, db)))
+
+    def boundary_source(self, side, species, n, u, vth, ppc):
+        """Plasma state of open boundary `side` (0: low x, 1: high x) for a species."""
+        uu = (C.c_double * 3)(*[float(v) for v in u])
+        self._check(lib().gx_boundary_source(self.h, int(side), int(species), float(n), uu, float(vth), int(ppc)))
 
     def deposit(self, stream=None):
         self._check(lib().gx_deposit(self.h, _stream(stream)))
@@ -337,12 +349,16 @@ class Context:
 
 def from_workload(wl, *, track_ids=0, precond=GX_PRECOND_NONE, gmres_tol=None, bin_slack=1.6, gmres_restart=50,
                   divb_clean=0):
-    """Create a context from a workloads.Workload (inputs copied from host)."""
+    """Create a context from a workloads.Workload (inputs copied from host); a
+    workload with open boundaries (notes["bc"]) also gets its boundary sources."""
     cfg = make_config(wl.n, wl.dx, c=wl.c, theta=wl.theta, dt=wl.dt, comoving=wl.comoving, lf_on=wl.lf_on,
                       lf_speed_c=wl.lf_speed_c, lf_beta=wl.lf_beta, ns_j=wl.ns_j, nsmooth_u=wl.nsmooth_u,
                       gmres_tol=wl.gmres_tol if gmres_tol is None else gmres_tol, precond=precond,
                       track_ids=track_ids, bin_slack=bin_slack, gmres_restart=gmres_restart,
                       divb_clean=divb_clean)
+    bc = wl.notes.get("bc") if isinstance(wl.notes, dict) else None
+    if bc:
+        cfg.bc_cells, cfg.bc_seed = int(bc["cells"]), int(bc["seed"])
     ctx = Context(cfg)
     for s in wl.species:
         ctx.species_add(s["q"], s["m"], np.ascontiguousarray(s["x"], np.float64),
@@ -350,4 +366,8 @@ def from_workload(wl, *, track_ids=0, precond=GX_PRECOND_NONE, gmres_tol=None, b
                         np.ascontiguousarray(s["vx"], np.float32), np.ascontiguousarray(s["vy"], np.float32),
                         np.ascontiguousarray(s["vz"], np.float32), np.ascontiguousarray(s["w"], np.float32))
     ctx.fields_set(np.ascontiguousarray(wl.E0, np.float64), np.ascontiguousarray(wl.B0, np.float64))
+    if bc:
+        for side in range(2):
+            for s, src in enumerate(bc["sources"][side]):
+                ctx.boundary_source(side, s, src["n"], src["u"], src["vth"], src["ppc"])
     return ctx

@@ -225,6 +225,9 @@ int gx_create(const gx_config *cfg, gx_ctx **out) {
     if (cfg->nsmooth_u < 0 || cfg->ns_j < 0 || cfg->nsmooth_e < 0)
         return fail(GX_EINVAL, "smoothing passes must be >= 0");
     if (cfg->nsmooth_e > 10) return fail(GX_EINVAL, "nsmooth_e must be <= 10");
+    if (cfg->bc_cells < 0 || (cfg->bc_cells > 0 && (cfg->bc_cells < 8 || 2 * cfg->bc_cells >= cfg->n[0])))
+        return fail(GX_EINVAL, "bc_cells must be 0 or >= 8 with 2 bc_cells < nx");
+    if (cfg->bc_cells > 0 && cfg->divb_clean) return fail(GX_EINVAL, "open boundaries without divb_clean");
     if (cfg->lf_on && cfg->lf_beta < 0) return fail(GX_EINVAL, "lf_beta must be >= 0");
     c->dim = 2;
     c->N = (int64_t)c->n[0] * c->n[1] * c->n[2];
@@ -323,6 +326,24 @@ int gx_fields_set(gx_ctx *c, const double *E, const double *B, int ptr_is_device
     c->moments_valid = 0;
     c->pending = 0;
     c->have_eth = 0;
+    return GX_OK;
+}
+
+int gx_boundary_source(gx_ctx *c, int side, int species, double n, const double *u, double vth, int ppc) {
+    if (!c) return GX_EINVAL;
+    if (c->cfg.bc_cells <= 0) { c->err = "gx_boundary_source needs cfg.bc_cells > 0"; return GX_EINVAL; }
+    if (side < 0 || side > 1 || species < 0 || species >= c->nspecies || !u || !(n >= 0.0) || !(vth >= 0.0) ||
+        ppc < 1 || ppc > 4096) {
+        c->err = "gx_boundary_source: side 0/1, an existing species, n >= 0, vth >= 0, 1 <= ppc <= 4096";
+        return GX_EINVAL;
+    }
+    BcSource &b = c->bsrc[side][species];
+    b.n = n;
+    b.u[0] = u[0]; b.u[1] = u[1]; b.u[2] = u[2];
+    b.vth = vth;
+    b.ppc = ppc;
+    // the refilled bins must hold ppc particles
+    if (ppc > c->sp[species].cap) TRY(gx_regrow_bins(c, species, ppc + ppc / 2, 0));
     return GX_OK;
 }
 

@@ -326,6 +326,10 @@ __global__ void k_jacobi(OpArgs a, double *jd, float *jd32) {
                 A[4 * c] += d;
             }
         }
+        if (g.bnode((int)(q % g.nx))) {   // Dirichlet row of an open boundary: the identity
+#pragma unroll
+            for (int e = 0; e < 9; ++e) A[e] = (e % 4 == 0) ? 1.0 : 0.0;
+        }
         const double c00 = A[4] * A[8] - A[5] * A[7], c01 = A[5] * A[6] - A[3] * A[8], c02 = A[3] * A[7] - A[4] * A[6];
         const double det = A[0] * c00 + A[1] * c01 + A[2] * c02;
         const double id = 1.0 / det;
@@ -402,6 +406,10 @@ __global__ void k_rhs(G2 g, const double *__restrict__ E, const double *__restri
             }
 #pragma unroll
             for (int r = 0; r < 3; ++r) out[r] = fma(mf, m[r], out[r]);
+        }
+        if (g.bnode(i)) {   // Dirichlet row: b = E^n
+#pragma unroll
+            for (int k = 0; k < 3; ++k) out[k] = E[k * N + q];
         }
 #pragma unroll
         for (int k = 0; k < 3; ++k) b[k * N + q] = out[k];
@@ -487,6 +495,7 @@ __global__ void k_lf_b(G2 g, const double *__restrict__ B, const double *__restr
                 }
             }
         }
+        if (g.bcell(i)) dn[0] = dn[1] = dn[2] = 0.0;   // boundary cells keep B
 #pragma unroll
         for (int k = 0; k < 3; ++k) D[k * N + q] = dn[k];
     }
@@ -515,6 +524,10 @@ __global__ void k_advance(G2 g, const double *__restrict__ E, const double *__re
         if (phi) {   // div B cleaning (Sec. 1.3): - dt grad phi^n, central over cells (hx = 1 / (2 dx))
             if (g.nx > 1) bn[0] -= dt * (phi[g.id(i + 1, j)] - phi[g.id(i - 1, j)]) * g.hx;
             if (g.ny > 1) bn[1] -= dt * (phi[g.id(i, j + 1)] - phi[g.id(i, j - 1)]) * g.hy;
+        }
+        if (g.bcell(i)) {   // open boundary: B keeps its value
+#pragma unroll
+            for (int k = 0; k < 3; ++k) bn[k] = B[k * N + q];
         }
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
@@ -577,7 +590,7 @@ __global__ void k_diag_particles(int64_t ncell, int cap, const int *cnt, const f
 }
 
 G2 geom(const gx_ctx *c) {
-    return G2{c->n[0], c->n[1], c->cfg.dx[0], c->cfg.dx[1], 0.5 / c->cfg.dx[0], 0.5 / c->cfg.dx[1]};
+    return G2{c->n[0], c->n[1], c->cfg.dx[0], c->cfg.dx[1], 0.5 / c->cfg.dx[0], 0.5 / c->cfg.dx[1], c->cfg.bc_cells};
 }
 
 SpecK speck(const gx_ctx *c) {

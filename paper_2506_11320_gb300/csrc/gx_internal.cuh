@@ -72,6 +72,11 @@ struct Species {
     int *cnt[2] = {};                   // particles per cell, per copy
 };
 
+struct BcSource {                       // plasma state of an open boundary, per species
+    double n = 0, u[3] = {0, 0, 0}, vth = 0;
+    int ppc = 0;
+};
+
 struct DevFlags {                       // written by kernels, read by the host
     int cfl;                            // a particle moved more than one cell
     int overflow;                       // a bin overflowed (particle dropped)
@@ -106,6 +111,8 @@ struct gx_ctx {
     // particles
     int nspecies = 0;
     Species sp[GX_MAX_SPECIES];
+    BcSource bsrc[2][GX_MAX_SPECIES];           // open-boundary states [side][species]
+    int64_t npush = 0;                          // pushes done: the counter of the boundary draws
     int cur = 0;                                // which copy is current
     int64_t np_total = 0;
 

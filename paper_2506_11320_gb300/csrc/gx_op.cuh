@@ -28,10 +28,15 @@ struct G2 {
     int nx, ny;
     double dx, dy;
     double hx, hy;          // 1 / (2 dx), 1 / (2 dy): the averaged differences' factors
+    int bc;                 // open x boundaries: cells per end held fixed (0: periodic)
     __device__ __forceinline__ int64_t id(int i, int j) const {
         return (int64_t)gx_wr(i, nx) + (int64_t)nx * gx_wr(j, ny);
     }
     __device__ __forceinline__ int64_t N() const { return (int64_t)nx * ny; }
+    // boundary cells: i < bc or i >= nx - bc; boundary nodes: both x-neighbouring cells are
+    // boundary cells (i <= bc - 1 or i >= nx - bc + 1)
+    __device__ __forceinline__ bool bcell(int i) const { return bc > 0 && (i < bc || i >= nx - bc); }
+    __device__ __forceinline__ bool bnode(int i) const { return bc > 0 && (i <= bc - 1 || i >= nx - bc + 1); }
 };
 
 struct OpArgs {
@@ -105,5 +110,9 @@ __device__ __forceinline__ void gx_apply_A_node(const OpArgs &a, const double *_
             if (g.ny > 1)
                 out[c] -= a.lfy * (ky[q] * (v[c][2][1] - v[c][1][1]) - ky[ym] * (v[c][1][1] - v[c][0][1]));
         }
+    }
+    if (g.bnode(i)) {   // Dirichlet row of an open boundary: E stays at its value
+#pragma unroll
+        for (int c = 0; c < 3; ++c) out[c] = v[c][1][1];
     }
 }

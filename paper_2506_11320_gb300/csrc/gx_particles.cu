@@ -267,6 +267,92 @@ __device__ __forceinline__ int seg_word(int w, int cap, int arrivals_only) {
     return arrivals_only ? (int)((unsigned)c & 0xffff0000u) : c;
 }
 
+// ------------------------------------------------------------ open boundaries
+// Philox4x64-10 (Salmon, Moraes, Dror and Shaw, SC 2011): ten rounds of
+// (x0, x1, x2, x3) <- (hi(M1 x2) ^ x1 ^ k0, lo(M1 x2), hi(M0 x0) ^ x3 ^ k1, lo(M0 x0)),
+// the key bumped by the Weyl constants between rounds.  The host-side test
+// code implements the same generator, so both inject identical particles.
+__device__ __forceinline__ void philox4x64(uint64_t k0, uint64_t k1, uint64_t x[4]) {
+    const uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+    const uint64_t W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) { k0 += W0; k1 += W1; }
+        const uint64_t hi0 = __umul64hi(M0, x[0]), lo0 = M0 * x[0];
+        const uint64_t hi1 = __umul64hi(M1, x[2]), lo1 = M1 * x[2];
+        const uint64_t y0 = hi1 ^ x[1] ^ k0, y2 = hi0 ^ x[3] ^ k1;
+        x[0] = y0; x[1] = lo1; x[2] = y2; x[3] = lo0;
+    }
+}
+
+struct BcArgs {
+    int nx, ny, G, cap;
+    int64_t N;
+    uint64_t seed, step;
+    int species, track;
+    float bc;                    // beta / c of the species (alpha)
+    int ppc[2];                  // per side (0: low x, 1: high x)
+    float w[2], vth[2], u[2][3];
+    float4 *bins;                // the current copy (after the push)
+    int *cnt;
+    float *rec;                  // [112][N] of the species
+    const float4 *dB, *dU;       // node B^{n+1} and u_ref of the deposit
+};
+
+// One CTA per boundary cell: replace its particles by the side's fresh draws
+// (key (seed, species), counter (step, cell, k, 0); offsets from the top 24
+// bits of words 0 and 1, three normals by Box-Muller from 24-bit uniforms of
+// words 2 and 3), deposit them with the push's deposit arithmetic and
+// overwrite the cell's record and count.
+__global__ void __launch_bounds__(128) k_bc_refill(BcArgs a) {
+    __shared__ float red[4][Rec<2>::SIZE];
+    const int t = blockIdx.x, G2c = 2 * a.G;
+    const int j = t / G2c, r = t % G2c;
+    const int side = r < a.G ? 0 : 1;
+    const int i = r < a.G ? r : a.nx - G2c + r;
+    const int64_t cell = (int64_t)j * a.nx + i;
+    int64_t nd[4];
+    corner_nodes(i, j, a.nx, a.ny, nd);
+    float4 cB[4], cU[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) { cB[c] = a.dB[nd[c]]; cU[c] = a.dU[nd[c]]; }
+    const int ppc = a.ppc[side];
+    const float w = a.w[side], vth = a.vth[side];
+    const float s24 = 1.0f / 16777216.0f;
+    RegAcc acc;
+    acc.zero();
+    for (int k = threadIdx.x; k < ppc; k += blockDim.x) {
+        uint64_t x[4] = {a.step, (uint64_t)cell, (uint64_t)k, 0ull};
+        philox4x64(a.seed, (uint64_t)a.species, x);
+        const float ox = (float)(x[0] >> 40) * s24;
+        const float oy = a.ny > 1 ? (float)(x[1] >> 40) * s24 : 0.f;
+        const float u1 = (float)((x[2] >> 40) + 1) * s24, u2 = (float)((x[2] >> 16) & 0xffffffu) * s24;
+        const float u3 = (float)((x[3] >> 40) + 1) * s24, u4 = (float)((x[3] >> 16) & 0xffffffu) * s24;
+        const float ra = sqrtf(-2.f * logf(u1)), rb = sqrtf(-2.f * logf(u3));
+        float sn, cs;
+        sincospif(2.f * u2, &sn, &cs);
+        const float vx = a.u[side][0] + vth * ra * cs;
+        const float vy = a.u[side][1] + vth * ra * sn;
+        const float vz = a.u[side][2] + vth * rb * cospif(2.f * u4);
+        const size_t o = (size_t)cell * a.cap + k;
+        a.bins[2 * o] = make_float4(ox, oy, vx, vy);
+        a.bins[2 * o + 1] = make_float4(vz, w, __int_as_float(a.track ? -1 : 0), 0.f);
+        deposit_one(acc, ox, oy, vx, vy, vz, w, cB, cU, a.bc);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < Rec<2>::SIZE; ++k) {
+        float v = acc.get(k);
+#pragma unroll
+        for (int m = 16; m > 0; m >>= 1) v += __shfl_xor_sync(kFull, v, m);
+        if (lane == 0) red[warp][k] = v;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < Rec<2>::SIZE; k += blockDim.x)
+        a.rec[(size_t)k * a.N + cell] = (red[0][k] + red[1][k]) + (red[2][k] + red[3][k]);
+    if (threadIdx.x == 0) a.cnt[cell] = ppc;          // front segment only
+}
+
 // ------------------------------------------------------------ fused kernel
 template <bool PUSH>
 __global__ void __launch_bounds__(kThreads, 1) k_pd(P2 p) {
@@ -777,6 +863,27 @@ static int launch_pd(gx_ctx *c, bool push, cudaStream_t st) {
             q.mE = nullptr; q.mB = nullptr;
             k_pd<false><<<grid, kThreads, pd_smem_bytes(), st>>>(q);
             GX_LAUNCHED(c);
+            if (c->cfg.bc_cells > 0) {
+                // open boundaries: the boundary cells' particles are replaced
+                BcArgs b{};
+                b.nx = c->n[0]; b.ny = c->n[1]; b.G = c->cfg.bc_cells; b.cap = S.cap; b.N = c->N;
+                b.seed = c->cfg.bc_seed; b.step = (uint64_t)(c->npush + 1); b.species = s;
+                b.track = c->cfg.track_ids;
+                b.bc = p.bc;
+                const double dV = c->cfg.dx[0] * c->cfg.dx[1] * c->cfg.dx[2];
+                for (int sd = 0; sd < 2; ++sd) {
+                    const BcSource &src = c->bsrc[sd][s];
+                    if (src.ppc < 1) { c->err = "open boundaries need gx_boundary_source for every species"; return GX_ESTATE; }
+                    if (src.ppc > S.cap) { c->err = "boundary ppc above the bin capacity"; return GX_EOVERFLOW; }
+                    b.ppc[sd] = src.ppc;
+                    b.w[sd] = (float)(src.n * dV / src.ppc);
+                    b.vth[sd] = (float)src.vth;
+                    for (int d = 0; d < 3; ++d) b.u[sd][d] = (float)src.u[d];
+                }
+                b.bins = p.out; b.cnt = p.cnt_out; b.rec = p.rec; b.dB = p.dB; b.dU = p.dU;
+                k_bc_refill<<<(unsigned)(2 * b.G * b.ny), 128, 0, st>>>(b);
+                GX_LAUNCHED(c);
+            }
         } else {
             p.mE = nullptr; p.mB = nullptr; p.dB = c->nB; p.dU = c->nUref;
             k_pd<false><<<grid, kThreads, pd_smem_bytes(), st>>>(p);
@@ -785,6 +892,7 @@ static int launch_pd(gx_ctx *c, bool push, cudaStream_t st) {
     }
     if (push) {
         c->cur = nxt;
+        c->npush++;
         GX_CHECK(c, cudaMemsetAsync(&c->dflags->maxcount, 0, sizeof(int), st));
         for (int s = 0; s < c->nspecies; ++s) {
             k_max_count<<<grid_for(c->N), 256, 0, st>>>(c->sp[s].cnt[c->cur], c->N, c->sp[s].cap, c->dflags);
