@@ -203,6 +203,39 @@ def run_reference(args):
     return 0
 
 
+def run_shock(gx, warmup, steps, barrier, dist, world):
+    """Push+deposit throughput on the shock-shaped plasma: the paper's quasi-
+    parallel shock (printed states, open boundaries refilled every step) over 940
+    x 8 cells of 0.4 d_i with 256 particles per cell and species (3.85 M
+    particles, the size of a 1024 x 8-cell, 256-ppc shock), timed like the main
+    workload (library CUDA events over push, refill and moments)."""
+    import torch
+    wl = workloads.shock_1d("parallel", ny=8, ppc=256)
+    ctx = gx.from_workload(wl)
+    for _ in range(warmup):
+        ctx.step(1, allow_noconv=True)
+    ctx.timers(reset=True)
+    barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for _ in range(steps):
+        ctx.step(1, allow_noconv=True)
+    ev1.record()
+    barrier()
+    tm = ctx.timers(reset=True)
+    npart = sum(ctx.species_count(s) for s in range(len(wl.species)))
+    ctx.close()
+    vals = torch.tensor([(tm["push_ms"] + tm["moments_ms"]) / steps, ev0.elapsed_time(ev1) / steps],
+                        dtype=torch.float64, device="cuda")
+    if dist:
+        dist.all_reduce(vals, op=dist.ReduceOp.MAX)
+    pd_ms, step_ms = float(vals[0]), float(vals[1])
+    return {"value": world * npart / (pd_ms / 1000.0), "unit": UNIT, "push_deposit_ms_per_step": pd_ms,
+            "ms_per_step": step_ms, "particles": npart,
+            "workload": f"{wl.name}: the paper's 1D quasi-parallel shock (printed up/downstream states, M_A 7, "
+                        f"m_i/m_e 25, c = 3000 km/s) on {wl.n[0]}x{wl.n[1]} cells, open x boundaries"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -213,6 +246,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-precond", action="store_true")
+    ap.add_argument("--no-shock", action="store_true")
     ap.add_argument("--precond-workload", default="harris_1024x512",
                     help="plasma of the learned-vs-plain GMRES comparison: harris_1024x512 (the learned-"
                          "preconditioner configuration: Harris reconnection, 1024x512 cells, 100 ppc/species) "
@@ -307,6 +341,11 @@ def main():
         solve_cmp["cells"] = list(pwl.n[:2])
         del pwl
 
+    # ------------------------------------------------------- shock-shaped plasma
+    shock = None
+    if not args.no_shock:
+        shock = run_shock(gx, args.warmup, args.steps, barrier, dist, world)
+
     # ------------------------------------------------------- end to end (host buffers)
     e2e = None
     if not args.no_e2e:
@@ -338,6 +377,7 @@ def main():
             "gmres_ms_per_step": solve_ms, "gmres_iters_per_step": statistics.mean(iters),
             "wall_ms_per_step": 1000 * wall / args.steps,
             "gmres_learned_vs_plain": solve_cmp,
+            "shock": shock,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "gpu_launches": int(tm["launches"]),
         }

@@ -474,7 +474,15 @@ int gx_fgmres(gx_ctx *c, cudaStream_t st) {
     const int64_t n = 3 * c->N;
     const int pc = c->cfg.precond;
     int rc;
-    if (pc == GX_PRECOND_JACOBI || pc == GX_PRECOND_NET) { rc = gx_build_jacobi(c, st); if (rc) return rc; }
+    // the learned preconditioner reads only the FP32 inverse; pair collection and the
+    // Jacobi preconditioner need the FP64 one
+    if (pc == GX_PRECOND_JACOBI || (pc == GX_PRECOND_NET && gx_net_collecting(c))) {
+        rc = gx_build_jacobi(c, st);
+        if (rc) return rc;
+    } else if (pc == GX_PRECOND_NET) {
+        rc = gx_build_jacobi32(c, st);
+        if (rc) return rc;
+    }
     const bool use_net = pc == GX_PRECOND_NET;
     const size_t smem = use_net ? (size_t)kNetSmemBytes : 0;
     static int grids[2] = {0, 0};

@@ -330,6 +330,20 @@ __global__ void k_jacobi(OpArgs a, double *jd, float *jd32) {
 #pragma unroll
             for (int e = 0; e < 9; ++e) A[e] = (e % 4 == 0) ? 1.0 : 0.0;
         }
+        if (!jd) {
+            // FP32 inverse only (the learned preconditioner's base): the block is
+            // assembled in FP64 and inverted at the FP32 rate
+            float F[9];
+#pragma unroll
+            for (int e = 0; e < 9; ++e) F[e] = (float)A[e];
+            const float f00 = F[4] * F[8] - F[5] * F[7], f01 = F[5] * F[6] - F[3] * F[8], f02 = F[3] * F[7] - F[4] * F[6];
+            const float fid = 1.0f / (F[0] * f00 + F[1] * f01 + F[2] * f02);
+            float *o32 = jd32 + (size_t)q * 9;
+            o32[0] = f00 * fid; o32[1] = (F[2] * F[7] - F[1] * F[8]) * fid; o32[2] = (F[1] * F[5] - F[2] * F[4]) * fid;
+            o32[3] = f01 * fid; o32[4] = (F[0] * F[8] - F[2] * F[6]) * fid; o32[5] = (F[2] * F[3] - F[0] * F[5]) * fid;
+            o32[6] = f02 * fid; o32[7] = (F[1] * F[6] - F[0] * F[7]) * fid; o32[8] = (F[0] * F[4] - F[1] * F[3]) * fid;
+            continue;
+        }
         const double c00 = A[4] * A[8] - A[5] * A[7], c01 = A[5] * A[6] - A[3] * A[8], c02 = A[3] * A[7] - A[4] * A[6];
         const double det = A[0] * c00 + A[1] * c01 + A[2] * c02;
         const double id = 1.0 / det;
@@ -716,6 +730,12 @@ int gx_apply_A_j(gx_ctx *c, const double *base, int64_t stride, const int *jptr,
 
 int gx_build_jacobi(gx_ctx *c, cudaStream_t st) {
     k_jacobi<<<blocks_for(c->N), kB, 0, st>>>(opargs(c), c->jdiag, c->jdiag32);
+    GX_LAUNCHED(c);
+    return GX_OK;
+}
+
+int gx_build_jacobi32(gx_ctx *c, cudaStream_t st) {
+    k_jacobi<<<blocks_for(c->N), kB, 0, st>>>(opargs(c), nullptr, c->jdiag32);
     GX_LAUNCHED(c);
     return GX_OK;
 }

@@ -211,6 +211,8 @@ int gx_apply_A(gx_ctx *c, const double *x, double *y, cudaStream_t st);
 int gx_apply_A_j(gx_ctx *c, const double *base, int64_t stride, const int *jptr, const int *doneptr, double *y,
                  cudaStream_t st);
 int gx_build_jacobi(gx_ctx *c, cudaStream_t st);
+// only the FP32 inverse (the learned preconditioner's base), inverted in FP32
+int gx_build_jacobi32(gx_ctx *c, cudaStream_t st);
 int gx_apply_jacobi(gx_ctx *c, const double *x, double *y, cudaStream_t st);
 int gx_advance(gx_ctx *c, cudaStream_t st);                  // Enew, Bnew from Eth
 int gx_initial_guess(gx_ctx *c, cudaStream_t st);            // Eth <- starting point of the solve

@@ -780,7 +780,7 @@ int gx_precond_apply(gx_ctx *c, const double *v, double *z, void *stream) {
         GX_CHECK(c, cudaStreamSynchronize(st));
         return GX_OK;
     }
-    int rc = gx_build_jacobi(c, st);
+    int rc = pc == GX_PRECOND_JACOBI ? gx_build_jacobi(c, st) : gx_build_jacobi32(c, st);
     if (rc) return rc;
     if (pc == GX_PRECOND_JACOBI) {
         if ((rc = gx_apply_jacobi(c, v, z, st))) return rc;

@@ -1,8 +1,9 @@
-"""GPU path with open x boundaries (the shock runs of Sec. 3.3) against the oracle.
+"""GPU path with open x boundaries (the shock runs of Sec. 3.3-3.4) against the oracle.
 
-The 1D quasi-parallel shock from the paper's printed upstream/downstream states,
-shortened to 48 d_i (120 cells of 0.4 d_i, 16 particles per cell and species, 8
-boundary cells per end).  Both sides refill the boundary cells after every push
+The paper's two 1D shocks from their printed upstream/downstream states,
+shortened to 120 cells (quasi-parallel: 48 d_i of 0.4 d_i cells; quasi-
+perpendicular: 24 d_i of 0.2 d_i = 4 d_e cells), 16 particles per cell and
+species, 8 boundary cells per end.  Both sides refill the boundary cells after every push
 from the same counter-based draws (Philox4x64-10), so the runs match:
   * E and B after three steps within 3e-6 relative (the 1e-6 per-step field
     tolerance, once per step; the injected velocities are FP32 Box-Muller on
@@ -38,12 +39,14 @@ def gx():
     return g
 
 
-def small_shock(**kw):
-    return workloads.shock_1d(dx=0.4, length=48.0, ppc=16, **kw)
+def small_shock(kind="parallel", **kw):
+    length = 48.0 if kind == "parallel" else 24.0
+    return workloads.shock_1d(kind, length=length, ppc=16, **kw)
 
 
-def test_shock_steps_match_oracle(gx):
-    wl = small_shock()
+@pytest.mark.parametrize("kind,ny", [("parallel", 1), ("perpendicular", 1), ("parallel", 3)])
+def test_shock_steps_match_oracle(gx, kind, ny):
+    wl = small_shock(kind, ny=ny)
     bc = wl.notes["bc"]
     G, nx = bc["cells"], wl.n[0]
     steps = 3
@@ -67,12 +70,14 @@ def test_shock_steps_match_oracle(gx):
     for s in range(2):
         assert len(parts[s]["x"]) == int((pl.sp == s).sum())
         ci = np.floor(parts[s]["x"] / wl.dx[0]).astype(int) % nx
-        counts = np.bincount(ci, minlength=nx)
-        assert np.all(counts[np.r_[0:G, nx - G:nx]] == bc["sources"][0][s]["ppc"])
+        cj = (np.floor(parts[s]["y"] / wl.dx[1]).astype(int) % ny) if ny > 1 else np.zeros_like(ci)
+        counts = np.bincount(ci + nx * cj, minlength=nx * ny).reshape(ny, nx)
+        assert np.all(counts[:, np.r_[0:G, nx - G:nx]] == bc["sources"][0][s]["ppc"])
 
 
-def test_boundary_fields_stay_fixed_and_shock_runs(gx):
-    wl = small_shock()
+@pytest.mark.parametrize("kind", ["parallel", "perpendicular"])
+def test_boundary_fields_stay_fixed_and_shock_runs(gx, kind):
+    wl = small_shock(kind)
     G, nx = wl.notes["bc"]["cells"], wl.n[0]
     ctx = gx.from_workload(wl)
     for _ in range(20):

@@ -274,70 +274,91 @@ def _state(rho_amu_cc, u_kms, B_nT, pe_npa, pi_npa, c_kms, mass_ratio):
                 vth_i=math.sqrt(ti / mp) / (c_kms * 1e3), B_nT=list(B_nT))
 
 
-def shock_1d(dx=0.4, length=None, ppc=100, bc_cells=8, seed=12345, cfl=0.2, steps=200, comoving=1, ns_j=1,
-             lf_on=1, lf_beta=1.0, gmres_tol=1e-8):
-    """1D quasi-parallel shock of Sec. 3.3 from the printed upstream and
-    downstream states (theta_Bn = 30 deg, p_e/p_i = 2), m_i/m_e = 25, reduced
-    light speed c = 3000 km/s, domain [-1.8e4, 3.2e4] km with the shock at x = 0
-    (downstream on the low-x side; the upstream flows in along -x).
+# The two 1D shocks of the paper as printed (Sec. 3.3 and 3.4): upstream and
+# downstream (rho [amu/cc], u [km/s], B [nT], p_e, p_i [nPa]), mass ratio,
+# reduced light speed [km/s], upstream ion inertial length [km], domain [km],
+# default cell size [d_i].
+SHOCKS = {
+    "parallel": dict(up=(3.0, (-440.6, 0.0, 0.0), (4.33, 2.5, 0.0), 0.00995, 0.004975),
+                     down=(10.9, (-121.3, -10.86, 0.0), (4.33, 9.47, 0.0), 0.4588, 0.2294),
+                     mass_ratio=25.0, c_kms=3000.0, di_km=133.0, domain=(-1.8e4, 3.2e4), dx=0.4),
+    "perpendicular": dict(up=(40.0, (-552.0, 0.0, 0.0), (20.0, 0.0, 34.6), 0.27613, 0.27613),
+                          down=(119.5, (-184.9, 0.0, -31.15), (20.0, 0.0, 106.85), 5.02, 5.02),
+                          mass_ratio=400.0, c_kms=10000.0, di_km=36.0, domain=(-2.0e3, 2.0e3), dx=0.2),
+}
 
-    Units: the upstream ion inertial length d_i = 133 km, velocities over the
+
+def shock_1d(kind="parallel", dx=None, length=None, ppc=100, bc_cells=8, seed=12345, cfl=0.2, steps=200,
+             comoving=1, ns_j=1, lf_on=1, lf_beta=1.0, gmres_tol=1e-8, ny=1):
+    """1D shock from the paper's printed upstream and downstream states:
+    "parallel" (Sec. 3.3: theta_Bn = 30 deg, p_e/p_i = 2, m_i/m_e = 25, reduced
+    c = 3000 km/s, domain [-1.8e4, 3.2e4] km, M_A = 7) or "perpendicular"
+    (Sec. 3.4: theta_Bn = 60 deg, p_e = p_i, m_i/m_e = 400, c = 10,000 km/s,
+    domain [-2e3, 2e3] km, M_A = 4), shock at x = 0, downstream on the low-x
+    side, the upstream flowing in along -x.
+
+    Units: the printed upstream ion inertial length d_i, velocities over the
     reduced c, densities over the upstream density (omega_pi = c / d_i there).
-    B is v_A / c with v_A = |B| / sqrt(mu0 n m_p) per component.  dt from
-    CFL 0.2 on the fastest speed of the two states, |u| + 3 vth_e (the paper
-    quotes CFL 0.2 without the speed it uses).  `length` (in d_i) shortens the
-    domain around the shock for tests, keeping the printed proportion of the
-    two sides.  bc_cells cells at each end hold the two states (open
-    boundaries, refilled after every push from counter-based draws keyed by
-    seed); ppc per species (not printed)."""
-    c_kms, mass_ratio, di_km = 3000.0, 25.0, 133.0
-    up = _state(3.0, (-440.6, 0.0, 0.0), (4.33, 2.5, 0.0), 0.00995, 0.004975, c_kms, mass_ratio)
-    dn = _state(10.9, (-121.3, -10.86, 0.0), (4.33, 9.47, 0.0), 0.4588, 0.2294, c_kms, mass_ratio)
+    B is v_A / c with v_A = |B| / sqrt(mu0 n m_p) per component.  dt from CFL
+    0.2 on the fastest speed of the two states, |u| + 3 vth_e (the paper quotes
+    CFL 0.2 without the speed it uses).  dx defaults to 0.4 d_i (parallel) and
+    0.2 d_i = 4 d_e (perpendicular); `length` (in d_i) shortens the domain
+    around the shock for tests, keeping the printed proportion of the two
+    sides.  bc_cells cells at each end hold the two states (open boundaries,
+    refilled after every push from counter-based draws keyed by seed); ppc per
+    species (not printed).  ny > 1 spreads the same planar shock over ny
+    periodic rows of square cells (a 2D grid of the 1D problem)."""
+    P = SHOCKS[kind]
+    c_kms, mass_ratio, di_km = P["c_kms"], P["mass_ratio"], P["di_km"]
+    up = _state(*P["up"], c_kms, mass_ratio)
+    dn = _state(*P["down"], c_kms, mass_ratio)
     mu0, mp = 4e-7 * math.pi, 1.67262192e-27
     n_up = up["n_si"]
     for st in (up, dn):
         st["n"] = st["n_si"] / n_up * N0
         st["B"] = [b * 1e-9 / math.sqrt(mu0 * n_up * mp) / (c_kms * 1e3) for b in st["B_nT"]]
-    L_full = (3.2e4 + 1.8e4) / di_km
+    dx = P["dx"] if dx is None else float(dx)
+    x0, x1 = P["domain"]
+    L_full = (x1 - x0) / di_km
     L = L_full if length is None else float(length)
     nx = int(round(L / dx))
-    x_shock = 1.8e4 / 5.0e4 * nx * dx
-    vmax = max(abs(up["u"][0]) + 3 * up["vth_e"], math.hypot(dn["u"][0], dn["u"][1]) + 3 * dn["vth_e"])
+    x_shock = (-x0) / (x1 - x0) * nx * dx
+    vmax = max(math.hypot(*up["u"]) + 3 * up["vth_e"], math.hypot(*dn["u"]) + 3 * dn["vth_e"])
     dt = cfl * dx / vmax
-    n = (nx, 1, 1)
-    dxs = (dx, 1.0, 1.0)
+    n = (nx, int(ny), 1)
+    dxs = (dx, dx if ny > 1 else 1.0, 1.0)
     rng_e, rng_i = _rng(seed, 1), _rng(seed, 0)
     xc = (np.arange(nx) + 0.5) * dx
     down_cell = xc < x_shock
     species = []
-    for k, (rng, q, m, key) in enumerate(((rng_e, -1.0, 1.0 / mass_ratio, "vth_e"), (rng_i, 1.0, 1.0, "vth_i"))):
+    for rng, q, m, key in ((rng_e, -1.0, 1.0 / mass_ratio, "vth_e"), (rng_i, 1.0, 1.0, "vth_i")):
         x, y, z = _uniform_positions(rng, n, dxs, ppc)
-        cell = np.floor(x / dx).astype(np.int64)
+        cell = np.floor(x / dx).astype(np.int64) % nx
         v = rng.standard_normal((3, x.size))
-        w = np.empty(x.size, np.float32)
         vel = []
         for d in range(3):
             ud = np.where(down_cell[cell], dn["u"][d], up["u"][d])
             vt = np.where(down_cell[cell], dn[key], up[key])
             vel.append((ud + vt * v[d]).astype(np.float32))
-        w[:] = np.where(down_cell[cell], dn["n"], up["n"]) * dx / ppc
-        species.append(dict(q=q, m=m, x=x, y=np.zeros_like(x), z=z, vx=vel[0], vy=vel[1], vz=vel[2], w=w))
-    Bc = np.zeros((3, 1, 1, nx))
-    E = np.zeros((3, 1, 1, nx))
+        w = (np.where(down_cell[cell], dn["n"], up["n"]) * dxs[0] * dxs[1] / ppc).astype(np.float32)
+        species.append(dict(q=q, m=m, x=x, y=y if ny > 1 else np.zeros_like(x), z=z, vx=vel[0], vy=vel[1],
+                            vz=vel[2], w=w))
+    Bc = np.zeros((3, 1, int(ny), nx))
+    E = np.zeros((3, 1, int(ny), nx))
     xn = np.arange(nx) * dx
     for d in range(3):
-        Bc[d, 0, 0] = np.where(down_cell, dn["B"][d], up["B"][d])
+        Bc[d, 0, :] = np.where(down_cell, dn["B"][d], up["B"][d])[None, :]
     for st, sel in ((dn, xn < x_shock), (up, xn >= x_shock)):
         u32 = np.asarray(st["u"], np.float32).astype(np.float64)
         Em = -np.cross(u32, np.asarray(st["B"]))
         for d in range(3):
-            E[d, 0, 0, sel] = Em[d]
+            E[d, 0][:, sel] = Em[d]
     sources = [[dict(n=st["n"], u=st["u"], vth=st[key], ppc=ppc) for key in ("vth_e", "vth_i")] for st in (dn, up)]
-    return Workload(name=f"shock_1d_{nx}x1_dx{dx}", n=n, dx=dxs, c=1.0, theta=0.5, dt=dt, comoving=comoving,
-                    lf_on=lf_on, lf_beta=lf_beta, lf_speed_c=0, ns_j=ns_j, nsmooth_u=5, gmres_tol=gmres_tol,
-                    species=species, E0=E, B0=Bc, steps=steps,
+    return Workload(name=f"shock_{kind}_{nx}x{int(ny)}_dx{dx}_ppc{ppc}", n=n, dx=dxs, c=1.0, theta=0.5, dt=dt,
+                    comoving=comoving, lf_on=lf_on, lf_beta=lf_beta, lf_speed_c=0, ns_j=ns_j, nsmooth_u=5,
+                    gmres_tol=gmres_tol, species=species, E0=E, B0=Bc, steps=steps,
                     notes=dict(bc=dict(cells=bc_cells, seed=seed, sources=sources), up=up, down=dn,
-                               x_shock=x_shock, mass_ratio=mass_ratio))
+                               x_shock=x_shock, mass_ratio=mass_ratio, kind=kind))
 
 
 def tophat_1d(n=80, dx=0.01, cfl=0.4, lf_on=1, lf_beta=1.0, theta=0.5):
