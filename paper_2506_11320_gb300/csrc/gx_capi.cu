@@ -246,7 +246,7 @@ int gx_create(const gx_config *cfg, gx_ctx **out) {
         (rc = dalloc(c, &c->hcol, 2 * (m + 2))) || (rc = dalloc(c, &c->dflags, 1)))
         return fail(rc, nullptr);
     if (cfg->precond != GX_PRECOND_NONE && (rc = dalloc(c, &c->Z, (size_t)m * 3 * N))) return fail(rc, nullptr);
-    if (cfg->lf_on && (rc = dalloc(c, &c->dBlf, 3 * N))) return fail(rc, nullptr);
+    if (cfg->lf_on && (rc = dalloc(c, &c->dBlf, 12 * N))) return fail(rc, nullptr);   // D, B~, face fluxes
     if (cfg->divb_clean) {
         if ((rc = dalloc(c, &c->phi, N))) return fail(rc, nullptr);
         if (cudaMemset(c->phi, 0, N * sizeof(double)) != cudaSuccess) return fail(GX_ECUDA, "cudaMemset failed");

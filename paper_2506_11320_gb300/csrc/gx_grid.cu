@@ -388,8 +388,8 @@ __global__ void k_motional(G2 g, const double *__restrict__ u, const double *__r
 
 // b = E^n + c theta dt [curl_N B^n - (4 pi / c)(J - (1/dV) M E_M)]   (Eq. 35)
 __global__ void k_rhs(G2 g, const double *__restrict__ E, const double *__restrict__ B, const double *__restrict__ J,
-                      const double *__restrict__ M, const double *__restrict__ EM, const double *__restrict__ D,
-                      double theta, double ctd, double jf, double mf, double *b) {
+                      const double *__restrict__ M, const double *__restrict__ EM, double ctd, double jf, double mf,
+                      double *b) {
     const int64_t N = g.N();
     GRID_LOOP(q, N) {
         const int i = (int)(q % g.nx), j = (int)(q / g.nx);
@@ -398,12 +398,6 @@ __global__ void k_rhs(G2 g, const double *__restrict__ E, const double *__restri
         cn[0] = dNy(g, Bz, i, j);
         cn[1] = -dNx(g, Bz, i, j);
         cn[2] = dNx(g, By, i, j) - dNy(g, Bx, i, j);
-        if (D) {   // B^{n+theta} holds theta D of the LF increment: curl (B^n + theta D)
-            const double *Dx = D, *Dy = D + N, *Dz = D + 2 * N;
-            cn[0] += theta * dNy(g, Dz, i, j);
-            cn[1] -= theta * dNx(g, Dz, i, j);
-            cn[2] += theta * (dNx(g, Dy, i, j) - dNy(g, Dx, i, j));
-        }
         double out[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) out[k] = E[k * N + q] + ctd * cn[k] - jf * J[k * N + q];
@@ -470,48 +464,57 @@ __global__ void k_kappa(G2 g, const double *__restrict__ E, const double *__rest
 
 // B^{n+1} = B^n - c dt curl_C E^{n+theta} + dt/dx_d (F_{c+1/2} - F_{c-1/2}),
 // F = (1 - phi_B) a / 2 (B_{c+1} - B_c)  (Eq. 5, 17, 18, 22);  E^{n+1} from Eq. 10.
-// Increment of the limited LF diffusion on B over one step (Eq. 17-18): per
-// component along every resolved axis D = dt/dx (F_{c+1/2} - F_{c-1/2}),
-// F = (1 - phi_B) a / 2 (B_{c+1} - B_c), phi_B = MC(r, beta), r = (B_c -
-// B_{c-1}) / (B_{c+1} - B_c), a = |u| averaged over the face (or c).  Computed
-// once per step: B^{n+1} receives D, and the E solve curls B^n + theta D (the
-// B^{n+theta} that holds it).
-__global__ void k_lf_b(G2 g, const double *__restrict__ B, const double *__restrict__ u, double c, double dt,
-                       double beta, int speed_c, double *D) {
+// Limited LF flux of B through the +x and +y faces of every cell (Eq. 17-18),
+// each face once: F = dt/dx (1 - phi_B) a / 2 (B_{c+1} - B_c) per component,
+// phi_B = MC(r, beta), r = (B_c - B_{c-1}) / (B_{c+1} - B_c), a = |u| averaged
+// over the face (or c).  Ff [2][3][N]: axis, component, cell.
+__global__ void k_lf_flux(G2 g, const double *__restrict__ B, const double *__restrict__ u, double c, double dt,
+                          double beta, int speed_c, double *Ff) {
     const int64_t N = g.N();
     GRID_LOOP(q, N) {
         const int i = (int)(q % g.nx), j = (int)(q / g.nx);
-        double dn[3] = {0.0, 0.0, 0.0};
+#pragma unroll
         for (int d = 0; d < 2; ++d) {
             if ((d == 0 && g.nx == 1) || (d == 1 && g.ny == 1)) continue;
             const double f = dt * 2.0 * (d == 0 ? g.hx : g.hy);
-            // faces c+1/2 (between c and c+e) and c-1/2 (between c-e and c)
-            for (int side = 0; side < 2; ++side) {
-                const int ci = d == 0 ? i - side : i, cj = d == 0 ? j : j - side;   // face between (ci,cj) and +e
-                const int64_t c0 = g.id(ci, cj);
-                const int64_t cp = d == 0 ? g.id(ci + 1, cj) : g.id(ci, cj + 1);
-                const int64_t cm = d == 0 ? g.id(ci - 1, cj) : g.id(ci, cj - 1);
-                double a;
-                if (speed_c) {
-                    a = c;
-                } else {
-                    const int64_t n0 = d == 0 ? g.id(ci + 1, cj) : g.id(ci, cj + 1);
-                    const int64_t n1 = g.id(ci + 1, cj + 1);
-                    a = 0.5 * (double)(umag(u, N, n0) + umag(u, N, n1));
-                }
+            const int64_t cp = d == 0 ? g.id(i + 1, j) : g.id(i, j + 1);
+            const int64_t cm = d == 0 ? g.id(i - 1, j) : g.id(i, j - 1);
+            double a;
+            if (speed_c) {
+                a = c;
+            } else {
+                const int64_t n1 = g.id(i + 1, j + 1);
+                a = 0.5 * (double)(umag(u, N, cp) + umag(u, N, n1));
+            }
 #pragma unroll
-                for (int k = 0; k < 3; ++k) {
-                    const double *Bk = B + k * N;
-                    const double dp = Bk[cp] - Bk[c0];
-                    const float r = ratio(Bk[c0] - Bk[cm], dp);
-                    const double F = (double)(1.0f - mc_limiter(r, (float)beta)) * a * 0.5 * dp;
-                    dn[k] += side == 0 ? f * F : -f * F;
-                }
+            for (int k = 0; k < 3; ++k) {
+                const double *Bk = B + k * N;
+                const double dp = Bk[cp] - Bk[q];
+                const float r = ratio(Bk[q] - Bk[cm], dp);
+                Ff[(d * 3 + k) * N + q] = f * ((double)(1.0f - mc_limiter(r, (float)beta)) * a * 0.5 * dp);
             }
         }
-        if (g.bcell(i)) dn[0] = dn[1] = dn[2] = 0.0;   // boundary cells keep B
+    }
+}
+
+// Increment of the limited LF diffusion on B over one step, D = F_{c+1/2} -
+// F_{c-1/2} along every resolved axis (0 in boundary cells), and B~ = B^n +
+// theta D, the part of B^{n+theta} the E solve curls: B^{n+1} receives D.
+__global__ void k_lf_b(G2 g, const double *__restrict__ B, const double *__restrict__ Ff, double theta, double *D,
+                       double *Bt) {
+    const int64_t N = g.N();
+    GRID_LOOP(q, N) {
+        const int i = (int)(q % g.nx), j = (int)(q / g.nx);
+        const int64_t xm = g.id(i - 1, j), ym = g.id(i, j - 1);
 #pragma unroll
-        for (int k = 0; k < 3; ++k) D[k * N + q] = dn[k];
+        for (int k = 0; k < 3; ++k) {
+            double dn = 0.0;
+            if (g.nx > 1) dn += Ff[(0 * 3 + k) * N + q] - Ff[(0 * 3 + k) * N + xm];
+            if (g.ny > 1) dn += Ff[(1 * 3 + k) * N + q] - Ff[(1 * 3 + k) * N + ym];
+            if (g.bcell(i)) dn = 0.0;   // boundary cells keep B
+            D[k * N + q] = dn;
+            Bt[k * N + q] = B[k * N + q] + theta * dn;
+        }
     }
 }
 
@@ -694,15 +697,20 @@ int gx_build_rhs(gx_ctx *c, cudaStream_t st) {
     }
     const double ctd = c->cfg.c * c->cfg.theta * c->cfg.dt;
     const double jf = 4.0 * GX_PI * c->cfg.theta * c->cfg.dt;
-    const double *D = nullptr;
+    // with LF on B, the right-hand side curls B~ = B^n + theta D (D: the LF increment
+    // B^{n+1} receives), held in dBlf + 3N; the fluxes go to dBlf + 6N
+    const double *Bc = c->B;
     if (c->cfg.lf_on) {
-        k_lf_b<<<blocks_for(c->N), kB, 0, st>>>(g, c->B, c->u, c->cfg.c, c->cfg.dt, c->cfg.lf_beta, c->cfg.lf_speed_c,
-                                                c->dBlf);
+        double *D = c->dBlf, *Bt = c->dBlf + 3 * c->N, *Ff = c->dBlf + 6 * c->N;
+        k_lf_flux<<<blocks_for(c->N), kB, 0, st>>>(g, c->B, c->u, c->cfg.c, c->cfg.dt, c->cfg.lf_beta,
+                                                   c->cfg.lf_speed_c, Ff);
         GX_LAUNCHED(c);
-        D = c->dBlf;
+        k_lf_b<<<blocks_for(c->N), kB, 0, st>>>(g, c->B, Ff, c->cfg.theta, D, Bt);
+        GX_LAUNCHED(c);
+        Bc = Bt;
     }
-    k_rhs<<<blocks_for(c->N), kB, 0, st>>>(g, c->E, c->B, c->J, c->M, cm ? c->EM : nullptr, D, c->cfg.theta, ctd,
-                                           jf, jf / c->dV, c->rhs);
+    k_rhs<<<blocks_for(c->N), kB, 0, st>>>(g, c->E, Bc, c->J, c->M, cm ? c->EM : nullptr, ctd, jf, jf / c->dV,
+                                           c->rhs);
     GX_LAUNCHED(c);
     return GX_OK;
 }

@@ -97,7 +97,7 @@ struct gx_ctx {
     // fields (FP64)
     double *E = nullptr, *B = nullptr;          // E^n (nodes), B^n (cells)
     double *phi = nullptr;                      // div B cleaning potential (cells), with divb_clean
-    double *dBlf = nullptr;                     // [3][N] LF increment of B over the step, with lf_on
+    double *dBlf = nullptr;                     // with lf_on: D [3][N] (LF increment of B), B^n + theta D [3][N], fluxes [2][3][N]
     double *Eth = nullptr, *Enew = nullptr, *Bnew = nullptr;
     int pending = 0;                            // a solve is waiting for the push
     int have_eth = 0;                           // Eth holds E^{n-1+theta} of the step that produced E
