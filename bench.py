@@ -40,6 +40,21 @@ UNIT = "particle-steps/s"
 ALG_BYTES_2D = 44          # per particle-step: read ox,oy,vx,vy,vz,w (24 B) + write ox,oy,vx,vy,vz (20 B)
 
 
+def max_over_ranks(values, dist, device):
+    """Element-wise maximum of per-rank timings over all ranks: the whole job is
+    as slow as its slowest replica."""
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t]
+
+
+def whole_job_rate(world, units_per_rank, ms):
+    """Units processed by all ranks per second of the slowest rank's time."""
+    return world * units_per_rank / (ms / 1000.0)
+
+
 def make_workload(name):
     if name == "harris":
         return workloads.harris(nx=512, ny=256, ppc=100), "2D Harris-sheet reconnection 512x256 cells, 100 ppc/species"
@@ -225,12 +240,9 @@ def run_shock(gx, warmup, steps, barrier, dist, world):
     tm = ctx.timers(reset=True)
     npart = sum(ctx.species_count(s) for s in range(len(wl.species)))
     ctx.close()
-    vals = torch.tensor([(tm["push_ms"] + tm["moments_ms"]) / steps, ev0.elapsed_time(ev1) / steps],
-                        dtype=torch.float64, device="cuda")
-    if dist:
-        dist.all_reduce(vals, op=dist.ReduceOp.MAX)
-    pd_ms, step_ms = float(vals[0]), float(vals[1])
-    return {"value": world * npart / (pd_ms / 1000.0), "unit": UNIT, "push_deposit_ms_per_step": pd_ms,
+    pd_ms, step_ms = max_over_ranks([(tm["push_ms"] + tm["moments_ms"]) / steps, ev0.elapsed_time(ev1) / steps],
+                                    dist, "cuda")
+    return {"value": whole_job_rate(world, npart, pd_ms), "unit": UNIT, "push_deposit_ms_per_step": pd_ms,
             "ms_per_step": step_ms, "particles": npart,
             "workload": f"{wl.name}: the paper's 1D quasi-parallel shock (printed up/downstream states, M_A 7, "
                         f"m_i/m_e 25, c = 3000 km/s) on {wl.n[0]}x{wl.n[1]} cells, open x boundaries"}
@@ -304,12 +316,8 @@ def main():
     kt = ctx.kernel_timer(reset=True)
     pd_ms = (tm["push_ms"] + tm["moments_ms"]) / args.steps
     solve_ms = tm["solve_ms"] / args.steps
-    # max over ranks
-    vals = torch.tensor([pd_ms, step_ms_dev, wall], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.all_reduce(vals, op=dist.ReduceOp.MAX)
-    pd_ms_max, step_ms_max = float(vals[0]), float(vals[1])
-    value = world * Np / (pd_ms_max / 1000.0)
+    pd_ms_max, step_ms_max, _ = max_over_ranks([pd_ms, step_ms_dev, wall], dist, "cuda")
+    value = whole_job_rate(world, Np, pd_ms_max)
 
     peak, peak_kind = load_peaks()
     # roofline of the dominant kernel: the fused mover + re-bin + deposit
@@ -349,7 +357,7 @@ def main():
     # ------------------------------------------------------- end to end (host buffers)
     e2e = None
     if not args.no_e2e:
-        e2e = run_e2e(gx, wl, args.steps, barrier)
+        e2e = run_e2e(gx, wl, args.steps, barrier, dist, world)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -430,7 +438,7 @@ def run_precond_compare(gx, wl, steps, barrier, collect_steps=24):
     return out
 
 
-def run_e2e(gx, wl, steps, barrier):
+def run_e2e(gx, wl, steps, barrier, dist=None, world=1):
     """Same metric through the public C ABI with host buffers: pinned host
     particle and field arrays are copied in (gx_species_add, gx_fields_set),
     every step's diagnostics (FP64 energies, momentum) are read back, and the
@@ -472,9 +480,10 @@ def run_e2e(gx, wl, steps, barrier):
     ctx.get_fields(Eout.numpy(), Bout.numpy())
     d2h += 2 * Eout.numel() * 8
     barrier()
-    wall = time.perf_counter() - t0
+    wall_ms = max_over_ranks([1000.0 * (time.perf_counter() - t0)], dist, "cuda")[0]
     ctx.close()
-    return {"value": wl.n_particles * steps / wall, "unit": UNIT, "h2d_bytes_per_step": h2d // steps,
+    return {"value": whole_job_rate(world, wl.n_particles * steps, wall_ms), "unit": UNIT,
+            "h2d_bytes_per_step": h2d // steps,
             "d2h_bytes_per_step": d2h // steps,
             "note": "context creation, binning of all particles from pinned host memory, every step's FP64 "
                     "diagnostics and the final fields read back are inside the timed region"}
