@@ -13,7 +13,10 @@ offset ``o = (ox+1) + 3 (oy+1) + 9 (oz+1)``.
 
 Parity status: every routine is pinned by ``tests/test_oracle_*.py`` except the
 learned-preconditioner network's *training usefulness* (its forward pass and
-gradients are pinned; what it learns is not a paper quantity).
+gradients are pinned; what it learns is not a paper quantity).  The open-boundary
+refill (``refill_boundaries``) is pinned by its generator (word for word against
+numpy's Philox), the statistics of its draws and the particle counts it leaves;
+the shock states themselves are the paper's printed numbers.
 """
 from __future__ import annotations
 

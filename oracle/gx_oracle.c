@@ -23,7 +23,8 @@
  *
  * Mesh (Sec. 1.1): collocated staggered grid, E at nodes, B at cell centres.
  * Node (i,j,k) sits at (i dx, j dy, k dz); cell (i,j,k) spans
- * [i,i+1]x[j,j+1]x[k,k+1] cell widths.  All axes are periodic.  An axis with a
+ * [i,i+1]x[j,j+1]x[k,k+1] cell widths.  All axes are periodic (with bc_cells,
+ * x has open ends held at fixed plasma states: see bcell/bnode).  An axis with a
  * single cell is "collapsed": the periodic wrap makes node i+1 the same node as
  * node i, so derivatives along it vanish and averages along it are the identity,
  * and the same code covers 1D, 2D and 3D.  Positions along a collapsed axis are
@@ -51,7 +52,16 @@
  *   - the diffusion speed a is |u| (the smoothed bulk velocity) averaged over
  *     the face / edge, or c for vacuum tests;
  *   - "plasma velocity" is mass weighted over all species, 0 where no mass;
- *   - a smoothness ratio with a zero denominator is taken as 0.
+ *   - a smoothness ratio with a zero denominator is taken as 0;
+ *   - the E solve curls B^n + theta D, D the LF increment B^{n+1} receives
+ *     (B^{n+theta} of Eq. 7 holds it);
+ *   - div B cleaning (Sec. 1.3): phi at cell centres, central differences,
+ *     B^{n+1} -= dt grad phi^n, then phi^{n+1} = exp(-0.1)(phi^n - dt c_h^2 div B^{n+1});
+ *   - the E-field filter of the Sec. 3.1 comparison acts on E^{n+1} in place
+ *     of the LF term on E;
+ *   - open boundaries (the shock runs of Sec. 3.3-3.4): Dirichlet rows for E at
+ *     boundary nodes, B held in boundary cells, boundary cells refilled after
+ *     every push from Philox4x64-10 draws (or_bc_sample).
  */
 #include <math.h>
 #include <stdint.h>

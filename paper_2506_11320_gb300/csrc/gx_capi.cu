@@ -383,6 +383,13 @@ int gx_field_solve(gx_ctx *c, void *stream, gx_solve_stats *stats) {
 int gx_push_and_deposit(gx_ctx *c, void *stream) {
     if (!c) return GX_EINVAL;
     if (!c->pending) { c->err = "gx_push_and_deposit needs a preceding gx_field_solve"; return GX_ESTATE; }
+    if (c->cfg.bc_cells > 0)      // refuse before anything is launched
+        for (int s = 0; s < c->nspecies; ++s)
+            for (int sd = 0; sd < 2; ++sd)
+                if (c->bsrc[sd][s].ppc < 1) {
+                    c->err = "open boundaries need gx_boundary_source for every species on both sides";
+                    return GX_ESTATE;
+                }
     cudaStream_t st = S(stream);
     // grow a species' bins when the last step left one above 90 % of capacity
     if (c->hflags->maxcount > 0) {

@@ -99,3 +99,39 @@ def test_boundary_fields_stay_fixed_and_shock_runs(gx, kind):
     lo, hi = dens[G:G + 4].mean(), dens[nx - G - 4:nx - G].mean()
     assert abs(lo / wl.notes["down"]["n"] - 1) < 0.3, (lo, wl.notes["down"]["n"])
     assert abs(hi / wl.notes["up"]["n"] - 1) < 0.3, (hi, wl.notes["up"]["n"])
+
+
+def test_boundary_api_edge_cases(gx):
+    wl = small_shock()
+    base = dict(c=wl.c, theta=wl.theta, dt=wl.dt, comoving=1, lf_on=1)
+    # fewer than 8 boundary cells, boundaries over half the domain, or with div B cleaning: rejected
+    for kw in (dict(bc_cells=4), dict(bc_cells=wl.n[0] // 2), dict(bc_cells=8, divb_clean=1)):
+        with pytest.raises(gx.GxError) as e:
+            gx.Context(gx.make_config(wl.n, wl.dx, **base, **kw))
+        assert e.value.status == gx.GX_EINVAL
+    # a push before every species has its sources: GX_ESTATE, and the context stays usable
+    ctx = gx.Context(gx.make_config(wl.n, wl.dx, **base, bc_cells=8, bc_seed=5))
+    for s in wl.species:
+        ctx.species_add(s["q"], s["m"], s["x"], s["y"], s["z"], s["vx"], s["vy"], s["vz"], s["w"])
+    ctx.fields_set(wl.E0, wl.B0)
+    with pytest.raises(gx.GxError) as e:
+        ctx.boundary_source(2, 0, 1.0, (0, 0, 0), 0.1, 16)          # no side 2
+    assert e.value.status == gx.GX_EINVAL
+    with pytest.raises(gx.GxError) as e:
+        ctx.boundary_source(0, 0, 1.0, (0, 0, 0), 0.1, 0)           # ppc must be >= 1
+    assert e.value.status == gx.GX_EINVAL
+    ctx.field_solve()
+    with pytest.raises(gx.GxError) as e:
+        ctx.push_and_deposit()
+    assert e.value.status == gx.GX_ESTATE
+    # sources with more particles per cell than the bins hold: the bins grow
+    src = wl.notes["bc"]["sources"]
+    for side in range(2):
+        for s in range(2):
+            ctx.boundary_source(side, s, src[side][s]["n"], src[side][s]["u"], src[side][s]["vth"], 300)
+    ctx.step(2)
+    G, nx = 8, wl.n[0]
+    x = ctx.get_particles(1)["x"]
+    counts = np.bincount(np.floor(x / wl.dx[0]).astype(int) % nx, minlength=nx)
+    assert np.all(counts[np.r_[0:G, nx - G:nx]] == 300)
+    ctx.close()
