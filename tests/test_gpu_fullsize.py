@@ -107,3 +107,33 @@ def test_fullsize_conservation(state):
     scale = sum(abs(s["q"]) * np.sum(np.asarray(s["w"], np.float64)) for s in wl.species)
     assert abs(q_grid - q_tot) <= 1e-6 * scale, (q_grid, q_tot)
     assert np.all(np.isfinite(S["E"])) and np.all(np.isfinite(S["B"]))
+
+
+def test_fullsize_shock_step_matches_oracle():
+    """The benchmark's shock-shaped plasma at full size (the quasi-parallel shock
+    on 940 x 8 cells, 256 particles per cell and species, 3.85 M particles, open
+    boundaries): one step through the C ABI against one oracle step with the same
+    boundary refill.  The oracle runs this whole step in seconds, so E and B are
+    compared everywhere (relative L2 <= 1e-6, the one-step field tolerance) and
+    the particle counts per species exactly."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2506_11320_gb300 as g
+    wl = workloads.shock_1d("parallel", ny=8, ppc=256)
+    bc = wl.notes["bc"]
+    ctx = g.from_workload(wl, gmres_tol=1e-12)
+    st = ctx.step(1)
+    assert st.converged == 1
+    E1, B1 = ctx.get_fields()
+    counts = [ctx.species_count(s) for s in range(2)]
+    ctx.close()
+    cfg = O.make_cfg(wl.n, wl.dx, bc_cells=bc["cells"], **wl.grid_kwargs())
+    cfg.gmres_tol = 1e-12
+    pl = O.Plasma.from_species(wl.species)
+    E, B = wl.E0.copy(), wl.B0.copy()
+    assert O.step(cfg, pl, E, B)["rc"] == 0
+    pl = O.refill_boundaries(cfg, pl, bc["sources"], 1, bc["seed"])
+    errs = {"E": rel(E1, E), "B": rel(B1, B)}
+    assert all(v <= 1e-6 for v in errs.values()), errs
+    assert counts == [int((pl.sp == s).sum()) for s in range(2)]
