@@ -582,9 +582,17 @@ __global__ void k_diag_grid(G2 g, const double *__restrict__ E, const double *__
     }
 }
 
+// Kinetic energy, momentum and count of one species.  The per-particle terms
+// w v_i v_i and w v_i come from the FP32 particle state and are formed in FP32;
+// each thread sums them over 16 cells in FP32 (about 16 terms) and adds those
+// partial sums into FP64 accumulators, which take the species mass at the end
+// (FP64 on this part runs at 1/64 of the FP32 rate, so FP64 per particle
+// would make this pass ten times slower than its memory traffic).
 __global__ void k_diag_particles(int64_t ncell, int cap, const int *cnt, const float4 *P, double mass, double *acc) {
     double ke = 0, px = 0, py = 0, pz = 0;
     double np = 0;
+    float fk = 0.f, fx = 0.f, fy = 0.f, fz = 0.f;
+    int since = 0;
     for (int64_t c = blockIdx.x; c < ncell; c += gridDim.x) {
         const int word = cnt[c];
         const int m = min(bin_count(word), cap);
@@ -592,13 +600,18 @@ __global__ void k_diag_particles(int64_t ncell, int cap, const int *cnt, const f
         for (int i = threadIdx.x; i < m; i += blockDim.x) {
             const size_t s = (size_t)c * cap + bin_slot(word, i, cap);
             const float4 s0 = P[2 * s], s1 = P[2 * s + 1];
-            const double mw = mass * s1.y;
-            const double a = s0.z, b = s0.w, d = s1.x;
-            ke += 0.5 * mw * (a * a + b * b + d * d);
-            px += mw * a; py += mw * b; pz += mw * d;
+            const float w = s1.y, wa = w * s0.z, wb = w * s0.w, wd = w * s1.x;
+            fk = fmaf(wa, s0.z, fmaf(wb, s0.w, fmaf(wd, s1.x, fk)));
+            fx += wa; fy += wb; fz += wd;
+        }
+        if (++since == 16) {
+            ke += fk; px += fx; py += fy; pz += fz;
+            fk = fx = fy = fz = 0.f;
+            since = 0;
         }
     }
-    double v[5] = {ke, px, py, pz, np};
+    ke += fk; px += fx; py += fy; pz += fz;
+    double v[5] = {0.5 * mass * ke, mass * px, mass * py, mass * pz, np};
     for (int k = 0; k < 5; ++k) {
         double s = v[k];
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);

@@ -152,6 +152,28 @@ def test_one_step_matches_oracle(gx, name):
     ctx.close()
 
 
+def test_diagnostics_match_fp64_sums(gx):
+    """The kinetic energy and momentum of gx_diagnostics against FP64 sums over
+    the particles read back (the device forms the per-particle terms in FP32
+    and sums them in FP64 per 16 cells): within 1e-7 of the scale."""
+    wl = workloads.harris(nx=64, ny=32, ppc=24, steps=1)
+    ctx = gx.from_workload(wl)
+    ctx.step(1)
+    d = ctx.diagnostics()
+    ke, P, scale = 0.0, np.zeros(3), np.zeros(3)
+    for s, sp in enumerate(wl.species):
+        p = ctx.get_particles(s)
+        v = np.stack([p["vx"], p["vy"], p["vz"]]).astype(np.float64)
+        mw = sp["m"] * p["w"].astype(np.float64)
+        ke += 0.5 * (mw * (v * v).sum(0)).sum()
+        P += (mw * v).sum(1)
+        scale += (mw * np.abs(v)).sum(1)
+    ctx.close()
+    assert abs(d["kinetic"] - ke) <= 1e-7 * ke
+    assert np.all(np.abs(np.array(d["momentum"]) - P) <= 1e-7 * scale)
+    assert d["n_particles"] == wl.n_particles
+
+
 def test_plain_ecsim_energy_conservation_on_gpu(gx):
     # theta = 0.5, standard current, no LF, no smoothing: particle + field
     # energy is conserved to the solver tolerance in exact arithmetic; the FP32
