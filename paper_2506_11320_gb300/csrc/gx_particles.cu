@@ -646,14 +646,18 @@ __global__ void k_counts(const int *cnt, int64_t n, int cap, int *out) {
 }
 
 // ---------------------------------------------------------------- binning
-__global__ void k_locate(int64_t n, const double *x, const double *y, int nx, int ny, double dx, double dy,
+// cell and in-cell offsets of every particle; positions scaled by the inverse
+// cell widths (no FP64 division or fmod: both run on the slow FP64 pipe), the
+// cell index wrapped in integers (positions within +-2^31 cells)
+__global__ void k_locate(int64_t n, const double *x, const double *y, int nx, int ny, double idx, double idy,
                          int *cell, float *ox, float *oy, int *count) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        double sx = x[i] / dx, sy = (ny > 1) ? y[i] / dy : 0.0;
+        double sx = x[i] * idx, sy = (ny > 1) ? y[i] * idy : 0.0;
         double fx = floor(sx), fy = floor(sy);
         double rx = sx - fx, ry = sy - fy;
-        int cx = wrap_idx((int)fmod(fx, (double)nx), nx);
-        int cy = ny > 1 ? wrap_idx((int)fmod(fy, (double)ny), ny) : 0;
+        const long long lx = (long long)fx, ly = (long long)fy;
+        int cx = (lx >= 0 && lx < nx) ? (int)lx : (int)(((lx % nx) + nx) % nx);   // inside the box: no division
+        int cy = ny == 1 ? 0 : ((ly >= 0 && ly < ny) ? (int)ly : (int)(((ly % ny) + ny) % ny));
         float fxo = (float)rx, fyo = (float)ry;
         if (fxo >= 1.f) { fxo = 0.f; cx = wrap_idx(cx + 1, nx); }
         if (fyo >= 1.f) { fyo = 0.f; cy = wrap_idx(cy + 1, ny); }
@@ -769,7 +773,8 @@ int gx_bin_particles(gx_ctx *c, int s, int64_t n, const double *x, const double 
     GX_CHECK(c, cudaMalloc(&count, c->N * sizeof(int)));
     GX_CHECK(c, cudaMemsetAsync(count, 0, c->N * sizeof(int), st));
     if (n > 0) {
-        k_locate<<<grid_for(n), 256, 0, st>>>(n, x, y, c->n[0], c->n[1], c->cfg.dx[0], c->cfg.dx[1], cell, ox, oy, count);
+        k_locate<<<grid_for(n), 256, 0, st>>>(n, x, y, c->n[0], c->n[1], 1.0 / c->cfg.dx[0], 1.0 / c->cfg.dx[1], cell, ox,
+                                               oy, count);
         GX_LAUNCHED(c);
     }
     DevFlags *dmax = nullptr;
