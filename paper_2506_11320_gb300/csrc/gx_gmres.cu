@@ -530,7 +530,10 @@ int gx_fgmres(gx_ctx *c, cudaStream_t st) {
     k_gm_init<<<1, 32, 0, st>>>(c->gm);
     GX_LAUNCHED(c);
     void *args[] = {&a};
-    GX_CHECK(c, cudaLaunchCooperativeKernel(kfn, dim3(grid), dim3(use_net ? kBNet : kB), args, smem, st));
+    // small grids: no more CTAs than one node per thread, so that the grid barriers
+    // of every Arnoldi step synchronise few CTAs (the network path keeps its grid)
+    const int ngrid = use_net ? grid : (int)std::max<int64_t>(1, std::min<int64_t>(grid, (c->N + kB - 1) / kB));
+    GX_CHECK(c, cudaLaunchCooperativeKernel(kfn, dim3(ngrid), dim3(use_net ? kBNet : kB), args, smem, st));
     c->launches++;
     struct Flags { int j, done, finished, conv, total; };
     Flags *hf = reinterpret_cast<Flags *>(c->hpin);
