@@ -152,6 +152,19 @@ __global__ void __launch_bounds__(256) k_filter_fused(G2 g, const double *__rest
     }
 }
 
+// FP32 -> FP64 widening written from the IEEE-754 binary32/binary64 layouts:
+// sign kept, exponent rebiased (127 -> 1023, i.e. + 896), the 23 mantissa bits
+// moved to the top of the 52.  Exact, and on the integer pipe: the hardware
+// conversion runs at the FP64 rate (1/64 of FP32 on this part).  Zeros,
+// infinities and NaNs map directly; subnormal inputs take the hardware path.
+__device__ __forceinline__ double widen_f32(float f) {
+    const uint32_t u = __float_as_uint(f);
+    const uint32_t e = (u >> 23) & 0xffu, m = u & 0x7fffffu, sign = u & 0x80000000u;
+    if (e == 0u && m != 0u) return (double)f;
+    const uint32_t hi = e == 0u ? sign : (sign | ((e == 0xffu ? 0x7ffu : e + 896u) << 20) | (m >> 3));
+    return __hiloint2double((int)hi, (int)(m << 29));
+}
+
 // Comoving current and mass-matrix rows at every node (Sec. 2.1, Eq. 33-35).
 // J: the records hold sum w alpha (v - u_ref); the comoving current subtracts
 // the plasma velocity u of this deposit, so the difference u - u_ref is
@@ -234,7 +247,7 @@ __global__ void k_assemble_main(G2 g, SpecK sk, Recs R, double inv_dV, int comov
                 }
             }
 #pragma unroll
-            for (int e = 0; e < 9; ++e) M[(size_t)(o * 9 + e) * N + q] = (double)blk[e];
+            for (int e = 0; e < 9; ++e) M[(size_t)(o * 9 + e) * N + q] = widen_f32(blk[e]);
         }
     }
 }
