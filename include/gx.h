@@ -105,8 +105,10 @@ typedef struct gx_ctx gx_ctx;
  *                 particles per species drawn from that side's source (see
  *                 gx_boundary_source).  y stays periodic.  Not with divb_clean;
  *                 2 G < nx.
- *   bc_seed       key of the boundary draws: Philox4x64-10 with key (bc_seed,
- *                 species) and counter (step, cell index, particle, 0). */
+ *   seed          key of the context's counter-based draws (Philox4x64-10 with
+ *                 key (seed, species)): the device-side Maxwellian species
+ *                 (gx_species_maxwellian, counter (0, cell, particle, 0)) and the
+ *                 boundary refill after push t (counter (t, cell, particle, 0)). */
 typedef struct {
     int32_t n[3];
     int32_t comoving;
@@ -129,7 +131,7 @@ typedef struct {
     int32_t nsmooth_e;
     int32_t bc_cells;
     int32_t reserved;
-    uint64_t bc_seed;
+    uint64_t seed;
 } gx_config;
 
 typedef struct {
@@ -177,6 +179,19 @@ int gx_species_add(gx_ctx *ctx, double q, double m, int64_t n,
                    const double *x, const double *y, const double *z,
                    const float *vx, const float *vy, const float *vz, const float *w,
                    int ptr_is_device, int *species_id);
+
+/* Add a species generated on the device: ppc particles in every cell, drifting
+ * Maxwellian with bulk velocity u[3] and per-component thermal speed vth,
+ * density n0 (weights n0 dV / ppc), charge q and mass m per unit weight.
+ * Particle k of cell (i, j) takes the four Philox4x64-10 words r of key
+ * (cfg.seed, species index) and counter (0, j nx + i, k, 0): offsets in the
+ * cell (r0 >> 40) 2^-24 and (r1 >> 40) 2^-24 (0 along y in 1D) and
+ * v = u + vth (n0, n1, n2) from the Box-Muller transform of the 24-bit uniforms
+ * ((r2 >> 40) + 1) 2^-24, ((r2 >> 16) & 0xffffff) 2^-24 (n0, n1) and the same
+ * of r3 (n2) -- the draws of gx_boundary_source at step 0.  No host data is
+ * involved.  1 <= ppc <= 4096; *species_id as for gx_species_add. */
+int gx_species_maxwellian(gx_ctx *ctx, double q, double m, int ppc, double n0, const double *u, double vth,
+                          int *species_id);
 
 /* Set E (nodes) and B (cell centres), each FP64 [3][nz][ny][nx]. */
 int gx_fields_set(gx_ctx *ctx, const double *E, const double *B, int ptr_is_device);

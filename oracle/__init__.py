@@ -392,6 +392,22 @@ def bc_sample(cfg, seed, species, step, i, j, ppc, u, vth):
     return x, y, vx, vy, vz
 
 
+def maxwellian_species(cfg, seed, species, ppc, n0, u, vth):
+    """The particles of a device-side drifting Maxwellian species: for every cell
+    (j, then i) the ppc draws of step 0 (or_bc_sample), weights n0 dV / ppc.
+    Returns dict x, y, z, vx, vy, vz, w (float64)."""
+    nx, ny = cfg.n[0], cfg.n[1]
+    parts = {k: [] for k in ("x", "y", "vx", "vy", "vz")}
+    for j in range(ny):
+        for i in range(nx):
+            for k, v in zip(("x", "y", "vx", "vy", "vz"), bc_sample(cfg, seed, species, 0, i, j, ppc, u, vth)):
+                parts[k].append(v)
+    out = {k: np.concatenate(v) for k, v in parts.items()}
+    out["z"] = np.zeros_like(out["x"])
+    out["w"] = np.full(out["x"].size, n0 * cfg.dx[0] * cfg.dx[1] * cfg.dx[2] / ppc)
+    return out
+
+
 def refill_boundaries(cfg, pl: Plasma, sources, step, seed):
     """Open x boundaries (cfg.bc_cells per end): drop every particle in a
     boundary cell and put in fresh ones from each side's plasma state.

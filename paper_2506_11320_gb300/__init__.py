@@ -48,7 +48,7 @@ class Config(C.Structure):
         ("nsmooth_e", C.c_int32),
         ("bc_cells", C.c_int32),
         ("reserved", C.c_int32),
-        ("bc_seed", C.c_uint64),
+        ("seed", C.c_uint64),
     ]
 
 
@@ -80,6 +80,8 @@ _SIGS = {
                                  C.POINTER(C.c_int)]),
     "gx_fields_set": (C.c_int, [_CTX, _V, _V, C.c_int]),
     "gx_boundary_source": (C.c_int, [_CTX, C.c_int, C.c_int, C.c_double, C.POINTER(C.c_double), C.c_double, C.c_int]),
+    "gx_species_maxwellian": (C.c_int, [_CTX, C.c_double, C.c_double, C.c_int, C.c_double, C.POINTER(C.c_double),
+                                        C.c_double, C.POINTER(C.c_int)]),
     "gx_deposit": (C.c_int, [_CTX, _V]),
     "gx_field_solve": (C.c_int, [_CTX, _V, C.POINTER(SolveStats)]),
     "gx_push_and_deposit": (C.c_int, [_CTX, _V]),
@@ -154,7 +156,7 @@ def _stream(stream):
 def make_config(n, dx, *, c=1.0, theta=0.5, dt=0.02, comoving=1, lf_on=1, lf_speed_c=0, lf_beta=1.0, ns_j=0,
                 nsmooth_u=5, gmres_tol=1e-8, gmres_restart=50, gmres_maxit=2000, precond=GX_PRECOND_NONE,
                 track_ids=0, bin_slack=1.6, divb_clean=0, nsmooth_e=0, bc_cells=0,
-                bc_seed=0) -> Config:
+                seed=0) -> Config:
     n = list(n) + [1] * (3 - len(n))
     dx = list(dx) + [1.0] * (3 - len(dx))
     cfg = Config()
@@ -169,7 +171,7 @@ def make_config(n, dx, *, c=1.0, theta=0.5, dt=0.02, comoving=1, lf_on=1, lf_spe
     cfg.divb_clean = int(divb_clean)
     cfg.nsmooth_e = int(nsmooth_e)
     cfg.bc_cells = int(bc_cells)
-    cfg.bc_seed = int(bc_seed)
+    cfg.seed = int(seed)
     return cfg
 
 
@@ -214,6 +216,14 @@ class Context:
     def fields_set(self, E, B):
         (pe, de), (pb, db) = _ptr(E), _ptr(B)
         self._check(lib().gx_fields_set(self.h, pe, pb, max(de, db)))
+
+    def species_maxwellian(self, q, m, ppc, n0, u, vth):
+        """Add a drifting Maxwellian species drawn on the device; returns its index."""
+        uu = (C.c_double * 3)(*[float(v) for v in u])
+        sid = C.c_int(-1)
+        self._check(lib().gx_species_maxwellian(self.h, float(q), float(m), int(ppc), float(n0), uu, float(vth),
+                                                C.byref(sid)))
+        return sid.value
 
     def boundary_source(self, side, species, n, u, vth, ppc):
         """Plasma state of open boundary `side` (0: low x, 1: high x) for a species."""
@@ -358,7 +368,7 @@ def from_workload(wl, *, track_ids=0, precond=GX_PRECOND_NONE, gmres_tol=None, b
                       divb_clean=divb_clean)
     bc = wl.notes.get("bc") if isinstance(wl.notes, dict) else None
     if bc:
-        cfg.bc_cells, cfg.bc_seed = int(bc["cells"]), int(bc["seed"])
+        cfg.bc_cells, cfg.seed = int(bc["cells"]), int(bc["seed"])
     ctx = Context(cfg)
     for s in wl.species:
         ctx.species_add(s["q"], s["m"], np.ascontiguousarray(s["x"], np.float64),

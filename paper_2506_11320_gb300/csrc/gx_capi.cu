@@ -316,6 +316,27 @@ int gx_species_add(gx_ctx *c, double q, double m, int64_t n, const double *x, co
     return GX_OK;
 }
 
+int gx_species_maxwellian(gx_ctx *c, double q, double m, int ppc, double n0, const double *u, double vth,
+                          int *species_id) {
+    if (!c) return GX_EINVAL;
+    if (c->nspecies >= GX_MAX_SPECIES) { c->err = "at most 4 species"; return GX_EINVAL; }
+    if (!(m > 0) || q == 0.0 || !u || ppc < 1 || ppc > 4096 || !(n0 >= 0.0) || !(vth >= 0.0) ||
+        (int64_t)ppc * c->N > (int64_t)2000000000) {
+        c->err = "gx_species_maxwellian: q != 0, m > 0, 1 <= ppc <= 4096, n0 >= 0, vth >= 0, under 2^31 particles";
+        return GX_EINVAL;
+    }
+    const int s = c->nspecies;
+    c->sp[s].q = q;
+    c->sp[s].m = m;
+    TRY(gx_species_maxwellian_init(c, s, ppc, n0, u, vth, 0));
+    c->nspecies++;
+    c->np_total += (int64_t)ppc * c->N;
+    c->moments_valid = 0;
+    c->pending = 0;
+    if (species_id) *species_id = s;
+    return GX_OK;
+}
+
 int gx_fields_set(gx_ctx *c, const double *E, const double *B, int ptr_is_device) {
     if (!c) return GX_EINVAL;
     const size_t bytes = 3 * c->N * sizeof(double);

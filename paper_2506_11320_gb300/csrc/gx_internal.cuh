@@ -200,6 +200,9 @@ int gx_run_push_deposit(gx_ctx *c, cudaStream_t st);         // mover + re-bin +
 int gx_particles_out(gx_ctx *c, int s, double *x, double *y, double *z, float *vx, float *vy, float *vz,
                      float *w, int32_t *id, cudaStream_t st);
 int gx_regrow_bins(gx_ctx *c, int s, int newcap, cudaStream_t st);
+// a drifting Maxwellian species drawn on the device straight into new bins of species s
+int gx_species_maxwellian_init(gx_ctx *c, int s, int ppc, double n0, const double u[3], double vth,
+                               cudaStream_t st);
 
 // grid (gx_grid.cu)
 int gx_node_fields(gx_ctx *c, const double *Eth, const double *Bcur, float4 *outE, float4 *outB,

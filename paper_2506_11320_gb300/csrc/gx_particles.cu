@@ -285,6 +285,46 @@ __device__ __forceinline__ void philox4x64(uint64_t k0, uint64_t k1, uint64_t x[
     }
 }
 
+// Particle k of cell `cell` in the draw of `step`: key (seed, species), counter
+// (step, cell, k, 0); offsets in the cell from the top 24 bits of words 0 and 1,
+// three normals by the Box-Muller transform of 24-bit uniforms of words 2 and 3;
+// v = u + vth n.  Step 0 is the device-side initialisation, steps >= 1 the
+// boundary refill after each push.
+__device__ __forceinline__ void draw_particle(uint64_t seed, int species, uint64_t step, int64_t cell, int k, int ny,
+                                              float ux, float uy, float uz, float vth, float &ox, float &oy,
+                                              float &vx, float &vy, float &vz) {
+    uint64_t x[4] = {step, (uint64_t)cell, (uint64_t)k, 0ull};
+    philox4x64(seed, (uint64_t)species, x);
+    const float s24 = 1.0f / 16777216.0f;
+    ox = (float)(x[0] >> 40) * s24;
+    oy = ny > 1 ? (float)(x[1] >> 40) * s24 : 0.f;
+    const float u1 = (float)((x[2] >> 40) + 1) * s24, u2 = (float)((x[2] >> 16) & 0xffffffu) * s24;
+    const float u3 = (float)((x[3] >> 40) + 1) * s24, u4 = (float)((x[3] >> 16) & 0xffffffu) * s24;
+    const float ra = sqrtf(-2.f * logf(u1)), rb = sqrtf(-2.f * logf(u3));
+    float sn, cs;
+    sincospif(2.f * u2, &sn, &cs);
+    vx = ux + vth * ra * cs;
+    vy = uy + vth * ra * sn;
+    vz = uz + vth * rb * cospif(2.f * u4);
+}
+
+// Device-side drifting Maxwellian species: ppc draws of step 0 in every cell,
+// written straight into the cell's bin (one CTA per cell).
+__global__ void k_maxwellian(int nx, int ny, int64_t N, int cap, int ppc, uint64_t seed, int species, float ux,
+                             float uy, float uz, float vth, float w, int track, float4 *bins, int *cnt) {
+    for (int64_t cell = blockIdx.x; cell < N; cell += gridDim.x) {
+        for (int k = threadIdx.x; k < ppc; k += blockDim.x) {
+            float ox, oy, vx, vy, vz;
+            draw_particle(seed, species, 0ull, cell, k, ny, ux, uy, uz, vth, ox, oy, vx, vy, vz);
+            const size_t o = (size_t)cell * cap + k;
+            bins[2 * o] = make_float4(ox, oy, vx, vy);
+            bins[2 * o + 1] = make_float4(vz, w, __int_as_float(track ? (int)(cell * ppc + k) : 0), 0.f);
+        }
+        if (threadIdx.x == 0) cnt[cell] = ppc;
+    }
+    (void)nx;
+}
+
 struct BcArgs {
     int nx, ny, G, cap;
     int64_t N;
@@ -318,22 +358,12 @@ __global__ void __launch_bounds__(128) k_bc_refill(BcArgs a) {
     for (int c = 0; c < 4; ++c) { cB[c] = a.dB[nd[c]]; cU[c] = a.dU[nd[c]]; }
     const int ppc = a.ppc[side];
     const float w = a.w[side], vth = a.vth[side];
-    const float s24 = 1.0f / 16777216.0f;
     RegAcc acc;
     acc.zero();
     for (int k = threadIdx.x; k < ppc; k += blockDim.x) {
-        uint64_t x[4] = {a.step, (uint64_t)cell, (uint64_t)k, 0ull};
-        philox4x64(a.seed, (uint64_t)a.species, x);
-        const float ox = (float)(x[0] >> 40) * s24;
-        const float oy = a.ny > 1 ? (float)(x[1] >> 40) * s24 : 0.f;
-        const float u1 = (float)((x[2] >> 40) + 1) * s24, u2 = (float)((x[2] >> 16) & 0xffffffu) * s24;
-        const float u3 = (float)((x[3] >> 40) + 1) * s24, u4 = (float)((x[3] >> 16) & 0xffffffu) * s24;
-        const float ra = sqrtf(-2.f * logf(u1)), rb = sqrtf(-2.f * logf(u3));
-        float sn, cs;
-        sincospif(2.f * u2, &sn, &cs);
-        const float vx = a.u[side][0] + vth * ra * cs;
-        const float vy = a.u[side][1] + vth * ra * sn;
-        const float vz = a.u[side][2] + vth * rb * cospif(2.f * u4);
+        float ox, oy, vx, vy, vz;
+        draw_particle(a.seed, a.species, a.step, cell, k, a.ny, a.u[side][0], a.u[side][1], a.u[side][2], vth, ox, oy,
+                      vx, vy, vz);
         const size_t o = (size_t)cell * a.cap + k;
         a.bins[2 * o] = make_float4(ox, oy, vx, vy);
         a.bins[2 * o + 1] = make_float4(vz, w, __int_as_float(a.track ? -1 : 0), 0.f);
@@ -802,6 +832,23 @@ int gx_bin_particles(gx_ctx *c, int s, int64_t n, const double *x, const double 
     return GX_OK;
 }
 
+int gx_species_maxwellian_init(gx_ctx *c, int s, int ppc, double n0, const double u[3], double vth,
+                               cudaStream_t st) {
+    const double slack = c->cfg.bin_slack > 1.2 ? c->cfg.bin_slack : 1.2;
+    const int cap = round_cap(std::max(64.0, ppc * slack));
+    if (cap >= 32768) { c->err = "more than 32767 particles per cell bin"; return GX_EINVAL; }
+    int rc = alloc_bins(c, s, cap);
+    if (rc) return rc;
+    const double dV = c->cfg.dx[0] * c->cfg.dx[1] * c->cfg.dx[2];
+    const unsigned grid = (unsigned)std::min<int64_t>(c->N, 152 * 64);
+    k_maxwellian<<<grid, 128, 0, st>>>(c->n[0], c->n[1], c->N, cap, ppc, c->cfg.seed, s, (float)u[0], (float)u[1],
+                                       (float)u[2], (float)vth, (float)(n0 * dV / ppc), c->cfg.track_ids,
+                                       c->sp[s].p[c->cur], c->sp[s].cnt[c->cur]);
+    GX_LAUNCHED(c);
+    GX_CHECK(c, cudaStreamSynchronize(st));
+    return GX_OK;
+}
+
 int gx_regrow_bins(gx_ctx *c, int s, int newcap, cudaStream_t st) {
     newcap = round_cap(newcap);
     if (newcap >= 32768) { c->err = "more than 32767 particles per cell bin"; return GX_EOVERFLOW; }
@@ -872,7 +919,7 @@ static int launch_pd(gx_ctx *c, bool push, cudaStream_t st) {
                 // open boundaries: the boundary cells' particles are replaced
                 BcArgs b{};
                 b.nx = c->n[0]; b.ny = c->n[1]; b.G = c->cfg.bc_cells; b.cap = S.cap; b.N = c->N;
-                b.seed = c->cfg.bc_seed; b.step = (uint64_t)(c->npush + 1); b.species = s;
+                b.seed = c->cfg.seed; b.step = (uint64_t)(c->npush + 1); b.species = s;
                 b.track = c->cfg.track_ids;
                 b.bc = p.bc;
                 const double dV = c->cfg.dx[0] * c->cfg.dx[1] * c->cfg.dx[2];

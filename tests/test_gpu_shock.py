@@ -110,7 +110,7 @@ def test_boundary_api_edge_cases(gx):
             gx.Context(gx.make_config(wl.n, wl.dx, **base, **kw))
         assert e.value.status == gx.GX_EINVAL
     # a push before every species has its sources: GX_ESTATE, and the context stays usable
-    ctx = gx.Context(gx.make_config(wl.n, wl.dx, **base, bc_cells=8, bc_seed=5))
+    ctx = gx.Context(gx.make_config(wl.n, wl.dx, **base, bc_cells=8, seed=5))
     for s in wl.species:
         ctx.species_add(s["q"], s["m"], s["x"], s["y"], s["z"], s["vx"], s["vy"], s["vz"], s["w"])
     ctx.fields_set(wl.E0, wl.B0)
