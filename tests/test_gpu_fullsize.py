@@ -1,6 +1,7 @@
-"""Parity at the benchmark's full size, in the launch configuration bench.py
-times: the 512 x 256 Harris workload, 100 particles per cell and species
-(26.2 M particles), one step of the CUDA path through the C ABI.
+"""Parity at the benchmark's full sizes, in the launch configuration bench.py
+times: the 512 x 256 Harris workload (26.2 M particles) and the 1024 x 512 one
+of the learned-preconditioner comparison (104.9 M particles), 100 particles per
+cell and species, one step of the CUDA path through the C ABI.
 
 The oracle cannot run the whole step at this size in seconds, so the check is
 on sampled outputs it can compute one by one: for a few 8 x 8-cell patches the
@@ -31,14 +32,15 @@ def rel(a, b):
     return float(np.linalg.norm(a - b) / (nb if nb > 0 else 1.0))
 
 
-@pytest.fixture(scope="module")
-def state():
+@pytest.fixture(scope="module", params=[(512, 256), (1024, 512)], ids=["512x256", "1024x512"])
+def state(request):
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     import paper_2506_11320_gb300 as g
     g.lib()
-    wl = workloads.harris(nx=512, ny=256, ppc=100)
+    nx, ny = request.param
+    wl = workloads.harris(nx=nx, ny=ny, ppc=100)
     ctx = g.from_workload(wl)
     st = ctx.step(1)
     assert st.converged
@@ -74,10 +76,13 @@ def patch_inputs(S, i0, j0):
     return cfg, Bsub, usub, species, gi, gj
 
 
-@pytest.mark.parametrize("i0,j0", [(100, 60), (240, 124), (508, 252)])
-def test_sampled_patch_moments_match_oracle(state, i0, j0):
+@pytest.mark.parametrize("where", ["interior", "centre", "periodic corner"])
+def test_sampled_patch_moments_match_oracle(state, where):
     S = state
     wl = S["wl"]
+    nx, ny = wl.n[0], wl.n[1]
+    i0, j0 = {"interior": (nx // 5, ny // 4 - 4), "centre": (nx // 2 - 16, ny // 2 - 4),
+              "periodic corner": (nx - 4, ny - 4)}[where]
     cfg, Bsub, usub, species, gi, gj = patch_inputs(S, i0, j0)
     assert sum(sp["x"].size for sp in species) > 8 * 8 * 100       # the patch is populated
     pl = O.Plasma.from_species(species)
