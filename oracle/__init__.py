@@ -62,7 +62,7 @@ class Cfg(C.Structure):
         ("lf_beta", C.c_double),
         ("gmres_tol", C.c_double),
         ("bc_cells", C.c_int32),
-        ("_pad", C.c_int32),
+        ("bc_wall", C.c_int32),
     ]
 
     @property
@@ -76,7 +76,7 @@ class Cfg(C.Structure):
 
 def make_cfg(n, dx, *, c=1.0, theta=0.5, dt=0.02, comoving=0, lf_on=0, lf_speed_c=0, lf_beta=1.0,
              ns_j=0, nsmooth_u=5, gmres_tol=1e-12, gmres_restart=50, gmres_maxit=5000, divb_clean=0,
-             nsmooth_e=0, bc_cells=0) -> Cfg:
+             nsmooth_e=0, bc_cells=0, bc_wall=0) -> Cfg:
     n = list(n) + [1] * (3 - len(n))
     dx = list(dx) + [1.0] * (3 - len(dx))
     cfg = Cfg()
@@ -90,8 +90,11 @@ def make_cfg(n, dx, *, c=1.0, theta=0.5, dt=0.02, comoving=0, lf_on=0, lf_speed_
     cfg.divb_clean = int(divb_clean)
     cfg.nsmooth_e = int(nsmooth_e)
     cfg.bc_cells = int(bc_cells)
+    cfg.bc_wall = int(bc_wall)
     if cfg.bc_cells and (cfg.divb_clean or 2 * cfg.bc_cells >= cfg.n[0]):
         raise ValueError("open boundaries: no divergence cleaning, and 2 bc_cells < nx")
+    if cfg.bc_wall and not cfg.bc_cells:
+        raise ValueError("a reflecting wall needs bc_cells > 0")
     return cfg
 
 
@@ -413,17 +416,19 @@ def refill_boundaries(cfg, pl: Plasma, sources, step, seed):
     boundary cell and put in fresh ones from each side's plasma state.
 
     sources[side][s] = dict(n=density, u=(ux, uy, uz), vth=thermal speed, ppc=count) for side 0 (low x)
-    and 1 (high x) and species s; weights n dV / ppc.  Returns the new Plasma; cells are visited in
-    index order (j, then i), species in order, so the result matches the device's bins as a set."""
+    and 1 (high x) and species s; weights n dV / ppc.  With cfg.bc_wall the high side is a reflecting
+    wall: no particles there and no refill (sources[1] unused).  Returns the new Plasma; cells are
+    visited in index order (j, then i), species in order, so the result matches the device's bins as
+    a set."""
     nx, ny, G = cfg.n[0], cfg.n[1], cfg.bc_cells
     ci = np.floor(pl.x / cfg.dx[0]).astype(np.int64) % nx
-    keep = ~((ci < G) | (ci >= nx - G))
+    keep = ~((ci < G) | ((ci >= nx - G) & (cfg.bc_wall == 0)))
     parts = {k: [getattr(pl, k)[keep]] for k in ("x", "y", "z", "vx", "vy", "vz", "w")}
     sp = [pl.sp[keep]]
     dV = cfg.dx[0] * cfg.dx[1] * cfg.dx[2]
     for s in range(len(pl.q)):
         for j in range(ny):
-            for i in list(range(G)) + list(range(nx - G, nx)):
+            for i in list(range(G)) + ([] if cfg.bc_wall else list(range(nx - G, nx))):
                 src = sources[0 if i < G else 1][s]
                 x, y, vx, vy, vz = bc_sample(cfg, seed, s, step, i, j, src["ppc"], src["u"], src["vth"])
                 for k, v in (("x", x), ("y", y), ("z", np.zeros_like(x)), ("vx", vx), ("vy", vy), ("vz", vz),

@@ -89,7 +89,7 @@ typedef struct {
     double lf_beta;        /* MC limiter parameter beta (Eq. 21) */
     double gmres_tol;      /* relative residual target */
     int32_t bc_cells;      /* open x boundaries: cells per end held at a fixed plasma state (0: periodic) */
-    int32_t _pad;
+    int32_t bc_wall;       /* 1: the high-x boundary cells are a reflecting conducting wall instead */
 } or_cfg;
 
 /* ---------------------------------------------------------------- indexing */
@@ -124,8 +124,12 @@ static inline int bcell(const or_cfg *g, int i) {
     return g->bc_cells > 0 && (i < g->bc_cells || i >= g->n[0] - g->bc_cells);
 }
 static inline int bnode(const or_cfg *g, int i) {
-    return g->bc_cells > 0 && (i <= g->bc_cells - 1 || i >= g->n[0] - g->bc_cells + 1);
+    return g->bc_cells > 0 && (i <= g->bc_cells - 1 || i >= g->n[0] - g->bc_cells + (g->bc_wall ? 0 : 1));
 }
+/* With bc_wall the high-x boundary cells are a perfect conductor at rest (the
+ * reflecting wall of the shock setups): no particles, E held (at 0 from the
+ * initial fields) from the wall face x_w = (nx - G) dx on, B held, and a
+ * particle that crosses x_w is reflected specularly: x -> 2 x_w - x, v_x -> -v_x. */
 
 /* ----------------------------------------------------------- shape function */
 
@@ -881,6 +885,10 @@ double or_mover(const or_cfg *g, const double *qs, const double *ms, int64_t np,
             double disp = g->dt * vn[d];
             double L = g->n[d] * g->dx[d];
             double xn = *xs[d] + disp;
+            if (d == 0 && g->bc_cells > 0 && g->bc_wall) {
+                const double xw = (g->n[0] - g->bc_cells) * g->dx[0];
+                if (xn >= xw) { xn = 2.0 * xw - xn; vx[p] = -vx[p]; }
+            }
             xn = fmod(xn, L);
             if (xn < 0.0) xn += L;
             if (xn >= L) xn -= L;

@@ -117,3 +117,44 @@ def test_dirichlet_rows_act_locally():
     mid = slice(40, 80)
     assert np.abs(res[8][0][..., mid] - res[0][0][..., mid]).max() <= 1e-12
     assert np.abs(res[8][1][..., mid] - res[0][1][..., mid]).max() <= 1e-12
+
+
+def test_wall_reflects_specularly():
+    """With no fields the mover moves a particle in a straight line (alpha = I);
+    one crossing the wall face x_w = (nx - G) dx comes back at 2 x_w - x with
+    v_x reversed, exactly, and the others are untouched."""
+    nx, G, dx, dt = 40, 8, 0.1, 0.05
+    cfg = O.make_cfg((nx, 1, 1), (dx, 1.0, 1.0), dt=dt, bc_cells=G, bc_wall=1)
+    xw = (nx - G) * dx
+    x0 = np.array([xw - 0.01, xw - 0.05, 1.0, xw - 0.002])
+    vx0 = np.array([0.8, -0.3, 0.5, 0.05])
+    z = np.zeros(4)
+    pl = O.Plasma([1.0], [1.0], np.zeros(4, np.int32), x0.copy(), z.copy(), z.copy(), vx0.copy(),
+                  np.full(4, 0.1), z.copy(), np.ones(4))
+    O.mover(cfg, pl, np.zeros((3, 1, 1, nx)), np.zeros((3, 1, 1, nx)))
+    moved = x0 + dt * vx0
+    refl = moved >= xw
+    assert refl.tolist() == [True, False, False, True]
+    assert np.array_equal(pl.x, np.where(refl, 2 * xw - moved, moved))
+    assert np.array_equal(pl.vx, np.where(refl, -vx0, vx0))
+    assert np.array_equal(pl.vy, np.full(4, 0.1))
+
+
+def test_wall_region_stays_empty_and_field_free():
+    wl = workloads.shock_wall(nx=96, ny=1, ppc=16, steps=4)
+    bc = wl.notes["bc"]
+    G, nx = bc["cells"], wl.n[0]
+    cfg = O.make_cfg(wl.n, wl.dx, bc_cells=G, bc_wall=1, **wl.grid_kwargs())
+    pl = O.Plasma.from_species(wl.species)
+    E, B = wl.E0.copy(), wl.B0.copy()
+    n_in = pl.np
+    for step in range(1, 5):
+        assert O.step(cfg, pl, E, B)["rc"] == 0
+        ci = np.floor(pl.x / wl.dx[0]).astype(int) % nx
+        assert not np.any(ci >= nx - G)                        # nothing crosses the wall
+        assert pl.np == n_in                                   # nor leaves through it
+        pl = O.refill_boundaries(cfg, pl, bc["sources"], step, bc["seed"])
+        n_in = pl.np
+    Ew = E.reshape(3, -1)[:, nx - G:]
+    assert np.all(Ew == 0.0)                                   # the conductor holds E = 0 from its face on
+    assert np.array_equal(B.reshape(3, -1)[:, nx - G:], wl.B0.reshape(3, -1)[:, nx - G:])

@@ -361,6 +361,41 @@ def shock_1d(kind="parallel", dx=None, length=None, ppc=100, bc_cells=8, seed=12
                                x_shock=x_shock, mass_ratio=mass_ratio, kind=kind))
 
 
+def shock_wall(nx=1024, ny=8, dx=0.1, ppc=256, u=0.2, vth_e=0.03, mass_ratio=100.0, b0=0.05, bc_cells=8,
+               seed=12345, comoving=1, ns_j=1, lf_on=1, lf_beta=1.0, gmres_tol=1e-8, steps=2000):
+    """Shock by reflection: a uniform plasma (density n0, bulk velocity u along
+    +x, B = b0 (cos 45, 0, sin 45), T_i = T_e) streams from an open boundary at
+    x = 0 onto a reflecting conducting wall at the high-x end (the last bc_cells
+    cells: no particles, E = 0, B frozen).  Defaults: 1024 x 8 cells of 0.1 d_i,
+    256 particles per cell and species, m_i/m_e = 100, vth_e = 0.03 c, vth_i =
+    vth_e / sqrt(mass_ratio), dt = 0.2 dx / (u + 3 vth_e).  The paper's shocks
+    are set up from printed Rankine-Hugoniot states instead (shock_1d); this is
+    the reflecting-wall form of the same physics."""
+    n = (nx, int(ny), 1)
+    dxs = (dx, dx if ny > 1 else 1.0, 1.0)
+    vth_i = vth_e / math.sqrt(mass_ratio)
+    dt = 0.2 * dx / (u + 3 * vth_e)
+    B = (b0 * math.cos(math.pi / 4), 0.0, b0 * math.sin(math.pi / 4))
+    uu = (u, 0.0, 0.0)
+    species = []
+    for k, (q, m, vth) in enumerate(((-1.0, 1.0 / mass_ratio, vth_e), (1.0, 1.0, vth_i))):
+        sp = drifting_species(n, dxs, ppc, q=q, m=m, density=N0, u=uu, vth=vth, seed=seed, k=1 - k)
+        keep = sp["x"] < (nx - bc_cells) * dx                     # the wall cells hold no particles
+        for key in ("x", "y", "z", "vx", "vy", "vz", "w"):
+            sp[key] = sp[key][keep]
+        if ny == 1:
+            sp["y"] = np.zeros_like(sp["x"])
+        species.append(sp)
+    E, Bc = _uniform_fields(n, 1.0, uu, B)
+    E[:, :, :, nx - bc_cells:] = 0.0                             # the conductor: E = 0 from the wall face on
+    src = [dict(n=N0, u=uu, vth=vth_e, ppc=ppc), dict(n=N0, u=uu, vth=vth_i, ppc=ppc)]
+    return Workload(name=f"shock_wall_{nx}x{int(ny)}_ppc{ppc}", n=n, dx=dxs, c=1.0, theta=0.5, dt=dt,
+                    comoving=comoving, lf_on=lf_on, lf_beta=lf_beta, lf_speed_c=0, ns_j=ns_j, nsmooth_u=5,
+                    gmres_tol=gmres_tol, species=species, E0=E, B0=Bc, steps=steps,
+                    notes=dict(bc=dict(cells=bc_cells, seed=seed, wall=1, sources=[src, src]), u=u,
+                               mass_ratio=mass_ratio))
+
+
 def tophat_1d(n=80, dx=0.01, cfl=0.4, lf_on=1, lf_beta=1.0, theta=0.5):
     """Vacuum light wave with a top-hat E_y = B_z = 1 for |x| < 0.2 on
     [-0.4, 0.4) (shifted to [0, 0.8)), c = 1; the advection test of Sec. 3.1."""
