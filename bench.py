@@ -218,14 +218,15 @@ def run_reference(args):
     return 0
 
 
-def run_shock(gx, warmup, steps, barrier, dist, world):
-    """Push+deposit throughput on the shock-shaped plasma: the paper's quasi-
-    parallel shock (printed states, open boundaries refilled every step) over 940
-    x 8 cells of 0.4 d_i with 256 particles per cell and species (3.85 M
-    particles, the size of a 1024 x 8-cell, 256-ppc shock), timed like the main
-    workload (library CUDA events over push, refill and moments)."""
+def run_shock(gx, warmup, steps, barrier, dist, world, wall=False):
+    """Push+deposit throughput on a shock-shaped plasma, timed like the main
+    workload (library CUDA events over push, refill and moments): the paper's
+    quasi-parallel shock (printed states, open boundaries refilled every step)
+    over 940 x 8 cells of 0.4 d_i with 256 particles per cell and species (3.85 M
+    particles), or with `wall` the shock by reflection (inflow at 0.2 c onto a
+    reflecting conducting wall, 1024 x 8 cells of 0.1 d_i, 256 ppc, 4.16 M)."""
     import torch
-    wl = workloads.shock_1d("parallel", ny=8, ppc=256)
+    wl = workloads.shock_wall() if wall else workloads.shock_1d("parallel", ny=8, ppc=256)
     ctx = gx.from_workload(wl)
     for _ in range(warmup):
         ctx.step(1, allow_noconv=True)
@@ -244,8 +245,10 @@ def run_shock(gx, warmup, steps, barrier, dist, world):
                                     dist, "cuda")
     return {"value": whole_job_rate(world, npart, pd_ms), "unit": UNIT, "push_deposit_ms_per_step": pd_ms,
             "ms_per_step": step_ms, "particles": npart,
-            "workload": f"{wl.name}: the paper's 1D quasi-parallel shock (printed up/downstream states, M_A 7, "
-                        f"m_i/m_e 25, c = 3000 km/s) on {wl.n[0]}x{wl.n[1]} cells, open x boundaries"}
+            "workload": (f"{wl.name}: inflow at 0.2 c onto a reflecting conducting wall, m_i/m_e 100, "
+                         f"{wl.n[0]}x{wl.n[1]} cells" if wall else
+                         f"{wl.name}: the paper's 1D quasi-parallel shock (printed up/downstream states, M_A 7, "
+                         f"m_i/m_e 25, c = 3000 km/s) on {wl.n[0]}x{wl.n[1]} cells, open x boundaries")}
 
 
 def main():
@@ -350,9 +353,10 @@ def main():
         del pwl
 
     # ------------------------------------------------------- shock-shaped plasma
-    shock = None
+    shock = shock_wall = None
     if not args.no_shock:
         shock = run_shock(gx, args.warmup, args.steps, barrier, dist, world)
+        shock_wall = run_shock(gx, args.warmup, args.steps, barrier, dist, world, wall=True)
 
     # ------------------------------------------------------- end to end (host buffers)
     e2e = None
@@ -385,7 +389,7 @@ def main():
             "gmres_ms_per_step": solve_ms, "gmres_iters_per_step": statistics.mean(iters),
             "wall_ms_per_step": 1000 * wall / args.steps,
             "gmres_learned_vs_plain": solve_cmp,
-            "shock": shock,
+            "shock": shock, "shock_wall": shock_wall,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "gpu_launches": int(tm["launches"]),
         }

@@ -105,6 +105,13 @@ typedef struct gx_ctx gx_ctx;
  *                 particles per species drawn from that side's source (see
  *                 gx_boundary_source).  y stays periodic.  Not with divb_clean;
  *                 2 G < nx.
+ *   bc_wall       with bc_cells: 1 turns the high-x boundary cells into a
+ *                 reflecting perfect conductor at rest (the shock-by-reflection
+ *                 setup): they hold no particles and get no refill, E is held
+ *                 (at its initial value, 0 for a conductor) from the wall face
+ *                 x_w = (nx - G) dx on, B is held, and a particle crossing x_w
+ *                 is reflected specularly (x -> 2 x_w - x, v_x -> -v_x).  Only
+ *                 side 0 then needs gx_boundary_source.
  *   seed          key of the context's counter-based draws (Philox4x64-10 with
  *                 key (seed, species)): the device-side Maxwellian species
  *                 (gx_species_maxwellian, counter (0, cell, particle, 0)) and the
@@ -130,7 +137,7 @@ typedef struct {
     int32_t divb_clean;
     int32_t nsmooth_e;
     int32_t bc_cells;
-    int32_t reserved;
+    int32_t bc_wall;
     uint64_t seed;
 } gx_config;
 

@@ -47,7 +47,7 @@ class Config(C.Structure):
         ("divb_clean", C.c_int32),
         ("nsmooth_e", C.c_int32),
         ("bc_cells", C.c_int32),
-        ("reserved", C.c_int32),
+        ("bc_wall", C.c_int32),
         ("seed", C.c_uint64),
     ]
 
@@ -156,7 +156,7 @@ def _stream(stream):
 def make_config(n, dx, *, c=1.0, theta=0.5, dt=0.02, comoving=1, lf_on=1, lf_speed_c=0, lf_beta=1.0, ns_j=0,
                 nsmooth_u=5, gmres_tol=1e-8, gmres_restart=50, gmres_maxit=2000, precond=GX_PRECOND_NONE,
                 track_ids=0, bin_slack=1.6, divb_clean=0, nsmooth_e=0, bc_cells=0,
-                seed=0) -> Config:
+                bc_wall=0, seed=0) -> Config:
     n = list(n) + [1] * (3 - len(n))
     dx = list(dx) + [1.0] * (3 - len(dx))
     cfg = Config()
@@ -171,6 +171,7 @@ def make_config(n, dx, *, c=1.0, theta=0.5, dt=0.02, comoving=1, lf_on=1, lf_spe
     cfg.divb_clean = int(divb_clean)
     cfg.nsmooth_e = int(nsmooth_e)
     cfg.bc_cells = int(bc_cells)
+    cfg.bc_wall = int(bc_wall)
     cfg.seed = int(seed)
     return cfg
 
@@ -368,7 +369,7 @@ def from_workload(wl, *, track_ids=0, precond=GX_PRECOND_NONE, gmres_tol=None, b
                       divb_clean=divb_clean)
     bc = wl.notes.get("bc") if isinstance(wl.notes, dict) else None
     if bc:
-        cfg.bc_cells, cfg.seed = int(bc["cells"]), int(bc["seed"])
+        cfg.bc_cells, cfg.seed, cfg.bc_wall = int(bc["cells"]), int(bc["seed"]), int(bc.get("wall", 0))
     ctx = Context(cfg)
     for s in wl.species:
         ctx.species_add(s["q"], s["m"], np.ascontiguousarray(s["x"], np.float64),
@@ -377,7 +378,7 @@ def from_workload(wl, *, track_ids=0, precond=GX_PRECOND_NONE, gmres_tol=None, b
                         np.ascontiguousarray(s["vz"], np.float32), np.ascontiguousarray(s["w"], np.float32))
     ctx.fields_set(np.ascontiguousarray(wl.E0, np.float64), np.ascontiguousarray(wl.B0, np.float64))
     if bc:
-        for side in range(2):
+        for side in range(1 if bc.get("wall", 0) else 2):
             for s, src in enumerate(bc["sources"][side]):
                 ctx.boundary_source(side, s, src["n"], src["u"], src["vth"], src["ppc"])
     return ctx

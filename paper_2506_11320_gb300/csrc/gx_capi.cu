@@ -228,6 +228,7 @@ int gx_create(const gx_config *cfg, gx_ctx **out) {
     if (cfg->bc_cells < 0 || (cfg->bc_cells > 0 && (cfg->bc_cells < 8 || 2 * cfg->bc_cells >= cfg->n[0])))
         return fail(GX_EINVAL, "bc_cells must be 0 or >= 8 with 2 bc_cells < nx");
     if (cfg->bc_cells > 0 && cfg->divb_clean) return fail(GX_EINVAL, "open boundaries without divb_clean");
+    if (cfg->bc_wall && cfg->bc_cells <= 0) return fail(GX_EINVAL, "a reflecting wall needs bc_cells > 0");
     if (cfg->lf_on && cfg->lf_beta < 0) return fail(GX_EINVAL, "lf_beta must be >= 0");
     c->dim = 2;
     c->N = (int64_t)c->n[0] * c->n[1] * c->n[2];
@@ -406,7 +407,7 @@ int gx_push_and_deposit(gx_ctx *c, void *stream) {
     if (!c->pending) { c->err = "gx_push_and_deposit needs a preceding gx_field_solve"; return GX_ESTATE; }
     if (c->cfg.bc_cells > 0)      // refuse before anything is launched
         for (int s = 0; s < c->nspecies; ++s)
-            for (int sd = 0; sd < 2; ++sd)
+            for (int sd = 0; sd < (c->cfg.bc_wall ? 1 : 2); ++sd)
                 if (c->bsrc[sd][s].ppc < 1) {
                     c->err = "open boundaries need gx_boundary_source for every species on both sides";
                     return GX_ESTATE;

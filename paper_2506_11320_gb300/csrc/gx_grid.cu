@@ -633,7 +633,8 @@ __global__ void k_diag_particles(int64_t ncell, int cap, const int *cnt, const f
 }
 
 G2 geom(const gx_ctx *c) {
-    return G2{c->n[0], c->n[1], c->cfg.dx[0], c->cfg.dx[1], 0.5 / c->cfg.dx[0], 0.5 / c->cfg.dx[1], c->cfg.bc_cells};
+    return G2{c->n[0], c->n[1], c->cfg.dx[0], c->cfg.dx[1], 0.5 / c->cfg.dx[0], 0.5 / c->cfg.dx[1], c->cfg.bc_cells,
+              c->cfg.bc_cells > 0 ? c->cfg.bc_wall : 0};
 }
 
 SpecK speck(const gx_ctx *c) {

@@ -29,14 +29,17 @@ struct G2 {
     double dx, dy;
     double hx, hy;          // 1 / (2 dx), 1 / (2 dy): the averaged differences' factors
     int bc;                 // open x boundaries: cells per end held fixed (0: periodic)
+    int wall;               // 1: the high-x boundary cells are a reflecting conductor
     __device__ __forceinline__ int64_t id(int i, int j) const {
         return (int64_t)gx_wr(i, nx) + (int64_t)nx * gx_wr(j, ny);
     }
     __device__ __forceinline__ int64_t N() const { return (int64_t)nx * ny; }
     // boundary cells: i < bc or i >= nx - bc; boundary nodes: both x-neighbouring cells are
-    // boundary cells (i <= bc - 1 or i >= nx - bc + 1)
+    // boundary cells (i <= bc - 1 or i >= nx - bc + 1), and with the wall also its face node nx - bc
     __device__ __forceinline__ bool bcell(int i) const { return bc > 0 && (i < bc || i >= nx - bc); }
-    __device__ __forceinline__ bool bnode(int i) const { return bc > 0 && (i <= bc - 1 || i >= nx - bc + 1); }
+    __device__ __forceinline__ bool bnode(int i) const {
+        return bc > 0 && (i <= bc - 1 || i >= nx - bc + (wall ? 0 : 1));
+    }
 };
 
 struct OpArgs {

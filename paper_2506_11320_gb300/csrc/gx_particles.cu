@@ -66,6 +66,7 @@ struct P2 {
     float *rec;                  // [112][N] for this species
     DevFlags *flags;
     int arrivals;                // deposit only the back segments (the particles that arrived)
+    int wall_ci;                 // x index of the last cell before a reflecting wall, or -1
 };
 
 // dynamic shared memory: mbarriers, staging [group][buffer][slot][2] float4,
@@ -331,6 +332,7 @@ struct BcArgs {
     uint64_t seed, step;
     int species, track;
     float bc;                    // beta / c of the species (alpha)
+    int nsides;                  // 2, or 1 with a reflecting wall on the high side (no refill there)
     int ppc[2];                  // per side (0: low x, 1: high x)
     float w[2], vth[2], u[2][3];
     float4 *bins;                // the current copy (after the push)
@@ -346,7 +348,7 @@ struct BcArgs {
 // overwrite the cell's record and count.
 __global__ void __launch_bounds__(128) k_bc_refill(BcArgs a) {
     __shared__ float red[4][Rec<2>::SIZE];
-    const int t = blockIdx.x, G2c = 2 * a.G;
+    const int t = blockIdx.x, G2c = a.nsides * a.G;
     const int j = t / G2c, r = t % G2c;
     const int side = r < a.G ? 0 : 1;
     const int i = r < a.G ? r : a.nx - G2c + r;
@@ -384,7 +386,10 @@ __global__ void __launch_bounds__(128) k_bc_refill(BcArgs a) {
 }
 
 // ------------------------------------------------------------ fused kernel
-template <bool PUSH>
+// WALL: the push reflects particles at the high-x face of cell x index
+// p.wall_ci (a reflecting wall); a separate instantiation, so that the push
+// without a wall compiles exactly as it would without the feature
+template <bool PUSH, bool WALL = false>
 __global__ void __launch_bounds__(kThreads, 1) k_pd(P2 p) {
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem);                         // [groups][2]
@@ -462,6 +467,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_pd(P2 p) {
         const int nchf = (bin_front(word) + kChunk - 1) / kChunk;
         const int wmax = __reduce_max_sync(kFull, nch);
         const int ci = valid ? (int)(cell % p.nx) : 0, cj = valid ? (int)(cell / p.nx) : 0;
+        const bool wallc = WALL && PUSH && ci == p.wall_ci;      // the wall is this cell's high-x face
         int64_t nd[4];
         corner_nodes(ci, cj, p.nx, p.ny, nd);
         float4 cB[4], cU[4], mE[4], mB[4];
@@ -522,6 +528,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_pd(P2 p) {
                         const float vbz = (az + (ax * by - ay * bx) + ab * bz) * inv;
                         vx = 2.f * vbx - vx; vy = 2.f * vby - vy; vz = 2.f * vbz - vz;
                         x = fmaf(vx, p.dtdx, x);
+                        if (WALL && wallc && x >= 1.f) { x = 2.f - x; vx = -vx; }   // specular reflection
                         y = fmaf(vy, p.dtdy, y);
                         float fx = floorf(x), fy = floorf(y);
                         x -= fx; y -= fy;
@@ -869,6 +876,8 @@ static int launch_pd(gx_ctx *c, bool push, cudaStream_t st) {
     static bool configured = false;
     if (!configured) {
         GX_CHECK(c, cudaFuncSetAttribute(k_pd<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pd_smem_bytes()));
+        GX_CHECK(c, cudaFuncSetAttribute(k_pd<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)pd_smem_bytes()));
         GX_CHECK(c, cudaFuncSetAttribute(k_pd<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pd_smem_bytes()));
         configured = true;
     }
@@ -895,12 +904,14 @@ static int launch_pd(gx_ctx *c, bool push, cudaStream_t st) {
         p.cnt_out = S.cnt[nxt];
         p.rec = c->rec + (size_t)s * c->N * Rec<2>::SIZE;
         p.flags = c->dflags;
+        p.wall_ci = (c->cfg.bc_cells > 0 && c->cfg.bc_wall) ? c->n[0] - c->cfg.bc_cells - 1 : -1;
         if (push) {
             p.mE = c->nE; p.mB = c->nB; p.dB = c->nBnext; p.dU = c->nUref;
             GX_CHECK(c, cudaMemsetAsync(S.cnt[nxt], 0, c->N * sizeof(int), st));
             cudaEvent_t e0 = gx_ev_get(c), e1 = gx_ev_get(c);
             GX_CHECK(c, cudaEventRecord(e0, st));
-            k_pd<true><<<grid, kThreads, pd_smem_bytes(), st>>>(p);
+            if (p.wall_ci >= 0) k_pd<true, true><<<grid, kThreads, pd_smem_bytes(), st>>>(p);
+            else k_pd<true><<<grid, kThreads, pd_smem_bytes(), st>>>(p);
             GX_LAUNCHED(c);
             GX_CHECK(c, cudaEventRecord(e1, st));
             gx_ev_push(c, GX_T_PDK, e0, e1);
@@ -923,7 +934,8 @@ static int launch_pd(gx_ctx *c, bool push, cudaStream_t st) {
                 b.track = c->cfg.track_ids;
                 b.bc = p.bc;
                 const double dV = c->cfg.dx[0] * c->cfg.dx[1] * c->cfg.dx[2];
-                for (int sd = 0; sd < 2; ++sd) {
+                b.nsides = c->cfg.bc_wall ? 1 : 2;
+                for (int sd = 0; sd < b.nsides; ++sd) {
                     const BcSource &src = c->bsrc[sd][s];
                     if (src.ppc < 1) { c->err = "open boundaries need gx_boundary_source for every species"; return GX_ESTATE; }
                     if (src.ppc > S.cap) { c->err = "boundary ppc above the bin capacity"; return GX_EOVERFLOW; }
@@ -933,7 +945,7 @@ static int launch_pd(gx_ctx *c, bool push, cudaStream_t st) {
                     for (int d = 0; d < 3; ++d) b.u[sd][d] = (float)src.u[d];
                 }
                 b.bins = p.out; b.cnt = p.cnt_out; b.rec = p.rec; b.dB = p.dB; b.dU = p.dU;
-                k_bc_refill<<<(unsigned)(2 * b.G * b.ny), 128, 0, st>>>(b);
+                k_bc_refill<<<(unsigned)(b.nsides * b.G * b.ny), 128, 0, st>>>(b);
                 GX_LAUNCHED(c);
             }
         } else {

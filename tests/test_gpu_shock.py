@@ -135,3 +135,33 @@ def test_boundary_api_edge_cases(gx):
     counts = np.bincount(np.floor(x / wl.dx[0]).astype(int) % nx, minlength=nx)
     assert np.all(counts[np.r_[0:G, nx - G:nx]] == 300)
     ctx.close()
+
+
+def test_wall_shock_matches_oracle(gx):
+    """Shock by reflection: inflow at x = 0 onto the reflecting conducting wall
+    (96 x 2 cells, 16 particles per cell and species): three steps against the
+    oracle (E and B within 3e-6), equal particle counts, an empty wall region
+    and E = 0 there bit for bit."""
+    wl = workloads.shock_wall(nx=96, ny=2, ppc=16, steps=3)
+    bc = wl.notes["bc"]
+    G, nx, ny = bc["cells"], wl.n[0], wl.n[1]
+    ctx = gx.from_workload(wl, gmres_tol=1e-12)
+    for _ in range(3):
+        assert ctx.step(1).converged == 1
+    E1, B1 = ctx.get_fields()
+    parts = [ctx.get_particles(s) for s in range(2)]
+    ctx.close()
+    cfg = O.make_cfg(wl.n, wl.dx, bc_cells=G, bc_wall=1, **wl.grid_kwargs())
+    cfg.gmres_tol = 1e-12
+    pl = O.Plasma.from_species(wl.species)
+    E, B = wl.E0.copy(), wl.B0.copy()
+    for t in range(1, 4):
+        assert O.step(cfg, pl, E, B)["rc"] == 0
+        pl = O.refill_boundaries(cfg, pl, bc["sources"], t, bc["seed"])
+    errs = {"E": rel(E1, E), "B": rel(B1, B)}
+    assert all(v <= 3e-6 for v in errs.values()), errs
+    for s in range(2):
+        assert len(parts[s]["x"]) == int((pl.sp == s).sum())
+        ci = np.floor(parts[s]["x"] / wl.dx[0]).astype(int) % nx
+        assert not np.any(ci >= nx - G)
+    assert np.all(E1.reshape(3, ny, nx)[:, :, nx - G:] == 0.0)
