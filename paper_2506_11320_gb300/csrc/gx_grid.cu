@@ -406,6 +406,11 @@ __global__ void k_rhs(G2 g, const double *__restrict__ E, const double *__restri
     const int64_t N = g.N();
     GRID_LOOP(q, N) {
         const int i = (int)(q % g.nx), j = (int)(q / g.nx);
+        if (g.bnode(i)) {   // Dirichlet row of an open boundary: b = E^n
+#pragma unroll
+            for (int c = 0; c < 3; ++c) b[c * N + q] = E[c * N + q];
+            continue;
+        }
         const double *Bx = B, *By = B + N, *Bz = B + 2 * N;
         double cn[3];
         cn[0] = dNy(g, Bz, i, j);
@@ -427,10 +432,6 @@ __global__ void k_rhs(G2 g, const double *__restrict__ E, const double *__restri
             }
 #pragma unroll
             for (int r = 0; r < 3; ++r) out[r] = fma(mf, m[r], out[r]);
-        }
-        if (g.bnode(i)) {   // Dirichlet row: b = E^n
-#pragma unroll
-            for (int k = 0; k < 3; ++k) out[k] = E[k * N + q];
         }
 #pragma unroll
         for (int k = 0; k < 3; ++k) b[k * N + q] = out[k];
