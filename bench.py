@@ -62,6 +62,11 @@ def make_workload(name):
         return workloads.harris(nx=128, ny=64, ppc=100), "2D Harris sheet 128x64 cells, 100 ppc/species"
     if name == "uniform":
         return workloads.uniform_drift(n=(32, 32, 1), ppc=64), "2D periodic 32x32, 64 ppc/species"
+    if name == "shock_parallel":
+        return (workloads.shock_1d("parallel", ny=8, ppc=256),
+                "quasi-parallel shock from the printed states, 940x8 cells, 256 ppc/species, open x boundaries")
+    if name == "shock_wall":
+        return workloads.shock_wall(), "shock by reflection: inflow onto a reflecting wall, 1024x8 cells, 256 ppc"
     raise SystemExit(f"unknown workload {name}")
 
 
