@@ -182,12 +182,17 @@ def test_plain_ecsim_energy_conservation_on_gpu(gx):
                                  dt=0.05)
     ctx = gx.from_workload(wl, gmres_tol=1e-12)
     W0 = ctx.diagnostics()["total"]
-    worst = 0.0
-    for _ in range(5):
+    worst, Ws = 0.0, []
+    for _ in range(6):
         ctx.step(1)
         W = ctx.diagnostics()["total"]
+        Ws.append(W)
         worst = max(worst, abs(W - W0) / W0)
     assert worst < 1e-6, worst
+    # past a transient over the first two steps (~2e-7, then ~5e-8) the total changes by a few
+    # 1e-9 per step (2e-9 to 7e-9 measured on GB300): guard the per-step figure at 2e-8
+    steps = [abs(b - a) / W0 for a, b in zip(Ws[:-1], Ws[1:])]
+    assert max(steps[1:]) < 2e-8, steps
     ctx.close()
 
 
