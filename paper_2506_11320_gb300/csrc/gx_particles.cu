@@ -77,11 +77,11 @@ struct P2 {
 // different shared-memory banks.
 constexpr int kGroupBuf = 2 * kChunk * 2 + 1;     // float4 per group: 2 buffers of 64 slots + pad
 constexpr int kCodeStride = kChunk + 1;
-constexpr size_t kBarBytes = 512;
+constexpr size_t kBarBytes = ((size_t)kGroups * 2 * sizeof(uint64_t) + 127) / 128 * 128;   // 2 mbarriers per group
 constexpr size_t kBufBytes = (size_t)kGroups * kGroupBuf * sizeof(float4);
 constexpr size_t kCodeBytes = (size_t)kGroups * kCodeStride * sizeof(int);
 constexpr size_t kMapBytes = (size_t)kGroups * kChunk;
-constexpr size_t kScrBytes = (size_t)8 * kScr * sizeof(float);
+constexpr size_t kScrBytes = (size_t)(kThreads / 32) * kScr * sizeof(float);
 // leaver counts per group and direction (8 neighbours)
 constexpr size_t kDirBytes = (size_t)kGroups * 8 * sizeof(int);
 size_t pd_smem_bytes() { return kBarBytes + kBufBytes + kCodeBytes + kMapBytes + kScrBytes + kDirBytes; }
@@ -393,10 +393,10 @@ template <bool PUSH, bool WALL = false>
 __global__ void __launch_bounds__(kThreads, 1) k_pd(P2 p) {
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem);                         // [groups][2]
-    float4 *bufs = reinterpret_cast<float4 *>(smem + kBarBytes);                  // [groups][2][64][2]
-    int *codes = reinterpret_cast<int *>(smem + kBarBytes + kBufBytes);           // [groups][64]
-    unsigned char *maps = smem + kBarBytes + kBufBytes + kCodeBytes;             // [groups][64]
-    float *scr_all = reinterpret_cast<float *>(smem + kBarBytes + kBufBytes + kCodeBytes + kMapBytes);  // [8][kScr]
+    float4 *bufs = reinterpret_cast<float4 *>(smem + kBarBytes);                  // [groups][2][kChunk][2]
+    int *codes = reinterpret_cast<int *>(smem + kBarBytes + kBufBytes);           // [groups][kChunk + 1]
+    unsigned char *maps = smem + kBarBytes + kBufBytes + kCodeBytes;             // [groups][kChunk]
+    float *scr_all = reinterpret_cast<float *>(smem + kBarBytes + kBufBytes + kCodeBytes + kMapBytes);  // [warps][kScr]
     int *dircnt = reinterpret_cast<int *>(smem + kBarBytes + kBufBytes + kCodeBytes + kMapBytes + kScrBytes);
 
     const int tid = threadIdx.x;
