@@ -165,3 +165,36 @@ def test_wall_shock_matches_oracle(gx):
         ci = np.floor(parts[s]["x"] / wl.dx[0]).astype(int) % nx
         assert not np.any(ci >= nx - G)
     assert np.all(E1.reshape(3, ny, nx)[:, :, nx - G:] == 0.0)
+
+
+@pytest.mark.parametrize("make", [lambda: small_shock("parallel"), lambda: workloads.shock_wall(nx=96, ny=2, ppc=16)],
+                         ids=["open", "wall"])
+def test_preconditioners_agree_with_open_boundaries(gx, make):
+    """With the Dirichlet rows of open boundaries (and of the wall) in the
+    operator, plain, block-Jacobi and network-corrected FGMRES (the network at its
+    default initialisation: any z is a valid flexible preconditioner) reach the
+    same E^{n+theta} (all solve to 1e-12).  Plain and block-Jacobi FGMRES keep the
+    boundary rows at E^n bit for bit (the initial guess holds E^n there and the
+    identity rows keep every Krylov and Jacobi vector zero at those nodes); the
+    network correction is nonzero everywhere, so with it the rows hold E^n to the
+    solver's precision."""
+    wl = make()
+    G, nx, ny = wl.notes["bc"]["cells"], wl.n[0], wl.n[1]
+    wall = wl.notes["bc"].get("wall", 0)
+    sols = []
+    for pc in (gx.GX_PRECOND_NONE, gx.GX_PRECOND_JACOBI, gx.GX_PRECOND_NET):
+        ctx = gx.from_workload(wl, precond=pc, gmres_tol=1e-12)
+        st = ctx.field_solve()
+        assert st.converged == 1 and st.relres <= 1e-12
+        sols.append(ctx.get_solution())
+        ctx.close()
+    assert rel(sols[1], sols[0]) < 1e-10 and rel(sols[2], sols[0]) < 1e-10
+    bn = np.r_[0:G, nx - G + (0 if wall else 1):nx]
+    E0 = wl.E0.reshape(3, ny, nx)
+    scale = np.linalg.norm(E0)          # |r|_inf <= |r|_2 <= 1e-12 |b|_2, b = E^n + O(dt)
+    for k, s in enumerate(sols):
+        sb = s.reshape(3, ny, nx)[:, :, bn]
+        if k < 2:
+            assert np.array_equal(sb, E0[:, :, bn])
+        else:
+            assert np.abs(sb - E0[:, :, bn]).max() <= 1e-12 * scale
