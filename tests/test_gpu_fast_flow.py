@@ -120,3 +120,28 @@ def test_tophat_with_E_filter_matches_oracle(gx, npass):
         assert np.ptp(E[1]) > 0.99
     else:
         assert np.ptp(E[1]) < 0.85
+
+
+def test_E_filter_with_plasma_matches_oracle(gx):
+    """The E-field filter with particles: the 32 x 32 drifting plasma with
+    nsmooth_e = 2 (and so no LF term on E), two steps against the oracle (fields
+    within 2e-6, the per-step field tolerance once per step)."""
+    wl = workloads.uniform_drift(n=(32, 32, 1), ppc=32, ns_j=1)
+    cfg = gx.make_config(wl.n, wl.dx, c=wl.c, theta=wl.theta, dt=wl.dt, comoving=wl.comoving, lf_on=1,
+                         lf_beta=wl.lf_beta, ns_j=wl.ns_j, nsmooth_u=wl.nsmooth_u, gmres_tol=1e-12, nsmooth_e=2)
+    ctx = gx.Context(cfg)
+    for sp in wl.species:
+        ctx.species_add(sp["q"], sp["m"], sp["x"], sp["y"], sp["z"], sp["vx"], sp["vy"], sp["vz"], sp["w"])
+    ctx.fields_set(wl.E0, wl.B0)
+    for _ in range(2):
+        assert ctx.step(1).converged == 1
+    E1, B1 = ctx.get_fields()
+    ctx.close()
+    ocfg = O.make_cfg(wl.n, wl.dx, **wl.grid_kwargs())
+    ocfg.gmres_tol, ocfg.nsmooth_e = 1e-12, 2
+    pl = O.Plasma.from_species(wl.species)
+    E, B = wl.E0.copy(), wl.B0.copy()
+    for _ in range(2):
+        assert O.step(ocfg, pl, E, B)["rc"] == 0
+    errs = {"E": rel(E1, E), "B": rel(B1, B)}
+    assert all(v <= 2e-6 for v in errs.values()), errs
