@@ -110,3 +110,40 @@ def test_dense_cells_one_step_matches_oracle(gx):
         return float(np.linalg.norm(a - b) / np.linalg.norm(b))
     assert rel(E1, Eo) <= 1e-6 and rel(B1, Bo) <= 1e-6, (rel(E1, Eo), rel(B1, Bo))
     assert counts == [n[0] * n[1] * ppc] * 2
+
+
+def test_four_species_step_matches_oracle(gx):
+    """The largest species count (4: electrons, protons, alpha particles and a
+    heavy ion): one whole step against the oracle on the same drawn particles
+    (fields within 1e-6), and a fifth species is refused."""
+    n, dx, seed = (16, 12, 1), (0.1, 0.1, 1.0), 9
+    sp4 = [(-1.0, 0.04, 24, 1.4 / (4 * np.pi), (0.2, 0.0, 0.0), 0.08),
+           (1.0, 1.0, 24, 1.0 / (4 * np.pi), (0.2, 0.0, 0.0), 0.015),
+           (2.0, 4.0, 16, 0.15 / (4 * np.pi), (0.2, 0.0, 0.0), 0.01),
+           (1.0, 16.0, 8, 0.1 / (4 * np.pi), (0.1, 0.05, 0.0), 0.005)]
+    cfg = gx.make_config(n, dx, dt=0.02, comoving=1, lf_on=1, seed=seed, gmres_tol=1e-12)
+    ctx = gx.Context(cfg)
+    ocfg = O.make_cfg(n, dx, dt=0.02, comoving=1, lf_on=1, gmres_tol=1e-12)
+    ref = []
+    for s, (q, m, ppc, n0, u, vth) in enumerate(sp4):
+        assert ctx.species_maxwellian(q, m, ppc, n0, u, vth) == s
+        ref.append(O.maxwellian_species(ocfg, seed, s, ppc, n0, u, vth))
+    with pytest.raises(gx.GxError) as e:
+        ctx.species_maxwellian(1.0, 1.0, 4, 0.01, (0, 0, 0), 0.01)
+    assert e.value.status == gx.GX_EINVAL
+    B = np.zeros((3, 1, n[1], n[0]))
+    B[2] = 0.1
+    E = np.zeros_like(B)
+    ctx.fields_set(E, B)
+    assert ctx.step(1).converged == 1
+    E1, B1 = ctx.get_fields()
+    ctx.close()
+    pl = O.Plasma([s[0] for s in sp4], [s[1] for s in sp4],
+                  np.concatenate([np.full(len(r["x"]), s, np.int32) for s, r in enumerate(ref)]),
+                  *[np.concatenate([r[k] for r in ref]) for k in ("x", "y", "z", "vx", "vy", "vz", "w")])
+    Eo, Bo = E.copy(), B.copy()
+    assert O.step(ocfg, pl, Eo, Bo)["rc"] == 0
+
+    def rel(a, b):
+        return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    assert rel(E1, Eo) <= 1e-6 and rel(B1, Bo) <= 1e-6, (rel(E1, Eo), rel(B1, Bo))
