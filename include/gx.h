@@ -104,7 +104,8 @@ typedef struct gx_ctx gx_ctx;
  *                 particles of every boundary cell are replaced by ppc fresh
  *                 particles per species drawn from that side's source (see
  *                 gx_boundary_source).  y stays periodic.  Not with divb_clean;
- *                 2 G < nx.
+ *                 2 G < nx.  Not with nsmooth_e (the filter would move the held
+ *                 boundary E).
  *   bc_wall       with bc_cells: 1 turns the high-x boundary cells into a
  *                 reflecting perfect conductor at rest (the shock-by-reflection
  *                 setup): they hold no particles and get no refill, E is held

@@ -95,6 +95,8 @@ def make_cfg(n, dx, *, c=1.0, theta=0.5, dt=0.02, comoving=0, lf_on=0, lf_speed_
         raise ValueError("open boundaries: no divergence cleaning, and 2 bc_cells < nx")
     if cfg.bc_wall and not cfg.bc_cells:
         raise ValueError("a reflecting wall needs bc_cells > 0")
+    if cfg.bc_cells and cfg.nsmooth_e:
+        raise ValueError("open boundaries without nsmooth_e (the filter would move the held boundary E)")
     return cfg
 
 

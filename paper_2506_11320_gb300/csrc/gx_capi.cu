@@ -229,6 +229,8 @@ int gx_create(const gx_config *cfg, gx_ctx **out) {
         return fail(GX_EINVAL, "bc_cells must be 0 or >= 8 with 2 bc_cells < nx");
     if (cfg->bc_cells > 0 && cfg->divb_clean) return fail(GX_EINVAL, "open boundaries without divb_clean");
     if (cfg->bc_wall && cfg->bc_cells <= 0) return fail(GX_EINVAL, "a reflecting wall needs bc_cells > 0");
+    if (cfg->bc_cells > 0 && cfg->nsmooth_e > 0)   // the filter would move the held boundary E
+        return fail(GX_EINVAL, "open boundaries without nsmooth_e");
     if (cfg->lf_on && cfg->lf_beta < 0) return fail(GX_EINVAL, "lf_beta must be >= 0");
     c->dim = 2;
     c->N = (int64_t)c->n[0] * c->n[1] * c->n[2];

@@ -44,9 +44,11 @@ def small_shock(kind="parallel", **kw):
     return workloads.shock_1d(kind, length=length, ppc=16, **kw)
 
 
-@pytest.mark.parametrize("kind,ny", [("parallel", 1), ("perpendicular", 1), ("parallel", 3)])
-def test_shock_steps_match_oracle(gx, kind, ny):
-    wl = small_shock(kind, ny=ny)
+@pytest.mark.parametrize("kind,ny,extra", [("parallel", 1, {}), ("perpendicular", 1, {}), ("parallel", 3, {}),
+                                           ("parallel", 1, dict(comoving=0, ns_j=0)), ("parallel", 1, dict(lf_on=0))],
+                         ids=["parallel", "perpendicular", "parallel-2d", "standard-current", "no-lf"])
+def test_shock_steps_match_oracle(gx, kind, ny, extra):
+    wl = small_shock(kind, ny=ny, **extra)
     bc = wl.notes["bc"]
     G, nx = bc["cells"], wl.n[0]
     steps = 3
@@ -105,7 +107,8 @@ def test_boundary_api_edge_cases(gx):
     wl = small_shock()
     base = dict(c=wl.c, theta=wl.theta, dt=wl.dt, comoving=1, lf_on=1)
     # fewer than 8 boundary cells, boundaries over half the domain, or with div B cleaning: rejected
-    for kw in (dict(bc_cells=4), dict(bc_cells=wl.n[0] // 2), dict(bc_cells=8, divb_clean=1)):
+    for kw in (dict(bc_cells=4), dict(bc_cells=wl.n[0] // 2), dict(bc_cells=8, divb_clean=1),
+               dict(bc_cells=8, nsmooth_e=1), dict(bc_wall=1)):
         with pytest.raises(gx.GxError) as e:
             gx.Context(gx.make_config(wl.n, wl.dx, **base, **kw))
         assert e.value.status == gx.GX_EINVAL
