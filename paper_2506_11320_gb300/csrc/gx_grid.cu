@@ -15,6 +15,10 @@
 namespace {
 
 constexpr int kB = 256;
+// CTAs per SM the register budget of the heavier one-thread-per-node kernels
+// must allow (64 registers a thread): a 512 x 256 node grid is then one wave
+// of 512 CTAs over 152 SMs instead of 1.7 waves at two CTAs per SM
+constexpr int kNodeCtas = 4;
 
 __device__ __forceinline__ int wr(int i, int n) { return gx_wr(i, n); }
 
@@ -63,7 +67,7 @@ struct Recs {
 // the per-species cell records of the 4 cells around it.  The cell sums of
 // one species are FP32 (the records are FP32 partial sums); species are
 // combined in FP64.
-__global__ void k_assemble_bulk(G2 g, SpecK sk, Recs R, double inv_dV, double *rho, double *rho_m, double *P,
+__global__ void __launch_bounds__(kB, kNodeCtas) k_assemble_bulk(G2 g, SpecK sk, Recs R, double inv_dV, double *rho, double *rho_m, double *P,
                                 double *u) {
     const int64_t N = g.N();
     GRID_LOOP(q, N) {
@@ -176,7 +180,7 @@ __device__ __forceinline__ double widen_f32(float f) {
 // species are FP32 (the records are FP32 partial sums); the current's species
 // are combined in FP64, the mass matrix (all species add with beta_s q_s > 0)
 // in FP32 and stored as FP64.
-__global__ void k_assemble_main(G2 g, SpecK sk, Recs R, double inv_dV, int comoving, const double *__restrict__ u,
+__global__ void __launch_bounds__(kB, kNodeCtas) k_assemble_main(G2 g, SpecK sk, Recs R, double inv_dV, int comoving, const double *__restrict__ u,
                                 const double *__restrict__ uref, double *J, double *M) {
     const int64_t N = g.N();
     GRID_LOOP(q, N) {
@@ -400,7 +404,7 @@ __global__ void k_motional(G2 g, const double *__restrict__ u, const double *__r
 }
 
 // b = E^n + c theta dt [curl_N B^n - (4 pi / c)(J - (1/dV) M E_M)]   (Eq. 35)
-__global__ void k_rhs(G2 g, const double *__restrict__ E, const double *__restrict__ B, const double *__restrict__ J,
+__global__ void __launch_bounds__(kB, kNodeCtas) k_rhs(G2 g, const double *__restrict__ E, const double *__restrict__ B, const double *__restrict__ J,
                       const double *__restrict__ M, const double *__restrict__ EM, double ctd, double jf, double mf,
                       double *b) {
     const int64_t N = g.N();
@@ -514,7 +518,7 @@ __global__ void k_lf_flux(G2 g, const double *__restrict__ B, const double *__re
 // Increment of the limited LF diffusion on B over one step, D = F_{c+1/2} -
 // F_{c-1/2} along every resolved axis (0 in boundary cells), and B~ = B^n +
 // theta D, the part of B^{n+theta} the E solve curls: B^{n+1} receives D.
-__global__ void k_lf_b(G2 g, const double *__restrict__ B, const double *__restrict__ Ff, double theta, double *D,
+__global__ void __launch_bounds__(kB, kNodeCtas) k_lf_b(G2 g, const double *__restrict__ B, const double *__restrict__ Ff, double theta, double *D,
                        double *Bt) {
     const int64_t N = g.N();
     GRID_LOOP(q, N) {
