@@ -360,9 +360,10 @@ int gx_precond_loss_grad(gx_ctx *ctx, int H, int W, const float *in, const float
  * diagnostics hook while the particle arrays fill the device, or a path that
  * must not synchronise).  It allocates nothing: its only scratch, the per-cell
  * output offsets, lives in a fixed device array of gx_noalloc_max_cells()
- * ints (262144, 1 MiB); larger grids get GX_EINVAL.  The first call on a
- * device looks that array up (once per device, with that device current) and
- * should come before any stream capture.  The array is shared by every context
+ * ints (262144, 1 MiB); larger grids get GX_EINVAL.  gx_create looks that
+ * array up (once per device, with the context's device current) and loads the
+ * code of this call then, so the call itself triggers no lazy module load
+ * (which would allocate and could synchronise).  The array is shared by every context
  * on the device, so calls that overlap in time race.  Output pointers are
  * device arrays of gx_species_count() entries (NULL to skip a field; id only
  * with track_ids); the call enqueues two kernels on `stream` and does not

@@ -9,6 +9,7 @@
 // All device work is enqueued on the caller's stream.
 #include <cstdio>
 #include <cstring>
+#include <initializer_list>
 
 #include "gx_internal.cuh"
 
@@ -47,6 +48,33 @@ int copy_out(gx_ctx *c, void *dst, const void *src, size_t bytes, int is_dev, cu
 }
 
 thread_local std::string g_create_err;
+
+// any non-finite value among n entries -> *bad = 1 (input validation of the
+// host or device arrays a caller passes in)
+template <class T>
+__global__ void k_nonfinite(int64_t n, const T *__restrict__ a, int *bad) {
+    bool b = false;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        b |= !isfinite(a[i]);
+    if (__any_sync(0xffffffffu, b) && (threadIdx.x & 31) == 0) atomicExch(bad, 1);
+}
+
+// 1 if any of the arrays (device copies) holds a NaN or an infinity
+template <class T>
+int any_nonfinite(gx_ctx *c, std::initializer_list<std::pair<const T *, int64_t>> arrays, cudaStream_t st, int *out) {
+    int *bad = &c->dflags->invalid;
+    GX_CHECK(c, cudaMemsetAsync(bad, 0, sizeof(int), st));
+    for (auto &a : arrays) {
+        if (!a.first || a.second <= 0) continue;
+        const int64_t blocks = std::min<int64_t>((a.second + 255) / 256, 152 * 8);
+        k_nonfinite<T><<<(unsigned)blocks, 256, 0, st>>>(a.second, a.first, bad);
+        GX_LAUNCHED(c);
+    }
+    GX_CHECK(c, cudaMemcpyAsync(&c->hflags->invalid, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+    GX_CHECK(c, cudaStreamSynchronize(st));
+    *out = c->hflags->invalid;
+    return GX_OK;
+}
 
 // CUDA-event timing on the launching stream.  Start/stop pairs are recorded
 // without synchronising and resolved later (gx_timers, or when many pile up),
@@ -214,6 +242,9 @@ int gx_create(const gx_config *cfg, gx_ctx **out) {
         if (!(cfg->dx[d] > 0)) return fail(GX_EINVAL, "dx[d] must be > 0");
         c->n[d] = cfg->n[d];
     }
+    if ((int64_t)cfg->n[0] * cfg->n[1] > (int64_t)1 << 31 ||
+        (int64_t)cfg->n[0] * cfg->n[1] * cfg->n[2] > (int64_t)1 << 31)
+        return fail(GX_EINVAL, "at most 2^31 cells");
     if (cfg->n[2] != 1) return fail(GX_ENOTIMPL, "this build implements the 2D (x-y) path: n[2] must be 1");
     if (!(cfg->c > 0) || !(cfg->dt > 0)) return fail(GX_EINVAL, "c and dt must be > 0");
     if (!(cfg->theta >= 0.5 && cfg->theta <= 1.0)) return fail(GX_EINVAL, "theta must be in [0.5, 1]");
@@ -231,7 +262,11 @@ int gx_create(const gx_config *cfg, gx_ctx **out) {
     if (cfg->bc_wall && cfg->bc_cells <= 0) return fail(GX_EINVAL, "a reflecting wall needs bc_cells > 0");
     if (cfg->bc_cells > 0 && cfg->nsmooth_e > 0)   // the filter would move the held boundary E
         return fail(GX_EINVAL, "open boundaries without nsmooth_e");
-    if (cfg->lf_on && cfg->lf_beta < 0) return fail(GX_EINVAL, "lf_beta must be >= 0");
+    if (cfg->lf_on && !(cfg->lf_beta >= 0 && cfg->lf_beta < 1e300)) return fail(GX_EINVAL, "lf_beta must be >= 0");
+    if (!(cfg->c < 1e300) || !(cfg->dt < 1e300) || !(cfg->gmres_tol < 1e300) || !(cfg->bin_slack == cfg->bin_slack))
+        return fail(GX_EINVAL, "c, dt, gmres_tol and bin_slack must be finite");
+    for (int d = 0; d < 3; ++d)
+        if (!(cfg->dx[d] < 1e300)) return fail(GX_EINVAL, "dx[d] must be finite");
     c->dim = 2;
     c->N = (int64_t)c->n[0] * c->n[1] * c->n[2];
     c->dV = cfg->dx[0] * cfg->dx[1] * cfg->dx[2];
@@ -279,6 +314,7 @@ int gx_create(const gx_config *cfg, gx_ctx **out) {
         cudaMemset(c->nUref, 0, N * sizeof(float4)) != cudaSuccess ||
         cudaDeviceSynchronize() != cudaSuccess)
         return fail(GX_ECUDA, "initialisation failed");
+    if ((rc = gx_noalloc_prepare(c))) return fail(rc, nullptr);
     *out = c;
     return GX_OK;
 }
@@ -307,7 +343,14 @@ int gx_species_add(gx_ctx *c, double q, double m, int64_t n, const double *x, co
         TRY(copy_in(c, dvz, vz, n * sizeof(float), 0, st)); TRY(copy_in(c, dw, w, n * sizeof(float), 0, st));
         px = dx_; py = dy_; pvx = dvx; pvy = dvy; pvz = dvz; pw = dw;
     }
-    int rc = gx_bin_particles(c, s, n, px, py, nullptr, pvx, pvy, pvz, pw, nullptr, st);
+    int rc = GX_OK, bad = 0;
+    if (n > 0) {
+        // a NaN or an infinity would bin a particle nowhere in particular: refuse the species
+        rc = any_nonfinite<double>(c, {{px, n}, {py, n}}, st, &bad);
+        if (!rc && !bad) rc = any_nonfinite<float>(c, {{pvx, n}, {pvy, n}, {pvz, n}, {pw, n}}, st, &bad);
+        if (!rc && bad) { c->err = "gx_species_add: a position, velocity or weight is not finite"; rc = GX_EINVAL; }
+    }
+    if (!rc) rc = gx_bin_particles(c, s, n, px, py, nullptr, pvx, pvy, pvz, pw, nullptr, st);
     if (dx_) { cudaFree(dx_); cudaFree(dy_); cudaFree(dvx); cudaFree(dvy); cudaFree(dvz); cudaFree(dw); }
     if (rc) return rc;
     TRY(check_flags(c, st));
@@ -343,8 +386,14 @@ int gx_species_maxwellian(gx_ctx *c, double q, double m, int ppc, double n0, con
 int gx_fields_set(gx_ctx *c, const double *E, const double *B, int ptr_is_device) {
     if (!c) return GX_EINVAL;
     const size_t bytes = 3 * c->N * sizeof(double);
-    if (E) TRY(copy_in(c, c->E, E, bytes, ptr_is_device, 0));
-    if (B) TRY(copy_in(c, c->B, B, bytes, ptr_is_device, 0));
+    // validate in the scratch vectors first, so that refused fields leave E^n and B^n as they were
+    if (E) TRY(copy_in(c, c->w, E, bytes, ptr_is_device, 0));
+    if (B) TRY(copy_in(c, c->r, B, bytes, ptr_is_device, 0));
+    int bad = 0;
+    TRY(any_nonfinite<double>(c, {{E ? c->w : nullptr, 3 * c->N}, {B ? c->r : nullptr, 3 * c->N}}, 0, &bad));
+    if (bad) { c->err = "gx_fields_set: E or B holds a value that is not finite"; return GX_EINVAL; }
+    if (E) TRY(copy_in(c, c->E, c->w, bytes, 1, 0));
+    if (B) TRY(copy_in(c, c->B, c->r, bytes, 1, 0));
     if (B && c->phi) GX_CHECK(c, cudaMemsetAsync(c->phi, 0, c->N * sizeof(double), 0));
     GX_CHECK(c, cudaStreamSynchronize(0));
     c->moments_valid = 0;

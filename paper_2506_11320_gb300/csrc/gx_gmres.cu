@@ -217,6 +217,23 @@ __global__ void __launch_bounds__(NET ? kBNet : kB, NET ? 1 : 2) k_fgmres(const 
         bnorm = sqrt(s_scalar[0]);
         if (writer) st->bnorm = bnorm;
     }
+    if (bnorm == 0.0) {
+        // b = 0: the operator is nonsingular, so the solution is exactly 0 (the
+        // starting guess is not kept: its residual could not be judged relative to ||b||)
+        NODE_LOOP(q) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) a.x[c * N + q] = 0.0;
+        }
+        if (writer) {
+            st->beta = 0.0;
+            st->relres = 0.0;
+            st->finished = 1;
+            st->conv = 1;
+            st->done = 1;
+            st->total = total;
+        }
+        return;
+    }
 
     for (;;) {
         if (done) {

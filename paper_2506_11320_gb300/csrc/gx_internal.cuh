@@ -82,6 +82,7 @@ struct DevFlags {                       // written by kernels, read by the host
     int overflow;                       // a bin overflowed (particle dropped)
     int timeout;                        // a bounded device wait gave up
     int maxcount;                       // largest bin count after the last push
+    int invalid;                        // an input array held a NaN or an infinity
 };
 
 // --------------------------------------------------------------- context
@@ -227,6 +228,10 @@ size_t gx_gm_state_bytes();
 size_t gx_gm_partial_count();
 int gx_gm_max_restart();
 double gx_norm_host(gx_ctx *c, const double *x, int64_t n, cudaStream_t st, int *status);
+
+// allocation-free particle gather (gx_noalloc.cu): scratch lookup and module
+// load at context creation
+int gx_noalloc_prepare(gx_ctx *c);
 
 // network (gx_net.cu)
 // device pointers the solver kernel needs to apply the network itself: BF16

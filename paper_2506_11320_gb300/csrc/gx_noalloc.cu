@@ -12,9 +12,12 @@
 // Limits and rules:
 //   * at most kMaxCells cells (the scratch holds one int per cell, 1 MiB);
 //     larger grids get GX_EINVAL;
-//   * the first call on a device looks the scratch address up with
-//     cudaGetSymbolAddress (once per device, with that device current); make
-//     that first call before any stream capture;
+//   * the scratch address is looked up with cudaGetSymbolAddress once per
+//     device, with that device current, and the module holding the scratch and
+//     the two kernels is loaded, when gx_create makes a context on the device
+//     (gx_noalloc_prepare): CUDA loads modules lazily, and loading one
+//     allocates device memory and can synchronise, so this happens at context
+//     creation and never inside gx_get_particles_noalloc;
 //   * the scratch is shared by every context on the device: calls that overlap
 //     in time (two streams, two host threads) race on it;
 //   * every offset the gather reads is written by the scan of the same call,
@@ -127,6 +130,19 @@ int scratch_for_current_device(gx_ctx *c, int **out) {
 
 }  // namespace
 
+// Called by gx_create with the context's device current: look the scratch up
+// and load the module of this file (its kernels) now, so that the gather
+// itself never triggers a lazy module load.
+int gx_noalloc_prepare(gx_ctx *c) {
+    int *p = nullptr;
+    int rc = scratch_for_current_device(c, &p);
+    if (rc) return rc;
+    cudaFuncAttributes fa;
+    GX_CHECK(c, cudaFuncGetAttributes(&fa, k_na_scan));
+    GX_CHECK(c, cudaFuncGetAttributes(&fa, k_na_gather));
+    return GX_OK;
+}
+
 extern "C" int gx_noalloc_max_cells(void) { return kMaxCells; }
 
 extern "C" int gx_get_particles_noalloc(gx_ctx *c, int s, double *x, double *y, double *z, float *vx, float *vy,
@@ -140,7 +156,7 @@ extern "C" int gx_get_particles_noalloc(gx_ctx *c, int s, double *x, double *y, 
         return GX_EINVAL;
     }
     int *offs = nullptr;
-    int rc = scratch_for_current_device(c, &offs);
+    int rc = scratch_for_current_device(c, &offs);   // set up by gx_create: a table lookup here
     if (rc) return rc;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const Species &S = c->sp[s];

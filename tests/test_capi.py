@@ -86,3 +86,44 @@ def test_missing_library_fails_loudly(tmp_path, monkeypatch):
     monkeypatch.setattr(gx, "_lib", None)
     with pytest.raises(RuntimeError):
         gx.lib()
+
+
+def test_corrupt_configs_are_refused_before_any_device_work(built):
+    # gx_create checks its config before it touches a device, so these run on a
+    # host without a GPU: every corrupt field gives GX_EINVAL (a 3D grid beyond
+    # the cell limit likewise), never a crash, and the error text names the field.
+    L = built.lib()
+    nan = float("nan")
+    cases = [
+        ("n", lambda c: c.n.__setitem__(0, 0), "n[d]"),
+        ("dx", lambda c: c.dx.__setitem__(1, -0.1), "dx"),
+        ("dx nan", lambda c: c.dx.__setitem__(0, nan), "dx"),
+        ("dx inf", lambda c: c.dx.__setitem__(0, float("inf")), "dx"),
+        ("c", lambda c: setattr(c, "c", 0.0), "c and dt"),
+        ("dt nan", lambda c: setattr(c, "dt", nan), "c and dt"),
+        ("dt inf", lambda c: setattr(c, "dt", float("inf")), "finite"),
+        ("theta", lambda c: setattr(c, "theta", 0.3), "theta"),
+        ("theta nan", lambda c: setattr(c, "theta", nan), "theta"),
+        ("restart", lambda c: setattr(c, "gmres_restart", 0), "gmres_restart"),
+        ("restart big", lambda c: setattr(c, "gmres_restart", 65), "gmres_restart"),
+        ("maxit", lambda c: setattr(c, "gmres_maxit", 0), "gmres_maxit"),
+        ("tol", lambda c: setattr(c, "gmres_tol", -1e-8), "gmres_tol"),
+        ("tol nan", lambda c: setattr(c, "gmres_tol", nan), "gmres_tol"),
+        ("precond", lambda c: setattr(c, "precond", 7), "precond"),
+        ("smoothing", lambda c: setattr(c, "ns_j", -1), "smoothing"),
+        ("lf_beta nan", lambda c: setattr(c, "lf_beta", nan), "lf_beta"),
+        ("lf_beta", lambda c: setattr(c, "lf_beta", -0.5), "lf_beta"),
+        ("bin_slack nan", lambda c: setattr(c, "bin_slack", nan), "bin_slack"),
+        ("bc_cells", lambda c: setattr(c, "bc_cells", 3), "bc_cells"),
+        ("wall", lambda c: setattr(c, "bc_wall", 1), "wall"),
+        ("cells", lambda c: (c.n.__setitem__(0, 1 << 16), c.n.__setitem__(1, 1 << 16)), "2^31"),
+    ]
+    for name, corrupt, text in cases:
+        cfg = built.make_config((16, 8, 1), (0.1, 0.1, 1.0))
+        corrupt(cfg)
+        h = built._CTX()
+        rc = L.gx_create(built.C.byref(cfg), built.C.byref(h))
+        assert rc == built.GX_EINVAL, name
+        assert not h.value, name
+        assert text in L.gx_last_error(None).decode(), (name, L.gx_last_error(None))
+    assert L.gx_create(None, None) == built.GX_EINVAL

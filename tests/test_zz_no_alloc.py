@@ -1,8 +1,17 @@
 """The allocation-free particle gather against the allocating one, through the
 C ABI.  Both copy the same FP32/FP64 values in the same bin order, so the
-comparison is exact (tolerance 0).  Collected last so that it also runs after
-every other test has used the device; it passes alone in a fresh process too.
+comparison is exact (tolerance 0).  The gather exists for callers that cannot
+allocate, so the tests also check that calls leave the device's free memory
+unchanged, including the first call in a fresh process (its scratch lookup
+and module load happen when the context is created).  Collected last so that
+it also runs after every other test has used the device; it passes alone in a
+fresh process too.
 """
+import os
+import subprocess
+import sys
+import textwrap
+
 import numpy as np
 import pytest
 
@@ -54,8 +63,50 @@ def test_noalloc_gather_matches_allocating_gather(env):
         ctx.step(2)
         for s in range(len(wl.species)):
             check_same(torch, ctx, s)
+        # repeated calls allocate nothing: the device's free memory stays put
+        outs = [device_out(torch, ctx.species_count(s)) for s in range(len(wl.species))]
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
+        for _ in range(3):
+            for s in range(len(wl.species)):
+                ctx.get_particles_noalloc(s, outs[s])
+        torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free0
     finally:
         ctx.close()
+
+
+def test_first_call_in_a_fresh_process_allocates_nothing(env):
+    # A new process: the context's creation looks the scratch up and loads the
+    # gather's code, so even the very first gather leaves free memory unchanged.
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    script = textwrap.dedent("""
+        import sys
+        sys.path.insert(0, %r)
+        import torch
+        import paper_2506_11320_gb300 as g
+        import workloads
+        torch.cuda.init()
+        wl = workloads.uniform_drift(n=(24, 16, 1), ppc=8)
+        ctx = g.from_workload(wl)
+        n = ctx.species_count(0)
+        out = {k: torch.zeros(n, dtype=torch.float64, device="cuda") for k in ("x", "y", "z")}
+        out.update({k: torch.zeros(n, dtype=torch.float32, device="cuda") for k in ("vx", "vy", "vz", "w")})
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
+        ctx.get_particles_noalloc(0, out)
+        torch.cuda.synchronize()
+        free1 = torch.cuda.mem_get_info()[0]
+        ref = ctx.get_particles(0)
+        assert all((out[k].cpu().numpy() == ref[k]).all() for k in out)
+        print("FREE", free0, free1)
+        ctx.close()
+    """) % root
+    r = subprocess.run([sys.executable, "-c", script], capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = [l for l in r.stdout.splitlines() if l.startswith("FREE")][-1]
+    free0, free1 = (int(v) for v in line.split()[1:])
+    assert free0 == free1, (free0, free1)
 
 
 def test_noalloc_gather_rejects_large_grids_and_bad_arguments(env):
