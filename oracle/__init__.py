@@ -124,6 +124,8 @@ _SIGS = {
     "or_grad_C": (None, [_P, _D, _D]),
     "or_mc_limiter": (C.c_double, [C.c_double, C.c_double]),
     "or_lf_kappa_E": (None, [_P, _D, _D, _D]),
+    "or_cell_sample3": (None, [_P, C.c_uint64, C.c_int, C.c_int64, C.c_int, C.c_int, C.c_int, C.c_int, _D,
+                               C.c_double, _D, _D, _D, _D, _D, _D]),
     "or_apply_A": (None, [_P, _D, _D, _D, _D]),
     "or_rhs": (None, [_P, _D, _D, _D, _D, _D, _D, _D]),
     "or_gmres": (C.c_int, [_P, _D, _D, _D, _D, _D, C.POINTER(C.c_int)]),
@@ -399,9 +401,25 @@ def bc_sample(cfg, seed, species, step, i, j, ppc, u, vth):
 
 def maxwellian_species(cfg, seed, species, ppc, n0, u, vth):
     """The particles of a device-side drifting Maxwellian species: for every cell
-    (j, then i) the ppc draws of step 0 (or_bc_sample), weights n0 dV / ppc.
+    (k, then j, then i) the ppc draws of step 0 (or_bc_sample in 2D,
+    or_cell_sample3 with a resolved z axis), weights n0 dV / ppc.
     Returns dict x, y, z, vx, vy, vz, w (float64)."""
-    nx, ny = cfg.n[0], cfg.n[1]
+    nx, ny, nz = cfg.n[0], cfg.n[1], cfg.n[2]
+    if nz > 1:
+        L = lib()
+        uu = _f64(np.asarray(u, float))
+        parts = {k: [] for k in ("x", "y", "z", "vx", "vy", "vz")}
+        for k in range(nz):
+            for j in range(ny):
+                for i in range(nx):
+                    a = [np.zeros(ppc) for _ in range(6)]
+                    L.or_cell_sample3(C.byref(cfg), int(seed), int(species), 0, i, j, k, int(ppc), _d(uu),
+                                      float(vth), *[_d(v) for v in a])
+                    for key, v in zip(("x", "y", "z", "vx", "vy", "vz"), a):
+                        parts[key].append(v)
+        out = {key: np.concatenate(v) for key, v in parts.items()}
+        out["w"] = np.full(out["x"].size, n0 * cfg.dx[0] * cfg.dx[1] * cfg.dx[2] / ppc)
+        return out
     parts = {k: [] for k in ("x", "y", "vx", "vy", "vz")}
     for j in range(ny):
         for i in range(nx):

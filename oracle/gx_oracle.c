@@ -1046,6 +1046,34 @@ void or_bc_sample(const or_cfg *g, uint64_t seed, int species, int64_t step, int
     }
 }
 
+/* The ppc draws of cell (i, j, k) in the draw of `step` on a grid with a
+ * resolved z axis: as or_bc_sample, with the counter's cell word the flat cell
+ * index i + nx (j + ny k) and the z offset from bits 16..39 of word 0 (the
+ * device-side Maxwellian species of a 3D grid draws its particles so). */
+void or_cell_sample3(const or_cfg *g, uint64_t seed, int species, int64_t step, int i, int j, int k, int ppc,
+                     const double u[3], double vth, double *x, double *y, double *z, double *vx, double *vy,
+                     double *vz) {
+    const uint64_t key[2] = {seed, (uint64_t)species};
+    const double s24 = 1.0 / 16777216.0, twopi = 2.0 * OR_PI;
+    const uint64_t cell = (uint64_t)i + (uint64_t)g->n[0] * ((uint64_t)j + (uint64_t)g->n[1] * (uint64_t)k);
+    for (int p = 0; p < ppc; ++p) {
+        const uint64_t ctr[4] = {(uint64_t)step, cell, (uint64_t)p, 0};
+        uint64_t r[4];
+        or_philox4x64(key, ctr, r);
+        const double ox = (double)(r[0] >> 40) * s24, oy = (double)(r[1] >> 40) * s24;
+        const double oz = (double)((r[0] >> 16) & 0xffffffu) * s24;
+        const double u1 = (double)((r[2] >> 40) + 1) * s24, u2 = (double)((r[2] >> 16) & 0xffffffu) * s24;
+        const double u3 = (double)((r[3] >> 40) + 1) * s24, u4 = (double)((r[3] >> 16) & 0xffffffu) * s24;
+        const double ra = sqrt(-2.0 * log(u1)), rb = sqrt(-2.0 * log(u3));
+        x[p] = (i + ox) * g->dx[0];
+        y[p] = g->n[1] > 1 ? (j + oy) * g->dx[1] : 0.0;
+        z[p] = g->n[2] > 1 ? (k + oz) * g->dx[2] : 0.0;
+        vx[p] = u[0] + vth * ra * cos(twopi * u2);
+        vy[p] = u[1] + vth * ra * sin(twopi * u2);
+        vz[p] = u[2] + vth * rb * cos(twopi * u4);
+    }
+}
+
 /* ------------------------------------------------- learned preconditioner net */
 
 /* The convolutional correction network of the learned GMRES preconditioner (an

@@ -303,7 +303,8 @@ int gx_create(const gx_config *cfg, gx_ctx **out) {
         cudaMallocHost(&c->hflags, sizeof(DevFlags)) != cudaSuccess)
         return fail(GX_ENOMEM, "pinned host allocation failed");
     std::memset(c->hflags, 0, sizeof(DevFlags));
-    if ((rc = dalloc(c, &c->rec, (size_t)GX_MAX_SPECIES * N * Rec<2>::SIZE))) return fail(rc, nullptr);
+    c->rec_size = c->dim == 3 ? Rec<3>::SIZE : Rec<2>::SIZE;
+    if ((rc = dalloc(c, &c->rec, (size_t)GX_MAX_SPECIES * N * c->rec_size))) return fail(rc, nullptr);
     double *zero3[] = {c->E, c->B, c->Eth, c->Enew, c->Bnew, c->u, c->J, c->uref64};
     for (auto p : zero3)
         if (cudaMemset(p, 0, 3 * N * sizeof(double)) != cudaSuccess) return fail(GX_ECUDA, "cudaMemset failed");
@@ -325,15 +326,17 @@ int gx_species_add(gx_ctx *c, double q, double m, int64_t n, const double *x, co
     if (!c) return GX_EINVAL;
     if (c->nspecies >= GX_MAX_SPECIES) { c->err = "at most 4 species"; return GX_EINVAL; }
     if (!(m > 0) || q == 0.0 || n < 0 || n > (int64_t)2000000000) { c->err = "need q != 0, m > 0, 0 <= n < 2^31"; return GX_EINVAL; }
-    if (n > 0 && (!x || !y || !vx || !vy || !vz || !w)) { c->err = "null particle array"; return GX_EINVAL; }
-    (void)z;
+    if (n > 0 && (!x || !y || !vx || !vy || !vz || !w || (c->dim == 3 && !z))) {
+        c->err = "null particle array";
+        return GX_EINVAL;
+    }
     cudaStream_t st = 0;
     const int s = c->nspecies;
     c->sp[s].q = q;
     c->sp[s].m = m;
-    double *dx_ = nullptr, *dy_ = nullptr;
+    double *dx_ = nullptr, *dy_ = nullptr, *dz_ = nullptr;
     float *dvx = nullptr, *dvy = nullptr, *dvz = nullptr, *dw = nullptr;
-    const double *px = x, *py = y;
+    const double *px = x, *py = y, *pz = c->dim == 3 ? z : nullptr;
     const float *pvx = vx, *pvy = vy, *pvz = vz, *pw = w;
     if (!ptr_is_device && n > 0) {
         TRY(dalloc(c, &dx_, n)); TRY(dalloc(c, &dy_, n));
@@ -341,17 +344,23 @@ int gx_species_add(gx_ctx *c, double q, double m, int64_t n, const double *x, co
         TRY(copy_in(c, dx_, x, n * sizeof(double), 0, st)); TRY(copy_in(c, dy_, y, n * sizeof(double), 0, st));
         TRY(copy_in(c, dvx, vx, n * sizeof(float), 0, st)); TRY(copy_in(c, dvy, vy, n * sizeof(float), 0, st));
         TRY(copy_in(c, dvz, vz, n * sizeof(float), 0, st)); TRY(copy_in(c, dw, w, n * sizeof(float), 0, st));
+        if (pz) {
+            TRY(dalloc(c, &dz_, n));
+            TRY(copy_in(c, dz_, z, n * sizeof(double), 0, st));
+            pz = dz_;
+        }
         px = dx_; py = dy_; pvx = dvx; pvy = dvy; pvz = dvz; pw = dw;
     }
     int rc = GX_OK, bad = 0;
     if (n > 0) {
         // a NaN or an infinity would bin a particle nowhere in particular: refuse the species
-        rc = any_nonfinite<double>(c, {{px, n}, {py, n}}, st, &bad);
+        rc = any_nonfinite<double>(c, {{px, n}, {py, n}, {pz, pz ? n : 0}}, st, &bad);
         if (!rc && !bad) rc = any_nonfinite<float>(c, {{pvx, n}, {pvy, n}, {pvz, n}, {pw, n}}, st, &bad);
         if (!rc && bad) { c->err = "gx_species_add: a position, velocity or weight is not finite"; rc = GX_EINVAL; }
     }
-    if (!rc) rc = gx_bin_particles(c, s, n, px, py, nullptr, pvx, pvy, pvz, pw, nullptr, st);
+    if (!rc) rc = gx_bin_particles(c, s, n, px, py, pz, pvx, pvy, pvz, pw, nullptr, st);
     if (dx_) { cudaFree(dx_); cudaFree(dy_); cudaFree(dvx); cudaFree(dvy); cudaFree(dvz); cudaFree(dw); }
+    if (dz_) cudaFree(dz_);
     if (rc) return rc;
     TRY(check_flags(c, st));
     c->nspecies++;

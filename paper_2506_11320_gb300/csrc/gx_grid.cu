@@ -606,7 +606,8 @@ __global__ void k_diag_grid(G2 g, const double *__restrict__ E, const double *__
 // partial sums into FP64 accumulators, which take the species mass at the end
 // (FP64 on this part runs at 1/64 of the FP32 rate, so FP64 per particle
 // would make this pass ten times slower than its memory traffic).
-__global__ void k_diag_particles(int64_t ncell, int cap, const int *cnt, const float4 *P, double mass, double *acc) {
+__global__ void k_diag_particles(int64_t ncell, int cap, int nf, int dim, const int *cnt, const float *P, double mass,
+                                 double *acc) {
     double ke = 0, px = 0, py = 0, pz = 0;
     double np = 0;
     float fk = 0.f, fx = 0.f, fy = 0.f, fz = 0.f;
@@ -615,11 +616,12 @@ __global__ void k_diag_particles(int64_t ncell, int cap, const int *cnt, const f
         const int word = cnt[c];
         const int m = min(bin_count(word), cap);
         if (threadIdx.x == 0) np += m;
+        const float *b = P + (size_t)c * cap * nf;
         for (int i = threadIdx.x; i < m; i += blockDim.x) {
-            const size_t s = (size_t)c * cap + bin_slot(word, i, cap);
-            const float4 s0 = P[2 * s], s1 = P[2 * s + 1];
-            const float w = s1.y, wa = w * s0.z, wb = w * s0.w, wd = w * s1.x;
-            fk = fmaf(wa, s0.z, fmaf(wb, s0.w, fmaf(wd, s1.x, fk)));
+            const float *q = b + bin_slot(word, i, cap);
+            const float vx = q[(size_t)dim * cap], vy = q[(size_t)(dim + 1) * cap], vz = q[(size_t)(dim + 2) * cap];
+            const float w = q[(size_t)(dim + 3) * cap], wa = w * vx, wb = w * vy, wd = w * vz;
+            fk = fmaf(wa, vx, fmaf(wb, vy, fmaf(wd, vz, fk)));
             fx += wa; fy += wb; fz += wd;
         }
         if (++since == 16) {
@@ -827,7 +829,7 @@ int gx_diag_run(gx_ctx *c, gx_diag *out, cudaStream_t st) {
     for (int s = 0; s < c->nspecies; ++s) {
         const Species &S = c->sp[s];
         k_diag_particles<<<(unsigned)std::min<int64_t>(c->N, 152 * 8), 128, 0, st>>>(
-            c->N, S.cap, S.cnt[c->cur], S.p[c->cur], S.m, acc + 5);
+            c->N, S.cap, S.nf, c->dim, S.cnt[c->cur], S.p[c->cur], S.m, acc + 5);
         GX_LAUNCHED(c);
     }
     double h[16];

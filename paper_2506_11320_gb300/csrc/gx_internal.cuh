@@ -4,10 +4,11 @@
 //   * fields: FP64, component-major [3][N] with N = nx ny nz; E at nodes, B at
 //     cell centres (collocated staggered mesh, Sec. 1.1 of the paper);
 //   * particles: per species, cell bins of fixed capacity `cap` (a multiple of
-//     64) of 32-byte slots (ox, oy, vx, vy | vz, w, id, 0) in FP32, ox and oy
-//     the cell-local offsets in [0,1).  A bin holds a bottom and a top segment
-//     (see bin_front / bin_back).  Two copies: the push reads one and writes
-//     the other, then they swap;
+//     32); each bin is a small structure of arrays of FP32 fields (o_0 ..
+//     o_{d-1}, v_x, v_y, v_z, w[, id]), o the cell-local offsets in [0,1):
+//     field f of slot s of cell c at p[(c cap) nf + f cap + s].  A bin holds a
+//     bottom and a top segment (see bin_front / bin_back).  Two copies: the
+//     push reads one and writes the other, then they swap;
 //   * deposit records: per species and cell, FP32 partial sums over the cell's
 //     particles (see Rec below), [species][112][N], written by the particle
 //     kernels and folded into the FP64 node moments by the grid kernels;
@@ -48,8 +49,8 @@ template <> struct Rec<3> {
 };
 
 // ------------------------------------------------------------- particles
-// One 32-byte slot per particle: float4 (ox, oy, vx, vy) then float4
-// (vz, w, id bits, 0); ox, oy are the cell-local offsets in [0, 1).
+// Per-bin structure of arrays: fields (o_0 .. o_{d-1}, v_x, v_y, v_z, w[, id
+// bits]) of 4 bytes, nf = d + 4 (+1 with track_ids) of them per slot.
 
 // A cell's bin holds two segments: particles that stayed in the cell during
 // the last push fill slots [0, front) from the bottom, particles that arrived
@@ -68,7 +69,8 @@ __host__ __device__ inline int bin_slot(int w, int i, int cap) {
 struct Species {
     double q = 0, m = 0;
     int cap = 0;                        // bin capacity (particles per cell)
-    float4 *p[2] = {};                  // [copy]: 2 float4 per slot, cap slots per cell
+    int nf = 0;                         // FP32 fields stored per particle
+    float *p[2] = {};                   // [copy]: [cell][field][cap]
     int *cnt[2] = {};                   // particles per cell, per copy
 };
 

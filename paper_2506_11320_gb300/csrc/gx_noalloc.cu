@@ -79,10 +79,12 @@ __global__ void __launch_bounds__(kScanThreads) k_na_scan(const int *__restrict_
 }
 
 // one CTA per cell: copy the cell's particles (front segment, then back) to
-// positions offs[c] .. offs[c] + count - 1; slots are (ox, oy, vx, vy | vz, w, id, 0)
-__global__ void k_na_gather(int64_t ncell, int cap, const int *__restrict__ cnt, const int *__restrict__ offs,
-                            const float4 *__restrict__ P, int nx, int ny, double dx, double dy, double *x, double *y,
-                            double *z, float *vx, float *vy, float *vz, float *w, int32_t *id) {
+// positions offs[c] .. offs[c] + count - 1; a bin holds nf fields of cap slots
+// each, (o_0 .. o_{dim-1}, v_x, v_y, v_z, w, id)
+__global__ void k_na_gather(int64_t ncell, int cap, int nf, int dim, const int *__restrict__ cnt,
+                            const int *__restrict__ offs, const float *__restrict__ P, int nx, int ny, double dx,
+                            double dy, double dz, double *x, double *y, double *z, float *vx, float *vy, float *vz,
+                            float *w, int32_t *id) {
     const int64_t c = blockIdx.x;
     if (c >= ncell) return;
     const int word = cnt[c];
@@ -90,19 +92,19 @@ __global__ void k_na_gather(int64_t ncell, int cap, const int *__restrict__ cnt,
     b = min(b, cap);
     f = min(f, cap - b);
     const int m = f + b;
-    const int cx = (int)(c % nx), cy = (int)(c / nx);
+    const int cx = (int)(c % nx), cy = (int)((c / nx) % ny), cz = (int)(c / ((int64_t)nx * ny));
+    const float *bin = P + (size_t)c * cap * nf;
     for (int i = threadIdx.x; i < m; i += blockDim.x) {
-        const size_t s = (size_t)c * cap + (i < f ? i : cap - b + (i - f));
-        const float4 s0 = P[2 * s], s1 = P[2 * s + 1];
+        const float *q = bin + (i < f ? i : cap - b + (i - f));
         const int o = offs[c] + i;
-        if (x) x[o] = (cx + (double)s0.x) * dx;
-        if (y) y[o] = ny > 1 ? (cy + (double)s0.y) * dy : 0.0;
-        if (z) z[o] = 0.0;
-        if (vx) vx[o] = s0.z;
-        if (vy) vy[o] = s0.w;
-        if (vz) vz[o] = s1.x;
-        if (w) w[o] = s1.y;
-        if (id) id[o] = __float_as_int(s1.z);
+        if (x) x[o] = (cx + (double)q[0]) * dx;
+        if (y) y[o] = ny > 1 ? (cy + (double)q[(size_t)cap]) * dy : 0.0;
+        if (z) z[o] = dim == 3 ? (cz + (double)q[(size_t)2 * cap]) * dz : 0.0;
+        if (vx) vx[o] = q[(size_t)dim * cap];
+        if (vy) vy[o] = q[(size_t)(dim + 1) * cap];
+        if (vz) vz[o] = q[(size_t)(dim + 2) * cap];
+        if (w) w[o] = q[(size_t)(dim + 3) * cap];
+        if (id) id[o] = __float_as_int(q[(size_t)(dim + 4) * cap]);
     }
 }
 
@@ -163,8 +165,9 @@ extern "C" int gx_get_particles_noalloc(gx_ctx *c, int s, double *x, double *y, 
     const int *cnt = S.cnt[c->cur];
     k_na_scan<<<1, kScanThreads, 0, st>>>(cnt, (int)c->N, S.cap, offs);
     GX_LAUNCHED(c);
-    k_na_gather<<<(unsigned)c->N, 128, 0, st>>>(c->N, S.cap, cnt, offs, S.p[c->cur], c->n[0], c->n[1],
-                                                c->cfg.dx[0], c->cfg.dx[1], x, y, z, vx, vy, vz, w, id);
+    k_na_gather<<<(unsigned)c->N, 128, 0, st>>>(c->N, S.cap, S.nf, c->dim, cnt, offs, S.p[c->cur], c->n[0],
+                                                c->n[1], c->cfg.dx[0], c->cfg.dx[1], c->cfg.dx[2], x, y, z, vx, vy,
+                                                vz, w, id);
     GX_LAUNCHED(c);
     return GX_OK;
 }

@@ -1,7 +1,7 @@
-// gx_particles.cu -- particle kernels of the GL-ECSIM hot path (2D).
+// gx_particles.cu -- particle kernels of the GL-ECSIM hot path (2D and 3D).
 //
-// k_pd<true> (the fused push) does, for every particle of a species, in one
-// pass over the cell bins:
+// k_pd<DIM, true> (the fused push) does, for every particle of a species, in
+// one pass over the cell bins:
 //   1. the theta-implicit mover of Sec. 2.1 (Eq. 29-30 and the ECSIM update):
 //      vbar = alpha (v^n + beta_s E^{n+theta}), v^{n+1} = 2 vbar - v^n,
 //      x^{n+3/2} = x^{n+1/2} + dt v^{n+1}, alpha from B^n (Eq. 30);
@@ -11,29 +11,36 @@
 //   3. re-binning into the other copy of the particle arrays: a cell's stayers
 //      fill its new bin from the bottom in order, particles that leave take
 //      slots at the top of their new cell's bin (see bin_front / bin_back).
-// k_pd<false> deposits without moving: the whole state (the deposit before
-// the first step), or, right after the push, only the particles that arrived
-// in each cell (the back segments of the new bins), added to the records the
-// push wrote with fire-and-forget atomic adds (one add per record entry, so
-// the sum is the same as adding the two records).
+// k_pd<DIM, false> deposits without moving: the whole state (the deposit
+// before the first step), or, right after the push, only the particles that
+// arrived in each cell (the back segments of the new bins), added to the
+// records the push wrote with fire-and-forget atomic adds.
 //
-// Particle layout: one 32-byte slot per particle, two float4
-// (ox, oy, vx, vy) and (vz, w, id bits, 0); cell c's bin is slots
-// [c cap, (c+1) cap).  A staged chunk of a bin is one contiguous bulk copy, a
-// particle that leaves its cell is one 32-byte sector written, and the
-// stayers of a chunk go out as contiguous runs of whole lines.
+// Particle layout: per species and copy, cell bins of `cap` slots, each bin a
+// small structure of arrays: field f of slot s of cell c at
+// p[(c cap + s) ... ] = p[c cap nf + f cap + s], fields (o_0 .. o_{d-1}, v_x,
+// v_y, v_z, w[, id]) with o the cell-local offsets in [0, 1).  A warp reads 32
+// consecutive slots of a field as one coalesced 128-byte line.
 //
-// Work decomposition (GB300-first): a persistent grid, one CTA of 8 warps per
-// SM; each warp is split into 4 groups of 8 lanes and a group owns one cell at
-// a time (32 consecutive cells per CTA batch).  A cell's bin is streamed into
-// shared memory in 64-particle chunks by the bulk-copy (TMA) engine, double
-// buffered per group and signalled through mbarriers (bounded waits), so the
-// next chunk's loads overlap the current chunk's arithmetic.  The mover and
-// the stayer deposit run with no warp collectives; each lane accumulates its
-// particles' 109 partial sums in registers and at the end of the cell the 8
-// lanes are reduced through shared memory and the record is stored with plain
-// stores.  The FP32 particle arithmetic stays on the CUDA cores: it is a
-// scatter, not a dense contraction.
+// Work decomposition (GB300-first): one warp per cell, cells strided over all
+// warps of a persistent grid.  The 32 lanes move 32 particles of the cell at a
+// time.  The deposit is output-stationary with register blocking: every lane
+// that deposits writes its particle's factors into the warp's shared table,
+// the 2^d x 2^d corner-pair weights w X_jx Y_jy (Z_jz) (9 pair classes in 2D,
+// 27 in 3D) and 16 columns (the nine entries of alpha, 1, v and
+// alpha (v - u_ref)).  The warp's lanes form particle groups; within a group
+// each lane owns a block of 9 pair classes x 4 columns (36 sums in registers,
+// kept over all chunks of the cell) and walks the group's particles, so each
+// particle's factors are read from shared memory by few lanes (2D: 8 groups of
+// 4 lanes; 3D: 2 groups of 12).  At the end of the cell the groups' sums are
+// added, and the cell's record follows from the 16 sums per pair class: the
+// mass-matrix sums are the alpha columns, and the charge, momentum and current
+// weights of corner a are the sums of the 2^d pair classes whose product makes
+// up W_a (for linear weights (1-o) = X_0 + X_1 and o = X_1 + X_2 per axis).  A
+// lane holds 36 sums instead of the record's 109 (2D) or 299 (3D), so many
+// warps fit an SM, and the same kernel serves both dimensions.  The FP32
+// particle arithmetic stays on the CUDA cores: it is a scatter, not a dense
+// contraction.
 #include <cub/cub.cuh>
 
 #include "gx_internal.cuh"
@@ -41,91 +48,57 @@
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kGroup = 8;                         // lanes per cell group
-constexpr int kGroups = kThreads / kGroup;        // 32 cells per CTA batch
-constexpr int kChunk = 64;                        // particles per staged chunk
-constexpr int kPerLane = kChunk / kGroup;         // 8
-constexpr int kScr = 56 * 33;                     // reduction scratch floats per warp
+constexpr int kWarpsPerCta = kThreads / 32;
+constexpr int kCols = 16;                         // alpha[9], 1, v[3], alpha (v - u_ref) [3]
+constexpr int kBlk = 36;                          // sums per lane: 9 pair classes x 4 columns
 constexpr unsigned kFull = 0xffffffffu;
-constexpr long long kSpinLimit = 1LL << 24;       // bounded mbarrier wait
 
-struct P2 {
-    int nx, ny;
+// NC corners; ROWS pair classes in groups of 9; factor table of TSTR floats
+// per particle (group g's 9 weights at 12 g, the 16 columns at COLOFF); LK
+// lanes per particle group (RG x 4 column quads), KG groups
+template <int DIM> struct Geo;
+template <> struct Geo<2> {
+    static constexpr int NC = 4, ROWS = 9, TSTR = 28, COLOFF = 12, LK = 4, KG = 8, CENTER = 4, CTAS = 3;
+};
+template <> struct Geo<3> {
+    static constexpr int NC = 8, ROWS = 27, TSTR = 52, COLOFF = 36, LK = 12, KG = 2, CENTER = 13, CTAS = 2;
+};
+// shared floats per warp: corner values [4][NC] float4, then the factor table
+// [32][TSTR], which at the end of a cell holds the lanes' sums [lane][36]
+template <int DIM>
+__host__ __device__ constexpr int warp_floats() {
+    return 16 * Geo<DIM>::NC + (32 * Geo<DIM>::TSTR > 32 * kBlk ? 32 * Geo<DIM>::TSTR : 32 * kBlk);
+}
+template <int DIM>
+constexpr size_t pd_smem_bytes() {
+    return (size_t)kWarpsPerCta * warp_floats<DIM>() * sizeof(float);
+}
+
+// field indices of a slot
+template <int DIM> struct PF {
+    static constexpr int V = DIM, W = DIM + 3, ID = DIM + 4;
+};
+
+struct PD {
+    int n[3];
     int64_t N;
-    int cap;
-    int nbatch;
-    float dtdx, dtdy;
+    int cap, nf;                 // bin capacity, fields stored per slot
+    float dtd[3];                // dt / dx_d
     float beta;                  // q dt / (2 m)
     float bc;                    // beta / c
-    const float4 *in;            // current copy: 2 float4 per slot
+    const float *in;             // current copy
     const int *cnt_in;
-    float4 *out;                 // other copy
+    float *out;                  // other copy
     int *cnt_out;
     const float4 *mE, *mB;       // mover: E^{n+theta}, B^n (node averaged)
     const float4 *dB, *dU;       // deposit: B for alpha, reference velocity u_ref
-    float *rec;                  // [112][N] for this species
+    float *rec;                  // [SIZE][N] for this species
     DevFlags *flags;
     int arrivals;                // deposit only the back segments (the particles that arrived)
     int wall_ci;                 // x index of the last cell before a reflecting wall, or -1
 };
 
-// dynamic shared memory: mbarriers, staging [group][buffer][slot][2] float4,
-// destination codes [group][slot], compaction maps [group][slot] (the slot of
-// the t-th stayer), reduction scratch [warp][kScr]
-// The per-group strides are padded (16 bytes, 4 bytes) so that the 4 groups of
-// a warp, which touch the same slot positions of their own buffers, land on
-// different shared-memory banks.
-constexpr int kGroupBuf = 2 * kChunk * 2 + 1;     // float4 per group: 2 buffers of 64 slots + pad
-constexpr int kCodeStride = kChunk + 1;
-constexpr size_t kBarBytes = ((size_t)kGroups * 2 * sizeof(uint64_t) + 127) / 128 * 128;   // 2 mbarriers per group
-constexpr size_t kBufBytes = (size_t)kGroups * kGroupBuf * sizeof(float4);
-constexpr size_t kCodeBytes = (size_t)kGroups * kCodeStride * sizeof(int);
-constexpr size_t kMapBytes = (size_t)kGroups * kChunk;
-constexpr size_t kScrBytes = (size_t)(kThreads / 32) * kScr * sizeof(float);
-// leaver counts per group and direction (8 neighbours)
-constexpr size_t kDirBytes = (size_t)kGroups * 8 * sizeof(int);
-size_t pd_smem_bytes() { return kBarBytes + kBufBytes + kCodeBytes + kMapBytes + kScrBytes + kDirBytes; }
-
-// ------------------------------------------------------------ PTX helpers
-__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-// 1D bulk copy global -> shared (TMA engine), completion counted on an mbarrier
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_u32(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
-                 : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t phase) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(phase)
-        : "memory");
-    return ok != 0;
-}
-// wait with an iteration limit; false if it gave up
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t phase) {
-    for (long long it = 0; it < kSpinLimit; ++it)
-        if (mbar_try_wait(bar, phase)) return true;
-    return false;
-}
-
-// one 32-byte particle slot written with a single 256-bit store (dst 32-byte aligned)
-__device__ __forceinline__ void st_slot(float4 *dst, float4 a, float4 b) {
-    asm volatile("st.global.v8.f32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(dst), "f"(a.x), "f"(a.y), "f"(a.z),
-                 "f"(a.w), "f"(b.x), "f"(b.y), "f"(b.z), "f"(b.w)
-                 : "memory");
-}
-
-// ------------------------------------------------------------ deposit math
+// ------------------------------------------------------------ helpers
 // alpha (Eq. 30) with b = beta B / c, row-major: alpha a = (a + a x b + (a.b) b)/(1 + b.b)
 __device__ __forceinline__ void alpha_tensor(float bx, float by, float bz, float al[9]) {
     const float inv = __frcp_rn(1.0f + bx * bx + by * by + bz * bz);
@@ -134,129 +107,8 @@ __device__ __forceinline__ void alpha_tensor(float bx, float by, float bz, float
     al[6] = (by + bz * bx) * inv;   al[7] = (bz * by - bx) * inv; al[8] = (1.0f + bz * bz) * inv;
 }
 
-// The 109 partial sums of one lane, held as 55 register pairs so that the
-// deposit can use the paired FP32 FMA (two rounded FMAs per instruction,
-// bit-identical to two fmaf):
-//   p[0..1]    RHO corner pairs (a0,a1), (a2,a3)
-//   p[2..7]    MV  [component][corner pair]
-//   p[8..13]   J   [component][corner pair]
-//   p[14..49]  M   [pair class j][alpha entries (0,1) (2,3) (4,5) (6,7)]
-//   p[50..54]  M   alpha entry 8 for pair classes (0,1) (2,3) (4,5) (6,7) (8,-)
-struct RegAcc {
-    float2 p[55];
-    __device__ __forceinline__ void zero() {
-#pragma unroll
-        for (int k = 0; k < 55; ++k) p[k] = make_float2(0.f, 0.f);
-    }
-    // record entry k (Rec<2> layout); k is a compile-time constant after unrolling
-    __device__ __forceinline__ float get(int k) const {
-        int idx, comp;
-        if (k < Rec<2>::MV) { idx = k >> 1; comp = k & 1; }
-        else if (k < Rec<2>::J) { const int t = k - Rec<2>::MV, a = t / 3, c = t % 3; idx = 2 + 2 * c + (a >> 1); comp = a & 1; }
-        else if (k < Rec<2>::M) { const int t = k - Rec<2>::J, a = t / 3, c = t % 3; idx = 8 + 2 * c + (a >> 1); comp = a & 1; }
-        else if (k < Rec<2>::USED) {
-            const int t = k - Rec<2>::M, j = t / 9, e = t % 9;
-            if (e < 8) { idx = 14 + 4 * j + (e >> 1); comp = e & 1; }
-            else { idx = 50 + (j >> 1); comp = j & 1; }
-        } else {
-            return 0.f;
-        }
-        return comp ? p[idx].y : p[idx].x;
-    }
-};
-
-__device__ __forceinline__ float2 dup2(float v) { return make_float2(v, v); }
-
-// Deposit of one particle at cell-local offsets (x, y) with the corner values
-// of B (for alpha) and u_ref: the partial sums of the record layout Rec<2>.
-__device__ __forceinline__ void deposit_one(RegAcc &acc, float x, float y, float vx, float vy, float vz, float w,
-                                            const float4 cB[4], const float4 cU[4], float bc) {
-    const float wx0 = 1.0f - x, wx1 = x, wy0 = 1.0f - y, wy1 = y;
-    const float W[4] = {wx0 * wy0, wx1 * wy0, wx0 * wy1, wx1 * wy1};
-    float bx = 0.f, by = 0.f, bz = 0.f, ux = 0.f, uy = 0.f, uz = 0.f;
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-        bx = fmaf(W[a], cB[a].x, bx); by = fmaf(W[a], cB[a].y, by); bz = fmaf(W[a], cB[a].z, bz);
-        ux = fmaf(W[a], cU[a].x, ux); uy = fmaf(W[a], cU[a].y, uy); uz = fmaf(W[a], cU[a].z, uz);
-    }
-    float al[9];
-    alpha_tensor(bc * bx, bc * by, bc * bz, al);
-    const float dx_ = vx - ux, dy_ = vy - uy, dz_ = vz - uz;
-    const float jx = w * (al[0] * dx_ + al[1] * dy_ + al[2] * dz_);
-    const float jy = w * (al[3] * dx_ + al[4] * dy_ + al[5] * dz_);
-    const float jz = w * (al[6] * dx_ + al[7] * dy_ + al[8] * dz_);
-    const float wv[3] = {w * vx, w * vy, w * vz};
-    const float jv[3] = {jx, jy, jz};
-    const float2 W01 = make_float2(W[0], W[1]), W23 = make_float2(W[2], W[3]);
-    acc.p[0] = __ffma2_rn(dup2(w), W01, acc.p[0]);
-    acc.p[1] = __ffma2_rn(dup2(w), W23, acc.p[1]);
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        acc.p[2 + 2 * c] = __ffma2_rn(dup2(wv[c]), W01, acc.p[2 + 2 * c]);
-        acc.p[3 + 2 * c] = __ffma2_rn(dup2(wv[c]), W23, acc.p[3 + 2 * c]);
-        acc.p[8 + 2 * c] = __ffma2_rn(dup2(jv[c]), W01, acc.p[8 + 2 * c]);
-        acc.p[9 + 2 * c] = __ffma2_rn(dup2(jv[c]), W23, acc.p[9 + 2 * c]);
-    }
-    const float X[3] = {w * wx0 * wx0, w * wx0 * wx1, w * wx1 * wx1};
-    const float Y[3] = {wy0 * wy0, wy0 * wy1, wy1 * wy1};
-    float pw[9];
-#pragma unroll
-    for (int j = 0; j < 9; ++j) pw[j] = X[j % 3] * Y[j / 3];
-    const float2 al2[4] = {make_float2(al[0], al[1]), make_float2(al[2], al[3]), make_float2(al[4], al[5]),
-                           make_float2(al[6], al[7])};
-#pragma unroll
-    for (int j = 0; j < 9; ++j)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) acc.p[14 + 4 * j + q] = __ffma2_rn(dup2(pw[j]), al2[q], acc.p[14 + 4 * j + q]);
-#pragma unroll
-    for (int j = 0; j < 8; j += 2)
-        acc.p[50 + j / 2] = __ffma2_rn(make_float2(pw[j], pw[j + 1]), dup2(al[8]), acc.p[50 + j / 2]);
-    acc.p[54].x = fmaf(pw[8], al[8], acc.p[54].x);
-}
-
-// Sum the 8 lanes of every group of the warp through the warp's shared scratch
-// (stride 33: conflict-free writes and column sums) and store the record of
-// the group's cell (or add it, without reading it back, when `add`).
-__device__ __forceinline__ void group_reduce_store(const RegAcc &acc, float *scr, int lane, int lig, int gshift,
-                                                   float *dst, int64_t stride, bool active, bool add) {
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-#pragma unroll
-        for (int k = 0; k < 56; ++k) scr[k * 33 + lane] = acc.get(h * 56 + k);
-        __syncwarp();
-        if (active) {
-#pragma unroll
-            for (int t = 0; t < 7; ++t) {
-                const int k = lig * 7 + t;
-                const float *c = scr + k * 33 + gshift;
-                const float s = ((c[0] + c[1]) + (c[2] + c[3])) + ((c[4] + c[5]) + (c[6] + c[7]));
-                if (add) atomicAdd(dst + (size_t)(h * 56 + k) * stride, s);
-                else dst[(size_t)(h * 56 + k) * stride] = s;
-            }
-        }
-        __syncwarp();
-    }
-}
-
-__device__ __forceinline__ void corner_nodes(int ci, int cj, int nx, int ny, int64_t nd[4]) {
-    const int ip = ci + 1 == nx ? 0 : ci + 1, jp = cj + 1 == ny ? 0 : cj + 1;
-    nd[0] = ci + (int64_t)nx * cj;
-    nd[1] = ip + (int64_t)nx * cj;
-    nd[2] = ci + (int64_t)nx * jp;
-    nd[3] = ip + (int64_t)nx * jp;
-}
-
-// bottom slot of chunk ch of a bin whose front holds nf and back nb particles:
-// front chunks are [64 ch, 64 ch + 64), back chunks count down from the top
-__device__ __forceinline__ int chunk_base(int ch, int nf, int cap) {
-    const int nchf = (nf + kChunk - 1) / kChunk;
-    return ch < nchf ? ch * kChunk : cap - (ch - nchf + 1) * kChunk;
-}
-__device__ __forceinline__ int bin_chunks(int word) {
-    return (bin_front(word) + kChunk - 1) / kChunk + (bin_back(word) + kChunk - 1) / kChunk;
-}
 // clamp a (possibly overflowed) count word to the capacity
-__device__ __forceinline__ int clamp_word(int w, int cap) {
+__host__ __device__ __forceinline__ int clamp_word(int w, int cap) {
     int f = bin_front(w), b = bin_back(w);
     b = min(b, cap);
     f = min(f, cap - b);
@@ -266,6 +118,296 @@ __device__ __forceinline__ int clamp_word(int w, int cap) {
 __device__ __forceinline__ int seg_word(int w, int cap, int arrivals_only) {
     const int c = clamp_word(w, cap);
     return arrivals_only ? (int)((unsigned)c & 0xffff0000u) : c;
+}
+
+// linear weights of the 2^DIM corners at cell-local offsets o (corner a: bit d
+// of a selects o_d, else 1 - o_d)
+template <int DIM>
+__device__ __forceinline__ void corner_weights(const float o[3], float W[Geo<DIM>::NC]) {
+    const float x0 = 1.f - o[0], y0 = 1.f - o[1];
+    W[0] = x0 * y0; W[1] = o[0] * y0; W[2] = x0 * o[1]; W[3] = o[0] * o[1];
+    if constexpr (DIM == 3) {
+        const float z0 = 1.f - o[2];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) { W[a + 4] = W[a] * o[2]; W[a] *= z0; }
+    }
+}
+
+// sum of a corner field at the particle: returns (x, y, z) of sum_a W_a f_a
+template <int DIM>
+__device__ __forceinline__ void gather(const float4 *f, const float W[Geo<DIM>::NC], float out[3]) {
+    out[0] = out[1] = out[2] = 0.f;
+#pragma unroll
+    for (int a = 0; a < Geo<DIM>::NC; ++a) {
+        const float4 v = f[a];
+        out[0] = fmaf(W[a], v.x, out[0]);
+        out[1] = fmaf(W[a], v.y, out[1]);
+        out[2] = fmaf(W[a], v.z, out[2]);
+    }
+}
+
+// record entry k of a cell from the lanes' block sums S[lane][36]: pair class
+// j, column c sits in block (rg = j / 9, cg = c / 4) of every particle group
+template <int DIM>
+__device__ __forceinline__ float record_entry(const float *S, int k) {
+    using R = Rec<DIM>;
+    using G = Geo<DIM>;
+    auto ssum = [&](int j, int col) {
+        const int lk = (j / 9) * 4 + col / 4, idx = (j % 9) * 4 + col % 4;
+        float s = 0.f;
+#pragma unroll
+        for (int g = 0; g < G::KG; ++g) s += S[(g * G::LK + lk) * kBlk + idx];
+        return s;
+    };
+    if (k >= R::USED) return 0.f;
+    if (k >= R::M) {
+        const int t = k - R::M;
+        return ssum(t / 9, t % 9);
+    }
+    int a, col;
+    if (k < R::MV) { a = k; col = 9; }
+    else if (k < R::J) { const int t = k - R::MV; a = t / 3; col = 10 + t % 3; }
+    else { const int t = k - R::J; a = t / 3; col = 13 + t % 3; }
+    const int ax = a & 1, ay = (a >> 1) & 1, az = (a >> 2) & 1;
+    float s = 0.f;
+#pragma unroll
+    for (int t = 0; t < G::NC; ++t) {
+        const int j = (ax + (t & 1)) + 3 * (ay + ((t >> 1) & 1)) + 9 * (az + ((t >> 2) & 1));
+        s += ssum(j, col);
+    }
+    return s;
+}
+
+__device__ __forceinline__ int64_t node_of(const int n[3], int i, int j, int k) {
+    i = i >= n[0] ? i - n[0] : i;
+    j = j >= n[1] ? j - n[1] : j;
+    k = k >= n[2] ? k - n[2] : k;
+    return (int64_t)i + (int64_t)n[0] * ((int64_t)j + (int64_t)n[1] * k);
+}
+
+// ------------------------------------------------------------ fused kernel
+// WALL: the push reflects particles at the high-x face of cell x index
+// p.wall_ci (a reflecting wall); a separate instantiation, so that the push
+// without a wall compiles exactly as it would without the feature
+template <int DIM, bool PUSH, bool WALL = false>
+__global__ void __launch_bounds__(kThreads, Geo<DIM>::CTAS) k_pd(const __grid_constant__ PD p) {
+    using G = Geo<DIM>;
+    using R = Rec<DIM>;
+    constexpr int NC = G::NC;
+    extern __shared__ __align__(16) float smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float *ws = smem + (size_t)warp * warp_floats<DIM>();
+    float4 *cor = reinterpret_cast<float4 *>(ws);            // [4][NC]: mover E, mover B, deposit B, u_ref
+    float *T = ws + 16 * NC;                                  // factor table [32][TSTR]; at a cell's end the sums [lane][36]
+    const unsigned lt = (1u << lane) - 1u;
+    // this lane's block and particle group: group kg walks the particles
+    // KG s + pg; in 2D the two groups of a quarter warp take particles 4 apart,
+    // which puts their table reads in different banks
+    const int kg = lane / G::LK, lk = lane % G::LK;
+    const bool role = kg < G::KG;
+    const int pg = DIM == 2 ? (kg >> 1) + 4 * (kg & 1) : kg;
+    const int roff = 12 * (lk / 4), coff = G::COLOFF + 4 * (lk % 4);
+    const bool res[3] = {p.n[0] > 1, p.n[1] > 1, DIM == 3 && p.n[2] > 1};
+    const int64_t nwarps = (int64_t)gridDim.x * kWarpsPerCta;
+
+    for (int64_t cell = (int64_t)blockIdx.x * kWarpsPerCta + warp; cell < p.N; cell += nwarps) {
+        const int word = seg_word(__ldg(p.cnt_in + cell), p.cap, p.arrivals);
+        const int nfr = bin_front(word), nbk = bin_back(word), n = nfr + nbk;
+        if (p.arrivals && n == 0) continue;
+        const int ci = (int)(cell % p.n[0]);
+        const int cj = (int)((cell / p.n[0]) % p.n[1]);
+        const int ck = DIM == 3 ? (int)(cell / ((int64_t)p.n[0] * p.n[1])) : 0;
+        __syncwarp();                                         // the previous cell's reads of cor and S are done
+        if (lane < 4 * NC) {
+            const int arr = lane / NC, a = lane % NC;
+            if (PUSH || arr >= 2) {
+                const int64_t nd = node_of(p.n, ci + (a & 1), cj + ((a >> 1) & 1), ck + ((a >> 2) & 1));
+                const float4 *src = arr == 0 ? p.mE : arr == 1 ? p.mB : arr == 2 ? p.dB : p.dU;
+                cor[lane] = __ldg(src + nd);
+            }
+        }
+        __syncwarp();
+        float2 accp[4][4];                                    // [column][row pair]: rows 0..7 of the block
+        float acc8[4];                                        // row 8
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            acc8[c] = 0.f;
+#pragma unroll
+            for (int r = 0; r < 4; ++r) accp[c][r] = make_float2(0.f, 0.f);
+        }
+        const float *bin_in = p.in + (size_t)cell * p.cap * p.nf;
+        float *bin_out = PUSH ? p.out + (size_t)cell * p.cap * p.nf : nullptr;
+        const bool wallc = WALL && PUSH && ci == p.wall_ci;   // the wall is this cell's high-x face
+        int fbase = 0;                                        // stayers written to this cell's new bin so far
+
+        for (int c0 = 0; c0 < n; c0 += 32) {
+            const int i = c0 + lane;
+            const bool valid = i < n;
+            const int slot = i < nfr ? i : p.cap - nbk + (i - nfr);
+            float o[3] = {0.5f, 0.5f, 0.5f}, v[3] = {0.f, 0.f, 0.f}, w = 0.f, idb = 0.f;
+            if (valid) {
+                const float *q = bin_in + slot;
+#pragma unroll
+                for (int d = 0; d < DIM; ++d) o[d] = __ldcs(q + (size_t)d * p.cap);
+#pragma unroll
+                for (int d = 0; d < 3; ++d) v[d] = __ldcs(q + (size_t)(PF<DIM>::V + d) * p.cap);
+                w = __ldcs(q + (size_t)PF<DIM>::W * p.cap);
+                if (PUSH && p.nf > PF<DIM>::ID) idb = __ldcs(q + (size_t)PF<DIM>::ID * p.cap);
+            }
+            if (DIM == 2) o[2] = 0.f;
+            bool dep = valid;
+            if (PUSH) {
+                // ---- mover (Eq. 29-30, ECSIM update)
+                float W[NC], E3[3], B3[3];
+                corner_weights<DIM>(o, W);
+                gather<DIM>(cor, W, E3);
+                gather<DIM>(cor + NC, W, B3);
+                const float bx = p.bc * B3[0], by = p.bc * B3[1], bz = p.bc * B3[2];
+                // a = v + beta E ; vbar = (a + a x b + (a.b) b) / (1 + b.b)
+                const float ax = fmaf(p.beta, E3[0], v[0]), ay = fmaf(p.beta, E3[1], v[1]), az = fmaf(p.beta, E3[2], v[2]);
+                const float inv = __frcp_rn(1.0f + bx * bx + by * by + bz * bz);
+                const float ab = ax * bx + ay * by + az * bz;
+                const float vbx = (ax + (ay * bz - az * by) + ab * bx) * inv;
+                const float vby = (ay + (az * bx - ax * bz) + ab * by) * inv;
+                const float vbz = (az + (ax * by - ay * bx) + ab * bz) * inv;
+                v[0] = 2.f * vbx - v[0]; v[1] = 2.f * vby - v[1]; v[2] = 2.f * vbz - v[2];
+                int s[3] = {0, 0, 0};
+                bool cfl = false;
+#pragma unroll
+                for (int d = 0; d < DIM; ++d) {
+                    o[d] = fmaf(v[d], p.dtd[d], o[d]);
+                    if (WALL && d == 0 && wallc && o[0] >= 1.f) { o[0] = 2.f - o[0]; v[0] = -v[0]; }   // specular reflection
+                    float f = floorf(o[d]);
+                    o[d] -= f;
+                    if (o[d] >= 1.f) { o[d] -= 1.f; f += 1.f; }
+                    s[d] = (int)f;
+                    if (s[d] < -1 || s[d] > 1) { cfl = true; s[d] = max(-1, min(1, s[d])); }
+                    if (!res[d]) { s[d] = 0; o[d] = 0.f; }
+                }
+                if (valid && cfl) atomicExch(&p.flags->cfl, 1);
+                const int code = (s[0] + 1) + 3 * (s[1] + 1) + (DIM == 3 ? 9 * (s[2] + 1) : 0);
+                const bool stay = code == G::CENTER;
+                // ---- re-bin: stayers to the bottom of this cell's new bin, in order
+                const unsigned ms = __ballot_sync(kFull, valid && stay);
+                const unsigned ml = __ballot_sync(kFull, valid && !stay);
+                float *dst = nullptr;
+                if (valid && stay) {
+                    dst = bin_out + fbase + __popc(ms & lt);
+                } else if (valid) {
+                    // leavers: one atomic per (warp, destination) reserves a run at the top of
+                    // the destination bin; each leaver takes its rank within the run
+                    int di = ci + s[0], dj = cj + s[1], dk = ck + s[2];
+                    di = di < 0 ? di + p.n[0] : (di >= p.n[0] ? di - p.n[0] : di);
+                    dj = dj < 0 ? dj + p.n[1] : (dj >= p.n[1] ? dj - p.n[1] : dj);
+                    if (DIM == 3) dk = dk < 0 ? dk + p.n[2] : (dk >= p.n[2] ? dk - p.n[2] : dk);
+                    const int64_t dest = (int64_t)di + (int64_t)p.n[0] * ((int64_t)dj + (int64_t)p.n[1] * dk);
+                    const unsigned peers = __match_any_sync(ml, code);
+                    const int leader = __ffs(peers) - 1;
+                    int old = 0;
+                    if (lane == leader) old = atomicAdd(p.cnt_out + dest, __popc(peers) << 16);
+                    old = __shfl_sync(peers, old, leader);
+                    const int back = bin_back(old) + __popc(peers & lt);
+                    if (back < p.cap) dst = p.out + (size_t)dest * p.cap * p.nf + (p.cap - 1 - back);
+                    else atomicExch(&p.flags->overflow, 1);
+                }
+                if (dst) {
+#pragma unroll
+                    for (int d = 0; d < DIM; ++d) __stcs(dst + (size_t)d * p.cap, o[d]);
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) __stcs(dst + (size_t)(PF<DIM>::V + d) * p.cap, v[d]);
+                    __stcs(dst + (size_t)PF<DIM>::W * p.cap, w);
+                    if (p.nf > PF<DIM>::ID) __stcs(dst + (size_t)PF<DIM>::ID * p.cap, idb);
+                }
+                fbase += __popc(ms);
+                dep = valid && stay;
+            }
+            // ---- deposit factors of this lane's particle (zero rows if it does not deposit)
+            {
+                float W[NC], B3[3], U3[3], al[9];
+                corner_weights<DIM>(o, W);
+                gather<DIM>(cor + 2 * NC, W, B3);
+                gather<DIM>(cor + 3 * NC, W, U3);
+                alpha_tensor(p.bc * B3[0], p.bc * B3[1], p.bc * B3[2], al);
+                const float d0 = v[0] - U3[0], d1 = v[1] - U3[1], d2 = v[2] - U3[2];
+                const float wd = dep ? w : 0.f;
+                float X[3][3];
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    const float a0 = 1.f - o[d];
+                    X[d][0] = a0 * a0; X[d][1] = a0 * o[d]; X[d][2] = o[d] * o[d];
+                }
+                float *tp = T + lane * G::TSTR;
+                float *col = tp + G::COLOFF;
+                *reinterpret_cast<float4 *>(col) = make_float4(al[0], al[1], al[2], al[3]);
+                *reinterpret_cast<float4 *>(col + 4) = make_float4(al[4], al[5], al[6], al[7]);
+                *reinterpret_cast<float4 *>(col + 8) = make_float4(al[8], 1.f, v[0], v[1]);
+                *reinterpret_cast<float4 *>(col + 12) =
+                    make_float4(v[2], fmaf(al[0], d0, fmaf(al[1], d1, al[2] * d2)),
+                                fmaf(al[3], d0, fmaf(al[4], d1, al[5] * d2)), fmaf(al[6], d0, fmaf(al[7], d1, al[8] * d2)));
+#pragma unroll
+                for (int jz = 0; jz < (DIM == 3 ? 3 : 1); ++jz) {
+                    float rw[9];
+#pragma unroll
+                    for (int jy = 0; jy < 3; ++jy) {
+                        const float wyz = DIM == 3 ? wd * X[1][jy] * X[2][jz] : wd * X[1][jy];
+#pragma unroll
+                        for (int jx = 0; jx < 3; ++jx) rw[jx + 3 * jy] = wyz * X[0][jx];
+                    }
+                    float *rp = tp + 12 * jz;
+                    *reinterpret_cast<float4 *>(rp) = make_float4(rw[0], rw[1], rw[2], rw[3]);
+                    *reinterpret_cast<float4 *>(rp + 4) = make_float4(rw[4], rw[5], rw[6], rw[7]);
+                    rp[8] = rw[8];
+                }
+            }
+            __syncwarp();
+            // ---- output-stationary accumulation: this lane adds, over its group's
+            // particles, its 9 pair classes x 4 columns
+            if (role) {
+                const int nv = min(32, n - c0);
+                for (int pp = pg; pp < nv; pp += G::KG) {
+                    const float *tp = T + pp * G::TSTR;
+                    const float4 r03 = *reinterpret_cast<const float4 *>(tp + roff);
+                    const float4 r47 = *reinterpret_cast<const float4 *>(tp + roff + 4);
+                    const float r8 = tp[roff + 8];
+                    const float4 cv = *reinterpret_cast<const float4 *>(tp + coff);
+                    const float cc[4] = {cv.x, cv.y, cv.z, cv.w};
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        const float2 d = make_float2(cc[c], cc[c]);
+                        accp[c][0] = __ffma2_rn(make_float2(r03.x, r03.y), d, accp[c][0]);
+                        accp[c][1] = __ffma2_rn(make_float2(r03.z, r03.w), d, accp[c][1]);
+                        accp[c][2] = __ffma2_rn(make_float2(r47.x, r47.y), d, accp[c][2]);
+                        accp[c][3] = __ffma2_rn(make_float2(r47.z, r47.w), d, accp[c][3]);
+                        acc8[c] = fmaf(r8, cc[c], acc8[c]);
+                    }
+                }
+            }
+            __syncwarp();                                    // the table is rewritten by the next chunk
+        }
+        // the stayers' count (the bottom segment) of this cell's new bin
+        if (PUSH && lane == 0 && fbase > 0) atomicAdd(p.cnt_out + cell, fbase);
+        // the lanes' sums [lane][row 0..8][column 0..3] into the table space
+        if (role) {
+            float4 *sd = reinterpret_cast<float4 *>(T + lane * kBlk);   // row i: columns 0..3
+#pragma unroll
+            for (int ip = 0; ip < 4; ++ip) {
+                sd[2 * ip] = make_float4(accp[0][ip].x, accp[1][ip].x, accp[2][ip].x, accp[3][ip].x);
+                sd[2 * ip + 1] = make_float4(accp[0][ip].y, accp[1][ip].y, accp[2][ip].y, accp[3][ip].y);
+            }
+            sd[8] = make_float4(acc8[0], acc8[1], acc8[2], acc8[3]);
+        }
+        __syncwarp();
+        // the cell's record
+        for (int k = lane; k < R::SIZE; k += 32) {
+            const float val = record_entry<DIM>(T, k);
+            float *dst = p.rec + (size_t)k * p.N + cell;
+            if (p.arrivals) {
+                if (val != 0.f) atomicAdd(dst, val);
+            } else {
+                *dst = val;
+            }
+        }
+    }
 }
 
 // ------------------------------------------------------------ open boundaries
@@ -287,47 +429,101 @@ __device__ __forceinline__ void philox4x64(uint64_t k0, uint64_t k1, uint64_t x[
 }
 
 // Particle k of cell `cell` in the draw of `step`: key (seed, species), counter
-// (step, cell, k, 0); offsets in the cell from the top 24 bits of words 0 and 1,
-// three normals by the Box-Muller transform of 24-bit uniforms of words 2 and 3;
-// v = u + vth n.  Step 0 is the device-side initialisation, steps >= 1 the
-// boundary refill after each push.
+// (step, cell, k, 0); offsets in the cell from the top 24 bits of words 0 and 1
+// (and, along a resolved z, bits 16..39 of word 0), three normals by the
+// Box-Muller transform of 24-bit uniforms of words 2 and 3; v = u + vth n.
+// Step 0 is the device-side initialisation, steps >= 1 the boundary refill
+// after each push.
 __device__ __forceinline__ void draw_particle(uint64_t seed, int species, uint64_t step, int64_t cell, int k, int ny,
-                                              float ux, float uy, float uz, float vth, float &ox, float &oy,
-                                              float &vx, float &vy, float &vz) {
+                                              int nz, float ux, float uy, float uz, float vth, float o[3], float v[3]) {
     uint64_t x[4] = {step, (uint64_t)cell, (uint64_t)k, 0ull};
     philox4x64(seed, (uint64_t)species, x);
     const float s24 = 1.0f / 16777216.0f;
-    ox = (float)(x[0] >> 40) * s24;
-    oy = ny > 1 ? (float)(x[1] >> 40) * s24 : 0.f;
+    o[0] = (float)(x[0] >> 40) * s24;
+    o[1] = ny > 1 ? (float)(x[1] >> 40) * s24 : 0.f;
+    o[2] = nz > 1 ? (float)((x[0] >> 16) & 0xffffffu) * s24 : 0.f;
     const float u1 = (float)((x[2] >> 40) + 1) * s24, u2 = (float)((x[2] >> 16) & 0xffffffu) * s24;
     const float u3 = (float)((x[3] >> 40) + 1) * s24, u4 = (float)((x[3] >> 16) & 0xffffffu) * s24;
     const float ra = sqrtf(-2.f * logf(u1)), rb = sqrtf(-2.f * logf(u3));
     float sn, cs;
     sincospif(2.f * u2, &sn, &cs);
-    vx = ux + vth * ra * cs;
-    vy = uy + vth * ra * sn;
-    vz = uz + vth * rb * cospif(2.f * u4);
+    v[0] = ux + vth * ra * cs;
+    v[1] = uy + vth * ra * sn;
+    v[2] = uz + vth * rb * cospif(2.f * u4);
+}
+
+// store particle (o, v, w, id) in slot `slot` of cell `cell`
+template <int DIM>
+__device__ __forceinline__ void put_particle(float *bins, int cap, int nf, int64_t cell, int slot, const float o[3],
+                                             const float v[3], float w, float idb) {
+    float *q = bins + (size_t)cell * cap * nf + slot;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) q[(size_t)d * cap] = o[d];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) q[(size_t)(PF<DIM>::V + d) * cap] = v[d];
+    q[(size_t)PF<DIM>::W * cap] = w;
+    if (nf > PF<DIM>::ID) q[(size_t)PF<DIM>::ID * cap] = idb;
 }
 
 // Device-side drifting Maxwellian species: ppc draws of step 0 in every cell,
 // written straight into the cell's bin (one CTA per cell).
-__global__ void k_maxwellian(int nx, int ny, int64_t N, int cap, int ppc, uint64_t seed, int species, float ux,
-                             float uy, float uz, float vth, float w, int track, float4 *bins, int *cnt) {
+template <int DIM>
+__global__ void k_maxwellian(int ny, int nz, int64_t N, int cap, int nf, int ppc, uint64_t seed, int species,
+                             float ux, float uy, float uz, float vth, float w, float *bins, int *cnt) {
     for (int64_t cell = blockIdx.x; cell < N; cell += gridDim.x) {
         for (int k = threadIdx.x; k < ppc; k += blockDim.x) {
-            float ox, oy, vx, vy, vz;
-            draw_particle(seed, species, 0ull, cell, k, ny, ux, uy, uz, vth, ox, oy, vx, vy, vz);
-            const size_t o = (size_t)cell * cap + k;
-            bins[2 * o] = make_float4(ox, oy, vx, vy);
-            bins[2 * o + 1] = make_float4(vz, w, __int_as_float(track ? (int)(cell * ppc + k) : 0), 0.f);
+            float o[3], v[3];
+            draw_particle(seed, species, 0ull, cell, k, ny, nz, ux, uy, uz, vth, o, v);
+            put_particle<DIM>(bins, cap, nf, cell, k, o, v, w, __int_as_float((int)(cell * ppc + k)));
         }
         if (threadIdx.x == 0) cnt[cell] = ppc;
     }
-    (void)nx;
+}
+
+// The 109 sums of the 2D record held per thread (register accumulation; used by
+// the boundary refill, whose few particles per cell are spread over a CTA)
+struct RegAcc {
+    float v[Rec<2>::SIZE];
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+        for (int k = 0; k < Rec<2>::SIZE; ++k) v[k] = 0.f;
+    }
+};
+
+// the 2D record sums of one particle at offsets (x, y) with corner values of
+// B (for alpha) and u_ref, in the layout Rec<2>
+__device__ __forceinline__ void deposit_one(RegAcc &acc, float x, float y, float vx, float vy, float vz, float w,
+                                            const float4 cB[4], const float4 cU[4], float bc) {
+    const float o[3] = {x, y, 0.f};
+    float W[4], B3[3], U3[3], al[9];
+    corner_weights<2>(o, W);
+    gather<2>(cB, W, B3);
+    gather<2>(cU, W, U3);
+    alpha_tensor(bc * B3[0], bc * B3[1], bc * B3[2], al);
+    const float d[3] = {vx - U3[0], vy - U3[1], vz - U3[2]};
+    const float vv[3] = {vx, vy, vz};
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        acc.v[Rec<2>::RHO + a] = fmaf(w, W[a], acc.v[Rec<2>::RHO + a]);
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            const float jr = fmaf(al[3 * r], d[0], fmaf(al[3 * r + 1], d[1], al[3 * r + 2] * d[2]));
+            acc.v[Rec<2>::MV + 3 * a + r] = fmaf(w * vv[r], W[a], acc.v[Rec<2>::MV + 3 * a + r]);
+            acc.v[Rec<2>::J + 3 * a + r] = fmaf(w * jr, W[a], acc.v[Rec<2>::J + 3 * a + r]);
+        }
+    }
+    const float X[3] = {w * (1.f - x) * (1.f - x), w * x * (1.f - x), w * x * x};
+    const float Y[3] = {(1.f - y) * (1.f - y), y * (1.f - y), y * y};
+#pragma unroll
+    for (int j = 0; j < 9; ++j) {
+        const float pw = X[j % 3] * Y[j / 3];
+#pragma unroll
+        for (int e = 0; e < 9; ++e) acc.v[Rec<2>::M + 9 * j + e] = fmaf(pw, al[e], acc.v[Rec<2>::M + 9 * j + e]);
+    }
 }
 
 struct BcArgs {
-    int nx, ny, G, cap;
+    int nx, ny, G, cap, nf;
     int64_t N;
     uint64_t seed, step;
     int species, track;
@@ -335,17 +531,15 @@ struct BcArgs {
     int nsides;                  // 2, or 1 with a reflecting wall on the high side (no refill there)
     int ppc[2];                  // per side (0: low x, 1: high x)
     float w[2], vth[2], u[2][3];
-    float4 *bins;                // the current copy (after the push)
+    float *bins;                 // the current copy (after the push)
     int *cnt;
     float *rec;                  // [112][N] of the species
     const float4 *dB, *dU;       // node B^{n+1} and u_ref of the deposit
 };
 
 // One CTA per boundary cell: replace its particles by the side's fresh draws
-// (key (seed, species), counter (step, cell, k, 0); offsets from the top 24
-// bits of words 0 and 1, three normals by Box-Muller from 24-bit uniforms of
-// words 2 and 3), deposit them with the push's deposit arithmetic and
-// overwrite the cell's record and count.
+// (key (seed, species), counter (step, cell, k, 0)), deposit them with the
+// deposit's arithmetic and overwrite the cell's record and count (2D).
 __global__ void __launch_bounds__(128) k_bc_refill(BcArgs a) {
     __shared__ float red[4][Rec<2>::SIZE];
     const int t = blockIdx.x, G2c = a.nsides * a.G;
@@ -353,28 +547,28 @@ __global__ void __launch_bounds__(128) k_bc_refill(BcArgs a) {
     const int side = r < a.G ? 0 : 1;
     const int i = r < a.G ? r : a.nx - G2c + r;
     const int64_t cell = (int64_t)j * a.nx + i;
-    int64_t nd[4];
-    corner_nodes(i, j, a.nx, a.ny, nd);
+    const int n3[3] = {a.nx, a.ny, 1};
     float4 cB[4], cU[4];
 #pragma unroll
-    for (int c = 0; c < 4; ++c) { cB[c] = a.dB[nd[c]]; cU[c] = a.dU[nd[c]]; }
+    for (int c = 0; c < 4; ++c) {
+        const int64_t nd = node_of(n3, i + (c & 1), j + (c >> 1), 0);
+        cB[c] = a.dB[nd];
+        cU[c] = a.dU[nd];
+    }
     const int ppc = a.ppc[side];
     const float w = a.w[side], vth = a.vth[side];
     RegAcc acc;
     acc.zero();
     for (int k = threadIdx.x; k < ppc; k += blockDim.x) {
-        float ox, oy, vx, vy, vz;
-        draw_particle(a.seed, a.species, a.step, cell, k, a.ny, a.u[side][0], a.u[side][1], a.u[side][2], vth, ox, oy,
-                      vx, vy, vz);
-        const size_t o = (size_t)cell * a.cap + k;
-        a.bins[2 * o] = make_float4(ox, oy, vx, vy);
-        a.bins[2 * o + 1] = make_float4(vz, w, __int_as_float(a.track ? -1 : 0), 0.f);
-        deposit_one(acc, ox, oy, vx, vy, vz, w, cB, cU, a.bc);
+        float o[3], v[3];
+        draw_particle(a.seed, a.species, a.step, cell, k, a.ny, 1, a.u[side][0], a.u[side][1], a.u[side][2], vth, o, v);
+        put_particle<2>(a.bins, a.cap, a.nf, cell, k, o, v, w, __int_as_float(a.track ? -1 : 0));
+        deposit_one(acc, o[0], o[1], v[0], v[1], v[2], w, cB, cU, a.bc);
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int k = 0; k < Rec<2>::SIZE; ++k) {
-        float v = acc.get(k);
+        float v = acc.v[k];
 #pragma unroll
         for (int m = 16; m > 0; m >>= 1) v += __shfl_xor_sync(kFull, v, m);
         if (lane == 0) red[warp][k] = v;
@@ -383,283 +577,6 @@ __global__ void __launch_bounds__(128) k_bc_refill(BcArgs a) {
     for (int k = threadIdx.x; k < Rec<2>::SIZE; k += blockDim.x)
         a.rec[(size_t)k * a.N + cell] = (red[0][k] + red[1][k]) + (red[2][k] + red[3][k]);
     if (threadIdx.x == 0) a.cnt[cell] = ppc;          // front segment only
-}
-
-// ------------------------------------------------------------ fused kernel
-// WALL: the push reflects particles at the high-x face of cell x index
-// p.wall_ci (a reflecting wall); a separate instantiation, so that the push
-// without a wall compiles exactly as it would without the feature
-template <bool PUSH, bool WALL = false>
-__global__ void __launch_bounds__(kThreads, 1) k_pd(P2 p) {
-    extern __shared__ __align__(128) unsigned char smem[];
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem);                         // [groups][2]
-    float4 *bufs = reinterpret_cast<float4 *>(smem + kBarBytes);                  // [groups][2][kChunk][2]
-    int *codes = reinterpret_cast<int *>(smem + kBarBytes + kBufBytes);           // [groups][kChunk + 1]
-    unsigned char *maps = smem + kBarBytes + kBufBytes + kCodeBytes;             // [groups][kChunk]
-    float *scr_all = reinterpret_cast<float *>(smem + kBarBytes + kBufBytes + kCodeBytes + kMapBytes);  // [warps][kScr]
-    int *dircnt = reinterpret_cast<int *>(smem + kBarBytes + kBufBytes + kCodeBytes + kMapBytes + kScrBytes);
-
-    const int tid = threadIdx.x;
-    const int lane = tid & 31, warp = tid >> 5;
-    const int g = tid / kGroup, lig = tid % kGroup;
-    const int gshift = (lane / kGroup) * kGroup;
-    float4 *mybuf = bufs + (size_t)g * kGroupBuf;
-    int *mycode = codes + g * kCodeStride;
-    unsigned char *mymap = maps + g * kChunk;
-    uint64_t *mybar = bars + 2 * g;
-    float *scr = scr_all + (size_t)warp * kScr;
-    int *mydir = dircnt + g * 8;
-
-    if (lig == 0) {
-        mbar_init(&mybar[0], 1);
-        mbar_init(&mybar[1], 1);
-    }
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    __syncthreads();
-
-    // producer state of this group (lane 0): next chunk to stream = chunk
-    // `ich` of the cell of batch `ib`
-    int ib = blockIdx.x, ich = 0, inch = -1, iword = 0;
-    int issued = 0, cons = 0;
-    auto find_next = [&]() -> bool {
-        while (ib < p.nbatch) {
-            if (inch < 0) {
-                const int64_t cell = (int64_t)ib * kGroups + g;
-                iword = cell < p.N ? seg_word(p.cnt_in[cell], p.cap, p.arrivals) : 0;
-                inch = bin_chunks(iword);
-            }
-            if (ich < inch) return true;
-            ib += gridDim.x;
-            ich = 0;
-            inch = -1;
-        }
-        return false;
-    };
-    // stream chunk `ich` of the cell: only the slots of its own segment (whole
-    // 32-byte slots are 16-byte aligned), into the same positions of the
-    // staging buffer
-    auto issue = [&]() {
-        const int slot = issued & 1;
-        const int64_t cell = (int64_t)ib * kGroups + g;
-        const int fr = bin_front(iword), sbase = chunk_base(ich, fr, p.cap);
-        int lo = 0, hi = kChunk;
-        if (ich < (fr + kChunk - 1) / kChunk) hi = min(kChunk, fr - sbase);
-        else lo = max(0, p.cap - bin_back(iword) - sbase);
-        const uint32_t bytes = (uint32_t)((hi - lo) * 2 * sizeof(float4));
-        const float4 *src = p.in + 2 * ((size_t)cell * p.cap + sbase + lo);
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_expect_tx(&mybar[slot], bytes);
-        bulk_g2s(mybuf + (size_t)(slot * kChunk + lo) * 2, src, bytes, &mybar[slot]);
-        ++issued;
-        ++ich;
-    };
-    if (lig == 0) {
-        if (find_next()) issue();
-        if (find_next()) issue();
-    }
-
-    bool abort = false;
-    for (int b = blockIdx.x; b < p.nbatch; b += gridDim.x) {
-        const int64_t cell = (int64_t)b * kGroups + g;
-        const bool valid = cell < p.N;
-        const int word = valid ? seg_word(p.cnt_in[cell], p.cap, p.arrivals) : 0;
-        const int nch = bin_chunks(word);
-        const int nchf = (bin_front(word) + kChunk - 1) / kChunk;
-        const int wmax = __reduce_max_sync(kFull, nch);
-        const int ci = valid ? (int)(cell % p.nx) : 0, cj = valid ? (int)(cell / p.nx) : 0;
-        const bool wallc = WALL && PUSH && ci == p.wall_ci;      // the wall is this cell's high-x face
-        int64_t nd[4];
-        corner_nodes(ci, cj, p.nx, p.ny, nd);
-        float4 cB[4], cU[4], mE[4], mB[4];
-#pragma unroll
-        for (int a = 0; a < 4; ++a) {
-            cB[a] = __ldg(p.dB + nd[a]);
-            cU[a] = __ldg(p.dU + nd[a]);
-            if (PUSH) { mE[a] = __ldg(p.mE + nd[a]); mB[a] = __ldg(p.mB + nd[a]); }
-        }
-        RegAcc acc;
-        acc.zero();
-        int fbase = 0;                      // stayers written to this cell's new bin so far
-
-        for (int ch = 0; ch < wmax; ++ch) {
-            const bool has = ch < nch;
-            const int slot = cons & 1;
-            bool ok = true;
-            if (has) ok = mbar_wait_bounded(&mybar[slot], (uint32_t)((cons >> 1) & 1));
-            if (__any_sync(kFull, !ok)) { abort = true; break; }
-            float4 *cbuf = mybuf + (size_t)slot * kChunk * 2;
-            const int sbase = has ? chunk_base(ch, bin_front(word), p.cap) : 0;
-            // particles of this chunk: slots of its own segment only
-            unsigned long long vmask = 0ull;
-            if (has) {
-                const int lo = ch < nchf ? 0 : max(0, p.cap - bin_back(word) - sbase);
-                const int hi = ch < nchf ? min(kChunk, bin_front(word) - sbase) : kChunk;
-                if (hi > lo) vmask = (hi - lo == 64 ? ~0ull : ((1ull << (hi - lo)) - 1ull)) << lo;
-            }
-            unsigned long long smask = vmask;   // stayers (all of them without the push)
-            int old[kPerLane];                  // ranks of this lane's leavers within their (group, neighbour)
-            int ddest = 0, dbase = 0;           // lane d: neighbour d's cell and its count word before the run
-            if (PUSH) {
-                // ---- A1: mover.  New state written back into the staged chunk,
-                // the destination cell of each leaver into the code row.
-                unsigned long long lv = 0ull;
-#pragma unroll 2
-                for (int k = 0; k < kPerLane; ++k) {
-                    const int j = k * kGroup + lig;
-                    bool leave = false;
-                    if ((vmask >> j) & 1ull) {
-                        const float4 s0 = cbuf[2 * j];
-                        float x = s0.x, y = s0.y, vx = s0.z, vy = s0.w;
-                        float vz = reinterpret_cast<const float *>(cbuf + 2 * j + 1)[0];
-                        const float wx0 = 1.f - x, wy0 = 1.f - y;
-                        const float W0 = wx0 * wy0, W1 = x * wy0, W2 = wx0 * y, W3 = x * y;
-                        const float ex = W0 * mE[0].x + W1 * mE[1].x + W2 * mE[2].x + W3 * mE[3].x;
-                        const float ey = W0 * mE[0].y + W1 * mE[1].y + W2 * mE[2].y + W3 * mE[3].y;
-                        const float ez = W0 * mE[0].z + W1 * mE[1].z + W2 * mE[2].z + W3 * mE[3].z;
-                        const float bx = p.bc * (W0 * mB[0].x + W1 * mB[1].x + W2 * mB[2].x + W3 * mB[3].x);
-                        const float by = p.bc * (W0 * mB[0].y + W1 * mB[1].y + W2 * mB[2].y + W3 * mB[3].y);
-                        const float bz = p.bc * (W0 * mB[0].z + W1 * mB[1].z + W2 * mB[2].z + W3 * mB[3].z);
-                        // a = v + beta E ; vbar = (a + a x b + (a.b) b) / (1 + b.b)
-                        const float ax = fmaf(p.beta, ex, vx), ay = fmaf(p.beta, ey, vy), az = fmaf(p.beta, ez, vz);
-                        const float inv = __frcp_rn(1.0f + bx * bx + by * by + bz * bz);
-                        const float ab = ax * bx + ay * by + az * bz;
-                        const float vbx = (ax + (ay * bz - az * by) + ab * bx) * inv;
-                        const float vby = (ay + (az * bx - ax * bz) + ab * by) * inv;
-                        const float vbz = (az + (ax * by - ay * bx) + ab * bz) * inv;
-                        vx = 2.f * vbx - vx; vy = 2.f * vby - vy; vz = 2.f * vbz - vz;
-                        x = fmaf(vx, p.dtdx, x);
-                        if (WALL && wallc && x >= 1.f) { x = 2.f - x; vx = -vx; }   // specular reflection
-                        y = fmaf(vy, p.dtdy, y);
-                        float fx = floorf(x), fy = floorf(y);
-                        x -= fx; y -= fy;
-                        if (x >= 1.f) { x -= 1.f; fx += 1.f; }
-                        if (y >= 1.f) { y -= 1.f; fy += 1.f; }
-                        int sx = (int)fx, sy = (int)fy;
-                        if (sx < -1 || sx > 1 || sy < -1 || sy > 1) {
-                            atomicExch(&p.flags->cfl, 1);
-                            sx = max(-1, min(1, sx)); sy = max(-1, min(1, sy));
-                        }
-                        if (p.ny == 1) { sy = 0; y = 0.f; }
-                        leave = sx != 0 || sy != 0;
-                        const int code = (sx + 1) + 3 * (sy + 1);          // 4 = stays
-                        cbuf[2 * j] = make_float4(x, y, vx, vy);
-                        reinterpret_cast<float *>(cbuf + 2 * j + 1)[0] = vz;
-                        mycode[j] = code < 4 ? code : code - 1;            // neighbour 0..7
-                    }
-                    if (leave) lv |= 1ull << j;
-                }
-                // gather the group's leaver bits (each lane knows its own slots)
-                unsigned long long all = lv;
-#pragma unroll
-                for (int o = 1; o < kGroup; o <<= 1) all |= __shfl_xor_sync(kFull, all, o);
-                smask = vmask & ~all;
-                __syncwarp();
-                // ---- B1: reserve the leavers' slots at the top of their new
-                // bins: each leaver takes a rank within its (group, neighbour)
-                // from a shared-memory counter, then lane d reserves the whole
-                // run of neighbour d with one global atomic (results used only
-                // after the deposit)
-                mydir[lig] = 0;
-                __syncwarp();
-#pragma unroll
-                for (int k = 0; k < kPerLane; ++k) {
-                    const int j = k * kGroup + lig;
-                    old[k] = (lv >> j) & 1ull ? atomicAdd(&mydir[mycode[j]], 1) : 0;
-                }
-                __syncwarp();
-                {
-                    const int cntd = mydir[lig];
-                    const int code = lig < 4 ? lig : lig + 1;
-                    int dxg = ci + code % 3 - 1, dyg = cj + code / 3 - 1;
-                    dxg = dxg < 0 ? dxg + p.nx : (dxg >= p.nx ? dxg - p.nx : dxg);
-                    dyg = dyg < 0 ? dyg + p.ny : (dyg >= p.ny ? dyg - p.ny : dyg);
-                    ddest = dxg + p.nx * dyg;
-                    dbase = cntd > 0 ? atomicAdd(&p.cnt_out[ddest], cntd << 16) : 0;
-                }
-            }
-            // ---- A2: deposit of the stayers (compacted, no idle lanes).  With
-            // the push the stayers are scattered over the chunk: each lane
-            // enters its own slots in the group's compaction map first.
-            const int ns = __popcll(smask);
-            const int vlo = vmask ? __ffsll((long long)vmask) - 1 : 0;
-            if (PUSH) {
-#pragma unroll
-                for (int k = 0; k < kPerLane; ++k) {
-                    const int j = k * kGroup + lig;
-                    if ((smask >> j) & 1ull) mymap[__popcll(smask & ((1ull << j) - 1ull))] = (unsigned char)j;
-                }
-                __syncwarp();
-            }
-            for (int t = lig; t < ns; t += kGroup) {
-                const int j = PUSH ? (int)mymap[t] : vlo + t;
-                const float4 s0 = cbuf[2 * j];
-                const float2 s1 = reinterpret_cast<const float2 *>(cbuf + 2 * j + 1)[0];
-                deposit_one(acc, s0.x, s0.y, s0.z, s0.w, s1.x, s1.y, cB, cU, p.bc);
-            }
-            // ---- B2: write the chunk into the other copy
-            if (PUSH) {
-                // stayers: bottom of this cell's new bin, in order.  The warp
-                // writes one group's run at a time, 16 slots (512 contiguous
-                // bytes) per store instruction.
-                const int boff = (int)(cbuf - bufs);
-                const int moff = (int)(mymap - maps);
-#pragma unroll
-                for (int gi = 0; gi < 4; ++gi) {
-                    const int src = gi * kGroup;
-                    const int ns_g = __shfl_sync(kFull, ns, src);
-                    if (ns_g == 0) continue;
-                    const int base_g = __shfl_sync(kFull, fbase, src);
-                    const long long cell_g = __shfl_sync(kFull, (long long)cell, src);
-                    const float4 *gbuf = bufs + __shfl_sync(kFull, boff, src);
-                    const unsigned char *gmap = maps + __shfl_sync(kFull, moff, src);
-                    float4 *dst = p.out + 2 * ((size_t)cell_g * p.cap + base_g);
-                    // 32 slots (1 KB contiguous) per round, one 256-bit store per lane
-                    for (int r0 = 0; r0 < ns_g; r0 += 32) {
-                        const int t = r0 + lane;
-                        if (t < ns_g) {
-                            const int j = gmap[t];
-                            st_slot(dst + 2 * t, gbuf[2 * j], gbuf[2 * j + 1]);
-                        }
-                    }
-                }
-                // leavers: the slot reserved in B1 (one 32-byte sector each)
-#pragma unroll
-                for (int k = 0; k < kPerLane; ++k) {
-                    const int j = k * kGroup + lig;
-                    const bool lvj = ((vmask >> j) & 1ull) && !((smask >> j) & 1ull);
-                    const int d = lvj ? mycode[j] : 0;
-                    const int dest = __shfl_sync(kFull, ddest, gshift + d);
-                    const int w0 = __shfl_sync(kFull, dbase, gshift + d);
-                    if (lvj) {
-                        const int back = bin_back(w0) + old[k];
-                        if (back < p.cap) {
-                            const size_t o = (size_t)dest * p.cap + p.cap - 1 - back;
-                            st_slot(p.out + 2 * o, cbuf[2 * j], cbuf[2 * j + 1]);
-                        } else {
-                            atomicExch(&p.flags->overflow, 1);
-                        }
-                    }
-                }
-                fbase += ns;
-            }
-            __syncwarp();
-            if (has) {
-                ++cons;
-                if (lig == 0 && find_next()) issue();       // refill the buffer just consumed
-            }
-        }
-        if (abort) break;
-        // the stayers' count (the bottom segment) of this cell's new bin
-        if (PUSH && valid && lig == 0 && fbase > 0) atomicAdd(&p.cnt_out[cell], fbase);
-        group_reduce_store(acc, scr, lane, lig, gshift, p.rec + cell, p.N, valid && (!p.arrivals || nch > 0),
-                           p.arrivals != 0);
-    }
-    if (abort) {
-        if (lane == 0) atomicExch(&p.flags->timeout, 1);
-        // drain this group's copies still in flight before the CTA exits
-        if (lig == 0)
-            for (int k = cons; k < issued; ++k) mbar_wait_bounded(&mybar[k & 1], (uint32_t)((k >> 1) & 1));
-    }
 }
 
 // largest bin count after a push; a bin whose two segments met has lost
@@ -686,75 +603,84 @@ __global__ void k_counts(const int *cnt, int64_t n, int cap, int *out) {
 // cell and in-cell offsets of every particle; positions scaled by the inverse
 // cell widths (no FP64 division or fmod: both run on the slow FP64 pipe), the
 // cell index wrapped in integers (positions within +-2^31 cells)
-__global__ void k_locate(int64_t n, const double *x, const double *y, int nx, int ny, double idx, double idy,
-                         int *cell, float *ox, float *oy, int *count) {
+__device__ __forceinline__ int cell_along(double pos, double inv_dx, int n, float &off) {
+    if (n == 1) { off = 0.f; return 0; }
+    const double sx = pos * inv_dx, fx = floor(sx);
+    const long long lx = (long long)fx;
+    int cx = (lx >= 0 && lx < n) ? (int)lx : (int)(((lx % n) + n) % n);   // inside the box: no division
+    off = (float)(sx - fx);
+    if (off >= 1.f) { off = 0.f; cx = wrap_idx(cx + 1, n); }
+    return cx;
+}
+
+__global__ void k_locate(int64_t n, const double *x, const double *y, const double *z, int nx, int ny, int nz,
+                         double idx, double idy, double idz, int64_t *cell, float *ox, float *oy, float *oz,
+                         int *count) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        double sx = x[i] * idx, sy = (ny > 1) ? y[i] * idy : 0.0;
-        double fx = floor(sx), fy = floor(sy);
-        double rx = sx - fx, ry = sy - fy;
-        const long long lx = (long long)fx, ly = (long long)fy;
-        int cx = (lx >= 0 && lx < nx) ? (int)lx : (int)(((lx % nx) + nx) % nx);   // inside the box: no division
-        int cy = ny == 1 ? 0 : ((ly >= 0 && ly < ny) ? (int)ly : (int)(((ly % ny) + ny) % ny));
-        float fxo = (float)rx, fyo = (float)ry;
-        if (fxo >= 1.f) { fxo = 0.f; cx = wrap_idx(cx + 1, nx); }
-        if (fyo >= 1.f) { fyo = 0.f; cy = wrap_idx(cy + 1, ny); }
-        if (ny == 1) fyo = 0.f;
-        const int c = cx + nx * cy;
+        float fx, fy, fz;
+        const int cx = cell_along(x[i], idx, nx, fx);
+        const int cy = cell_along(ny > 1 ? y[i] : 0.0, idy, ny, fy);
+        const int cz = cell_along(nz > 1 ? z[i] : 0.0, idz, nz, fz);
+        const int64_t c = cx + (int64_t)nx * (cy + (int64_t)ny * cz);
         cell[i] = c;
-        ox[i] = fxo;
-        oy[i] = fyo;
+        ox[i] = fx;
+        oy[i] = fy;
+        oz[i] = fz;
         atomicAdd(&count[c], 1);
     }
 }
 
-__global__ void k_scatter(int64_t n, const int *cell, const float *ox, const float *oy, const float *vx,
-                          const float *vy, const float *vz, const float *w, const int32_t *id, int cap,
-                          int *cursor, float4 *out, int track, DevFlags *f) {
+template <int DIM>
+__global__ void k_scatter(int64_t n, const int64_t *cell, const float *ox, const float *oy, const float *oz,
+                          const float *vx, const float *vy, const float *vz, const float *w, const int32_t *id,
+                          int cap, int nf, int *cursor, float *out, DevFlags *f) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int c = cell[i];
+        const int64_t c = cell[i];
         const int slot = atomicAdd(&cursor[c], 1);
         if (slot >= cap) { atomicExch(&f->overflow, 1); continue; }
-        const size_t o = (size_t)c * cap + slot;
-        const int idv = track ? (id ? id[i] : (int32_t)i) : 0;
-        out[2 * o] = make_float4(ox[i], oy[i], vx[i], vy[i]);
-        out[2 * o + 1] = make_float4(vz[i], w[i], __int_as_float(idv), 0.f);
+        const int idv = id ? id[i] : (int32_t)i;
+        const float o[3] = {ox[i], oy[i], oz[i]}, v[3] = {vx[i], vy[i], vz[i]};
+        put_particle<DIM>(out, cap, nf, c, slot, o, v, w[i], __int_as_float(idv));
     }
 }
 
 // copy bins into bins of a new capacity (both segments into the new front)
-__global__ void k_rebin_copy(int64_t ncell, int oldcap, int newcap, const int *cnt, int *newcnt, const float4 *src,
-                             float4 *dst) {
+__global__ void k_rebin_copy(int64_t ncell, int oldcap, int newcap, int nf, const int *cnt, int *newcnt,
+                             const float *src, float *dst) {
     const int64_t c = blockIdx.x;
     if (c >= ncell) return;
     const int word = clamp_word(cnt[c], oldcap);
     const int m = min(bin_count(word), newcap);
-    for (int i = threadIdx.x; i < 2 * m; i += blockDim.x) {
-        const size_t s = (size_t)c * oldcap + bin_slot(word, i >> 1, oldcap);
-        dst[2 * ((size_t)c * newcap + (i >> 1)) + (i & 1)] = src[2 * s + (i & 1)];
+    const float *s = src + (size_t)c * oldcap * nf;
+    float *d = dst + (size_t)c * newcap * nf;
+    for (int t = threadIdx.x; t < m * nf; t += blockDim.x) {
+        const int f = t / m, i = t % m;
+        d[(size_t)f * newcap + i] = s[(size_t)f * oldcap + bin_slot(word, i, oldcap)];
     }
     if (threadIdx.x == 0) newcnt[c] = m;
 }
 
-__global__ void k_gather_out(int64_t ncell, int cap, const int *cnt, const int *offs, const float4 *src, int nx,
-                             int ny, double dx, double dy, double *x, double *y, double *z, float *vx, float *vy,
-                             float *vz, float *w, int32_t *id) {
+template <int DIM>
+__global__ void k_gather_out(int64_t ncell, int cap, int nf, const int *cnt, const int *offs, const float *src,
+                             int nx, int ny, double dx, double dy, double dz, double *x, double *y, double *z,
+                             float *vx, float *vy, float *vz, float *w, int32_t *id) {
     const int64_t c = blockIdx.x;
     if (c >= ncell) return;
     const int word = clamp_word(cnt[c], cap);
     const int m = bin_count(word);
-    const int cx = (int)(c % nx), cy = (int)(c / nx);
+    const int cx = (int)(c % nx), cy = (int)((c / nx) % ny), cz = (int)(c / ((int64_t)nx * ny));
+    const float *b = src + (size_t)c * cap * nf;
     for (int i = threadIdx.x; i < m; i += blockDim.x) {
-        const size_t s = (size_t)c * cap + bin_slot(word, i, cap);
-        const float4 a = src[2 * s], b = src[2 * s + 1];
+        const float *q = b + bin_slot(word, i, cap);
         const int o = offs[c] + i;
-        if (x) x[o] = (cx + (double)a.x) * dx;
-        if (y) y[o] = ny > 1 ? (cy + (double)a.y) * dy : 0.0;
-        if (z) z[o] = 0.0;
-        if (vx) vx[o] = a.z;
-        if (vy) vy[o] = a.w;
-        if (vz) vz[o] = b.x;
-        if (w) w[o] = b.y;
-        if (id) id[o] = __float_as_int(b.z);
+        if (x) x[o] = (cx + (double)q[0]) * dx;
+        if (y) y[o] = ny > 1 ? (cy + (double)q[(size_t)cap]) * dy : 0.0;
+        if (z) z[o] = DIM == 3 ? (cz + (double)q[(size_t)2 * cap]) * dz : 0.0;
+        if (vx) vx[o] = q[(size_t)PF<DIM>::V * cap];
+        if (vy) vy[o] = q[(size_t)(PF<DIM>::V + 1) * cap];
+        if (vz) vz[o] = q[(size_t)(PF<DIM>::V + 2) * cap];
+        if (w) w[o] = q[(size_t)PF<DIM>::W * cap];
+        if (id) id[o] = __float_as_int(q[(size_t)PF<DIM>::ID * cap]);
     }
 }
 
@@ -766,10 +692,11 @@ int grid_for(int64_t n, int block = 256) {
 
 int alloc_bins(gx_ctx *c, int s, int cap) {
     Species &S = c->sp[s];
-    const size_t nslot = (size_t)c->N * cap;
+    S.nf = c->dim + 4 + (c->cfg.track_ids ? 1 : 0);
+    const size_t nfl = (size_t)c->N * cap * S.nf;
     for (int b = 0; b < 2; ++b) {
         S.p[b] = nullptr;
-        GX_CHECK(c, cudaMalloc(&S.p[b], nslot * 2 * sizeof(float4)));
+        GX_CHECK(c, cudaMalloc(&S.p[b], nfl * sizeof(float)));
         GX_CHECK(c, cudaMalloc(&S.cnt[b], c->N * sizeof(int)));
         GX_CHECK(c, cudaMemset(S.cnt[b], 0, c->N * sizeof(int)));
     }
@@ -786,115 +713,61 @@ void free_bins(Species &S) {
     }
 }
 
-// bin capacity: a multiple of the 64-particle chunk (staged chunks stay inside
-// their bin) and below 2^15 (the packed count word)
+// bin capacity: a multiple of 32 (a warp's chunk of the front segment is one
+// aligned line per field) and below 2^15 (the packed count word)
 int round_cap(double v) {
     int cap = (int)ceil(v);
-    cap = (cap + kChunk - 1) / kChunk * kChunk;
-    return cap < kChunk ? kChunk : cap;
+    cap = (cap + 31) / 32 * 32;
+    return cap < 32 ? 32 : cap;
 }
 
-}  // namespace
-
-// --------------------------------------------------------------- binning
-int gx_bin_particles(gx_ctx *c, int s, int64_t n, const double *x, const double *y, const double *z,
-                     const float *vx, const float *vy, const float *vz, const float *w, const int32_t *id,
-                     cudaStream_t st) {
-    (void)z;
-    Species &S = c->sp[s];
-    int *cell = nullptr, *count = nullptr;
-    float *ox = nullptr, *oy = nullptr;
-    GX_CHECK(c, cudaMalloc(&cell, (n + 1) * sizeof(int)));
-    GX_CHECK(c, cudaMalloc(&ox, (n + 1) * sizeof(float)));
-    GX_CHECK(c, cudaMalloc(&oy, (n + 1) * sizeof(float)));
-    GX_CHECK(c, cudaMalloc(&count, c->N * sizeof(int)));
-    GX_CHECK(c, cudaMemsetAsync(count, 0, c->N * sizeof(int), st));
-    if (n > 0) {
-        k_locate<<<grid_for(n), 256, 0, st>>>(n, x, y, c->n[0], c->n[1], 1.0 / c->cfg.dx[0], 1.0 / c->cfg.dx[1], cell, ox,
-                                               oy, count);
-        GX_LAUNCHED(c);
-    }
-    DevFlags *dmax = nullptr;
-    GX_CHECK(c, cudaMalloc(&dmax, sizeof(DevFlags)));
-    GX_CHECK(c, cudaMemsetAsync(dmax, 0, sizeof(DevFlags), st));
-    k_max_count<<<grid_for(c->N), 256, 0, st>>>(count, c->N, 0, dmax);
-    GX_LAUNCHED(c);
-    DevFlags hf{};
-    GX_CHECK(c, cudaMemcpyAsync(&hf, dmax, sizeof(DevFlags), cudaMemcpyDeviceToHost, st));
-    GX_CHECK(c, cudaStreamSynchronize(st));
-    const double slack = c->cfg.bin_slack > 1.2 ? c->cfg.bin_slack : 1.2;
-    const int cap = round_cap(std::max(64.0, hf.maxcount * slack));
-    GX_CHECK(c, cudaFree(dmax));
-    if (cap >= 32768) { c->err = "more than 32767 particles per cell bin"; return GX_EINVAL; }
-    int rc = alloc_bins(c, s, cap);
-    if (rc) return rc;
-    GX_CHECK(c, cudaMemsetAsync(S.cnt[c->cur], 0, c->N * sizeof(int), st));
-    if (n > 0) {
-        k_scatter<<<grid_for(n), 256, 0, st>>>(n, cell, ox, oy, vx, vy, vz, w, id, cap, S.cnt[c->cur], S.p[c->cur],
-                                                c->cfg.track_ids, c->dflags);
-        GX_LAUNCHED(c);
-    }
-    GX_CHECK(c, cudaStreamSynchronize(st));
-    cudaFree(cell); cudaFree(ox); cudaFree(oy); cudaFree(count);
+template <int DIM>
+int configure_pd(gx_ctx *c) {
+    static bool done = false;
+    if (done) return GX_OK;
+    const int sm = (int)pd_smem_bytes<DIM>();
+    GX_CHECK(c, cudaFuncSetAttribute(k_pd<DIM, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    GX_CHECK(c, cudaFuncSetAttribute(k_pd<DIM, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    if constexpr (DIM == 2)
+        GX_CHECK(c, cudaFuncSetAttribute(k_pd<DIM, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    done = true;
     return GX_OK;
 }
 
-int gx_species_maxwellian_init(gx_ctx *c, int s, int ppc, double n0, const double u[3], double vth,
-                               cudaStream_t st) {
-    const double slack = c->cfg.bin_slack > 1.2 ? c->cfg.bin_slack : 1.2;
-    const int cap = round_cap(std::max(64.0, ppc * slack));
-    if (cap >= 32768) { c->err = "more than 32767 particles per cell bin"; return GX_EINVAL; }
-    int rc = alloc_bins(c, s, cap);
-    if (rc) return rc;
-    const double dV = c->cfg.dx[0] * c->cfg.dx[1] * c->cfg.dx[2];
-    const unsigned grid = (unsigned)std::min<int64_t>(c->N, 152 * 64);
-    k_maxwellian<<<grid, 128, 0, st>>>(c->n[0], c->n[1], c->N, cap, ppc, c->cfg.seed, s, (float)u[0], (float)u[1],
-                                       (float)u[2], (float)vth, (float)(n0 * dV / ppc), c->cfg.track_ids,
-                                       c->sp[s].p[c->cur], c->sp[s].cnt[c->cur]);
-    GX_LAUNCHED(c);
-    GX_CHECK(c, cudaStreamSynchronize(st));
-    return GX_OK;
-}
-
-int gx_regrow_bins(gx_ctx *c, int s, int newcap, cudaStream_t st) {
-    newcap = round_cap(newcap);
-    if (newcap >= 32768) { c->err = "more than 32767 particles per cell bin"; return GX_EOVERFLOW; }
-    Species &S = c->sp[s];
-    Species old = S;
-    int rc = alloc_bins(c, s, newcap);
-    if (rc) return rc;
-    k_rebin_copy<<<(unsigned)c->N, 128, 0, st>>>(c->N, old.cap, newcap, old.cnt[c->cur], S.cnt[c->cur],
-                                                  old.p[c->cur], S.p[c->cur]);
-    GX_LAUNCHED(c);
-    GX_CHECK(c, cudaStreamSynchronize(st));
-    free_bins(old);
-    return GX_OK;
-}
-
-// ------------------------------------------------------------ hot path
-static int launch_pd(gx_ctx *c, bool push, cudaStream_t st) {
-    static bool configured = false;
-    if (!configured) {
-        GX_CHECK(c, cudaFuncSetAttribute(k_pd<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pd_smem_bytes()));
-        GX_CHECK(c, cudaFuncSetAttribute(k_pd<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)pd_smem_bytes()));
-        GX_CHECK(c, cudaFuncSetAttribute(k_pd<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pd_smem_bytes()));
-        configured = true;
+// persistent grid: as many CTAs as fit on the device at once
+template <int DIM>
+int pd_grid(gx_ctx *c, int64_t ncell) {
+    static int per_sm = 0;
+    if (!per_sm) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pd<DIM, true>, kThreads, pd_smem_bytes<DIM>()) !=
+                cudaSuccess ||
+            per_sm < 1)
+            per_sm = 1;
     }
     int dev = 0, nsm = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    const int nbatch = (int)((c->N + kGroups - 1) / kGroups);
-    const int grid = std::max(1, std::min(nbatch, nsm));
+    const int64_t need = (ncell + kWarpsPerCta - 1) / kWarpsPerCta;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)nsm * per_sm));
+}
+
+template <int DIM>
+int launch_pd(gx_ctx *c, bool push, cudaStream_t st) {
+    int rc = configure_pd<DIM>(c);
+    if (rc) return rc;
+    const int grid = pd_grid<DIM>(c, c->N);
+    const size_t smem = pd_smem_bytes<DIM>();
     const int nxt = 1 - c->cur;
     for (int s = 0; s < c->nspecies; ++s) {
         Species &S = c->sp[s];
-        P2 p{};
-        p.nx = c->n[0]; p.ny = c->n[1]; p.N = c->N;
+        PD p{};
+        for (int d = 0; d < 3; ++d) {
+            p.n[d] = c->n[d];
+            p.dtd[d] = (float)(c->cfg.dt / c->cfg.dx[d]);
+        }
+        p.N = c->N;
         p.cap = S.cap;
-        p.nbatch = nbatch;
-        p.dtdx = (float)(c->cfg.dt / c->cfg.dx[0]);
-        p.dtdy = (float)(c->cfg.dt / c->cfg.dx[1]);
+        p.nf = S.nf;
         const double beta = S.q * c->cfg.dt / (2.0 * S.m);
         p.beta = (float)beta;
         p.bc = (float)(beta / c->cfg.c);
@@ -902,7 +775,7 @@ static int launch_pd(gx_ctx *c, bool push, cudaStream_t st) {
         p.out = S.p[nxt];
         p.cnt_in = S.cnt[c->cur];
         p.cnt_out = S.cnt[nxt];
-        p.rec = c->rec + (size_t)s * c->N * Rec<2>::SIZE;
+        p.rec = c->rec + (size_t)s * c->N * c->rec_size;
         p.flags = c->dflags;
         p.wall_ci = (c->cfg.bc_cells > 0 && c->cfg.bc_wall) ? c->n[0] - c->cfg.bc_cells - 1 : -1;
         if (push) {
@@ -910,26 +783,29 @@ static int launch_pd(gx_ctx *c, bool push, cudaStream_t st) {
             GX_CHECK(c, cudaMemsetAsync(S.cnt[nxt], 0, c->N * sizeof(int), st));
             cudaEvent_t e0 = gx_ev_get(c), e1 = gx_ev_get(c);
             GX_CHECK(c, cudaEventRecord(e0, st));
-            if (p.wall_ci >= 0) k_pd<true, true><<<grid, kThreads, pd_smem_bytes(), st>>>(p);
-            else k_pd<true><<<grid, kThreads, pd_smem_bytes(), st>>>(p);
+            if constexpr (DIM == 2) {
+                if (p.wall_ci >= 0) k_pd<DIM, true, true><<<grid, kThreads, smem, st>>>(p);
+                else k_pd<DIM, true><<<grid, kThreads, smem, st>>>(p);
+            } else {
+                k_pd<DIM, true><<<grid, kThreads, smem, st>>>(p);
+            }
             GX_LAUNCHED(c);
             GX_CHECK(c, cudaEventRecord(e1, st));
             gx_ev_push(c, GX_T_PDK, e0, e1);
             c->n_pdk++;
-            // the particles that arrived in each cell: the same pipelined
-            // deposit over the back segments of the new bins, added to the
-            // records the push just wrote
-            P2 q = p;
+            // the particles that arrived in each cell: the same deposit over the
+            // back segments of the new bins, added to the records the push just wrote
+            PD q = p;
             q.arrivals = 1;
             q.in = p.out;
             q.cnt_in = p.cnt_out;
             q.mE = nullptr; q.mB = nullptr;
-            k_pd<false><<<grid, kThreads, pd_smem_bytes(), st>>>(q);
+            k_pd<DIM, false><<<grid, kThreads, smem, st>>>(q);
             GX_LAUNCHED(c);
-            if (c->cfg.bc_cells > 0) {
+            if (DIM == 2 && c->cfg.bc_cells > 0) {
                 // open boundaries: the boundary cells' particles are replaced
                 BcArgs b{};
-                b.nx = c->n[0]; b.ny = c->n[1]; b.G = c->cfg.bc_cells; b.cap = S.cap; b.N = c->N;
+                b.nx = c->n[0]; b.ny = c->n[1]; b.G = c->cfg.bc_cells; b.cap = S.cap; b.nf = S.nf; b.N = c->N;
                 b.seed = c->cfg.seed; b.step = (uint64_t)(c->npush + 1); b.species = s;
                 b.track = c->cfg.track_ids;
                 b.bc = p.bc;
@@ -950,7 +826,7 @@ static int launch_pd(gx_ctx *c, bool push, cudaStream_t st) {
             }
         } else {
             p.mE = nullptr; p.mB = nullptr; p.dB = c->nB; p.dU = c->nUref;
-            k_pd<false><<<grid, kThreads, pd_smem_bytes(), st>>>(p);
+            k_pd<DIM, false><<<grid, kThreads, smem, st>>>(p);
             GX_LAUNCHED(c);
         }
     }
@@ -966,8 +842,100 @@ static int launch_pd(gx_ctx *c, bool push, cudaStream_t st) {
     return GX_OK;
 }
 
-int gx_run_deposit(gx_ctx *c, cudaStream_t st) { return launch_pd(c, false, st); }
-int gx_run_push_deposit(gx_ctx *c, cudaStream_t st) { return launch_pd(c, true, st); }
+}  // namespace
+
+// --------------------------------------------------------------- binning
+int gx_bin_particles(gx_ctx *c, int s, int64_t n, const double *x, const double *y, const double *z,
+                     const float *vx, const float *vy, const float *vz, const float *w, const int32_t *id,
+                     cudaStream_t st) {
+    Species &S = c->sp[s];
+    int64_t *cell = nullptr;
+    int *count = nullptr;
+    float *ox = nullptr, *oy = nullptr, *oz = nullptr;
+    GX_CHECK(c, cudaMalloc(&cell, (n + 1) * sizeof(int64_t)));
+    GX_CHECK(c, cudaMalloc(&ox, (n + 1) * sizeof(float)));
+    GX_CHECK(c, cudaMalloc(&oy, (n + 1) * sizeof(float)));
+    GX_CHECK(c, cudaMalloc(&oz, (n + 1) * sizeof(float)));
+    GX_CHECK(c, cudaMalloc(&count, c->N * sizeof(int)));
+    GX_CHECK(c, cudaMemsetAsync(count, 0, c->N * sizeof(int), st));
+    if (n > 0) {
+        k_locate<<<grid_for(n), 256, 0, st>>>(n, x, y, z, c->n[0], c->n[1], c->n[2], 1.0 / c->cfg.dx[0],
+                                               1.0 / c->cfg.dx[1], 1.0 / c->cfg.dx[2], cell, ox, oy, oz, count);
+        GX_LAUNCHED(c);
+    }
+    DevFlags *dmax = nullptr;
+    GX_CHECK(c, cudaMalloc(&dmax, sizeof(DevFlags)));
+    GX_CHECK(c, cudaMemsetAsync(dmax, 0, sizeof(DevFlags), st));
+    k_max_count<<<grid_for(c->N), 256, 0, st>>>(count, c->N, 0, dmax);
+    GX_LAUNCHED(c);
+    DevFlags hf{};
+    GX_CHECK(c, cudaMemcpyAsync(&hf, dmax, sizeof(DevFlags), cudaMemcpyDeviceToHost, st));
+    GX_CHECK(c, cudaStreamSynchronize(st));
+    const double slack = c->cfg.bin_slack > 1.2 ? c->cfg.bin_slack : 1.2;
+    const int cap = round_cap(std::max(32.0, hf.maxcount * slack));
+    GX_CHECK(c, cudaFree(dmax));
+    if (cap >= 32768) { c->err = "more than 32767 particles per cell bin"; return GX_EINVAL; }
+    int rc = alloc_bins(c, s, cap);
+    if (rc) return rc;
+    GX_CHECK(c, cudaMemsetAsync(S.cnt[c->cur], 0, c->N * sizeof(int), st));
+    if (n > 0) {
+        if (c->dim == 3)
+            k_scatter<3><<<grid_for(n), 256, 0, st>>>(n, cell, ox, oy, oz, vx, vy, vz, w, id, cap, S.nf,
+                                                      S.cnt[c->cur], S.p[c->cur], c->dflags);
+        else
+            k_scatter<2><<<grid_for(n), 256, 0, st>>>(n, cell, ox, oy, oz, vx, vy, vz, w, id, cap, S.nf,
+                                                      S.cnt[c->cur], S.p[c->cur], c->dflags);
+        GX_LAUNCHED(c);
+    }
+    GX_CHECK(c, cudaStreamSynchronize(st));
+    cudaFree(cell); cudaFree(ox); cudaFree(oy); cudaFree(oz); cudaFree(count);
+    return GX_OK;
+}
+
+int gx_species_maxwellian_init(gx_ctx *c, int s, int ppc, double n0, const double u[3], double vth,
+                               cudaStream_t st) {
+    const double slack = c->cfg.bin_slack > 1.2 ? c->cfg.bin_slack : 1.2;
+    const int cap = round_cap(std::max(32.0, ppc * slack));
+    if (cap >= 32768) { c->err = "more than 32767 particles per cell bin"; return GX_EINVAL; }
+    int rc = alloc_bins(c, s, cap);
+    if (rc) return rc;
+    const double dV = c->cfg.dx[0] * c->cfg.dx[1] * c->cfg.dx[2];
+    const unsigned grid = (unsigned)std::min<int64_t>(c->N, 152 * 64);
+    const float wgt = (float)(n0 * dV / ppc);
+    Species &S = c->sp[s];
+    if (c->dim == 3)
+        k_maxwellian<3><<<grid, 128, 0, st>>>(c->n[1], c->n[2], c->N, cap, S.nf, ppc, c->cfg.seed, s, (float)u[0],
+                                              (float)u[1], (float)u[2], (float)vth, wgt, S.p[c->cur], S.cnt[c->cur]);
+    else
+        k_maxwellian<2><<<grid, 128, 0, st>>>(c->n[1], 1, c->N, cap, S.nf, ppc, c->cfg.seed, s, (float)u[0],
+                                              (float)u[1], (float)u[2], (float)vth, wgt, S.p[c->cur], S.cnt[c->cur]);
+    GX_LAUNCHED(c);
+    GX_CHECK(c, cudaStreamSynchronize(st));
+    return GX_OK;
+}
+
+int gx_regrow_bins(gx_ctx *c, int s, int newcap, cudaStream_t st) {
+    newcap = round_cap(newcap);
+    if (newcap >= 32768) { c->err = "more than 32767 particles per cell bin"; return GX_EOVERFLOW; }
+    Species &S = c->sp[s];
+    Species old = S;
+    int rc = alloc_bins(c, s, newcap);
+    if (rc) return rc;
+    k_rebin_copy<<<(unsigned)c->N, 128, 0, st>>>(c->N, old.cap, newcap, S.nf, old.cnt[c->cur], S.cnt[c->cur],
+                                                  old.p[c->cur], S.p[c->cur]);
+    GX_LAUNCHED(c);
+    GX_CHECK(c, cudaStreamSynchronize(st));
+    free_bins(old);
+    return GX_OK;
+}
+
+// ------------------------------------------------------------ hot path
+int gx_run_deposit(gx_ctx *c, cudaStream_t st) {
+    return c->dim == 3 ? launch_pd<3>(c, false, st) : launch_pd<2>(c, false, st);
+}
+int gx_run_push_deposit(gx_ctx *c, cudaStream_t st) {
+    return c->dim == 3 ? launch_pd<3>(c, true, st) : launch_pd<2>(c, true, st);
+}
 
 int gx_particles_out(gx_ctx *c, int s, double *x, double *y, double *z, float *vx, float *vy, float *vz, float *w,
                      int32_t *id, cudaStream_t st) {
@@ -982,8 +950,14 @@ int gx_particles_out(gx_ctx *c, int s, double *x, double *y, double *z, float *v
     cub::DeviceScan::ExclusiveSum(nullptr, tmpb, counts, offs, (int)c->N, st);
     GX_CHECK(c, cudaMalloc(&tmp, tmpb + 16));
     GX_CHECK(c, cub::DeviceScan::ExclusiveSum(tmp, tmpb, counts, offs, (int)c->N, st));
-    k_gather_out<<<(unsigned)c->N, 128, 0, st>>>(c->N, S.cap, S.cnt[c->cur], offs, S.p[c->cur], c->n[0], c->n[1],
-                                                  c->cfg.dx[0], c->cfg.dx[1], x, y, z, vx, vy, vz, w, id);
+    if (c->dim == 3)
+        k_gather_out<3><<<(unsigned)c->N, 128, 0, st>>>(c->N, S.cap, S.nf, S.cnt[c->cur], offs, S.p[c->cur], c->n[0],
+                                                        c->n[1], c->cfg.dx[0], c->cfg.dx[1], c->cfg.dx[2], x, y, z, vx,
+                                                        vy, vz, w, id);
+    else
+        k_gather_out<2><<<(unsigned)c->N, 128, 0, st>>>(c->N, S.cap, S.nf, S.cnt[c->cur], offs, S.p[c->cur], c->n[0],
+                                                        c->n[1], c->cfg.dx[0], c->cfg.dx[1], c->cfg.dx[2], x, y, z, vx,
+                                                        vy, vz, w, id);
     GX_LAUNCHED(c);
     GX_CHECK(c, cudaStreamSynchronize(st));
     cudaFree(offs); cudaFree(counts); cudaFree(tmp);
