@@ -205,7 +205,7 @@ void gx_destroy(gx_ctx *c) {
     gx_free_bins(c);
     double **dp[] = {&c->E, &c->B, &c->Eth, &c->Enew, &c->Bnew, &c->rho, &c->rho_m, &c->P, &c->u, &c->J,
                      &c->M, &c->tmp3, &c->uref64, &c->kappa, &c->rhs, &c->EM, &c->jdiag, &c->V, &c->Z,
-                     &c->w, &c->r, &c->dred, &c->hcol, &c->dBlf};
+                     &c->w, &c->r, &c->dred, &c->hcol, &c->dBlf, &c->A3};
     for (auto p : dp)
         if (*p) cudaFree(*p);
     if (c->jdiag32) cudaFree(c->jdiag32);
@@ -245,7 +245,9 @@ int gx_create(const gx_config *cfg, gx_ctx **out) {
     if ((int64_t)cfg->n[0] * cfg->n[1] > (int64_t)1 << 31 ||
         (int64_t)cfg->n[0] * cfg->n[1] * cfg->n[2] > (int64_t)1 << 31)
         return fail(GX_EINVAL, "at most 2^31 cells");
-    if (cfg->n[2] != 1) return fail(GX_ENOTIMPL, "this build implements the 2D (x-y) path: n[2] must be 1");
+    const bool three = cfg->n[2] > 1;
+    if (three && (cfg->bc_cells > 0 || cfg->bc_wall || cfg->divb_clean || cfg->precond == GX_PRECOND_NET))
+        return fail(GX_ENOTIMPL, "a 3D grid runs periodic, without divb_clean and without the learned preconditioner");
     if (!(cfg->c > 0) || !(cfg->dt > 0)) return fail(GX_EINVAL, "c and dt must be > 0");
     if (!(cfg->theta >= 0.5 && cfg->theta <= 1.0)) return fail(GX_EINVAL, "theta must be in [0.5, 1]");
     if (cfg->gmres_restart < 1 || cfg->gmres_restart > gx_gm_max_restart())
@@ -267,10 +269,10 @@ int gx_create(const gx_config *cfg, gx_ctx **out) {
         return fail(GX_EINVAL, "c, dt, gmres_tol and bin_slack must be finite");
     for (int d = 0; d < 3; ++d)
         if (!(cfg->dx[d] < 1e300)) return fail(GX_EINVAL, "dx[d] must be finite");
-    c->dim = 2;
+    c->dim = three ? 3 : 2;
     c->N = (int64_t)c->n[0] * c->n[1] * c->n[2];
     c->dV = cfg->dx[0] * cfg->dx[1] * cfg->dx[2];
-    c->noff = 9;
+    c->noff = three ? 27 : 9;
     const int64_t N = c->N;
     const int m = cfg->gmres_restart;
     int rc = GX_OK;
@@ -278,13 +280,14 @@ int gx_create(const gx_config *cfg, gx_ctx **out) {
                        &c->rhs, &c->EM, &c->w, &c->r};
     for (auto p : vec3)
         if ((rc = dalloc(c, p, 3 * N))) return fail(rc, nullptr);
-    if ((rc = dalloc(c, &c->rho, N)) || (rc = dalloc(c, &c->rho_m, N)) || (rc = dalloc(c, &c->M, 81 * N)) ||
-        (rc = dalloc(c, &c->kappa, 6 * N)) || (rc = dalloc(c, &c->jdiag, 9 * N)) || (rc = dalloc(c, &c->jdiag32, 9 * N)) ||
+    const int nax = three ? 3 : 2;
+    if ((rc = dalloc(c, &c->rho, N)) || (rc = dalloc(c, &c->rho_m, N)) || (rc = dalloc(c, &c->M, (size_t)c->noff * 9 * N)) ||
+        (rc = dalloc(c, &c->kappa, (size_t)nax * 3 * N)) || (three && (rc = dalloc(c, &c->A3, (size_t)243 * N))) || (rc = dalloc(c, &c->jdiag, 9 * N)) || (rc = dalloc(c, &c->jdiag32, 9 * N)) ||
         (rc = dalloc(c, &c->V, (size_t)(m + 1) * 3 * N)) || (rc = dalloc(c, &c->dred, 64)) ||
         (rc = dalloc(c, &c->hcol, 2 * (m + 2))) || (rc = dalloc(c, &c->dflags, 1)))
         return fail(rc, nullptr);
     if (cfg->precond != GX_PRECOND_NONE && (rc = dalloc(c, &c->Z, (size_t)m * 3 * N))) return fail(rc, nullptr);
-    if (cfg->lf_on && (rc = dalloc(c, &c->dBlf, 12 * N))) return fail(rc, nullptr);   // D, B~, face fluxes
+    if (cfg->lf_on && (rc = dalloc(c, &c->dBlf, (size_t)(6 + 3 * nax) * N))) return fail(rc, nullptr);   // D, B~, face fluxes
     if (cfg->divb_clean) {
         if ((rc = dalloc(c, &c->phi, N))) return fail(rc, nullptr);
         if (cudaMemset(c->phi, 0, N * sizeof(double)) != cudaSuccess) return fail(GX_ECUDA, "cudaMemset failed");
@@ -308,9 +311,9 @@ int gx_create(const gx_config *cfg, gx_ctx **out) {
     double *zero3[] = {c->E, c->B, c->Eth, c->Enew, c->Bnew, c->u, c->J, c->uref64};
     for (auto p : zero3)
         if (cudaMemset(p, 0, 3 * N * sizeof(double)) != cudaSuccess) return fail(GX_ECUDA, "cudaMemset failed");
-    if (cudaMemset(c->M, 0, 81 * N * sizeof(double)) != cudaSuccess ||
+    if (cudaMemset(c->M, 0, (size_t)c->noff * 9 * N * sizeof(double)) != cudaSuccess ||
         cudaMemset(c->rho, 0, N * sizeof(double)) != cudaSuccess ||
-        cudaMemset(c->kappa, 0, 6 * N * sizeof(double)) != cudaSuccess ||
+        cudaMemset(c->kappa, 0, (size_t)nax * 3 * N * sizeof(double)) != cudaSuccess ||
         cudaMemset(c->dflags, 0, sizeof(DevFlags)) != cudaSuccess ||
         cudaMemset(c->nUref, 0, N * sizeof(float4)) != cudaSuccess ||
         cudaDeviceSynchronize() != cudaSuccess)
@@ -535,12 +538,13 @@ int gx_get_moments(gx_ctx *c, double *rho, double *J, double *M, double *u, int 
     if (J) TRY(copy_out(c, J, c->J, 3 * N * sizeof(double), ptr_is_device, 0));
     if (u) TRY(copy_out(c, u, c->u, 3 * N * sizeof(double), ptr_is_device, 0));
     if (M) {
-        // device rows are [81][N] (entry o*9 + e over the 9 in-plane offsets);
-        // expand to the node-major 27-offset layout (oz = 0 -> offset + 9)
-        std::vector<double> h(81 * N), full(243 * N, 0.0);
-        GX_CHECK(c, cudaMemcpy(h.data(), c->M, 81 * N * sizeof(double), cudaMemcpyDeviceToHost));
+        // device rows are [noff * 9][N] (entry o*9 + e); node-major 27-offset layout
+        // for the caller (in 2D the 9 in-plane offsets are oz = 0: offset + 9)
+        const int rows = c->noff * 9, base = c->dim == 3 ? 0 : 81;
+        std::vector<double> h((size_t)rows * N), full((size_t)243 * N, 0.0);
+        GX_CHECK(c, cudaMemcpy(h.data(), c->M, (size_t)rows * N * sizeof(double), cudaMemcpyDeviceToHost));
         for (int64_t q = 0; q < N; ++q)
-            for (int k = 0; k < 81; ++k) full[(size_t)q * 243 + 81 + k] = h[(size_t)k * N + q];
+            for (int k = 0; k < rows; ++k) full[(size_t)q * 243 + base + k] = h[(size_t)k * N + q];
         if (ptr_is_device) GX_CHECK(c, cudaMemcpy(M, full.data(), 243 * N * sizeof(double), cudaMemcpyHostToDevice));
         else std::memcpy(M, full.data(), 243 * N * sizeof(double));
     }

@@ -182,7 +182,7 @@ __device__ void net_apply(const CoArgs &a, cg::grid_group &grid, int j, unsigned
 
 // NET: the learned preconditioner is applied in the kernel (the plain and
 // Jacobi instantiation is smaller and fits two CTAs per SM)
-template <bool NET>
+template <bool NET, int DIM = 2>
 __global__ void __launch_bounds__(NET ? kBNet : kB, NET ? 1 : 2) k_fgmres(const __grid_constant__ CoArgs a) {
     extern __shared__ __align__(128) unsigned char gsm_raw[];
     unsigned char *gsm = gsm_raw + ((128 - (gxt::smem_addr(gsm_raw) & 127)) & 127);
@@ -241,7 +241,7 @@ __global__ void __launch_bounds__(NET ? kBNet : kB, NET ? 1 : 2) k_fgmres(const 
             double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
             NODE_LOOP(q) {
                 double ax[3];
-                gx_apply_A_node<true>(a.op, a.x, q, ax);
+                gx_apply_node<DIM, true>(a.op, a.x, q, ax);
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
                     const double rv = a.b[c * N + q] - ax[c];
@@ -293,7 +293,7 @@ __global__ void __launch_bounds__(NET ? kBNet : kB, NET ? 1 : 2) k_fgmres(const 
             NODE_LOOP(q) {
                 double wq[3];
                 if (i0 == 0) {
-                    gx_apply_A_node<true>(a.op, zj, q, wq);
+                    gx_apply_node<DIM, true>(a.op, zj, q, wq);
 #pragma unroll
                     for (int c = 0; c < 3; ++c) a.w[c * N + q] = wq[c];
                 } else {
@@ -491,6 +491,7 @@ int gx_fgmres(gx_ctx *c, cudaStream_t st) {
     const int64_t n = 3 * c->N;
     const int pc = c->cfg.precond;
     int rc;
+    if (c->dim == 3 && (rc = gx3_build_op(c, st))) return rc;   // the operator's blocks for this solve
     // the learned preconditioner reads only the FP32 inverse; pair collection and the
     // Jacobi preconditioner need the FP64 one
     if (pc == GX_PRECOND_JACOBI || (pc == GX_PRECOND_NET && gx_net_collecting(c))) {
@@ -502,9 +503,10 @@ int gx_fgmres(gx_ctx *c, cudaStream_t st) {
     }
     const bool use_net = pc == GX_PRECOND_NET;
     const size_t smem = use_net ? (size_t)kNetSmemBytes : 0;
-    static int grids[2] = {0, 0};
-    int &grid = grids[use_net ? 1 : 0];
-    const void *kfn = use_net ? (const void *)k_fgmres<true> : (const void *)k_fgmres<false>;
+    static int grids[3] = {0, 0, 0};
+    int &grid = grids[c->dim == 3 ? 2 : (use_net ? 1 : 0)];
+    const void *kfn = c->dim == 3 ? (const void *)k_fgmres<false, 3>
+                                  : (use_net ? (const void *)k_fgmres<true> : (const void *)k_fgmres<false>);
     if (!grid) {
         int dev = 0, nsm = 0, per = 0;
         GX_CHECK(c, cudaGetDevice(&dev));

@@ -666,6 +666,10 @@ OpArgs opargs(const gx_ctx *c) {
     a.lfy = c->cfg.theta * c->cfg.dt / c->cfg.dx[1];
     a.M = c->nspecies > 0 ? c->M : nullptr;
     a.kappa = (c->cfg.lf_on && c->cfg.nsmooth_e == 0) ? c->kappa : nullptr;   // the E filter replaces LF on E
+    if (c->dim == 3) {
+        a.g3 = G3{c->n[0], c->n[1], c->n[2], c->cfg.dx[0], c->cfg.dx[1], c->cfg.dx[2]};
+        a.A3 = c->A3;
+    }
     return a;
 }
 
@@ -695,6 +699,7 @@ int filter_passes(gx_ctx *c, double *f, int passes, bool alternate, cudaStream_t
 OpArgs gx_opargs(const gx_ctx *c) { return opargs(c); }
 
 int gx_node_fields(gx_ctx *c, const double *Eth, const double *Bcur, float4 *outE, float4 *outB, cudaStream_t st) {
+    if (c->dim == 3) return gx3_node_fields(c, Eth, Bcur, outE, outB, st);
     k_node_fields<<<blocks_for(c->N), kB, 0, st>>>(geom(c), Eth, Bcur, outE, outB);
     GX_LAUNCHED(c);
     return GX_OK;
@@ -703,6 +708,7 @@ int gx_node_fields(gx_ctx *c, const double *Eth, const double *Bcur, float4 *out
 // records -> rho, u (smoothed), J (comoving or standard, smoothed), M; then
 // the reference velocity of the next deposit becomes this u.
 int gx_assemble_moments(gx_ctx *c, cudaStream_t st) {
+    if (c->dim == 3) return gx3_assemble_moments(c, st);
     const G2 g = geom(c);
     const SpecK sk = speck(c);
     const Recs R{c->rec, c->N};
@@ -723,6 +729,7 @@ int gx_assemble_moments(gx_ctx *c, cudaStream_t st) {
 }
 
 int gx_build_rhs(gx_ctx *c, cudaStream_t st) {
+    if (c->dim == 3) return gx3_build_rhs(c, st);
     const G2 g = geom(c);
     const bool cm = c->cfg.comoving && c->nspecies > 0;
     if (cm) {
@@ -750,6 +757,7 @@ int gx_build_rhs(gx_ctx *c, cudaStream_t st) {
 }
 
 int gx_build_kappa(gx_ctx *c, cudaStream_t st) {
+    if (c->dim == 3) return gx3_build_kappa(c, st);
     if (!c->cfg.lf_on || c->cfg.nsmooth_e > 0) return GX_OK;
     k_kappa<<<blocks_for(c->N), kB, 0, st>>>(geom(c), c->E, c->u, c->cfg.lf_beta, c->cfg.lf_speed_c, c->cfg.c,
                                               c->kappa);
@@ -758,6 +766,7 @@ int gx_build_kappa(gx_ctx *c, cudaStream_t st) {
 }
 
 int gx_apply_A(gx_ctx *c, const double *x, double *y, cudaStream_t st) {
+    if (c->dim == 3) return gx3_apply_A(c, x, y, st);
     k_matvec<<<blocks_for(c->N), kB, 0, st>>>(opargs(c), x, y, nullptr, 0, nullptr);
     GX_LAUNCHED(c);
     return GX_OK;
@@ -771,12 +780,14 @@ int gx_apply_A_j(gx_ctx *c, const double *base, int64_t stride, const int *jptr,
 }
 
 int gx_build_jacobi(gx_ctx *c, cudaStream_t st) {
+    if (c->dim == 3) return gx3_build_jacobi(c, true, st);
     k_jacobi<<<blocks_for(c->N), kB, 0, st>>>(opargs(c), c->jdiag, c->jdiag32);
     GX_LAUNCHED(c);
     return GX_OK;
 }
 
 int gx_build_jacobi32(gx_ctx *c, cudaStream_t st) {
+    if (c->dim == 3) return gx3_build_jacobi(c, false, st);
     k_jacobi<<<blocks_for(c->N), kB, 0, st>>>(opargs(c), nullptr, c->jdiag32);
     GX_LAUNCHED(c);
     return GX_OK;
@@ -797,6 +808,7 @@ int gx_initial_guess(gx_ctx *c, cudaStream_t st) {
 }
 
 int gx_advance(gx_ctx *c, cudaStream_t st) {
+    if (c->dim == 3) return gx3_advance(c, st);
     // the LF increment D was computed from B^n and u when the right-hand side was built
     k_advance<<<blocks_for(c->N), kB, 0, st>>>(geom(c), c->E, c->B, c->Eth, c->cfg.c, c->cfg.dt, c->cfg.theta,
                                                c->cfg.lf_on ? c->dBlf : nullptr, c->phi, c->Enew, c->Bnew);
@@ -824,8 +836,13 @@ int gx_copy_uref(gx_ctx *c, int zero, cudaStream_t st) {
 int gx_diag_run(gx_ctx *c, gx_diag *out, cudaStream_t st) {
     double *acc = c->dred;
     GX_CHECK(c, cudaMemsetAsync(acc, 0, 16 * sizeof(double), st));
-    k_diag_grid<<<blocks_for(c->N), kB, 0, st>>>(geom(c), c->E, c->B, c->moments_valid ? c->rho : nullptr, acc);
-    GX_LAUNCHED(c);
+    if (c->dim == 3) {
+        int rc = gx3_diag_grid(c, acc, st);
+        if (rc) return rc;
+    } else {
+        k_diag_grid<<<blocks_for(c->N), kB, 0, st>>>(geom(c), c->E, c->B, c->moments_valid ? c->rho : nullptr, acc);
+        GX_LAUNCHED(c);
+    }
     for (int s = 0; s < c->nspecies; ++s) {
         const Species &S = c->sp[s];
         k_diag_particles<<<(unsigned)std::min<int64_t>(c->N, 152 * 8), 128, 0, st>>>(

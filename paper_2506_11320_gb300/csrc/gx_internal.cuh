@@ -127,7 +127,8 @@ struct gx_ctx {
     double *rho = nullptr, *rho_m = nullptr;    // [N]
     double *P = nullptr, *u = nullptr;          // [3][N]
     double *J = nullptr;                        // [3][N]
-    double *M = nullptr;                        // [N][noff][9]
+    double *M = nullptr;                        // [noff * 9][N] (offset o, alpha entry e at row o * 9 + e)
+    double *A3 = nullptr;                       // 3D: the implicit operator as 27 blocks per node [243][N]
     double *tmp3 = nullptr;                     // [3][N] scratch for filters
     double *uref64 = nullptr;                   // [3][N] FP64 copy of nUref values
     int moments_valid = 0;
@@ -223,6 +224,18 @@ int gx_apply_jacobi(gx_ctx *c, const double *x, double *y, cudaStream_t st);
 int gx_advance(gx_ctx *c, cudaStream_t st);                  // Enew, Bnew from Eth
 int gx_initial_guess(gx_ctx *c, cudaStream_t st);            // Eth <- starting point of the solve
 int gx_diag_run(gx_ctx *c, gx_diag *out, cudaStream_t st);
+
+// 3D grid (gx_grid3.cu): the same steps on a grid with a resolved z axis
+int gx3_node_fields(gx_ctx *c, const double *Eth, const double *Bcur, float4 *outE, float4 *outB, cudaStream_t st);
+int gx3_assemble_moments(gx_ctx *c, cudaStream_t st);
+int gx3_build_rhs(gx_ctx *c, cudaStream_t st);
+int gx3_build_kappa(gx_ctx *c, cudaStream_t st);
+int gx3_build_op(gx_ctx *c, cudaStream_t st);            // assemble the operator blocks A3 for this solve
+int gx3_apply_A(gx_ctx *c, const double *x, double *y, cudaStream_t st);
+int gx3_build_jacobi(gx_ctx *c, bool fp64, cudaStream_t st);
+int gx3_advance(gx_ctx *c, cudaStream_t st);
+int gx3_filter(gx_ctx *c, double *f, int passes, bool alternate, cudaStream_t st);
+int gx3_diag_grid(gx_ctx *c, double *acc, cudaStream_t st);
 
 // solver (gx_gmres.cu)
 int gx_fgmres(gx_ctx *c, cudaStream_t st);

@@ -42,8 +42,26 @@ struct G2 {
     }
 };
 
+// 3D geometry (all axes periodic; an axis of one cell collapses through the wrap)
+struct G3 {
+    int nx, ny, nz;
+    double dx, dy, dz;
+    __device__ __forceinline__ int64_t id(int i, int j, int k) const {
+        return (int64_t)gx_wr(i, nx) + (int64_t)nx * ((int64_t)gx_wr(j, ny) + (int64_t)ny * gx_wr(k, nz));
+    }
+    __device__ __forceinline__ int64_t N() const { return (int64_t)nx * ny * nz; }
+    __device__ __forceinline__ void ijk(int64_t q, int &i, int &j, int &k) const {
+        i = (int)(q % nx);
+        const int64_t r = q / nx;
+        j = (int)(r % ny);
+        k = (int)(r / ny);
+    }
+};
+
 struct OpArgs {
     G2 g;
+    G3 g3;                 // 3D: the geometry, and
+    const double *A3;      // the operator assembled as 27 node blocks [27 * 9][N] (or null in 2D)
     double ct2;            // (c theta dt)^2
     double mfac;           // 4 pi theta dt / dV
     double lfx, lfy;       // theta dt / dx, theta dt / dy
@@ -118,4 +136,36 @@ __device__ __forceinline__ void gx_apply_A_node(const OpArgs &a, const double *_
 #pragma unroll
         for (int c = 0; c < 3; ++c) out[c] = v[c][1][1];
     }
+}
+
+// 3D: (A x) at node q from the assembled blocks, (A x)_r = sum_o sum_c
+// A3[(o 9 + 3 r + c) N + q] x_c(q + o), o = (ox+1) + 3 (oy+1) + 9 (oz+1).
+template <bool CG = false>
+__device__ __forceinline__ void gx_apply_A3_node(const OpArgs &a, const double *__restrict__ x, int64_t q,
+                                                 double out[3]) {
+    const G3 &g = a.g3;
+    const int64_t N = g.N();
+    int i, j, k;
+    g.ijk(q, i, j, k);
+    out[0] = out[1] = out[2] = 0.0;
+#pragma unroll 3
+    for (int o = 0; o < 27; ++o) {
+        const int64_t nb = g.id(i + o % 3 - 1, j + (o / 3) % 3 - 1, k + o / 9 - 1);
+        double xv[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) xv[c] = CG ? __ldcg(x + c * N + nb) : x[c * N + nb];
+        const double *blk = a.A3 + (size_t)o * 9 * N + q;
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) out[r] = fma(blk[(size_t)(3 * r + c) * N], xv[c], out[r]);
+    }
+}
+
+// the operator of a DIM-dimensional grid at node q
+template <int DIM, bool CG = false>
+__device__ __forceinline__ void gx_apply_node(const OpArgs &a, const double *__restrict__ x, int64_t q,
+                                              double out[3]) {
+    if constexpr (DIM == 3) gx_apply_A3_node<CG>(a, x, q, out);
+    else gx_apply_A_node<CG>(a, x, q, out);
 }
