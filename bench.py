@@ -38,6 +38,13 @@ import workloads  # noqa: E402
 METRIC = "particle-steps/s (push+deposit) & GMRES time/step, learned vs plain"
 UNIT = "particle-steps/s"
 ALG_BYTES_2D = 44          # per particle-step: read ox,oy,vx,vy,vz,w (24 B) + write ox,oy,vx,vy,vz (20 B)
+ALG_BYTES_3D = 52          # per particle-step: read ox,oy,oz,vx,vy,vz,w (28 B) + write ox,oy,oz,vx,vy,vz (24 B)
+# FP32 flops of the 3D push kernel per particle: mover 172 (corner weights 15, E and B
+# gathered from 8 corners 96, rotation 55, position 6), deposit factors 214 (weights 15,
+# B and u_ref gathered 96, alpha 25, alpha (v - u_ref) 21, pair weights 57), and the
+# sums of 27 pair classes x 16 columns, 864
+FLOP_3D = 1250
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12    # SMs x FP32 lanes x FMA x max SM clock: 80.5 TFLOP/s
 
 
 def max_over_ranks(values, dist, device):
@@ -68,6 +75,67 @@ def make_workload(name):
     if name == "shock_wall":
         return workloads.shock_wall(), "shock by reflection: inflow onto a reflecting wall, 1024x8 cells, 256 ppc"
     raise SystemExit(f"unknown workload {name}")
+
+
+def drift3d_config(n=128, ppc=64):
+    """The 3D periodic drifting plasma: n^3 cells of 0.1 d_i, electrons and ions
+    (m_i/m_e 25) drawn on the device as drifting Maxwellians (u = 0.3 c along x,
+    vth_e = 0.05 c, vth_i = 0.01 c, ppc per cell and species), B = 0.1 along z,
+    E = -u x B / c, theta = 1/2, dt = 0.1 / omega_pe, comoving current and
+    limited LF on, FGMRES to 1e-8."""
+    return dict(n=(n, n, n), dx=(0.1, 0.1, 0.1), ppc=ppc, u=(0.3, 0.0, 0.0), B=(0.0, 0.0, 0.1),
+                vth_e=0.05, vth_i=0.01, mass_ratio=25.0, dt=0.02)
+
+
+def drift3d_context(gx, n=128, ppc=64, seed=2024):
+    c3 = drift3d_config(n, ppc)
+    cfg = gx.make_config(c3["n"], c3["dx"], dt=c3["dt"], comoving=1, lf_on=1, gmres_tol=1e-8, seed=seed)
+    ctx = gx.Context(cfg)
+    n0 = workloads.N0
+    ctx.species_maxwellian(-1.0, 1.0 / c3["mass_ratio"], ppc, n0, c3["u"], c3["vth_e"])
+    ctx.species_maxwellian(1.0, 1.0, ppc, n0, c3["u"], c3["vth_i"])
+    u32 = np.asarray(c3["u"], np.float32).astype(np.float64)
+    Em = -np.cross(u32, np.asarray(c3["B"], float))
+    shape = (3, n, n, n)
+    E = np.empty(shape)
+    B = np.empty(shape)
+    for d in range(3):
+        E[d] = Em[d]
+        B[d] = c3["B"][d]
+    ctx.fields_set(E, B)
+    return ctx, 2 * ppc * n ** 3
+
+
+def run_drift3d(gx, ppc, warmup, steps, barrier, dist, world, n=128):
+    """Push+deposit throughput of the 3D drifting plasma at `ppc` particles per
+    cell and species, with the push kernel's HBM and FP32 fractions."""
+    peak, peak_kind = load_peaks()
+    ctx, npart = drift3d_context(gx, n, ppc)
+    for _ in range(warmup):
+        ctx.step(1, allow_noconv=True)
+    ctx.timers(reset=True)
+    ctx.kernel_timer(reset=True)
+    iters = []
+    barrier()
+    for _ in range(steps):
+        iters.append(ctx.step(1, allow_noconv=True).iters)
+    barrier()
+    tm = ctx.timers(reset=True)
+    kt = ctx.kernel_timer(reset=True)
+    ctx.close()
+    pd_ms = (tm["push_ms"] + tm["moments_ms"]) / steps
+    kms = kt["pd_kernel_ms"] / max(1, kt["pd_launches"])
+    pd_ms, kms = max_over_ranks([pd_ms, kms], dist, "cuda")
+    per_launch = npart / 2
+    hbm = ALG_BYTES_3D * per_launch / (kms / 1000.0) / 1e9
+    alu = FLOP_3D * per_launch / (kms / 1000.0) / 1e12
+    return {"ppc": ppc, "particles": npart, "value": whole_job_rate(world, npart, pd_ms), "unit": UNIT,
+            "push_deposit_ms_per_step": pd_ms, "push_kernel_ms_per_launch": kms,
+            "solve_ms_per_step": tm["solve_ms"] / steps, "gmres_iters_per_step": statistics.mean(iters),
+            "hbm": {"achieved": hbm, "peak": peak, "unit": "GB/s", "frac": hbm / peak, "peak_kind": peak_kind,
+                    "alg_bytes_per_particle": ALG_BYTES_3D},
+            "alu": {"achieved": alu, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": alu / FP32_PEAK_TFLOPS,
+                    "flop_per_particle": FLOP_3D}}
 
 
 def load_peaks():
@@ -267,6 +335,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-precond", action="store_true")
     ap.add_argument("--no-shock", action="store_true")
+    ap.add_argument("--no-3d", action="store_true", help="skip the 3D drifting-plasma sweep")
+    ap.add_argument("--sweep3d", default="8,16,32,64,128,256",
+                    help="particles per cell and species of the 3D 128^3 sweep")
     ap.add_argument("--precond-workload", default="harris_1024x512",
                     help="plasma of the learned-vs-plain GMRES comparison: harris_1024x512 (the learned-"
                          "preconditioner configuration: Harris reconnection, 1024x512 cells, 100 ppc/species) "
@@ -363,6 +434,16 @@ def main():
         shock = run_shock(gx, args.warmup, args.steps, barrier, dist, world)
         shock_wall = run_shock(gx, args.warmup, args.steps, barrier, dist, world, wall=True)
 
+    # ------------------------------------------------------- 3D drifting plasma, 128^3, ppc sweep
+    sweep3d = None
+    if not args.no_3d:
+        sweep3d = {"workload": "3D periodic drifting Maxwellian plasma, 128^3 cells of 0.1 d_i, u = 0.3 c along x, "
+                               "vth_e 0.05 c, vth_i 0.01 c, m_i/m_e 25, B = 0.1 along z, comoving current and "
+                               "limited LF on, particles drawn on the device",
+                   "points": []}
+        for ppc in [int(v) for v in args.sweep3d.split(",") if v]:
+            sweep3d["points"].append(run_drift3d(gx, ppc, 1, 3, barrier, dist, world))
+
     # ------------------------------------------------------- end to end (host buffers)
     e2e = None
     if not args.no_e2e:
@@ -394,7 +475,7 @@ def main():
             "gmres_ms_per_step": solve_ms, "gmres_iters_per_step": statistics.mean(iters),
             "wall_ms_per_step": 1000 * wall / args.steps,
             "gmres_learned_vs_plain": solve_cmp,
-            "shock": shock, "shock_wall": shock_wall,
+            "shock": shock, "shock_wall": shock_wall, "drift3d_128": sweep3d,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "gpu_launches": int(tm["launches"]),
         }

@@ -35,7 +35,7 @@ __global__ void k_node_fields(G2 g, const double *__restrict__ E, const double *
                               float4 *outB) {
     const int64_t N = g.N();
     GRID_LOOP(q, N) {
-        const int i = (int)(q % g.nx), j = (int)(q / g.nx);
+        const int j = (int)((unsigned)q / (unsigned)g.nx), i = (int)q - j * g.nx;
         if (outE) outE[q] = make_float4((float)E[q], (float)E[N + q], (float)E[2 * N + q], 0.f);
         if (outB) {
             const int64_t c0 = g.id(i - 1, j - 1), c1 = g.id(i, j - 1), c2 = g.id(i - 1, j), c3 = q;
@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(kB, kNodeCtas) k_assemble_bulk(G2 g, SpecK sk,
                                 double *u) {
     const int64_t N = g.N();
     GRID_LOOP(q, N) {
-        const int i = (int)(q % g.nx), j = (int)(q / g.nx);
+        const int j = (int)((unsigned)q / (unsigned)g.nx), i = (int)q - j * g.nx;
         int64_t cell[4];
 #pragma unroll
         for (int a = 0; a < 4; ++a) cell[a] = g.id(i - (a & 1), j - (a >> 1));   // corner a of that cell is this node
@@ -184,7 +184,7 @@ __global__ void __launch_bounds__(kB, kNodeCtas) k_assemble_main(G2 g, SpecK sk,
                                 const double *__restrict__ uref, double *J, double *M) {
     const int64_t N = g.N();
     GRID_LOOP(q, N) {
-        const int i = (int)(q % g.nx), j = (int)(q / g.nx);
+        const int j = (int)((unsigned)q / (unsigned)g.nx), i = (int)q - j * g.nx;
         double jc[3] = {0, 0, 0};
         float du[3][3][3];          // (u - u_ref) at the 3x3 nodes around q: [dy+1][dx+1][k]
         if (comoving) {
@@ -309,7 +309,7 @@ __global__ void k_matvec(OpArgs a, const double *__restrict__ x, double *__restr
 __global__ void k_divb_phi(G2 g, const double *__restrict__ B, double dtch2, double decay, double *phi) {
     const int64_t N = g.N();
     GRID_LOOP(q, N) {
-        const int i = (int)(q % g.nx), j = (int)(q / g.nx);
+        const int j = (int)((unsigned)q / (unsigned)g.nx), i = (int)q - j * g.nx;
         double d = 0.0;
         if (g.nx > 1) d += (B[g.id(i + 1, j)] - B[g.id(i - 1, j)]) * g.hx;
         if (g.ny > 1) d += (B[N + g.id(i, j + 1)] - B[N + g.id(i, j - 1)]) * g.hy;
@@ -333,7 +333,7 @@ __global__ void k_jacobi(OpArgs a, double *jd, float *jd32) {
             for (int e = 0; e < 9; ++e) A[e] += a.mfac * a.M[(size_t)(4 * 9 + e) * N + q];   // centre offset
         }
         if (a.kappa) {
-            const int i = (int)(q % g.nx), j = (int)(q / g.nx);
+            const int j = (int)((unsigned)q / (unsigned)g.nx), i = (int)q - j * g.nx;
             const int64_t xm = g.id(i - 1, j), ym = g.id(i, j - 1);
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
@@ -343,7 +343,7 @@ __global__ void k_jacobi(OpArgs a, double *jd, float *jd32) {
                 A[4 * c] += d;
             }
         }
-        if (g.bnode((int)(q % g.nx))) {   // Dirichlet row of an open boundary: the identity
+        if (g.bnode((int)q - (int)((unsigned)q / (unsigned)g.nx) * g.nx)) {   // Dirichlet row of an open boundary: the identity
 #pragma unroll
             for (int e = 0; e < 9; ++e) A[e] = (e % 4 == 0) ? 1.0 : 0.0;
         }
@@ -390,7 +390,7 @@ __global__ void k_apply_jacobi(int64_t N, const double *__restrict__ jd, const d
 __global__ void k_motional(G2 g, const double *__restrict__ u, const double *__restrict__ B, double c, double *EM) {
     const int64_t N = g.N();
     GRID_LOOP(q, N) {
-        const int i = (int)(q % g.nx), j = (int)(q / g.nx);
+        const int j = (int)((unsigned)q / (unsigned)g.nx), i = (int)q - j * g.nx;
         const int64_t c0 = g.id(i - 1, j - 1), c1 = g.id(i, j - 1), c2 = g.id(i - 1, j), c3 = q;
         double b[3];
 #pragma unroll
@@ -409,7 +409,7 @@ __global__ void __launch_bounds__(kB, kNodeCtas) k_rhs(G2 g, const double *__res
                       double *b) {
     const int64_t N = g.N();
     GRID_LOOP(q, N) {
-        const int i = (int)(q % g.nx), j = (int)(q / g.nx);
+        const int j = (int)((unsigned)q / (unsigned)g.nx), i = (int)q - j * g.nx;
         if (g.bnode(i)) {   // Dirichlet row of an open boundary: b = E^n
 #pragma unroll
             for (int c = 0; c < 3; ++c) b[c * N + q] = E[c * N + q];
@@ -465,7 +465,7 @@ __global__ void k_kappa(G2 g, const double *__restrict__ E, const double *__rest
                         double c, double *kappa) {
     const int64_t N = g.N();
     GRID_LOOP(q, N) {
-        const int i = (int)(q % g.nx), j = (int)(q / g.nx);
+        const int j = (int)((unsigned)q / (unsigned)g.nx), i = (int)q - j * g.nx;
         for (int d = 0; d < 2; ++d) {
             const int64_t p = d == 0 ? g.id(i + 1, j) : g.id(i, j + 1);
             const int64_t m = d == 0 ? g.id(i - 1, j) : g.id(i, j - 1);
@@ -490,7 +490,7 @@ __global__ void k_lf_flux(G2 g, const double *__restrict__ B, const double *__re
                           double beta, int speed_c, double *Ff) {
     const int64_t N = g.N();
     GRID_LOOP(q, N) {
-        const int i = (int)(q % g.nx), j = (int)(q / g.nx);
+        const int j = (int)((unsigned)q / (unsigned)g.nx), i = (int)q - j * g.nx;
 #pragma unroll
         for (int d = 0; d < 2; ++d) {
             if ((d == 0 && g.nx == 1) || (d == 1 && g.ny == 1)) continue;
@@ -522,7 +522,7 @@ __global__ void __launch_bounds__(kB, kNodeCtas) k_lf_b(G2 g, const double *__re
                        double *Bt) {
     const int64_t N = g.N();
     GRID_LOOP(q, N) {
-        const int i = (int)(q % g.nx), j = (int)(q / g.nx);
+        const int j = (int)((unsigned)q / (unsigned)g.nx), i = (int)q - j * g.nx;
         const int64_t xm = g.id(i - 1, j), ym = g.id(i, j - 1);
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
@@ -543,7 +543,7 @@ __global__ void k_advance(G2 g, const double *__restrict__ E, const double *__re
                           const double *__restrict__ D, const double *__restrict__ phi, double *Enew, double *Bnew) {
     const int64_t N = g.N();
     GRID_LOOP(q, N) {
-        const int i = (int)(q % g.nx), j = (int)(q / g.nx);
+        const int j = (int)((unsigned)q / (unsigned)g.nx), i = (int)q - j * g.nx;
         const int64_t Nq = N;
         double cu[3];
         cu[0] = dCy(g, Eth + 2 * Nq, i, j);
@@ -578,7 +578,7 @@ __global__ void k_diag_grid(G2 g, const double *__restrict__ E, const double *__
     const int64_t N = g.N();
     double we = 0, wb = 0, ch = 0, gl = 0, db = 0;
     GRID_LOOP(q, N) {
-        const int i = (int)(q % g.nx), j = (int)(q / g.nx);
+        const int j = (int)((unsigned)q / (unsigned)g.nx), i = (int)q - j * g.nx;
         for (int k = 0; k < 3; ++k) {
             we += E[k * N + q] * E[k * N + q];
             wb += B[k * N + q] * B[k * N + q];

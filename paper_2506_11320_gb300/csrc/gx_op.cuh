@@ -50,11 +50,12 @@ struct G3 {
         return (int64_t)gx_wr(i, nx) + (int64_t)nx * ((int64_t)gx_wr(j, ny) + (int64_t)ny * gx_wr(k, nz));
     }
     __device__ __forceinline__ int64_t N() const { return (int64_t)nx * ny * nz; }
+    // node coordinates (grids hold fewer than 2^31 nodes: 32-bit division)
     __device__ __forceinline__ void ijk(int64_t q, int &i, int &j, int &k) const {
-        i = (int)(q % nx);
-        const int64_t r = q / nx;
-        j = (int)(r % ny);
-        k = (int)(r / ny);
+        const unsigned u = (unsigned)q, r = u / (unsigned)nx;
+        i = (int)(u - r * (unsigned)nx);
+        k = (int)(r / (unsigned)ny);
+        j = (int)(r - (unsigned)k * (unsigned)ny);
     }
 };
 
@@ -79,7 +80,7 @@ __device__ __forceinline__ void gx_apply_A_node(const OpArgs &a, const double *_
                                                 double out[3]) {
     const G2 &g = a.g;
     const int64_t N = g.N();
-    const int i = (int)(q % g.nx), j = (int)(q / g.nx);
+    const int j = (int)((unsigned)q / (unsigned)g.nx), i = (int)q - j * g.nx;
     const int im = gx_wr(i - 1, g.nx), ip = gx_wr(i + 1, g.nx), jm = gx_wr(j - 1, g.ny), jp = gx_wr(j + 1, g.ny);
     const int xs[3] = {im, i, ip};
     const int64_t ys[3] = {(int64_t)jm * g.nx, (int64_t)j * g.nx, (int64_t)jp * g.nx};

@@ -64,10 +64,17 @@ template <> struct Geo<3> {
     static constexpr int NC = 8, ROWS = 27, TSTR = 52, COLOFF = 36, LK = 12, KG = 2, CENTER = 13, CTAS = 2;
 };
 // shared floats per warp: corner values [4][NC] float4, then the factor table
-// [32][TSTR], which at the end of a cell holds the lanes' sums [lane][36]
+// [32][TSTR], which at the end of a cell holds the groups' sums [KG][ROWS][16]
+// followed by the species-free column totals [7][ROWS]
+template <int DIM>
+__host__ __device__ constexpr int table_floats() {
+    return 32 * Geo<DIM>::TSTR > (Geo<DIM>::KG + 1) * Geo<DIM>::ROWS * kCols
+               ? 32 * Geo<DIM>::TSTR
+               : (Geo<DIM>::KG + 1) * Geo<DIM>::ROWS * kCols;
+}
 template <int DIM>
 __host__ __device__ constexpr int warp_floats() {
-    return 16 * Geo<DIM>::NC + (32 * Geo<DIM>::TSTR > 32 * kBlk ? 32 * Geo<DIM>::TSTR : 32 * kBlk);
+    return 16 * Geo<DIM>::NC + table_floats<DIM>();
 }
 template <int DIM>
 constexpr size_t pd_smem_bytes() {
@@ -146,35 +153,29 @@ __device__ __forceinline__ void gather(const float4 *f, const float W[Geo<DIM>::
     }
 }
 
-// record entry k of a cell from the lanes' block sums S[lane][36]: pair class
-// j, column c sits in block (rg = j / 9, cg = c / 4) of every particle group
+// record entry k of a cell from the groups' sums S[kg][j][16] (pair class j,
+// column c) and the totals U[c - 9][j] of the columns 9..15 over the groups
 template <int DIM>
-__device__ __forceinline__ float record_entry(const float *S, int k) {
+__device__ __forceinline__ float record_entry(const float *S, const float *U, int k) {
     using R = Rec<DIM>;
     using G = Geo<DIM>;
-    auto ssum = [&](int j, int col) {
-        const int lk = (j / 9) * 4 + col / 4, idx = (j % 9) * 4 + col % 4;
+    if (k >= R::USED) return 0.f;
+    if (k >= R::M) {                                          // M entry (j, e): the alpha column e
+        const int t = k - R::M, j = t / 9, e = t - 9 * j;
         float s = 0.f;
 #pragma unroll
-        for (int g = 0; g < G::KG; ++g) s += S[(g * G::LK + lk) * kBlk + idx];
+        for (int g = 0; g < G::KG; ++g) s += S[(g * G::ROWS + j) * kCols + e];
         return s;
-    };
-    if (k >= R::USED) return 0.f;
-    if (k >= R::M) {
-        const int t = k - R::M;
-        return ssum(t / 9, t % 9);
     }
     int a, col;
-    if (k < R::MV) { a = k; col = 9; }
-    else if (k < R::J) { const int t = k - R::MV; a = t / 3; col = 10 + t % 3; }
-    else { const int t = k - R::J; a = t / 3; col = 13 + t % 3; }
-    const int ax = a & 1, ay = (a >> 1) & 1, az = (a >> 2) & 1;
+    if (k < R::MV) { a = k; col = 0; }
+    else if (k < R::J) { const int t = k - R::MV; a = t / 3; col = 1 + t - 3 * a; }
+    else { const int t = k - R::J; a = t / 3; col = 4 + t - 3 * a; }
+    const float *u = U + col * G::ROWS;
+    const int j0 = (a & 1) + 3 * ((a >> 1) & 1) + 9 * ((a >> 2) & 1);
     float s = 0.f;
 #pragma unroll
-    for (int t = 0; t < G::NC; ++t) {
-        const int j = (ax + (t & 1)) + 3 * (ay + ((t >> 1) & 1)) + 9 * (az + ((t >> 2) & 1));
-        s += ssum(j, col);
-    }
+    for (int t = 0; t < G::NC; ++t) s += u[j0 + (t & 1) + 3 * ((t >> 1) & 1) + 9 * ((t >> 2) & 1)];
     return s;
 }
 
@@ -209,14 +210,18 @@ __global__ void __launch_bounds__(kThreads, Geo<DIM>::CTAS) k_pd(const __grid_co
     const int roff = 12 * (lk / 4), coff = G::COLOFF + 4 * (lk % 4);
     const bool res[3] = {p.n[0] > 1, p.n[1] > 1, DIM == 3 && p.n[2] > 1};
     const int64_t nwarps = (int64_t)gridDim.x * kWarpsPerCta;
+    // cell coordinates, stepped by the warp stride without divisions (cells < 2^31)
+    const unsigned c0u = blockIdx.x * kWarpsPerCta + warp, nwu = (unsigned)nwarps;
+    const unsigned nx = (unsigned)p.n[0], ny = (unsigned)p.n[1];
+    int ci = (int)(c0u % nx), cj = (int)((c0u / nx) % ny), ck = (int)(c0u / nx / ny);
+    const int si = (int)(nwu % nx), sj = (int)((nwu / nx) % ny), sk = (int)(nwu / nx / ny);
 
-    for (int64_t cell = (int64_t)blockIdx.x * kWarpsPerCta + warp; cell < p.N; cell += nwarps) {
+    for (int64_t cell = c0u; cell < p.N; cell += nwarps, ci += si, cj += sj, ck += sk) {
+        if (ci >= p.n[0]) { ci -= p.n[0]; ++cj; }
+        if (cj >= p.n[1]) { cj -= p.n[1]; ++ck; }
         const int word = seg_word(__ldg(p.cnt_in + cell), p.cap, p.arrivals);
         const int nfr = bin_front(word), nbk = bin_back(word), n = nfr + nbk;
         if (p.arrivals && n == 0) continue;
-        const int ci = (int)(cell % p.n[0]);
-        const int cj = (int)((cell / p.n[0]) % p.n[1]);
-        const int ck = DIM == 3 ? (int)(cell / ((int64_t)p.n[0] * p.n[1])) : 0;
         __syncwarp();                                         // the previous cell's reads of cor and S are done
         if (lane < 4 * NC) {
             const int arr = lane / NC, a = lane % NC;
@@ -386,20 +391,30 @@ __global__ void __launch_bounds__(kThreads, Geo<DIM>::CTAS) k_pd(const __grid_co
         }
         // the stayers' count (the bottom segment) of this cell's new bin
         if (PUSH && lane == 0 && fbase > 0) atomicAdd(p.cnt_out + cell, fbase);
-        // the lanes' sums [lane][row 0..8][column 0..3] into the table space
+        // the groups' sums: S[kg][pair class][column], this lane's 9 x 4 block
         if (role) {
-            float4 *sd = reinterpret_cast<float4 *>(T + lane * kBlk);   // row i: columns 0..3
+            float4 *sd = reinterpret_cast<float4 *>(T + (kg * G::ROWS + 9 * (lk / 4)) * kCols + 4 * (lk % 4));
 #pragma unroll
             for (int ip = 0; ip < 4; ++ip) {
-                sd[2 * ip] = make_float4(accp[0][ip].x, accp[1][ip].x, accp[2][ip].x, accp[3][ip].x);
-                sd[2 * ip + 1] = make_float4(accp[0][ip].y, accp[1][ip].y, accp[2][ip].y, accp[3][ip].y);
+                sd[(2 * ip) * (kCols / 4)] = make_float4(accp[0][ip].x, accp[1][ip].x, accp[2][ip].x, accp[3][ip].x);
+                sd[(2 * ip + 1) * (kCols / 4)] = make_float4(accp[0][ip].y, accp[1][ip].y, accp[2][ip].y, accp[3][ip].y);
             }
-            sd[8] = make_float4(acc8[0], acc8[1], acc8[2], acc8[3]);
+            sd[8 * (kCols / 4)] = make_float4(acc8[0], acc8[1], acc8[2], acc8[3]);
+        }
+        __syncwarp();
+        // totals over the groups of the columns 1, v, alpha (v - u_ref): U[c - 9][j]
+        float *U = T + G::KG * G::ROWS * kCols;
+        for (int t = lane; t < 7 * G::ROWS; t += 32) {
+            const int c = t / G::ROWS, j = t - c * G::ROWS;
+            float v = 0.f;
+#pragma unroll
+            for (int g = 0; g < G::KG; ++g) v += T[(g * G::ROWS + j) * kCols + 9 + c];
+            U[t] = v;
         }
         __syncwarp();
         // the cell's record
         for (int k = lane; k < R::SIZE; k += 32) {
-            const float val = record_entry<DIM>(T, k);
+            const float val = record_entry<DIM>(T, U, k);
             float *dst = p.rec + (size_t)k * p.N + cell;
             if (p.arrivals) {
                 if (val != 0.f) atomicAdd(dst, val);
