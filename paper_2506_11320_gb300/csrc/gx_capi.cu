@@ -307,7 +307,7 @@ int gx_create(const gx_config *cfg, gx_ctx **out) {
         return fail(GX_ENOMEM, "pinned host allocation failed");
     std::memset(c->hflags, 0, sizeof(DevFlags));
     c->rec_size = c->dim == 3 ? Rec<3>::SIZE : Rec<2>::SIZE;
-    if ((rc = dalloc(c, &c->rec, (size_t)GX_MAX_SPECIES * N * c->rec_size))) return fail(rc, nullptr);
+    if ((rc = dalloc(c, &c->rec, (size_t)GX_MAX_SPECIES * rec_block(c->rec_size, N)))) return fail(rc, nullptr);
     double *zero3[] = {c->E, c->B, c->Eth, c->Enew, c->Bnew, c->u, c->J, c->uref64};
     for (auto p : zero3)
         if (cudaMemset(p, 0, 3 * N * sizeof(double)) != cudaSuccess) return fail(GX_ECUDA, "cudaMemset failed");

@@ -9,7 +9,7 @@
 // Layouts (component-major so that neighbouring threads touch neighbouring
 // addresses): vector fields [3][N], mass-matrix rows [81][N] (entry o*9 + e:
 // neighbour offset o = (ox+1) + 3 (oy+1), alpha component e), deposit records
-// [species][112][N].
+// tile-major per species (rec_index).
 #include "gx_op.cuh"
 
 namespace {
@@ -56,10 +56,10 @@ struct SpecK {
 
 // Record value of species s, row k, cell (FP32, as the particle kernels wrote it).
 struct Recs {
-    const float *a;           // [S][112][N]
+    const float *a;           // species blocks of the tile-major records
     int64_t N;
     __device__ __forceinline__ float get(int s, int k, int64_t cell) const {
-        return a[((size_t)s * Rec<2>::SIZE + k) * N + cell];
+        return a[(size_t)s * rec_block(Rec<2>::SIZE, N) + rec_index(Rec<2>::SIZE, k, cell)];
     }
 };
 

@@ -41,13 +41,14 @@ struct SpecK3 {
     int ns;
     double q[GX_MAX_SPECIES], m[GX_MAX_SPECIES];
     float bqf[GX_MAX_SPECIES];   // beta_s q_s
+    float qf[GX_MAX_SPECIES];    // q_s
 };
 
 struct Recs3 {
-    const float *a;       // [S][300][N]
+    const float *a;       // species blocks of the tile-major records
     int64_t N;
     __device__ __forceinline__ float get(int s, int k, int64_t cell) const {
-        return a[((size_t)s * Rec<3>::SIZE + k) * N + cell];
+        return a[(size_t)s * rec_block(Rec<3>::SIZE, N) + rec_index(Rec<3>::SIZE, k, cell)];
     }
 };
 
@@ -140,9 +141,13 @@ __global__ void k3_assemble_bulk(G3 g, SpecK3 sk, Recs3 R, double inv_dV, double
 // comoving current and the 27 mass-matrix blocks at every node (Sec. 2.1,
 // Eq. 33-35).  J: the records hold sum w alpha (v - u_ref) W; the plasma
 // velocity u of this deposit replaces u_ref through the mass-matrix sums
-// (alpha is linear in the velocity).  M: block o of node q collects every cell
-// holding both q and q + o; per axis: o_d = 0 -> cells -1 (pair class 2) and 0
-// (class 0), o_d = +1 -> cell 0 (class 1), o_d = -1 -> cell -1 (class 1).
+// (alpha is linear in the velocity): J_C(q) = sum_s q_s [sum_cells J records
+// - sum_o Mraw_s,o(q) (u - u_ref)(q + o)] / dV, Mraw_s,o the unweighted pair
+// sums of block o.  M: block o of node q collects every cell holding both q
+// and q + o; per axis: o_d = 0 -> cells -1 (pair class 2) and 0 (class 0),
+// o_d = +1 -> cell 0 (class 1), o_d = -1 -> cell -1 (class 1).  One pass over
+// the blocks reads each (cell, class) record row once for both: weighted by
+// beta_s q_s into M, by q_s into the current's correction.
 __global__ void k3_assemble_main(G3 g, SpecK3 sk, Recs3 R, double inv_dV, int comoving,
                                  const double *__restrict__ u, const double *__restrict__ uref, double *J,
                                  double *M) {
@@ -150,40 +155,24 @@ __global__ void k3_assemble_main(G3 g, SpecK3 sk, Recs3 R, double inv_dV, int co
     GRID_LOOP(q, N) {
         int i, j, k;
         g.ijk(q, i, j, k);
-        double jc[3] = {0, 0, 0};
+        float jc[3] = {0.f, 0.f, 0.f};                       // comoving correction, summed over species
+        double jr[3] = {0, 0, 0};                            // current records, species combined in FP64
         for (int s = 0; s < sk.ns; ++s) {
             float js[3] = {0.f, 0.f, 0.f};
+#pragma unroll
             for (int a = 0; a < 8; ++a) {
-                const int ax = a & 1, ay = (a >> 1) & 1, az = (a >> 2) & 1;
-                const int64_t cell = g.id(i - ax, j - ay, k - az);
+                const int64_t cell = g.id(i - (a & 1), j - ((a >> 1) & 1), k - ((a >> 2) & 1));
 #pragma unroll
                 for (int c = 0; c < 3; ++c) js[c] += R.get(s, Rec<3>::J + 3 * a + c, cell);
-                if (comoving) {
-                    for (int b = 0; b < 8; ++b) {
-                        const int bx = b & 1, by = (b >> 1) & 1, bz = (b >> 2) & 1;
-                        const int cx = ax == bx ? 2 * ax : 1, cy = ay == by ? 2 * ay : 1, cz = az == bz ? 2 * az : 1;
-                        const int mrow = Rec<3>::M + 9 * (cx + 3 * cy + 9 * cz);
-                        const int64_t nb = g.id(i - ax + bx, j - ay + by, k - az + bz);
-                        float d[3];
-#pragma unroll
-                        for (int c = 0; c < 3; ++c) d[c] = (float)(u[c * N + nb] - uref[c * N + nb]);
-#pragma unroll
-                        for (int r = 0; r < 3; ++r)
-                            js[r] -= R.get(s, mrow + 3 * r, cell) * d[0] + R.get(s, mrow + 3 * r + 1, cell) * d[1] +
-                                     R.get(s, mrow + 3 * r + 2, cell) * d[2];
-                    }
-                }
             }
 #pragma unroll
-            for (int c = 0; c < 3; ++c) jc[c] += sk.q[s] * (double)js[c];
+            for (int c = 0; c < 3; ++c) jr[c] += sk.q[s] * (double)js[c];
         }
-#pragma unroll
-        for (int c = 0; c < 3; ++c) J[c * N + q] = jc[c] * inv_dV;
         for (int o = 0; o < 27; ++o) {
             const int oo[3] = {o % 3 - 1, (o / 3) % 3 - 1, o / 9 - 1};
-            float blk[9];
+            float blk[9], blq[9];
 #pragma unroll
-            for (int e = 0; e < 9; ++e) blk[e] = 0.f;
+            for (int e = 0; e < 9; ++e) { blk[e] = 0.f; blq[e] = 0.f; }
             const int nt = (oo[0] == 0 ? 2 : 1) * (oo[1] == 0 ? 2 : 1) * (oo[2] == 0 ? 2 : 1);
             for (int t = 0; t < nt; ++t) {
                 int cof[3], cls[3], tt = t;
@@ -202,14 +191,28 @@ __global__ void k3_assemble_main(G3 g, SpecK3 sk, Recs3 R, double inv_dV, int co
                 const int64_t cell = g.id(i + cof[0], j + cof[1], k + cof[2]);
                 const int mrow = Rec<3>::M + 9 * (cls[0] + 3 * cls[1] + 9 * cls[2]);
                 for (int s = 0; s < sk.ns; ++s) {
-                    const float f = sk.bqf[s];
+                    const float f = sk.bqf[s], fq = sk.qf[s];
 #pragma unroll
-                    for (int e = 0; e < 9; ++e) blk[e] = fmaf(f, R.get(s, mrow + e, cell), blk[e]);
+                    for (int e = 0; e < 9; ++e) {
+                        const float r = R.get(s, mrow + e, cell);
+                        blk[e] = fmaf(f, r, blk[e]);
+                        blq[e] = fmaf(fq, r, blq[e]);
+                    }
                 }
             }
 #pragma unroll
             for (int e = 0; e < 9; ++e) M[(size_t)(o * 9 + e) * N + q] = (double)blk[e];
+            if (comoving) {
+                const int64_t nb = g.id(i + oo[0], j + oo[1], k + oo[2]);
+                float d[3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) d[c] = (float)(u[c * N + nb] - uref[c * N + nb]);
+#pragma unroll
+                for (int r = 0; r < 3; ++r) jc[r] += blq[3 * r] * d[0] + blq[3 * r + 1] * d[1] + blq[3 * r + 2] * d[2];
+            }
         }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) J[c * N + q] = (jr[c] - (double)jc[c]) * inv_dV;
     }
 }
 
@@ -532,6 +535,7 @@ SpecK3 speck3(const gx_ctx *c) {
         sk.q[s] = c->sp[s].q;
         sk.m[s] = c->sp[s].m;
         sk.bqf[s] = (float)(c->sp[s].q * c->cfg.dt / (2.0 * c->sp[s].m) * c->sp[s].q);
+        sk.qf[s] = (float)c->sp[s].q;
     }
     return sk;
 }

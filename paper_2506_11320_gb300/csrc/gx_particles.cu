@@ -99,7 +99,7 @@ struct PD {
     int *cnt_out;
     const float4 *mE, *mB;       // mover: E^{n+theta}, B^n (node averaged)
     const float4 *dB, *dU;       // deposit: B for alpha, reference velocity u_ref
-    float *rec;                  // [SIZE][N] for this species
+    float *rec;                  // this species' tile-major records (rec_index)
     DevFlags *flags;
     int arrivals;                // deposit only the back segments (the particles that arrived)
     int wall_ci;                 // x index of the last cell before a reflecting wall, or -1
@@ -415,7 +415,7 @@ __global__ void __launch_bounds__(kThreads, Geo<DIM>::CTAS) k_pd(const __grid_co
         // the cell's record
         for (int k = lane; k < R::SIZE; k += 32) {
             const float val = record_entry<DIM>(T, U, k);
-            float *dst = p.rec + (size_t)k * p.N + cell;
+            float *dst = p.rec + rec_index(R::SIZE, k, cell);
             if (p.arrivals) {
                 if (val != 0.f) atomicAdd(dst, val);
             } else {
@@ -548,7 +548,7 @@ struct BcArgs {
     float w[2], vth[2], u[2][3];
     float *bins;                 // the current copy (after the push)
     int *cnt;
-    float *rec;                  // [112][N] of the species
+    float *rec;                  // the species' tile-major records (rec_index)
     const float4 *dB, *dU;       // node B^{n+1} and u_ref of the deposit
 };
 
@@ -590,7 +590,7 @@ __global__ void __launch_bounds__(128) k_bc_refill(BcArgs a) {
     }
     __syncthreads();
     for (int k = threadIdx.x; k < Rec<2>::SIZE; k += blockDim.x)
-        a.rec[(size_t)k * a.N + cell] = (red[0][k] + red[1][k]) + (red[2][k] + red[3][k]);
+        a.rec[rec_index(Rec<2>::SIZE, k, cell)] = (red[0][k] + red[1][k]) + (red[2][k] + red[3][k]);
     if (threadIdx.x == 0) a.cnt[cell] = ppc;          // front segment only
 }
 
@@ -790,7 +790,7 @@ int launch_pd(gx_ctx *c, bool push, cudaStream_t st) {
         p.out = S.p[nxt];
         p.cnt_in = S.cnt[c->cur];
         p.cnt_out = S.cnt[nxt];
-        p.rec = c->rec + (size_t)s * c->N * c->rec_size;
+        p.rec = c->rec + (size_t)s * rec_block(c->rec_size, c->N);
         p.flags = c->dflags;
         p.wall_ci = (c->cfg.bc_cells > 0 && c->cfg.bc_wall) ? c->n[0] - c->cfg.bc_cells - 1 : -1;
         if (push) {
