@@ -113,6 +113,23 @@ typedef struct gx_ctx gx_ctx;
  *                 x_w = (nx - G) dx on, B is held, and a particle crossing x_w
  *                 is reflected specularly (x -> 2 x_w - x, v_x -> -v_x).  Only
  *                 side 0 then needs gx_boundary_source.
+ *   lf_rhs_printed with lf_on: 1 makes the right-hand side of the E solve curl
+ *                 B^n, as Eq. 7 prints it; 0 (default) curls B^n + theta D, D
+ *                 the LF increment that B^{n+1} receives (Eq. 17-18), the
+ *                 B^{n+theta} that Eq. 7 comes from.  At theta = 1/2 and
+ *                 c dt / dx >> 1 the printed form lets the shortest light modes
+ *                 grow by about 1 + 2 a dt / dx per step.
+ *   gl_gamma      > 0: the Gauss's-law position correction of GL-ECSIM (the
+ *                 paper names it by citation; this library's reading): with
+ *                 R_c = (div_C E^n)_c / (4 pi) - rhobar_c the Gauss residual of
+ *                 cell c (rhobar the mean of the deposited charge density over
+ *                 the cell's corner nodes) and phi_g the mean of R over the
+ *                 cells around node g, every particle's position update of the
+ *                 push gains dx_p = gl_gamma eps q_s w_p grad phi(x_p^{n+1/2}),
+ *                 eps = 1 / (Q2 sum_d 4 / dx_d^2), Q2 = sum_p (q_s w_p)^2 / V:
+ *                 one steepest-descent step on (dV / 2) sum_c R_c^2, which damps
+ *                 every residual mode for 0 < gl_gamma <= 1.  0 (default): off.
+ *                 Periodic grids only (not with bc_cells).
  *   seed          key of the context's counter-based draws (Philox4x64-10 with
  *                 key (seed, species)): the device-side Maxwellian species
  *                 (gx_species_maxwellian, counter (0, cell, particle, 0)) and the
@@ -140,6 +157,8 @@ typedef struct {
     int32_t bc_cells;
     int32_t bc_wall;
     uint64_t seed;
+    int32_t lf_rhs_printed;
+    double gl_gamma;
 } gx_config;
 
 typedef struct {

@@ -63,6 +63,8 @@ class Cfg(C.Structure):
         ("gmres_tol", C.c_double),
         ("bc_cells", C.c_int32),
         ("bc_wall", C.c_int32),
+        ("lf_rhs_printed", C.c_int32),
+        ("gl_gamma", C.c_double),
     ]
 
     @property
@@ -76,7 +78,7 @@ class Cfg(C.Structure):
 
 def make_cfg(n, dx, *, c=1.0, theta=0.5, dt=0.02, comoving=0, lf_on=0, lf_speed_c=0, lf_beta=1.0,
              ns_j=0, nsmooth_u=5, gmres_tol=1e-12, gmres_restart=50, gmres_maxit=5000, divb_clean=0,
-             nsmooth_e=0, bc_cells=0, bc_wall=0) -> Cfg:
+             nsmooth_e=0, bc_cells=0, bc_wall=0, lf_rhs_printed=0, gl_gamma=0.0) -> Cfg:
     n = list(n) + [1] * (3 - len(n))
     dx = list(dx) + [1.0] * (3 - len(dx))
     cfg = Cfg()
@@ -91,6 +93,10 @@ def make_cfg(n, dx, *, c=1.0, theta=0.5, dt=0.02, comoving=0, lf_on=0, lf_speed_
     cfg.nsmooth_e = int(nsmooth_e)
     cfg.bc_cells = int(bc_cells)
     cfg.bc_wall = int(bc_wall)
+    cfg.lf_rhs_printed = int(lf_rhs_printed)
+    cfg.gl_gamma = float(gl_gamma)
+    if cfg.bc_cells and cfg.gl_gamma > 0:
+        raise ValueError("the Gauss's-law correction runs on periodic grids only")
     if cfg.bc_cells and (cfg.divb_clean or 2 * cfg.bc_cells >= cfg.n[0]):
         raise ValueError("open boundaries: no divergence cleaning, and 2 bc_cells < nx")
     if cfg.bc_wall and not cfg.bc_cells:
@@ -124,6 +130,7 @@ _SIGS = {
     "or_grad_C": (None, [_P, _D, _D]),
     "or_mc_limiter": (C.c_double, [C.c_double, C.c_double]),
     "or_lf_kappa_E": (None, [_P, _D, _D, _D]),
+    "or_gl_displacement": (None, [_P, _D, C.c_int64, _I32, _D, _D, _D, _D, _D, C.c_double, _D, _D, _D, _D]),
     "or_cell_sample3": (None, [_P, C.c_uint64, C.c_int, C.c_int64, C.c_int, C.c_int, C.c_int, C.c_int, _D,
                                C.c_double, _D, _D, _D, _D, _D, _D]),
     "or_apply_A": (None, [_P, _D, _D, _D, _D]),
@@ -380,6 +387,17 @@ def step(cfg, pl: Plasma, E, B, want=(), phi=None):
     res = {k: v for k, v in outs.items() if v is not None}
     res.update(rc=rc, iters=int(stats[0]), relres=stats[1], maxdisp=stats[2])
     return res
+
+
+def gl_displacement(cfg, pl: Plasma, E, gamma):
+    """Gauss's-law position correction: per-particle displacements (dx, dy, dz)
+    and F = (dV/2) sum_c R_c^2 at the current positions (or_gl_displacement)."""
+    d = [np.zeros(pl.np) for _ in range(3)]
+    F = C.c_double(0.0)
+    lib().or_gl_displacement(C.byref(cfg), _d(pl.q), pl.np, pl.sp.ctypes.data_as(_I32), _d(pl.x), _d(pl.y),
+                             _d(pl.z), _d(pl.w), _d(_f64(E)), float(gamma), _d(d[0]), _d(d[1]), _d(d[2]),
+                             C.byref(F))
+    return d[0], d[1], d[2], F.value
 
 
 def philox4x64(key, ctr):

@@ -90,6 +90,8 @@ typedef struct {
     double gmres_tol;      /* relative residual target */
     int32_t bc_cells;      /* open x boundaries: cells per end held at a fixed plasma state (0: periodic) */
     int32_t bc_wall;       /* 1: the high-x boundary cells are a reflecting conducting wall instead */
+    int32_t lf_rhs_printed; /* 1: the E solve curls B^n as Eq. 7 prints it, without theta D */
+    double gl_gamma;       /* > 0: Gauss's-law position correction of GL-ECSIM, step fraction (see or_gl_displacement) */
 } or_cfg;
 
 /* ---------------------------------------------------------------- indexing */
@@ -540,7 +542,7 @@ void or_rhs(const or_cfg *g, const double *En, const double *Bc, const double *J
             const double *u, const double *Bn, double *b) {
     int64_t N = n_nodes(g);
     double *cn = (double *)malloc(sizeof(double) * 3 * N);
-    if (g->lf_on) {
+    if (g->lf_on && !g->lf_rhs_printed) {
         /* B^{n+theta} = (1 - theta) B^n + theta B^{n+1} holds the LF increment D
          * of B^{n+1} too, so the curl on the right acts on B^n + theta D */
         double *Bt = (double *)malloc(sizeof(double) * 3 * N);
@@ -900,6 +902,94 @@ double or_mover(const or_cfg *g, const double *qs, const double *ms, int64_t np,
     return maxdisp;
 }
 
+/* ------------------------------------------------ Gauss's-law correction */
+
+/* Particle-position correction for Gauss's law, the "GL" of GL-ECSIM (the
+ * paper names the method by citation only; this is the reading used here).
+ * With R_c = (div_C E)_c / (4 pi) - rhobar_c the Gauss residual of cell c,
+ * rhobar_c the mean over the cell's 8 corner nodes of the particles' CIC
+ * charge density rho, and
+ *   F(x_1, ..., x_np) = (dV / 2) sum_c R_c^2,
+ * the derivative of F with respect to a particle position is
+ *   dF/dx_p = -q_p grad phi(x_p),  phi_g = mean of R over the 8 cells around node g,
+ * phi interpolated with the particles' own linear weights (q_p = q_s w_p).  The
+ * correction is one steepest-descent step,
+ *   dx_p = gamma eps q_p grad phi(x_p),  eps = 1 / (Q2 sum_d 4 / dx_d^2),  Q2 = sum_p q_p^2 / V,
+ * V the domain volume and the sum over resolved axes: for a uniform plasma the
+ * linearised step multiplies a residual mode by about 1 - gamma eps Q2 k^2,
+ * with k^2 <= sum_d 4 / dx_d^2 on the grid, so 0 < gamma <= 1 damps every mode.
+ * Writes the displacements and, in F_out (may be NULL), F at the given positions.
+ * Collapsed axes get no displacement. */
+void or_gl_displacement(const or_cfg *g, const double *qs, int64_t np, const int32_t *sp,
+                        const double *x, const double *y, const double *z, const double *w,
+                        const double *E, double gamma, double *dx, double *dy, double *dz, double *F_out) {
+    int64_t N = n_nodes(g);
+    double dV = cell_volume(g);
+    double *rho = (double *)calloc((size_t)N, sizeof(double));
+    double *div = (double *)malloc(sizeof(double) * N);
+    double *R = (double *)malloc(sizeof(double) * N);
+    double *phi = (double *)malloc(sizeof(double) * N);
+    double Q2 = 0.0;
+    for (int64_t p = 0; p < np; ++p) {
+        double qp = qs[sp[p]] * w[p];
+        double pos[3] = {x[p], y[p], z[p]}, W[8];
+        int cell[3];
+        shape(g, pos, cell, W);
+        for (int a = 0; a < 8; ++a) rho[corner_node(g, cell, a)] += qp * W[a] / dV;
+        Q2 += qp * qp;
+    }
+    Q2 /= (double)N * dV;
+    or_div_C(g, E, div);
+    for (int64_t c = 0; c < N; ++c) {
+        int i, j, k;
+        unix3(g, c, &i, &j, &k);
+        double rb = 0.0;
+        for (int a = 0; a < 8; ++a) rb += rho[ix(g, i + (a & 1), j + ((a >> 1) & 1), k + ((a >> 2) & 1))];
+        R[c] = div[c] / (4.0 * OR_PI) - rb / 8.0;
+    }
+    double F = 0.0;
+    for (int64_t c = 0; c < N; ++c) F += 0.5 * dV * R[c] * R[c];
+    for (int64_t nd = 0; nd < N; ++nd) {
+        int i, j, k;
+        unix3(g, nd, &i, &j, &k);
+        double s = 0.0;
+        for (int a = 0; a < 8; ++a) s += R[ix(g, i - 1 + (a & 1), j - 1 + ((a >> 1) & 1), k - 1 + ((a >> 2) & 1))];
+        phi[nd] = s / 8.0;
+    }
+    double lap = 0.0;
+    for (int d = 0; d < 3; ++d)
+        if (g->n[d] > 1) lap += 4.0 / (g->dx[d] * g->dx[d]);
+    const double eps = (Q2 > 0.0 && lap > 0.0) ? 1.0 / (Q2 * lap) : 0.0;
+    for (int64_t p = 0; p < np; ++p) {
+        double qp = qs[sp[p]] * w[p];
+        double pos[3] = {x[p], y[p], z[p]}, f[3];
+        int cell[3];
+        for (int d = 0; d < 3; ++d) {
+            double sd = pos[d] / g->dx[d], fl = floor(sd);
+            cell[d] = (int)fl;
+            f[d] = (g->n[d] == 1) ? 0.0 : sd - fl;
+        }
+        double grad[3] = {0.0, 0.0, 0.0};
+        for (int a = 0; a < 8; ++a) {
+            int ab[3] = {a & 1, (a >> 1) & 1, (a >> 2) & 1};
+            double ph = phi[corner_node(g, cell, a)];
+            for (int d = 0; d < 3; ++d) {
+                if (g->n[d] == 1) continue;
+                /* d W_a / d x_d: the derivative of the linear factor along d times the other two factors */
+                double t = (ab[d] ? 1.0 : -1.0) / g->dx[d];
+                for (int e = 0; e < 3; ++e)
+                    if (e != d) t *= ab[e] ? f[e] : 1.0 - f[e];
+                grad[d] += t * ph;
+            }
+        }
+        dx[p] = gamma * eps * qp * grad[0];
+        dy[p] = gamma * eps * qp * grad[1];
+        dz[p] = gamma * eps * qp * grad[2];
+    }
+    if (F_out) *F_out = F;
+    free(rho); free(div); free(R); free(phi);
+}
+
 /* -------------------------------------------------------------- diagnostics */
 
 /* out[0] = electric energy dV sum |E|^2 / 8 pi, out[1] = magnetic energy,
@@ -974,7 +1064,30 @@ int or_step(const or_cfg *g, const double *qs, const double *ms, int64_t np, con
     if (g->divb_clean && phi) or_divb_clean(g, Bn1, phi);
     /* E^{n+1} smoothed by nsmooth_e passes of Eq. 26, phi = 0.5, strides 1, 2, 1, ... */
     for (int pass = 0; pass < g->nsmooth_e; ++pass) or_filter(g, En1, 3, (pass % 2 == 0) ? 1 : 2, 0.5);
+    /* GL correction (or_gl_displacement): the displacement of x^{n+1/2} from E^n and
+     * the particles' own charge, added to the mover's update of the positions */
+    double *gdx = NULL, *gdy = NULL, *gdz = NULL;
+    if (g->gl_gamma > 0.0) {
+        gdx = (double *)malloc(sizeof(double) * (np > 0 ? np : 1));
+        gdy = (double *)malloc(sizeof(double) * (np > 0 ? np : 1));
+        gdz = (double *)malloc(sizeof(double) * (np > 0 ? np : 1));
+        or_gl_displacement(g, qs, np, sp, x, y, z, w, E, g->gl_gamma, gdx, gdy, gdz, NULL);
+    }
     double md = or_mover(g, qs, ms, np, sp, x, y, z, vx, vy, vz, Eth, Bn, vbar_out);
+    if (gdx) {
+        double *xs[3] = {x, y, z}, *ds[3] = {gdx, gdy, gdz};
+        for (int d = 0; d < 3; ++d) {
+            if (g->n[d] == 1) continue;
+            double L = g->n[d] * g->dx[d];
+            for (int64_t p = 0; p < np; ++p) {
+                double xn = fmod(xs[d][p] + ds[d][p], L);
+                if (xn < 0.0) xn += L;
+                if (xn >= L) xn -= L;
+                xs[d][p] = xn;
+            }
+        }
+        free(gdx); free(gdy); free(gdz);
+    }
     memcpy(E, En1, sizeof(double) * 3 * N);
     memcpy(Bc, Bn1, sizeof(double) * 3 * N);
     if (Eth_out) memcpy(Eth_out, Eth, sizeof(double) * 3 * N);

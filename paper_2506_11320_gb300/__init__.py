@@ -49,6 +49,8 @@ class Config(C.Structure):
         ("bc_cells", C.c_int32),
         ("bc_wall", C.c_int32),
         ("seed", C.c_uint64),
+        ("lf_rhs_printed", C.c_int32),
+        ("gl_gamma", C.c_double),
     ]
 
 
@@ -156,7 +158,7 @@ def _stream(stream):
 def make_config(n, dx, *, c=1.0, theta=0.5, dt=0.02, comoving=1, lf_on=1, lf_speed_c=0, lf_beta=1.0, ns_j=0,
                 nsmooth_u=5, gmres_tol=1e-8, gmres_restart=50, gmres_maxit=2000, precond=GX_PRECOND_NONE,
                 track_ids=0, bin_slack=1.6, divb_clean=0, nsmooth_e=0, bc_cells=0,
-                bc_wall=0, seed=0) -> Config:
+                bc_wall=0, seed=0, lf_rhs_printed=0, gl_gamma=0.0) -> Config:
     n = list(n) + [1] * (3 - len(n))
     dx = list(dx) + [1.0] * (3 - len(dx))
     cfg = Config()
@@ -173,6 +175,8 @@ def make_config(n, dx, *, c=1.0, theta=0.5, dt=0.02, comoving=1, lf_on=1, lf_spe
     cfg.bc_cells = int(bc_cells)
     cfg.bc_wall = int(bc_wall)
     cfg.seed = int(seed)
+    cfg.lf_rhs_printed = int(lf_rhs_printed)
+    cfg.gl_gamma = float(gl_gamma)
     return cfg
 
 

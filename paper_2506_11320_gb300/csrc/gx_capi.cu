@@ -59,6 +59,14 @@ __global__ void k_nonfinite(int64_t n, const T *__restrict__ a, int *bad) {
     if (__any_sync(0xffffffffu, b) && (threadIdx.x & 31) == 0) atomicExch(bad, 1);
 }
 
+__global__ void k_sum_sq(int64_t n, const float *__restrict__ a, double *out) {
+    double s = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        s += (double)a[i] * (double)a[i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(out, s);
+}
+
 // 1 if any of the arrays (device copies) holds a NaN or an infinity
 template <class T>
 int any_nonfinite(gx_ctx *c, std::initializer_list<std::pair<const T *, int64_t>> arrays, cudaStream_t st, int *out) {
@@ -174,6 +182,17 @@ int check_flags(gx_ctx *c, cudaStream_t st) {
 }  // namespace
 
 cudaEvent_t gx_ev_get(gx_ctx *c) { return ev_get(c); }
+
+int gx_sum_squares(gx_ctx *c, const float *a, int64_t n, cudaStream_t st, double *out) {
+    double *acc = c->dred;
+    GX_CHECK(c, cudaMemsetAsync(acc, 0, sizeof(double), st));
+    const int64_t blocks = std::min<int64_t>((n + 255) / 256, 152 * 8);
+    k_sum_sq<<<(unsigned)std::max<int64_t>(1, blocks), 256, 0, st>>>(n, a, acc);
+    GX_LAUNCHED(c);
+    GX_CHECK(c, cudaMemcpyAsync(out, acc, sizeof(double), cudaMemcpyDeviceToHost, st));
+    GX_CHECK(c, cudaStreamSynchronize(st));
+    return GX_OK;
+}
 void gx_ev_push(gx_ctx *c, int cat, cudaEvent_t a, cudaEvent_t b) {
     c->evpend[cat].push_back({a, b});
     if (c->evpend[cat].size() > 512) ev_resolve(c);
@@ -265,6 +284,8 @@ int gx_create(const gx_config *cfg, gx_ctx **out) {
     if (cfg->bc_cells > 0 && cfg->nsmooth_e > 0)   // the filter would move the held boundary E
         return fail(GX_EINVAL, "open boundaries without nsmooth_e");
     if (cfg->lf_on && !(cfg->lf_beta >= 0 && cfg->lf_beta < 1e300)) return fail(GX_EINVAL, "lf_beta must be >= 0");
+    if (!(cfg->gl_gamma >= 0 && cfg->gl_gamma <= 1)) return fail(GX_EINVAL, "gl_gamma must be in [0, 1]");
+    if (cfg->gl_gamma > 0 && cfg->bc_cells > 0) return fail(GX_EINVAL, "gl_gamma needs a periodic grid (no bc_cells)");
     if (!(cfg->c < 1e300) || !(cfg->dt < 1e300) || !(cfg->gmres_tol < 1e300) || !(cfg->bin_slack == cfg->bin_slack))
         return fail(GX_EINVAL, "c, dt, gmres_tol and bin_slack must be finite");
     for (int d = 0; d < 3; ++d)
@@ -362,6 +383,8 @@ int gx_species_add(gx_ctx *c, double q, double m, int64_t n, const double *x, co
         if (!rc && bad) { c->err = "gx_species_add: a position, velocity or weight is not finite"; rc = GX_EINVAL; }
     }
     if (!rc) rc = gx_bin_particles(c, s, n, px, py, pz, pvx, pvy, pvz, pw, nullptr, st);
+    c->sp[s].w2 = 0.0;
+    if (!rc && n > 0) rc = gx_sum_squares(c, pw, n, st, &c->sp[s].w2);
     if (dx_) { cudaFree(dx_); cudaFree(dy_); cudaFree(dvx); cudaFree(dvy); cudaFree(dvz); cudaFree(dw); }
     if (dz_) cudaFree(dz_);
     if (rc) return rc;
@@ -387,6 +410,8 @@ int gx_species_maxwellian(gx_ctx *c, double q, double m, int ppc, double n0, con
     c->sp[s].q = q;
     c->sp[s].m = m;
     TRY(gx_species_maxwellian_init(c, s, ppc, n0, u, vth, 0));
+    const double wm = (double)(float)(n0 * c->dV / ppc);          // every particle's FP32 weight
+    c->sp[s].w2 = (double)ppc * (double)c->N * wm * wm;
     c->nspecies++;
     c->np_total += (int64_t)ppc * c->N;
     c->moments_valid = 0;
@@ -484,6 +509,7 @@ int gx_push_and_deposit(gx_ctx *c, void *stream) {
     }
     {
         EvTimer t(c, st, 0);
+        if (c->cfg.gl_gamma > 0) TRY(c->dim == 3 ? gx3_gl_potential(c, st) : gx_gl_potential(c, st));
         TRY(gx_run_push_deposit(c, st));
         t.stop();
     }

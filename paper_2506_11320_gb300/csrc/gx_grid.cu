@@ -20,7 +20,6 @@ constexpr int kB = 256;
 // of 512 CTAs over 152 SMs instead of 1.7 waves at two CTAs per SM
 constexpr int kNodeCtas = 4;
 
-__device__ __forceinline__ int wr(int i, int n) { return gx_wr(i, n); }
 
 inline int blocks_for(int64_t n) {
     int64_t b = (n + kB - 1) / kB;
@@ -314,6 +313,26 @@ __global__ void k_divb_phi(G2 g, const double *__restrict__ B, double dtch2, dou
         if (g.nx > 1) d += (B[g.id(i + 1, j)] - B[g.id(i - 1, j)]) * g.hx;
         if (g.ny > 1) d += (B[N + g.id(i, j + 1)] - B[N + g.id(i, j - 1)]) * g.hy;
         phi[q] = decay * (phi[q] - dtch2 * d);
+    }
+}
+
+// Gauss residual of cell (i,j): R = (div_C E) / (4 pi) - rhobar, rhobar the mean
+// of rho over the cell's 4 corner nodes (the Gauss's-law correction)
+__global__ void k_gl_residual(G2 g, const double *__restrict__ E, const double *__restrict__ rho, double *R) {
+    const int64_t N = g.N();
+    GRID_LOOP(q, N) {
+        const int j = (int)((unsigned)q / (unsigned)g.nx), i = (int)q - j * g.nx;
+        const double divE = dCx(g, E, i, j) + dCy(g, E + N, i, j);
+        const double rb = 0.25 * (rho[q] + rho[g.id(i + 1, j)] + rho[g.id(i, j + 1)] + rho[g.id(i + 1, j + 1)]);
+        R[q] = divE * (0.25 / GX_PI) - rb;
+    }
+}
+// phi at node (i,j): the mean of R over the 4 cells around it, into nE[q].w
+__global__ void k_gl_phi(G2 g, const double *__restrict__ R, float4 *nE) {
+    const int64_t N = g.N();
+    GRID_LOOP(q, N) {
+        const int j = (int)((unsigned)q / (unsigned)g.nx), i = (int)q - j * g.nx;
+        nE[q].w = (float)(0.25 * (R[g.id(i - 1, j - 1)] + R[g.id(i, j - 1)] + R[g.id(i - 1, j)] + R[q]));
     }
 }
 
@@ -748,7 +767,7 @@ int gx_build_rhs(gx_ctx *c, cudaStream_t st) {
         GX_LAUNCHED(c);
         k_lf_b<<<blocks_for(c->N), kB, 0, st>>>(g, c->B, Ff, c->cfg.theta, D, Bt);
         GX_LAUNCHED(c);
-        Bc = Bt;
+        if (!c->cfg.lf_rhs_printed) Bc = Bt;   // the printed Eq. 7 curls B^n alone
     }
     k_rhs<<<blocks_for(c->N), kB, 0, st>>>(g, c->E, Bc, c->J, c->M, cm ? c->EM : nullptr, ctd, jf, jf / c->dV,
                                            c->rhs);
@@ -824,6 +843,14 @@ int gx_advance(gx_ctx *c, cudaStream_t st) {
     }
     // E^{n+1} smoothed by nsmooth_e filter passes (strides 1, 2, 1, ...) in place of LF on E
     return filter_passes(c, c->Enew, c->cfg.nsmooth_e, true, st);
+}
+
+int gx_gl_potential(gx_ctx *c, cudaStream_t st) {
+    k_gl_residual<<<blocks_for(c->N), kB, 0, st>>>(geom(c), c->E, c->rho, c->tmp3);
+    GX_LAUNCHED(c);
+    k_gl_phi<<<blocks_for(c->N), kB, 0, st>>>(geom(c), c->tmp3, c->nE);
+    GX_LAUNCHED(c);
+    return GX_OK;
 }
 
 int gx_copy_uref(gx_ctx *c, int zero, cudaStream_t st);

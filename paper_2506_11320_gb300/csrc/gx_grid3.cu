@@ -520,6 +520,29 @@ __global__ void k3_diag_grid(G3 g, H4 h, const double *__restrict__ E, const dou
     }
 }
 
+// Gauss residual of cell (i,j,k) and its mean over the cells around a node (the
+// Gauss's-law correction), as in 2D with 8 corners and 8 cells
+__global__ void k3_gl_residual(G3 g, H4 h, const double *__restrict__ E, const double *__restrict__ rho, double *R) {
+    const int64_t N = g.N();
+    GRID_LOOP(q, N) {
+        int i, j, k;
+        g.ijk(q, i, j, k);
+        const double divE = dC3(g, h, E, i, j, k, 0) + dC3(g, h, E + N, i, j, k, 1) + dC3(g, h, E + 2 * N, i, j, k, 2);
+        double rb = 0.0;
+#pragma unroll
+        for (int a = 0; a < 8; ++a) rb += rho[g.id(i + (a & 1), j + ((a >> 1) & 1), k + ((a >> 2) & 1))];
+        R[q] = divE * (0.25 / GX_PI) - 0.125 * rb;
+    }
+}
+__global__ void k3_gl_phi(G3 g, const double *__restrict__ R, float4 *nE) {
+    const int64_t N = g.N();
+    GRID_LOOP(q, N) {
+        int i, j, k;
+        g.ijk(q, i, j, k);
+        nE[q].w = (float)cell_mean(g, R, i, j, k);
+    }
+}
+
 G3 geom3(const gx_ctx *c) {
     return G3{c->n[0], c->n[1], c->n[2], c->cfg.dx[0], c->cfg.dx[1], c->cfg.dx[2]};
 }
@@ -632,7 +655,7 @@ int gx3_build_rhs(gx_ctx *c, cudaStream_t st) {
         GX_LAUNCHED(c);
         k3_lf_b<<<blocks_for(c->N), kB, 0, st>>>(g, c->B, Ff, c->cfg.theta, D, Bt);
         GX_LAUNCHED(c);
-        Bc = Bt;
+        if (!c->cfg.lf_rhs_printed) Bc = Bt;   // the printed Eq. 7 curls B^n alone
     }
     k3_rhs<<<blocks_for(c->N), kB, 0, st>>>(g, h4(c), c->E, Bc, c->J, c->M, cm ? c->EM : nullptr, ctd, jf,
                                             jf / c->dV, c->rhs);
@@ -678,6 +701,14 @@ int gx3_advance(gx_ctx *c, cudaStream_t st) {
                                                 c->cfg.theta, c->cfg.lf_on ? c->dBlf : nullptr, c->Enew, c->Bnew);
     GX_LAUNCHED(c);
     return gx3_filter(c, c->Enew, c->cfg.nsmooth_e, true, st);
+}
+
+int gx3_gl_potential(gx_ctx *c, cudaStream_t st) {
+    k3_gl_residual<<<blocks_for(c->N), kB, 0, st>>>(geom3(c), h4(c), c->E, c->rho, c->tmp3);
+    GX_LAUNCHED(c);
+    k3_gl_phi<<<blocks_for(c->N), kB, 0, st>>>(geom3(c), c->tmp3, c->nE);
+    GX_LAUNCHED(c);
+    return GX_OK;
 }
 
 int gx3_diag_grid(gx_ctx *c, double *acc, cudaStream_t st) {

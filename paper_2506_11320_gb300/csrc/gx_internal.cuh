@@ -84,6 +84,7 @@ struct Species {
     int nf = 0;                         // FP32 fields stored per particle
     float *p[2] = {};                   // [copy]: [cell][field][cap]
     int *cnt[2] = {};                   // particles per cell, per copy
+    double w2 = 0;                      // sum of the squared weights (the Gauss's-law correction's step)
 };
 
 struct BcSource {                       // plasma state of an open boundary, per species
@@ -236,6 +237,13 @@ int gx_apply_jacobi(gx_ctx *c, const double *x, double *y, cudaStream_t st);
 int gx_advance(gx_ctx *c, cudaStream_t st);                  // Enew, Bnew from Eth
 int gx_initial_guess(gx_ctx *c, cudaStream_t st);            // Eth <- starting point of the solve
 int gx_diag_run(gx_ctx *c, gx_diag *out, cudaStream_t st);
+
+// Gauss's-law correction: the potential phi of the Gauss residual of E^n and the
+// current deposit, into the .w of the node copy nE that the push reads
+int gx_gl_potential(gx_ctx *c, cudaStream_t st);
+int gx3_gl_potential(gx_ctx *c, cudaStream_t st);
+// sum of squares of n device floats (FP64), read back (synchronises st)
+int gx_sum_squares(gx_ctx *c, const float *a, int64_t n, cudaStream_t st, double *out);
 
 // 3D grid (gx_grid3.cu): the same steps on a grid with a resolved z axis
 int gx3_node_fields(gx_ctx *c, const double *Eth, const double *Bcur, float4 *outE, float4 *outB, cudaStream_t st);

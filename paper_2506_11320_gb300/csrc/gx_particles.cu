@@ -50,7 +50,6 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kWarpsPerCta = kThreads / 32;
 constexpr int kCols = 16;                         // alpha[9], 1, v[3], alpha (v - u_ref) [3]
-constexpr int kBlk = 36;                          // sums per lane: 9 pair classes x 4 columns
 constexpr unsigned kFull = 0xffffffffu;
 
 // NC corners; ROWS pair classes in groups of 9; factor table of TSTR floats
@@ -103,6 +102,8 @@ struct PD {
     DevFlags *flags;
     int arrivals;                // deposit only the back segments (the particles that arrived)
     int wall_ci;                 // x index of the last cell before a reflecting wall, or -1
+    int glon;                    // Gauss's-law correction: phi in the .w of the mover's E corners
+    float gl[3];                 // its step per axis in cell units: gamma eps q / dx_d^2
 };
 
 // ------------------------------------------------------------ helpers
@@ -276,11 +277,27 @@ __global__ void __launch_bounds__(kThreads, Geo<DIM>::CTAS) k_pd(const __grid_co
                 const float vby = (ay + (az * bx - ax * bz) + ab * by) * inv;
                 const float vbz = (az + (ax * by - ay * bx) + ab * bz) * inv;
                 v[0] = 2.f * vbx - v[0]; v[1] = 2.f * vby - v[1]; v[2] = 2.f * vbz - v[2];
+                // Gauss's-law correction: gamma eps q w grad phi at x^{n+1/2}, in cell
+                // units (d W_a / d o_d = +-1 times the other axes' linear factors)
+                float gd[3] = {0.f, 0.f, 0.f};
+                if (p.glon) {
+#pragma unroll
+                    for (int a = 0; a < NC; ++a) {
+                        const float ph = cor[a].w;
+                        const float fx = (a & 1) ? o[0] : 1.f - o[0], fy = (a & 2) ? o[1] : 1.f - o[1];
+                        const float fz = DIM == 3 ? ((a & 4) ? o[2] : 1.f - o[2]) : 1.f;
+                        gd[0] += ((a & 1) ? ph : -ph) * fy * fz;
+                        gd[1] += ((a & 2) ? ph : -ph) * fx * fz;
+                        if (DIM == 3) gd[2] += ((a & 4) ? ph : -ph) * fx * fy;
+                    }
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) gd[d] *= p.gl[d] * w;
+                }
                 int s[3] = {0, 0, 0};
                 bool cfl = false;
 #pragma unroll
                 for (int d = 0; d < DIM; ++d) {
-                    o[d] = fmaf(v[d], p.dtd[d], o[d]);
+                    o[d] = fmaf(v[d], p.dtd[d], o[d]) + gd[d];
                     if (WALL && d == 0 && wallc && o[0] >= 1.f) { o[0] = 2.f - o[0]; v[0] = -v[0]; }   // specular reflection
                     float f = floorf(o[d]);
                     o[d] -= f;
@@ -793,6 +810,18 @@ int launch_pd(gx_ctx *c, bool push, cudaStream_t st) {
         p.rec = c->rec + (size_t)s * rec_block(c->rec_size, c->N);
         p.flags = c->dflags;
         p.wall_ci = (c->cfg.bc_cells > 0 && c->cfg.bc_wall) ? c->n[0] - c->cfg.bc_cells - 1 : -1;
+        if (push && c->cfg.gl_gamma > 0) {
+            // eps = 1 / (Q2 sum_d 4 / dx_d^2), Q2 = sum_p (q_s w_p)^2 / V
+            double Q2 = 0.0, lap = 0.0;
+            for (int t = 0; t < c->nspecies; ++t) Q2 += c->sp[t].q * c->sp[t].q * c->sp[t].w2;
+            Q2 /= (double)c->N * c->dV;
+            for (int d = 0; d < 3; ++d)
+                if (c->n[d] > 1) lap += 4.0 / (c->cfg.dx[d] * c->cfg.dx[d]);
+            const double eps = (Q2 > 0 && lap > 0) ? 1.0 / (Q2 * lap) : 0.0;
+            p.glon = eps > 0;
+            for (int d = 0; d < 3; ++d)
+                p.gl[d] = c->n[d] > 1 ? (float)(c->cfg.gl_gamma * eps * S.q / (c->cfg.dx[d] * c->cfg.dx[d])) : 0.f;
+        }
         if (push) {
             p.mE = c->nE; p.mB = c->nB; p.dB = c->nBnext; p.dU = c->nUref;
             GX_CHECK(c, cudaMemsetAsync(S.cnt[nxt], 0, c->N * sizeof(int), st));

@@ -83,3 +83,27 @@ def test_lf_increment_in_the_solve_keeps_fast_light_modes_bounded():
         radii_without.append(max(abs(np.linalg.eigvals(mode_matrix(s, theta, nu, sigma, False)))))
     assert max(radii_with) <= 1.0 + 1e-12
     assert max(radii_without) > 1.5
+
+
+@pytest.mark.parametrize("m,cfl", [(5, 0.4), (13, 2.0)])
+def test_printed_form_follows_its_own_closed_form(m, cfl):
+    """With lf_rhs_printed the solve curls B^n alone, as Eq. 7 prints it: the
+    same mode then follows the recurrence without the theta D term, and leaves
+    the one with it (so the switch selects exactly that term)."""
+    n, dx, c, theta = 40, 0.02, 1.0, 0.5
+    dt = cfl * dx / c
+    k = 2 * np.pi * m / (n * dx)
+    e0, b0 = 0.3 + 0.1j, -0.5 + 0.4j
+    E, B = mode_fields(n, dx, k, e0, b0)
+    cfg = O.make_cfg((n, 1, 1), (dx, 1.0, 1.0), c=c, theta=theta, dt=dt, lf_on=1, lf_speed_c=1, lf_beta=0.0,
+                     gmres_tol=1e-14, nsmooth_u=0, lf_rhs_printed=1)
+    args = (c * theta * dt * 2 * np.sin(k * dx / 2) / dx, theta, c * dt / dx, 2 * np.sin(k * dx / 2) ** 2)
+    steps = 4
+    for _ in range(steps):
+        assert O.step(cfg, empty_plasma(), E, B)["rc"] == 0
+    e, b = np.linalg.matrix_power(mode_matrix(*args, with_theta_d=False), steps) @ np.array([e0, b0])
+    Ee, Be = mode_fields(n, dx, k, e, b)
+    assert np.abs(E - Ee).max() <= 1e-10 and np.abs(B - Be).max() <= 1e-10
+    e, b = np.linalg.matrix_power(mode_matrix(*args), steps) @ np.array([e0, b0])
+    Ee, _ = mode_fields(n, dx, k, e, b)
+    assert np.abs(E - Ee).max() > 1e-6
