@@ -130,6 +130,16 @@ typedef struct gx_ctx gx_ctx;
  *                 one steepest-descent step on (dV / 2) sum_c R_c^2, which damps
  *                 every residual mode for 0 < gl_gamma <= 1.  0 (default): off.
  *                 Periodic grids only (not with bc_cells).
+ *   gmres_mixed   1: mixed-precision FGMRES (iterative refinement).  Every
+ *                 restart computes the true residual b - A x and updates x in
+ *                 FP64; the Arnoldi cycles between restarts keep the Krylov
+ *                 basis in FP32 and apply FP32 copies of the operator's
+ *                 coefficients, with FP64 inner products, and each cycle stops
+ *                 once its residual estimate has dropped by 1e-4.  The solve
+ *                 still ends when the FP64 true residual reaches gmres_tol (the
+ *                 relres of gx_solve_stats).  Costs 4 bytes per coefficient more
+ *                 device memory; not with precond GX_PRECOND_NET.  0 (default):
+ *                 all-FP64 FGMRES.
  *   seed          key of the context's counter-based draws (Philox4x64-10 with
  *                 key (seed, species)): the device-side Maxwellian species
  *                 (gx_species_maxwellian, counter (0, cell, particle, 0)) and the
@@ -159,6 +169,7 @@ typedef struct {
     uint64_t seed;
     int32_t lf_rhs_printed;
     double gl_gamma;
+    int32_t gmres_mixed;
 } gx_config;
 
 typedef struct {

@@ -51,6 +51,7 @@ class Config(C.Structure):
         ("seed", C.c_uint64),
         ("lf_rhs_printed", C.c_int32),
         ("gl_gamma", C.c_double),
+        ("gmres_mixed", C.c_int32),
     ]
 
 
@@ -158,7 +159,7 @@ def _stream(stream):
 def make_config(n, dx, *, c=1.0, theta=0.5, dt=0.02, comoving=1, lf_on=1, lf_speed_c=0, lf_beta=1.0, ns_j=0,
                 nsmooth_u=5, gmres_tol=1e-8, gmres_restart=50, gmres_maxit=2000, precond=GX_PRECOND_NONE,
                 track_ids=0, bin_slack=1.6, divb_clean=0, nsmooth_e=0, bc_cells=0,
-                bc_wall=0, seed=0, lf_rhs_printed=0, gl_gamma=0.0) -> Config:
+                bc_wall=0, seed=0, lf_rhs_printed=0, gl_gamma=0.0, gmres_mixed=0) -> Config:
     n = list(n) + [1] * (3 - len(n))
     dx = list(dx) + [1.0] * (3 - len(dx))
     cfg = Config()
@@ -177,6 +178,7 @@ def make_config(n, dx, *, c=1.0, theta=0.5, dt=0.02, comoving=1, lf_on=1, lf_spe
     cfg.seed = int(seed)
     cfg.lf_rhs_printed = int(lf_rhs_printed)
     cfg.gl_gamma = float(gl_gamma)
+    cfg.gmres_mixed = int(gmres_mixed)
     return cfg
 
 
@@ -363,14 +365,14 @@ class Context:
         return L.value
 
 def from_workload(wl, *, track_ids=0, precond=GX_PRECOND_NONE, gmres_tol=None, bin_slack=1.6, gmres_restart=50,
-                  divb_clean=0):
+                  divb_clean=0, gmres_mixed=0):
     """Create a context from a workloads.Workload (inputs copied from host); a
     workload with open boundaries (notes["bc"]) also gets its boundary sources."""
     cfg = make_config(wl.n, wl.dx, c=wl.c, theta=wl.theta, dt=wl.dt, comoving=wl.comoving, lf_on=wl.lf_on,
                       lf_speed_c=wl.lf_speed_c, lf_beta=wl.lf_beta, ns_j=wl.ns_j, nsmooth_u=wl.nsmooth_u,
                       gmres_tol=wl.gmres_tol if gmres_tol is None else gmres_tol, precond=precond,
                       track_ids=track_ids, bin_slack=bin_slack, gmres_restart=gmres_restart,
-                      divb_clean=divb_clean)
+                      divb_clean=divb_clean, gmres_mixed=gmres_mixed)
     bc = wl.notes.get("bc") if isinstance(wl.notes, dict) else None
     if bc:
         cfg.bc_cells, cfg.seed, cfg.bc_wall = int(bc["cells"]), int(bc["seed"]), int(bc.get("wall", 0))

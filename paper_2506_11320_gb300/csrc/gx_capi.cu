@@ -228,6 +228,9 @@ void gx_destroy(gx_ctx *c) {
     for (auto p : dp)
         if (*p) cudaFree(*p);
     if (c->jdiag32) cudaFree(c->jdiag32);
+    float **f32[] = {&c->M32, &c->kappa32, &c->A3f};
+    for (auto p : f32)
+        if (*p) cudaFree(*p);
     if (c->phi) cudaFree(c->phi);
     float4 **fp[] = {&c->nE, &c->nB, &c->nBnext, &c->nUref};
     for (auto p : fp)
@@ -285,6 +288,9 @@ int gx_create(const gx_config *cfg, gx_ctx **out) {
         return fail(GX_EINVAL, "open boundaries without nsmooth_e");
     if (cfg->lf_on && !(cfg->lf_beta >= 0 && cfg->lf_beta < 1e300)) return fail(GX_EINVAL, "lf_beta must be >= 0");
     if (!(cfg->gl_gamma >= 0 && cfg->gl_gamma <= 1)) return fail(GX_EINVAL, "gl_gamma must be in [0, 1]");
+    if (cfg->gmres_mixed != 0 && cfg->gmres_mixed != 1) return fail(GX_EINVAL, "gmres_mixed must be 0 or 1");
+    if (cfg->gmres_mixed && cfg->precond == GX_PRECOND_NET)
+        return fail(GX_EINVAL, "gmres_mixed is not combined with the learned preconditioner");
     if (cfg->gl_gamma > 0 && cfg->bc_cells > 0) return fail(GX_EINVAL, "gl_gamma needs a periodic grid (no bc_cells)");
     if (!(cfg->c < 1e300) || !(cfg->dt < 1e300) || !(cfg->gmres_tol < 1e300) || !(cfg->bin_slack == cfg->bin_slack))
         return fail(GX_EINVAL, "c, dt, gmres_tol and bin_slack must be finite");
@@ -308,6 +314,10 @@ int gx_create(const gx_config *cfg, gx_ctx **out) {
         (rc = dalloc(c, &c->hcol, 2 * (m + 2))) || (rc = dalloc(c, &c->dflags, 1)))
         return fail(rc, nullptr);
     if (cfg->precond != GX_PRECOND_NONE && (rc = dalloc(c, &c->Z, (size_t)m * 3 * N))) return fail(rc, nullptr);
+    if (cfg->gmres_mixed &&
+        (three ? (rc = dalloc(c, &c->A3f, (size_t)243 * N))
+               : ((rc = dalloc(c, &c->M32, (size_t)c->noff * 9 * N)) || (rc = dalloc(c, &c->kappa32, (size_t)nax * 3 * N)))))
+        return fail(rc, nullptr);
     if (cfg->lf_on && (rc = dalloc(c, &c->dBlf, (size_t)(6 + 3 * nax) * N))) return fail(rc, nullptr);   // D, B~, face fluxes
     if (cfg->divb_clean) {
         if ((rc = dalloc(c, &c->phi, N))) return fail(rc, nullptr);

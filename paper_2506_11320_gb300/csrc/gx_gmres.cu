@@ -25,6 +25,7 @@
 // each layer, and the last adds the correction to the block-Jacobi image, so a
 // solve is one launch with every preconditioner.
 #include <cooperative_groups.h>
+#include <type_traits>
 
 #include "gx_netpipe.cuh"
 #include "gx_op.cuh"
@@ -124,6 +125,15 @@ __device__ __forceinline__ const double *pbuf(const CoArgs &a, int ph) {
     return a.part + (size_t)(ph & 1) * kMaxGrid * kPartStride;
 }
 
+// z = D^-1 v at node q from the FP32 inverse (the mixed-precision cycles)
+__device__ __forceinline__ void jacobi_node(const float *jd, const float *v, float *z, int64_t N, int64_t q) {
+    const float *o = jd + (size_t)q * 9;
+    const float x0 = v[q], x1 = v[N + q], x2 = v[2 * N + q];
+    z[q] = o[0] * x0 + o[1] * x1 + o[2] * x2;
+    z[N + q] = o[3] * x0 + o[4] * x1 + o[5] * x2;
+    z[2 * N + q] = o[6] * x0 + o[7] * x1 + o[8] * x2;
+}
+
 // z = D^-1 v at node q (3x3 block)
 __device__ __forceinline__ void jacobi_node(const double *jd, const double *v, double *z, int64_t N, int64_t q) {
     const double *o = jd + (size_t)q * 9;
@@ -181,9 +191,24 @@ __device__ void net_apply(const CoArgs &a, cg::grid_group &grid, int j, unsigned
 }
 
 // NET: the learned preconditioner is applied in the kernel (the plain and
-// Jacobi instantiation is smaller and fits two CTAs per SM)
-template <bool NET, int DIM = 2>
+// Jacobi instantiation is smaller and fits two CTAs per SM).
+// MIX: mixed-precision iterative refinement (Carson and Higham, SIAM J. Sci.
+// Comput. 40, 2018): every restart computes the true residual b - A x and
+// updates x in FP64; the Arnoldi cycle between restarts keeps its basis, the
+// preconditioned vectors and w in FP32 and applies the operator from FP32 copies
+// of M and kappa (3D: of the assembled blocks), while its inner products and
+// norms accumulate in FP64.  A cycle stops once its residual estimate has
+// fallen by kCycleDrop (well above the FP32 floor of the Arnoldi relation), and
+// the next restart judges the FP64 true residual, so the solve still ends at
+// the requested tolerance (the FP32 correction of a cycle is accurate to about
+// kappa(A) 6e-8 of the residual it corrects, far below kCycleDrop for these
+// operators, which are the identity plus positive semi-definite terms scaled by
+// (c theta dt)^2 and the plasma's mass matrix).  GB300 runs FP64 at 1/64 of the FP32 rate: the cycle
+// is where the FP64 solve spent it.
+constexpr double kCycleDrop = 1e-4;
+template <bool NET, int DIM = 2, bool MIX = false>
 __global__ void __launch_bounds__(NET ? kBNet : kB, NET ? 1 : 2) k_fgmres(const __grid_constant__ CoArgs a) {
+    using VT = typename std::conditional<MIX, float, double>::type;   // Krylov storage and arithmetic
     extern __shared__ __align__(128) unsigned char gsm_raw[];
     unsigned char *gsm = gsm_raw + ((128 - (gxt::smem_addr(gsm_raw) & 127)) & 127);
     cg::grid_group grid = cg::this_grid();
@@ -195,8 +220,12 @@ __global__ void __launch_bounds__(NET ? kBNet : kB, NET ? 1 : 2) k_fgmres(const 
     const int64_t N = a.N, n = 3 * N;
     const int m = a.m;
     const bool flex = a.Z != a.V;
+    VT *const V = reinterpret_cast<VT *>(a.V);
+    VT *const Z = reinterpret_cast<VT *>(a.Z);
+    VT *const w = reinterpret_cast<VT *>(a.w);
     int j = st->j, done = st->done, total = st->total, breakdown = st->breakdown;
     double bnorm = st->bnorm;
+    double ctol = a.tol;                            // this cycle's target for the residual estimate
     if (st->finished) return;
     for (int i = threadIdx.x; i < kMaxM; i += blockDim.x) { s_cs[i] = st->cs[i]; s_sn[i] = st->sn[i]; }
     for (int i = threadIdx.x; i <= kMaxM; i += blockDim.x) s_g[i] = st->g[i];
@@ -267,13 +296,18 @@ __global__ void __launch_bounds__(NET ? kBNet : kB, NET ? 1 : 2) k_fgmres(const 
             }
             j = 0;
             done = 0;
+            if (MIX) ctol = fmax(a.tol, relres * kCycleDrop);
             for (int i = threadIdx.x; i <= kMaxM; i += blockDim.x) s_g[i] = i == 0 ? beta : 0.0;
             const double inv = 1.0 / beta;
             NODE_LOOP(q) {
 #pragma unroll
-                for (int c = 0; c < 3; ++c) a.V[c * N + q] = a.r[c * N + q] * inv;
-                if (a.jd && !NET) jacobi_node(a.jd, a.V, a.Z, N, q);
-                if (NET) net_pack_node(a, q, a.V[q], a.V[N + q], a.V[2 * N + q]);
+                for (int c = 0; c < 3; ++c) V[c * N + q] = (VT)(a.r[c * N + q] * inv);
+                if constexpr (MIX) {
+                    if (a.jd) jacobi_node(a.jd32, V, Z, N, q);
+                } else {
+                    if (a.jd && !NET) jacobi_node(a.jd, V, Z, N, q);
+                    if (NET) net_pack_node(a, q, V[q], V[N + q], V[2 * N + q]);
+                }
             }
             __syncthreads();
             if (writer) {
@@ -286,25 +320,25 @@ __global__ void __launch_bounds__(NET ? kBNet : kB, NET ? 1 : 2) k_fgmres(const 
 
         // ---- Arnoldi step j: w = A z_j, two classical Gram-Schmidt passes
         const int k = j + 1;
-        const double *zj = (flex ? a.Z : a.V) + (size_t)j * n;
+        const VT *zj = (flex ? Z : V) + (size_t)j * n;
         // pass 1: w = A z_j, partial h0_i = V_i . w
         for (int i0 = 0; i0 < k; i0 += 8) {
             double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
             NODE_LOOP(q) {
-                double wq[3];
+                VT wq[3];
                 if (i0 == 0) {
-                    gx_apply_node<DIM, true>(a.op, zj, q, wq);
+                    gx_apply_node<DIM, true, VT>(a.op, zj, q, wq);
 #pragma unroll
-                    for (int c = 0; c < 3; ++c) a.w[c * N + q] = wq[c];
+                    for (int c = 0; c < 3; ++c) w[c * N + q] = wq[c];
                 } else {
 #pragma unroll
-                    for (int c = 0; c < 3; ++c) wq[c] = a.w[c * N + q];
+                    for (int c = 0; c < 3; ++c) wq[c] = w[c * N + q];
                 }
 #pragma unroll
                 for (int ii = 0; ii < 8; ++ii)
                     if (i0 + ii < k) {
-                        const double *vi = a.V + (size_t)(i0 + ii) * n;
-                        acc[ii] += vi[q] * wq[0] + vi[N + q] * wq[1] + vi[2 * N + q] * wq[2];
+                        const VT *vi = V + (size_t)(i0 + ii) * n;
+                        acc[ii] += (double)(vi[q] * wq[0] + vi[N + q] * wq[1] + vi[2 * N + q] * wq[2]);
                     }
             }
             cta_partials(acc, min(8, k - i0), sred, prow(a, ph) + i0);
@@ -316,20 +350,20 @@ __global__ void __launch_bounds__(NET ? kBNet : kB, NET ? 1 : 2) k_fgmres(const 
         NODE_LOOP(q) {
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                double v = a.w[c * N + q];
-                for (int i = 0; i < k; ++i) v -= hs[0][i] * a.V[(size_t)i * n + c * N + q];
-                a.w[c * N + q] = v;
+                VT v = w[c * N + q];
+                for (int i = 0; i < k; ++i) v -= (VT)hs[0][i] * V[(size_t)i * n + c * N + q];
+                w[c * N + q] = v;
             }
         }
         for (int i0 = 0; i0 < k; i0 += 8) {
             double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
             NODE_LOOP(q) {
-                const double w0 = a.w[q], w1 = a.w[N + q], w2 = a.w[2 * N + q];
+                const VT w0 = w[q], w1 = w[N + q], w2 = w[2 * N + q];
 #pragma unroll
                 for (int ii = 0; ii < 8; ++ii)
                     if (i0 + ii < k) {
-                        const double *vi = a.V + (size_t)(i0 + ii) * n;
-                        acc[ii] += vi[q] * w0 + vi[N + q] * w1 + vi[2 * N + q] * w2;
+                        const VT *vi = V + (size_t)(i0 + ii) * n;
+                        acc[ii] += (double)(vi[q] * w0 + vi[N + q] * w1 + vi[2 * N + q] * w2);
                     }
             }
             cta_partials(acc, min(8, k - i0), sred, prow(a, ph) + i0);
@@ -343,10 +377,10 @@ __global__ void __launch_bounds__(NET ? kBNet : kB, NET ? 1 : 2) k_fgmres(const 
             NODE_LOOP(q) {
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    double v = a.w[c * N + q];
-                    for (int i = 0; i < k; ++i) v -= hs[1][i] * a.V[(size_t)i * n + c * N + q];
-                    a.w[c * N + q] = v;
-                    acc[0] += v * v;
+                    VT v = w[c * N + q];
+                    for (int i = 0; i < k; ++i) v -= (VT)hs[1][i] * V[(size_t)i * n + c * N + q];
+                    w[c * N + q] = v;
+                    acc[0] += (double)v * (double)v;
                 }
             }
             cta_partials(acc, 1, sred, prow(a, ph));
@@ -386,17 +420,21 @@ __global__ void __launch_bounds__(NET ? kBNet : kB, NET ? 1 : 2) k_fgmres(const 
         total += 1;
         if (hn == 0.0) breakdown = 1;
         const double est = s_scalar[1];
-        const bool ended = est <= a.tol || total >= a.maxit || hn == 0.0 || j + 1 == m;
+        const bool ended = est <= ctol || total >= a.maxit || hn == 0.0 || j + 1 == m;
         if (writer) { st->total = total; st->est = est; st->breakdown = breakdown; }
         if (!ended) {
             // V_{j+1} = w / hn (and its block-Jacobi image)
-            const double inv = 1.0 / hn;
-            double *v1 = a.V + (size_t)(j + 1) * n;
+            const VT inv = (VT)(1.0 / hn);
+            VT *v1 = V + (size_t)(j + 1) * n;
             NODE_LOOP(q) {
 #pragma unroll
-                for (int c = 0; c < 3; ++c) v1[c * N + q] = a.w[c * N + q] * inv;
-                if (a.jd && !NET) jacobi_node(a.jd, v1, a.Z + (size_t)(j + 1) * n, N, q);
-                if (NET) net_pack_node(a, q, v1[q], v1[N + q], v1[2 * N + q]);
+                for (int c = 0; c < 3; ++c) v1[c * N + q] = w[c * N + q] * inv;
+                if constexpr (MIX) {
+                    if (a.jd) jacobi_node(a.jd32, v1, Z + (size_t)(j + 1) * n, N, q);
+                } else {
+                    if (a.jd && !NET) jacobi_node(a.jd, v1, Z + (size_t)(j + 1) * n, N, q);
+                    if (NET) net_pack_node(a, q, v1[q], v1[N + q], v1[2 * N + q]);
+                }
             }
             ++j;
             if (writer) st->j = j;
@@ -414,12 +452,12 @@ __global__ void __launch_bounds__(NET ? kBNet : kB, NET ? 1 : 2) k_fgmres(const 
             }
         }
         __syncthreads();
-        const double *Zb = flex ? a.Z : a.V;
+        const VT *Zb = flex ? Z : V;
         NODE_LOOP(q) {
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 double v = a.x[c * N + q];
-                for (int i = 0; i <= j; ++i) v += s_y[i] * Zb[(size_t)i * n + c * N + q];
+                for (int i = 0; i <= j; ++i) v += s_y[i] * (double)Zb[(size_t)i * n + c * N + q];
                 a.x[c * N + q] = v;
             }
         }
@@ -452,6 +490,12 @@ __global__ void k_norm2(const double *__restrict__ x, int64_t n, double *out) {
         for (int w = 0; w < kWarps; ++w) t += sh[w];
         atomicAdd(out, t);
     }
+}
+
+// FP32 copy of the operator's coefficients for the mixed-precision cycles
+__global__ void k_to_f32(const double *__restrict__ src, float *__restrict__ dst, int64_t n) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+        dst[t] = (float)src[t];
 }
 
 __global__ void k_sub(const double *__restrict__ b, const double *__restrict__ ax, double *r, int64_t n) {
@@ -503,10 +547,14 @@ int gx_fgmres(gx_ctx *c, cudaStream_t st) {
     }
     const bool use_net = pc == GX_PRECOND_NET;
     const size_t smem = use_net ? (size_t)kNetSmemBytes : 0;
-    static int grids[3] = {0, 0, 0};
-    int &grid = grids[c->dim == 3 ? 2 : (use_net ? 1 : 0)];
-    const void *kfn = c->dim == 3 ? (const void *)k_fgmres<false, 3>
-                                  : (use_net ? (const void *)k_fgmres<true> : (const void *)k_fgmres<false>);
+    const bool mix = c->cfg.gmres_mixed && !use_net;
+    static int grids[5] = {0, 0, 0, 0, 0};
+    const int kind = use_net ? 1 : (c->dim == 3 ? (mix ? 4 : 2) : (mix ? 3 : 0));
+    int &grid = grids[kind];
+    const void *kfns[5] = {(const void *)k_fgmres<false>, (const void *)k_fgmres<true>,
+                           (const void *)k_fgmres<false, 3>, (const void *)k_fgmres<false, 2, true>,
+                           (const void *)k_fgmres<false, 3, true>};
+    const void *kfn = kfns[kind];
     if (!grid) {
         int dev = 0, nsm = 0, per = 0;
         GX_CHECK(c, cudaGetDevice(&dev));
@@ -518,6 +566,18 @@ int gx_fgmres(gx_ctx *c, cudaStream_t st) {
     }
     CoArgs a{};
     a.op = gx_opargs(c);
+    if (mix) {
+        // this solve's coefficients in FP32 (the operator changes every step)
+        struct Cv { const double *s; float *d; int64_t n; };
+        const Cv cv[3] = {{a.op.M, c->M32, c->dim == 3 ? 0 : (int64_t)c->noff * 9 * c->N},
+                          {a.op.kappa, c->kappa32, c->dim == 3 ? 0 : (int64_t)2 * 3 * c->N},
+                          {a.op.A3, c->A3f, c->dim == 3 ? (int64_t)243 * c->N : 0}};
+        for (const Cv &e : cv) {
+            if (!e.s || !e.d || e.n == 0) continue;
+            k_to_f32<<<nblocks(e.n), kB, 0, st>>>(e.s, e.d, e.n);
+            GX_LAUNCHED(c);
+        }
+    }
     a.b = c->rhs;
     a.x = c->Eth;
     a.V = c->V;

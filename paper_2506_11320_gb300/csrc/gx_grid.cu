@@ -689,6 +689,9 @@ OpArgs opargs(const gx_ctx *c) {
         a.g3 = G3{c->n[0], c->n[1], c->n[2], c->cfg.dx[0], c->cfg.dx[1], c->cfg.dx[2]};
         a.A3 = c->A3;
     }
+    a.M32 = c->M32;
+    a.kappa32 = c->kappa32;
+    a.A3f = c->A3f;
     return a;
 }
 

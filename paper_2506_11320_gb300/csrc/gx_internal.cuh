@@ -142,6 +142,9 @@ struct gx_ctx {
     double *J = nullptr;                        // [3][N]
     double *M = nullptr;                        // [noff * 9][N] (offset o, alpha entry e at row o * 9 + e)
     double *A3 = nullptr;                       // 3D: the implicit operator as 27 blocks per node [243][N]
+    float *M32 = nullptr;                       // gmres_mixed: FP32 copies of M (2D), kappa (2D) and A3 (3D)
+    float *kappa32 = nullptr;
+    float *A3f = nullptr;
     double *tmp3 = nullptr;                     // [3][N] scratch for filters
     double *uref64 = nullptr;                   // [3][N] FP64 copy of nUref values
     int moments_valid = 0;

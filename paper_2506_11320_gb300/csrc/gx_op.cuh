@@ -63,6 +63,10 @@ struct OpArgs {
     G2 g;
     G3 g3;                 // 3D: the geometry, and
     const double *A3;      // the operator assembled as 27 node blocks [27 * 9][N] (or null in 2D)
+    // FP32 copies for the mixed-precision Krylov cycles (null when not kept)
+    const float *M32;      // 2D: M [81][N]
+    const float *kappa32;  // 2D: kappa [2][3][N]
+    const float *A3f;      // 3D: A3 [243][N]
     double ct2;            // (c theta dt)^2
     double mfac;           // 4 pi theta dt / dV
     double lfx, lfy;       // theta dt / dx, theta dt / dy
@@ -74,63 +78,74 @@ struct OpArgs {
 OpArgs gx_opargs(const gx_ctx *c);
 
 // (A x) at node q, x component-major [3][N].  With CG the neighbourhood of x
-// is read through L2 only (x was written by other CTAs of the same launch).
-template <bool CG = false>
-__device__ __forceinline__ void gx_apply_A_node(const OpArgs &a, const double *__restrict__ x, int64_t q,
-                                                double out[3]) {
+// is read through L2 only (x was written by other CTAs of the same launch).  T
+// = double is the operator; T = float the same operator from the FP32 copies of
+// M and kappa (the mixed-precision Krylov cycles).
+template <bool CG = false, typename T = double>
+__device__ __forceinline__ void gx_apply_A_node(const OpArgs &a, const T *__restrict__ x, int64_t q, T out[3]) {
+    constexpr bool F32 = sizeof(T) == 4;
     const G2 &g = a.g;
     const int64_t N = g.N();
     const int j = (int)((unsigned)q / (unsigned)g.nx), i = (int)q - j * g.nx;
     const int im = gx_wr(i - 1, g.nx), ip = gx_wr(i + 1, g.nx), jm = gx_wr(j - 1, g.ny), jp = gx_wr(j + 1, g.ny);
     const int xs[3] = {im, i, ip};
     const int64_t ys[3] = {(int64_t)jm * g.nx, (int64_t)j * g.nx, (int64_t)jp * g.nx};
-    double v[3][3][3];   // [comp][row y][col x]
+    T v[3][3][3];   // [comp][row y][col x]
 #pragma unroll
     for (int c = 0; c < 3; ++c)
 #pragma unroll
         for (int r = 0; r < 3; ++r)
 #pragma unroll
             for (int s = 0; s < 3; ++s) v[c][r][s] = CG ? __ldcg(x + c * N + ys[r] + xs[s]) : x[c * N + ys[r] + xs[s]];
-    const double hx = g.hx, hy = g.hy;
-    const double hxx = hx * hx, hyy = hy * hy, hxy = hx * hy;
+    const T hx = (T)g.hx, hy = (T)g.hy;
+    const T hxx = hx * hx, hyy = hy * hy, hxy = hx * hy;
+    const T two = (T)2;
     auto Dyy = [&](int c) {
-        const double s0 = v[c][0][0] + 2.0 * v[c][0][1] + v[c][0][2];
-        const double s1 = v[c][1][0] + 2.0 * v[c][1][1] + v[c][1][2];
-        const double s2 = v[c][2][0] + 2.0 * v[c][2][1] + v[c][2][2];
-        return 2.0 * s1 - s0 - s2;
+        const T s0 = v[c][0][0] + two * v[c][0][1] + v[c][0][2];
+        const T s1 = v[c][1][0] + two * v[c][1][1] + v[c][1][2];
+        const T s2 = v[c][2][0] + two * v[c][2][1] + v[c][2][2];
+        return two * s1 - s0 - s2;
     };
     auto Dxx = [&](int c) {
-        const double s0 = v[c][0][0] + 2.0 * v[c][1][0] + v[c][2][0];
-        const double s1 = v[c][0][1] + 2.0 * v[c][1][1] + v[c][2][1];
-        const double s2 = v[c][0][2] + 2.0 * v[c][1][2] + v[c][2][2];
-        return 2.0 * s1 - s0 - s2;
+        const T s0 = v[c][0][0] + two * v[c][1][0] + v[c][2][0];
+        const T s1 = v[c][0][1] + two * v[c][1][1] + v[c][2][1];
+        const T s2 = v[c][0][2] + two * v[c][1][2] + v[c][2][2];
+        return two * s1 - s0 - s2;
     };
     auto Dxy = [&](int c) { return (v[c][0][0] - v[c][0][2]) - (v[c][2][0] - v[c][2][2]); };
-    out[0] = v[0][1][1] + a.ct2 * (hyy * Dyy(0) + hxy * Dxy(1));
-    out[1] = v[1][1][1] + a.ct2 * (hxy * Dxy(0) + hxx * Dxx(1));
-    out[2] = v[2][1][1] + a.ct2 * (hxx * Dxx(2) + hyy * Dyy(2));
-    if (a.M) {
-        double m[3] = {0.0, 0.0, 0.0};
+    const T ct2 = (T)a.ct2;
+    out[0] = v[0][1][1] + ct2 * (hyy * Dyy(0) + hxy * Dxy(1));
+    out[1] = v[1][1][1] + ct2 * (hxy * Dxy(0) + hxx * Dxx(1));
+    out[2] = v[2][1][1] + ct2 * (hxx * Dxx(2) + hyy * Dyy(2));
+    const T *Mp = nullptr;
+    if constexpr (F32) Mp = a.M ? a.M32 : nullptr;
+    else Mp = a.M;
+    if (Mp) {
+        T m[3] = {0, 0, 0};
 #pragma unroll
         for (int o = 0; o < 9; ++o) {
             const int ox = o % 3, oy = o / 3;
 #pragma unroll
             for (int r = 0; r < 3; ++r)
 #pragma unroll
-                for (int e = 0; e < 3; ++e) m[r] = fma(a.M[(size_t)(o * 9 + 3 * r + e) * N + q], v[e][oy][ox], m[r]);
+                for (int e = 0; e < 3; ++e) m[r] = fma(Mp[(size_t)(o * 9 + 3 * r + e) * N + q], v[e][oy][ox], m[r]);
         }
 #pragma unroll
-        for (int r = 0; r < 3; ++r) out[r] = fma(a.mfac, m[r], out[r]);
+        for (int r = 0; r < 3; ++r) out[r] = fma((T)a.mfac, m[r], out[r]);
     }
-    if (a.kappa) {
+    const T *Kp = nullptr;
+    if constexpr (F32) Kp = a.kappa ? a.kappa32 : nullptr;
+    else Kp = a.kappa;
+    if (Kp) {
         const int64_t xm = ys[1] + im, ym = ys[0] + i;
+        const T lfx = (T)a.lfx, lfy = (T)a.lfy;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            const double *kx = a.kappa + (0 * 3 + c) * N, *ky = a.kappa + (1 * 3 + c) * N;
+            const T *kx = Kp + (0 * 3 + c) * N, *ky = Kp + (1 * 3 + c) * N;
             if (g.nx > 1)
-                out[c] -= a.lfx * (kx[q] * (v[c][1][2] - v[c][1][1]) - kx[xm] * (v[c][1][1] - v[c][1][0]));
+                out[c] -= lfx * (kx[q] * (v[c][1][2] - v[c][1][1]) - kx[xm] * (v[c][1][1] - v[c][1][0]));
             if (g.ny > 1)
-                out[c] -= a.lfy * (ky[q] * (v[c][2][1] - v[c][1][1]) - ky[ym] * (v[c][1][1] - v[c][0][1]));
+                out[c] -= lfy * (ky[q] * (v[c][2][1] - v[c][1][1]) - ky[ym] * (v[c][1][1] - v[c][0][1]));
         }
     }
     if (g.bnode(i)) {   // Dirichlet row of an open boundary: E stays at its value
@@ -141,21 +156,23 @@ __device__ __forceinline__ void gx_apply_A_node(const OpArgs &a, const double *_
 
 // 3D: (A x) at node q from the assembled blocks, (A x)_r = sum_o sum_c
 // A3[(o 9 + 3 r + c) N + q] x_c(q + o), o = (ox+1) + 3 (oy+1) + 9 (oz+1).
-template <bool CG = false>
-__device__ __forceinline__ void gx_apply_A3_node(const OpArgs &a, const double *__restrict__ x, int64_t q,
-                                                 double out[3]) {
+template <bool CG = false, typename T = double>
+__device__ __forceinline__ void gx_apply_A3_node(const OpArgs &a, const T *__restrict__ x, int64_t q, T out[3]) {
     const G3 &g = a.g3;
     const int64_t N = g.N();
     int i, j, k;
     g.ijk(q, i, j, k);
-    out[0] = out[1] = out[2] = 0.0;
+    out[0] = out[1] = out[2] = 0;
+    const T *A = nullptr;
+    if constexpr (sizeof(T) == 4) A = a.A3f;
+    else A = a.A3;
 #pragma unroll 3
     for (int o = 0; o < 27; ++o) {
         const int64_t nb = g.id(i + o % 3 - 1, j + (o / 3) % 3 - 1, k + o / 9 - 1);
-        double xv[3];
+        T xv[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) xv[c] = CG ? __ldcg(x + c * N + nb) : x[c * N + nb];
-        const double *blk = a.A3 + (size_t)o * 9 * N + q;
+        const T *blk = A + (size_t)o * 9 * N + q;
 #pragma unroll
         for (int r = 0; r < 3; ++r)
 #pragma unroll
@@ -163,10 +180,9 @@ __device__ __forceinline__ void gx_apply_A3_node(const OpArgs &a, const double *
     }
 }
 
-// the operator of a DIM-dimensional grid at node q
-template <int DIM, bool CG = false>
-__device__ __forceinline__ void gx_apply_node(const OpArgs &a, const double *__restrict__ x, int64_t q,
-                                              double out[3]) {
-    if constexpr (DIM == 3) gx_apply_A3_node<CG>(a, x, q, out);
-    else gx_apply_A_node<CG>(a, x, q, out);
+// the operator of a DIM-dimensional grid at node q (T = float: from the FP32 copies)
+template <int DIM, bool CG = false, typename T = double>
+__device__ __forceinline__ void gx_apply_node(const OpArgs &a, const T *__restrict__ x, int64_t q, T out[3]) {
+    if constexpr (DIM == 3) gx_apply_A3_node<CG, T>(a, x, q, out);
+    else gx_apply_A_node<CG, T>(a, x, q, out);
 }

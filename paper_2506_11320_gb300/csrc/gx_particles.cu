@@ -246,22 +246,55 @@ __global__ void __launch_bounds__(kThreads, Geo<DIM>::CTAS) k_pd(const __grid_co
         const bool wallc = WALL && PUSH && ci == p.wall_ci;   // the wall is this cell's high-x face
         int fbase = 0;                                        // stayers written to this cell's new bin so far
 
+        // the chunk's fields are loaded one chunk ahead (registers), so the loads of
+        // chunk k + 1 are in flight while chunk k is moved and deposited
+        float po[DIM], pv[3], pw = 0.f, pid = 0.f;
+        auto fetch = [&](int c0) {
+            const int i = c0 + lane;
+#pragma unroll
+            for (int d = 0; d < DIM; ++d) po[d] = 0.5f;
+            pv[0] = pv[1] = pv[2] = 0.f;
+            pw = 0.f;
+            if (i < n) {
+                const float *q = bin_in + (i < nfr ? i : p.cap - nbk + (i - nfr));
+#pragma unroll
+                for (int d = 0; d < DIM; ++d) po[d] = __ldcs(q + (size_t)d * p.cap);
+#pragma unroll
+                for (int d = 0; d < 3; ++d) pv[d] = __ldcs(q + (size_t)(PF<DIM>::V + d) * p.cap);
+                pw = __ldcs(q + (size_t)PF<DIM>::W * p.cap);
+                if (PUSH && p.nf > PF<DIM>::ID) pid = __ldcs(q + (size_t)PF<DIM>::ID * p.cap);
+            }
+        };
+        fetch(0);
         for (int c0 = 0; c0 < n; c0 += 32) {
             const int i = c0 + lane;
             const bool valid = i < n;
-            const int slot = i < nfr ? i : p.cap - nbk + (i - nfr);
-            float o[3] = {0.5f, 0.5f, 0.5f}, v[3] = {0.f, 0.f, 0.f}, w = 0.f, idb = 0.f;
-            if (valid) {
-                const float *q = bin_in + slot;
+            float o[3] = {0.5f, 0.5f, 0.5f}, v[3] = {pv[0], pv[1], pv[2]}, w = pw, idb = pid;
 #pragma unroll
-                for (int d = 0; d < DIM; ++d) o[d] = __ldcs(q + (size_t)d * p.cap);
-#pragma unroll
-                for (int d = 0; d < 3; ++d) v[d] = __ldcs(q + (size_t)(PF<DIM>::V + d) * p.cap);
-                w = __ldcs(q + (size_t)PF<DIM>::W * p.cap);
-                if (PUSH && p.nf > PF<DIM>::ID) idb = __ldcs(q + (size_t)PF<DIM>::ID * p.cap);
-            }
+            for (int d = 0; d < DIM; ++d) o[d] = po[d];
+            if (c0 + 32 < n) fetch(c0 + 32);
             if (DIM == 2) o[2] = 0.f;
             bool dep = valid;
+            // a leaver's reservation (destination, its run's lanes and leader, the leader's atomic)
+            bool leaver = false;
+            unsigned peers = 0u;
+            int leader = 0, lold = 0;
+            int64_t dest = 0;
+            auto store_leaver = [&]() {
+                const int old = __shfl_sync(peers, lold, leader);
+                const int back = bin_back(old) + __popc(peers & lt);
+                if (back < p.cap) {
+                    float *dst = p.out + (size_t)dest * p.cap * p.nf + (p.cap - 1 - back);
+#pragma unroll
+                    for (int d = 0; d < DIM; ++d) __stcs(dst + (size_t)d * p.cap, o[d]);
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) __stcs(dst + (size_t)(PF<DIM>::V + d) * p.cap, v[d]);
+                    __stcs(dst + (size_t)PF<DIM>::W * p.cap, w);
+                    if (p.nf > PF<DIM>::ID) __stcs(dst + (size_t)PF<DIM>::ID * p.cap, idb);
+                } else {
+                    atomicExch(&p.flags->overflow, 1);
+                }
+            };
             if (PUSH) {
                 // ---- mover (Eq. 29-30, ECSIM update)
                 float W[NC], E3[3], B3[3];
@@ -312,33 +345,29 @@ __global__ void __launch_bounds__(kThreads, Geo<DIM>::CTAS) k_pd(const __grid_co
                 // ---- re-bin: stayers to the bottom of this cell's new bin, in order
                 const unsigned ms = __ballot_sync(kFull, valid && stay);
                 const unsigned ml = __ballot_sync(kFull, valid && !stay);
-                float *dst = nullptr;
                 if (valid && stay) {
-                    dst = bin_out + fbase + __popc(ms & lt);
-                } else if (valid) {
-                    // leavers: one atomic per (warp, destination) reserves a run at the top of
-                    // the destination bin; each leaver takes its rank within the run
-                    int di = ci + s[0], dj = cj + s[1], dk = ck + s[2];
-                    di = di < 0 ? di + p.n[0] : (di >= p.n[0] ? di - p.n[0] : di);
-                    dj = dj < 0 ? dj + p.n[1] : (dj >= p.n[1] ? dj - p.n[1] : dj);
-                    if (DIM == 3) dk = dk < 0 ? dk + p.n[2] : (dk >= p.n[2] ? dk - p.n[2] : dk);
-                    const int64_t dest = (int64_t)di + (int64_t)p.n[0] * ((int64_t)dj + (int64_t)p.n[1] * dk);
-                    const unsigned peers = __match_any_sync(ml, code);
-                    const int leader = __ffs(peers) - 1;
-                    int old = 0;
-                    if (lane == leader) old = atomicAdd(p.cnt_out + dest, __popc(peers) << 16);
-                    old = __shfl_sync(peers, old, leader);
-                    const int back = bin_back(old) + __popc(peers & lt);
-                    if (back < p.cap) dst = p.out + (size_t)dest * p.cap * p.nf + (p.cap - 1 - back);
-                    else atomicExch(&p.flags->overflow, 1);
-                }
-                if (dst) {
+                    float *dst = bin_out + fbase + __popc(ms & lt);
 #pragma unroll
                     for (int d = 0; d < DIM; ++d) __stcs(dst + (size_t)d * p.cap, o[d]);
 #pragma unroll
                     for (int d = 0; d < 3; ++d) __stcs(dst + (size_t)(PF<DIM>::V + d) * p.cap, v[d]);
                     __stcs(dst + (size_t)PF<DIM>::W * p.cap, w);
                     if (p.nf > PF<DIM>::ID) __stcs(dst + (size_t)PF<DIM>::ID * p.cap, idb);
+                } else if (valid) {
+                    // leavers: one atomic per (warp, destination) reserves a run at the top of
+                    // the destination bin; each leaver takes its rank within the run.  In 3D
+                    // the atomic's result is used after the deposit below, which hides its
+                    // latency (in 2D the registers that keeps live cost more than it saves).
+                    leaver = true;
+                    int di = ci + s[0], dj = cj + s[1], dk = ck + s[2];
+                    di = di < 0 ? di + p.n[0] : (di >= p.n[0] ? di - p.n[0] : di);
+                    dj = dj < 0 ? dj + p.n[1] : (dj >= p.n[1] ? dj - p.n[1] : dj);
+                    if (DIM == 3) dk = dk < 0 ? dk + p.n[2] : (dk >= p.n[2] ? dk - p.n[2] : dk);
+                    dest = (int64_t)di + (int64_t)p.n[0] * ((int64_t)dj + (int64_t)p.n[1] * dk);
+                    peers = __match_any_sync(ml, code);
+                    leader = __ffs(peers) - 1;
+                    if (lane == leader) lold = atomicAdd(p.cnt_out + dest, __popc(peers) << 16);
+                    if (DIM == 2) store_leaver();
                 }
                 fbase += __popc(ms);
                 dep = valid && stay;
@@ -404,6 +433,8 @@ __global__ void __launch_bounds__(kThreads, Geo<DIM>::CTAS) k_pd(const __grid_co
                     }
                 }
             }
+            // ---- 3D leavers: the slot their run reserved
+            if (PUSH && DIM == 3 && leaver) store_leaver();
             __syncwarp();                                    // the table is rewritten by the next chunk
         }
         // the stayers' count (the bottom segment) of this cell's new bin

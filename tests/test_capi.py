@@ -117,6 +117,10 @@ def test_corrupt_configs_are_refused_before_any_device_work(built):
         ("bc_cells", lambda c: setattr(c, "bc_cells", 3), "bc_cells"),
         ("wall", lambda c: setattr(c, "bc_wall", 1), "wall"),
         ("cells", lambda c: (c.n.__setitem__(0, 1 << 16), c.n.__setitem__(1, 1 << 16)), "2^31"),
+        ("gl_gamma", lambda c: setattr(c, "gl_gamma", 1.5), "gl_gamma"),
+        ("gmres_mixed", lambda c: setattr(c, "gmres_mixed", 2), "gmres_mixed"),
+        ("gmres_mixed net", lambda c: (setattr(c, "gmres_mixed", 1), setattr(c, "precond", built.GX_PRECOND_NET)),
+         "gmres_mixed"),
     ]
     for name, corrupt, text in cases:
         cfg = built.make_config((16, 8, 1), (0.1, 0.1, 1.0))
