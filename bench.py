@@ -386,6 +386,7 @@ def main():
     ap.add_argument("--no-precond", action="store_true")
     ap.add_argument("--no-shock", action="store_true")
     ap.add_argument("--no-3d", action="store_true", help="skip the 3D drifting-plasma sweep")
+    ap.add_argument("--n3d", type=int, default=128, help="cells per axis of the 3D drifting plasma")
     ap.add_argument("--sweep3d", default="8,16,32,64,128,256",
                     help="particles per cell and species of the 3D 128^3 sweep")
     ap.add_argument("--precond-workload", default="harris_1024x512",
@@ -487,12 +488,12 @@ def main():
     # ------------------------------------------------------- 3D drifting plasma, 128^3, ppc sweep
     sweep3d = None
     if not args.no_3d:
-        sweep3d = {"workload": "3D periodic drifting Maxwellian plasma, 128^3 cells of 0.1 d_i, u = 0.3 c along x, "
+        sweep3d = {"workload": f"3D periodic drifting Maxwellian plasma, {args.n3d}^3 cells of 0.1 d_i, u = 0.3 c along x, "
                                "vth_e 0.05 c, vth_i 0.01 c, m_i/m_e 25, B = 0.1 along z, comoving current and "
                                "limited LF on, particles drawn on the device",
                    "points": []}
         for ppc in [int(v) for v in args.sweep3d.split(",") if v]:
-            sweep3d["points"].append(run_drift3d(gx, ppc, 1, 3, barrier, dist, world))
+            sweep3d["points"].append(run_drift3d(gx, ppc, 1, 3, barrier, dist, world, n=args.n3d))
 
     # ------------------------------------------------------- end to end (host buffers)
     e2e = None
@@ -528,7 +529,7 @@ def main():
             "gmres_ms_per_step": solve_ms, "gmres_iters_per_step": statistics.mean(iters),
             "wall_ms_per_step": 1000 * wall / args.steps,
             "gmres_learned_vs_plain": solve_cmp,
-            "shock": shock, "shock_wall": shock_wall, "drift3d_128": sweep3d,
+            "shock": shock, "shock_wall": shock_wall, f"drift3d_{args.n3d}": sweep3d,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "gpu_launches": int(tm["launches"]),
         }

@@ -11,8 +11,8 @@
 //     push reads one and writes the other, then they swap;
 //   * deposit records: per species and cell, FP32 partial sums over the cell's
 //     particles (see Rec below), tile-major: entry k of cell c at
-//     rec_index(size, k, c) = ((c / 32) size + k) 32 + c % 32 within the
-//     species' block of ceil(N / 32) 32 size floats; written by the particle
+//     rec_index(size, k, c) = ((c / 8) size + k) 8 + c % 8 within the
+//     species' block of ceil(N / 8) 8 size floats; written by the particle
 //     kernels and folded into the FP64 node moments by the grid kernels;
 //   * mass matrix: FP64 rows [o*9 + e][N], o over the 9 neighbour offsets
 //     (o = (ox+1) + 3 (oy+1)), e the alpha component.
@@ -40,15 +40,18 @@
 //   [REC_J + 3a + i]         sum w (alpha (v - u_ref(x_p)))_i W_a
 //   [REC_M + 9 j + e]        sum w alpha_e P_j          (alpha row-major, e = 3 r + c)
 // The species factors q_s, m_s, beta_s are applied when the records are folded.
-// Tile-major record layout: the 32 consecutive cells of a tile share each
-// entry's 128-byte line, and one cell's whole record lies in the tile's
-// size x 128 bytes.  The particle kernel's warps, which work on consecutive
-// cells at the same time, so fill whole lines together, and the grid kernels'
-// threads, one per node, read consecutive cells' entries as one line.
+// Tile-major record layout: the kRecTile = 8 consecutive cells of a tile share
+// each entry's 32-byte sector, and a tile's records are one contiguous block of
+// size x 32 bytes.  The particle kernel works on the 8 cells of a tile at once
+// (one warp each) and writes the block as whole sectors; the grid kernels'
+// threads, one per node, read consecutive cells' entries as whole sectors.
+constexpr int kRecTile = 8;
 __host__ __device__ inline size_t rec_index(int size, int k, int64_t cell) {
-    return ((size_t)(cell >> 5) * size + k) * 32 + (size_t)(cell & 31);
+    return ((size_t)(cell >> 3) * size + k) * kRecTile + (size_t)(cell & 7);
 }
-__host__ __device__ inline size_t rec_block(int size, int64_t N) { return (size_t)((N + 31) >> 5) * size * 32; }
+__host__ __device__ inline size_t rec_block(int size, int64_t N) {
+    return (size_t)((N + kRecTile - 1) / kRecTile) * size * kRecTile;
+}
 
 template <int DIM> struct Rec;
 template <> struct Rec<2> {

@@ -57,14 +57,15 @@ constexpr unsigned kFull = 0xffffffffu;
 // lanes per particle group (RG x 4 column quads), KG groups
 template <int DIM> struct Geo;
 template <> struct Geo<2> {
-    static constexpr int NC = 4, ROWS = 9, TSTR = 28, COLOFF = 12, LK = 4, KG = 8, CENTER = 4, CTAS = 3;
+    static constexpr int NC = 4, ROWS = 9, TSTR = 28, COLOFF = 12, LK = 4, KG = 8, CENTER = 4, CTAS = 2;
 };
 template <> struct Geo<3> {
     static constexpr int NC = 8, ROWS = 27, TSTR = 52, COLOFF = 36, LK = 12, KG = 2, CENTER = 13, CTAS = 2;
 };
-// shared floats per warp: corner values [4][NC] float4, then the factor table
-// [32][TSTR], which at the end of a cell holds the groups' sums [KG][ROWS][16]
-// followed by the species-free column totals [7][ROWS]
+// shared floats per warp: the cell's interpolation coefficients [4][NC] float4,
+// then the factor table [32][TSTR], which at the end of a cell holds the groups'
+// sums [KG][ROWS][16] followed by their totals [ROWS][16]; after the warps, the
+// CTA's two record-tile stages
 template <int DIM>
 __host__ __device__ constexpr int table_floats() {
     return 32 * Geo<DIM>::TSTR > (Geo<DIM>::KG + 1) * Geo<DIM>::ROWS * kCols
@@ -77,8 +78,9 @@ __host__ __device__ constexpr int warp_floats() {
 }
 template <int DIM>
 constexpr size_t pd_smem_bytes() {
-    return (size_t)kWarpsPerCta * warp_floats<DIM>() * sizeof(float);
+    return ((size_t)kWarpsPerCta * warp_floats<DIM>() + 2 * (size_t)Rec<DIM>::SIZE * kRecTile) * sizeof(float);
 }
+static_assert(kWarpsPerCta == kRecTile, "one warp per cell of a record tile");
 
 // field indices of a slot
 template <int DIM> struct PF {
@@ -107,9 +109,20 @@ struct PD {
 };
 
 // ------------------------------------------------------------ helpers
+// 1 / x for 1 <= x < 2^126: the PTX approximate reciprocal (rcp.approx.ftz,
+// within about 1 ulp) refined by one Newton-Raphson step r + r (1 - x r), which
+// squares its relative error, so the result is within about 1 ulp of 1 / x.
+// The mover's v^{n+1} feeds the comoving current alpha (v - u_ref), a small
+// difference of large terms, so an unrefined approximation shows there.
+__device__ __forceinline__ float recip_nr(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return fmaf(r, fmaf(-x, r, 1.0f), r);
+}
+
 // alpha (Eq. 30) with b = beta B / c, row-major: alpha a = (a + a x b + (a.b) b)/(1 + b.b)
 __device__ __forceinline__ void alpha_tensor(float bx, float by, float bz, float al[9]) {
-    const float inv = __frcp_rn(1.0f + bx * bx + by * by + bz * bz);
+    const float inv = recip_nr(fmaf(bx, bx, fmaf(by, by, fmaf(bz, bz, 1.0f))));
     al[0] = (1.0f + bx * bx) * inv; al[1] = (bz + bx * by) * inv; al[2] = (bx * bz - by) * inv;
     al[3] = (by * bx - bz) * inv;   al[4] = (1.0f + by * by) * inv; al[5] = (bx + by * bz) * inv;
     al[6] = (by + bz * bx) * inv;   al[7] = (bz * by - bx) * inv; al[8] = (1.0f + bz * bz) * inv;
@@ -154,30 +167,49 @@ __device__ __forceinline__ void gather(const float4 *f, const float W[Geo<DIM>::
     }
 }
 
-// record entry k of a cell from the groups' sums S[kg][j][16] (pair class j,
-// column c) and the totals U[c - 9][j] of the columns 9..15 over the groups
+// The multilinear interpolant sum_a W_a(o) f_a of a cell's corner values, as
+// the polynomial sum_S c_S prod_{d in S} o_d over the subsets S of the axes
+// (c_S the coefficient of corner index S: c_0 = f_0, c_1 = f_1 - f_0, ...,
+// the Moebius transform of the corner values over the bits of the corner
+// index).  interp evaluates its x, y, z components by Horner steps, grad_w the
+// gradient of its w component with respect to o.
 template <int DIM>
-__device__ __forceinline__ float record_entry(const float *S, const float *U, int k) {
-    using R = Rec<DIM>;
-    using G = Geo<DIM>;
-    if (k >= R::USED) return 0.f;
-    if (k >= R::M) {                                          // M entry (j, e): the alpha column e
-        const int t = k - R::M, j = t / 9, e = t - 9 * j;
-        float s = 0.f;
-#pragma unroll
-        for (int g = 0; g < G::KG; ++g) s += S[(g * G::ROWS + j) * kCols + e];
-        return s;
+__device__ __forceinline__ void interp(const float4 *c, const float o[3], float out[3]) {
+    const float4 c0 = c[0], c1 = c[1], c2 = c[2], c3 = c[3];
+    out[0] = fmaf(o[1], fmaf(o[0], c3.x, c2.x), fmaf(o[0], c1.x, c0.x));
+    out[1] = fmaf(o[1], fmaf(o[0], c3.y, c2.y), fmaf(o[0], c1.y, c0.y));
+    out[2] = fmaf(o[1], fmaf(o[0], c3.z, c2.z), fmaf(o[0], c1.z, c0.z));
+    if constexpr (DIM == 3) {
+        const float4 c4 = c[4], c5 = c[5], c6 = c[6], c7 = c[7];
+        out[0] = fmaf(o[2], fmaf(o[1], fmaf(o[0], c7.x, c6.x), fmaf(o[0], c5.x, c4.x)), out[0]);
+        out[1] = fmaf(o[2], fmaf(o[1], fmaf(o[0], c7.y, c6.y), fmaf(o[0], c5.y, c4.y)), out[1]);
+        out[2] = fmaf(o[2], fmaf(o[1], fmaf(o[0], c7.z, c6.z), fmaf(o[0], c5.z, c4.z)), out[2]);
     }
-    int a, col;
-    if (k < R::MV) { a = k; col = 0; }
-    else if (k < R::J) { const int t = k - R::MV; a = t / 3; col = 1 + t - 3 * a; }
-    else { const int t = k - R::J; a = t / 3; col = 4 + t - 3 * a; }
-    const float *u = U + col * G::ROWS;
-    const int j0 = (a & 1) + 3 * ((a >> 1) & 1) + 9 * ((a >> 2) & 1);
-    float s = 0.f;
+}
+template <int DIM>
+__device__ __forceinline__ void grad_w(const float4 *c, const float o[3], float g[3]) {
+    if constexpr (DIM == 2) {
+        g[0] = fmaf(o[1], c[3].w, c[1].w);
+        g[1] = fmaf(o[0], c[3].w, c[2].w);
+        g[2] = 0.f;
+    } else {
+        g[0] = fmaf(o[2], fmaf(o[1], c[7].w, c[5].w), fmaf(o[1], c[3].w, c[1].w));
+        g[1] = fmaf(o[2], fmaf(o[0], c[7].w, c[6].w), fmaf(o[0], c[3].w, c[2].w));
+        g[2] = fmaf(o[1], fmaf(o[0], c[7].w, c[6].w), fmaf(o[0], c[5].w, c[4].w));
+    }
+}
+
+// corner a's coefficient from the corner values held by the lanes of its array
+// (lanes a ^ (1 << d) within the NC-lane group); every lane of the warp calls it
+template <int DIM>
+__device__ __forceinline__ float4 to_coef(float4 v, int a) {
 #pragma unroll
-    for (int t = 0; t < G::NC; ++t) s += u[j0 + (t & 1) + 3 * ((t >> 1) & 1) + 9 * ((t >> 2) & 1)];
-    return s;
+    for (int d = 0; d < DIM; ++d) {
+        const float qx = __shfl_xor_sync(kFull, v.x, 1 << d), qy = __shfl_xor_sync(kFull, v.y, 1 << d);
+        const float qz = __shfl_xor_sync(kFull, v.z, 1 << d), qw = __shfl_xor_sync(kFull, v.w, 1 << d);
+        if ((a >> d) & 1) { v.x -= qx; v.y -= qy; v.z -= qz; v.w -= qw; }
+    }
+    return v;
 }
 
 __device__ __forceinline__ int64_t node_of(const int n[3], int i, int j, int k) {
@@ -187,7 +219,50 @@ __device__ __forceinline__ int64_t node_of(const int n[3], int i, int j, int k) 
     return (int64_t)i + (int64_t)n[0] * ((int64_t)j + (int64_t)n[1] * k);
 }
 
+// lane < 4 NC: corner a = lane % NC of array lane / NC (mover E, mover B,
+// deposit B, u_ref) of cell (ci, cj, ck); the deposit pass needs arrays 2, 3 only
+template <int DIM, bool PUSH>
+__device__ __forceinline__ float4 load_corner(const PD &p, int lane, int ci, int cj, int ck) {
+    constexpr int NC = Geo<DIM>::NC;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int arr = lane / NC, a = lane % NC;
+    if (lane < 4 * NC && (PUSH || arr >= 2)) {
+        const int64_t nd = node_of(p.n, ci + (a & 1), cj + ((a >> 1) & 1), ck + ((a >> 2) & 1));
+        const float4 *src = arr == 0 ? p.mE : arr == 1 ? p.mB : arr == 2 ? p.dB : p.dU;
+        v = __ldg(src + nd);
+    }
+    return v;
+}
+
+// record entry k of a cell from the group-summed pair-class sums Gs[j][16]
+// (pair class j, column c: alpha 0..8, 1, v 10..12, alpha (v - u_ref) 13..15)
+template <int DIM>
+__device__ __forceinline__ float record_value(const float *Gs, int k) {
+    using R = Rec<DIM>;
+    using G = Geo<DIM>;
+    if (k >= R::USED) return 0.f;
+    if (k >= R::M) {                                          // M entry (j, e): the alpha column e
+        const int t = k - R::M, j = t / 9, e = t - 9 * j;
+        return Gs[j * kCols + e];
+    }
+    int a, col;
+    if (k < R::MV) { a = k; col = 9; }
+    else if (k < R::J) { const int t = k - R::MV; a = t / 3; col = 10 + t - 3 * a; }
+    else { const int t = k - R::J; a = t / 3; col = 13 + t - 3 * a; }
+    // W_a = prod_d (X_0 + X_1 or X_1 + X_2): the 2^d pair classes j0 + (bits of t)
+    const int j0 = (a & 1) + 3 * ((a >> 1) & 1) + 9 * ((a >> 2) & 1);
+    float s = 0.f;
+#pragma unroll
+    for (int t = 0; t < G::NC; ++t) s += Gs[(j0 + (t & 1) + 3 * ((t >> 1) & 1) + 9 * ((t >> 2) & 1)) * kCols + col];
+    return s;
+}
+
 // ------------------------------------------------------------ fused kernel
+// A CTA's 8 warps take the 8 cells of a record tile (one cell each), tiles
+// strided over the persistent grid; the tile's records are staged in shared
+// memory and written (or, for the arrivals, added) as one contiguous block.
+// Every warp prefetches the next tile's cell: its count and corner values at the
+// start of a cell, its first chunk of particles with the last chunk of the cell.
 // WALL: the push reflects particles at the high-x face of cell x index
 // p.wall_ci (a reflecting wall); a separate instantiation, so that the push
 // without a wall compiles exactly as it would without the feature
@@ -196,11 +271,13 @@ __global__ void __launch_bounds__(kThreads, Geo<DIM>::CTAS) k_pd(const __grid_co
     using G = Geo<DIM>;
     using R = Rec<DIM>;
     constexpr int NC = G::NC;
+    constexpr int TILE = R::SIZE * kRecTile;                 // floats of a tile's record block
     extern __shared__ __align__(16) float smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float *ws = smem + (size_t)warp * warp_floats<DIM>();
-    float4 *cor = reinterpret_cast<float4 *>(ws);            // [4][NC]: mover E, mover B, deposit B, u_ref
-    float *T = ws + 16 * NC;                                  // factor table [32][TSTR]; at a cell's end the sums [lane][36]
+    float4 *cor = reinterpret_cast<float4 *>(ws);            // [4][NC] coefficients: mover E, mover B, deposit B, u_ref
+    float *T = ws + 16 * NC;                                  // factor table [32][TSTR]; at a cell's end the sums
+    float *stage = smem + (size_t)kWarpsPerCta * warp_floats<DIM>();   // [2][TILE]
     const unsigned lt = (1u << lane) - 1u;
     // this lane's block and particle group: group kg walks the particles
     // KG s + pg; in 2D the two groups of a quarter warp take particles 4 apart,
@@ -210,27 +287,67 @@ __global__ void __launch_bounds__(kThreads, Geo<DIM>::CTAS) k_pd(const __grid_co
     const int pg = DIM == 2 ? (kg >> 1) + 4 * (kg & 1) : kg;
     const int roff = 12 * (lk / 4), coff = G::COLOFF + 4 * (lk % 4);
     const bool res[3] = {p.n[0] > 1, p.n[1] > 1, DIM == 3 && p.n[2] > 1};
-    const int64_t nwarps = (int64_t)gridDim.x * kWarpsPerCta;
-    // cell coordinates, stepped by the warp stride without divisions (cells < 2^31)
-    const unsigned c0u = blockIdx.x * kWarpsPerCta + warp, nwu = (unsigned)nwarps;
+    const int64_t ntiles = (p.N + kRecTile - 1) / kRecTile;
+    const int64_t cstride = (int64_t)p.cap * p.nf;           // floats per bin
+    // this warp's cell in its first tile and its coordinates, stepped by the warp's
+    // cell stride without divisions (cells < 2^31)
     const unsigned nx = (unsigned)p.n[0], ny = (unsigned)p.n[1];
-    int ci = (int)(c0u % nx), cj = (int)((c0u / nx) % ny), ck = (int)(c0u / nx / ny);
-    const int si = (int)(nwu % nx), sj = (int)((nwu / nx) % ny), sk = (int)(nwu / nx / ny);
+    const unsigned cs = gridDim.x * (unsigned)kRecTile;
+    int64_t cell = (int64_t)blockIdx.x * kRecTile + warp;
+    int ci, cj, ck;
+    {
+        const unsigned c0u = (unsigned)cell;
+        ci = (int)(c0u % nx); cj = (int)((c0u / nx) % ny); ck = (int)(c0u / nx / ny);
+    }
+    const int si = (int)(cs % nx), sj = (int)((cs / nx) % ny), sk = (int)(cs / nx / ny);
+    // scale of this lane's corner array: beta E (w: phi), beta / c B, beta / c B, u_ref
+    const int carr = lane / NC, ca = lane % NC;
+    const float csc = carr == 0 ? p.beta : (carr == 3 ? 1.f : p.bc);
 
-    for (int64_t cell = c0u; cell < p.N; cell += nwarps, ci += si, cj += sj, ck += sk) {
-        if (ci >= p.n[0]) { ci -= p.n[0]; ++cj; }
-        if (cj >= p.n[1]) { cj -= p.n[1]; ++ck; }
-        const int word = seg_word(__ldg(p.cnt_in + cell), p.cap, p.arrivals);
-        const int nfr = bin_front(word), nbk = bin_back(word), n = nfr + nbk;
-        if (p.arrivals && n == 0) continue;
-        __syncwarp();                                         // the previous cell's reads of cor and S are done
-        if (lane < 4 * NC) {
-            const int arr = lane / NC, a = lane % NC;
-            if (PUSH || arr >= 2) {
-                const int64_t nd = node_of(p.n, ci + (a & 1), cj + ((a >> 1) & 1), ck + ((a >> 2) & 1));
-                const float4 *src = arr == 0 ? p.mE : arr == 1 ? p.mB : arr == 2 ? p.dB : p.dU;
-                cor[lane] = __ldg(src + nd);
-            }
+    int wcur = cell < p.N ? seg_word(__ldg(p.cnt_in + cell), p.cap, p.arrivals) : 0;
+    float4 ccur = cell < p.N ? load_corner<DIM, PUSH>(p, lane, ci, cj, ck) : make_float4(0.f, 0.f, 0.f, 0.f);
+
+    // the next chunk's fields (registers): loaded one chunk ahead, across cells
+    float po[DIM], pv[3], pw = 0.f, pid = 0.f;
+    auto fetch = [&](const float *bin, int word, int c0) {
+        const int nf_ = bin_front(word), nb_ = bin_back(word);
+        const int i = c0 + lane;
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) po[d] = 0.5f;
+        pv[0] = pv[1] = pv[2] = 0.f;
+        pw = 0.f;
+        if (i < nf_ + nb_) {
+            const float *q = bin + (i < nf_ ? i : p.cap - nb_ + (i - nf_));
+#pragma unroll
+            for (int d = 0; d < DIM; ++d) po[d] = __ldcs(q + (size_t)d * p.cap);
+#pragma unroll
+            for (int d = 0; d < 3; ++d) pv[d] = __ldcs(q + (size_t)(PF<DIM>::V + d) * p.cap);
+            pw = __ldcs(q + (size_t)PF<DIM>::W * p.cap);
+            if (PUSH && p.nf > PF<DIM>::ID) pid = __ldcs(q + (size_t)PF<DIM>::ID * p.cap);
+        }
+    };
+    if (cell < p.N) fetch(p.in + cell * cstride, wcur, 0);
+
+    int it = 0;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+        // the next tile's cell of this warp: count and corners now, first chunk later
+        const int64_t ncell = cell + cs;
+        int nci = ci + si, ncj = cj + sj, nck = ck + sk;
+        if (nci >= p.n[0]) { nci -= p.n[0]; ++ncj; }
+        if (ncj >= p.n[1]) { ncj -= p.n[1]; ++nck; }
+        const bool has_next = ncell < p.N;
+        const int wnext = has_next ? seg_word(__ldg(p.cnt_in + ncell), p.cap, p.arrivals) : 0;
+        const float4 cnext =
+            has_next ? load_corner<DIM, PUSH>(p, lane, nci, ncj, nck) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float *bin_nx = p.in + ncell * cstride;
+
+        const int nfr = bin_front(wcur), nbk = bin_back(wcur), n = nfr + nbk;
+        __syncwarp();                                         // the previous cell's reads of cor and T are done
+        {
+            float4 v = ccur;
+            v.x *= csc; v.y *= csc; v.z *= csc;
+            v = to_coef<DIM>(v, ca);
+            if (lane < 4 * NC) cor[lane] = v;
         }
         __syncwarp();
         float2 accp[4][4];                                    // [column][row pair]: rows 0..7 of the block
@@ -241,38 +358,18 @@ __global__ void __launch_bounds__(kThreads, Geo<DIM>::CTAS) k_pd(const __grid_co
 #pragma unroll
             for (int r = 0; r < 4; ++r) accp[c][r] = make_float2(0.f, 0.f);
         }
-        const float *bin_in = p.in + (size_t)cell * p.cap * p.nf;
-        float *bin_out = PUSH ? p.out + (size_t)cell * p.cap * p.nf : nullptr;
+        float *bin_out = PUSH ? p.out + cell * cstride : nullptr;
         const bool wallc = WALL && PUSH && ci == p.wall_ci;   // the wall is this cell's high-x face
         int fbase = 0;                                        // stayers written to this cell's new bin so far
 
-        // the chunk's fields are loaded one chunk ahead (registers), so the loads of
-        // chunk k + 1 are in flight while chunk k is moved and deposited
-        float po[DIM], pv[3], pw = 0.f, pid = 0.f;
-        auto fetch = [&](int c0) {
-            const int i = c0 + lane;
-#pragma unroll
-            for (int d = 0; d < DIM; ++d) po[d] = 0.5f;
-            pv[0] = pv[1] = pv[2] = 0.f;
-            pw = 0.f;
-            if (i < n) {
-                const float *q = bin_in + (i < nfr ? i : p.cap - nbk + (i - nfr));
-#pragma unroll
-                for (int d = 0; d < DIM; ++d) po[d] = __ldcs(q + (size_t)d * p.cap);
-#pragma unroll
-                for (int d = 0; d < 3; ++d) pv[d] = __ldcs(q + (size_t)(PF<DIM>::V + d) * p.cap);
-                pw = __ldcs(q + (size_t)PF<DIM>::W * p.cap);
-                if (PUSH && p.nf > PF<DIM>::ID) pid = __ldcs(q + (size_t)PF<DIM>::ID * p.cap);
-            }
-        };
-        fetch(0);
         for (int c0 = 0; c0 < n; c0 += 32) {
             const int i = c0 + lane;
             const bool valid = i < n;
             float o[3] = {0.5f, 0.5f, 0.5f}, v[3] = {pv[0], pv[1], pv[2]}, w = pw, idb = pid;
 #pragma unroll
             for (int d = 0; d < DIM; ++d) o[d] = po[d];
-            if (c0 + 32 < n) fetch(c0 + 32);
+            if (c0 + 32 < n) fetch(p.in + cell * cstride, wcur, c0 + 32);
+            else if (has_next) fetch(bin_nx, wnext, 0);
             if (DIM == 2) o[2] = 0.f;
             bool dep = valid;
             // a leaver's reservation (destination, its run's lanes and leader, the leader's atomic)
@@ -284,7 +381,7 @@ __global__ void __launch_bounds__(kThreads, Geo<DIM>::CTAS) k_pd(const __grid_co
                 const int old = __shfl_sync(peers, lold, leader);
                 const int back = bin_back(old) + __popc(peers & lt);
                 if (back < p.cap) {
-                    float *dst = p.out + (size_t)dest * p.cap * p.nf + (p.cap - 1 - back);
+                    float *dst = p.out + dest * cstride + (p.cap - 1 - back);
 #pragma unroll
                     for (int d = 0; d < DIM; ++d) __stcs(dst + (size_t)d * p.cap, o[d]);
 #pragma unroll
@@ -296,33 +393,23 @@ __global__ void __launch_bounds__(kThreads, Geo<DIM>::CTAS) k_pd(const __grid_co
                 }
             };
             if (PUSH) {
-                // ---- mover (Eq. 29-30, ECSIM update)
-                float W[NC], E3[3], B3[3];
-                corner_weights<DIM>(o, W);
-                gather<DIM>(cor, W, E3);
-                gather<DIM>(cor + NC, W, B3);
-                const float bx = p.bc * B3[0], by = p.bc * B3[1], bz = p.bc * B3[2];
+                // ---- mover (Eq. 29-30, ECSIM update): e = beta E^{n+theta}, b = beta B^n / c
+                float e3[3], b3[3];
+                interp<DIM>(cor, o, e3);
+                interp<DIM>(cor + NC, o, b3);
+                const float bx = b3[0], by = b3[1], bz = b3[2];
                 // a = v + beta E ; vbar = (a + a x b + (a.b) b) / (1 + b.b)
-                const float ax = fmaf(p.beta, E3[0], v[0]), ay = fmaf(p.beta, E3[1], v[1]), az = fmaf(p.beta, E3[2], v[2]);
-                const float inv = __frcp_rn(1.0f + bx * bx + by * by + bz * bz);
+                const float ax = v[0] + e3[0], ay = v[1] + e3[1], az = v[2] + e3[2];
+                const float inv = recip_nr(fmaf(bx, bx, fmaf(by, by, fmaf(bz, bz, 1.0f))));
                 const float ab = ax * bx + ay * by + az * bz;
                 const float vbx = (ax + (ay * bz - az * by) + ab * bx) * inv;
                 const float vby = (ay + (az * bx - ax * bz) + ab * by) * inv;
                 const float vbz = (az + (ax * by - ay * bx) + ab * bz) * inv;
                 v[0] = 2.f * vbx - v[0]; v[1] = 2.f * vby - v[1]; v[2] = 2.f * vbz - v[2];
-                // Gauss's-law correction: gamma eps q w grad phi at x^{n+1/2}, in cell
-                // units (d W_a / d o_d = +-1 times the other axes' linear factors)
+                // Gauss's-law correction: gamma eps q w grad phi at x^{n+1/2}, in cell units
                 float gd[3] = {0.f, 0.f, 0.f};
                 if (p.glon) {
-#pragma unroll
-                    for (int a = 0; a < NC; ++a) {
-                        const float ph = cor[a].w;
-                        const float fx = (a & 1) ? o[0] : 1.f - o[0], fy = (a & 2) ? o[1] : 1.f - o[1];
-                        const float fz = DIM == 3 ? ((a & 4) ? o[2] : 1.f - o[2]) : 1.f;
-                        gd[0] += ((a & 1) ? ph : -ph) * fy * fz;
-                        gd[1] += ((a & 2) ? ph : -ph) * fx * fz;
-                        if (DIM == 3) gd[2] += ((a & 4) ? ph : -ph) * fx * fy;
-                    }
+                    grad_w<DIM>(cor, o, gd);
 #pragma unroll
                     for (int d = 0; d < 3; ++d) gd[d] *= p.gl[d] * w;
                 }
@@ -363,7 +450,7 @@ __global__ void __launch_bounds__(kThreads, Geo<DIM>::CTAS) k_pd(const __grid_co
                     di = di < 0 ? di + p.n[0] : (di >= p.n[0] ? di - p.n[0] : di);
                     dj = dj < 0 ? dj + p.n[1] : (dj >= p.n[1] ? dj - p.n[1] : dj);
                     if (DIM == 3) dk = dk < 0 ? dk + p.n[2] : (dk >= p.n[2] ? dk - p.n[2] : dk);
-                    dest = (int64_t)di + (int64_t)p.n[0] * ((int64_t)dj + (int64_t)p.n[1] * dk);
+                    dest = (int64_t)(di + p.n[0] * (dj + p.n[1] * dk));
                     peers = __match_any_sync(ml, code);
                     leader = __ffs(peers) - 1;
                     if (lane == leader) lold = atomicAdd(p.cnt_out + dest, __popc(peers) << 16);
@@ -372,13 +459,13 @@ __global__ void __launch_bounds__(kThreads, Geo<DIM>::CTAS) k_pd(const __grid_co
                 fbase += __popc(ms);
                 dep = valid && stay;
             }
-            // ---- deposit factors of this lane's particle (zero rows if it does not deposit)
+            // ---- deposit factors of this lane's particle (zero rows if it does not deposit):
+            // b = beta B^{n+1} / c and u_ref at the particle
             {
-                float W[NC], B3[3], U3[3], al[9];
-                corner_weights<DIM>(o, W);
-                gather<DIM>(cor + 2 * NC, W, B3);
-                gather<DIM>(cor + 3 * NC, W, U3);
-                alpha_tensor(p.bc * B3[0], p.bc * B3[1], p.bc * B3[2], al);
+                float b3[3], U3[3], al[9];
+                interp<DIM>(cor + 2 * NC, o, b3);
+                interp<DIM>(cor + 3 * NC, o, U3);
+                alpha_tensor(b3[0], b3[1], b3[2], al);
                 const float d0 = v[0] - U3[0], d1 = v[1] - U3[1], d2 = v[2] - U3[2];
                 const float wd = dep ? w : 0.f;
                 float X[3][3];
@@ -437,39 +524,266 @@ __global__ void __launch_bounds__(kThreads, Geo<DIM>::CTAS) k_pd(const __grid_co
             if (PUSH && DIM == 3 && leaver) store_leaver();
             __syncwarp();                                    // the table is rewritten by the next chunk
         }
+        if (n == 0 && has_next) fetch(bin_nx, wnext, 0);
         // the stayers' count (the bottom segment) of this cell's new bin
         if (PUSH && lane == 0 && fbase > 0) atomicAdd(p.cnt_out + cell, fbase);
-        // the groups' sums: S[kg][pair class][column], this lane's 9 x 4 block
-        if (role) {
-            float4 *sd = reinterpret_cast<float4 *>(T + (kg * G::ROWS + 9 * (lk / 4)) * kCols + 4 * (lk % 4));
+        float *st = stage + (size_t)(it & 1) * TILE;
+        if (n > 0) {
+            // the groups' sums: S[kg][pair class][column], this lane's 9 x 4 block
+            if (role) {
+                float4 *sd = reinterpret_cast<float4 *>(T + (kg * G::ROWS + 9 * (lk / 4)) * kCols + 4 * (lk % 4));
 #pragma unroll
-            for (int ip = 0; ip < 4; ++ip) {
-                sd[(2 * ip) * (kCols / 4)] = make_float4(accp[0][ip].x, accp[1][ip].x, accp[2][ip].x, accp[3][ip].x);
-                sd[(2 * ip + 1) * (kCols / 4)] = make_float4(accp[0][ip].y, accp[1][ip].y, accp[2][ip].y, accp[3][ip].y);
+                for (int ip = 0; ip < 4; ++ip) {
+                    sd[(2 * ip) * (kCols / 4)] = make_float4(accp[0][ip].x, accp[1][ip].x, accp[2][ip].x, accp[3][ip].x);
+                    sd[(2 * ip + 1) * (kCols / 4)] =
+                        make_float4(accp[0][ip].y, accp[1][ip].y, accp[2][ip].y, accp[3][ip].y);
+                }
+                sd[8 * (kCols / 4)] = make_float4(acc8[0], acc8[1], acc8[2], acc8[3]);
             }
-            sd[8 * (kCols / 4)] = make_float4(acc8[0], acc8[1], acc8[2], acc8[3]);
-        }
-        __syncwarp();
-        // totals over the groups of the columns 1, v, alpha (v - u_ref): U[c - 9][j]
-        float *U = T + G::KG * G::ROWS * kCols;
-        for (int t = lane; t < 7 * G::ROWS; t += 32) {
-            const int c = t / G::ROWS, j = t - c * G::ROWS;
-            float v = 0.f;
+            __syncwarp();
+            // totals over the groups, Gs[pair class][column], one column quad per lane and item
+            float *Gs = T + G::KG * G::ROWS * kCols;
+            for (int item = lane; item < G::ROWS * 4; item += 32) {
+                const int j = item >> 2, q = item & 3;
+                float4 s4 = *reinterpret_cast<const float4 *>(T + j * kCols + 4 * q);
 #pragma unroll
-            for (int g = 0; g < G::KG; ++g) v += T[(g * G::ROWS + j) * kCols + 9 + c];
-            U[t] = v;
+                for (int g = 1; g < G::KG; ++g) {
+                    const float4 u = *reinterpret_cast<const float4 *>(T + (g * G::ROWS + j) * kCols + 4 * q);
+                    s4.x += u.x; s4.y += u.y; s4.z += u.z; s4.w += u.w;
+                }
+                *reinterpret_cast<float4 *>(Gs + j * kCols + 4 * q) = s4;
+            }
+            __syncwarp();
+            for (int k = lane; k < R::SIZE; k += 32) st[k * kRecTile + warp] = record_value<DIM>(Gs, k);
+        } else {
+            for (int k = lane; k < R::SIZE; k += 32) st[k * kRecTile + warp] = 0.f;
         }
-        __syncwarp();
-        // the cell's record
-        for (int k = lane; k < R::SIZE; k += 32) {
-            const float val = record_entry<DIM>(T, U, k);
-            float *dst = p.rec + rec_index(R::SIZE, k, cell);
-            if (p.arrivals) {
-                if (val != 0.f) atomicAdd(dst, val);
-            } else {
-                *dst = val;
+        // ---- the tile's record block: written whole (or added, for the arrivals)
+        __syncthreads();
+        {
+            const float4 *src = reinterpret_cast<const float4 *>(st);
+            float4 *dst = reinterpret_cast<float4 *>(p.rec + (size_t)t * TILE);
+            for (int i = threadIdx.x; i < TILE / 4; i += kThreads) {
+                const float4 v = src[i];
+                if (p.arrivals) {
+                    if (v.x != 0.f || v.y != 0.f || v.z != 0.f || v.w != 0.f) atomicAdd(dst + i, v);
+                } else {
+                    dst[i] = v;
+                }
             }
         }
+        cell = ncell; ci = nci; cj = ncj; ck = nck;
+        wcur = wnext;
+        ccur = cnext;
+    }
+}
+
+// ------------------------------------------------------------ arrivals deposit
+// The particles that arrived in a cell during the push (the back segment of its
+// new bin) are few, about the fraction of particles that cross a face in a step,
+// so their deposit uses an entry-stationary scheme without a per-cell
+// reduction: lane l owns the record entries k = l + 32 i, each a sum over the
+// arrivals of a product a_k b_k of two per-particle factors (pair weight x
+// alpha entry, or w W_a x (1, v_c, (alpha (v - u_ref))_c)).  The factors sit in
+// a field-major table [field][particle], read as particle pairs: one packed FMA
+// adds two particles' products.  Same tile structure and record write-out
+// (atomic adds) as k_pd.
+template <int DIM> struct AF;   // factor table fields: pair weights, alpha, w W_a, v, alpha (v - u_ref), 1
+template <> struct AF<2> { static constexpr int R = 0, AL = 9, WW = 18, V = 22, AD = 25, ONE = 28, NF = 29, E = 4; };
+template <> struct AF<3> { static constexpr int R = 0, AL = 27, WW = 36, V = 44, AD = 47, ONE = 50, NF = 51, E = 10; };
+constexpr int kArrStride = 34;   // floats per table field: 32 particles + 2, which spreads the fields over the banks
+
+template <int DIM>
+__host__ __device__ constexpr int arr_warp_floats() {
+    return (8 * Geo<DIM>::NC + AF<DIM>::NF * kArrStride + 3) / 4 * 4;
+}
+template <int DIM>
+constexpr size_t arr_smem_bytes() {
+    return ((size_t)kWarpsPerCta * arr_warp_floats<DIM>() + 2 * (size_t)Rec<DIM>::SIZE * kRecTile) * sizeof(float);
+}
+
+// the two table fields whose product makes record entry k
+template <int DIM>
+__device__ __forceinline__ void arr_entry(int k, int &ia, int &ib) {
+    using R = Rec<DIM>;
+    using F = AF<DIM>;
+    if (k >= R::M) {
+        const int t = k - R::M, j = t / 9;
+        ia = F::R + min(j, R::NPAIR - 1); ib = F::AL + t - 9 * j;
+    } else if (k >= R::J) {
+        const int t = k - R::J, a = t / 3;
+        ia = F::WW + a; ib = F::AD + t - 3 * a;
+    } else if (k >= R::MV) {
+        const int t = k - R::MV, a = t / 3;
+        ia = F::WW + a; ib = F::V + t - 3 * a;
+    } else {
+        ia = F::WW + k; ib = F::ONE;
+    }
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(kThreads, DIM == 2 ? 3 : 2) k_arr(const __grid_constant__ PD p) {
+    using G = Geo<DIM>;
+    using R = Rec<DIM>;
+    using F = AF<DIM>;
+    constexpr int NC = G::NC;
+    constexpr int TILE = R::SIZE * kRecTile;
+    constexpr int E = F::E;
+    extern __shared__ __align__(16) float smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float *ws = smem + (size_t)warp * arr_warp_floats<DIM>();
+    float4 *cor = reinterpret_cast<float4 *>(ws);            // [2][NC] coefficients: deposit B (beta / c), u_ref
+    float *T = ws + 8 * NC;                                   // [NF][kArrStride]
+    float *stage = smem + (size_t)kWarpsPerCta * arr_warp_floats<DIM>();
+    int oa[E], ob[E];                                         // table offsets of this lane's entries' factors
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+        int a, b;
+        arr_entry<DIM>(min(lane + 32 * i, R::SIZE - 1), a, b);
+        oa[i] = a * kArrStride;
+        ob[i] = b * kArrStride;
+    }
+    const int64_t ntiles = (p.N + kRecTile - 1) / kRecTile;
+    const int64_t cstride = (int64_t)p.cap * p.nf;
+    const unsigned nx = (unsigned)p.n[0], ny = (unsigned)p.n[1];
+    const unsigned cs = gridDim.x * (unsigned)kRecTile;
+    int64_t cell = (int64_t)blockIdx.x * kRecTile + warp;
+    int ci, cj, ck;
+    {
+        const unsigned c0u = (unsigned)cell;
+        ci = (int)(c0u % nx); cj = (int)((c0u / nx) % ny); ck = (int)(c0u / nx / ny);
+    }
+    const int si = (int)(cs % nx), sj = (int)((cs / nx) % ny), sk = (int)(cs / nx / ny);
+    const int carr = lane / NC, ca = lane % NC;
+    auto corner = [&](int i, int j, int k) {
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (lane < 2 * NC) {
+            const int64_t nd = node_of(p.n, i + (ca & 1), j + ((ca >> 1) & 1), k + ((ca >> 2) & 1));
+            v = __ldg((carr == 0 ? p.dB : p.dU) + nd);
+        }
+        return v;
+    };
+    int wcur = cell < p.N ? seg_word(__ldg(p.cnt_in + cell), p.cap, 1) : 0;
+    float4 ccur = cell < p.N ? corner(ci, cj, ck) : make_float4(0.f, 0.f, 0.f, 0.f);
+    float po[DIM], pv[3], pw = 0.f;
+    auto fetch = [&](const float *bin, int word, int c0) {
+        const int nb_ = bin_back(word);
+        const int i = c0 + lane;
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) po[d] = 0.5f;
+        pv[0] = pv[1] = pv[2] = 0.f;
+        pw = 0.f;
+        if (i < nb_) {
+            const float *q = bin + (p.cap - nb_ + i);
+#pragma unroll
+            for (int d = 0; d < DIM; ++d) po[d] = __ldcs(q + (size_t)d * p.cap);
+#pragma unroll
+            for (int d = 0; d < 3; ++d) pv[d] = __ldcs(q + (size_t)(PF<DIM>::V + d) * p.cap);
+            pw = __ldcs(q + (size_t)PF<DIM>::W * p.cap);
+        }
+    };
+    if (cell < p.N) fetch(p.in + cell * cstride, wcur, 0);
+
+    int it = 0;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+        const int64_t ncell = cell + cs;
+        int nci = ci + si, ncj = cj + sj, nck = ck + sk;
+        if (nci >= p.n[0]) { nci -= p.n[0]; ++ncj; }
+        if (ncj >= p.n[1]) { ncj -= p.n[1]; ++nck; }
+        const bool has_next = ncell < p.N;
+        const int wnext = has_next ? seg_word(__ldg(p.cnt_in + ncell), p.cap, 1) : 0;
+        const float4 cnext = has_next ? corner(nci, ncj, nck) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float *bin_nx = p.in + ncell * cstride;
+        const int n = bin_back(wcur);
+        float2 acc[E];
+#pragma unroll
+        for (int i = 0; i < E; ++i) acc[i] = make_float2(0.f, 0.f);
+        if (n > 0) {
+            __syncwarp();                                     // the previous cell's reads of cor are done
+            {
+                float4 v = ccur;
+                const float sc = carr == 0 ? p.bc : 1.f;
+                v.x *= sc; v.y *= sc; v.z *= sc;
+                v = to_coef<DIM>(v, ca);
+                if (lane < 2 * NC) cor[lane] = v;
+            }
+            __syncwarp();
+        }
+        for (int c0 = 0; c0 < n; c0 += 32) {
+            const bool valid = c0 + lane < n;
+            float o[3] = {0.5f, 0.5f, 0.f}, v[3] = {pv[0], pv[1], pv[2]};
+#pragma unroll
+            for (int d = 0; d < DIM; ++d) o[d] = po[d];
+            const float w = valid ? pw : 0.f;
+            if (c0 + 32 < n) fetch(p.in + cell * cstride, wcur, c0 + 32);
+            else if (has_next) fetch(bin_nx, wnext, 0);
+            // ---- this lane's factors into column `lane` of the table
+            {
+                float b3[3], U3[3], al[9], W[NC];
+                interp<DIM>(cor, o, b3);
+                interp<DIM>(cor + NC, o, U3);
+                alpha_tensor(b3[0], b3[1], b3[2], al);
+                corner_weights<DIM>(o, W);
+                const float d0 = v[0] - U3[0], d1 = v[1] - U3[1], d2 = v[2] - U3[2];
+                float X[3][3];
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    const float a0 = 1.f - o[d];
+                    X[d][0] = a0 * a0; X[d][1] = a0 * o[d]; X[d][2] = o[d] * o[d];
+                }
+                float *tc = T + lane;
+#pragma unroll
+                for (int jz = 0; jz < (DIM == 3 ? 3 : 1); ++jz)
+#pragma unroll
+                    for (int jy = 0; jy < 3; ++jy) {
+                        const float wyz = DIM == 3 ? w * X[1][jy] * X[2][jz] : w * X[1][jy];
+#pragma unroll
+                        for (int jx = 0; jx < 3; ++jx) tc[(F::R + jx + 3 * jy + 9 * jz) * kArrStride] = wyz * X[0][jx];
+                    }
+#pragma unroll
+                for (int e = 0; e < 9; ++e) tc[(F::AL + e) * kArrStride] = al[e];
+#pragma unroll
+                for (int a = 0; a < NC; ++a) tc[(F::WW + a) * kArrStride] = w * W[a];
+#pragma unroll
+                for (int d = 0; d < 3; ++d) tc[(F::V + d) * kArrStride] = v[d];
+                tc[(F::AD + 0) * kArrStride] = fmaf(al[0], d0, fmaf(al[1], d1, al[2] * d2));
+                tc[(F::AD + 1) * kArrStride] = fmaf(al[3], d0, fmaf(al[4], d1, al[5] * d2));
+                tc[(F::AD + 2) * kArrStride] = fmaf(al[6], d0, fmaf(al[7], d1, al[8] * d2));
+                tc[F::ONE * kArrStride] = 1.f;
+            }
+            __syncwarp();
+            // ---- this lane's entries over the chunk's particles, two at a time (an
+            // odd count's last pair reads a lane whose factors carry w = 0)
+            const int nv = min(32, n - c0);
+            for (int pp = 0; pp < nv; pp += 2) {
+#pragma unroll
+                for (int i = 0; i < E; ++i) {
+                    const float2 a2 = *reinterpret_cast<const float2 *>(T + oa[i] + pp);
+                    const float2 b2 = *reinterpret_cast<const float2 *>(T + ob[i] + pp);
+                    acc[i] = __ffma2_rn(a2, b2, acc[i]);
+                }
+            }
+            __syncwarp();                                    // the table is rewritten by the next chunk
+        }
+        if (n == 0 && has_next) fetch(bin_nx, wnext, 0);
+        float *st = stage + (size_t)(it & 1) * TILE;
+#pragma unroll
+        for (int i = 0; i < E; ++i) {
+            const int k = lane + 32 * i;
+            if (k < R::SIZE) st[k * kRecTile + warp] = k < R::USED ? acc[i].x + acc[i].y : 0.f;
+        }
+        __syncthreads();
+        {
+            const float4 *src = reinterpret_cast<const float4 *>(st);
+            float4 *dst = reinterpret_cast<float4 *>(p.rec + (size_t)t * TILE);
+            for (int i = threadIdx.x; i < TILE / 4; i += kThreads) {
+                const float4 v = src[i];
+                if (v.x != 0.f || v.y != 0.f || v.z != 0.f || v.w != 0.f) atomicAdd(dst + i, v);
+            }
+        }
+        cell = ncell; ci = nci; cj = ncj; ck = nck;
+        wcur = wnext;
+        ccur = cnext;
     }
 }
 
@@ -793,6 +1107,7 @@ int configure_pd(gx_ctx *c) {
     GX_CHECK(c, cudaFuncSetAttribute(k_pd<DIM, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
     if constexpr (DIM == 2)
         GX_CHECK(c, cudaFuncSetAttribute(k_pd<DIM, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    GX_CHECK(c, cudaFuncSetAttribute(k_arr<DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)arr_smem_bytes<DIM>()));
     done = true;
     return GX_OK;
 }
@@ -803,6 +1118,23 @@ int pd_grid(gx_ctx *c, int64_t ncell) {
     static int per_sm = 0;
     if (!per_sm) {
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pd<DIM, true>, kThreads, pd_smem_bytes<DIM>()) !=
+                cudaSuccess ||
+            per_sm < 1)
+            per_sm = 1;
+    }
+    int dev = 0, nsm = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t need = (ncell + kWarpsPerCta - 1) / kWarpsPerCta;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)nsm * per_sm));
+}
+
+// persistent grid of the arrivals deposit
+template <int DIM>
+int arr_grid(int64_t ncell) {
+    static int per_sm = 0;
+    if (!per_sm) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_arr<DIM>, kThreads, arr_smem_bytes<DIM>()) !=
                 cudaSuccess ||
             per_sm < 1)
             per_sm = 1;
@@ -875,7 +1207,7 @@ int launch_pd(gx_ctx *c, bool push, cudaStream_t st) {
             q.in = p.out;
             q.cnt_in = p.cnt_out;
             q.mE = nullptr; q.mB = nullptr;
-            k_pd<DIM, false><<<grid, kThreads, smem, st>>>(q);
+            k_arr<DIM><<<arr_grid<DIM>(c->N), kThreads, arr_smem_bytes<DIM>(), st>>>(q);
             GX_LAUNCHED(c);
             if (DIM == 2 && c->cfg.bc_cells > 0) {
                 // open boundaries: the boundary cells' particles are replaced
