@@ -347,6 +347,9 @@ int gx_create(const gx_config *cfg, gx_ctx **out) {
         cudaMemset(c->kappa, 0, (size_t)nax * 3 * N * sizeof(double)) != cudaSuccess ||
         cudaMemset(c->dflags, 0, sizeof(DevFlags)) != cudaSuccess ||
         cudaMemset(c->nUref, 0, N * sizeof(float4)) != cudaSuccess ||
+        (c->M32 && cudaMemset(c->M32, 0, (size_t)c->noff * 9 * N * sizeof(float)) != cudaSuccess) ||
+        (c->kappa32 && cudaMemset(c->kappa32, 0, (size_t)nax * 3 * N * sizeof(float)) != cudaSuccess) ||
+        (c->A3f && cudaMemset(c->A3f, 0, (size_t)243 * N * sizeof(float)) != cudaSuccess) ||
         cudaDeviceSynchronize() != cudaSuccess)
         return fail(GX_ECUDA, "initialisation failed");
     if ((rc = gx_noalloc_prepare(c))) return fail(rc, nullptr);

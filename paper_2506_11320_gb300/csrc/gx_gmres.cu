@@ -492,12 +492,6 @@ __global__ void k_norm2(const double *__restrict__ x, int64_t n, double *out) {
     }
 }
 
-// FP32 copy of the operator's coefficients for the mixed-precision cycles
-__global__ void k_to_f32(const double *__restrict__ src, float *__restrict__ dst, int64_t n) {
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
-        dst[t] = (float)src[t];
-}
-
 __global__ void k_sub(const double *__restrict__ b, const double *__restrict__ ax, double *r, int64_t n) {
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
         r[t] = b[t] - ax[t];
@@ -565,19 +559,7 @@ int gx_fgmres(gx_ctx *c, cudaStream_t st) {
         grid = std::max(1, std::min(per * nsm, kMaxGrid));
     }
     CoArgs a{};
-    a.op = gx_opargs(c);
-    if (mix) {
-        // this solve's coefficients in FP32 (the operator changes every step)
-        struct Cv { const double *s; float *d; int64_t n; };
-        const Cv cv[3] = {{a.op.M, c->M32, c->dim == 3 ? 0 : (int64_t)c->noff * 9 * c->N},
-                          {a.op.kappa, c->kappa32, c->dim == 3 ? 0 : (int64_t)2 * 3 * c->N},
-                          {a.op.A3, c->A3f, c->dim == 3 ? (int64_t)243 * c->N : 0}};
-        for (const Cv &e : cv) {
-            if (!e.s || !e.d || e.n == 0) continue;
-            k_to_f32<<<nblocks(e.n), kB, 0, st>>>(e.s, e.d, e.n);
-            GX_LAUNCHED(c);
-        }
-    }
+    a.op = gx_opargs(c);   // with gmres_mixed, its FP32 copies were written with M, kappa and the 3D blocks
     a.b = c->rhs;
     a.x = c->Eth;
     a.V = c->V;

@@ -180,7 +180,7 @@ __device__ __forceinline__ double widen_f32(float f) {
 // are combined in FP64, the mass matrix (all species add with beta_s q_s > 0)
 // in FP32 and stored as FP64.
 __global__ void __launch_bounds__(kB, kNodeCtas) k_assemble_main(G2 g, SpecK sk, Recs R, double inv_dV, int comoving, const double *__restrict__ u,
-                                const double *__restrict__ uref, double *J, double *M) {
+                                const double *__restrict__ uref, double *J, double *M, float *M32) {
     const int64_t N = g.N();
     GRID_LOOP(q, N) {
         const int j = (int)((unsigned)q / (unsigned)g.nx), i = (int)q - j * g.nx;
@@ -251,6 +251,9 @@ __global__ void __launch_bounds__(kB, kNodeCtas) k_assemble_main(G2 g, SpecK sk,
             }
 #pragma unroll
             for (int e = 0; e < 9; ++e) M[(size_t)(o * 9 + e) * N + q] = widen_f32(blk[e]);
+            if (M32)   // the FP32 copy the mixed-precision Krylov cycles apply
+#pragma unroll
+                for (int e = 0; e < 9; ++e) M32[(size_t)(o * 9 + e) * N + q] = blk[e];
         }
     }
 }
@@ -481,7 +484,7 @@ __device__ __forceinline__ float umag(const double *u, int64_t N, int64_t q) {
 // phi_E from E^n (frozen, keeps the solve linear), a = |u| averaged over the
 // edge's two nodes or a = c.
 __global__ void k_kappa(G2 g, const double *__restrict__ E, const double *__restrict__ u, double beta, int speed_c,
-                        double c, double *kappa) {
+                        double c, double *kappa, float *kappa32) {
     const int64_t N = g.N();
     GRID_LOOP(q, N) {
         const int j = (int)((unsigned)q / (unsigned)g.nx), i = (int)q - j * g.nx;
@@ -493,7 +496,9 @@ __global__ void k_kappa(G2 g, const double *__restrict__ E, const double *__rest
             for (int comp = 0; comp < 3; ++comp) {
                 const double *Ec = E + comp * N;
                 const float r = ratio(Ec[q] - Ec[m], Ec[p] - Ec[q]);
-                kappa[(d * 3 + comp) * N + q] = (double)(1.0f - mc_limiter(r, (float)beta)) * a * 0.5;
+                const double kv = (double)(1.0f - mc_limiter(r, (float)beta)) * a * 0.5;
+                kappa[(d * 3 + comp) * N + q] = kv;
+                if (kappa32) kappa32[(d * 3 + comp) * N + q] = (float)kv;
             }
         }
     }
@@ -739,7 +744,7 @@ int gx_assemble_moments(gx_ctx *c, cudaStream_t st) {
     int rc = filter_passes(c, c->u, c->cfg.nsmooth_u, true, st);
     if (rc) return rc;
     k_assemble_main<<<blocks_for(c->N), kB, 0, st>>>(g, sk, R, 1.0 / c->dV, c->cfg.comoving, c->u, c->uref64, c->J,
-                                                       c->M);
+                                                       c->M, c->M32);
     GX_LAUNCHED(c);
     rc = filter_passes(c, c->J, c->cfg.ns_j, false, st);
     if (rc) return rc;
@@ -782,7 +787,7 @@ int gx_build_kappa(gx_ctx *c, cudaStream_t st) {
     if (c->dim == 3) return gx3_build_kappa(c, st);
     if (!c->cfg.lf_on || c->cfg.nsmooth_e > 0) return GX_OK;
     k_kappa<<<blocks_for(c->N), kB, 0, st>>>(geom(c), c->E, c->u, c->cfg.lf_beta, c->cfg.lf_speed_c, c->cfg.c,
-                                              c->kappa);
+                                              c->kappa, c->kappa32);
     GX_LAUNCHED(c);
     return GX_OK;
 }

@@ -404,9 +404,11 @@ __global__ void k3_advance(G3 g, H4 h, const double *__restrict__ E, const doubl
 
 // the 27 blocks of the operator at every node (see the file comment); LF: the
 // diffusive term -theta dt / dx_d [kappa_+ (x_+ - x) - kappa_- (x - x_-)] per
-// resolved axis and component
+// resolved axis and component.  A3f (or null): the same blocks rounded to FP32
+// for the mixed-precision Krylov cycles.
 __global__ void k3_assemble_A(G3 g, K3 K, double mfac, const double *__restrict__ M,
-                              const double *__restrict__ kappa, double lfx, double lfy, double lfz, double *A3) {
+                              const double *__restrict__ kappa, double lfx, double lfy, double lfz, double *A3,
+                              float *A3f) {
     const int64_t N = g.N();
     const int n3[3] = {g.nx, g.ny, g.nz};
     const double lf[3] = {lfx, lfy, lfz};
@@ -450,6 +452,9 @@ __global__ void k3_assemble_A(G3 g, K3 K, double mfac, const double *__restrict_
             }
 #pragma unroll
             for (int e = 0; e < 9; ++e) A3[(size_t)(o * 9 + e) * N + q] = blk[e];
+            if (A3f)
+#pragma unroll
+                for (int e = 0; e < 9; ++e) A3f[(size_t)(o * 9 + e) * N + q] = (float)blk[e];
         }
     }
 }
@@ -679,7 +684,8 @@ int gx3_build_op(gx_ctx *c, cudaStream_t st) {
     const double f = c->cfg.theta * c->cfg.dt;
     k3_assemble_A<<<blocks_for(c->N), kB, 0, st>>>(geom3(c), curlcurl(c, ct * ct), mfac,
                                                     c->nspecies > 0 ? c->M : nullptr, lfe ? c->kappa : nullptr,
-                                                    f / c->cfg.dx[0], f / c->cfg.dx[1], f / c->cfg.dx[2], c->A3);
+                                                    f / c->cfg.dx[0], f / c->cfg.dx[1], f / c->cfg.dx[2], c->A3,
+                                                    c->cfg.gmres_mixed ? c->A3f : nullptr);
     GX_LAUNCHED(c);
     return GX_OK;
 }
