@@ -500,24 +500,35 @@ __global__ void __launch_bounds__(kThreads, Geo<DIM>::CTAS) k_pd(const __grid_co
             __syncwarp();
             // ---- output-stationary accumulation: this lane adds, over its group's
             // particles, its 9 pair classes x 4 columns
+            auto accumulate = [&](int pp) {
+                const float *tp = T + pp * G::TSTR;
+                const float4 r03 = *reinterpret_cast<const float4 *>(tp + roff);
+                const float4 r47 = *reinterpret_cast<const float4 *>(tp + roff + 4);
+                const float r8 = tp[roff + 8];
+                const float4 cv = *reinterpret_cast<const float4 *>(tp + coff);
+                const float cc[4] = {cv.x, cv.y, cv.z, cv.w};
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const float2 d = make_float2(cc[c], cc[c]);
+                    accp[c][0] = __ffma2_rn(make_float2(r03.x, r03.y), d, accp[c][0]);
+                    accp[c][1] = __ffma2_rn(make_float2(r03.z, r03.w), d, accp[c][1]);
+                    accp[c][2] = __ffma2_rn(make_float2(r47.x, r47.y), d, accp[c][2]);
+                    accp[c][3] = __ffma2_rn(make_float2(r47.z, r47.w), d, accp[c][3]);
+                    acc8[c] = fmaf(r8, cc[c], acc8[c]);
+                }
+            };
             if (role) {
                 const int nv = min(32, n - c0);
-                for (int pp = pg; pp < nv; pp += G::KG) {
-                    const float *tp = T + pp * G::TSTR;
-                    const float4 r03 = *reinterpret_cast<const float4 *>(tp + roff);
-                    const float4 r47 = *reinterpret_cast<const float4 *>(tp + roff + 4);
-                    const float r8 = tp[roff + 8];
-                    const float4 cv = *reinterpret_cast<const float4 *>(tp + coff);
-                    const float cc[4] = {cv.x, cv.y, cv.z, cv.w};
+                if constexpr (DIM == 3) {
+                    // a fixed trip count (rows of absent particles are 0; the warp-uniform
+                    // break skips the iterations past the chunk's end): faster in 3D only
 #pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        const float2 d = make_float2(cc[c], cc[c]);
-                        accp[c][0] = __ffma2_rn(make_float2(r03.x, r03.y), d, accp[c][0]);
-                        accp[c][1] = __ffma2_rn(make_float2(r03.z, r03.w), d, accp[c][1]);
-                        accp[c][2] = __ffma2_rn(make_float2(r47.x, r47.y), d, accp[c][2]);
-                        accp[c][3] = __ffma2_rn(make_float2(r47.z, r47.w), d, accp[c][3]);
-                        acc8[c] = fmaf(r8, cc[c], acc8[c]);
+                    for (int si = 0; si < 32 / G::KG; ++si) {
+                        if (G::KG * si >= nv) break;
+                        accumulate(pg + G::KG * si);
                     }
+                } else {
+                    for (int pp = pg; pp < nv; pp += G::KG) accumulate(pp);
                 }
             }
             // ---- 3D leavers: the slot their run reserved
@@ -586,20 +597,29 @@ __global__ void __launch_bounds__(kThreads, Geo<DIM>::CTAS) k_pd(const __grid_co
 // arrivals of a product a_k b_k of two per-particle factors (pair weight x
 // alpha entry, or w W_a x (1, v_c, (alpha (v - u_ref))_c)).  The factors sit in
 // a field-major table [field][particle], read as particle pairs: one packed FMA
-// adds two particles' products.  Same tile structure and record write-out
-// (atomic adds) as k_pd.
+// adds two particles' products.  A warp takes CPW consecutive cells at once: their
+// arrivals share the 32-lane chunks, each cell's run padded to an even count
+// (padding slots carry w = 0), so the factor pass and the per-cell set-up are
+// spread over several cells' particles.  A CTA's 8 warps cover CPW record tiles,
+// staged in shared memory and added to the records with 16-byte atomic adds.
 template <int DIM> struct AF;   // factor table fields: pair weights, alpha, w W_a, v, alpha (v - u_ref), 1
-template <> struct AF<2> { static constexpr int R = 0, AL = 9, WW = 18, V = 22, AD = 25, ONE = 28, NF = 29, E = 4; };
-template <> struct AF<3> { static constexpr int R = 0, AL = 27, WW = 36, V = 44, AD = 47, ONE = 50, NF = 51, E = 10; };
+template <> struct AF<2> { static constexpr int R = 0, AL = 9, WW = 18, V = 22, AD = 25, ONE = 28, NF = 29, E = 4, CPW = 4; };
+template <> struct AF<3> { static constexpr int R = 0, AL = 27, WW = 36, V = 44, AD = 47, ONE = 50, NF = 51, E = 10, CPW = 2; };
+// AF::CPW cells per warp on large grids; one on grids too small to fill the GPU that way
 constexpr int kArrStride = 34;   // floats per table field: 32 particles + 2, which spreads the fields over the banks
 
-template <int DIM>
+// per warp: the CPW cells' coefficients [CPW][2 NC + 1] float4 (the +1 puts the cells
+// in different banks), then the factor table
+template <int DIM, int CPW>
+__host__ __device__ constexpr int arr_cor_floats() { return CPW * (2 * Geo<DIM>::NC + 1) * 4; }
+template <int DIM, int CPW>
 __host__ __device__ constexpr int arr_warp_floats() {
-    return (8 * Geo<DIM>::NC + AF<DIM>::NF * kArrStride + 3) / 4 * 4;
+    return arr_cor_floats<DIM, CPW>() + (AF<DIM>::NF * kArrStride + 3) / 4 * 4;
 }
-template <int DIM>
+template <int DIM, int CPW>
 constexpr size_t arr_smem_bytes() {
-    return ((size_t)kWarpsPerCta * arr_warp_floats<DIM>() + 2 * (size_t)Rec<DIM>::SIZE * kRecTile) * sizeof(float);
+    return ((size_t)kWarpsPerCta * arr_warp_floats<DIM, CPW>() + 2 * (size_t)CPW * Rec<DIM>::SIZE * kRecTile) *
+           sizeof(float);
 }
 
 // the two table fields whose product makes record entry k
@@ -621,7 +641,7 @@ __device__ __forceinline__ void arr_entry(int k, int &ia, int &ib) {
     }
 }
 
-template <int DIM>
+template <int DIM, int CPW>
 __global__ void __launch_bounds__(kThreads, DIM == 2 ? 3 : 2) k_arr(const __grid_constant__ PD p) {
     using G = Geo<DIM>;
     using R = Rec<DIM>;
@@ -629,12 +649,14 @@ __global__ void __launch_bounds__(kThreads, DIM == 2 ? 3 : 2) k_arr(const __grid
     constexpr int NC = G::NC;
     constexpr int TILE = R::SIZE * kRecTile;
     constexpr int E = F::E;
+    constexpr int SUP = kWarpsPerCta * CPW;                   // cells per CTA (CPW record tiles)
+    static_assert(CPW * 2 * NC <= 32, "at most one corner value per lane");
     extern __shared__ __align__(16) float smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    float *ws = smem + (size_t)warp * arr_warp_floats<DIM>();
-    float4 *cor = reinterpret_cast<float4 *>(ws);            // [2][NC] coefficients: deposit B (beta / c), u_ref
-    float *T = ws + 8 * NC;                                   // [NF][kArrStride]
-    float *stage = smem + (size_t)kWarpsPerCta * arr_warp_floats<DIM>();
+    float *ws = smem + (size_t)warp * arr_warp_floats<DIM, CPW>();
+    float4 *cor = reinterpret_cast<float4 *>(ws);            // [CPW][2 NC + 1]: deposit B (beta / c), u_ref
+    float *T = ws + arr_cor_floats<DIM, CPW>();               // [NF][kArrStride]
+    float *stage = smem + (size_t)kWarpsPerCta * arr_warp_floats<DIM, CPW>();   // [2][CPW TILE]
     int oa[E], ob[E];                                         // table offsets of this lane's entries' factors
 #pragma unroll
     for (int i = 0; i < E; ++i) {
@@ -643,85 +665,77 @@ __global__ void __launch_bounds__(kThreads, DIM == 2 ? 3 : 2) k_arr(const __grid
         oa[i] = a * kArrStride;
         ob[i] = b * kArrStride;
     }
+    const int64_t nsup = (p.N + SUP - 1) / SUP;
     const int64_t ntiles = (p.N + kRecTile - 1) / kRecTile;
     const int64_t cstride = (int64_t)p.cap * p.nf;
     const unsigned nx = (unsigned)p.n[0], ny = (unsigned)p.n[1];
-    const unsigned cs = gridDim.x * (unsigned)kRecTile;
-    int64_t cell = (int64_t)blockIdx.x * kRecTile + warp;
-    int ci, cj, ck;
-    {
-        const unsigned c0u = (unsigned)cell;
-        ci = (int)(c0u % nx); cj = (int)((c0u / nx) % ny); ck = (int)(c0u / nx / ny);
-    }
-    const int si = (int)(cs % nx), sj = (int)((cs / nx) % ny), sk = (int)(cs / nx / ny);
-    const int carr = lane / NC, ca = lane % NC;
-    auto corner = [&](int i, int j, int k) {
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (lane < 2 * NC) {
-            const int64_t nd = node_of(p.n, i + (ca & 1), j + ((ca >> 1) & 1), k + ((ca >> 2) & 1));
-            v = __ldg((carr == 0 ? p.dB : p.dU) + nd);
-        }
-        return v;
-    };
-    int wcur = cell < p.N ? seg_word(__ldg(p.cnt_in + cell), p.cap, 1) : 0;
-    float4 ccur = cell < p.N ? corner(ci, cj, ck) : make_float4(0.f, 0.f, 0.f, 0.f);
-    float po[DIM], pv[3], pw = 0.f;
-    auto fetch = [&](const float *bin, int word, int c0) {
-        const int nb_ = bin_back(word);
-        const int i = c0 + lane;
-#pragma unroll
-        for (int d = 0; d < DIM; ++d) po[d] = 0.5f;
-        pv[0] = pv[1] = pv[2] = 0.f;
-        pw = 0.f;
-        if (i < nb_) {
-            const float *q = bin + (p.cap - nb_ + i);
-#pragma unroll
-            for (int d = 0; d < DIM; ++d) po[d] = __ldcs(q + (size_t)d * p.cap);
-#pragma unroll
-            for (int d = 0; d < 3; ++d) pv[d] = __ldcs(q + (size_t)(PF<DIM>::V + d) * p.cap);
-            pw = __ldcs(q + (size_t)PF<DIM>::W * p.cap);
-        }
-    };
-    if (cell < p.N) fetch(p.in + cell * cstride, wcur, 0);
+    // this lane's corner value: cell lc of the warp's CPW, array larr (0: B, 1: u_ref), corner la
+    const int lc = lane / (2 * NC), larr = (lane / NC) & 1, la = lane % NC;
+    const float lsc = larr == 0 ? p.bc : 1.f;
 
     int it = 0;
-    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
-        const int64_t ncell = cell + cs;
-        int nci = ci + si, ncj = cj + sj, nck = ck + sk;
-        if (nci >= p.n[0]) { nci -= p.n[0]; ++ncj; }
-        if (ncj >= p.n[1]) { ncj -= p.n[1]; ++nck; }
-        const bool has_next = ncell < p.N;
-        const int wnext = has_next ? seg_word(__ldg(p.cnt_in + ncell), p.cap, 1) : 0;
-        const float4 cnext = has_next ? corner(nci, ncj, nck) : make_float4(0.f, 0.f, 0.f, 0.f);
-        const float *bin_nx = p.in + ncell * cstride;
-        const int n = bin_back(wcur);
-        float2 acc[E];
-#pragma unroll
-        for (int i = 0; i < E; ++i) acc[i] = make_float2(0.f, 0.f);
-        if (n > 0) {
-            __syncwarp();                                     // the previous cell's reads of cor are done
-            {
-                float4 v = ccur;
-                const float sc = carr == 0 ? p.bc : 1.f;
-                v.x *= sc; v.y *= sc; v.z *= sc;
-                v = to_coef<DIM>(v, ca);
-                if (lane < 2 * NC) cor[lane] = v;
+    for (int64_t st = blockIdx.x; st < nsup; st += gridDim.x, ++it) {
+        const int64_t cell0 = st * SUP + (int64_t)warp * CPW;
+        int nbl = 0;
+        if (lane < CPW && cell0 + lane < p.N) nbl = bin_back(seg_word(__ldg(p.cnt_in + cell0 + lane), p.cap, 1));
+        float4 v4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        {
+            const int64_t mc = cell0 + lc;
+            if (lc < CPW && mc < p.N) {
+                const unsigned u = (unsigned)mc;
+                const int ci = (int)(u % nx), cj = (int)((u / nx) % ny), ck = (int)(u / nx / ny);
+                const int64_t nd = node_of(p.n, ci + (la & 1), cj + ((la >> 1) & 1), ck + ((la >> 2) & 1));
+                v4 = __ldg((larr == 0 ? p.dB : p.dU) + nd);
             }
+        }
+        // the cells' arrival counts and their even-padded offsets in the warp's chunk space
+        int nb[CPW], ps[CPW + 1];
+        ps[0] = 0;
+#pragma unroll
+        for (int c = 0; c < CPW; ++c) {
+            nb[c] = __shfl_sync(kFull, nbl, c);
+            ps[c + 1] = ps[c] + ((nb[c] + 1) & ~1);
+        }
+        const int total = ps[CPW];
+        float2 acc[CPW][E];
+#pragma unroll
+        for (int c = 0; c < CPW; ++c)
+#pragma unroll
+            for (int i = 0; i < E; ++i) acc[c][i] = make_float2(0.f, 0.f);
+        if (total > 0) {
+            __syncwarp();                                     // the previous cells' reads of cor are done
+            v4.x *= lsc; v4.y *= lsc; v4.z *= lsc;
+            v4 = to_coef<DIM>(v4, la);
+            if (lc < CPW) cor[lc * (2 * NC + 1) + larr * NC + la] = v4;
             __syncwarp();
         }
-        for (int c0 = 0; c0 < n; c0 += 32) {
-            const bool valid = c0 + lane < n;
-            float o[3] = {0.5f, 0.5f, 0.f}, v[3] = {pv[0], pv[1], pv[2]};
+        for (int c0 = 0; c0 < total; c0 += 32) {
+            // ---- this lane's slot: cell c, arrival j (or padding)
+            const int g = c0 + lane;
+            int c = 0;
 #pragma unroll
-            for (int d = 0; d < DIM; ++d) o[d] = po[d];
-            const float w = valid ? pw : 0.f;
-            if (c0 + 32 < n) fetch(p.in + cell * cstride, wcur, c0 + 32);
-            else if (has_next) fetch(bin_nx, wnext, 0);
+            for (int cc = 1; cc < CPW; ++cc) c = g >= ps[cc] ? cc : c;
+            int nbc = nb[0], psc = ps[0];
+#pragma unroll
+            for (int cc = 1; cc < CPW; ++cc)
+                if (c == cc) { nbc = nb[cc]; psc = ps[cc]; }
+            const int j = g - psc;
+            const bool valid = g < total && j < nbc;
+            float o[3] = {0.5f, 0.5f, 0.f}, v[3] = {0.f, 0.f, 0.f}, w = 0.f;
+            if (valid) {
+                const float *q = p.in + (cell0 + c) * cstride + (p.cap - nbc + j);
+#pragma unroll
+                for (int d = 0; d < DIM; ++d) o[d] = __ldcs(q + (size_t)d * p.cap);
+#pragma unroll
+                for (int d = 0; d < 3; ++d) v[d] = __ldcs(q + (size_t)(PF<DIM>::V + d) * p.cap);
+                w = __ldcs(q + (size_t)PF<DIM>::W * p.cap);
+            }
             // ---- this lane's factors into column `lane` of the table
             {
+                const float4 *cc4 = cor + c * (2 * NC + 1);
                 float b3[3], U3[3], al[9], W[NC];
-                interp<DIM>(cor, o, b3);
-                interp<DIM>(cor + NC, o, U3);
+                interp<DIM>(cc4, o, b3);
+                interp<DIM>(cc4 + NC, o, U3);
                 alpha_tensor(b3[0], b3[1], b3[2], al);
                 corner_weights<DIM>(o, W);
                 const float d0 = v[0] - U3[0], d1 = v[1] - U3[1], d2 = v[2] - U3[2];
@@ -752,38 +766,43 @@ __global__ void __launch_bounds__(kThreads, DIM == 2 ? 3 : 2) k_arr(const __grid
                 tc[F::ONE * kArrStride] = 1.f;
             }
             __syncwarp();
-            // ---- this lane's entries over the chunk's particles, two at a time (an
-            // odd count's last pair reads a lane whose factors carry w = 0)
-            const int nv = min(32, n - c0);
-            for (int pp = 0; pp < nv; pp += 2) {
+            // ---- every cell's entries over its (even-aligned) slots of this chunk
 #pragma unroll
-                for (int i = 0; i < E; ++i) {
-                    const float2 a2 = *reinterpret_cast<const float2 *>(T + oa[i] + pp);
-                    const float2 b2 = *reinterpret_cast<const float2 *>(T + ob[i] + pp);
-                    acc[i] = __ffma2_rn(a2, b2, acc[i]);
+            for (int cc = 0; cc < CPW; ++cc) {
+                const int lo = max(ps[cc], c0), hi = min(ps[cc + 1], c0 + 32);
+                for (int pp = lo - c0; pp < hi - c0; pp += 2) {
+#pragma unroll
+                    for (int i = 0; i < E; ++i) {
+                        const float2 a2 = *reinterpret_cast<const float2 *>(T + oa[i] + pp);
+                        const float2 b2 = *reinterpret_cast<const float2 *>(T + ob[i] + pp);
+                        acc[cc][i] = __ffma2_rn(a2, b2, acc[cc][i]);
+                    }
                 }
             }
             __syncwarp();                                    // the table is rewritten by the next chunk
         }
-        if (n == 0 && has_next) fetch(bin_nx, wnext, 0);
-        float *st = stage + (size_t)(it & 1) * TILE;
+        // ---- the cells' records into the stage, then the CTA's record tiles
+        float *stg = stage + (size_t)(it & 1) * CPW * TILE;
 #pragma unroll
-        for (int i = 0; i < E; ++i) {
-            const int k = lane + 32 * i;
-            if (k < R::SIZE) st[k * kRecTile + warp] = k < R::USED ? acc[i].x + acc[i].y : 0.f;
+        for (int cc = 0; cc < CPW; ++cc) {
+            const int sc = warp * CPW + cc;
+            float *dstc = stg + (sc / kRecTile) * TILE + sc % kRecTile;
+#pragma unroll
+            for (int i = 0; i < E; ++i) {
+                const int k = lane + 32 * i;
+                if (k < R::SIZE) dstc[k * kRecTile] = k < R::USED ? acc[cc][i].x + acc[cc][i].y : 0.f;
+            }
         }
         __syncthreads();
         {
-            const float4 *src = reinterpret_cast<const float4 *>(st);
-            float4 *dst = reinterpret_cast<float4 *>(p.rec + (size_t)t * TILE);
-            for (int i = threadIdx.x; i < TILE / 4; i += kThreads) {
-                const float4 v = src[i];
-                if (v.x != 0.f || v.y != 0.f || v.z != 0.f || v.w != 0.f) atomicAdd(dst + i, v);
+            const float4 *src = reinterpret_cast<const float4 *>(stg);
+            float4 *dst = reinterpret_cast<float4 *>(p.rec + (size_t)st * CPW * TILE);
+            for (int i = threadIdx.x; i < CPW * TILE / 4; i += kThreads) {
+                if (st * CPW + (4 * i) / TILE >= ntiles) break;   // record tiles past the grid
+                const float4 vv = src[i];
+                if (vv.x != 0.f || vv.y != 0.f || vv.z != 0.f || vv.w != 0.f) atomicAdd(dst + i, vv);
             }
         }
-        cell = ncell; ci = nci; cj = ncj; ck = nck;
-        wcur = wnext;
-        ccur = cnext;
     }
 }
 
@@ -1107,7 +1126,10 @@ int configure_pd(gx_ctx *c) {
     GX_CHECK(c, cudaFuncSetAttribute(k_pd<DIM, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
     if constexpr (DIM == 2)
         GX_CHECK(c, cudaFuncSetAttribute(k_pd<DIM, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-    GX_CHECK(c, cudaFuncSetAttribute(k_arr<DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)arr_smem_bytes<DIM>()));
+    GX_CHECK(c, cudaFuncSetAttribute(k_arr<DIM, AF<DIM>::CPW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)arr_smem_bytes<DIM, AF<DIM>::CPW>()));
+    GX_CHECK(c, cudaFuncSetAttribute(k_arr<DIM, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)arr_smem_bytes<DIM, 1>()));
     done = true;
     return GX_OK;
 }
@@ -1129,21 +1151,35 @@ int pd_grid(gx_ctx *c, int64_t ncell) {
     return (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)nsm * per_sm));
 }
 
-// persistent grid of the arrivals deposit
-template <int DIM>
-int arr_grid(int64_t ncell) {
+// the arrivals deposit: AF::CPW cells per warp where that still gives every CTA slot
+// of the GPU at least two CTAs' work, else one; a persistent grid
+template <int DIM, int CPW>
+int arr_slots() {
     static int per_sm = 0;
     if (!per_sm) {
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_arr<DIM>, kThreads, arr_smem_bytes<DIM>()) !=
-                cudaSuccess ||
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_arr<DIM, CPW>, kThreads,
+                                                          arr_smem_bytes<DIM, CPW>()) != cudaSuccess ||
             per_sm < 1)
             per_sm = 1;
     }
     int dev = 0, nsm = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    const int64_t need = (ncell + kWarpsPerCta - 1) / kWarpsPerCta;
-    return (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)nsm * per_sm));
+    return nsm * per_sm;
+}
+template <int DIM>
+void launch_arr(const PD &q, int64_t ncell, cudaStream_t st) {
+    constexpr int CPW = AF<DIM>::CPW;
+    const int64_t big = (ncell + kWarpsPerCta * CPW - 1) / (kWarpsPerCta * CPW);
+    const int slots = arr_slots<DIM, CPW>();
+    if (big >= 2 * (int64_t)slots) {
+        k_arr<DIM, CPW><<<(unsigned)std::min<int64_t>(big, slots), kThreads, arr_smem_bytes<DIM, CPW>(), st>>>(q);
+    } else {
+        const int64_t one = (ncell + kWarpsPerCta - 1) / kWarpsPerCta;
+        const int s1 = arr_slots<DIM, 1>();
+        k_arr<DIM, 1><<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(one, s1)), kThreads, arr_smem_bytes<DIM, 1>(),
+                        st>>>(q);
+    }
 }
 
 template <int DIM>
@@ -1207,7 +1243,7 @@ int launch_pd(gx_ctx *c, bool push, cudaStream_t st) {
             q.in = p.out;
             q.cnt_in = p.cnt_out;
             q.mE = nullptr; q.mB = nullptr;
-            k_arr<DIM><<<arr_grid<DIM>(c->N), kThreads, arr_smem_bytes<DIM>(), st>>>(q);
+            launch_arr<DIM>(q, c->N, st);
             GX_LAUNCHED(c);
             if (DIM == 2 && c->cfg.bc_cells > 0) {
                 // open boundaries: the boundary cells' particles are replaced
