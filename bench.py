@@ -564,18 +564,22 @@ def run_precond_compare(gx, wl, steps, barrier, collect_steps=24):
     """Field-solve time per step with the learned preconditioner against plain
     GMRES and block Jacobi on the same plasma.  Three contexts start from the
     same state and step together; the learned one keeps training pairs from its
-    first `collect_steps` solves, trains on the device, then all three are timed
-    for `steps` steps (solve time from CUDA events in the library)."""
+    first `collect_steps` solves (each solve gives (r0, e) and six Krylov pairs,
+    each pair cut into 122 windows of 40^2 nodes: 20,480 crops in a ring, the
+    20k residual/solution pairs of the learned-preconditioner configuration),
+    trains on the device, then all three are timed for `steps` steps (solve time
+    from CUDA events in the library)."""
     kinds = (("plain", gx.GX_PRECOND_NONE), ("jacobi", gx.GX_PRECOND_JACOBI), ("learned", gx.GX_PRECOND_NET))
     ctxs = {k: gx.from_workload(wl, precond=p) for k, p in kinds}
     net = ctxs["learned"]
-    net.precond_collect(512)
+    crops, crop, per_pair = 20480, 32, 122
+    net.precond_collect_crops(crops, crop, per_pair, seed=7)
     for _ in range(collect_steps):
         for c in ctxs.values():
             c.step(1, allow_noconv=True)
     barrier()
     t0 = time.perf_counter()
-    losses = net.precond_train(npairs=512, crop=32, batch=32, epochs=200, lr=2e-3, seed=7)
+    losses = net.precond_train(npairs=512, crop=crop, batch=32, epochs=200, lr=2e-3, seed=7)
     barrier()
     train_s = time.perf_counter() - t0
     net.precond_collect(0)
@@ -591,8 +595,9 @@ def run_precond_compare(gx, wl, steps, barrier, collect_steps=24):
         tm = c.timers(reset=True)
         out[k] = {"ms_per_step": tm["solve_ms"] / steps, "iters_per_step": statistics.mean(its[k])}
     out["learned_speedup_vs_plain"] = out["plain"]["ms_per_step"] / out["learned"]["ms_per_step"]
-    out["training"] = {"pairs": net.precond_pairs(), "collect_steps": collect_steps, "epochs": len(losses),
-                       "samples_per_epoch": 512, "crop": 32, "seconds": train_s,
+    out["training"] = {"pairs": net.precond_pairs(), "pair_kind": f"crops of {crop + 8}^2 nodes ({per_pair} per "
+                       "field pair)", "collect_steps": collect_steps, "epochs": len(losses),
+                       "samples_per_epoch": 512, "crop": crop, "seconds": train_s,
                        "loss_first": float(losses[0]), "loss_last": float(losses[-1])}
     out["note"] = ("solve = LF coefficients + right-hand side + FGMRES to 1e-8 relative residual + field "
                    "advance, FP64; learned = block Jacobi plus a BF16 conv-net correction trained on this "

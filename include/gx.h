@@ -344,6 +344,25 @@ int gx_precond_get_weights(gx_ctx *ctx, float *params, int64_t n, int ptr_is_dev
  * 6, one matrix-vector product each), which resemble what the preconditioner
  * is applied to.  capacity = 0 stops collecting. */
 int gx_precond_collect(gx_ctx *ctx, int capacity);
+
+/* Collect the same pairs as crops: every pair the following converged solves
+ * produce is cut into `per_pair` windows of (crop + 8)^2 nodes (a crop x crop
+ * training window with its 4-node halo, periodic wrap) at positions drawn by a
+ * counter-based hash of `seed`, stored in FP32 already divided by the pair's
+ * scale s = ||r||_2 / sqrt(3 N), as [2][3][crop+8][crop+8] (r / s, then
+ * (e - D^-1 r) / s), with s; up to `capacity` crops (a ring).  About 6 (crop+8)^2
+ * x 4 bytes a crop (38 KB at crop 32), so tens of thousands of training pairs fit
+ * where whole fields would take 12.6 MB each at 1024 x 512.  With gmres_mixed
+ * (FP32 Krylov basis) only (r0, e) is kept per solve.  gx_precond_train then
+ * samples these crops (its `crop` must equal this one) and gx_precond_pairs
+ * counts them.  capacity = 0 stops collecting; crop >= 8, crop + 8 <= nx, ny. */
+int gx_precond_collect_crops(gx_ctx *ctx, int capacity, int crop, int per_pair, uint64_t seed);
+
+/* Copy crop k (0 <= k < gx_precond_pairs) of the crop store to host memory:
+ * out [2][3][crop+8][crop+8] FP32 as stored, *scale its s.  For tests. */
+int gx_precond_crop(gx_ctx *ctx, int k, float *out, float *scale);
+
+/* Number of training pairs kept: field pairs, or crops after gx_precond_collect_crops. */
 int gx_precond_pairs(gx_ctx *ctx);
 
 /* Train the network on the device with Adam (lr, beta1 0.9, beta2 0.999,

@@ -103,6 +103,8 @@ _SIGS = {
     "gx_precond_get_weights": (C.c_int, [_CTX, _V, C.c_int64, C.c_int]),
     "gx_precond_collect": (C.c_int, [_CTX, C.c_int]),
     "gx_precond_pairs": (C.c_int, [_CTX]),
+    "gx_precond_collect_crops": (C.c_int, [_CTX, C.c_int, C.c_int, C.c_int, C.c_uint64]),
+    "gx_precond_crop": (C.c_int, [_CTX, C.c_int, _V, _V]),
     "gx_precond_train": (C.c_int, [_CTX, C.c_int, C.c_int, C.c_int, C.c_int, C.c_float, C.c_uint64, _V, _V]),
     "gx_precond_forward": (C.c_int, [_CTX, C.c_int, C.c_int, _V, _V, _V]),
     "gx_precond_loss_grad": (C.c_int, [_CTX, C.c_int, C.c_int, _V, _V, _V, _V, _V]),
@@ -338,6 +340,16 @@ class Context:
 
     def precond_pairs(self):
         return int(lib().gx_precond_pairs(self.h))
+
+    def precond_collect_crops(self, capacity, crop, per_pair, seed=0):
+        self._check(lib().gx_precond_collect_crops(self.h, int(capacity), int(crop), int(per_pair), int(seed)))
+
+    def precond_crop(self, k, crop):
+        S = crop + 8
+        out = np.empty((2, 3, S, S), np.float32)
+        sc = np.empty(1, np.float32)
+        self._check(lib().gx_precond_crop(self.h, int(k), out.ctypes.data, sc.ctypes.data))
+        return out, float(sc[0])
 
     def precond_train(self, npairs, crop, batch, epochs, lr, seed=0, stream=None):
         losses = np.zeros(epochs, np.float32)

@@ -366,6 +366,69 @@ __global__ void k_store_rt(const double *jd, const double *r, const double *e, i
     }
 }
 
+// crop store: sum of squares of a pair slot's r (for its scale), and the cut of
+// `count` windows of S^2 nodes (periodic) at positions drawn from a counter-based
+// hash of (seed, counter), stored scaled as [2][3][S][S] (r / s, t / s)
+__global__ void k_sumsq_r(const float *r, int64_t n3, double *acc) {
+    double s = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x)
+        s += (double)r[i] * r[i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(acc, s);
+}
+__host__ __device__ inline uint64_t splitmix64(uint64_t x) {
+    x += 0x9E3779B97F4A7C15ull;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    return x ^ (x >> 31);
+}
+struct CutArgs {
+    const float *pair;        // [2][3][N] (r, t)
+    int64_t N;
+    int nx, ny, S;
+    uint64_t seed, counter;   // crop b of this cut: position from splitmix64(seed ^ splitmix64(counter + b))
+    const double *sumsq;      // sum of r^2 over the field
+    float *crops, *scales;    // the store [cap][6][S][S], [cap]
+    int cap, next;
+};
+__global__ void k_cut_crops(CutArgs a) {
+    const int b = blockIdx.y;
+    const uint64_t h = splitmix64(a.seed ^ splitmix64(a.counter + (uint64_t)b));
+    const int x0 = (int)((h & 0xffffffffull) % (uint64_t)a.nx), y0 = (int)((h >> 32) % (uint64_t)a.ny);
+    const double rms = sqrt(*a.sumsq / (3.0 * a.N));
+    const float s = rms > 0 ? (float)rms : 1.f, inv = 1.f / s;
+    const int slot = (a.next + b) % a.cap;
+    float *dst = a.crops + (size_t)slot * 6 * a.S * a.S;
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.scales[slot] = s;
+    const int SS = a.S * a.S;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < SS; t += gridDim.x * blockDim.x) {
+        const int yy = t / a.S, xx = t % a.S;
+        const int gy = wrapn(y0 + yy, a.ny), gx = wrapn(x0 + xx, a.nx);
+        const int64_t q = gy * (int64_t)a.nx + gx;
+#pragma unroll
+        for (int c = 0; c < 6; ++c) dst[(size_t)c * SS + t] = a.pair[(size_t)c * a.N + q] * inv;
+    }
+}
+// a training batch from the crop store: input r / s (BF16, halo ring), target t / s
+// on the central C^2
+__global__ void k_crop_gather_store(const float *crops, const CropSpec *spec, int C, bf16 *x0, float *target) {
+    const int b = blockIdx.y;
+    const int S = C + 8, SS = S * S;
+    const float *src = crops + (size_t)spec[b].pair * 6 * SS;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < SS; t += gridDim.x * blockDim.x) {
+        const int yy = t / S, xx = t % S;
+        const __nv_bfloat162 p01 = __floats2bfloat162_rn(src[t], src[SS + t]);
+        const __nv_bfloat162 p2 = __floats2bfloat162_rn(src[2 * SS + t], 0.f);
+        const uint4 val[2] = {make_uint4(*reinterpret_cast<const uint32_t *>(&p01),
+                                         *reinterpret_cast<const uint32_t *>(&p2), 0, 0),
+                              make_uint4(0, 0, 0, 0)};
+        gxv::store_with_halo<16>(x0, b, yy, xx, S, S, 0, val);
+        const bool inner = yy >= 4 && yy < 4 + C && xx >= 4 && xx < 4 + C;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) target[((int64_t)b * SS + t) * 3 + c] = inner ? src[(3 + c) * SS + t] : 0.f;
+    }
+}
+
 inline int nblk(int64_t n, int b = 256) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + b - 1) / b, 152 * 16)); }
 
 }  // namespace
@@ -388,6 +451,12 @@ struct Net {
     float *pairs = nullptr;
     int cap_pairs = 0, npairs = 0, next_pair = 0, collect = 0;
     int pending_pair = 0;
+    // crop store (gx_precond_collect_crops): [cap][2][3][S][S] scaled windows and their
+    // scales; the pair slots above then hold one field pair, the cut's source
+    float *crops = nullptr, *cscales = nullptr;
+    double *csum = nullptr;
+    int crop_mode = 0, cap_crops = 0, ncrops = 0, next_crop = 0, crop_C = 0, per_pair = 0;
+    uint64_t crop_seed = 0, crop_counter = 0;
     int adam_t = 0;
 };
 
@@ -594,9 +663,30 @@ int gx_net_pair_begin(gx_ctx *c, const double *r0, cudaStream_t st) {
     return GX_OK;
 }
 
-static void advance_slot(Net *n) {
-    n->next_pair = (n->next_pair + 1) % n->cap_pairs;
-    n->npairs = std::min(n->npairs + 1, n->cap_pairs);
+// the pair slot next_pair is complete: keep it (ring of field pairs), or, with the
+// crop store, cut its windows and reuse the slot
+static int advance_slot(gx_ctx *c, cudaStream_t st) {
+    Net *n = c->net;
+    if (!n->crop_mode) {
+        n->next_pair = (n->next_pair + 1) % n->cap_pairs;
+        n->npairs = std::min(n->npairs + 1, n->cap_pairs);
+        return GX_OK;
+    }
+    const float *pair = n->pairs + (size_t)n->next_pair * 6 * c->N;
+    GX_CHECK(c, cudaMemsetAsync(n->csum, 0, sizeof(double), st));
+    k_sumsq_r<<<nblk(3 * c->N), 256, 0, st>>>(pair, 3 * c->N, n->csum);
+    GX_LAUNCHED(c);
+    CutArgs a{};
+    a.pair = pair; a.N = c->N; a.nx = c->n[0]; a.ny = c->n[1]; a.S = n->crop_C + 8;
+    a.seed = n->crop_seed; a.counter = n->crop_counter; a.sumsq = n->csum;
+    a.crops = n->crops; a.scales = n->cscales; a.cap = n->cap_crops; a.next = n->next_crop;
+    const int cnt = std::min(n->per_pair, n->cap_crops);
+    k_cut_crops<<<dim3(std::max(1, (a.S * a.S + 255) / 256), cnt), 256, 0, st>>>(a);
+    GX_LAUNCHED(c);
+    n->crop_counter += (uint64_t)cnt;
+    n->next_crop = (n->next_crop + cnt) % n->cap_crops;
+    n->ncrops = std::min(n->ncrops + cnt, n->cap_crops);
+    return GX_OK;
 }
 
 int gx_net_pair_end(gx_ctx *c, int converged, int nbasis, cudaStream_t st) {
@@ -608,16 +698,18 @@ int gx_net_pair_end(gx_ctx *c, int converged, int nbasis, cudaStream_t st) {
     float *dst = n->pairs + (size_t)n->next_pair * 6 * c->N;
     k_store_t<<<nblk(c->N), 256, 0, st>>>(c->jdiag, c->Eth, c->E, c->N, dst);
     GX_LAUNCHED(c);
-    advance_slot(n);
-    const int nv = std::min(nbasis, kKrylovPairs);
+    int rc = advance_slot(c, st);
+    if (rc) return rc;
+    // the mixed-precision solve keeps its Krylov basis in FP32: only (r0, e) then
+    const int nv = c->cfg.gmres_mixed ? 0 : std::min(nbasis, kKrylovPairs);
     for (int j = 0; j < nv; ++j) {
         const double *v = c->V + (size_t)j * n3;
-        int rc = gx_apply_A(c, v, c->w, st);
+        rc = gx_apply_A(c, v, c->w, st);
         if (rc) return rc;
         dst = n->pairs + (size_t)n->next_pair * 6 * c->N;
         k_store_rt<<<nblk(c->N), 256, 0, st>>>(c->jdiag, c->w, v, c->N, dst);
         GX_LAUNCHED(c);
-        advance_slot(n);
+        if ((rc = advance_slot(c, st))) return rc;
     }
     return GX_OK;
 }
@@ -626,7 +718,7 @@ void gx_net_free(gx_ctx *c) {
     Net *n = c->net;
     if (!n) return;
     void *ps[] = {n->params, n->grad, n->m1, n->m2, n->x0, n->h1, n->h2, n->h3, n->d4, n->d3, n->d2, n->d1, n->y,
-                  n->target, n->dsum, n->pairs, n->flags};
+                  n->target, n->dsum, n->pairs, n->flags, n->crops, n->cscales, n->csum};
     for (void *p : ps)
         if (p) cudaFree(p);
     for (int l = 0; l < kNL; ++l) {
@@ -677,6 +769,7 @@ int gx_precond_collect(gx_ctx *c, int capacity) {
     if (rc) return rc;
     Net *n = c->net;
     if (capacity == 0) { n->collect = 0; return GX_OK; }
+    n->crop_mode = 0;
     if (capacity != n->cap_pairs) {
         if (n->pairs) cudaFree(n->pairs);
         n->pairs = nullptr;
@@ -689,14 +782,72 @@ int gx_precond_collect(gx_ctx *c, int capacity) {
     return GX_OK;
 }
 
-int gx_precond_pairs(gx_ctx *c) { return c ? (c->net ? c->net->npairs : 0) : -1; }
+int gx_precond_collect_crops(gx_ctx *c, int capacity, int crop, int per_pair, uint64_t seed) {
+    if (!c || capacity < 0 || (capacity > 0 && (crop < 8 || per_pair < 1))) return GX_EINVAL;
+    if (c->dim != 2) { c->err = "the learned preconditioner is 2D"; return GX_ENOTIMPL; }
+    int rc = net_alloc(c);
+    if (rc) return rc;
+    Net *n = c->net;
+    if (capacity == 0) { n->collect = 0; return GX_OK; }
+    const int S = crop + 8;
+    if (S > c->n[0] || S > c->n[1]) { c->err = "crop + 8 exceeds the grid"; return GX_EINVAL; }
+    // one field pair slot as the cut's source
+    if (n->cap_pairs != 1) {
+        if (n->pairs) cudaFree(n->pairs);
+        n->pairs = nullptr;
+        GX_CHECK(c, cudaMalloc(&n->pairs, (size_t)6 * c->N * sizeof(float)));
+        n->cap_pairs = 1;
+    }
+    n->npairs = 0;
+    n->next_pair = 0;
+    if (capacity != n->cap_crops || crop != n->crop_C) {
+        if (n->crops) cudaFree(n->crops);
+        if (n->cscales) cudaFree(n->cscales);
+        n->crops = nullptr;
+        n->cscales = nullptr;
+        GX_CHECK(c, cudaMalloc(&n->crops, (size_t)capacity * 6 * S * S * sizeof(float)));
+        GX_CHECK(c, cudaMalloc(&n->cscales, (size_t)capacity * sizeof(float)));
+        n->cap_crops = capacity;
+        n->crop_C = crop;
+        n->ncrops = 0;
+        n->next_crop = 0;
+    }
+    if (!n->csum) GX_CHECK(c, cudaMalloc(&n->csum, sizeof(double)));
+    n->per_pair = per_pair;
+    n->crop_seed = seed;
+    n->crop_mode = 1;
+    n->collect = 1;
+    return GX_OK;
+}
+
+int gx_precond_crop(gx_ctx *c, int k, float *out, float *scale) {
+    if (!c || !out || !scale) return GX_EINVAL;
+    Net *n = c->net;
+    if (!n || !n->crop_mode || k < 0 || k >= n->ncrops) { if (c) c->err = "no such crop"; return GX_EINVAL; }
+    const int S = n->crop_C + 8;
+    GX_CHECK(c, cudaMemcpy(out, n->crops + (size_t)k * 6 * S * S, (size_t)6 * S * S * sizeof(float),
+                           cudaMemcpyDeviceToHost));
+    GX_CHECK(c, cudaMemcpy(scale, n->cscales + k, sizeof(float), cudaMemcpyDeviceToHost));
+    return GX_OK;
+}
+
+int gx_precond_pairs(gx_ctx *c) {
+    if (!c) return -1;
+    if (!c->net) return 0;
+    return c->net->crop_mode ? c->net->ncrops : c->net->npairs;
+}
 
 int gx_precond_train(gx_ctx *c, int npairs, int crop, int batch, int epochs, float lr, uint64_t seed,
                      float *loss_out, void *stream) {
     if (!c || npairs < 1 || crop < 8 || batch < 1 || epochs < 1 || !(lr > 0)) return GX_EINVAL;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     Net *n = c->net;
-    if (!n || n->npairs < 1) { c->err = "no collected pairs: call gx_precond_collect and run some solves"; return GX_ESTATE; }
+    const bool from_crops = n && n->crop_mode;
+    if (!n || (from_crops ? n->ncrops : n->npairs) < 1) {
+        c->err = "no collected pairs: call gx_precond_collect and run some solves";
+        return GX_ESTATE;
+    }
+    if (from_crops && crop != n->crop_C) { c->err = "crop differs from the collected crops' size"; return GX_EINVAL; }
     if (!n->have_weights) { int rc = net_refresh(c, st); if (rc) return rc; }
     const int S = crop + 8;
     int rc = net_reserve(c, batch, S, S);
@@ -717,17 +868,23 @@ int gx_precond_train(gx_ctx *c, int npairs, int crop, int batch, int epochs, flo
         for (int done = 0; done < npairs; done += batch, ++nb) {
             const int B = std::min(batch, npairs - done);
             for (int b = 0; b < B; ++b) {
-                spec[b].pair = (int)(rng() % (uint64_t)n->npairs);
+                spec[b].pair = (int)(rng() % (uint64_t)(from_crops ? n->ncrops : n->npairs));
                 spec[b].y0 = (int)(rng() % (uint64_t)c->n[1]);
                 spec[b].x0 = (int)(rng() % (uint64_t)c->n[0]);
                 spec[b].pad = 0;
             }
             GX_CHECK(c, cudaMemcpyAsync(dspec, spec.data(), B * sizeof(CropSpec), cudaMemcpyHostToDevice, st));
-            k_crop_scale<<<B, 1024, 0, st>>>(n->pairs, c->N, dspec, dscale);
-            GX_LAUNCHED(c);
-            k_crop_gather<<<dim3(nblk((int64_t)S * S), B), 256, 0, st>>>(n->pairs, c->N, c->n[0], c->n[1], dspec, crop,
-                                                                           dscale, n->x0, n->target);
-            GX_LAUNCHED(c);
+            if (from_crops) {
+                k_crop_gather_store<<<dim3(nblk((int64_t)S * S), B), 256, 0, st>>>(n->crops, dspec, crop, n->x0,
+                                                                                   n->target);
+                GX_LAUNCHED(c);
+            } else {
+                k_crop_scale<<<B, 1024, 0, st>>>(n->pairs, c->N, dspec, dscale);
+                GX_LAUNCHED(c);
+                k_crop_gather<<<dim3(nblk((int64_t)S * S), B), 256, 0, st>>>(n->pairs, c->N, c->n[0], c->n[1], dspec,
+                                                                               crop, dscale, n->x0, n->target);
+                GX_LAUNCHED(c);
+            }
             if ((rc = net_forward(c, B, S, S, 0, st))) return rc;
             const float inv_nout = 1.f / (3.f * crop * crop * B);
             k_loss<<<nblk((int64_t)B * S * S), 256, 0, st>>>(n->y, n->target, B, S, S, 4, 4, crop, crop, inv_nout,

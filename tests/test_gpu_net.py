@@ -271,3 +271,66 @@ def test_trained_network_reduces_gmres_iterations(env):
     finally:
         for c in ctxs.values():
             c.close()
+
+
+def _splitmix64(x):
+    m = (1 << 64) - 1
+    x = (x + 0x9E3779B97F4A7C15) & m
+    x = ((x ^ (x >> 30)) * 0xBF58476D1CE4E5B9) & m
+    x = ((x ^ (x >> 27)) * 0x94D049BB133111EB) & m
+    return x ^ (x >> 31)
+
+
+def test_crop_store_geometry_and_training(env):
+    """The crop store (gx_precond_collect_crops): every collected pair is cut into
+    per_pair windows at the documented hash positions; windows of one pair agree
+    wherever they overlap on the periodic grid (same field values, same scale),
+    the scale is the pair's s > 0, the count is the ring's, and a network trained
+    on the crops alone still cuts the Krylov steps of the solve."""
+    g, torch, _ = env
+    wl = workloads.harris(nx=64, ny=32, ppc=16, steps=40)
+    C, per, seed = 16, 48, 11
+    S = C + 8
+    ctxs = {k: g.from_workload(wl, precond=p) for k, p in
+            (("plain", g.GX_PRECOND_NONE), ("net", g.GX_PRECOND_NET))}
+    try:
+        net = ctxs["net"]
+        net.precond_collect_crops(4096, C, per, seed)
+        its = {k: [] for k in ctxs}
+        for _ in range(12):
+            for k, c in ctxs.items():
+                its[k].append(c.step(1).iters)
+        n = net.precond_pairs()
+        assert n == min(4096, 12 * 7 * per), n           # (r0, e) and 6 Krylov pairs per solve
+        # the first pair's windows: positions from the hash, overlaps consistent
+        nx, ny = wl.n[0], wl.n[1]
+        full = np.full((6, ny, nx), np.nan)
+        scales = set()
+        for b in range(per):
+            crop, s = net.precond_crop(b, C)
+            assert np.all(np.isfinite(crop)) and s > 0
+            scales.add(s)
+            h = _splitmix64(seed ^ _splitmix64(b))
+            x0, y0 = (h & 0xFFFFFFFF) % nx, (h >> 32) % ny
+            vals = crop.reshape(6, S, S)
+            ys = (y0 + np.arange(S)) % ny
+            xs = (x0 + np.arange(S)) % nx
+            prev = full[:, ys[:, None], xs[None, :]]
+            seen = np.isfinite(prev)
+            assert np.array_equal(prev[seen], vals[seen]), b
+            full[:, ys[:, None], xs[None, :]] = vals
+        assert len(scales) == 1                          # one pair, one scale
+        assert np.isfinite(full).mean() > 0.9            # the windows cover most of the grid
+        losses = net.precond_train(npairs=256, crop=C, batch=32, epochs=300, lr=3e-3, seed=3)
+        assert np.all(np.isfinite(losses)) and losses[-1] < 0.5 * losses[0], losses
+        net.precond_collect(0)
+        after = {k: [] for k in ctxs}
+        for _ in range(8):
+            for k, c in ctxs.items():
+                st = c.step(1)
+                assert st.converged and st.relres <= wl.gmres_tol, (k, st.relres)
+                after[k].append(st.iters)
+        assert np.mean(after["net"]) < np.mean(after["plain"]), (after, its)
+    finally:
+        for c in ctxs.values():
+            c.close()
