@@ -86,15 +86,19 @@ static_assert(kBNet % gxv::kThreads == 0 && kBNet / gxv::kThreads <= 2, "the con
 #define NODE_LOOP(q) \
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < N; q += (int64_t)gridDim.x * blockDim.x)
 
-// CTA sums of up to 8 thread values -> dst[0..kk) (global partial row)
-__device__ __forceinline__ void cta_partials(double acc[8], int kk, double *sred, double *dst) {
+// CTA sums of kk <= 8 thread values -> dst[0..kk) (global partial row).  AT is the
+// type of the thread and warp sums: double, or float for the mixed-precision cycles
+// (whose vectors are FP32); the sums across warps and CTAs are FP64 either way.
+template <typename AT>
+__device__ __forceinline__ void cta_partials(AT acc[8], int kk, double *sred, double *dst) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-        double v = acc[i];
+        if (i >= kk) break;                                   // kk is the same for the whole CTA
+        AT v = acc[i];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) sred[warp * 8 + i] = v;
+        if (lane == 0) sred[warp * 8 + i] = (double)v;
     }
     __syncthreads();
     if (threadIdx.x < kk) {
@@ -323,7 +327,7 @@ __global__ void __launch_bounds__(NET ? kBNet : kB, NET ? 1 : 2) k_fgmres(const 
         const VT *zj = (flex ? Z : V) + (size_t)j * n;
         // pass 1: w = A z_j, partial h0_i = V_i . w
         for (int i0 = 0; i0 < k; i0 += 8) {
-            double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            VT acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
             NODE_LOOP(q) {
                 VT wq[3];
                 if (i0 == 0) {
@@ -338,7 +342,7 @@ __global__ void __launch_bounds__(NET ? kBNet : kB, NET ? 1 : 2) k_fgmres(const 
                 for (int ii = 0; ii < 8; ++ii)
                     if (i0 + ii < k) {
                         const VT *vi = V + (size_t)(i0 + ii) * n;
-                        acc[ii] += (double)(vi[q] * wq[0] + vi[N + q] * wq[1] + vi[2 * N + q] * wq[2]);
+                        acc[ii] += vi[q] * wq[0] + vi[N + q] * wq[1] + vi[2 * N + q] * wq[2];
                     }
             }
             cta_partials(acc, min(8, k - i0), sred, prow(a, ph) + i0);
@@ -356,14 +360,14 @@ __global__ void __launch_bounds__(NET ? kBNet : kB, NET ? 1 : 2) k_fgmres(const 
             }
         }
         for (int i0 = 0; i0 < k; i0 += 8) {
-            double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            VT acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
             NODE_LOOP(q) {
                 const VT w0 = w[q], w1 = w[N + q], w2 = w[2 * N + q];
 #pragma unroll
                 for (int ii = 0; ii < 8; ++ii)
                     if (i0 + ii < k) {
                         const VT *vi = V + (size_t)(i0 + ii) * n;
-                        acc[ii] += (double)(vi[q] * w0 + vi[N + q] * w1 + vi[2 * N + q] * w2);
+                        acc[ii] += vi[q] * w0 + vi[N + q] * w1 + vi[2 * N + q] * w2;
                     }
             }
             cta_partials(acc, min(8, k - i0), sred, prow(a, ph) + i0);
@@ -373,14 +377,14 @@ __global__ void __launch_bounds__(NET ? kBNet : kB, NET ? 1 : 2) k_fgmres(const 
         ++ph;
         // pass 3: w -= sum h1_i V_i, partial ||w||^2
         {
-            double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            VT acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
             NODE_LOOP(q) {
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
                     VT v = w[c * N + q];
                     for (int i = 0; i < k; ++i) v -= (VT)hs[1][i] * V[(size_t)i * n + c * N + q];
                     w[c * N + q] = v;
-                    acc[0] += (double)v * (double)v;
+                    acc[0] += v * v;
                 }
             }
             cta_partials(acc, 1, sred, prow(a, ph));
