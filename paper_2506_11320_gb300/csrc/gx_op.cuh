@@ -166,7 +166,7 @@ __device__ __forceinline__ void gx_apply_A3_node(const OpArgs &a, const T *__res
     const T *A = nullptr;
     if constexpr (sizeof(T) == 4) A = a.A3f;
     else A = a.A3;
-#pragma unroll 3
+#pragma unroll 1
     for (int o = 0; o < 27; ++o) {
         const int64_t nb = g.id(i + o % 3 - 1, j + (o / 3) % 3 - 1, k + o / 9 - 1);
         T xv[3];
