@@ -65,7 +65,7 @@ template <> struct Geo<3> {
 // shared floats per warp: the cell's interpolation coefficients [4][NC] float4,
 // then the factor table [32][TSTR], which at the end of a cell holds the groups'
 // sums [KG][ROWS][16] followed by their totals [ROWS][16]; after the warps, the
-// CTA's two record-tile stages
+// CTA's record-tile stages (pd_stages)
 template <int DIM>
 __host__ __device__ constexpr int table_floats() {
     return 32 * Geo<DIM>::TSTR > (Geo<DIM>::KG + 1) * Geo<DIM>::ROWS * kCols
@@ -76,9 +76,15 @@ template <int DIM>
 __host__ __device__ constexpr int warp_floats() {
     return 16 * Geo<DIM>::NC + table_floats<DIM>();
 }
+// record-tile stages, double-buffered: in 2D two tiles are staged between CTA
+// barriers (one barrier per two tiles, so a warp's cells of two tiles even out);
+// in 3D one (the larger shared footprint cost more than the barrier saved)
+template <int DIM>
+__host__ __device__ constexpr int pd_stages() { return DIM == 2 ? 4 : 2; }
 template <int DIM>
 constexpr size_t pd_smem_bytes() {
-    return ((size_t)kWarpsPerCta * warp_floats<DIM>() + 2 * (size_t)Rec<DIM>::SIZE * kRecTile) * sizeof(float);
+    return ((size_t)kWarpsPerCta * warp_floats<DIM>() + pd_stages<DIM>() * (size_t)Rec<DIM>::SIZE * kRecTile) *
+           sizeof(float);
 }
 static_assert(kWarpsPerCta == kRecTile, "one warp per cell of a record tile");
 
@@ -277,7 +283,8 @@ __global__ void __launch_bounds__(kThreads, Geo<DIM>::CTAS) k_pd(const __grid_co
     float *ws = smem + (size_t)warp * warp_floats<DIM>();
     float4 *cor = reinterpret_cast<float4 *>(ws);            // [4][NC] coefficients: mover E, mover B, deposit B, u_ref
     float *T = ws + 16 * NC;                                  // factor table [32][TSTR]; at a cell's end the sums
-    float *stage = smem + (size_t)kWarpsPerCta * warp_floats<DIM>();   // [2][TILE]
+    float *stage = smem + (size_t)kWarpsPerCta * warp_floats<DIM>();   // [pd_stages][TILE]
+    constexpr int NST = pd_stages<DIM>(), TPB = NST / 2;     // stages, tiles per CTA barrier
     const unsigned lt = (1u << lane) - 1u;
     // this lane's block and particle group: group kg walks the particles
     // KG s + pg; in 2D the two groups of a quarter warp take particles 4 apart,
@@ -538,7 +545,7 @@ __global__ void __launch_bounds__(kThreads, Geo<DIM>::CTAS) k_pd(const __grid_co
         if (n == 0 && has_next) fetch(bin_nx, wnext, 0);
         // the stayers' count (the bottom segment) of this cell's new bin
         if (PUSH && lane == 0 && fbase > 0) atomicAdd(p.cnt_out + cell, fbase);
-        float *st = stage + (size_t)(it & 1) * TILE;
+        float *st = stage + (size_t)(it & (NST - 1)) * TILE;
         if (n > 0) {
             // the groups' sums: S[kg][pair class][column], this lane's 9 x 4 block
             if (role) {
@@ -569,17 +576,20 @@ __global__ void __launch_bounds__(kThreads, Geo<DIM>::CTAS) k_pd(const __grid_co
         } else {
             for (int k = lane; k < R::SIZE; k += 32) st[k * kRecTile + warp] = 0.f;
         }
-        // ---- the tile's record block: written whole (or added, for the arrivals)
-        __syncthreads();
-        {
-            const float4 *src = reinterpret_cast<const float4 *>(st);
-            float4 *dst = reinterpret_cast<float4 *>(p.rec + (size_t)t * TILE);
-            for (int i = threadIdx.x; i < TILE / 4; i += kThreads) {
-                const float4 v = src[i];
-                if (p.arrivals) {
-                    if (v.x != 0.f || v.y != 0.f || v.z != 0.f || v.w != 0.f) atomicAdd(dst + i, v);
-                } else {
-                    dst[i] = v;
+        // ---- the record blocks of the tiles staged since the last barrier: written whole
+        // (or added, for the arrivals) after one CTA barrier
+        if (it % TPB == TPB - 1 || t + gridDim.x >= ntiles) {
+            __syncthreads();
+            for (int h = it % TPB; h >= 0; --h) {
+                const float4 *src = reinterpret_cast<const float4 *>(stage + (size_t)((it - h) & (NST - 1)) * TILE);
+                float4 *dst = reinterpret_cast<float4 *>(p.rec + (size_t)(t - (int64_t)h * gridDim.x) * TILE);
+                for (int i = threadIdx.x; i < TILE / 4; i += kThreads) {
+                    const float4 v = src[i];
+                    if (p.arrivals) {
+                        if (v.x != 0.f || v.y != 0.f || v.z != 0.f || v.w != 0.f) atomicAdd(dst + i, v);
+                    } else {
+                        dst[i] = v;
+                    }
                 }
             }
         }
