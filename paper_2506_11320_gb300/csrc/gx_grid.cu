@@ -196,38 +196,30 @@ __global__ void __launch_bounds__(kB, kNodeCtas) k_assemble_main(G2 g, SpecK sk,
                     for (int k = 0; k < 3; ++k) du[dy + 1][dx + 1][k] = (float)(u[k * N + nb] - uref[k * N + nb]);
                 }
         }
-        for (int s = 0; s < sk.ns; ++s) {
-            float js[3] = {0.f, 0.f, 0.f};
+        // the raw current: the J entries of the 4 cells (corner a of each is this node)
+        float js[GX_MAX_SPECIES][3];
+#pragma unroll
+        for (int s = 0; s < GX_MAX_SPECIES; ++s) js[s][0] = js[s][1] = js[s][2] = 0.f;
+#pragma unroll
+        for (int s = 0; s < GX_MAX_SPECIES; ++s) {
+            if (s >= sk.ns) break;
 #pragma unroll
             for (int cy = -1; cy <= 0; ++cy)
 #pragma unroll
                 for (int cx = -1; cx <= 0; ++cx) {
                     const int64_t cell = g.id(i + cx, j + cy);
-                    const int ax = -cx, ay = -cy, a = ax + 2 * ay;
+                    const int a = -cx + 2 * (-cy);
 #pragma unroll
-                    for (int k = 0; k < 3; ++k) js[k] += R.get(s, Rec<2>::J + 3 * a + k, cell);
-                    if (comoving) {
-#pragma unroll
-                        for (int b = 0; b < 4; ++b) {
-                            const int bx = b & 1, by = b >> 1;
-                            const int jx = (ax == bx) ? 2 * ax : 1, jy = (ay == by) ? 2 * ay : 1;
-                            const int mrow = Rec<2>::M + 9 * (jx + 3 * jy);
-                            const float *d = du[cy + by + 1][cx + bx + 1];
-#pragma unroll
-                            for (int r = 0; r < 3; ++r)
-                                js[r] -= R.get(s, mrow + 3 * r, cell) * d[0] + R.get(s, mrow + 3 * r + 1, cell) * d[1] +
-                                         R.get(s, mrow + 3 * r + 2, cell) * d[2];
-                        }
-                    }
+                    for (int k = 0; k < 3; ++k) js[s][k] += R.get(s, Rec<2>::J + 3 * a + k, cell);
                 }
-#pragma unroll
-            for (int k = 0; k < 3; ++k) jc[k] += sk.q[s] * (double)js[k];
         }
-#pragma unroll
-        for (int k = 0; k < 3; ++k) J[k * N + q] = jc[k] * inv_dV;
+        // the mass-matrix blocks; the comoving correction -M^0 (u - u_ref) reads the same
+        // record entries (block o of this node pairs it with node q + o, whose u - u_ref
+        // the entries multiply), so it is accumulated here, each entry loaded once
 #pragma unroll
         for (int o = 0; o < 9; ++o) {
             const int ox = o % 3 - 1, oy = o / 3 - 1;
+            const float *d = du[oy + 1][ox + 1];
             float blk[9];
 #pragma unroll
             for (int e = 0; e < 9; ++e) blk[e] = 0.f;
@@ -242,10 +234,21 @@ __global__ void __launch_bounds__(kB, kNodeCtas) k_assemble_main(G2 g, SpecK sk,
                     const int jx = ox == 0 ? (cx == -1 ? 2 : 0) : 1;
                     const int64_t cell = g.id(i + cx, j + cy);
                     const int mrow = Rec<2>::M + 9 * (jx + 3 * jy);
-                    for (int s = 0; s < sk.ns; ++s) {
-                        const float f = sk.bqf[s];
 #pragma unroll
-                        for (int e = 0; e < 9; ++e) blk[e] = fmaf(f, R.get(s, mrow + e, cell), blk[e]);
+                    for (int s = 0; s < GX_MAX_SPECIES; ++s) {
+                        if (s >= sk.ns) break;
+                        const float f = sk.bqf[s];
+                        float mv[9];
+#pragma unroll
+                        for (int e = 0; e < 9; ++e) {
+                            mv[e] = R.get(s, mrow + e, cell);
+                            blk[e] = fmaf(f, mv[e], blk[e]);
+                        }
+                        if (comoving) {
+#pragma unroll
+                            for (int r = 0; r < 3; ++r)
+                                js[s][r] -= mv[3 * r] * d[0] + mv[3 * r + 1] * d[1] + mv[3 * r + 2] * d[2];
+                        }
                     }
                 }
             }
@@ -255,6 +258,13 @@ __global__ void __launch_bounds__(kB, kNodeCtas) k_assemble_main(G2 g, SpecK sk,
 #pragma unroll
                 for (int e = 0; e < 9; ++e) M32[(size_t)(o * 9 + e) * N + q] = blk[e];
         }
+#pragma unroll
+        for (int s = 0; s < GX_MAX_SPECIES; ++s)
+            if (s < sk.ns)
+#pragma unroll
+                for (int k = 0; k < 3; ++k) jc[k] += sk.q[s] * (double)js[s][k];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) J[k * N + q] = jc[k] * inv_dV;
     }
 }
 
