@@ -57,10 +57,10 @@ constexpr unsigned kFull = 0xffffffffu;
 // lanes per particle group (RG x 4 column quads), KG groups
 template <int DIM> struct Geo;
 template <> struct Geo<2> {
-    static constexpr int NC = 4, ROWS = 9, TSTR = 28, COLOFF = 12, LK = 4, KG = 8, CENTER = 4, CTAS = 2;
+    static constexpr int NC = 4, ROWS = 9, TSTR = 28, COLOFF = 12, NCB = 2, LK = 8, KG = 4, CENTER = 4, CTAS = 3;
 };
 template <> struct Geo<3> {
-    static constexpr int NC = 8, ROWS = 27, TSTR = 52, COLOFF = 36, LK = 12, KG = 2, CENTER = 13, CTAS = 2;
+    static constexpr int NC = 8, ROWS = 27, TSTR = 52, COLOFF = 36, NCB = 4, LK = 12, KG = 2, CENTER = 13, CTAS = 2;
 };
 // shared floats per warp: the cell's interpolation coefficients [4][NC] float4,
 // then the factor table [32][TSTR], which at the end of a cell holds the groups'
@@ -291,8 +291,9 @@ __global__ void __launch_bounds__(kThreads, Geo<DIM>::CTAS) k_pd(const __grid_co
     // which puts their table reads in different banks
     const int kg = lane / G::LK, lk = lane % G::LK;
     const bool role = kg < G::KG;
-    const int pg = DIM == 2 ? (kg >> 1) + 4 * (kg & 1) : kg;
-    const int roff = 12 * (lk / 4), coff = G::COLOFF + 4 * (lk % 4);
+    const int pg = kg;
+    constexpr int NCB = G::NCB, NQ = kCols / NCB;             // columns of a lane's block, blocks per row set
+    const int roff = 12 * (lk / NQ), coff = G::COLOFF + NCB * (lk % NQ);
     const bool res[3] = {p.n[0] > 1, p.n[1] > 1, DIM == 3 && p.n[2] > 1};
     const int64_t ntiles = (p.N + kRecTile - 1) / kRecTile;
     const int64_t cstride = (int64_t)p.cap * p.nf;           // floats per bin
@@ -357,10 +358,10 @@ __global__ void __launch_bounds__(kThreads, Geo<DIM>::CTAS) k_pd(const __grid_co
             if (lane < 4 * NC) cor[lane] = v;
         }
         __syncwarp();
-        float2 accp[4][4];                                    // [column][row pair]: rows 0..7 of the block
-        float acc8[4];                                        // row 8
+        float2 accp[NCB][4];                                  // [column][row pair]: rows 0..7 of the block
+        float acc8[NCB];                                      // row 8
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
+        for (int c = 0; c < NCB; ++c) {
             acc8[c] = 0.f;
 #pragma unroll
             for (int r = 0; r < 4; ++r) accp[c][r] = make_float2(0.f, 0.f);
@@ -512,10 +513,16 @@ __global__ void __launch_bounds__(kThreads, Geo<DIM>::CTAS) k_pd(const __grid_co
                 const float4 r03 = *reinterpret_cast<const float4 *>(tp + roff);
                 const float4 r47 = *reinterpret_cast<const float4 *>(tp + roff + 4);
                 const float r8 = tp[roff + 8];
-                const float4 cv = *reinterpret_cast<const float4 *>(tp + coff);
-                const float cc[4] = {cv.x, cv.y, cv.z, cv.w};
+                float cc[NCB];
+                if constexpr (NCB == 4) {
+                    const float4 cv = *reinterpret_cast<const float4 *>(tp + coff);
+                    cc[0] = cv.x; cc[1] = cv.y; cc[2] = cv.z; cc[3] = cv.w;
+                } else {
+                    const float2 cv = *reinterpret_cast<const float2 *>(tp + coff);
+                    cc[0] = cv.x; cc[1] = cv.y;
+                }
 #pragma unroll
-                for (int c = 0; c < 4; ++c) {
+                for (int c = 0; c < NCB; ++c) {
                     const float2 d = make_float2(cc[c], cc[c]);
                     accp[c][0] = __ffma2_rn(make_float2(r03.x, r03.y), d, accp[c][0]);
                     accp[c][1] = __ffma2_rn(make_float2(r03.z, r03.w), d, accp[c][1]);
@@ -549,14 +556,16 @@ __global__ void __launch_bounds__(kThreads, Geo<DIM>::CTAS) k_pd(const __grid_co
         if (n > 0) {
             // the groups' sums: S[kg][pair class][column], this lane's 9 x 4 block
             if (role) {
-                float4 *sd = reinterpret_cast<float4 *>(T + (kg * G::ROWS + 9 * (lk / 4)) * kCols + 4 * (lk % 4));
+                float *sd = T + (kg * G::ROWS + 9 * (lk / NQ)) * kCols + NCB * (lk % NQ);
 #pragma unroll
-                for (int ip = 0; ip < 4; ++ip) {
-                    sd[(2 * ip) * (kCols / 4)] = make_float4(accp[0][ip].x, accp[1][ip].x, accp[2][ip].x, accp[3][ip].x);
-                    sd[(2 * ip + 1) * (kCols / 4)] =
-                        make_float4(accp[0][ip].y, accp[1][ip].y, accp[2][ip].y, accp[3][ip].y);
-                }
-                sd[8 * (kCols / 4)] = make_float4(acc8[0], acc8[1], acc8[2], acc8[3]);
+                for (int ip = 0; ip < 4; ++ip)
+#pragma unroll
+                    for (int c = 0; c < NCB; ++c) {
+                        sd[(2 * ip) * kCols + c] = accp[c][ip].x;
+                        sd[(2 * ip + 1) * kCols + c] = accp[c][ip].y;
+                    }
+#pragma unroll
+                for (int c = 0; c < NCB; ++c) sd[8 * kCols + c] = acc8[c];
             }
             __syncwarp();
             // totals over the groups, Gs[pair class][column], one column quad per lane and item
