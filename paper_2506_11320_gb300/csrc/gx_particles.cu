@@ -293,6 +293,7 @@ __global__ void __launch_bounds__(kThreads, Geo<DIM>::CTAS) k_pd(const __grid_co
     const bool role = kg < G::KG;
     const int pg = kg;
     constexpr int NCB = G::NCB, NQ = kCols / NCB;             // columns of a lane's block, blocks per row set
+    static_assert(NCB == 1 || NCB == 2 || NCB == 4, "lane blocks of 1, 2 or 4 columns");
     const int roff = 12 * (lk / NQ), coff = G::COLOFF + NCB * (lk % NQ);
     const bool res[3] = {p.n[0] > 1, p.n[1] > 1, DIM == 3 && p.n[2] > 1};
     const int64_t ntiles = (p.N + kRecTile - 1) / kRecTile;
@@ -517,9 +518,11 @@ __global__ void __launch_bounds__(kThreads, Geo<DIM>::CTAS) k_pd(const __grid_co
                 if constexpr (NCB == 4) {
                     const float4 cv = *reinterpret_cast<const float4 *>(tp + coff);
                     cc[0] = cv.x; cc[1] = cv.y; cc[2] = cv.z; cc[3] = cv.w;
-                } else {
+                } else if constexpr (NCB == 2) {
                     const float2 cv = *reinterpret_cast<const float2 *>(tp + coff);
                     cc[0] = cv.x; cc[1] = cv.y;
+                } else {
+                    cc[0] = tp[coff];
                 }
 #pragma unroll
                 for (int c = 0; c < NCB; ++c) {
