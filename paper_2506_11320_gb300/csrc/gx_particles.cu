@@ -29,16 +29,17 @@
 // the 2^d x 2^d corner-pair weights w X_jx Y_jy (Z_jz) (9 pair classes in 2D,
 // 27 in 3D) and 16 columns (the nine entries of alpha, 1, v and
 // alpha (v - u_ref)).  The warp's lanes form particle groups; within a group
-// each lane owns a block of 9 pair classes x 4 columns (36 sums in registers,
+// each lane owns a block of 9 pair classes x NCB columns (sums in registers,
 // kept over all chunks of the cell) and walks the group's particles, so each
-// particle's factors are read from shared memory by few lanes (2D: 8 groups of
-// 4 lanes; 3D: 2 groups of 12).  At the end of the cell the groups' sums are
-// added, and the cell's record follows from the 16 sums per pair class: the
-// mass-matrix sums are the alpha columns, and the charge, momentum and current
-// weights of corner a are the sums of the 2^d pair classes whose product makes
-// up W_a (for linear weights (1-o) = X_0 + X_1 and o = X_1 + X_2 per axis).  A
-// lane holds 36 sums instead of the record's 109 (2D) or 299 (3D), so many
-// warps fit an SM, and the same kernel serves both dimensions.  The FP32
+// particle's factors are read from shared memory by few lanes (2D: 4 groups of
+// 8 lanes with 9 x 2 blocks; 3D: 2 groups of 12 with 9 x 4).  At the end of
+// the cell the groups' sums are added, and the cell's record follows from the
+// 16 sums per pair class: the mass-matrix sums are the alpha columns, and the
+// charge, momentum and current weights of corner a are the sums of the 2^d pair
+// classes whose product makes up W_a (for linear weights (1-o) = X_0 + X_1 and
+// o = X_1 + X_2 per axis).  A lane holds 18 (2D) or 36 (3D) sums instead of the
+// record's 109 or 299, so many warps fit an SM, and the same kernel serves both
+// dimensions.  The FP32
 // particle arithmetic stays on the CUDA cores: it is a scatter, not a dense
 // contraction.
 #include <cub/cub.cuh>
@@ -53,8 +54,9 @@ constexpr int kCols = 16;                         // alpha[9], 1, v[3], alpha (v
 constexpr unsigned kFull = 0xffffffffu;
 
 // NC corners; ROWS pair classes in groups of 9; factor table of TSTR floats
-// per particle (group g's 9 weights at 12 g, the 16 columns at COLOFF); LK
-// lanes per particle group (RG x 4 column quads), KG groups
+// per particle (group g's 9 weights at 12 g, the 16 columns at COLOFF); NCB
+// columns per lane block; LK lanes per particle group (row sets x 16 / NCB
+// column blocks), KG groups; CTAS resident CTAs per SM
 template <int DIM> struct Geo;
 template <> struct Geo<2> {
     static constexpr int NC = 4, ROWS = 9, TSTR = 28, COLOFF = 12, NCB = 2, LK = 8, KG = 4, CENTER = 4, CTAS = 3;
