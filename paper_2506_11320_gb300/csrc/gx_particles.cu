@@ -83,9 +83,22 @@ __host__ __device__ constexpr int warp_floats() {
 // in 3D one (the larger shared footprint cost more than the barrier saved)
 template <int DIM>
 __host__ __device__ constexpr int pd_stages() { return DIM == 2 ? 4 : 2; }
+// in 2D a warp's leavers wait in shared memory (kLeaverCap of them) until their
+// cell ends or the next chunk might not fit: per leaver its offsets, velocity,
+// weight, id and move code (leaver_stride floats).  In 3D each chunk writes its
+// own leavers after its deposit, which hides the reservation's latency (a
+// buffer there cost 12 % at 64 particles per cell).
+template <int DIM>
+__host__ __device__ constexpr int leaver_stride() { return DIM == 2 ? 8 : 12; }
+constexpr int kLeaverCap = 64;
+template <int DIM>
+__host__ __device__ constexpr bool leaver_buffer() { return DIM == 2; }
+template <int DIM>
+__host__ __device__ constexpr int leaver_floats() { return leaver_buffer<DIM>() ? kLeaverCap * leaver_stride<DIM>() : 0; }
 template <int DIM>
 constexpr size_t pd_smem_bytes() {
-    return ((size_t)kWarpsPerCta * warp_floats<DIM>() + pd_stages<DIM>() * (size_t)Rec<DIM>::SIZE * kRecTile) *
+    return ((size_t)kWarpsPerCta * (warp_floats<DIM>() + leaver_floats<DIM>()) +
+            pd_stages<DIM>() * (size_t)Rec<DIM>::SIZE * kRecTile) *
            sizeof(float);
 }
 static_assert(kWarpsPerCta == kRecTile, "one warp per cell of a record tile");
@@ -339,6 +352,63 @@ __global__ void __launch_bounds__(kThreads, Geo<DIM>::CTAS) k_pd(const __grid_co
     };
     if (cell < p.N) fetch(p.in + cell * cstride, wcur, 0);
 
+    // leavers wait in this warp's shared buffer (kLeaverCap entries of LVS floats:
+    // offsets, velocity, weight, id, move code) and are written out at the start
+    // of a chunk when more than 32 are pending, and at the end of their cell: one
+    // atomic per destination and round of 32 reserves a run at the top of the
+    // destination bin (its back segment), and each leaver takes its rank within
+    // the run
+    constexpr int LVS = leaver_stride<DIM>();
+    constexpr bool LB = leaver_buffer<DIM>();
+    float *lbuf = stage + (size_t)NST * TILE + (size_t)warp * leaver_floats<DIM>();
+    int lpend = 0;                                            // leavers in lbuf (warp-uniform)
+    auto flush_leavers = [&]() {
+        __syncwarp();
+        for (int b0 = 0; b0 < lpend; b0 += 32) {
+        const int k = min(32, lpend - b0);
+        const unsigned mk = k >= 32 ? kFull : ((1u << k) - 1u);
+        if (lane < k) {
+            const float *e = lbuf + (b0 + lane) * LVS;
+            const float4 e0 = *reinterpret_cast<const float4 *>(e);
+            const float4 e1 = *reinterpret_cast<const float4 *>(e + 4);
+            float lo[3], lv[3], lw, lid;
+            int code;
+            if (DIM == 2) {
+                lo[0] = e0.x; lo[1] = e0.y; lo[2] = 0.f;
+                lv[0] = e0.z; lv[1] = e0.w; lv[2] = e1.x;
+                lw = e1.y; lid = e1.z; code = __float_as_int(e1.w);
+            } else {
+                lo[0] = e0.x; lo[1] = e0.y; lo[2] = e0.z;
+                lv[0] = e0.w; lv[1] = e1.x; lv[2] = e1.y;
+                lw = e1.z; lid = e1.w; code = __float_as_int(e[8]);
+            }
+            int di = ci + code % 3 - 1, dj = cj + (code / 3) % 3 - 1, dk = ck + (DIM == 3 ? code / 9 - 1 : 0);
+            di = di < 0 ? di + p.n[0] : (di >= p.n[0] ? di - p.n[0] : di);
+            dj = dj < 0 ? dj + p.n[1] : (dj >= p.n[1] ? dj - p.n[1] : dj);
+            if (DIM == 3) dk = dk < 0 ? dk + p.n[2] : (dk >= p.n[2] ? dk - p.n[2] : dk);
+            const int64_t dest = (int64_t)(di + p.n[0] * (dj + p.n[1] * dk));
+            const unsigned peers = __match_any_sync(mk, code);
+            const int leader = __ffs(peers) - 1;
+            int lold = 0;
+            if (lane == leader) lold = atomicAdd(p.cnt_out + dest, __popc(peers) << 16);
+            const int back = bin_back(__shfl_sync(peers, lold, leader)) + __popc(peers & lt);
+            if (back < p.cap) {
+                float *dst = p.out + dest * cstride + (p.cap - 1 - back);
+#pragma unroll
+                for (int d = 0; d < DIM; ++d) __stcs(dst + (size_t)d * p.cap, lo[d]);
+#pragma unroll
+                for (int d = 0; d < 3; ++d) __stcs(dst + (size_t)(PF<DIM>::V + d) * p.cap, lv[d]);
+                __stcs(dst + (size_t)PF<DIM>::W * p.cap, lw);
+                if (p.nf > PF<DIM>::ID) __stcs(dst + (size_t)PF<DIM>::ID * p.cap, lid);
+            } else {
+                atomicExch(&p.flags->overflow, 1);
+            }
+        }
+        }
+        __syncwarp();
+        lpend = 0;
+    };
+
     int it = 0;
     for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
         // the next tile's cell of this warp: count and corners now, first chunk later
@@ -374,6 +444,7 @@ __global__ void __launch_bounds__(kThreads, Geo<DIM>::CTAS) k_pd(const __grid_co
         int fbase = 0;                                        // stayers written to this cell's new bin so far
 
         for (int c0 = 0; c0 < n; c0 += 32) {
+            if (PUSH && LB && lpend > kLeaverCap - 32) flush_leavers();   // room for this chunk's leavers
             const int i = c0 + lane;
             const bool valid = i < n;
             float o[3] = {0.5f, 0.5f, 0.5f}, v[3] = {pv[0], pv[1], pv[2]}, w = pw, idb = pid;
@@ -383,26 +454,12 @@ __global__ void __launch_bounds__(kThreads, Geo<DIM>::CTAS) k_pd(const __grid_co
             else if (has_next) fetch(bin_nx, wnext, 0);
             if (DIM == 2) o[2] = 0.f;
             bool dep = valid;
-            // a leaver's reservation (destination, its run's lanes and leader, the leader's atomic)
+            // 3D: a leaver's reservation (destination, its run's lanes and leader, the
+            // leader's atomic), used after the chunk's deposit
             bool leaver = false;
             unsigned peers = 0u;
             int leader = 0, lold = 0;
             int64_t dest = 0;
-            auto store_leaver = [&]() {
-                const int old = __shfl_sync(peers, lold, leader);
-                const int back = bin_back(old) + __popc(peers & lt);
-                if (back < p.cap) {
-                    float *dst = p.out + dest * cstride + (p.cap - 1 - back);
-#pragma unroll
-                    for (int d = 0; d < DIM; ++d) __stcs(dst + (size_t)d * p.cap, o[d]);
-#pragma unroll
-                    for (int d = 0; d < 3; ++d) __stcs(dst + (size_t)(PF<DIM>::V + d) * p.cap, v[d]);
-                    __stcs(dst + (size_t)PF<DIM>::W * p.cap, w);
-                    if (p.nf > PF<DIM>::ID) __stcs(dst + (size_t)PF<DIM>::ID * p.cap, idb);
-                } else {
-                    atomicExch(&p.flags->overflow, 1);
-                }
-            };
             if (PUSH) {
                 // ---- mover (Eq. 29-30, ECSIM update): e = beta E^{n+theta}, b = beta B^n / c
                 float e3[3], b3[3];
@@ -451,11 +508,9 @@ __global__ void __launch_bounds__(kThreads, Geo<DIM>::CTAS) k_pd(const __grid_co
                     for (int d = 0; d < 3; ++d) __stcs(dst + (size_t)(PF<DIM>::V + d) * p.cap, v[d]);
                     __stcs(dst + (size_t)PF<DIM>::W * p.cap, w);
                     if (p.nf > PF<DIM>::ID) __stcs(dst + (size_t)PF<DIM>::ID * p.cap, idb);
-                } else if (valid) {
-                    // leavers: one atomic per (warp, destination) reserves a run at the top of
-                    // the destination bin; each leaver takes its rank within the run.  In 3D
-                    // the atomic's result is used after the deposit below, which hides its
-                    // latency (in 2D the registers that keeps live cost more than it saves).
+                } else if (!LB && valid) {
+                    // ---- leavers: one atomic per (warp, destination) reserves a run at the
+                    // top of the destination bin; each leaver takes its rank within the run
                     leaver = true;
                     int di = ci + s[0], dj = cj + s[1], dk = ck + s[2];
                     di = di < 0 ? di + p.n[0] : (di >= p.n[0] ? di - p.n[0] : di);
@@ -465,7 +520,25 @@ __global__ void __launch_bounds__(kThreads, Geo<DIM>::CTAS) k_pd(const __grid_co
                     peers = __match_any_sync(ml, code);
                     leader = __ffs(peers) - 1;
                     if (lane == leader) lold = atomicAdd(p.cnt_out + dest, __popc(peers) << 16);
-                    if (DIM == 2) store_leaver();
+                }
+                if constexpr (LB) {
+                    // ---- leavers: into the warp's buffer, written out at the cell's end
+                    // (or at a chunk's start when the buffer might not hold its leavers)
+                    const int nl = __popc(ml);
+                    if (nl > 0) {                             // warp-uniform
+                        if (valid && !stay) {
+                            float *e = lbuf + (lpend + __popc(ml & lt)) * LVS;
+                            if (DIM == 2) {
+                                *reinterpret_cast<float4 *>(e) = make_float4(o[0], o[1], v[0], v[1]);
+                                *reinterpret_cast<float4 *>(e + 4) = make_float4(v[2], w, idb, __int_as_float(code));
+                            } else {
+                                *reinterpret_cast<float4 *>(e) = make_float4(o[0], o[1], o[2], v[0]);
+                                *reinterpret_cast<float4 *>(e + 4) = make_float4(v[1], v[2], w, idb);
+                                e[8] = __int_as_float(code);
+                            }
+                        }
+                        lpend += nl;
+                    }
                 }
                 fbase += __popc(ms);
                 dep = valid && stay;
@@ -547,14 +620,31 @@ __global__ void __launch_bounds__(kThreads, Geo<DIM>::CTAS) k_pd(const __grid_co
                         accumulate(pg + G::KG * si);
                     }
                 } else {
+                    // two particles per trip (the loop overhead and the table loads of
+                    // both in flight together)
+#pragma unroll 2
                     for (int pp = pg; pp < nv; pp += G::KG) accumulate(pp);
                 }
             }
             // ---- 3D leavers: the slot their run reserved
-            if (PUSH && DIM == 3 && leaver) store_leaver();
+            if (PUSH && !LB && leaver) {
+                const int back = bin_back(__shfl_sync(peers, lold, leader)) + __popc(peers & lt);
+                if (back < p.cap) {
+                    float *dst = p.out + dest * cstride + (p.cap - 1 - back);
+#pragma unroll
+                    for (int d = 0; d < DIM; ++d) __stcs(dst + (size_t)d * p.cap, o[d]);
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) __stcs(dst + (size_t)(PF<DIM>::V + d) * p.cap, v[d]);
+                    __stcs(dst + (size_t)PF<DIM>::W * p.cap, w);
+                    if (p.nf > PF<DIM>::ID) __stcs(dst + (size_t)PF<DIM>::ID * p.cap, idb);
+                } else {
+                    atomicExch(&p.flags->overflow, 1);
+                }
+            }
             __syncwarp();                                    // the table is rewritten by the next chunk
         }
         if (n == 0 && has_next) fetch(bin_nx, wnext, 0);
+        if (PUSH && LB && lpend > 0) flush_leavers();
         // the stayers' count (the bottom segment) of this cell's new bin
         if (PUSH && lane == 0 && fbase > 0) atomicAdd(p.cnt_out + cell, fbase);
         float *st = stage + (size_t)(it & (NST - 1)) * TILE;
