@@ -353,9 +353,9 @@ __global__ void __launch_bounds__(kThreads, Geo<DIM>::CTAS) k_pd(const __grid_co
     if (cell < p.N) fetch(p.in + cell * cstride, wcur, 0);
 
     // leavers wait in this warp's shared buffer (kLeaverCap entries of LVS floats:
-    // offsets, velocity, weight, id, move code) and are written out at the start
-    // of a chunk when more than 32 are pending, and at the end of their cell: one
-    // atomic per destination and round of 32 reserves a run at the top of the
+    // offsets, velocity, weight, id, destination cell) and are written out at the
+    // start of a chunk when more than 32 are pending, and at the end: one atomic
+    // per destination and round of 32 reserves a run at the top of the
     // destination bin (its back segment), and each leaver takes its rank within
     // the run
     constexpr int LVS = leaver_stride<DIM>();
@@ -372,22 +372,18 @@ __global__ void __launch_bounds__(kThreads, Geo<DIM>::CTAS) k_pd(const __grid_co
             const float4 e0 = *reinterpret_cast<const float4 *>(e);
             const float4 e1 = *reinterpret_cast<const float4 *>(e + 4);
             float lo[3], lv[3], lw, lid;
-            int code;
+            int dcell;
             if (DIM == 2) {
                 lo[0] = e0.x; lo[1] = e0.y; lo[2] = 0.f;
                 lv[0] = e0.z; lv[1] = e0.w; lv[2] = e1.x;
-                lw = e1.y; lid = e1.z; code = __float_as_int(e1.w);
+                lw = e1.y; lid = e1.z; dcell = __float_as_int(e1.w);
             } else {
                 lo[0] = e0.x; lo[1] = e0.y; lo[2] = e0.z;
                 lv[0] = e0.w; lv[1] = e1.x; lv[2] = e1.y;
-                lw = e1.z; lid = e1.w; code = __float_as_int(e[8]);
+                lw = e1.z; lid = e1.w; dcell = __float_as_int(e[8]);
             }
-            int di = ci + code % 3 - 1, dj = cj + (code / 3) % 3 - 1, dk = ck + (DIM == 3 ? code / 9 - 1 : 0);
-            di = di < 0 ? di + p.n[0] : (di >= p.n[0] ? di - p.n[0] : di);
-            dj = dj < 0 ? dj + p.n[1] : (dj >= p.n[1] ? dj - p.n[1] : dj);
-            if (DIM == 3) dk = dk < 0 ? dk + p.n[2] : (dk >= p.n[2] ? dk - p.n[2] : dk);
-            const int64_t dest = (int64_t)(di + p.n[0] * (dj + p.n[1] * dk));
-            const unsigned peers = __match_any_sync(mk, code);
+            const int64_t dest = dcell;
+            const unsigned peers = __match_any_sync(mk, dcell);
             const int leader = __ffs(peers) - 1;
             int lold = 0;
             if (lane == leader) lold = atomicAdd(p.cnt_out + dest, __popc(peers) << 16);
@@ -522,19 +518,24 @@ __global__ void __launch_bounds__(kThreads, Geo<DIM>::CTAS) k_pd(const __grid_co
                     if (lane == leader) lold = atomicAdd(p.cnt_out + dest, __popc(peers) << 16);
                 }
                 if constexpr (LB) {
-                    // ---- leavers: into the warp's buffer, written out at the cell's end
-                    // (or at a chunk's start when the buffer might not hold its leavers)
+                    // ---- leavers: into the warp's buffer with their destination cell, written
+                    // out at a chunk's start when the buffer might not hold its leavers
                     const int nl = __popc(ml);
                     if (nl > 0) {                             // warp-uniform
                         if (valid && !stay) {
+                            int di = ci + s[0], dj = cj + s[1], dk = ck + s[2];
+                            di = di < 0 ? di + p.n[0] : (di >= p.n[0] ? di - p.n[0] : di);
+                            dj = dj < 0 ? dj + p.n[1] : (dj >= p.n[1] ? dj - p.n[1] : dj);
+                            if (DIM == 3) dk = dk < 0 ? dk + p.n[2] : (dk >= p.n[2] ? dk - p.n[2] : dk);
+                            const int dcell = di + p.n[0] * (dj + p.n[1] * dk);
                             float *e = lbuf + (lpend + __popc(ml & lt)) * LVS;
                             if (DIM == 2) {
                                 *reinterpret_cast<float4 *>(e) = make_float4(o[0], o[1], v[0], v[1]);
-                                *reinterpret_cast<float4 *>(e + 4) = make_float4(v[2], w, idb, __int_as_float(code));
+                                *reinterpret_cast<float4 *>(e + 4) = make_float4(v[2], w, idb, __int_as_float(dcell));
                             } else {
                                 *reinterpret_cast<float4 *>(e) = make_float4(o[0], o[1], o[2], v[0]);
                                 *reinterpret_cast<float4 *>(e + 4) = make_float4(v[1], v[2], w, idb);
-                                e[8] = __int_as_float(code);
+                                e[8] = __int_as_float(dcell);
                             }
                         }
                         lpend += nl;
@@ -644,7 +645,6 @@ __global__ void __launch_bounds__(kThreads, Geo<DIM>::CTAS) k_pd(const __grid_co
             __syncwarp();                                    // the table is rewritten by the next chunk
         }
         if (n == 0 && has_next) fetch(bin_nx, wnext, 0);
-        if (PUSH && LB && lpend > 0) flush_leavers();
         // the stayers' count (the bottom segment) of this cell's new bin
         if (PUSH && lane == 0 && fbase > 0) atomicAdd(p.cnt_out + cell, fbase);
         float *st = stage + (size_t)(it & (NST - 1)) * TILE;
@@ -701,6 +701,7 @@ __global__ void __launch_bounds__(kThreads, Geo<DIM>::CTAS) k_pd(const __grid_co
         wcur = wnext;
         ccur = cnext;
     }
+    if (PUSH && LB && lpend > 0) flush_leavers();
 }
 
 // ------------------------------------------------------------ arrivals deposit
