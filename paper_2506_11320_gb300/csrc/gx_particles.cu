@@ -83,11 +83,11 @@ __host__ __device__ constexpr int warp_floats() {
 // in 3D one (the larger shared footprint cost more than the barrier saved)
 template <int DIM>
 __host__ __device__ constexpr int pd_stages() { return DIM == 2 ? 4 : 2; }
-// in 2D a warp's leavers wait in shared memory (kLeaverCap of them) until their
-// cell ends or the next chunk might not fit: per leaver its offsets, velocity,
-// weight, id and move code (leaver_stride floats).  In 3D each chunk writes its
-// own leavers after its deposit, which hides the reservation's latency (a
-// buffer there cost 12 % at 64 particles per cell).
+// in 2D a warp's leavers wait in shared memory (kLeaverCap of them) until the
+// next chunk's might not fit, and to the end of the kernel: per leaver its
+// offsets, velocity, weight, id and destination cell (leaver_stride floats).
+// In 3D each chunk writes its own leavers after its deposit, which hides the
+// reservation's latency (a buffer there cost 12 % at 64 particles per cell).
 template <int DIM>
 __host__ __device__ constexpr int leaver_stride() { return DIM == 2 ? 8 : 12; }
 constexpr int kLeaverCap = 64;
