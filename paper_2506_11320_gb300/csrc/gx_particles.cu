@@ -78,11 +78,11 @@ template <int DIM>
 __host__ __device__ constexpr int warp_floats() {
     return 16 * Geo<DIM>::NC + table_floats<DIM>();
 }
-// record-tile stages, double-buffered: in 2D two tiles are staged between CTA
-// barriers (one barrier per two tiles, so a warp's cells of two tiles even out);
-// in 3D one (the larger shared footprint cost more than the barrier saved)
+// record-tile stages, double-buffered: in 2D four tiles are staged between CTA
+// barriers (one barrier per four tiles, so a warp's cells of four tiles even
+// out); in 3D one (the larger shared footprint cost more than the barrier saved)
 template <int DIM>
-__host__ __device__ constexpr int pd_stages() { return DIM == 2 ? 4 : 2; }
+__host__ __device__ constexpr int pd_stages() { return DIM == 2 ? 8 : 2; }
 // in 2D a warp's leavers wait in shared memory (kLeaverCap of them) until the
 // next chunk's might not fit, and to the end of the kernel: per leaver its
 // offsets, velocity, weight, id and destination cell (leaver_stride floats).
