@@ -544,47 +544,54 @@ __global__ void __launch_bounds__(kThreads, Geo<DIM>::CTAS) k_pd(const __grid_co
                 fbase += __popc(ms);
                 dep = valid && stay;
             }
-            // ---- deposit factors of this lane's particle (zero rows if it does not deposit):
-            // b = beta B^{n+1} / c and u_ref at the particle
+            // ---- deposit factors of this lane's particle: in 2D written (if it deposits) as
+            // row `its rank among the depositing lanes`, so that the rows [0, nrows) are
+            // dense; in 3D as row `lane`, zero weights if it does not deposit (compacting
+            // spilled registers there): b = beta B^{n+1} / c and u_ref at the particle
+            constexpr bool CR = DIM == 2;
+            const unsigned md = CR ? __ballot_sync(kFull, dep) : 0u;
+            const int nrows = CR ? __popc(md) : min(32, n - c0);
             {
                 float b3[3], U3[3], al[9];
                 interp<DIM>(cor + 2 * NC, o, b3);
                 interp<DIM>(cor + 3 * NC, o, U3);
                 alpha_tensor(b3[0], b3[1], b3[2], al);
                 const float d0 = v[0] - U3[0], d1 = v[1] - U3[1], d2 = v[2] - U3[2];
-                const float wd = dep ? w : 0.f;
+                const float wd = CR || dep ? w : 0.f;
                 float X[3][3];
 #pragma unroll
                 for (int d = 0; d < 3; ++d) {
                     const float a0 = 1.f - o[d];
                     X[d][0] = a0 * a0; X[d][1] = a0 * o[d]; X[d][2] = o[d] * o[d];
                 }
-                float *tp = T + lane * G::TSTR;
+                float *tp = T + (CR ? __popc(md & lt) : lane) * G::TSTR;
                 float *col = tp + G::COLOFF;
-                *reinterpret_cast<float4 *>(col) = make_float4(al[0], al[1], al[2], al[3]);
-                *reinterpret_cast<float4 *>(col + 4) = make_float4(al[4], al[5], al[6], al[7]);
-                *reinterpret_cast<float4 *>(col + 8) = make_float4(al[8], 1.f, v[0], v[1]);
-                *reinterpret_cast<float4 *>(col + 12) =
-                    make_float4(v[2], fmaf(al[0], d0, fmaf(al[1], d1, al[2] * d2)),
-                                fmaf(al[3], d0, fmaf(al[4], d1, al[5] * d2)), fmaf(al[6], d0, fmaf(al[7], d1, al[8] * d2)));
+                if (!CR || dep) {
+                    *reinterpret_cast<float4 *>(col) = make_float4(al[0], al[1], al[2], al[3]);
+                    *reinterpret_cast<float4 *>(col + 4) = make_float4(al[4], al[5], al[6], al[7]);
+                    *reinterpret_cast<float4 *>(col + 8) = make_float4(al[8], 1.f, v[0], v[1]);
+                    *reinterpret_cast<float4 *>(col + 12) =
+                        make_float4(v[2], fmaf(al[0], d0, fmaf(al[1], d1, al[2] * d2)),
+                                    fmaf(al[3], d0, fmaf(al[4], d1, al[5] * d2)), fmaf(al[6], d0, fmaf(al[7], d1, al[8] * d2)));
 #pragma unroll
-                for (int jz = 0; jz < (DIM == 3 ? 3 : 1); ++jz) {
-                    float rw[9];
+                    for (int jz = 0; jz < (DIM == 3 ? 3 : 1); ++jz) {
+                        float rw[9];
 #pragma unroll
-                    for (int jy = 0; jy < 3; ++jy) {
-                        const float wyz = DIM == 3 ? wd * X[1][jy] * X[2][jz] : wd * X[1][jy];
+                        for (int jy = 0; jy < 3; ++jy) {
+                            const float wyz = DIM == 3 ? wd * X[1][jy] * X[2][jz] : wd * X[1][jy];
 #pragma unroll
-                        for (int jx = 0; jx < 3; ++jx) rw[jx + 3 * jy] = wyz * X[0][jx];
+                            for (int jx = 0; jx < 3; ++jx) rw[jx + 3 * jy] = wyz * X[0][jx];
+                        }
+                        float *rp = tp + 12 * jz;
+                        *reinterpret_cast<float4 *>(rp) = make_float4(rw[0], rw[1], rw[2], rw[3]);
+                        *reinterpret_cast<float4 *>(rp + 4) = make_float4(rw[4], rw[5], rw[6], rw[7]);
+                        rp[8] = rw[8];
                     }
-                    float *rp = tp + 12 * jz;
-                    *reinterpret_cast<float4 *>(rp) = make_float4(rw[0], rw[1], rw[2], rw[3]);
-                    *reinterpret_cast<float4 *>(rp + 4) = make_float4(rw[4], rw[5], rw[6], rw[7]);
-                    rp[8] = rw[8];
                 }
             }
             __syncwarp();
             // ---- output-stationary accumulation: this lane adds, over its group's
-            // particles, its 9 pair classes x 4 columns
+            // particles, its 9 pair classes x NCB columns
             auto accumulate = [&](int pp) {
                 const float *tp = T + pp * G::TSTR;
                 const float4 r03 = *reinterpret_cast<const float4 *>(tp + roff);
@@ -611,20 +618,19 @@ __global__ void __launch_bounds__(kThreads, Geo<DIM>::CTAS) k_pd(const __grid_co
                 }
             };
             if (role) {
-                const int nv = min(32, n - c0);
                 if constexpr (DIM == 3) {
-                    // a fixed trip count (rows of absent particles are 0; the warp-uniform
-                    // break skips the iterations past the chunk's end): faster in 3D only
+                    // a fixed trip count (the warp-uniform break skips the iterations past
+                    // the last row): faster in 3D only
 #pragma unroll
                     for (int si = 0; si < 32 / G::KG; ++si) {
-                        if (G::KG * si >= nv) break;
-                        accumulate(pg + G::KG * si);
+                        if (G::KG * si >= nrows) break;
+                        accumulate(pg + G::KG * si);   // rows past the chunk's end are zero
                     }
                 } else {
                     // two particles per trip (the loop overhead and the table loads of
                     // both in flight together)
 #pragma unroll 2
-                    for (int pp = pg; pp < nv; pp += G::KG) accumulate(pp);
+                    for (int pp = pg; pp < nrows; pp += G::KG) accumulate(pp);
                 }
             }
             // ---- 3D leavers: the slot their run reserved
