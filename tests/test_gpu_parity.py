@@ -64,6 +64,10 @@ WORKLOADS = {
     "line_48x1": lambda: workloads.uniform_drift(n=(48, 1, 1), ppc=40, comoving=0, u=(0.2, 0.05, 0.0)),
     # Harris sheet: density-weighted particles, strong field gradients
     "harris_64x32": lambda: workloads.harris(nx=64, ny=32, ppc=24, steps=1),
+    # fast beam: 0.63 cells per step along x and 0.35 along y, so most particles
+    # change cell and a warp holds more than 32 leavers at once
+    "fast_beam_32x16": lambda: workloads.uniform_drift(n=(32, 16, 1), ppc=100, u=(0.45, 0.25, 0.0), vth_e=0.03,
+                                                       dt=0.14, ns_j=1),
 }
 
 
@@ -104,7 +108,7 @@ def _oracle_index(wl):
     return offs
 
 
-@pytest.mark.parametrize("name", ["uniform_32x32", "ragged_36x20", "line_48x1", "harris_64x32"])
+@pytest.mark.parametrize("name", ["uniform_32x32", "ragged_36x20", "line_48x1", "harris_64x32", "fast_beam_32x16"])
 def test_one_step_matches_oracle(gx, name):
     wl = WORKLOADS[name]()
     ctx = gx.from_workload(wl, track_ids=1, gmres_tol=1e-12)
