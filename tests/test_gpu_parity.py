@@ -64,10 +64,6 @@ WORKLOADS = {
     "line_48x1": lambda: workloads.uniform_drift(n=(48, 1, 1), ppc=40, comoving=0, u=(0.2, 0.05, 0.0)),
     # Harris sheet: density-weighted particles, strong field gradients
     "harris_64x32": lambda: workloads.harris(nx=64, ny=32, ppc=24, steps=1),
-    # fast beam: 0.63 cells per step along x and 0.35 along y, so most particles
-    # change cell and a warp holds more than 32 leavers at once
-    "fast_beam_32x16": lambda: workloads.uniform_drift(n=(32, 16, 1), ppc=100, u=(0.45, 0.25, 0.0), vth_e=0.03,
-                                                       dt=0.14, ns_j=1),
 }
 
 
@@ -108,7 +104,7 @@ def _oracle_index(wl):
     return offs
 
 
-@pytest.mark.parametrize("name", ["uniform_32x32", "ragged_36x20", "line_48x1", "harris_64x32", "fast_beam_32x16"])
+@pytest.mark.parametrize("name", ["uniform_32x32", "ragged_36x20", "line_48x1", "harris_64x32"])
 def test_one_step_matches_oracle(gx, name):
     wl = WORKLOADS[name]()
     ctx = gx.from_workload(wl, track_ids=1, gmres_tol=1e-12)
@@ -153,6 +149,83 @@ def test_one_step_matches_oracle(gx, name):
     orho, oJ, oM, ou = oracle_moments(wl1)
     errs = {"rho": rel(rho1, orho), "J": rel(J1, oJ), "M": rel(M1, oM), "u": rel(u1, ou)}
     assert all(v <= TOL_MOM for v in errs.values()), errs
+    ctx.close()
+
+
+def _fast_beam():
+    # 0.63 cells per step along x and 0.35 along y: 76 % of the particles change
+    # cell, so a warp holds more than 32 leavers at once
+    return workloads.uniform_drift(n=(32, 16, 1), ppc=100, u=(0.45, 0.25, 0.0), vth_e=0.03, dt=0.14, ns_j=1)
+
+
+def test_fast_beam_push_matches_oracle(gx):
+    """One push of a fast drifting beam, most particles leaving their cell.
+    Every particle (matched by id) against the oracle's mover; the deposit the
+    push made against the oracle's deposit of the same moved particles (1e-5,
+    the re-binning and the leavers' write-out included); the whole step's
+    moments against the oracle's step.  For the last, J is judged against the
+    beam's current scale |rho| |u|: the comoving current of a uniform beam is
+    the cells' thermal residue (7 % of |rho| |u| here), and the FP32 rounding of
+    the drift velocity, the same for every particle, adds coherently into it
+    (measured 2.2e-5 of |J| with the comoving current, 4e-7 without it, and
+    1.0e-6 for the deposit of the moved particles)."""
+    wl = _fast_beam()
+    ctx = gx.from_workload(wl, track_ids=1, gmres_tol=1e-12)
+    st = ctx.field_solve()
+    assert st.converged == 1
+    ctx.push_and_deposit()
+    E1, B1 = ctx.get_fields()
+    rho1, J1, M1, u1 = ctx.get_moments()
+
+    cfg = oracle_cfg(wl)
+    pl = O.Plasma.from_species(wl.species)
+    E, B = wl.E0.copy(), wl.B0.copy()
+    r = O.step(cfg, pl, E, B, want=("Eth",))
+    assert r["rc"] == 0
+    assert rel(E1, E) <= TOL_FIELD and rel(B1, B) <= TOL_FIELD
+
+    offs = _oracle_index(wl)
+    L = [wl.n[d] * wl.dx[d] for d in range(3)]
+    moved = _fast_beam()
+    left = 0
+    for s in range(len(wl.species)):
+        p = ctx.get_particles(s, ids=True)
+        assert np.array_equal(np.sort(p["id"]), np.arange(len(wl.species[s]["x"])))
+        idx = offs[s] + p["id"]
+        vmax = max(np.abs(pl.vx).max(), np.abs(pl.vy).max(), np.abs(pl.vz).max())
+        for key, ref in (("vx", pl.vx), ("vy", pl.vy), ("vz", pl.vz)):
+            assert np.abs(p[key] - ref[idx]).max() <= 1e-6 * vmax, key
+        for key, ref, d in (("x", pl.x, 0), ("y", pl.y, 1)):
+            dd = (p[key] - ref[idx] + 0.5 * L[d]) % L[d] - 0.5 * L[d]
+            assert np.abs(dd).max() <= 1e-5 * wl.dx[d], key
+        x0 = np.floor(np.asarray(wl.species[s]["x"]) / wl.dx[0])[p["id"]]
+        y0 = np.floor(np.asarray(wl.species[s]["y"]) / wl.dx[1])[p["id"]]
+        left += int(np.count_nonzero((np.floor(p["x"] / wl.dx[0]) != x0) | (np.floor(p["y"] / wl.dx[1]) != y0)))
+        o = np.argsort(p["id"])
+        sp = moved.species[s]
+        for key in ("x", "y", "vx", "vy", "vz"):
+            sp[key] = np.asarray(p[key])[o]
+        sp["z"] = np.zeros(len(o))
+    assert left > 0.7 * sum(len(sp["x"]) for sp in wl.species)
+
+    # the deposit of the moved particles, re-binning included
+    moved.B0 = B1
+    drho, dJ, dM, du = oracle_moments(moved)
+    errs = {"rho": rel(rho1, drho), "J": rel(J1, dJ), "M": rel(M1, dM), "u": rel(u1, du)}
+    assert all(v <= TOL_MOM for v in errs.values()), errs
+
+    # the whole step's moments against the oracle's step
+    wl1 = _fast_beam()
+    for s, sp in enumerate(wl1.species):
+        sel = slice(offs[s], offs[s] + len(sp["x"]))
+        sp["x"], sp["y"], sp["z"] = pl.x[sel], pl.y[sel], pl.z[sel]
+        sp["vx"], sp["vy"], sp["vz"] = pl.vx[sel], pl.vy[sel], pl.vz[sel]
+    wl1.B0 = B
+    orho, oJ, oM, ou = oracle_moments(wl1)
+    errs = {"rho": rel(rho1, orho), "M": rel(M1, oM), "u": rel(u1, ou)}
+    assert all(v <= TOL_MOM for v in errs.values()), errs
+    ubeam = float(np.hypot(0.45, 0.25))
+    assert np.linalg.norm(J1 - oJ) <= TOL_MOM * np.linalg.norm(orho) * ubeam
     ctx.close()
 
 
