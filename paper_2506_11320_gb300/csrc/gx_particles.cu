@@ -365,41 +365,41 @@ __global__ void __launch_bounds__(kThreads, Geo<DIM>::CTAS) k_pd(const __grid_co
     auto flush_leavers = [&]() {
         __syncwarp();
         for (int b0 = 0; b0 < lpend; b0 += 32) {
-        const int k = min(32, lpend - b0);
-        const unsigned mk = k >= 32 ? kFull : ((1u << k) - 1u);
-        if (lane < k) {
-            const float *e = lbuf + (b0 + lane) * LVS;
-            const float4 e0 = *reinterpret_cast<const float4 *>(e);
-            const float4 e1 = *reinterpret_cast<const float4 *>(e + 4);
-            float lo[3], lv[3], lw, lid;
-            int dcell;
-            if (DIM == 2) {
-                lo[0] = e0.x; lo[1] = e0.y; lo[2] = 0.f;
-                lv[0] = e0.z; lv[1] = e0.w; lv[2] = e1.x;
-                lw = e1.y; lid = e1.z; dcell = __float_as_int(e1.w);
-            } else {
-                lo[0] = e0.x; lo[1] = e0.y; lo[2] = e0.z;
-                lv[0] = e0.w; lv[1] = e1.x; lv[2] = e1.y;
-                lw = e1.z; lid = e1.w; dcell = __float_as_int(e[8]);
-            }
-            const int64_t dest = dcell;
-            const unsigned peers = __match_any_sync(mk, dcell);
-            const int leader = __ffs(peers) - 1;
-            int lold = 0;
-            if (lane == leader) lold = atomicAdd(p.cnt_out + dest, __popc(peers) << 16);
-            const int back = bin_back(__shfl_sync(peers, lold, leader)) + __popc(peers & lt);
-            if (back < p.cap) {
-                float *dst = p.out + dest * cstride + (p.cap - 1 - back);
+            const int k = min(32, lpend - b0);
+            const unsigned mk = k >= 32 ? kFull : ((1u << k) - 1u);
+            if (lane < k) {
+                const float *e = lbuf + (b0 + lane) * LVS;
+                const float4 e0 = *reinterpret_cast<const float4 *>(e);
+                const float4 e1 = *reinterpret_cast<const float4 *>(e + 4);
+                float lo[3], lv[3], lw, lid;
+                int dcell;
+                if (DIM == 2) {
+                    lo[0] = e0.x; lo[1] = e0.y; lo[2] = 0.f;
+                    lv[0] = e0.z; lv[1] = e0.w; lv[2] = e1.x;
+                    lw = e1.y; lid = e1.z; dcell = __float_as_int(e1.w);
+                } else {
+                    lo[0] = e0.x; lo[1] = e0.y; lo[2] = e0.z;
+                    lv[0] = e0.w; lv[1] = e1.x; lv[2] = e1.y;
+                    lw = e1.z; lid = e1.w; dcell = __float_as_int(e[8]);
+                }
+                const int64_t dest = dcell;
+                const unsigned peers = __match_any_sync(mk, dcell);
+                const int leader = __ffs(peers) - 1;
+                int lold = 0;
+                if (lane == leader) lold = atomicAdd(p.cnt_out + dest, __popc(peers) << 16);
+                const int back = bin_back(__shfl_sync(peers, lold, leader)) + __popc(peers & lt);
+                if (back < p.cap) {
+                    float *dst = p.out + dest * cstride + (p.cap - 1 - back);
 #pragma unroll
-                for (int d = 0; d < DIM; ++d) __stcs(dst + (size_t)d * p.cap, lo[d]);
+                    for (int d = 0; d < DIM; ++d) __stcs(dst + (size_t)d * p.cap, lo[d]);
 #pragma unroll
-                for (int d = 0; d < 3; ++d) __stcs(dst + (size_t)(PF<DIM>::V + d) * p.cap, lv[d]);
-                __stcs(dst + (size_t)PF<DIM>::W * p.cap, lw);
-                if (p.nf > PF<DIM>::ID) __stcs(dst + (size_t)PF<DIM>::ID * p.cap, lid);
-            } else {
-                atomicExch(&p.flags->overflow, 1);
+                    for (int d = 0; d < 3; ++d) __stcs(dst + (size_t)(PF<DIM>::V + d) * p.cap, lv[d]);
+                    __stcs(dst + (size_t)PF<DIM>::W * p.cap, lw);
+                    if (p.nf > PF<DIM>::ID) __stcs(dst + (size_t)PF<DIM>::ID * p.cap, lid);
+                } else {
+                    atomicExch(&p.flags->overflow, 1);
+                }
             }
-        }
         }
         __syncwarp();
         lpend = 0;
