@@ -50,7 +50,7 @@ enum {
     GX_ENOCONV = 4,    /* GMRES stopped at gmres_maxit; the best iterate is kept */
     GX_ECFL = 5,       /* a particle moved more than one cell in one step */
     GX_ETIMEOUT = 6,   /* a bounded device-side wait gave up */
-    GX_ENOTIMPL = 7,   /* feature not available in this build */
+    GX_ENOTIMPL = 7,   /* feature not available for this configuration (e.g. 3D with divb_clean) */
     GX_EOVERFLOW = 8,  /* a cell's particle bin overflowed (particles were lost) */
     GX_ESTATE = 9      /* call out of order (e.g. push before a field solve) */
 };

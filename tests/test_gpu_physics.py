@@ -1,5 +1,5 @@
 """Whole-step physics of the CUDA path (Sec. 1.1, 2.1), with the FP64 oracle
-and its operators as the judge:
+and its operators as the reference:
 
 * Gauss consistency: with the E diffusion off, div_C(E^{n+1} - E^n) =
   -4 pi dt div_C(Jbar) (div_C curl_N = 0 on this mesh), both for the current
