@@ -175,25 +175,37 @@ def load_traffic(summary_name, source):
 
 
 class Clocks:
-    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region:
+    the sampler (every 20 ms, each line time-stamped) is started and seen running
+    before the region begins; the summary keeps the samples taken inside it (or,
+    when the region is shorter than the sampling interval, the ones nearest to
+    it, and says so)."""
+
+    QUERY = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, dev):
         self.dev, self.p, self.out = dev, None, os.path.join("/tmp", f"gx_clocks_{os.getpid()}.csv")
+        self.t0 = self.t1 = None
 
     def __enter__(self):
-        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
             self.f = open(self.out, "w")
-            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
-                                       "-lms", "200", "-i", str(self.dev)], stdout=self.f, stderr=subprocess.DEVNULL)
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                                       "-lms", "20", "-i", str(self.dev)], stdout=self.f, stderr=subprocess.DEVNULL)
+            deadline = time.time() + 5.0
+            while time.time() < deadline and os.path.getsize(self.out) == 0:
+                time.sleep(0.02)
         except Exception:
             self.p = None
+        self.t0 = time.time()
         return self
 
     def __exit__(self, *a):
+        self.t1 = time.time()
         if self.p:
+            time.sleep(0.05)                  # one sample past the region's end
             self.p.terminate()
             try:
                 self.p.wait(timeout=5)
@@ -204,24 +216,50 @@ class Clocks:
     def summary(self):
         if not self.p or not os.path.exists(self.out):
             return None
-        sm, mx, reasons = [], [], set()
-        for line in open(self.out):
-            parts = [x.strip() for x in line.split(",")]
-            if len(parts) < 9:
-                continue
-            try:
-                sm.append(float(parts[1]))
-                mx.append(float(parts[2]))
-            except ValueError:
-                continue
-            for name, v in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"),
-                               parts[5:9]):
-                if v.lower() == "active":
-                    reasons.add(name)
-        if not sm:
-            return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+        return summarize_clock_lines(open(self.out).read().splitlines(), self.t0, self.t1)
+
+
+def summarize_clock_lines(lines, t0, t1):
+    """Median SM clock, maximum clock and the throttle reasons seen, from
+    nvidia-smi CSV lines (timestamp, index, clocks.sm, clocks.max.sm, power,
+    active mask, hw_slowdown, hw_thermal_slowdown, sw_thermal_slowdown,
+    sw_power_cap), over the samples time-stamped within [t0, t1]; if there are
+    none, over the sample nearest to either end ("window": "nearest")."""
+    import datetime
+    rows = []
+    for line in lines:
+        parts = [x.strip() for x in line.split(",")]
+        if len(parts) < 10:
+            continue
+        try:
+            sm, mx = float(parts[2]), float(parts[3])
+        except ValueError:
+            continue
+        try:
+            ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+        except ValueError:
+            ts = None
+        rows.append((ts, sm, mx, parts[6:10]))
+    if not rows:
+        return None
+    timed = [r for r in rows if r[0] is not None]
+    inside = [r for r in timed if t0 is not None and t1 is not None and t0 <= r[0] <= t1]
+    window = "during"
+    if not inside:
+        ref = [t for t in (t0, t1) if t is not None]
+        if timed and ref:
+            window = "nearest"
+            inside = [min(timed, key=lambda r: min(abs(r[0] - t) for t in ref))]
+        else:
+            window = "untimed"
+            inside = rows
+    reasons = set()
+    for r in inside:
+        for name, v in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"), r[3]):
+            if v.lower() == "active":
+                reasons.add(name)
+    return {"sm_mhz": statistics.median([r[1] for r in inside]), "sm_max_mhz": max(r[2] for r in inside),
+            "reasons": sorted(reasons), "samples": len(inside), "window": window}
 
 
 def oracle_push_deposit_rate(wl, budget_s=15.0, cells=(64, 32)):
