@@ -21,9 +21,17 @@ constexpr int kB = 256;
 constexpr int kNodeCtas = 4;
 
 
-inline int blocks_for(int64_t n) {
-    int64_t b = (n + kB - 1) / kB;
-    return (int)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 32));
+// threads and CTAs of the one-thread-per-node kernels: 256-thread CTAs once the
+// grid gives every SM two of them; on smaller grids (the narrow shock grids)
+// smaller CTAs, down to one warp, so that the nodes still spread over all SMs
+inline int node_threads(int64_t n) {
+    int t = kB;
+    while (t > 32 && (n + t - 1) / t < 2 * 152) t >>= 1;
+    return t;
+}
+inline int node_blocks(int64_t n) {
+    const int t = node_threads(n);
+    return (int)std::max<int64_t>(1, std::min<int64_t>((n + t - 1) / t, (int64_t)152 * 32 * (kB / t)));
 }
 
 #define GRID_LOOP(i, n) for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (n); i += (int64_t)gridDim.x * blockDim.x)
@@ -737,7 +745,7 @@ OpArgs gx_opargs(const gx_ctx *c) { return opargs(c); }
 
 int gx_node_fields(gx_ctx *c, const double *Eth, const double *Bcur, float4 *outE, float4 *outB, cudaStream_t st) {
     if (c->dim == 3) return gx3_node_fields(c, Eth, Bcur, outE, outB, st);
-    k_node_fields<<<blocks_for(c->N), kB, 0, st>>>(geom(c), Eth, Bcur, outE, outB);
+    k_node_fields<<<node_blocks(c->N), node_threads(c->N), 0, st>>>(geom(c), Eth, Bcur, outE, outB);
     GX_LAUNCHED(c);
     return GX_OK;
 }
@@ -749,17 +757,17 @@ int gx_assemble_moments(gx_ctx *c, cudaStream_t st) {
     const G2 g = geom(c);
     const SpecK sk = speck(c);
     const Recs R{c->rec, c->N};
-    k_assemble_bulk<<<blocks_for(c->N), kB, 0, st>>>(g, sk, R, 1.0 / c->dV, c->rho, c->rho_m, c->P, c->u);
+    k_assemble_bulk<<<node_blocks(c->N), node_threads(c->N), 0, st>>>(g, sk, R, 1.0 / c->dV, c->rho, c->rho_m, c->P, c->u);
     GX_LAUNCHED(c);
     int rc = filter_passes(c, c->u, c->cfg.nsmooth_u, true, st);
     if (rc) return rc;
-    k_assemble_main<<<blocks_for(c->N), kB, 0, st>>>(g, sk, R, 1.0 / c->dV, c->cfg.comoving, c->u, c->uref64, c->J,
+    k_assemble_main<<<node_blocks(c->N), node_threads(c->N), 0, st>>>(g, sk, R, 1.0 / c->dV, c->cfg.comoving, c->u, c->uref64, c->J,
                                                        c->M, c->M32);
     GX_LAUNCHED(c);
     rc = filter_passes(c, c->J, c->cfg.ns_j, false, st);
     if (rc) return rc;
     // reference velocity of the next deposit: this u (comoving) or 0
-    k_copy_uref<<<blocks_for(c->N), kB, 0, st>>>(c->N, c->u, c->nUref, c->uref64, c->cfg.comoving ? 0 : 1);
+    k_copy_uref<<<node_blocks(c->N), node_threads(c->N), 0, st>>>(c->N, c->u, c->nUref, c->uref64, c->cfg.comoving ? 0 : 1);
     GX_LAUNCHED(c);
     c->have_u = 1;
     return GX_OK;
@@ -770,7 +778,7 @@ int gx_build_rhs(gx_ctx *c, cudaStream_t st) {
     const G2 g = geom(c);
     const bool cm = c->cfg.comoving && c->nspecies > 0;
     if (cm) {
-        k_motional<<<blocks_for(c->N), kB, 0, st>>>(g, c->u, c->B, c->cfg.c, c->EM);
+        k_motional<<<node_blocks(c->N), node_threads(c->N), 0, st>>>(g, c->u, c->B, c->cfg.c, c->EM);
         GX_LAUNCHED(c);
     }
     const double ctd = c->cfg.c * c->cfg.theta * c->cfg.dt;
@@ -780,14 +788,14 @@ int gx_build_rhs(gx_ctx *c, cudaStream_t st) {
     const double *Bc = c->B;
     if (c->cfg.lf_on) {
         double *D = c->dBlf, *Bt = c->dBlf + 3 * c->N, *Ff = c->dBlf + 6 * c->N;
-        k_lf_flux<<<blocks_for(c->N), kB, 0, st>>>(g, c->B, c->u, c->cfg.c, c->cfg.dt, c->cfg.lf_beta,
+        k_lf_flux<<<node_blocks(c->N), node_threads(c->N), 0, st>>>(g, c->B, c->u, c->cfg.c, c->cfg.dt, c->cfg.lf_beta,
                                                    c->cfg.lf_speed_c, Ff);
         GX_LAUNCHED(c);
-        k_lf_b<<<blocks_for(c->N), kB, 0, st>>>(g, c->B, Ff, c->cfg.theta, D, Bt);
+        k_lf_b<<<node_blocks(c->N), node_threads(c->N), 0, st>>>(g, c->B, Ff, c->cfg.theta, D, Bt);
         GX_LAUNCHED(c);
         if (!c->cfg.lf_rhs_printed) Bc = Bt;   // the printed Eq. 7 curls B^n alone
     }
-    k_rhs<<<blocks_for(c->N), kB, 0, st>>>(g, c->E, Bc, c->J, c->M, cm ? c->EM : nullptr, ctd, jf, jf / c->dV,
+    k_rhs<<<node_blocks(c->N), node_threads(c->N), 0, st>>>(g, c->E, Bc, c->J, c->M, cm ? c->EM : nullptr, ctd, jf, jf / c->dV,
                                            c->rhs);
     GX_LAUNCHED(c);
     return GX_OK;
@@ -796,7 +804,7 @@ int gx_build_rhs(gx_ctx *c, cudaStream_t st) {
 int gx_build_kappa(gx_ctx *c, cudaStream_t st) {
     if (c->dim == 3) return gx3_build_kappa(c, st);
     if (!c->cfg.lf_on || c->cfg.nsmooth_e > 0) return GX_OK;
-    k_kappa<<<blocks_for(c->N), kB, 0, st>>>(geom(c), c->E, c->u, c->cfg.lf_beta, c->cfg.lf_speed_c, c->cfg.c,
+    k_kappa<<<node_blocks(c->N), node_threads(c->N), 0, st>>>(geom(c), c->E, c->u, c->cfg.lf_beta, c->cfg.lf_speed_c, c->cfg.c,
                                               c->kappa, c->kappa32);
     GX_LAUNCHED(c);
     return GX_OK;
@@ -804,34 +812,34 @@ int gx_build_kappa(gx_ctx *c, cudaStream_t st) {
 
 int gx_apply_A(gx_ctx *c, const double *x, double *y, cudaStream_t st) {
     if (c->dim == 3) return gx3_apply_A(c, x, y, st);
-    k_matvec<<<blocks_for(c->N), kB, 0, st>>>(opargs(c), x, y, nullptr, 0, nullptr);
+    k_matvec<<<node_blocks(c->N), node_threads(c->N), 0, st>>>(opargs(c), x, y, nullptr, 0, nullptr);
     GX_LAUNCHED(c);
     return GX_OK;
 }
 
 int gx_apply_A_j(gx_ctx *c, const double *base, int64_t stride, const int *jptr, const int *doneptr, double *y,
                  cudaStream_t st) {
-    k_matvec<<<blocks_for(c->N), kB, 0, st>>>(opargs(c), base, y, jptr, stride, doneptr);
+    k_matvec<<<node_blocks(c->N), node_threads(c->N), 0, st>>>(opargs(c), base, y, jptr, stride, doneptr);
     GX_LAUNCHED(c);
     return GX_OK;
 }
 
 int gx_build_jacobi(gx_ctx *c, cudaStream_t st) {
     if (c->dim == 3) return gx3_build_jacobi(c, true, st);
-    k_jacobi<<<blocks_for(c->N), kB, 0, st>>>(opargs(c), c->jdiag, c->jdiag32);
+    k_jacobi<<<node_blocks(c->N), node_threads(c->N), 0, st>>>(opargs(c), c->jdiag, c->jdiag32);
     GX_LAUNCHED(c);
     return GX_OK;
 }
 
 int gx_build_jacobi32(gx_ctx *c, cudaStream_t st) {
     if (c->dim == 3) return gx3_build_jacobi(c, false, st);
-    k_jacobi<<<blocks_for(c->N), kB, 0, st>>>(opargs(c), nullptr, c->jdiag32);
+    k_jacobi<<<node_blocks(c->N), node_threads(c->N), 0, st>>>(opargs(c), nullptr, c->jdiag32);
     GX_LAUNCHED(c);
     return GX_OK;
 }
 
 int gx_apply_jacobi(gx_ctx *c, const double *x, double *y, cudaStream_t st) {
-    k_apply_jacobi<<<blocks_for(c->N), kB, 0, st>>>(c->N, c->jdiag, x, y);
+    k_apply_jacobi<<<node_blocks(c->N), node_threads(c->N), 0, st>>>(c->N, c->jdiag, x, y);
     GX_LAUNCHED(c);
     return GX_OK;
 }
@@ -839,7 +847,7 @@ int gx_apply_jacobi(gx_ctx *c, const double *x, double *y, cudaStream_t st) {
 int gx_initial_guess(gx_ctx *c, cudaStream_t st) {
     const double th = c->cfg.theta;
     const double f = (c->have_eth && th < 1.0) ? th / (1.0 - th) : 0.0;
-    k_guess<<<blocks_for(3 * c->N), kB, 0, st>>>(3 * c->N, c->E, c->Eth, f);
+    k_guess<<<node_blocks(3 * c->N), node_threads(3 * c->N), 0, st>>>(3 * c->N, c->E, c->Eth, f);
     GX_LAUNCHED(c);
     return GX_OK;
 }
@@ -847,7 +855,7 @@ int gx_initial_guess(gx_ctx *c, cudaStream_t st) {
 int gx_advance(gx_ctx *c, cudaStream_t st) {
     if (c->dim == 3) return gx3_advance(c, st);
     // the LF increment D was computed from B^n and u when the right-hand side was built
-    k_advance<<<blocks_for(c->N), kB, 0, st>>>(geom(c), c->E, c->B, c->Eth, c->cfg.c, c->cfg.dt, c->cfg.theta,
+    k_advance<<<node_blocks(c->N), node_threads(c->N), 0, st>>>(geom(c), c->E, c->B, c->Eth, c->cfg.c, c->cfg.dt, c->cfg.theta,
                                                c->cfg.lf_on ? c->dBlf : nullptr, c->phi, c->Enew, c->Bnew);
     GX_LAUNCHED(c);
     if (c->phi) {
@@ -855,7 +863,7 @@ int gx_advance(gx_ctx *c, cudaStream_t st) {
         const double dxmin = std::min(c->n[0] > 1 ? c->cfg.dx[0] : 1e300, c->n[1] > 1 ? c->cfg.dx[1] : 1e300);
         if (dxmin < 1e300) {
             const double ch = 0.8 * dxmin / c->cfg.dt;
-            k_divb_phi<<<blocks_for(c->N), kB, 0, st>>>(geom(c), c->Bnew, c->cfg.dt * ch * ch, std::exp(-0.1), c->phi);
+            k_divb_phi<<<node_blocks(c->N), node_threads(c->N), 0, st>>>(geom(c), c->Bnew, c->cfg.dt * ch * ch, std::exp(-0.1), c->phi);
             GX_LAUNCHED(c);
         }
     }
@@ -864,16 +872,16 @@ int gx_advance(gx_ctx *c, cudaStream_t st) {
 }
 
 int gx_gl_potential(gx_ctx *c, cudaStream_t st) {
-    k_gl_residual<<<blocks_for(c->N), kB, 0, st>>>(geom(c), c->E, c->rho, c->tmp3);
+    k_gl_residual<<<node_blocks(c->N), node_threads(c->N), 0, st>>>(geom(c), c->E, c->rho, c->tmp3);
     GX_LAUNCHED(c);
-    k_gl_phi<<<blocks_for(c->N), kB, 0, st>>>(geom(c), c->tmp3, c->nE);
+    k_gl_phi<<<node_blocks(c->N), node_threads(c->N), 0, st>>>(geom(c), c->tmp3, c->nE);
     GX_LAUNCHED(c);
     return GX_OK;
 }
 
 int gx_copy_uref(gx_ctx *c, int zero, cudaStream_t st);
 int gx_copy_uref(gx_ctx *c, int zero, cudaStream_t st) {
-    k_copy_uref<<<blocks_for(c->N), kB, 0, st>>>(c->N, c->u, c->nUref, c->uref64, zero);
+    k_copy_uref<<<node_blocks(c->N), node_threads(c->N), 0, st>>>(c->N, c->u, c->nUref, c->uref64, zero);
     GX_LAUNCHED(c);
     return GX_OK;
 }
@@ -885,7 +893,7 @@ int gx_diag_run(gx_ctx *c, gx_diag *out, cudaStream_t st) {
         int rc = gx3_diag_grid(c, acc, st);
         if (rc) return rc;
     } else {
-        k_diag_grid<<<blocks_for(c->N), kB, 0, st>>>(geom(c), c->E, c->B, c->moments_valid ? c->rho : nullptr, acc);
+        k_diag_grid<<<node_blocks(c->N), node_threads(c->N), 0, st>>>(geom(c), c->E, c->B, c->moments_valid ? c->rho : nullptr, acc);
         GX_LAUNCHED(c);
     }
     for (int s = 0; s < c->nspecies; ++s) {
